@@ -1,0 +1,271 @@
+"""FP64 brute-force oracle for the recursive transparent-mesh tracer.
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` are the only users.  The CUDA library never
+imports, links or calls anything here, and nothing here touches the library.
+
+The arithmetic lives in ``difftrans_oracle.cpp`` (plain C++, double precision,
+OpenMP over pixels); this module compiles it with g++ on first use and wraps
+its C entry points with ctypes.  Each wrapper names the part of the paper
+(DiffTrans, arXiv 2603.00413) it follows.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "difftrans_oracle.cpp")
+_LIB_PATH = os.path.join(_HERE, "liborc_difftrans.so")
+_lock = threading.Lock()
+_lib = None
+
+# segment flag bits, same meaning as in difftrans_oracle.cpp
+SEG_NEAR_EDGE = 1
+SEG_NEAR_TIE = 2
+SEG_INSIDE = 4
+SEG_TIR = 8
+SEG_BACKFACING = 16
+SEG_NEAR_CRITICAL = 32
+SEG_GRAZING = 64
+SEG_DISCARDED = 128
+SEG_NEAR_POLE = 256
+SEG_MISS = 512
+SEG_DEGENERATE = SEG_NEAR_EDGE | SEG_NEAR_TIE | SEG_NEAR_CRITICAL | SEG_GRAZING | SEG_NEAR_POLE
+
+COUNTER_NAMES = ("segments", "hits", "misses", "discarded", "leaks", "backfacing", "tir", "degenerate")
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into a shared library next to its source."""
+    with _lock:
+        if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+            tmp = _LIB_PATH + ".tmp%d" % os.getpid()
+            cmd = ["g++", "-O2", "-std=c++17", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC]
+            subprocess.run(cmd, check=True)
+            os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        P = ctypes.c_void_p
+        I = ctypes.c_int
+        D = ctypes.c_double
+        U64 = ctypes.c_uint64
+        I64 = ctypes.c_int64
+        lib.orc_vertex_normals.argtypes = [P, I, P, I, P]
+        lib.orc_closest_hit.argtypes = [P, I, P, I, P, P, P, I, D, P, P, P, P, P]
+        lib.orc_interface.argtypes = [P, P, P, P, I, P, P, P, P, P]
+        lib.orc_env_lookup.argtypes = [P, I, I, P, I, P]
+        lib.orc_camera_rays.argtypes = [P, I, I, I, I, U64, I, P, P]
+        lib.orc_pcg_hash.argtypes = [ctypes.c_uint32]
+        lib.orc_pcg_hash.restype = ctypes.c_uint32
+        lib.orc_render.argtypes = [P, I, P, I, D, P, P, I, I, P, I, I, I, I, I, U64, I, D,
+                                   P, P, P, P, P, P, I64, P, P]
+        lib.orc_render_rays.argtypes = [P, I, P, I, D, P, P, I, I, P, P, I, I, D,
+                                        P, P, P, P, P, P, I64, P, P]
+        lib.orc_render_jvp.argtypes = [P, I, P, I, D, P, P, I, I, P, I, I, I, I, I, U64, I, D,
+                                       I, P, P, P, P, P]
+        _lib = lib
+    return _lib
+
+
+def _d(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _i(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def vertex_normals(V, F) -> np.ndarray:
+    """Eq. 13: N_v = (1/3) * sum of unit normals of the faces around v."""
+    V, F = _d(V), _i(F)
+    N = np.zeros_like(V)
+    _load().orc_vertex_normals(_p(V), V.shape[0], _p(F), F.shape[0], _p(N))
+    return N
+
+
+def closest_hit(V, F, o, d, src=None, t_min: float = 1e-5):
+    """Brute-force closest hit over all triangles (Sec. 3.4 step 2)."""
+    V, F, o, d = _d(V), _i(F), _d(o).reshape(-1, 3), _d(d).reshape(-1, 3)
+    n = o.shape[0]
+    s = _i(src) if src is not None else None
+    tri = np.zeros(n, np.int32)
+    t, b1, b2 = np.zeros(n), np.zeros(n), np.zeros(n)
+    fl = np.zeros(n, np.int32)
+    _load().orc_closest_hit(_p(V), V.shape[0], _p(F), F.shape[0], _p(o), _p(d), _p(s), n, t_min,
+                            _p(tri), _p(t), _p(b1), _p(b2), _p(fl))
+    return tri, t, b1, b2, fl
+
+
+def interface(d, n, eta1, eta2):
+    """Sec. 3.3: reflection (Eq. 3), refraction (Eqs. 4-6), TIR, Fresnel
+    (Eqs. 7-8) at one interface.  d: incoming direction, n: shading normal on
+    the incoming side."""
+    d, n = _d(d).reshape(-1, 3), _d(n).reshape(-1, 3)
+    m = d.shape[0]
+    e1 = _d(np.broadcast_to(eta1, (m,)))
+    e2 = _d(np.broadcast_to(eta2, (m,)))
+    wr, wt = np.zeros((m, 3)), np.zeros((m, 3))
+    R, T = np.zeros(m), np.zeros(m)
+    tir = np.zeros(m, np.int32)
+    _load().orc_interface(_p(d), _p(n), _p(e1), _p(e2), m, _p(wr), _p(wt), _p(R), _p(T), _p(tir))
+    return wr, wt, R, T, tir.astype(bool)
+
+
+def env_lookup(env, dirs) -> np.ndarray:
+    """Bilinear equirectangular lookup (Sec. 3.4 step 3 with an environment map)."""
+    env = _d(env)
+    H, W = env.shape[0], env.shape[1]
+    dirs = _d(dirs).reshape(-1, 3)
+    out = np.zeros_like(dirs)
+    _load().orc_env_lookup(_p(env), W, H, _p(dirs), dirs.shape[0], _p(out))
+    return out
+
+
+def camera_rays(cam, spp: int = 1, jitter: int = 0, seed: int = 0, view: int = 0):
+    """Pinhole camera rays of one view, ray index (py*W + px)*spp + s."""
+    c = _d(cam.as_array())
+    n = cam.width * cam.height * spp
+    o, d = np.zeros((n, 3)), np.zeros((n, 3))
+    _load().orc_camera_rays(_p(c), cam.width, cam.height, spp, jitter, seed, view, _p(o), _p(d))
+    return o, d
+
+
+def pcg_hash(v: int) -> int:
+    return int(_load().orc_pcg_hash(ctypes.c_uint32(v & 0xFFFFFFFF)))
+
+
+def _common(V, F, ior, sigma, env, cam):
+    return _d(V), _i(F), float(ior), _d(sigma).reshape(3), _d(env), _d(cam.as_array())
+
+
+def render(V, F, ior, sigma, env, cam, max_depth: int, spp: int = 1, jitter: int = 0, seed: int = 0,
+           view: int = 0, t_min: float = 1e-5, segments: bool = False) -> dict:
+    """FP64 render of one view: the recursive ray tree of Sec. 3.4 steps 1-5.
+
+    Returns dict(img [H,W,3], discard [H,W,3], pix_flags [H,W], pix_sig [H,W],
+    counters {...}) and, with segments=True, seg_i [n,4] = (ray, heap node,
+    tri, flags) and seg_f [n,9] = (t, b1, b2, origin xyz, direction xyz).
+    discard is the path weight lost to the depth limit or to a backfacing
+    shading normal."""
+    V, F, ior, sigma, env, c = _common(V, F, ior, sigma, env, cam)
+    H, W = cam.height, cam.width
+    img = np.zeros((H * W, 3))
+    disc = np.zeros((H * W, 3))
+    pf = np.zeros(H * W, np.int32)
+    sig = np.zeros(H * W, np.uint64)
+    cnt = np.zeros(8, np.int64)
+    nseg = np.zeros(1, np.int64)
+    lib = _load()
+    args = (_p(V), V.shape[0], _p(F), F.shape[0], ior, _p(sigma), _p(env), env.shape[1], env.shape[0],
+            _p(c), W, H, int(max_depth), int(spp), int(jitter), int(seed), int(view), float(t_min),
+            _p(img), _p(disc), _p(pf), _p(sig))
+    seg_i, seg_f = _run_with_segments(lib.orc_render, args, segments, nseg, cnt)
+    out = dict(img=img.reshape(H, W, 3), discard=disc.reshape(H, W, 3), pix_flags=pf.reshape(H, W),
+               pix_sig=sig.reshape(H, W), counters=dict(zip(COUNTER_NAMES, cnt.tolist())))
+    if segments:
+        out["seg_i"], out["seg_f"] = seg_i, seg_f
+    return out
+
+
+def _run_with_segments(fn, args, segments, nseg, cnt):
+    if not segments:
+        fn(*args, None, None, 0, None, _p(cnt))
+        return None, None
+    fn(*args, None, None, 0, _p(nseg), _p(cnt))
+    n = int(nseg[0])
+    seg_i = np.zeros((max(n, 1), 4), np.int32)
+    seg_f = np.zeros((max(n, 1), 9))
+    fn(*args, _p(seg_i), _p(seg_f), n, _p(nseg), _p(cnt))
+    return seg_i[:n], seg_f[:n]
+
+
+def render_rays(V, F, ior, sigma, env, o, d, max_depth: int, t_min: float = 1e-5,
+                segments: bool = False) -> dict:
+    """The same FP64 ray tree for arbitrary primary rays (o, d: [n,3], d
+    unit), one sample each.  Outputs as render() with pixels = rays."""
+    V, F = _d(V), _i(F)
+    sigma, env = _d(sigma).reshape(3), _d(env)
+    o, d = _d(o).reshape(-1, 3), _d(d).reshape(-1, 3)
+    n = o.shape[0]
+    img = np.zeros((n, 3))
+    disc = np.zeros((n, 3))
+    pf = np.zeros(n, np.int32)
+    sig = np.zeros(n, np.uint64)
+    cnt = np.zeros(8, np.int64)
+    nseg = np.zeros(1, np.int64)
+    lib = _load()
+    args = (_p(V), V.shape[0], _p(F), F.shape[0], float(ior), _p(sigma), _p(env), env.shape[1], env.shape[0],
+            _p(o), _p(d), n, int(max_depth), float(t_min), _p(img), _p(disc), _p(pf), _p(sig))
+    seg_i, seg_f = _run_with_segments(lib.orc_render_rays, args, segments, nseg, cnt)
+    out = dict(img=img, discard=disc, pix_flags=pf, pix_sig=sig, counters=dict(zip(COUNTER_NAMES, cnt.tolist())))
+    if segments:
+        out["seg_i"], out["seg_f"] = seg_i, seg_f
+    return out
+
+
+def render_jvp(V, F, ior, sigma, env, cam, max_depth: int, tV=None, tior=None, tsigma=None,
+               spp: int = 1, jitter: int = 0, seed: int = 0, view: int = 0, t_min: float = 1e-5):
+    """Forward-mode derivative of the FP64 render along ntan directions at
+    fixed events.  tV: [ntan, nv, 3], tior: [ntan], tsigma: [ntan, 3].
+    Returns (img [H,W,3], dimg [ntan,H,W,3])."""
+    V, F, ior, sigma, env, c = _common(V, F, ior, sigma, env, cam)
+    nt = None
+    for a in (tV, tior, tsigma):
+        if a is not None:
+            nt = np.asarray(a).shape[0]
+    assert nt is not None and nt > 0
+    tV = _d(tV) if tV is not None else None
+    tior = _d(tior) if tior is not None else None
+    tsigma = _d(tsigma) if tsigma is not None else None
+    H, W = cam.height, cam.width
+    img = np.zeros((H * W, 3))
+    dimg = np.zeros((nt, H * W, 3))
+    _load().orc_render_jvp(_p(V), V.shape[0], _p(F), F.shape[0], ior, _p(sigma), _p(env), env.shape[1],
+                           env.shape[0], _p(c), W, H, int(max_depth), int(spp), int(jitter), int(seed),
+                           int(view), float(t_min), nt, _p(tV), _p(tior), _p(tsigma), _p(img), _p(dimg))
+    return img.reshape(H, W, 3), dimg.reshape(nt, H, W, 3)
+
+
+def grad_full(V, F, ior, sigma, env, cam, max_depth: int, g, vert_subset=None, chunk: int = 64, **kw):
+    """Gradient of J = sum(g * I) w.r.t. (V, ior, sigma) by forward mode over
+    every parameter (one tangent per coordinate).  vert_subset limits the
+    vertex coordinates probed (others reported as 0).  Slow; small cases only.
+    Returns (dV [nv,3], dior, dsigma [3])."""
+    V = _d(V)
+    nv = V.shape[0]
+    g = _d(g)
+    verts = np.arange(nv) if vert_subset is None else np.asarray(vert_subset)
+    coords = [(int(v), a) for v in verts for a in range(3)]
+    dV = np.zeros((nv, 3))
+    # ior and sigma first
+    tior = np.array([1.0, 0, 0, 0])
+    tsig = np.zeros((4, 3))
+    tsig[1, 0] = tsig[2, 1] = tsig[3, 2] = 1.0
+    _, dimg = render_jvp(V, F, ior, sigma, env, cam, max_depth, None, tior, tsig, **kw)
+    J = np.einsum("khwc,hwc->k", dimg, g)
+    dior, dsig = J[0], J[1:4]
+    for s in range(0, len(coords), chunk):
+        part = coords[s:s + chunk]
+        tV = np.zeros((len(part), nv, 3))
+        for j, (v, a) in enumerate(part):
+            tV[j, v, a] = 1.0
+        _, dimg = render_jvp(V, F, ior, sigma, env, cam, max_depth, tV, None, None, **kw)
+        J = np.einsum("khwc,hwc->k", dimg, g)
+        for j, (v, a) in enumerate(part):
+            dV[v, a] = J[j]
+    return dV, float(dior), dsig

@@ -1,0 +1,494 @@
+"""Pins of the FP64 oracle to facts fixed by optics, geometry and calculus.
+
+Each test checks the oracle against something other than itself: Fresnel's
+sine/tangent laws (a different closed form from the one the oracle codes),
+Snell's law and the reflection law as geometric facts, the critical and
+Brewster angles, exact invariants of the ray tree (IoR 1 reproduces the
+environment; R + T = 1 conserves energy), closed-form light paths through a
+slab and a sphere, an independent ray/triangle intersection, and central
+finite differences for the forward-mode derivatives.  A plausible slip in the
+oracle (a dropped term, a wrong sign or index, a swapped eta) fails one.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2603_00413_gb300 import scenes as S
+
+
+def _unit(v):
+    v = np.asarray(v, dtype=np.float64)
+    return v / np.linalg.norm(v, axis=-1, keepdims=True)
+
+
+def _configs(rng, theta):
+    """Incoming directions d at angle theta to the normal n (d . n = -cos)."""
+    m = theta.size
+    n = _unit(rng.normal(size=(m, 3)))
+    t = _unit(np.cross(n, rng.normal(size=(m, 3))))
+    d = -(np.cos(theta)[:, None] * n) + np.sin(theta)[:, None] * t
+    return _unit(d), n
+
+
+# ---------------------------------------------------------------------------
+# Sec. 3.3: Eqs. 3-8 at one interface
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("eta1,eta2", [(1.0, 1.5), (1.0, 1.3), (1.5, 1.0), (1.7, 1.0), (1.0, 1.0 / 1.5)])
+def test_fresnel_matches_sine_and_tangent_laws(eta1, eta2):
+    """Fresnel's laws in angle form: Rs = sin^2(ti-tt)/sin^2(ti+tt),
+    Rp = tan^2(ti-tt)/tan^2(ti+tt) (Hecht, Optics, Sec. 4.6)."""
+    rng = np.random.default_rng(1)
+    crit = math.asin(eta2 / eta1) if eta2 < eta1 else math.pi / 2
+    th = rng.uniform(math.radians(1.0), min(math.radians(85.0), crit - 1e-3), size=200)
+    d, n = _configs(rng, th)
+    wr, wt, R, T, tir = O.interface(d, n, eta1, eta2)
+    assert not tir.any()
+    tt = np.arcsin(eta1 * np.sin(th) / eta2)
+    Rs = np.sin(th - tt) ** 2 / np.sin(th + tt) ** 2
+    Rp = np.tan(th - tt) ** 2 / np.tan(th + tt) ** 2
+    np.testing.assert_allclose(R, 0.5 * (Rs + Rp), rtol=1e-10, atol=1e-14)
+    np.testing.assert_allclose(R + T, 1.0, rtol=0, atol=1e-15)
+    assert (R >= 0).all() and (R <= 1).all()
+
+
+@pytest.mark.parametrize("eta1,eta2", [(1.0, 1.5), (1.5, 1.0)])
+def test_normal_incidence(eta1, eta2):
+    """At normal incidence R = ((n1-n2)/(n1+n2))^2 = 0.04 for glass, and the
+    refracted ray continues straight."""
+    n = _unit(np.array([[0.3, -0.2, 0.9]]))
+    wr, wt, R, T, tir = O.interface(-n, n, eta1, eta2)
+    assert R[0] == pytest.approx(0.04, abs=1e-15)
+    np.testing.assert_allclose(wt[0], -n[0], atol=1e-15)
+    np.testing.assert_allclose(wr[0], n[0], atol=1e-15)
+
+
+def test_brewster_angle_kills_p_polarisation():
+    """At theta_B = atan(n2/n1) the p-term vanishes: R = Rs/2 exactly."""
+    for eta1, eta2 in [(1.0, 1.5), (1.5, 1.0), (1.0, 1.33)]:
+        th = math.atan(eta2 / eta1)
+        d, n = _configs(np.random.default_rng(2), np.array([th]))
+        _, _, R, _, _ = O.interface(d, n, eta1, eta2)
+        tt = math.asin(eta1 * math.sin(th) / eta2)
+        Rs = math.sin(th - tt) ** 2 / math.sin(th + tt) ** 2
+        assert abs(th + tt - math.pi / 2) < 1e-12
+        assert R[0] == pytest.approx(0.5 * Rs, rel=1e-12)
+
+
+@pytest.mark.parametrize("eta1,eta2", [(1.0, 1.5), (1.5, 1.0), (1.3, 1.0)])
+def test_snell_reflection_law_and_coplanarity(eta1, eta2):
+    rng = np.random.default_rng(3)
+    crit = math.asin(eta2 / eta1) if eta2 < eta1 else math.pi / 2
+    th = rng.uniform(0.01, min(1.5, crit - 1e-3), size=300)
+    d, n = _configs(rng, th)
+    wr, wt, R, T, tir = O.interface(d, n, eta1, eta2)
+    wi = -d
+    # reflection: equal angles, unit length, wr + wi along n
+    np.testing.assert_allclose(np.einsum("ij,ij->i", wr, n), np.einsum("ij,ij->i", wi, n), atol=1e-14)
+    np.testing.assert_allclose(np.linalg.norm(wr, axis=1), 1.0, atol=1e-14)
+    np.testing.assert_allclose(np.linalg.norm(np.cross(wr + wi, n), axis=1), 0.0, atol=1e-14)
+    # refraction: unit, crosses to the other side, coplanar, Snell
+    np.testing.assert_allclose(np.linalg.norm(wt, axis=1), 1.0, atol=1e-14)
+    assert (np.einsum("ij,ij->i", wt, n) < 0).all()
+    np.testing.assert_allclose(np.einsum("ij,ij->i", np.cross(wi, n), wt), 0.0, atol=1e-14)
+    sin_t = np.linalg.norm(np.cross(wt, n), axis=1)
+    np.testing.assert_allclose(eta2 * sin_t, eta1 * np.sin(th), rtol=1e-12)
+
+
+def test_total_internal_reflection_at_critical_angle():
+    """Leaving glass (1.5 -> 1): theta_c = asin(1/1.5) = 41.81 deg; just below
+    it both rays exist and R -> 1, just above only reflection with R = 1."""
+    th_c = math.asin(1.0 / 1.5)
+    assert math.degrees(th_c) == pytest.approx(41.8103149, abs=1e-6)
+    below = np.array([th_c - 1e-4, th_c - 1e-7])
+    above = np.array([th_c + 1e-7, th_c + 1e-2, 1.2])
+    d, n = _configs(np.random.default_rng(4), below)
+    _, wt, R, T, tir = O.interface(d, n, 1.5, 1.0)
+    assert not tir.any()
+    assert R[0] > 0.8 and R[1] > 0.99
+    d, n = _configs(np.random.default_rng(5), above)
+    _, wt, R, T, tir = O.interface(d, n, 1.5, 1.0)
+    assert tir.all()
+    np.testing.assert_array_equal(R, 1.0)
+    np.testing.assert_array_equal(T, 0.0)
+
+
+def test_fresnel_reciprocity_and_grazing():
+    """R(n1 -> n2, theta_i) = R(n2 -> n1, theta_t) (Stokes relations), and
+    R -> 1 at grazing incidence."""
+    rng = np.random.default_rng(6)
+    th = rng.uniform(0.05, 1.4, size=100)
+    d, n = _configs(rng, th)
+    _, wt, R, _, _ = O.interface(d, n, 1.0, 1.5)
+    # reverse path: incoming along -wt from the other side with normal -n
+    _, _, R2, _, tir = O.interface(-wt, -n, 1.5, 1.0)
+    assert not tir.any()
+    np.testing.assert_allclose(R2, R, rtol=1e-10)
+    d, n = _configs(rng, np.array([math.pi / 2 - 1e-6]))
+    _, _, R, _, _ = O.interface(d, n, 1.0, 1.5)
+    assert R[0] > 0.9999
+
+
+# ---------------------------------------------------------------------------
+# Eq. 13: vertex normals
+# ---------------------------------------------------------------------------
+def test_vertex_normals_octahedron_closed_form():
+    """Regular octahedron: four faces with unit normals (+-1,+-1,+-1)/sqrt3
+    meet at (1,0,0), so N = (1/3) * (4/sqrt3, 0, 0)."""
+    V = np.array([[1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]], np.float64)
+    F = []
+    for sx in (0, 1):
+        for sy in (2, 3):
+            for sz in (4, 5):
+                F.append((sx, sy, sz))
+    F = np.array(F, np.int64)
+    a, b, c = V[F[:, 0]], V[F[:, 1]], V[F[:, 2]]
+    flip = np.einsum("ij,ij->i", np.cross(b - a, c - a), a + b + c) < 0
+    F[flip] = F[flip][:, [0, 2, 1]]
+    N = O.vertex_normals(V, F)
+    for i in range(6):
+        np.testing.assert_allclose(N[i], V[i] * 4.0 / (3.0 * math.sqrt(3.0)), atol=1e-15)
+
+
+def test_vertex_normals_icosahedron_closed_form():
+    """Icosahedron: five faces per vertex, each at cos(alpha) = r_in / r_out
+    = phi^2 / (sqrt3 * sqrt(phi * sqrt5)) to the vertex direction, so
+    N_v = (5/3) cos(alpha) v_hat."""
+    V, F = S.icosphere(0)
+    V = V.astype(np.float64)
+    V = V / np.linalg.norm(V, axis=1, keepdims=True)
+    phi = (1 + math.sqrt(5)) / 2
+    cos_a = phi ** 2 / (math.sqrt(3) * math.sqrt(phi * math.sqrt(5)))
+    N = O.vertex_normals(V, F)
+    np.testing.assert_allclose(N, V * (5.0 / 3.0) * cos_a, atol=2e-7)  # V came through float32
+
+
+def test_vertex_normals_flat_grid_interior():
+    """A vertex strictly inside a flat grid face touches six coplanar
+    triangles: N = (6/3) n = 2 n."""
+    V, F = S.box_grid(3)
+    N = O.vertex_normals(V, F)
+    V = V.astype(np.float64)
+    interior = (np.abs(V) < 0.999).sum(axis=1) == 2
+    assert interior.sum() == 6 * 4
+    for i in np.nonzero(interior)[0]:
+        n = np.where(np.abs(V[i]) > 0.999, np.sign(V[i]), 0.0)
+        np.testing.assert_allclose(N[i], 2.0 * n, atol=1e-15)
+
+
+# ---------------------------------------------------------------------------
+# Sec. 3.4 step 2: closest hit, against an independent intersection
+# ---------------------------------------------------------------------------
+def _closest_hit_by_areas(V, F, o, d, t_min):
+    """Plane intersection plus signed-area barycentrics, all triangles."""
+    V = V.astype(np.float64)
+    a, b, c = V[F[:, 0]], V[F[:, 1]], V[F[:, 2]]
+    n = np.cross(b - a, c - a)
+    nn = np.einsum("ij,ij->i", n, n)
+    out = []
+    for oi, di in zip(o, d):
+        den = n @ di
+        with np.errstate(divide="ignore", invalid="ignore"):
+            t = np.einsum("ij,ij->i", a - oi, n) / den
+        p = oi + t[:, None] * di
+        wa = np.einsum("ij,ij->i", np.cross(b - p, c - p), n) / nn
+        wb = np.einsum("ij,ij->i", np.cross(c - p, a - p), n) / nn
+        wc = 1.0 - wa - wb
+        ok = (t > t_min) & (wa >= 0) & (wb >= 0) & (wc >= 0) & (den != 0)
+        if not ok.any():
+            out.append((-1, 0, 0, 0))
+            continue
+        idx = np.nonzero(ok)[0]
+        k = idx[np.argmin(t[idx])]
+        out.append((k, t[k], wb[k], wc[k]))
+    return out
+
+
+def test_closest_hit_matches_area_barycentrics():
+    V, F = S.icosphere(2)
+    rng = np.random.default_rng(7)
+    m = 400
+    o = rng.uniform(-2.5, 2.5, size=(m, 3))
+    o[: m // 2] = _unit(rng.normal(size=(m // 2, 3))) * rng.uniform(0, 0.85, size=(m // 2, 1))
+    d = _unit(rng.normal(size=(m, 3)))
+    tri, t, b1, b2, fl = O.closest_hit(V, F, o, d, None, 1e-5)
+    ref = _closest_hit_by_areas(V, F, o, d, 1e-5)
+    checked = 0
+    for i in range(m):
+        if fl[i] & (O.SEG_NEAR_EDGE | O.SEG_NEAR_TIE):
+            continue
+        checked += 1
+        assert tri[i] == ref[i][0]
+        if tri[i] >= 0:
+            assert t[i] == pytest.approx(ref[i][1], rel=1e-10)
+            assert b1[i] == pytest.approx(ref[i][2], abs=1e-10)
+            assert b2[i] == pytest.approx(ref[i][3], abs=1e-10)
+    assert checked > 0.95 * m
+    assert (tri[: m // 2] >= 0).all()  # rays from inside a closed mesh always hit
+
+
+def test_closest_hit_skips_source_and_respects_t_min():
+    V = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1], [1, 0, 1], [0, 1, 1]], np.float64)
+    F = np.array([[0, 1, 2], [3, 4, 5]], np.int32)
+    o = np.array([[0.2, 0.2, 0.0], [0.2, 0.2, 0.0], [0.2, 0.2, -1e-6]])
+    d = np.array([[0, 0, 1.0], [0, 0, 1.0], [0, 0, 1.0]])
+    tri, t, *_ = O.closest_hit(V, F, o, d, np.array([0, -1, -1]), 1e-5)
+    assert list(tri) == [1, 1, 1]  # the start triangle is skipped / within t_min
+    assert t[0] == pytest.approx(1.0)
+
+
+# ---------------------------------------------------------------------------
+# environment lookup
+# ---------------------------------------------------------------------------
+def test_env_lookup_texel_centres_midpoints_and_wrap():
+    W, H = 16, 8
+    rng = np.random.default_rng(8)
+    env = rng.uniform(0.1, 2.0, size=(H, W, 3))
+    TH, PH = S.texel_directions(W, H)
+    dirs = np.stack([np.sin(TH) * np.cos(PH), np.cos(TH), np.sin(TH) * np.sin(PH)], -1).reshape(-1, 3)
+    np.testing.assert_allclose(O.env_lookup(env, dirs), env.reshape(-1, 3), rtol=1e-12)
+    # halfway between columns j and j+1 of row i: the average
+    i, j = 3, 5
+    th = (i + 0.5) / H * math.pi
+    ph = (j + 1.0) / W * 2 * math.pi
+    dd = np.array([[math.sin(th) * math.cos(ph), math.cos(th), math.sin(th) * math.sin(ph)]])
+    np.testing.assert_allclose(O.env_lookup(env, dd)[0], 0.5 * (env[i, j] + env[i, j + 1]), rtol=1e-12)
+    # phi = 0 (+x) sits halfway between the last and the first column
+    dd = np.array([[math.sin(th), math.cos(th), 0.0]])
+    np.testing.assert_allclose(O.env_lookup(env, dd)[0], 0.5 * (env[i, 0] + env[i, W - 1]), rtol=1e-12)
+    # continuity across the seam
+    eps = 1e-9
+    a = O.env_lookup(env, np.array([[math.cos(eps), 0.0, math.sin(eps)]]))
+    b = O.env_lookup(env, np.array([[math.cos(-eps), 0.0, math.sin(-eps)]]))
+    np.testing.assert_allclose(a, b, atol=1e-7)
+    # poles: clamped rows
+    np.testing.assert_allclose(O.env_lookup(env, np.array([[0, 1.0, 0]]))[0],
+                               O.env_lookup(env, np.array([[1e-12, 1.0, 0]]))[0], atol=1e-9)
+    const = S.constant_env(W, H, (0.25, 0.5, 0.75))
+    np.testing.assert_allclose(O.env_lookup(const, _unit(rng.normal(size=(50, 3)))),
+                               np.tile([0.25, 0.5, 0.75], (50, 1)), rtol=1e-15)
+
+
+# ---------------------------------------------------------------------------
+# camera
+# ---------------------------------------------------------------------------
+def test_camera_geometry():
+    cam = S.camera((1.0, 2.0, 3.0), (0.0, 0.5, 0.0), (0, 1, 0), 45.0, 65, 33)
+    o, d = O.camera_rays(cam)
+    fwd = _unit(np.array(cam.at) - np.array(cam.eye))
+    right = _unit(np.cross(fwd, cam.up))
+    up = np.cross(right, fwd)
+    D = d.reshape(33, 65, 3)
+    np.testing.assert_allclose(D[16, 32], fwd, atol=1e-15)          # centre pixel
+    np.testing.assert_allclose(np.linalg.norm(d, axis=1), 1.0, atol=1e-15)
+    np.testing.assert_allclose(o, np.tile(cam.eye, (o.shape[0], 1)))
+    assert D[0, 32] @ up > 0 and D[-1, 32] @ up < 0                  # row 0 on top
+    assert D[16, 0] @ right < 0 and D[16, -1] @ right > 0            # column 0 on the left
+    # mirror symmetry of pixel centres about the optical axis
+    np.testing.assert_allclose(D[0, 32] @ up, -(D[-1, 32] @ up), atol=1e-15)
+    # the rows span the vertical field of view: angle between the first and
+    # last row centres = 2 atan((1 - 1/H) tan(fov/2)) -> fov as H grows
+    tall = S.camera((0, 0, 3.0), (0, 0, 0), (0, 1, 0), 45.0, 1, 4001)
+    _, dt = O.camera_rays(tall)
+    ang = math.acos(np.clip(dt[0] @ dt[-1], -1, 1))
+    assert ang == pytest.approx(math.radians(45.0), abs=2e-4)
+
+
+def test_jitter_offsets_are_uniform_and_deterministic():
+    """The per-sample offsets (a counter-based PCG hash, a convention both
+    sides implement) lie in [0,1)^2, look uniform, and repeat exactly."""
+    cam = S.camera((0, 0, 3.0), width=32, height=32)
+    o1, d1 = O.camera_rays(cam, spp=8, jitter=1, seed=123)
+    o2, d2 = O.camera_rays(cam, spp=8, jitter=1, seed=123)
+    _, d3 = O.camera_rays(cam, spp=8, jitter=1, seed=124)
+    np.testing.assert_array_equal(d1, d2)
+    assert not np.array_equal(d1, d3)
+    _, dc = O.camera_rays(cam)
+    # every jittered ray stays inside its pixel's footprint around the centre ray
+    ang = np.arccos(np.clip(np.einsum("ij,ij->i", d1, np.repeat(dc, 8, axis=0)), -1, 1))
+    pix = 2 * math.tan(math.radians(22.5)) / 32
+    assert ang.max() < pix
+    assert O.pcg_hash(0) != O.pcg_hash(1)
+    vals = np.array([O.pcg_hash(i) >> 8 for i in range(20000)]) / 2.0 ** 24
+    hist, _ = np.histogram(vals, bins=16, range=(0, 1))
+    chi2 = ((hist - 1250.0) ** 2 / 1250.0).sum()
+    assert chi2 < 40.0  # 15 dof, p ~ 5e-4
+
+
+# ---------------------------------------------------------------------------
+# the whole ray tree (Sec. 3.4 steps 1-5)
+# ---------------------------------------------------------------------------
+def test_ior_one_reproduces_environment_and_has_no_vertex_gradient():
+    """IoR 1, no absorption: R = 0, T = 1, refraction is the identity, so
+    every pixel shows E(d_camera) exactly and moving vertices changes nothing."""
+    sc = S.glass_icosphere_scene(width=32, height=32)
+    cam = sc.cams[0]
+    r = O.render(sc.V, sc.F, 1.0, np.zeros(3), sc.env, cam, 4)
+    _, d = O.camera_rays(cam)
+    np.testing.assert_allclose(r["img"].reshape(-1, 3), O.env_lookup(sc.env, d), rtol=1e-12, atol=0)
+    assert r["counters"]["hits"] > 0
+    tV = np.random.default_rng(9).normal(size=(2,) + sc.V.shape)
+    _, dimg = O.render_jvp(sc.V, sc.F, 1.0, np.zeros(3), sc.env, cam, 4, tV=tV)
+    assert np.abs(dimg).max() < 1e-12
+
+
+@pytest.mark.parametrize("which", ["icosphere", "blob"])
+def test_energy_conservation_with_constant_environment(which):
+    """No absorption and a constant environment E: every leaf of the tree is E
+    or lost (depth limit, backfacing), and R + T = 1 splits weight exactly, so
+    pixel = E * (1 - lost weight)."""
+    if which == "icosphere":
+        V, F = S.icosphere(3)
+    else:
+        V, F = S.mesh_from_field(S.random_blob_field(np.random.default_rng(10)), 1500)
+    env = S.constant_env(8, 4, (0.3, 0.6, 0.9))
+    E = env[0, 0].astype(np.float64)
+    cam = S.camera((0.3, 0.8, 2.7), width=24, height=24)
+    r = O.render(V, F, 1.5, np.zeros(3), env, cam, 6)
+    np.testing.assert_allclose(r["img"], E * (1.0 - r["discard"]), rtol=1e-12, atol=1e-14)
+    assert r["counters"]["discarded"] > 0
+
+
+def _slab_series(ior, sigma, h, E, D):
+    """Closed form for a slab at normal incidence: camera ray (depth 0) hits
+    the front face; interior segments of length h alternate between faces,
+    each hit reflecting R0 back inside and transmitting T0 out to E."""
+    R0 = ((ior - 1.0) / (ior + 1.0)) ** 2
+    T0 = 1.0 - R0
+    A = np.exp(-np.asarray(sigma) * h)
+    L_in = np.zeros(3)  # radiance of the interior segment at depth D: 0
+    for k in range(D - 1, 0, -1):
+        L_in = A * (R0 * L_in + T0 * E)
+    return R0 * E + T0 * L_in
+
+
+def _slab_scene(h):
+    V, F = S.box_grid(3, (1.0, 1.0, h / 2))
+    return V, F
+
+
+@pytest.mark.parametrize("D", [1, 2, 5, 8])
+def test_slab_normal_incidence_multiple_reflection_series(D):
+    h = 0.4
+    V, F = _slab_scene(h)
+    sigma = np.array([0.3, 1.0, 2.0])
+    env = S.constant_env(8, 4, (0.3, 0.6, 0.9))
+    E = env[0, 0].astype(np.float64)
+    cam = S.camera((0.1, 0.05, 3.0), (0.1, 0.05, 0.0), (0, 1, 0), 45.0, 1, 1)
+    r = O.render(V, F, 1.5, sigma, env, cam, D, segments=True)
+    expect = _slab_series(1.5, sigma, float(np.float32(h / 2)) * 2, E, D)
+    np.testing.assert_allclose(r["img"][0, 0], expect, rtol=1e-12)
+    inside = (r["seg_i"][:, 3] & O.SEG_INSIDE) != 0
+    np.testing.assert_allclose(r["seg_f"][inside, 0], float(np.float32(h / 2)) * 2, rtol=1e-12)
+
+
+def test_slab_derivatives_match_closed_form():
+    """d(pixel)/d(sigma_c) and d(pixel)/d(IoR) of the slab series (central
+    differences of the closed form) against the oracle's forward mode."""
+    h, D = 0.4, 6
+    V, F = _slab_scene(h)
+    hh = float(np.float32(h / 2)) * 2
+    sigma = np.array([0.3, 1.0, 2.0])
+    env = S.constant_env(8, 4, (0.3, 0.6, 0.9))
+    E = env[0, 0].astype(np.float64)
+    cam = S.camera((0.1, 0.05, 3.0), (0.1, 0.05, 0.0), (0, 1, 0), 45.0, 1, 1)
+    tsig = np.eye(3)
+    tior = np.array([0.0, 0.0, 0.0, 1.0])
+    tsig4 = np.vstack([tsig, np.zeros(3)])
+    _, dimg = O.render_jvp(V, F, 1.5, sigma, env, cam, D, tior=tior, tsigma=tsig4)
+    eps = 1e-6
+    for c in range(3):
+        sp, sm = sigma.copy(), sigma.copy()
+        sp[c] += eps
+        sm[c] -= eps
+        fd = (_slab_series(1.5, sp, hh, E, D) - _slab_series(1.5, sm, hh, E, D)) / (2 * eps)
+        np.testing.assert_allclose(dimg[c, 0, 0], fd, rtol=1e-7, atol=1e-12)
+    fd = (_slab_series(1.5 + eps, sigma, hh, E, D) - _slab_series(1.5 - eps, sigma, hh, E, D)) / (2 * eps)
+    np.testing.assert_allclose(dimg[3, 0, 0], fd, rtol=1e-7, atol=1e-12)
+
+
+def test_slab_oblique_lateral_shift():
+    """Oblique ray through a parallel slab: it leaves parallel to how it came
+    in, shifted sideways by h sin(theta - theta_t) / cos(theta_t), after an
+    interior path of length h / cos(theta_t)."""
+    h, ior = 0.4, 1.5
+    V, F = _slab_scene(h)
+    hh = float(np.float32(h / 2)) * 2
+    th = math.radians(30.0)
+    d = np.array([[math.sin(th), 0.0, -math.cos(th)]])
+    o = np.array([[-0.1 - (3.0 - hh / 2) * math.tan(th), 0.05, 3.0]])
+    r = O.render_rays(V, F, ior, np.zeros(3), S.constant_env(8, 4, (1, 1, 1)), o, d, 3, segments=True)
+    nodes = {int(n): i for i, n in enumerate(r["seg_i"][:, 1])}
+    assert {1, 3, 7} <= set(nodes)
+    assert r["seg_i"][nodes[7], 2] == -1          # the transmitted ray escapes
+    sf = r["seg_f"]
+    tt = math.asin(math.sin(th) / ior)
+    np.testing.assert_allclose(sf[nodes[3], 0], hh / math.cos(tt), rtol=1e-12)
+    d_out = sf[nodes[7], 6:9]
+    np.testing.assert_allclose(d_out, d[0], atol=1e-14)
+    x_out = sf[nodes[7], 3:6]
+    off = x_out - o[0]
+    shift = np.linalg.norm(off - (off @ d[0]) * d[0])
+    assert shift == pytest.approx(hh * math.sin(th - tt) / math.cos(tt), rel=1e-11)
+
+
+def test_sphere_refraction_converges_quadratically():
+    """Rays parallel to -z at impact parameter b on a unit sphere:
+    theta_i = asin(b), theta_t = asin(b / n); interior chord 2 cos(theta_t);
+    deviation after two refractions 2 (theta_i - theta_t).  The icosphere's
+    error must shrink about 4x per subdivision (faceting is O(h^2))."""
+    ior = 1.5
+    rng = np.random.default_rng(11)
+    bs = np.array([0.3, 0.55, 0.7])
+    az = rng.uniform(0, 2 * math.pi, size=bs.size)
+    o = np.stack([bs * np.cos(az), bs * np.sin(az), np.full(bs.size, 3.0)], -1)
+    d = np.tile([0.0, 0.0, -1.0], (bs.size, 1))
+    errs = []
+    for s in (3, 4, 5, 6):
+        V, F = S.icosphere(s)
+        r = O.render_rays(V, F, ior, np.zeros(3), S.constant_env(8, 4, (1, 1, 1)), o, d, 2, segments=True)
+        e = 0.0
+        for k in range(bs.size):
+            m = r["seg_i"][:, 0] == k
+            nodes = {int(n): i for i, n in zip(np.nonzero(m)[0], r["seg_i"][m, 1])}
+            ti, tt = math.asin(bs[k]), math.asin(bs[k] / ior)
+            chord = r["seg_f"][nodes[3], 0]
+            dout = r["seg_f"][nodes[7], 6:9]
+            dev = math.acos(np.clip(dout @ d[k], -1, 1))
+            e = max(e, abs(chord - 2 * math.cos(tt)), abs(dev - 2 * (ti - tt)))
+        errs.append(e)
+    for a, b in zip(errs, errs[1:]):
+        assert b < a / 2.5, errs
+    assert errs[-1] < 2e-3
+
+
+def test_forward_mode_matches_central_differences():
+    """The dual-number derivative of the whole tree equals central finite
+    differences of the value code, on pixels whose event signature (hit ids,
+    inside/outside, TIR) is the same at +h and -h."""
+    sc = S.glass_icosphere_scene(width=24, height=24)
+    sigma = np.array([0.5, 1.0, 1.5])
+    cam = sc.cams[0]
+    rng = np.random.default_rng(12)
+    tV = rng.normal(size=(1,) + sc.V.shape)
+    _, dV = O.render_jvp(sc.V, sc.F, sc.ior, sigma, sc.env, cam, 4, tV=tV)
+    _, dP = O.render_jvp(sc.V, sc.F, sc.ior, sigma, sc.env, cam, 4, tior=np.array([1.0, 0, 0]),
+                         tsigma=np.array([[0, 0, 0], [1.0, 0, 0], [0, 0, 1.0]]))
+    h = 1e-6
+    V64 = sc.V.astype(np.float64)
+    cases = [(V64 + h * tV[0], V64 - h * tV[0], sc.ior, sc.ior, sigma, sigma, dV[0])]
+    cases.append((V64, V64, sc.ior + h, sc.ior - h, sigma, sigma, dP[0]))
+    sp, sm = sigma.copy(), sigma.copy()
+    sp[0] += h
+    sm[0] -= h
+    cases.append((V64, V64, sc.ior, sc.ior, sp, sm, dP[1]))
+    for Vp, Vm, ip, im, sp_, sm_, jvp in cases:
+        a = O.render(Vp, sc.F, ip, sp_, sc.env, cam, 4)
+        b = O.render(Vm, sc.F, im, sm_, sc.env, cam, 4)
+        stable = a["pix_sig"] == b["pix_sig"]
+        assert stable.mean() > 0.9
+        fd = (a["img"] - b["img"]) / (2 * h)
+        scale = np.abs(jvp).max()
+        assert scale > 0
+        np.testing.assert_allclose(jvp[stable], fd[stable], rtol=0, atol=2e-6 * scale)
