@@ -1,0 +1,428 @@
+"""Throughput of the recursive differentiable transparent-mesh tracer on GB300.
+
+Default workload (one GPU): forward+backward of the genus-2 two-tori mesh
+(about 52.5k triangles), 100 views on a Fibonacci sphere at 512x512, depth 8,
+IoR ~ U[1.3,1.7] and per-channel absorption ~ U[0,2] from seed 1, L2 loss
+against a render of the vertices perturbed by N(0, 0.005).  One step =
+vertex normals + LBVH refit + forward render of all views + loss seed +
+backward (all in libdifftrans kernels).  The metric is traced ray segments
+(closest-hit queries) per second over forward+backward.
+
+    python bench.py [--steps K] [--warmup W] [--gpus N] [--impl reference]
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle on a bounded
+sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ray-segments/s fwd and fwd+bwd vs plain kernel; p50/p99 request latency"
+UNIT = "segments/s"
+
+# Algorithmic bytes each kernel must move per unit of work (see the design doc,
+# "Roofline"): the tape and ray records it reads and writes once, the scene
+# data of the hit, and the BVH nodes / triangles the traversal visits.
+RAY_RECORD = 48          # origin+sample, direction+node, throughput+source tri
+HIT_RECORD = 16          # t, b1, b2, tri
+LINK_RECORD = 8          # child index + flags
+NODE_BYTES = 64          # one internal node: two child boxes + child ids
+TRI_BYTES = 48           # v0, e1, e2 of a leaf triangle
+HIT_SCENE = 84           # 3 indices + 3 positions + 3 vertex normals
+ENV_MISS = 4 * 12 + 12   # 4 texels + pixel accumulation
+ADJ_OUT = 36             # (L, obar, dbar) handed to the parent
+ADJ_ATOMICS = 18 * 4     # dV and dN of three vertices
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--views", type=int, default=100)
+    ap.add_argument("--res", type=int, default=512)
+    ap.add_argument("--depth", type=int, default=8)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    ap.add_argument("--cpu-sample", type=int, default=12, help="pixels in the CPU oracle sample")
+    return ap.parse_args()
+
+
+def kernel_sources_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2603_00413_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path))
+    except Exception:
+        return None
+    e = d.get(kernel)
+    if not e or e.get("kernel_sources") != kernel_sources_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def genus2_workload(n_views, res, depth, seed=1):
+    from paper_2603_00413_gb300 import scenes as S
+    sc, Vt = S.genus2_scene(n_views=n_views, width=res, height=res, max_depth=depth, seed=seed)
+    return sc, Vt
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (every 200 ms)."""
+
+    def __init__(self, gpu_index=0):
+        self.rows, self.proc, self.gpu = [], None, gpu_index
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except FileNotFoundError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"]}
+        sm = [float(r[1]) for r in self.rows if len(r) > 8 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 8 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows if len(r) > 8 for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg
+# ---------------------------------------------------------------------------
+def oracle_sample(sc, Vt, n_pix, seed=12345):
+    """A bounded, seeded sample of the workload for the FP64 oracle: n_pix
+    random pixels of the 100 views, traced forward and differentiated
+    (forward mode over every parameter that can influence them)."""
+    import oracle as O
+    rng = np.random.default_rng(seed)
+    views = rng.integers(0, len(sc.cams), size=n_pix)
+    cam0 = sc.cams[0]
+    pix = rng.integers(0, cam0.width * cam0.height, size=n_pix)
+    o = np.zeros((n_pix, 3))
+    d = np.zeros((n_pix, 3))
+    for i, (v, p) in enumerate(zip(views, pix)):
+        oo, dd = O.camera_rays(sc.cams[v])
+        o[i], d[i] = oo[p], dd[p]
+    g = rng.normal(size=(n_pix, 3))
+    t0 = time.perf_counter()
+    dV, dior, dsig, nseg = O.rays_grad(sc.V, sc.F, sc.ior, sc.sigma, sc.env, o, d, sc.max_depth, g)
+    dt = time.perf_counter() - t0
+    return nseg, dt
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count()
+
+
+def run_reference(args):
+    """The reference arm: the FP64 oracle as it stands, on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+    O.build()
+    sc, Vt = genus2_workload(args.views, args.res, args.depth)
+    n_pix = max(1, args.cpu_sample // 3)
+    for w in range(args.warmup):
+        oracle_sample(sc, Vt, n_pix, seed=1000 + w)
+    segs, secs = 0, 0.0
+    for k in range(args.steps):
+        n, t = oracle_sample(sc, Vt, n_pix, seed=2000 + k)
+        segs += n
+        secs += t
+    value = segs / secs
+    sample = (f"{n_pix} seeded pixels per step of the 100-view 512^2 genus-2 workload (depth {args.depth}); "
+              f"forward + gradient by forward mode over the parameters those paths touch")
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000.0 * secs / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "impl": "reference",
+        "config": {"workload": f"genus-2 two-tori mesh {sc.F.shape[0]} triangles, {args.views} views "
+                               f"{args.res}x{args.res}, depth {args.depth}, fwd+bwd; CPU sample", "spp": 1},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+# ---------------------------------------------------------------------------
+# GPU leg
+# ---------------------------------------------------------------------------
+# kernels launched per profiled scope (a scope may hold more than one kernel)
+KERNELS_PER_SCOPE = {"k_vertex_normals": 2, "k_refit": 1, "k_camera": 1, "k_trace": 1, "k_shade": 1,
+                     "k_l2_loss_grad": 1, "k_adjoint": 1, "k_face_normals_backward": 1, "lbvh_build": 14}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as tdist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    from paper_2603_00413_gb300 import build as B
+    B.build()
+    import paper_2603_00413_gb300 as dt
+
+    sc, Vt_np = genus2_workload(args.views, args.res, args.depth)
+    # disjoint view sets per rank (weak scaling): rotate the Fibonacci set
+    if world > 1:
+        from paper_2603_00413_gb300 import scenes as S
+        allc = S.fibonacci_views(args.views * world, 3.0, args.res, args.res)
+        sc.cams = allc[rank::world]
+    res, D = args.res, args.depth
+    nvw = len(sc.cams)
+    V = torch.from_numpy(sc.V).to(dev)
+    F = torch.from_numpy(sc.F).to(dev)
+    ior = torch.tensor([sc.ior], dtype=torch.float32, device=dev)
+    sigma = torch.from_numpy(sc.sigma).to(dev)
+    env = torch.from_numpy(sc.env).to(dev)
+    cams = torch.from_numpy(np.stack([c.as_array() for c in sc.cams])).to(dev)
+    params = dt.Params(D)
+    stream = torch.cuda.current_stream()
+
+    # target images: render of the perturbed vertices
+    Vtt = torch.from_numpy(Vt_np).to(dev)
+    bvh_t = dt.build_bvh(Vtt, F)
+    target, tape_t = dt.render(Vtt, F, bvh_t, dt.vertex_normals(Vtt, F), ior, sigma, env, cams, res, res, params)
+    del tape_t, bvh_t
+    # workspaces sized by a first render, kept for every step
+    bvh = dt.build_bvh(V, F)
+    N = dt.vertex_normals(V, F)
+    img, tape = dt.render(V, F, bvh, N, ior, sigma, env, cams, res, res, params)
+    stats = tape.stats
+    ws = tape.ws
+    bws_bytes = dt.backward_workspace_size(stats["max_level"], V.shape[0])
+    _, bws = dt._aligned_empty(bws_bytes, dev)
+    grad = torch.empty_like(img)
+    loss = torch.empty(1, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
+
+    def step(fwd_only=False):
+        dt.vertex_normals(V, F, out=N)
+        bvh.refit(V, F)
+        out, tp = dt.render(V, F, bvh, N, ior, sigma, env, cams, res, res, params, ws=ws, out=img, check=False)
+        if fwd_only:
+            return None
+        tp.stats = stats
+        dt.l2_loss_grad(out, target, grad=grad, loss=loss)
+        return dt.render_backward(tp, grad, bws=bws)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    chk = dt.read_stats(ws)
+    assert chk["status"] == dt.DT_OK and chk["segments"] == stats["segments"], chk
+
+    # ---- timed fwd+bwd ----------------------------------------------------
+    def timed(fwd_only, k_steps, profile=False):
+        times = []
+        if world > 1:
+            tdist.barrier()
+        torch.cuda.synchronize()
+        if profile:
+            dt.profile_read()
+            dt.profile_enable(True)
+        for _ in range(k_steps):
+            flush.fill_(1.0)  # evict L2 between steps (outside the events)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(fwd_only)
+            e1.record(stream)
+            times.append((e0, e1))
+        torch.cuda.synchronize()
+        prof = None
+        if profile:
+            dt.profile_enable(False)
+            prof = dt.profile_read()
+        ms = [a.elapsed_time(b) for a, b in times]
+        if world > 1:
+            tdist.barrier()
+        return ms, prof
+
+    with ClockSampler(dev.index or 0) as clk:
+        ms, prof = timed(False, args.steps, profile=True)
+    ms_fwd, _ = timed(True, args.steps)
+    total_ms = float(sum(ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    seg = stats["segments"]
+    value = seg * world * args.steps / (total_ms / 1000.0)
+    fwd_value = seg * world * args.steps / (sum(ms_fwd) / 1000.0)
+    chk = dt.read_stats(ws)
+    assert chk["status"] == dt.DT_OK and chk["segments"] == seg, chk
+
+    # ---- roofline of the dominant kernel ---------------------------------
+    peaks = {}
+    pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pp):
+        peaks = json.load(open(pp))
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    kt = {k: v for k, v in prof.items()}
+    dom = max(kt, key=lambda k: kt[k][1])
+    nl = stats["n_levels"]
+    hits, misses = stats["hits"], stats["misses"]
+    spawners = hits - stats["discarded"] - stats["backfacing"]
+    per_step_bytes = {
+        "k_trace": seg * (RAY_RECORD + HIT_RECORD) + stats["nodes_visited"] * NODE_BYTES
+        + stats["tris_tested"] * TRI_BYTES,
+        "k_shade": seg * (RAY_RECORD + HIT_RECORD + LINK_RECORD) + hits * HIT_SCENE + misses * ENV_MISS
+        + (stats["segments"] - nvw * res * res) * RAY_RECORD,
+        "k_adjoint": seg * (RAY_RECORD + HIT_RECORD + LINK_RECORD + ADJ_OUT) + misses * 48
+        + spawners * (HIT_SCENE + 2 * ADJ_OUT + ADJ_ATOMICS),
+    }
+    launches, dom_ms = kt[dom]
+    per_launch_ms = dom_ms / launches
+    bytes_per_launch = per_step_bytes.get(dom, 0) * args.steps / launches
+    achieved = bytes_per_launch / (per_launch_ms / 1000.0) / 1e9
+    traffic = ncu_traffic(dom)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": traffic, "kernel": dom,
+                "peak_source": peak_src, "bytes_per_launch": bytes_per_launch, "ms_per_launch": per_launch_ms}
+    gpu_launches = int(sum(v[0] * KERNELS_PER_SCOPE.get(k, 1) for k, v in kt.items()))
+    kernel_share = {k: round(v[1] / sum(x[1] for x in kt.values()), 4) for k, v in kt.items()}
+
+    # ---- end to end through the public API with host buffers -------------
+    e2e = None
+    if not args.no_e2e:
+        hV = torch.from_numpy(sc.V).pin_memory()
+        hior = torch.tensor([sc.ior], dtype=torch.float32).pin_memory()
+        hsig = torch.from_numpy(sc.sigma).pin_memory()
+        htarget = target.cpu().pin_memory()
+        outV = torch.empty_like(hV).pin_memory()
+        outs = torch.empty(5, dtype=torch.float32).pin_memory()
+        h2d = hV.numel() * 4 + 4 + 12 + htarget.numel() * 4
+        d2h = outV.numel() * 4 + 5 * 4
+
+        def e2e_step():
+            V.copy_(hV, non_blocking=True)
+            ior.copy_(hior, non_blocking=True)
+            sigma.copy_(hsig, non_blocking=True)
+            target.copy_(htarget, non_blocking=True)
+            dV, dior, dsig = step()
+            outV.copy_(dV, non_blocking=True)
+            outs[0:1].copy_(dior, non_blocking=True)
+            outs[1:4].copy_(dsig, non_blocking=True)
+            outs[4:5].copy_(loss, non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        tt = []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e2e_step()
+            torch.cuda.synchronize()
+            tt.append(time.perf_counter() - t0)
+        e2e = {"value": seg * world * args.steps / sum(tt), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle as O
+        O.build()
+        nseg, secs = oracle_sample(sc, Vt_np, args.cpu_sample)
+        cpu = {"value": nseg / secs, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"{args.cpu_sample} seeded pixels of the same workload ({nseg} segments), forward + "
+                         f"gradient by forward mode over the parameters those paths touch, {secs:.1f} s"}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"genus-2 two-tori mesh ({sc.F.shape[0]} triangles), {nvw} views {res}x{res}, "
+                                   f"depth {D}, 1 spp, IoR {sc.ior:.4f}, fwd+bwd of an L2 image loss",
+                       "views": nvw, "width": res, "height": res, "max_depth": D, "triangles": int(sc.F.shape[0]),
+                       "segments_per_step": int(seg), "l2": "flushed by a 512 MB write before every timed step",
+                       "parallelism": f"replicas over disjoint views x{world}"},
+            "fwd_segments_per_s": fwd_value,
+            "ms_per_step_fwd": float(sum(ms_fwd)) / args.steps,
+            "roofline": roofline,
+            "kernel_share": kernel_share,
+            "gpu_launches": gpu_launches,
+            "clocks": clk.summary(),
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "levels": stats["level_count"],
+            "nodes_per_segment": stats["nodes_visited"] / seg,
+            "tris_per_segment": stats["tris_tested"] / seg,
+        }
+        print(json.dumps(out))
+    if world > 1:
+        tdist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

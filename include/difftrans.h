@@ -1,0 +1,267 @@
+/*
+ * difftrans.h -- C ABI of the GB300 (sm_103a) recursive differentiable
+ * transparent-mesh ray tracer of DiffTrans (arXiv 2603.00413).
+ *
+ * Problem statement (Sec. 3.4, "Differentiable Mesh Intersection" and
+ * "Optimization"): a closed triangle mesh M = (V, E, F) with a uniform index
+ * of refraction and an absorption rate is rendered by a recursive ray tracer
+ * (Sec. 3.4 "Recursive Ray Tracing", steps 1-5) whose rays split at every
+ * surface hit into a Fresnel-weighted reflected and a Snell-refracted ray
+ * (Sec. 3.3, Eqs. 3-8), are attenuated inside the object by Beer-Lambert
+ * absorption (Eqs. 9-11), and read the environment where they escape.  The
+ * backward pass returns the gradient of an image loss with respect to the
+ * vertex positions, the IoR and the per-channel absorption.
+ *
+ * Conventions of the whole interface
+ *  - Every pointer named d_* is DEVICE memory of the current CUDA device,
+ *    owned by the caller; every other pointer is host memory owned by the
+ *    caller.  The library allocates no device memory: each call that needs
+ *    workspace takes a caller buffer whose size a *_size query returns.
+ *  - Every call is ordered on the given stream (a cudaStream_t; NULL = the
+ *    legacy default stream) and returns as soon as its work is enqueued.
+ *    Nothing synchronises except dt_read_stats (documented there).
+ *  - FP32 throughout.  Arrays are row-major and tightly packed:
+ *    V float[nv][3], F int32[nf][3] (counter-clockwise seen from outside,
+ *    i.e. (v1 - v0) x (v2 - v0) points out of the object), environment
+ *    float[env_h][env_w][3] equirectangular with +y up (row 0 = +y pole,
+ *    column 0 starts at azimuth 0 = +x, azimuth grows toward +z), images
+ *    float[n_views][height][width][3] with row 0 at the top.
+ *  - Return value: DT_OK, or an error code with a message in dt_last_error()
+ *    (thread-local).  Argument errors are detected on the host before any
+ *    work is enqueued.  Errors that only the GPU can see (a full segment
+ *    arena, a traversal stack overflow) are recorded in the workspace's
+ *    device status word and reported by dt_read_stats; the affected work is
+ *    dropped, never written out of bounds.
+ */
+#ifndef DIFFTRANS_H_
+#define DIFFTRANS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int dt_status;
+#define DT_OK 0
+#define DT_ERR_INVALID_ARG 1
+#define DT_ERR_CUDA 2
+#define DT_ERR_QUEUE_OVERFLOW 3 /* the segment arena was too small */
+#define DT_ERR_STACK_OVERFLOW 4 /* BVH deeper than the traversal stack */
+#define DT_ERR_NOT_IMPLEMENTED 5
+
+typedef void* dt_stream; /* cudaStream_t */
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* dt_last_error(void);
+/* Library version string. */
+const char* dt_version(void);
+
+/* ------------------------------------------------------------------------
+ * Vertex normals, Sec. 3.4 Eq. 13: N_v = (1/3) * sum over the faces f that
+ * contain v of the unit face normal (v_f1 - v_f0) x (v_f2 - v_f0) / |...|.
+ * d_V float[nv][3], d_F int32[nf][3] (every index in [0, nv)), d_N
+ * float[nv][3] is overwritten.  The sums are accumulated in 64-bit fixed
+ * point (2^-40) in d_scratch (>= dt_vertex_normals_scratch_size bytes,
+ * 8-byte aligned, contents undefined afterwards), so the result is the same
+ * bits on every run.  A face of zero area yields NaN normals.
+ * ------------------------------------------------------------------------ */
+dt_status dt_vertex_normals_scratch_size(int32_t nv, size_t* bytes);
+dt_status dt_vertex_normals(const float* d_V, int32_t nv, const int32_t* d_F, int32_t nf, float* d_N,
+                            void* d_scratch, dt_stream stream);
+
+/* Backward of dt_vertex_normals: d_dV[nv][3] += (dN/dV)^T d_dN, for a
+ * gradient d_dN float[nv][3] with respect to the normals.  d_dV is
+ * accumulated into, not overwritten. */
+dt_status dt_vertex_normals_backward(const float* d_V, int32_t nv, const int32_t* d_F, int32_t nf,
+                                     const float* d_dN, float* d_dV, dt_stream stream);
+
+/* ------------------------------------------------------------------------
+ * LBVH over the triangles (the paper traces with OptiX, Sec. 3.4; this
+ * acceleration structure is the library's own): 30-bit Morton codes of the
+ * triangle centroids, a stable radix sort, the Karras (2012) binary
+ * hierarchy with one triangle per leaf, then bottom-up bounds.
+ *
+ * dt_bvh_size: bytes of the BVH buffer and of the build scratch for nf
+ *   triangles (nf >= 1).
+ * dt_build_bvh: builds into d_bvh (>= bvh_bytes, 256-byte aligned) using
+ *   d_scratch (>= scratch_bytes, 256-byte aligned, contents undefined
+ *   afterwards).  The BVH keeps no pointer to V or F.
+ * dt_refit_bvh: recomputes the bounds and the stored triangle data of an
+ *   existing BVH for moved vertices (same F, same nf), keeping the
+ *   hierarchy; d_scratch as for the build.
+ * ------------------------------------------------------------------------ */
+dt_status dt_bvh_size(int32_t nf, size_t* bvh_bytes, size_t* scratch_bytes);
+dt_status dt_build_bvh(const float* d_V, int32_t nv, const int32_t* d_F, int32_t nf, void* d_bvh,
+                       void* d_scratch, dt_stream stream);
+dt_status dt_refit_bvh(const float* d_V, int32_t nv, const int32_t* d_F, int32_t nf, void* d_bvh,
+                       void* d_scratch, dt_stream stream);
+
+/* ------------------------------------------------------------------------
+ * Scene, views and parameters of a render.
+ * ------------------------------------------------------------------------ */
+typedef struct dt_scene {
+  const float* d_V;     /* float[nv][3] vertex positions */
+  const int32_t* d_F;   /* int32[nf][3] */
+  int32_t nv, nf;
+  const void* d_bvh;    /* built (or refitted) for exactly these V and F */
+  const float* d_N;     /* float[nv][3] vertex normals of V (dt_vertex_normals) */
+  const float* d_ior;   /* float[1]: index of refraction of the object (outside = 1) */
+  const float* d_sigma; /* float[3]: absorption rate per channel inside the object */
+  const float* d_env;   /* float[env_h][env_w][3] environment */
+  int32_t env_w, env_h;
+} dt_scene;
+
+/* n_views pinhole cameras sharing one image size.  d_cams float[n_views][10]
+ * = eye xyz, look-at point xyz, up xyz, vertical field of view in degrees.
+ * The ray of image point (sx, sy) (pixel px covers sx in [px, px+1)) has
+ * origin eye and direction normalize(f + a r + b u) with f = normalize(at -
+ * eye), r = normalize(f x up) (f x (0,0,1) if f x up = 0), u = r x f,
+ * a = (2 sx / width - 1) tan(fov/2) width/height, b = (1 - 2 sy / height)
+ * tan(fov/2). */
+typedef struct dt_views {
+  const float* d_cams;
+  int32_t n_views, width, height;
+} dt_views;
+
+/* Parameters.
+ *  max_depth: D, the number of surface interactions a path may have
+ *    (0 <= D <= 30).  Segments of depth k <= D are intersected; a hit at
+ *    depth D contributes nothing (Sec. 3.4 step 1; App. A.3.4 uses 4 in
+ *    training and 8 at inference).
+ *  spp: samples per pixel (>= 1); pixel = mean over its samples.
+ *  jitter: 0 = every sample at the pixel centre; 1 = sample s of pixel p in
+ *    view v at p + (hx, hy), hx, hy = the top 24 bits of pcg(h),
+ *    pcg(h ^ 0x9E3779B9) times 2^-24, h = pcg(pcg(pcg(pcg(seed_lo ^
+ *    pcg(seed_hi)) ^ v) ^ p) ^ s), pcg = the PCG hash of Jarzynski and Olano
+ *    (JCGT 2020).
+ *  t_min: hits need t > t_min (the triangle a ray leaves from is skipped
+ *    as well).  1e-5 for meshes scaled to the unit sphere. */
+typedef struct dt_params {
+  int32_t max_depth;
+  int32_t spp;
+  int32_t jitter;
+  int32_t reserved0;
+  uint64_t seed;
+  float t_min;
+  int32_t reserved1;
+} dt_params;
+
+/* ------------------------------------------------------------------------
+ * Forward render (Sec. 3.4 steps 1-5), wavefront by depth: camera rays;
+ * then for k = 0..D a closest-hit pass over the level-k segments and a
+ * shading pass that accumulates escaped rays into the image and appends the
+ * reflected and refracted children to level k+1.  Every segment of every
+ * level is kept in the workspace (the "tape") for dt_render_backward.
+ *
+ * dt_render_workspace_size: bytes for a workspace holding seg_capacity
+ *   segments (all levels together; seg_capacity <= 2^31 - 1).  A segment is
+ *   one closest-hit query; a pixel sample with a convex object needs at most
+ *   2D + 1, any object at most 2^(D+1) - 1.
+ * dt_render: d_out float[n_views][height][width][3] is overwritten with the
+ *   image.  d_ws (256-byte aligned) of ws_bytes holds the tape afterwards and
+ *   must stay untouched until dt_render_backward has run.  When the arena is
+ *   too small the excess segments are dropped and the status word records
+ *   DT_ERR_QUEUE_OVERFLOW with a lower bound on the capacity needed.
+ * ------------------------------------------------------------------------ */
+dt_status dt_render_workspace_size(int64_t seg_capacity, size_t* ws_bytes);
+dt_status dt_render(const dt_scene* scene, const dt_views* views, const dt_params* params, float* d_out,
+                    void* d_ws, size_t ws_bytes, dt_stream stream);
+
+/* Statistics of the last dt_render into d_ws (ws_bytes as passed to it).
+ * Copies them to host memory, which waits for the stream to reach this point
+ * (the one synchronising call).  status is DT_OK or the first device-side
+ * error; after DT_ERR_QUEUE_OVERFLOW, seg_needed is a lower bound on the
+ * capacity to retry with. */
+typedef struct dt_stats {
+  int32_t status;
+  int32_t n_levels;            /* depth levels that held segments */
+  int64_t segments;            /* closest-hit queries traced */
+  int64_t seg_needed;          /* lower bound on seg_capacity (overflow) */
+  int64_t level_count[32];     /* segments per depth */
+  int64_t level_start[32];     /* arena offset of each depth */
+  int64_t hits, misses, discarded, backfacing, tir;
+  int64_t nodes_visited;       /* BVH nodes whose child boxes were tested */
+  int64_t tris_tested;         /* ray/triangle tests */
+  int64_t max_level;           /* largest level_count */
+} dt_stats;
+dt_status dt_read_stats(const void* d_ws, size_t ws_bytes, dt_stats* out, dt_stream stream);
+
+/* ------------------------------------------------------------------------
+ * Backward of dt_render: reverse sweep k = D..0 over the tape.  For an image
+ * gradient d_grad_out float[n_views][height][width][3] (= dLoss/dImage) it
+ * returns the gradient at fixed discrete events (hit triangles,
+ * inside/outside, total internal reflection) with respect to the vertex
+ * positions, the IoR and sigma, through every term of Sec. 3.3-3.4: the
+ * environment lookup, the Fresnel terms (Eqs. 7-8), reflection and
+ * refraction (Eqs. 3-6), the interpolated normal (Eq. 12) and the vertex
+ * normals (Eq. 13), the barycentric hit point (Sec. 3.4: intersection points
+ * interpolated from vertex positions), and the absorption exp(-sigma t).
+ *
+ * The scene, views and params must be those of the dt_render that filled
+ * d_ws (ws_bytes as passed to it), and that render must have finished with
+ * status DT_OK.  dt_backward_workspace_size: bytes of the backward scratch
+ * d_bws (256-byte aligned) for a render whose largest level held max_level
+ * segments (dt_stats.max_level); pass the same max_level to
+ * dt_render_backward.  Outputs are overwritten: d_grad_V float[nv][3],
+ * d_grad_ior float[1], d_grad_sigma float[3].
+ * ------------------------------------------------------------------------ */
+dt_status dt_backward_workspace_size(int64_t max_level, int32_t nv, size_t* bytes);
+dt_status dt_render_backward(const dt_scene* scene, const dt_views* views, const dt_params* params,
+                             const void* d_ws, size_t ws_bytes, const float* d_grad_out, float* d_grad_V,
+                             float* d_grad_ior, float* d_grad_sigma, void* d_bws, size_t bws_bytes,
+                             int64_t max_level, dt_stream stream);
+
+/* ------------------------------------------------------------------------
+ * Debug / parity: every segment of the tape in arena order (level by
+ * level).  d_seg_i int32[cap][4] = (sample index, heap node id, hit triangle
+ * or -1, flags); d_seg_f float[cap][9] = (t, b1, b2, origin xyz, direction
+ * xyz).  Sample index = (view*height*width + py*width + px)*spp + s; the
+ * heap node id of a camera ray is 1 and the children of node m are 2m
+ * (reflected) and 2m+1 (refracted).  Flag bits: 4 inside (hit from inside),
+ * 8 total internal reflection, 16 backfacing shading normal, 128 hit at
+ * depth D, 512 miss.  Writes min(cap, segments) records.
+ * ------------------------------------------------------------------------ */
+dt_status dt_dump_segments(const void* d_ws, size_t ws_bytes, int32_t* d_seg_i, float* d_seg_f, int64_t cap,
+                           dt_stream stream);
+
+/* Closest hit (Sec. 3.4 step 2) of n arbitrary rays through a BVH built for
+ * nf triangles (tooling and tests): d_o, d_d float[n][3]; d_src int32[n]
+ * (triangle to skip, -1 for none; may be NULL); hits need t > t_min, ties
+ * in t go to the smaller triangle id.  Outputs d_tri int32[n] (-1 = miss,
+ * -2 = traversal stack overflow) and d_tbb float[n][3] = (t, b1, b2), the
+ * hit point being (1 - b1 - b2) v0 + b1 v1 + b2 v2. */
+dt_status dt_closest_hit(const void* d_bvh, int32_t nf, const float* d_o, const float* d_d, const int32_t* d_src,
+                         int32_t n, float t_min, int32_t* d_tri, float* d_tbb, dt_stream stream);
+
+/* ------------------------------------------------------------------------
+ * Image loss seed for the backward pass.  The paper supervises the rendered
+ * colours with an L2 loss (Sec. 3.4 "Optimization"); this is its plain
+ * mean-squared form over n values: loss = scale * sum (img - target)^2 and
+ * d_grad = 2 scale (img - target), with scale = 1/n for the mean.
+ * d_img, d_target, d_grad float[n]; d_loss float[1] is overwritten.
+ * ------------------------------------------------------------------------ */
+dt_status dt_l2_loss_grad(const float* d_img, const float* d_target, int64_t n, float scale, float* d_grad,
+                          float* d_loss, dt_stream stream);
+
+/* ------------------------------------------------------------------------
+ * Per-kernel timing.  While enabled, every launch of the library's main
+ * kernels is bracketed by CUDA events recorded on its launch stream.
+ * dt_profile_read waits for those events, returns per kernel name the
+ * number of launches and the summed event time in milliseconds (at most
+ * cap entries, *n = number of names), and clears the record.
+ * ------------------------------------------------------------------------ */
+typedef struct dt_kernel_time {
+  char name[40];
+  int64_t launches;
+  double total_ms;
+} dt_kernel_time;
+dt_status dt_profile_enable(int32_t enable);
+dt_status dt_profile_read(dt_kernel_time* out, int32_t cap, int32_t* n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DIFFTRANS_H_ */

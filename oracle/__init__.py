@@ -35,7 +35,8 @@ SEG_GRAZING = 64
 SEG_DISCARDED = 128
 SEG_NEAR_POLE = 256
 SEG_MISS = 512
-SEG_DEGENERATE = SEG_NEAR_EDGE | SEG_NEAR_TIE | SEG_NEAR_CRITICAL | SEG_GRAZING | SEG_NEAR_POLE
+SEG_UNSTABLE = 1024
+SEG_DEGENERATE = SEG_NEAR_EDGE | SEG_NEAR_TIE | SEG_NEAR_CRITICAL | SEG_GRAZING | SEG_NEAR_POLE | SEG_UNSTABLE
 
 COUNTER_NAMES = ("segments", "hits", "misses", "discarded", "leaks", "backfacing", "tir", "degenerate")
 
@@ -68,12 +69,13 @@ def _load():
         lib.orc_camera_rays.argtypes = [P, I, I, I, I, U64, I, P, P]
         lib.orc_pcg_hash.argtypes = [ctypes.c_uint32]
         lib.orc_pcg_hash.restype = ctypes.c_uint32
-        lib.orc_render.argtypes = [P, I, P, I, D, P, P, I, I, P, I, I, I, I, I, U64, I, D,
+        lib.orc_render.argtypes = [P, I, P, I, D, P, P, I, I, P, I, I, I, I, I, U64, I, D, D,
                                    P, P, P, P, P, P, I64, P, P]
-        lib.orc_render_rays.argtypes = [P, I, P, I, D, P, P, I, I, P, P, I, I, D,
+        lib.orc_render_rays.argtypes = [P, I, P, I, D, P, P, I, I, P, P, I, I, D, D,
                                         P, P, P, P, P, P, I64, P, P]
         lib.orc_render_jvp.argtypes = [P, I, P, I, D, P, P, I, I, P, I, I, I, I, I, U64, I, D,
                                        I, P, P, P, P, P]
+        lib.orc_render_rays_jvp.argtypes = [P, I, P, I, D, P, P, I, I, P, P, I, I, D, I, P, P, P, P, P]
         _lib = lib
     return _lib
 
@@ -154,14 +156,16 @@ def _common(V, F, ior, sigma, env, cam):
 
 
 def render(V, F, ior, sigma, env, cam, max_depth: int, spp: int = 1, jitter: int = 0, seed: int = 0,
-           view: int = 0, t_min: float = 1e-5, segments: bool = False) -> dict:
+           view: int = 0, t_min: float = 1e-5, segments: bool = False, probe: float = 0.0) -> dict:
     """FP64 render of one view: the recursive ray tree of Sec. 3.4 steps 1-5.
 
     Returns dict(img [H,W,3], discard [H,W,3], pix_flags [H,W], pix_sig [H,W],
     counters {...}) and, with segments=True, seg_i [n,4] = (ray, heap node,
     tri, flags) and seg_f [n,9] = (t, b1, b2, origin xyz, direction xyz).
     discard is the path weight lost to the depth limit or to a backfacing
-    shading normal."""
+    shading normal.  probe > 0 re-traces every primary ray tilted by probe
+    radians four ways and flags pixels whose path events change
+    (SEG_UNSTABLE in pix_flags)."""
     V, F, ior, sigma, env, c = _common(V, F, ior, sigma, env, cam)
     H, W = cam.height, cam.width
     img = np.zeros((H * W, 3))
@@ -172,7 +176,7 @@ def render(V, F, ior, sigma, env, cam, max_depth: int, spp: int = 1, jitter: int
     nseg = np.zeros(1, np.int64)
     lib = _load()
     args = (_p(V), V.shape[0], _p(F), F.shape[0], ior, _p(sigma), _p(env), env.shape[1], env.shape[0],
-            _p(c), W, H, int(max_depth), int(spp), int(jitter), int(seed), int(view), float(t_min),
+            _p(c), W, H, int(max_depth), int(spp), int(jitter), int(seed), int(view), float(t_min), float(probe),
             _p(img), _p(disc), _p(pf), _p(sig))
     seg_i, seg_f = _run_with_segments(lib.orc_render, args, segments, nseg, cnt)
     out = dict(img=img.reshape(H, W, 3), discard=disc.reshape(H, W, 3), pix_flags=pf.reshape(H, W),
@@ -195,7 +199,7 @@ def _run_with_segments(fn, args, segments, nseg, cnt):
 
 
 def render_rays(V, F, ior, sigma, env, o, d, max_depth: int, t_min: float = 1e-5,
-                segments: bool = False) -> dict:
+                segments: bool = False, probe: float = 0.0) -> dict:
     """The same FP64 ray tree for arbitrary primary rays (o, d: [n,3], d
     unit), one sample each.  Outputs as render() with pixels = rays."""
     V, F = _d(V), _i(F)
@@ -210,7 +214,7 @@ def render_rays(V, F, ior, sigma, env, o, d, max_depth: int, t_min: float = 1e-5
     nseg = np.zeros(1, np.int64)
     lib = _load()
     args = (_p(V), V.shape[0], _p(F), F.shape[0], float(ior), _p(sigma), _p(env), env.shape[1], env.shape[0],
-            _p(o), _p(d), n, int(max_depth), float(t_min), _p(img), _p(disc), _p(pf), _p(sig))
+            _p(o), _p(d), n, int(max_depth), float(t_min), float(probe), _p(img), _p(disc), _p(pf), _p(sig))
     seg_i, seg_f = _run_with_segments(lib.orc_render_rays, args, segments, nseg, cnt)
     out = dict(img=img, discard=disc, pix_flags=pf, pix_sig=sig, counters=dict(zip(COUNTER_NAMES, cnt.tolist())))
     if segments:
@@ -239,6 +243,71 @@ def render_jvp(V, F, ior, sigma, env, cam, max_depth: int, tV=None, tior=None, t
                            env.shape[0], _p(c), W, H, int(max_depth), int(spp), int(jitter), int(seed),
                            int(view), float(t_min), nt, _p(tV), _p(tior), _p(tsigma), _p(img), _p(dimg))
     return img.reshape(H, W, 3), dimg.reshape(nt, H, W, 3)
+
+
+def render_rays_jvp(V, F, ior, sigma, env, o, d, max_depth: int, tV=None, tior=None, tsigma=None,
+                    t_min: float = 1e-5):
+    """Forward-mode derivative of the FP64 tree of arbitrary primary rays.
+    Returns (radiance [n,3], d radiance [ntan,n,3])."""
+    V, F = _d(V), _i(F)
+    sigma, env = _d(sigma).reshape(3), _d(env)
+    o, d = _d(o).reshape(-1, 3), _d(d).reshape(-1, 3)
+    n = o.shape[0]
+    nt = None
+    for a in (tV, tior, tsigma):
+        if a is not None:
+            nt = np.asarray(a).shape[0]
+    assert nt is not None and nt > 0
+    tV = _d(tV) if tV is not None else None
+    tior = _d(tior) if tior is not None else None
+    tsigma = _d(tsigma) if tsigma is not None else None
+    img = np.zeros((n, 3))
+    dimg = np.zeros((nt, n, 3))
+    _load().orc_render_rays_jvp(_p(V), V.shape[0], _p(F), F.shape[0], float(ior), _p(sigma), _p(env), env.shape[1],
+                                env.shape[0], _p(o), _p(d), n, int(max_depth), float(t_min), nt, _p(tV), _p(tior),
+                                _p(tsigma), _p(img), _p(dimg))
+    return img, dimg
+
+
+def support_vertices(F, tris):
+    """Vertices whose positions can move the radiance of paths that hit the
+    given triangles: the triangles' own vertices and, through the Eq. 13
+    vertex normals, every vertex of a face that touches one of them."""
+    F = np.asarray(F, dtype=np.int64)
+    tris = np.unique(np.asarray(tris, dtype=np.int64))
+    tris = tris[tris >= 0]
+    core = np.unique(F[tris].reshape(-1))
+    touching = np.isin(F, core).any(axis=1)
+    return np.unique(np.concatenate([core, F[touching].reshape(-1)]))
+
+
+def rays_grad(V, F, ior, sigma, env, o, d, max_depth: int, g, t_min: float = 1e-5, chunk: int = 256):
+    """Gradient of J = sum(g * radiance(rays)) w.r.t. (V, ior, sigma) by
+    forward mode over every parameter that can influence these rays (the
+    support of their hit triangles); all other vertex gradients are 0.
+    Returns (dV [nv,3], dior, dsigma [3], segments traced in the forward)."""
+    V = _d(V)
+    nv = V.shape[0]
+    g = _d(g).reshape(-1, 3)
+    fw = render_rays(V, F, ior, sigma, env, o, d, max_depth, t_min, segments=True)
+    verts = support_vertices(F, fw["seg_i"][:, 2])
+    tior = np.array([1.0, 0, 0, 0])
+    tsig = np.zeros((4, 3))
+    tsig[1, 0] = tsig[2, 1] = tsig[3, 2] = 1.0
+    _, dimg = render_rays_jvp(V, F, ior, sigma, env, o, d, max_depth, None, tior, tsig, t_min)
+    J = np.einsum("knc,nc->k", dimg, g)
+    coords = [(int(v), a) for v in verts for a in range(3)]
+    dV = np.zeros((nv, 3))
+    for s in range(0, len(coords), chunk):
+        part = coords[s:s + chunk]
+        tV = np.zeros((len(part), nv, 3))
+        for j, (v, a) in enumerate(part):
+            tV[j, v, a] = 1.0
+        _, dd = render_rays_jvp(V, F, ior, sigma, env, o, d, max_depth, tV, None, None, t_min)
+        Jv = np.einsum("knc,nc->k", dd, g)
+        for j, (v, a) in enumerate(part):
+            dV[v, a] = Jv[j]
+    return dV, float(J[0]), J[1:4], int(fw["counters"]["segments"])
 
 
 def grad_full(V, F, ior, sigma, env, cam, max_depth: int, g, vert_subset=None, chunk: int = 64, **kw):

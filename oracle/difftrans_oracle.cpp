@@ -170,8 +170,10 @@ enum : int {
   SEG_DISCARDED = 128,   // hit at depth D: contributes 0
   SEG_NEAR_POLE = 256,   // environment lookup within 1e-6 of a pole
   SEG_MISS = 512,        // no hit: environment lookup
+  SEG_UNSTABLE = 1024,   // pixel only: the path's events change when the primary ray is tilted by probe_delta
 };
-const int SEG_DEGENERATE = SEG_NEAR_EDGE | SEG_NEAR_TIE | SEG_NEAR_CRITICAL | SEG_GRAZING | SEG_NEAR_POLE;
+const int SEG_DEGENERATE =
+    SEG_NEAR_EDGE | SEG_NEAR_TIE | SEG_NEAR_CRITICAL | SEG_GRAZING | SEG_NEAR_POLE | SEG_UNSTABLE;
 
 struct Hit {
   int tri = -1;
@@ -340,6 +342,7 @@ struct SegRec {
 struct PixelState {
   int flags_or = 0;
   uint64_t sig = 1469598103934665603ull;  // FNV-1a over the event signature
+  uint64_t path_sig = 1469598103934665603ull;  // the same without environment texel cells
   V3d discard;
   std::vector<SegRec>* segs = nullptr;
   int32_t ray = 0;
@@ -413,6 +416,8 @@ V3<T> radiance(const Scene<T>& S, const V3<T>& o, const V3<T>& d, int k, uint32_
         P.flags_or |= rec.flags;
         sig_mix(P.sig, (uint64_t)node | ((uint64_t)(uint32_t)h.tri << 32));
         sig_mix(P.sig, (uint64_t)(rec.flags & (SEG_INSIDE | SEG_TIR | SEG_BACKFACING | SEG_DISCARDED | SEG_MISS)));
+        sig_mix(P.path_sig, (uint64_t)node | ((uint64_t)(uint32_t)h.tri << 32));
+        sig_mix(P.path_sig, (uint64_t)(rec.flags & (SEG_INSIDE | SEG_TIR | SEG_BACKFACING | SEG_DISCARDED | SEG_MISS)));
         if (P.segs) P.segs->push_back(rec);
         // step 4: reflected child at node 2m, refracted child at node 2m+1
         // the reflected ray stays on the incoming side, the refracted one crosses
@@ -429,6 +434,8 @@ V3<T> radiance(const Scene<T>& S, const V3<T>& o, const V3<T>& d, int k, uint32_
   P.flags_or |= rec.flags;
   sig_mix(P.sig, (uint64_t)node | ((uint64_t)(uint32_t)h.tri << 32));
   sig_mix(P.sig, (uint64_t)(rec.flags & (SEG_INSIDE | SEG_TIR | SEG_BACKFACING | SEG_DISCARDED | SEG_MISS)));
+  sig_mix(P.path_sig, (uint64_t)node | ((uint64_t)(uint32_t)h.tri << 32));
+  sig_mix(P.path_sig, (uint64_t)(rec.flags & (SEG_INSIDE | SEG_TIR | SEG_BACKFACING | SEG_DISCARDED | SEG_MISS)));
   if (rec.flags & SEG_DEGENERATE) P.counters[7]++;
   if (P.segs) P.segs->push_back(rec);
   return L;
@@ -480,6 +487,51 @@ void render_pixels(int npix, int spp, const Scene<T>& S, RayFn ray_od, std::vect
     }
     img[p] = acc * T(1.0 / spp);
     P.discard = P.discard * (1.0 / spp);
+  }
+}
+
+// Stability probe: re-trace every sample's primary ray and four copies of it
+// tilted by delta radians (two orthogonal axes, both signs).  A pixel is
+// flagged SEG_UNSTABLE when, for any copy, the path signature (hit triangles
+// and inside/TIR/backfacing/depth/miss events, not the environment cells)
+// differs, or the radiance moves by more than rel_tol relative.  It marks the
+// paths that pass so close to an edge, or so near a singular point of the
+// optics (the TIR critical angle), that a tracer carrying slightly different
+// rounding may take another branch or land far away.
+template <class RayFn>
+void probe_stability(int npix, int spp, const Scene<double>& S, RayFn ray_od, double delta,
+                     std::vector<PixelState>& ps, double rel_tol = 1e-4) {
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int p = 0; p < npix; ++p) {
+    for (int s = 0; s < spp; ++s) {
+      V3d o, d;
+      ray_od(p, s, o, d);
+      V3d a = std::fabs(d.x) < 0.9 ? V3d(1.0, 0.0, 0.0) : V3d(0.0, 1.0, 0.0);
+      V3d t1 = normalize(cross(d, a)), t2 = cross(d, t1);
+      uint64_t ref = 0;
+      V3d L0;
+      for (int q = 0; q < 5; ++q) {
+        V3d dq = d;
+        if (q > 0) {
+          const double sg = (q & 1) ? delta : -delta;
+          dq = normalize(d + ((q <= 2) ? t1 : t2) * sg);
+        }
+        PixelState P;
+        V3d L = radiance(S, o, dq, 0, 1u, -1, false, V3d(1.0, 1.0, 1.0), P);
+        if (q == 0) {
+          ref = P.path_sig;
+          L0 = L;
+          continue;
+        }
+        const double dx = std::fabs(L.x - L0.x), dy = std::fabs(L.y - L0.y), dz = std::fabs(L.z - L0.z);
+        if (P.path_sig != ref || dx > rel_tol * std::fabs(L0.x) + 1e-12 || dy > rel_tol * std::fabs(L0.y) + 1e-12 ||
+            dz > rel_tol * std::fabs(L0.z) + 1e-12) {
+          ps[p].flags_or |= SEG_UNSTABLE;
+          break;
+        }
+      }
+      if (ps[p].flags_or & SEG_UNSTABLE) break;
+    }
   }
 }
 
@@ -614,7 +666,7 @@ static int write_outputs(int npix, const std::vector<V3d>& im, const std::vector
 // Returns 0, or 1 when cap was too small (n_seg tells how many are needed).
 int orc_render(const double* V, int nv, const int* F, int nf, double ior, const double* sigma,
                const double* env, int env_w, int env_h, const double* cam, int width, int height,
-               int max_depth, int spp, int jitter, uint64_t seed, int view, double t_min,
+               int max_depth, int spp, int jitter, uint64_t seed, int view, double t_min, double probe_delta,
                double* img, double* discard, int* pix_flags, uint64_t* pix_sig,
                int32_t* seg_i, double* seg_f, int64_t cap, int64_t* n_seg, int64_t* counters) {
   Inputs in{V, nv, F, nf, ior, sigma, env, env_w, env_h, cam, width, height, max_depth, spp, jitter, seed,
@@ -627,6 +679,14 @@ int orc_render(const double* V, int nv, const int* F, int nf, double ior, const 
   std::vector<std::vector<SegRec>> segs;
   const bool keep = seg_i != nullptr || n_seg != nullptr;
   render_view(in, S, im, ps, keep, segs);
+  if (probe_delta > 0.0) {
+    auto cam_ray = [&](int p, int s, V3d& o, V3d& d) {
+      double jx = 0.5, jy = 0.5;
+      if (jitter) jitter_offset(seed, (uint32_t)view, (uint32_t)p, (uint32_t)s, jx, jy);
+      camera_ray(cam, width, height, (p % width) + jx, (p / width) + jy, o, d);
+    };
+    probe_stability(width * height, spp, S, cam_ray, probe_delta, ps);
+  }
   return write_outputs(width * height, im, ps, segs, keep, img, discard, pix_flags, pix_sig, seg_i, seg_f,
                        cap, n_seg, counters);
 }
@@ -635,7 +695,7 @@ int orc_render(const double* V, int nv, const int* F, int nf, double ior, const 
 // sample each; outputs as orc_render with npix = n.
 int orc_render_rays(const double* V, int nv, const int* F, int nf, double ior, const double* sigma,
                     const double* env, int env_w, int env_h, const double* o, const double* d, int n,
-                    int max_depth, double t_min, double* img, double* discard, int* pix_flags,
+                    int max_depth, double t_min, double probe_delta, double* img, double* discard, int* pix_flags,
                     uint64_t* pix_sig, int32_t* seg_i, double* seg_f, int64_t cap, int64_t* n_seg,
                     int64_t* counters) {
   Inputs in{V, nv, F, nf, ior, sigma, env, env_w, env_h, nullptr, n, 1, max_depth, 1, 0, 0, 0, t_min};
@@ -651,22 +711,21 @@ int orc_render_rays(const double* V, int nv, const int* F, int nf, double ior, c
     dd = V3d(d[3 * p], d[3 * p + 1], d[3 * p + 2]);
   };
   render_pixels(n, 1, S, given, im, ps, keep, segs);
+  if (probe_delta > 0.0) probe_stability(n, 1, S, given, probe_delta, ps);
   return write_outputs(n, im, ps, segs, keep, img, discard, pix_flags, pix_sig, seg_i, seg_f, cap, n_seg,
                        counters);
 }
 
-// Forward-mode derivative of one view's image along ntan directions at once.
-// tV: [ntan][nv][3], tior: [ntan], tsigma: [ntan][3] (each nullable = 0).
-// img: [H*W][3] (the same values as orc_render); dimg: [ntan][H*W][3].
-int orc_render_jvp(const double* V, int nv, const int* F, int nf, double ior, const double* sigma,
-                   const double* env, int env_w, int env_h, const double* cam, int width, int height,
-                   int max_depth, int spp, int jitter, uint64_t seed, int view, double t_min,
-                   int ntan, const double* tV, const double* tior, const double* tsigma,
-                   double* img, double* dimg) {
+}  // extern "C"
+
+namespace orc {
+// Forward-mode derivative along ntan tangent directions, 32 per pass; each
+// pass re-runs the tree with dual numbers.  ray_od gives the primary rays.
+template <class RayFn>
+void jvp_passes(const Inputs& in, int npix, int spp, RayFn ray_od, int ntan, const double* tV,
+                       const double* tior, const double* tsigma, double* img, double* dimg) {
   constexpr int K = 32;
-  Inputs in{V, nv, F, nf, ior, sigma, env, env_w, env_h, cam, width, height, max_depth, spp, jitter, seed,
-            view, t_min};
-  const int npix = width * height;
+  const int nv = in.nv;
   for (int base = 0; base < ntan; base += K) {
     const int kk = std::min(K, ntan - base);
     Scene<Dual<K>> S;
@@ -681,11 +740,11 @@ int orc_render_jvp(const double* V, int nv, const int* F, int nf, double ior, co
       if (tior) S.ior.d[j] = tior[g];
       if (tsigma) for (int c = 0; c < 3; ++c) S.sigma[c].d[j] = tsigma[3 * g + c];
     }
-    vertex_normals(S.V, F, nf, S.N);
+    vertex_normals(S.V, in.F, in.nf, S.N);
     std::vector<V3<Dual<K>>> im;
     std::vector<PixelState> ps;
     std::vector<std::vector<SegRec>> segs;
-    render_view(in, S, im, ps, false, segs);
+    render_pixels(npix, spp, S, ray_od, im, ps, false, segs);
     for (int p = 0; p < npix; ++p) {
       if (img && base == 0) { img[3 * p] = im[p].x.v; img[3 * p + 1] = im[p].y.v; img[3 * p + 2] = im[p].z.v; }
       for (int j = 0; j < kk; ++j) {
@@ -694,6 +753,42 @@ int orc_render_jvp(const double* V, int nv, const int* F, int nf, double ior, co
       }
     }
   }
+}
+}  // namespace orc
+
+extern "C" {
+
+// Forward-mode derivative of one view's image along ntan directions at once.
+// tV: [ntan][nv][3], tior: [ntan], tsigma: [ntan][3] (each nullable = 0).
+// img: [H*W][3] (the same values as orc_render); dimg: [ntan][H*W][3].
+int orc_render_jvp(const double* V, int nv, const int* F, int nf, double ior, const double* sigma,
+                   const double* env, int env_w, int env_h, const double* cam, int width, int height,
+                   int max_depth, int spp, int jitter, uint64_t seed, int view, double t_min,
+                   int ntan, const double* tV, const double* tior, const double* tsigma,
+                   double* img, double* dimg) {
+  Inputs in{V, nv, F, nf, ior, sigma, env, env_w, env_h, cam, width, height, max_depth, spp, jitter, seed,
+            view, t_min};
+  auto cam_ray = [&](int p, int s, V3d& o, V3d& d) {
+    double jx = 0.5, jy = 0.5;
+    if (jitter) jitter_offset(seed, (uint32_t)view, (uint32_t)p, (uint32_t)s, jx, jy);
+    camera_ray(cam, width, height, (p % width) + jx, (p / width) + jy, o, d);
+  };
+  jvp_passes(in, width * height, spp, cam_ray, ntan, tV, tior, tsigma, img, dimg);
+  return 0;
+}
+
+// The same for n arbitrary primary rays (o, d: [n][3]); img: [n][3];
+// dimg: [ntan][n][3].
+int orc_render_rays_jvp(const double* V, int nv, const int* F, int nf, double ior, const double* sigma,
+                        const double* env, int env_w, int env_h, const double* o, const double* d, int n,
+                        int max_depth, double t_min, int ntan, const double* tV, const double* tior,
+                        const double* tsigma, double* img, double* dimg) {
+  Inputs in{V, nv, F, nf, ior, sigma, env, env_w, env_h, nullptr, n, 1, max_depth, 1, 0, 0, 0, t_min};
+  auto given = [&](int p, int, V3d& oo, V3d& dd) {
+    oo = V3d(o[3 * p], o[3 * p + 1], o[3 * p + 2]);
+    dd = V3d(d[3 * p], d[3 * p + 1], d[3 * p + 2]);
+  };
+  jvp_passes(in, n, 1, given, ntan, tV, tior, tsigma, img, dimg);
   return 0;
 }
 

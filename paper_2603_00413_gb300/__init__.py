@@ -1,0 +1,436 @@
+"""GB300 (sm_103a) recursive differentiable transparent-mesh ray tracer.
+
+DiffTrans (arXiv 2603.00413), Sec. 3.3-3.4: camera rays traced through a
+closed triangle mesh, split at every hit into Fresnel-weighted reflected and
+Snell-refracted rays, attenuated inside by Beer-Lambert absorption, reading an
+environment map where they escape; with the adjoint that returns image-loss
+gradients for vertex positions, IoR and absorption.
+
+This module is a thin ctypes binding of ``libdifftrans.so`` (C ABI in
+``include/difftrans.h``): it marshals torch CUDA tensors into pointers and
+sizes, and allocates the workspaces the library asks for.  Every step of the
+computation runs in the library's kernels; there is no CPU path.  If the
+library has not been built the calls raise instead of falling back.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_char_p, c_float, c_int32, c_int64, c_size_t, c_uint64, c_void_p
+
+import torch
+
+__all__ = [
+    "DiffTransError", "load_library", "vertex_normals", "vertex_normals_backward", "Bvh", "build_bvh",
+    "refit_bvh", "Params", "render", "render_backward", "read_stats", "dump_segments", "closest_hit",
+    "render_workspace_size", "backward_workspace_size", "Tape", "DiffTransRender", "render_differentiable",
+    "l2_loss_grad", "profile_enable", "profile_read",
+]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdifftrans.so")
+
+DT_OK = 0
+DT_ERR_INVALID_ARG = 1
+DT_ERR_CUDA = 2
+DT_ERR_QUEUE_OVERFLOW = 3
+DT_ERR_STACK_OVERFLOW = 4
+DT_ERR_NOT_IMPLEMENTED = 5
+
+SF_INSIDE, SF_TIR, SF_BACKFACING, SF_DISCARDED, SF_MISS = 4, 8, 16, 128, 512
+
+
+class DiffTransError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"difftrans error {code}: {msg}")
+        self.code = code
+
+
+class DtScene(ctypes.Structure):
+    _fields_ = [("d_V", c_void_p), ("d_F", c_void_p), ("nv", c_int32), ("nf", c_int32), ("d_bvh", c_void_p),
+                ("d_N", c_void_p), ("d_ior", c_void_p), ("d_sigma", c_void_p), ("d_env", c_void_p),
+                ("env_w", c_int32), ("env_h", c_int32)]
+
+
+class DtViews(ctypes.Structure):
+    _fields_ = [("d_cams", c_void_p), ("n_views", c_int32), ("width", c_int32), ("height", c_int32)]
+
+
+class DtParams(ctypes.Structure):
+    _fields_ = [("max_depth", c_int32), ("spp", c_int32), ("jitter", c_int32), ("reserved0", c_int32),
+                ("seed", c_uint64), ("t_min", c_float), ("reserved1", c_int32)]
+
+
+class DtStats(ctypes.Structure):
+    _fields_ = [("status", c_int32), ("n_levels", c_int32), ("segments", c_int64), ("seg_needed", c_int64),
+                ("level_count", c_int64 * 32), ("level_start", c_int64 * 32), ("hits", c_int64),
+                ("misses", c_int64), ("discarded", c_int64), ("backfacing", c_int64), ("tir", c_int64),
+                ("nodes_visited", c_int64), ("tris_tested", c_int64), ("max_level", c_int64)]
+
+    def as_dict(self):
+        n = self.n_levels
+        return {
+            "status": self.status, "n_levels": n, "segments": self.segments, "seg_needed": self.seg_needed,
+            "level_count": list(self.level_count[:max(n, 1)]), "hits": self.hits, "misses": self.misses,
+            "discarded": self.discarded, "backfacing": self.backfacing, "tir": self.tir,
+            "nodes_visited": self.nodes_visited, "tris_tested": self.tris_tested, "max_level": self.max_level,
+        }
+
+
+class DtKernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 40), ("launches", c_int64), ("total_ms", ctypes.c_double)]
+
+
+# exported symbol -> (restype, argtypes)
+_PROTOS = {
+    "dt_last_error": (c_char_p, []),
+    "dt_version": (c_char_p, []),
+    "dt_vertex_normals_scratch_size": (c_int32, [c_int32, POINTER(c_size_t)]),
+    "dt_vertex_normals": (c_int32, [c_void_p, c_int32, c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
+    "dt_vertex_normals_backward": (c_int32, [c_void_p, c_int32, c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
+    "dt_bvh_size": (c_int32, [c_int32, POINTER(c_size_t), POINTER(c_size_t)]),
+    "dt_build_bvh": (c_int32, [c_void_p, c_int32, c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
+    "dt_refit_bvh": (c_int32, [c_void_p, c_int32, c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
+    "dt_render_workspace_size": (c_int32, [c_int64, POINTER(c_size_t)]),
+    "dt_render": (c_int32, [POINTER(DtScene), POINTER(DtViews), POINTER(DtParams), c_void_p, c_void_p, c_size_t,
+                            c_void_p]),
+    "dt_read_stats": (c_int32, [c_void_p, c_size_t, POINTER(DtStats), c_void_p]),
+    "dt_backward_workspace_size": (c_int32, [c_int64, c_int32, POINTER(c_size_t)]),
+    "dt_render_backward": (c_int32, [POINTER(DtScene), POINTER(DtViews), POINTER(DtParams), c_void_p, c_size_t,
+                                     c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_int64,
+                                     c_void_p]),
+    "dt_dump_segments": (c_int32, [c_void_p, c_size_t, c_void_p, c_void_p, c_int64, c_void_p]),
+    "dt_closest_hit": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_int32, c_float, c_void_p,
+                                 c_void_p, c_void_p]),
+    "dt_l2_loss_grad": (c_int32, [c_void_p, c_void_p, c_int64, c_float, c_void_p, c_void_p, c_void_p]),
+    "dt_profile_enable": (c_int32, [c_int32]),
+    "dt_profile_read": (c_int32, [POINTER(DtKernelTime), c_int32, POINTER(c_int32)]),
+}
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libdifftrans.so (built by ``paper_2603_00413_gb300.build``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with `python -m paper_2603_00413_gb300.build` "
+                               "(there is no fallback implementation)")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _PROTOS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(code):
+    if code != DT_OK:
+        msg = load_library().dt_last_error().decode(errors="replace")
+        raise DiffTransError(code, msg)
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _need(t, dtype, shape_tail=None, name="tensor"):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape_tail is not None and tuple(t.shape[-len(shape_tail):]) != tuple(shape_tail):
+        raise ValueError(f"{name} must end in shape {shape_tail}, got {tuple(t.shape)}")
+    return t
+
+
+def _aligned_empty(nbytes: int, device, align: int = 256):
+    """A uint8 buffer whose data pointer is `align`-byte aligned (returns the
+    owning tensor and the aligned view)."""
+    raw = torch.empty(nbytes + align, dtype=torch.uint8, device=device)
+    off = (-raw.data_ptr()) % align
+    return raw, raw[off:off + nbytes]
+
+
+# ---------------------------------------------------------------------------
+# geometry
+# ---------------------------------------------------------------------------
+_scratch_cache = {}
+
+
+def _normals_scratch(nv, device):
+    b = c_size_t()
+    _check(load_library().dt_vertex_normals_scratch_size(nv, ctypes.byref(b)))
+    key = (device, b.value)
+    if key not in _scratch_cache:
+        _scratch_cache.clear()
+        _scratch_cache[key] = _aligned_empty(b.value, device)
+    return _scratch_cache[key][1]
+
+
+def vertex_normals(V, F, out=None, stream=None, scratch=None):
+    """Eq. 13 vertex normals: (1/3) * sum of unit face normals per vertex
+    (bit-reproducible: fixed-point accumulation in a scratch buffer)."""
+    _need(V, torch.float32, (3,), "V")
+    _need(F, torch.int32, (3,), "F")
+    N = torch.empty_like(V) if out is None else out
+    scratch = _normals_scratch(V.shape[0], V.device) if scratch is None else scratch
+    _check(load_library().dt_vertex_normals(_ptr(V), V.shape[0], _ptr(F), F.shape[0], _ptr(N), _ptr(scratch),
+                                            _stream(stream)))
+    return N
+
+
+def vertex_normals_backward(V, F, dN, dV=None, stream=None):
+    """dV += (dN/dV)^T dN for the Eq. 13 normals."""
+    dV = torch.zeros_like(V) if dV is None else dV
+    _check(load_library().dt_vertex_normals_backward(_ptr(V), V.shape[0], _ptr(F), F.shape[0], _ptr(dN), _ptr(dV),
+                                                     _stream(stream)))
+    return dV
+
+
+class Bvh:
+    """An LBVH built by the library into a caller-owned device buffer."""
+
+    def __init__(self, nf: int, device):
+        bb, sb = c_size_t(), c_size_t()
+        _check(load_library().dt_bvh_size(nf, ctypes.byref(bb), ctypes.byref(sb)))
+        self.nf = nf
+        self.bytes = bb.value
+        self._raw, self.buf = _aligned_empty(bb.value, device)
+        self._sraw, self.scratch = _aligned_empty(sb.value, device)
+
+    def build(self, V, F, stream=None):
+        _need(V, torch.float32, (3,), "V")
+        _need(F, torch.int32, (3,), "F")
+        _check(load_library().dt_build_bvh(_ptr(V), V.shape[0], _ptr(F), F.shape[0], _ptr(self.buf),
+                                           _ptr(self.scratch), _stream(stream)))
+        return self
+
+    def refit(self, V, F, stream=None):
+        _check(load_library().dt_refit_bvh(_ptr(V), V.shape[0], _ptr(F), F.shape[0], _ptr(self.buf),
+                                           _ptr(self.scratch), _stream(stream)))
+        return self
+
+
+def build_bvh(V, F, stream=None) -> Bvh:
+    return Bvh(F.shape[0], V.device).build(V, F, stream)
+
+
+def refit_bvh(bvh: Bvh, V, F, stream=None) -> Bvh:
+    return bvh.refit(V, F, stream)
+
+
+def closest_hit(bvh: Bvh, o, d, src=None, t_min: float = 1e-5, stream=None):
+    """Closest hit of arbitrary rays through the BVH: (tri int32 [n], tbb [n,3])."""
+    _need(o, torch.float32, (3,), "o")
+    _need(d, torch.float32, (3,), "d")
+    n = o.shape[0]
+    tri = torch.empty(n, dtype=torch.int32, device=o.device)
+    tbb = torch.empty(n, 3, dtype=torch.float32, device=o.device)
+    _check(load_library().dt_closest_hit(_ptr(bvh.buf), bvh.nf, _ptr(o), _ptr(d), _ptr(src), n, float(t_min),
+                                         _ptr(tri), _ptr(tbb), _stream(stream)))
+    return tri, tbb
+
+
+# ---------------------------------------------------------------------------
+# render / backward
+# ---------------------------------------------------------------------------
+class Params:
+    def __init__(self, max_depth: int, spp: int = 1, jitter: int = 0, seed: int = 0, t_min: float = 1e-5):
+        self.max_depth, self.spp, self.jitter, self.seed, self.t_min = max_depth, spp, jitter, seed, t_min
+
+    def c(self):
+        return DtParams(self.max_depth, self.spp, self.jitter, 0, self.seed & (2 ** 64 - 1), self.t_min, 0)
+
+
+def render_workspace_size(seg_capacity: int) -> int:
+    b = c_size_t()
+    _check(load_library().dt_render_workspace_size(int(seg_capacity), ctypes.byref(b)))
+    return b.value
+
+
+def backward_workspace_size(max_level: int, nv: int) -> int:
+    b = c_size_t()
+    _check(load_library().dt_backward_workspace_size(int(max_level), int(nv), ctypes.byref(b)))
+    return b.value
+
+
+class Workspace:
+    """A caller-owned segment arena (the tape) for dt_render."""
+
+    def __init__(self, seg_capacity: int, device):
+        self.capacity = int(seg_capacity)
+        self.bytes = render_workspace_size(self.capacity)
+        self._raw, self.buf = _aligned_empty(self.bytes, device)
+
+
+def _scene_struct(V, F, bvh, N, ior, sigma, env):
+    _need(V, torch.float32, (3,), "V")
+    _need(F, torch.int32, (3,), "F")
+    _need(N, torch.float32, (3,), "N")
+    _need(env, torch.float32, (3,), "env")
+    _need(ior, torch.float32, None, "ior")
+    _need(sigma, torch.float32, None, "sigma")
+    if ior.numel() != 1 or sigma.numel() != 3:
+        raise ValueError("ior needs 1 element and sigma 3")
+    return DtScene(V.data_ptr(), F.data_ptr(), V.shape[0], F.shape[0], bvh.buf.data_ptr(), N.data_ptr(),
+                   ior.data_ptr(), sigma.data_ptr(), env.data_ptr(), env.shape[1], env.shape[0])
+
+
+def _views_struct(cams, width, height):
+    _need(cams, torch.float32, (10,), "cams")
+    return DtViews(cams.data_ptr(), cams.shape[0], int(width), int(height))
+
+
+def read_stats(ws: Workspace, stream=None) -> dict:
+    st = DtStats()
+    _check(load_library().dt_read_stats(_ptr(ws.buf), ws.bytes, ctypes.byref(st), _stream(stream)))
+    return st.as_dict()
+
+
+class Tape:
+    """Everything dt_render_backward needs from a forward call."""
+
+    def __init__(self, ws, scene_args, cams, width, height, params, stats):
+        self.ws, self.scene_args, self.cams = ws, scene_args, cams
+        self.width, self.height, self.params, self.stats = width, height, params, stats
+
+
+def default_capacity(n_primary: int, max_depth: int) -> int:
+    """First guess of the segment arena: 2D + 3 segments per primary ray is
+    what a convex object needs; the arena grows on overflow."""
+    return int(min(2 ** 31 - 1, max(n_primary * (2 * max_depth + 3), 1024)))
+
+
+def render(V, F, bvh: Bvh, N, ior, sigma, env, cams, width: int, height: int, params: Params, ws: Workspace = None,
+           out=None, stream=None, check: bool = True):
+    """Forward render (Sec. 3.4 steps 1-5) of cams.shape[0] views.
+
+    Returns (image [n_views, height, width, 3], Tape).  With check=True the
+    device status is read back (one synchronisation) and an arena overflow is
+    retried with a larger workspace."""
+    lib = load_library()
+    n_views = cams.shape[0]
+    n0 = n_views * width * height * params.spp
+    if ws is None:
+        ws = Workspace(default_capacity(n0, params.max_depth), V.device)
+    if out is None:
+        out = torch.empty(n_views, height, width, 3, dtype=torch.float32, device=V.device)
+    sc = _scene_struct(V, F, bvh, N, ior, sigma, env)
+    vw = _views_struct(cams, width, height)
+    pc = params.c()
+    while True:
+        _check(lib.dt_render(ctypes.byref(sc), ctypes.byref(vw), ctypes.byref(pc), _ptr(out), _ptr(ws.buf),
+                             ws.bytes, _stream(stream)))
+        if not check:
+            return out, Tape(ws, (V, F, bvh, N, ior, sigma, env), cams, width, height, params, None)
+        stats = read_stats(ws, stream)
+        if stats["status"] == DT_ERR_QUEUE_OVERFLOW:
+            grow = max(2 * ws.capacity, int(1.3 * stats["seg_needed"]))
+            ws = Workspace(min(grow, 2 ** 31 - 1), V.device)
+            continue
+        if stats["status"] != DT_OK:
+            raise DiffTransError(stats["status"], "device-side error during render")
+        return out, Tape(ws, (V, F, bvh, N, ior, sigma, env), cams, width, height, params, stats)
+
+
+def render_backward(tape: Tape, grad_out, stream=None, bws=None):
+    """Gradient of sum(grad_out * image) w.r.t. (V, ior, sigma) at the
+    forward's fixed events.  Returns (dV [nv,3], dior [1], dsigma [3])."""
+    lib = load_library()
+    V, F, bvh, N, ior, sigma, env = tape.scene_args
+    stats = tape.stats if tape.stats is not None else read_stats(tape.ws, stream)
+    if stats["status"] != DT_OK:
+        raise DiffTransError(stats["status"], "the forward render did not finish cleanly")
+    grad_out = _need(grad_out.contiguous(), torch.float32, (3,), "grad_out")
+    max_level = max(1, stats["max_level"])
+    nbytes = backward_workspace_size(max_level, V.shape[0])
+    if bws is None or bws.numel() < nbytes:
+        _, bws = _aligned_empty(nbytes, V.device)
+    dV = torch.empty_like(V)
+    dior = torch.empty(1, dtype=torch.float32, device=V.device)
+    dsig = torch.empty(3, dtype=torch.float32, device=V.device)
+    sc = _scene_struct(V, F, bvh, N, ior, sigma, env)
+    vw = _views_struct(tape.cams, tape.width, tape.height)
+    pc = tape.params.c()
+    _check(lib.dt_render_backward(ctypes.byref(sc), ctypes.byref(vw), ctypes.byref(pc), _ptr(tape.ws.buf),
+                                  tape.ws.bytes, _ptr(grad_out), _ptr(dV), _ptr(dior), _ptr(dsig), _ptr(bws),
+                                  bws.numel(), max_level, _stream(stream)))
+    return dV, dior, dsig
+
+
+def dump_segments(tape: Tape, stream=None):
+    """Every segment of the tape: (seg_i int32 [n,4] = (sample, heap node, tri,
+    flags), seg_f float32 [n,9] = (t, b1, b2, origin, direction))."""
+    stats = tape.stats if tape.stats is not None else read_stats(tape.ws, stream)
+    n = stats["segments"]
+    dev = tape.ws.buf.device
+    si = torch.empty(max(n, 1), 4, dtype=torch.int32, device=dev)
+    sf = torch.empty(max(n, 1), 9, dtype=torch.float32, device=dev)
+    _check(load_library().dt_dump_segments(_ptr(tape.ws.buf), tape.ws.bytes, _ptr(si), _ptr(sf), n,
+                                           _stream(stream)))
+    return si[:n], sf[:n]
+
+
+def l2_loss_grad(img, target, grad=None, loss=None, stream=None):
+    """Mean-squared image loss and its gradient, in the library's kernel:
+    loss = mean((img - target)^2), grad = 2 (img - target) / n."""
+    _need(img, torch.float32, None, "img")
+    _need(target, torch.float32, None, "target")
+    n = img.numel()
+    grad = torch.empty_like(img) if grad is None else grad
+    loss = torch.empty(1, dtype=torch.float32, device=img.device) if loss is None else loss
+    _check(load_library().dt_l2_loss_grad(_ptr(img), _ptr(target), n, 1.0 / max(n, 1), _ptr(grad), _ptr(loss),
+                                          _stream(stream)))
+    return grad, loss
+
+
+def profile_enable(on: bool = True):
+    _check(load_library().dt_profile_enable(1 if on else 0))
+
+
+def profile_read() -> dict:
+    """{kernel name: (launches, total ms)} since the last read (synchronises)."""
+    buf = (DtKernelTime * 64)()
+    n = c_int32()
+    _check(load_library().dt_profile_read(buf, 64, ctypes.byref(n)))
+    return {buf[i].name.decode(): (buf[i].launches, buf[i].total_ms) for i in range(min(n.value, 64))}
+
+
+# ---------------------------------------------------------------------------
+# autograd
+# ---------------------------------------------------------------------------
+class DiffTransRender(torch.autograd.Function):
+    """image = render(V, ior, sigma); backward through render_backward and the
+    vertex-normal adjoint (both in the library)."""
+
+    @staticmethod
+    def forward(ctx, V, ior, sigma, F, env, cams, width, height, params, bvh):
+        V = V.detach().contiguous()
+        N = vertex_normals(V, F)
+        if bvh is None:
+            bvh = build_bvh(V, F)
+        img, tape = render(V, F, bvh, N, ior.detach(), sigma.detach(), env, cams, width, height, params)
+        ctx.tape = tape
+        return img
+
+    @staticmethod
+    def backward(ctx, grad_img):
+        dV, dior, dsig = render_backward(ctx.tape, grad_img.contiguous())
+        ctx.tape = None
+        return dV, dior, dsig, None, None, None, None, None, None, None
+
+
+def render_differentiable(V, F, ior, sigma, env, cams, width, height, params: Params, bvh: Bvh = None):
+    """Differentiable render: gradients flow to V, ior and sigma.  Builds the
+    LBVH for V unless a BVH already built or refitted for V is given."""
+    return DiffTransRender.apply(V, ior, sigma, F, env, cams, width, height, params, bvh)

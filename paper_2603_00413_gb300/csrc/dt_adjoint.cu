@@ -1,0 +1,257 @@
+// Backward of the recursive tracer: a reverse sweep over the tape, deepest
+// level first.  For every segment s with radiance L_s it propagates
+// gbar_s = dJ/dL_s = g_pixel * W_s / spp (W_s = forward throughput) through
+// the operations of DiffTrans Sec. 3.3-3.4 at its hit:
+//   L_s = A (R L_r + T L_t)   A = exp(-sigma t) inside (Eq. 11)
+//   R, T = Fresnel (Eqs. 7-8); wr (Eq. 3); wt (Eqs. 4-6)
+//   n = normalize(sum b_i N_i) (Eq. 12), N_v from Eq. 13
+//   (t, b1, b2) from o + t d = v0 + b1 e1 + b2 e2 (hit point interpolated
+//   from the vertex positions, Sec. 3.4 "Differentiable Mesh Intersection")
+// and hands (L_s, dJ/do_s, dJ/dd_s) to its parent.  Vertex-position,
+// vertex-normal, IoR and sigma gradients are accumulated atomically.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dt_internal.cuh"
+#include "dt_shade.cuh"
+
+namespace dt {
+
+void launch_vertex_normals_backward(const float* V, int32_t nv, const int32_t* F, int32_t nf, const float* dN,
+                                    float* dV, cudaStream_t s);
+
+// backward scratch: two level buffers of (L, obar, dbar) and dN
+struct BwsLayout {
+  size_t off_buf0, off_buf1, off_dN, total;
+  BwsLayout(unsigned long long max_level, int32_t nv) {
+    const size_t lvl = (size_t)max_level * 3 * sizeof(float4);
+    off_buf0 = 0;
+    off_buf1 = align_up(off_buf0 + lvl, 256);
+    off_dN = align_up(off_buf1 + lvl, 256);
+    total = align_up(off_dN + (size_t)nv * 3 * sizeof(float), 256);
+  }
+};
+
+size_t backward_ws_bytes(unsigned long long max_level, int32_t nv) { return BwsLayout(max_level, nv).total; }
+
+struct AdjScene {
+  const float* V;
+  const int32_t* F;
+  const float* N;
+  const float* ior;
+  const float* sigma;
+  const float* env;
+  int env_w, env_h;
+};
+
+__device__ __forceinline__ void atomic_add3(float* p, float3 v) {
+  atomicAdd(p, v.x);
+  atomicAdd(p + 1, v.y);
+  atomicAdd(p + 2, v.z);
+}
+
+// out_next: (L, obar, dbar) of level k+1 indexed by position in that level;
+// out_cur: the same for level k (not written for k = 0: camera rays have no
+// parent).  Each entry is 3 float4 (xyz used).
+__global__ void __launch_bounds__(256) k_adjoint(WsView W, AdjScene S, int k, int spp, uint32_t n_pix,
+                                                 const float* __restrict__ grad_out,
+                                                 const float4* __restrict__ out_next, float4* __restrict__ out_cur,
+                                                 float* __restrict__ dV, float* __restrict__ dN,
+                                                 float* __restrict__ dior, float* __restrict__ dsigma) {
+  const WsHeader* H = W.hdr;
+  const uint32_t n = level_size(H, k);
+  const uint32_t start = H->level_start[k];
+  const uint32_t next_start = H->level_start[k + 1];
+  const uint32_t n_next = level_size(H, k + 1);
+  const float ior = __ldg(S.ior);
+  const float3 sigma = mk(__ldg(S.sigma), __ldg(S.sigma + 1), __ldg(S.sigma + 2));
+  const float inv_spp = 1.0f / (float)spp;
+  float acc_ior = 0.f;
+  float3 acc_sig = mk(0.f, 0.f, 0.f);
+  const uint32_t stride = gridDim.x * blockDim.x;
+  const uint32_t nloop = (n + 31u) & ~31u;  // whole warps, for the reductions at the end
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nloop; i += stride) {
+    if (i >= n) continue;
+    const uint32_t a = start + i;
+    const float4 ro = W.ray_o[a], rd = W.ray_d[a], rw = W.ray_w[a], hh = W.hit[a];
+    const uint32_t fl = W.sflag[a];
+    const uint32_t pix = __float_as_uint(ro.w) / (uint32_t)spp;
+    float3 L = mk(0.f, 0.f, 0.f), obar = L, dbar = L;
+    if (pix < n_pix) {
+      const float3 g = mk(__ldg(grad_out + 3 * (size_t)pix), __ldg(grad_out + 3 * (size_t)pix + 1),
+                          __ldg(grad_out + 3 * (size_t)pix + 2));
+      const float3 gbar = mul(g, mk(rw.x, rw.y, rw.z)) * inv_spp;
+      const float3 o = xyz(ro), d = xyz(rd);
+      const int32_t ch = W.child[a];
+      if (fl & SF_MISS) {
+        L = env_lookup(S.env, S.env_w, S.env_h, d);
+        dbar = env_grad_dir(S.env, S.env_w, S.env_h, d, gbar);
+      } else if (!(fl & (SF_DISCARDED | SF_BACKFACING)) && ch >= 0) {
+        const int tri = __float_as_int(hh.w);
+        const float t = hh.x, b1 = hh.y, b2 = hh.z, b0 = 1.0f - b1 - b2;
+        const int i0 = __ldg(S.F + 3 * tri), i1 = __ldg(S.F + 3 * tri + 1), i2 = __ldg(S.F + 3 * tri + 2);
+        const float3 v0 = load3(S.V + 3 * i0), v1 = load3(S.V + 3 * i1), v2 = load3(S.V + 3 * i2);
+        const float3 N0 = load3(S.N + 3 * i0), N1 = load3(S.N + 3 * i1), N2 = load3(S.N + 3 * i2);
+        const bool tir = (fl & SF_TIR) != 0;
+        HitShade h;
+        shade_hit(o, d, t, b1, b2, v0, v1, v2, N0, N1, N2, ior, sigma, h, tir ? 1 : 0);
+        // children: reflected at ch, refracted at ch + 1
+        float3 Lr = mk(0.f, 0.f, 0.f), orb = Lr, drb = Lr, Lt = Lr, otb = Lr, dtb = Lr;
+        const uint32_t jr = (uint32_t)ch - next_start;
+        if (jr < n_next) {
+          Lr = xyz(out_next[3 * jr]); orb = xyz(out_next[3 * jr + 1]); drb = xyz(out_next[3 * jr + 2]);
+        }
+        if (!tir && jr + 1 < n_next) {
+          Lt = xyz(out_next[3 * (jr + 1)]); otb = xyz(out_next[3 * (jr + 1) + 1]); dtb = xyz(out_next[3 * (jr + 1) + 2]);
+        }
+        const float R = tir ? 1.0f : h.R, T = tir ? 0.0f : h.T;
+        const float3 mix = Lr * R + Lt * T;
+        L = mul(h.A, mix);
+        // L = A (R Lr + T Lt)
+        const float3 Abar = mul(gbar, mix);
+        const float3 gA = mul(gbar, h.A);
+        const float Rbar = dot(gA, Lr), Tbar = dot(gA, Lt);
+        float tbar = 0.f;
+        if (!h.entering) {  // A_c = exp(-sigma_c t)
+          const float3 aa = mul(Abar, h.A);
+          acc_sig = acc_sig + aa * (-t);
+          tbar -= dot(aa, sigma);
+        }
+        float cbar = 0.f, etabar = 0.f, eta1bar = 0.f, eta2bar = 0.f;
+        float3 nsbar = mk(0.f, 0.f, 0.f), wibar = nsbar;
+        if (!tir) {
+          // R = (rs^2 + rp^2)/2, T = 1 - R
+          const float Re = Rbar - Tbar;
+          const float rsb = Re * h.rs, rpb = Re * h.rp;
+          const float asb = rsb / h.bs_, bsb = -rsb * h.rs / h.bs_;
+          const float apb = rpb / h.bp_, bpb = -rpb * h.rp / h.bp_;
+          // rs = (eta1 c - eta2 cos_t) / (eta1 c + eta2 cos_t)
+          eta1bar += (asb + bsb) * h.c;
+          cbar += (asb + bsb) * h.eta1;
+          eta2bar += (bsb - asb) * h.cos_t;
+          float costb = (bsb - asb) * h.eta2;
+          // rp = (eta1 cos_t - eta2 c) / (eta1 cos_t + eta2 c)
+          eta1bar += (apb + bpb) * h.cos_t;
+          costb += (apb + bpb) * h.eta1;
+          eta2bar += (bpb - apb) * h.c;
+          cbar += (bpb - apb) * h.eta2;
+          // wt = (c ns - wi) / eta - cos_t ns
+          const float3 wtb = dtb;
+          const float3 q = h.ns * h.c - h.wi;
+          wibar = wibar + wtb * (-1.0f / h.eta);
+          cbar += dot(wtb, h.ns) / h.eta;
+          nsbar = nsbar + wtb * (h.c / h.eta - h.cos_t);
+          etabar -= dot(wtb, q) / (h.eta * h.eta);
+          costb -= dot(wtb, h.ns);
+          // cos_t = sqrt(kappa) / eta, kappa = eta^2 - 1 + c^2
+          const float skb = costb / h.eta;
+          etabar -= costb * h.cos_t / h.eta;
+          const float kb = h.sk > 0.f ? skb * 0.5f / h.sk : 0.f;
+          etabar += 2.0f * h.eta * kb;
+          cbar += 2.0f * h.c * kb;
+        }
+        // wr = 2 c ns - wi
+        cbar += 2.0f * dot(drb, h.ns);
+        nsbar = nsbar + drb * (2.0f * h.c);
+        wibar = wibar - drb;
+        // eta = eta2 / eta1; the object's IoR is eta2 entering, eta1 leaving
+        eta2bar += etabar / h.eta1;
+        eta1bar -= etabar * h.eta / h.eta1;
+        acc_ior += h.entering ? eta2bar : eta1bar;
+        // c = wi . ns, wi = -d
+        wibar = wibar + h.ns * cbar;
+        nsbar = nsbar + h.wi * cbar;
+        dbar = -wibar;
+        // ns = +-n, n = m / |m|
+        const float3 nbar = h.entering ? nsbar : -nsbar;
+        const float3 mbar = (nbar - h.n * dot(h.n, nbar)) * (1.0f / h.lm);
+        // m = b0 N0 + b1 N1 + b2 N2
+        atomic_add3(dN + 3 * i0, mbar * b0);
+        atomic_add3(dN + 3 * i1, mbar * b1);
+        atomic_add3(dN + 3 * i2, mbar * b2);
+        const float b0b = dot(N0, mbar);
+        const float b1b = dot(N1, mbar) - b0b;
+        const float b2b = dot(N2, mbar) - b0b;
+        // children start at x = o + t d
+        const float3 xbar = orb + otb;
+        obar = xbar;
+        dbar = dbar + xbar * t;
+        tbar += dot(xbar, d);
+        // (t, b1, b2) solve o + t d - b0 v0 - b1 v1 - b2 v2 = 0; with
+        // J = [d, -e1, -e2], lambda = -J^-T (tbar, b1bar, b2bar):
+        // obar += lambda, dbar += t lambda, vibar -= bi lambda
+        const float3 p = cross(d, h.e2);
+        const float D3 = dot(d, h.ng);
+        const float3 lam = D3 != 0.0f ? (h.ng * (-tbar) - p * b1b + cross(d, h.e1) * b2b) * (1.0f / D3)
+                                      : mk(0.f, 0.f, 0.f);
+        obar = obar + lam;
+        dbar = dbar + lam * t;
+        atomic_add3(dV + 3 * i0, lam * (-b0));
+        atomic_add3(dV + 3 * i1, lam * (-b1));
+        atomic_add3(dV + 3 * i2, lam * (-b2));
+      }
+    }
+    if (k > 0) {
+      out_cur[3 * i] = make_float4(L.x, L.y, L.z, 0.f);
+      out_cur[3 * i + 1] = make_float4(obar.x, obar.y, obar.z, 0.f);
+      out_cur[3 * i + 2] = make_float4(dbar.x, dbar.y, dbar.z, 0.f);
+    }
+  }
+  // one atomic per warp for the scalar parameters
+  const float si = warp_sum(acc_ior);
+  const float sx = warp_sum(acc_sig.x), sy = warp_sum(acc_sig.y), sz = warp_sum(acc_sig.z);
+  if ((threadIdx.x & 31) == 0) {
+    if (si != 0.f) atomicAdd(dior, si);
+    if (sx != 0.f) atomicAdd(dsigma, sx);
+    if (sy != 0.f) atomicAdd(dsigma + 1, sy);
+    if (sz != 0.f) atomicAdd(dsigma + 2, sz);
+  }
+}
+
+// L2 seed: grad = 2 scale (img - target); loss = scale sum (img - target)^2
+__global__ void k_l2_loss_grad(const float* __restrict__ img, const float* __restrict__ target, int64_t n,
+                               float scale, float* __restrict__ grad, float* __restrict__ loss) {
+  float acc = 0.f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float r = img[i] - target[i];
+    grad[i] = 2.0f * scale * r;
+    acc += r * r;
+  }
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0 && acc != 0.f) atomicAdd(loss, acc * scale);
+}
+
+void launch_l2_loss_grad(const float* img, const float* target, int64_t n, float scale, float* grad, float* loss,
+                         cudaStream_t s) {
+  cudaMemsetAsync(loss, 0, sizeof(float), s);
+  if (n == 0) return;
+  int64_t b = (n + 255) / 256;
+  if (b > 8 * num_sms()) b = 8 * num_sms();
+  ProfScope ps("k_l2_loss_grad", s);
+  k_l2_loss_grad<<<(int)b, 256, 0, s>>>(img, target, n, scale, grad, loss);
+}
+
+void launch_backward(const dt_scene& sc, const dt_views& vw, const dt_params& p, const void* ws,
+                     unsigned long long cap, const float* grad_out, float* dV, float* dior, float* dsigma, void* bws,
+                     unsigned long long max_level, cudaStream_t s) {
+  WsView W = ws_view(ws, cap);
+  BwsLayout L(max_level, sc.nv);
+  char* b = (char*)bws;
+  float4* buf[2] = {(float4*)(b + L.off_buf0), (float4*)(b + L.off_buf1)};
+  float* dN = (float*)(b + L.off_dN);
+  cudaMemsetAsync(dN, 0, sizeof(float) * 3 * (size_t)sc.nv, s);
+  cudaMemsetAsync(dV, 0, sizeof(float) * 3 * (size_t)sc.nv, s);
+  cudaMemsetAsync(dior, 0, sizeof(float), s);
+  cudaMemsetAsync(dsigma, 0, sizeof(float) * 3, s);
+  AdjScene S{sc.d_V, sc.d_F, sc.d_N, sc.d_ior, sc.d_sigma, sc.d_env, sc.env_w, sc.env_h};
+  const uint32_t n_pix = (uint32_t)vw.n_views * vw.width * vw.height;
+  const int blocks = 8 * num_sms();
+  for (int k = p.max_depth; k >= 0; --k) {
+    ProfScope ps("k_adjoint", s);
+    k_adjoint<<<blocks, 256, 0, s>>>(W, S, k, p.spp, n_pix, grad_out, buf[(k + 1) & 1], buf[k & 1], dV, dN, dior,
+                                     dsigma);
+  }
+  launch_vertex_normals_backward(sc.d_V, sc.nv, sc.d_F, sc.nf, dN, dV, s);
+}
+
+}  // namespace dt

@@ -1,0 +1,354 @@
+// C ABI of libdifftrans (declared in include/difftrans.h): argument checks on
+// the host, then stream-ordered launches.  No device memory is allocated
+// here; every buffer comes from the caller.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "dt_internal.cuh"
+
+namespace dt {
+
+// implemented in the other translation units
+void launch_vertex_normals(const float* V, int32_t nv, const int32_t* F, int32_t nf, float* N, void* scratch,
+                           cudaStream_t s);
+size_t normals_scratch_bytes(int32_t nv);
+void launch_vertex_normals_backward(const float* V, int32_t nv, const int32_t* F, int32_t nf, const float* dN,
+                                    float* dV, cudaStream_t s);
+size_t bvh_scratch_bytes(int32_t nf);
+void launch_build(const float* V, const int32_t* F, int32_t nf, void* bvh, void* scratch, cudaStream_t s);
+void launch_refit(const float* V, const int32_t* F, int32_t nf, void* bvh, void* scratch, cudaStream_t s);
+void launch_forward(const dt_scene& sc, const dt_views& vw, const dt_params& p, float* out, void* ws,
+                    unsigned long long cap, cudaStream_t s);
+void launch_dump(const void* ws, unsigned long long cap, int32_t* si, float* sf, unsigned long long n,
+                 cudaStream_t s);
+void launch_closest_hit(const void* bvh, int32_t nf, const float* o, const float* d, const int32_t* src, int32_t n,
+                        float tmin, int32_t* tri, float* tbb, cudaStream_t s);
+size_t backward_ws_bytes(unsigned long long max_level, int32_t nv);
+void launch_l2_loss_grad(const float* img, const float* target, int64_t n, float scale, float* grad, float* loss,
+                         cudaStream_t s);
+void launch_backward(const dt_scene& sc, const dt_views& vw, const dt_params& p, const void* ws,
+                     unsigned long long cap, const float* grad_out, float* dV, float* dior, float* dsigma, void* bws,
+                     unsigned long long max_level, cudaStream_t s);
+
+static thread_local char g_err[512] = "";
+
+dt_status set_error(dt_status code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+dt_status check_launch(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(DT_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+  g_err[0] = 0;
+  return DT_OK;
+}
+
+int num_sms() {
+  static std::mutex mu;
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!cache[dev]) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+    cache[dev] = n;
+  }
+  return cache[dev];
+}
+
+static bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+// ---- per-kernel CUDA-event timing ------------------------------------------
+namespace {
+struct ProfRec {
+  std::string name;
+  cudaEvent_t start, stop;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfRec> g_prof;
+std::vector<cudaEvent_t> g_prof_pool;
+
+cudaEvent_t prof_event() {
+  if (!g_prof_pool.empty()) {
+    cudaEvent_t e = g_prof_pool.back();
+    g_prof_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+}  // namespace
+
+ProfScope::ProfScope(const char* name, cudaStream_t s) : slot(-1), stream(s) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (!g_prof_on) return;
+  ProfRec r{name, prof_event(), prof_event()};
+  cudaEventRecord(r.start, s);
+  g_prof.push_back(r);
+  slot = (int)g_prof.size() - 1;
+}
+
+ProfScope::~ProfScope() {
+  if (slot < 0) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (slot < (int)g_prof.size()) cudaEventRecord(g_prof[slot].stop, stream);
+}
+
+// the largest segment capacity whose layout fits in ws_bytes
+static unsigned long long cap_from_bytes(size_t ws_bytes) {
+  if (ws_bytes < 4096) return 0;
+  unsigned long long cap = (ws_bytes - 1024) / 72;
+  if (cap > 0x7fffffffull) cap = 0x7fffffffull;
+  while (cap > 0 && WsLayout(cap).total > ws_bytes) --cap;
+  return cap;
+}
+
+static dt_status check_scene(const dt_scene* sc) {
+  if (!sc) return set_error(DT_ERR_INVALID_ARG, "scene is NULL");
+  if (!sc->d_V || !sc->d_F || !sc->d_bvh || !sc->d_N || !sc->d_ior || !sc->d_sigma || !sc->d_env)
+    return set_error(DT_ERR_INVALID_ARG, "scene has a NULL device pointer");
+  if (sc->nv < 3 || sc->nf < 1) return set_error(DT_ERR_INVALID_ARG, "scene needs nv >= 3 and nf >= 1 (nv=%d nf=%d)",
+                                                 sc->nv, sc->nf);
+  if (sc->env_w < 1 || sc->env_h < 1) return set_error(DT_ERR_INVALID_ARG, "environment size must be positive");
+  if (!aligned(sc->d_bvh, 256)) return set_error(DT_ERR_INVALID_ARG, "BVH buffer must be 256-byte aligned");
+  return DT_OK;
+}
+
+static dt_status check_views_params(const dt_views* vw, const dt_params* p) {
+  if (!vw || !p) return set_error(DT_ERR_INVALID_ARG, "views or params is NULL");
+  if (!vw->d_cams) return set_error(DT_ERR_INVALID_ARG, "views.d_cams is NULL");
+  if (vw->n_views < 1 || vw->width < 1 || vw->height < 1)
+    return set_error(DT_ERR_INVALID_ARG, "views need n_views, width, height >= 1");
+  if (p->max_depth < 0 || p->max_depth > kMaxDepth)
+    return set_error(DT_ERR_INVALID_ARG, "max_depth must be in [0, %d] (got %d)", kMaxDepth, p->max_depth);
+  if (p->spp < 1) return set_error(DT_ERR_INVALID_ARG, "spp must be >= 1");
+  if (!(p->t_min >= 0.0f)) return set_error(DT_ERR_INVALID_ARG, "t_min must be >= 0");
+  const unsigned long long n0 = (unsigned long long)vw->n_views * vw->width * vw->height * p->spp;
+  if (n0 >= 0xffffffffull) return set_error(DT_ERR_INVALID_ARG, "too many primary rays in one call (%llu)", n0);
+  return DT_OK;
+}
+
+}  // namespace dt
+
+using namespace dt;
+
+extern "C" {
+
+const char* dt_last_error(void) { return g_err; }
+const char* dt_version(void) { return "difftrans-gb300 0.1 (sm_103a)"; }
+
+dt_status dt_vertex_normals_scratch_size(int32_t nv, size_t* bytes) {
+  if (nv < 1 || !bytes) return set_error(DT_ERR_INVALID_ARG, "need nv >= 1 and a size pointer");
+  *bytes = normals_scratch_bytes(nv);
+  return DT_OK;
+}
+
+dt_status dt_vertex_normals(const float* d_V, int32_t nv, const int32_t* d_F, int32_t nf, float* d_N,
+                            void* d_scratch, dt_stream stream) {
+  if (!d_V || !d_F || !d_N || !d_scratch) return set_error(DT_ERR_INVALID_ARG, "NULL pointer");
+  if (nv < 1 || nf < 1) return set_error(DT_ERR_INVALID_ARG, "nv and nf must be >= 1");
+  if (!aligned(d_scratch, 8)) return set_error(DT_ERR_INVALID_ARG, "scratch must be 8-byte aligned");
+  launch_vertex_normals(d_V, nv, d_F, nf, d_N, d_scratch, (cudaStream_t)stream);
+  return check_launch("dt_vertex_normals");
+}
+
+dt_status dt_vertex_normals_backward(const float* d_V, int32_t nv, const int32_t* d_F, int32_t nf, const float* d_dN,
+                                     float* d_dV, dt_stream stream) {
+  if (!d_V || !d_F || !d_dN || !d_dV) return set_error(DT_ERR_INVALID_ARG, "NULL pointer");
+  if (nv < 1 || nf < 1) return set_error(DT_ERR_INVALID_ARG, "nv and nf must be >= 1");
+  launch_vertex_normals_backward(d_V, nv, d_F, nf, d_dN, d_dV, (cudaStream_t)stream);
+  return check_launch("dt_vertex_normals_backward");
+}
+
+dt_status dt_bvh_size(int32_t nf, size_t* bvh_bytes, size_t* scratch_bytes) {
+  if (nf < 1) return set_error(DT_ERR_INVALID_ARG, "nf must be >= 1");
+  if (nf > (1 << 30)) return set_error(DT_ERR_INVALID_ARG, "nf must be <= 2^30");
+  if (bvh_bytes) *bvh_bytes = BvhLayout(nf).total;
+  if (scratch_bytes) *scratch_bytes = bvh_scratch_bytes(nf);
+  return DT_OK;
+}
+
+dt_status dt_build_bvh(const float* d_V, int32_t nv, const int32_t* d_F, int32_t nf, void* d_bvh, void* d_scratch,
+                       dt_stream stream) {
+  if (!d_V || !d_F || !d_bvh || !d_scratch) return set_error(DT_ERR_INVALID_ARG, "NULL pointer");
+  if (nv < 3 || nf < 1 || nf > (1 << 30)) return set_error(DT_ERR_INVALID_ARG, "need nv >= 3 and 1 <= nf <= 2^30");
+  if (!aligned(d_bvh, 256) || !aligned(d_scratch, 256))
+    return set_error(DT_ERR_INVALID_ARG, "BVH and scratch buffers must be 256-byte aligned");
+  launch_build(d_V, d_F, nf, d_bvh, d_scratch, (cudaStream_t)stream);
+  return check_launch("dt_build_bvh");
+}
+
+dt_status dt_refit_bvh(const float* d_V, int32_t nv, const int32_t* d_F, int32_t nf, void* d_bvh, void* d_scratch,
+                       dt_stream stream) {
+  if (!d_V || !d_F || !d_bvh || !d_scratch) return set_error(DT_ERR_INVALID_ARG, "NULL pointer");
+  if (nv < 3 || nf < 1 || nf > (1 << 30)) return set_error(DT_ERR_INVALID_ARG, "need nv >= 3 and 1 <= nf <= 2^30");
+  if (!aligned(d_bvh, 256) || !aligned(d_scratch, 256))
+    return set_error(DT_ERR_INVALID_ARG, "BVH and scratch buffers must be 256-byte aligned");
+  launch_refit(d_V, d_F, nf, d_bvh, d_scratch, (cudaStream_t)stream);
+  return check_launch("dt_refit_bvh");
+}
+
+dt_status dt_render_workspace_size(int64_t seg_capacity, size_t* ws_bytes) {
+  if (seg_capacity < 1 || seg_capacity > 0x7fffffffll)
+    return set_error(DT_ERR_INVALID_ARG, "seg_capacity must be in [1, 2^31-1]");
+  if (!ws_bytes) return set_error(DT_ERR_INVALID_ARG, "ws_bytes is NULL");
+  *ws_bytes = WsLayout((unsigned long long)seg_capacity).total;
+  return DT_OK;
+}
+
+dt_status dt_render(const dt_scene* scene, const dt_views* views, const dt_params* params, float* d_out, void* d_ws,
+                    size_t ws_bytes, dt_stream stream) {
+  dt_status st = check_scene(scene);
+  if (st) return st;
+  if ((st = check_views_params(views, params))) return st;
+  if (!d_out || !d_ws) return set_error(DT_ERR_INVALID_ARG, "NULL output or workspace");
+  if (!aligned(d_ws, 256)) return set_error(DT_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+  const unsigned long long cap = cap_from_bytes(ws_bytes);
+  const unsigned long long n0 = (unsigned long long)views->n_views * views->width * views->height * params->spp;
+  if (cap < n0)
+    return set_error(DT_ERR_INVALID_ARG, "workspace holds %llu segments, fewer than the %llu camera rays", cap, n0);
+  launch_forward(*scene, *views, *params, d_out, d_ws, cap, (cudaStream_t)stream);
+  return check_launch("dt_render");
+}
+
+dt_status dt_read_stats(const void* d_ws, size_t ws_bytes, dt_stats* out, dt_stream stream) {
+  if (!d_ws || !out) return set_error(DT_ERR_INVALID_ARG, "NULL pointer");
+  if (cap_from_bytes(ws_bytes) == 0) return set_error(DT_ERR_INVALID_ARG, "workspace too small");
+  WsHeader h;
+  cudaError_t e = cudaMemcpyAsync(&h, d_ws, sizeof(WsHeader), cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return set_error(DT_ERR_CUDA, "dt_read_stats: %s", cudaGetErrorString(e));
+  memset(out, 0, sizeof(*out));
+  out->status = (h.status & ST_QUEUE_OVERFLOW) ? DT_ERR_QUEUE_OVERFLOW
+              : (h.status & ST_STACK_OVERFLOW) ? DT_ERR_STACK_OVERFLOW : DT_OK;
+  out->n_levels = (int32_t)h.n_levels;
+  long long seg = 0, need = 0, mx = 0;
+  for (int k = 0; k < kMaxLevels; ++k) {
+    const unsigned long long start = h.level_start[k];
+    unsigned long long n = h.level_count[k];
+    need += (long long)n;
+    if (k >= (int)h.n_levels) n = 0;
+    const unsigned long long room = start < h.capacity ? h.capacity - start : 0ull;
+    if (n > room) n = room;
+    out->level_count[k] = (int64_t)n;
+    out->level_start[k] = (int64_t)start;
+    seg += (long long)n;
+    if ((long long)n > mx) mx = (long long)n;
+  }
+  out->segments = seg;
+  out->seg_needed = need;
+  out->max_level = mx;
+  out->hits = (int64_t)h.counters[CNT_HITS];
+  out->misses = (int64_t)h.counters[CNT_MISSES];
+  out->discarded = (int64_t)h.counters[CNT_DISCARDED];
+  out->backfacing = (int64_t)h.counters[CNT_BACKFACING];
+  out->tir = (int64_t)h.counters[CNT_TIR];
+  out->nodes_visited = (int64_t)h.counters[CNT_NODES];
+  out->tris_tested = (int64_t)h.counters[CNT_TRIS];
+  g_err[0] = 0;
+  return DT_OK;
+}
+
+dt_status dt_backward_workspace_size(int64_t max_level, int32_t nv, size_t* bytes) {
+  if (max_level < 1 || nv < 1 || !bytes) return set_error(DT_ERR_INVALID_ARG, "need max_level >= 1, nv >= 1");
+  *bytes = backward_ws_bytes((unsigned long long)max_level, nv);
+  return DT_OK;
+}
+
+dt_status dt_render_backward(const dt_scene* scene, const dt_views* views, const dt_params* params, const void* d_ws,
+                             size_t ws_bytes, const float* d_grad_out, float* d_grad_V, float* d_grad_ior,
+                             float* d_grad_sigma, void* d_bws, size_t bws_bytes, int64_t max_level,
+                             dt_stream stream) {
+  dt_status st = check_scene(scene);
+  if (st) return st;
+  if ((st = check_views_params(views, params))) return st;
+  if (!d_ws || !d_grad_out || !d_grad_V || !d_grad_ior || !d_grad_sigma || !d_bws)
+    return set_error(DT_ERR_INVALID_ARG, "NULL pointer");
+  const unsigned long long cap = cap_from_bytes(ws_bytes);
+  if (cap == 0) return set_error(DT_ERR_INVALID_ARG, "workspace too small");
+  if (max_level < 1) return set_error(DT_ERR_INVALID_ARG, "max_level must be >= 1");
+  if (bws_bytes < backward_ws_bytes((unsigned long long)max_level, scene->nv))
+    return set_error(DT_ERR_INVALID_ARG, "backward workspace smaller than dt_backward_workspace_size");
+  if (!aligned(d_bws, 256)) return set_error(DT_ERR_INVALID_ARG, "backward workspace must be 256-byte aligned");
+  launch_backward(*scene, *views, *params, d_ws, cap, d_grad_out, d_grad_V, d_grad_ior, d_grad_sigma, d_bws,
+                  (unsigned long long)max_level, (cudaStream_t)stream);
+  return check_launch("dt_render_backward");
+}
+
+dt_status dt_dump_segments(const void* d_ws, size_t ws_bytes, int32_t* d_seg_i, float* d_seg_f, int64_t cap,
+                           dt_stream stream) {
+  if (!d_ws || !d_seg_i || !d_seg_f || cap < 0) return set_error(DT_ERR_INVALID_ARG, "bad argument");
+  const unsigned long long wcap = cap_from_bytes(ws_bytes);
+  if (wcap == 0) return set_error(DT_ERR_INVALID_ARG, "workspace too small");
+  launch_dump(d_ws, wcap, d_seg_i, d_seg_f, (unsigned long long)cap, (cudaStream_t)stream);
+  return check_launch("dt_dump_segments");
+}
+
+dt_status dt_profile_enable(int32_t enable) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof_on = enable != 0;
+  return DT_OK;
+}
+
+dt_status dt_profile_read(dt_kernel_time* out, int32_t cap, int32_t* n) {
+  if (!n || (cap > 0 && !out)) return set_error(DT_ERR_INVALID_ARG, "NULL pointer");
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  std::vector<std::string> names;
+  std::vector<int64_t> cnt;
+  std::vector<double> ms;
+  for (ProfRec& r : g_prof) {
+    cudaError_t e = cudaEventSynchronize(r.stop);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, r.start, r.stop);
+    if (e != cudaSuccess) return set_error(DT_ERR_CUDA, "dt_profile_read: %s", cudaGetErrorString(e));
+    size_t k = 0;
+    while (k < names.size() && names[k] != r.name) ++k;
+    if (k == names.size()) { names.push_back(r.name); cnt.push_back(0); ms.push_back(0.0); }
+    cnt[k] += 1;
+    ms[k] += t;
+    g_prof_pool.push_back(r.start);
+    g_prof_pool.push_back(r.stop);
+  }
+  g_prof.clear();
+  *n = (int32_t)names.size();
+  for (int32_t k = 0; k < *n && k < cap; ++k) {
+    memset(out[k].name, 0, sizeof(out[k].name));
+    strncpy(out[k].name, names[k].c_str(), sizeof(out[k].name) - 1);
+    out[k].launches = cnt[k];
+    out[k].total_ms = ms[k];
+  }
+  return DT_OK;
+}
+
+dt_status dt_l2_loss_grad(const float* d_img, const float* d_target, int64_t n, float scale, float* d_grad,
+                          float* d_loss, dt_stream stream) {
+  if (!d_img || !d_target || !d_grad || !d_loss || n < 0) return set_error(DT_ERR_INVALID_ARG, "bad argument");
+  launch_l2_loss_grad(d_img, d_target, n, scale, d_grad, d_loss, (cudaStream_t)stream);
+  return check_launch("dt_l2_loss_grad");
+}
+
+dt_status dt_closest_hit(const void* d_bvh, int32_t nf, const float* d_o, const float* d_d, const int32_t* d_src,
+                         int32_t n, float t_min, int32_t* d_tri, float* d_tbb, dt_stream stream) {
+  if (!d_bvh || !d_o || !d_d || !d_tri || !d_tbb) return set_error(DT_ERR_INVALID_ARG, "NULL pointer");
+  if (nf < 1 || n < 0) return set_error(DT_ERR_INVALID_ARG, "need nf >= 1 and n >= 0");
+  if (!aligned(d_bvh, 256)) return set_error(DT_ERR_INVALID_ARG, "BVH buffer must be 256-byte aligned");
+  if (n == 0) return DT_OK;
+  launch_closest_hit(d_bvh, nf, d_o, d_d, d_src, n, t_min, d_tri, d_tbb, (cudaStream_t)stream);
+  return check_launch("dt_closest_hit");
+}
+
+}  // extern "C"

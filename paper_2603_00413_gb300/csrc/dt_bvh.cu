@@ -1,0 +1,432 @@
+// Geometry kernels: vertex normals (DiffTrans Sec. 3.4, Eq. 13) and their
+// backward, and the LBVH (Morton codes, a stable LSD radix sort, the Karras
+// 2012 hierarchy, bottom-up bounds written straight into the float4 node
+// layout that the traversal reads).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dt_internal.cuh"
+
+namespace dt {
+
+// ---------------------------------------------------------------------------
+// Eq. 13: N_v = (1/3) sum_{f containing v} unit((v1 - v0) x (v2 - v0)).
+// One thread per face adds its unit normal, in 2^-40 fixed point, to its
+// three vertices with 64-bit integer atomics: integer addition is
+// associative, so the sums -- and every ray that depends on them -- are the
+// same bits on every run whatever order the atomics land in.  A second pass
+// converts to float and applies the 1/3.
+// ---------------------------------------------------------------------------
+constexpr double kNormalFix = 1099511627776.0;  // 2^40
+
+__global__ void k_face_normals_scatter(const float* __restrict__ V, const int32_t* __restrict__ F, int32_t nf,
+                                       unsigned long long* __restrict__ acc) {
+  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nf; f += gridDim.x * blockDim.x) {
+    const int i0 = F[3 * f], i1 = F[3 * f + 1], i2 = F[3 * f + 2];
+    const float3 v0 = load3(V + 3 * i0), v1 = load3(V + 3 * i1), v2 = load3(V + 3 * i2);
+    const float3 u = normalize(cross(v1 - v0, v2 - v0));
+    const long long q[3] = {__double2ll_rn((double)u.x * kNormalFix), __double2ll_rn((double)u.y * kNormalFix),
+                            __double2ll_rn((double)u.z * kNormalFix)};
+    const int idx[3] = {i0, i1, i2};
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) atomicAdd(acc + 3 * (size_t)idx[k] + c, (unsigned long long)q[c]);
+  }
+}
+
+__global__ void k_normals_finish(const unsigned long long* __restrict__ acc, int64_t n3, float* __restrict__ N) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x)
+    N[i] = (float)((double)(long long)acc[i] * (1.0 / kNormalFix) / 3.0);
+}
+
+// Backward of Eq. 13.  Face f's unit normal u = c/|c|, c = e1 x e2, feeds
+// (1/3) u to each of its vertices, so du = (1/3)(dN_v0 + dN_v1 + dN_v2);
+// dc = (du - u (u.du)) / |c|; c = e1 x e2 gives de1 = e2 x dc, de2 = dc x e1;
+// then dv1 += de1, dv2 += de2, dv0 -= de1 + de2.
+__global__ void k_face_normals_backward(const float* __restrict__ V, const int32_t* __restrict__ F, int32_t nf,
+                                        const float* __restrict__ dN, float* __restrict__ dV) {
+  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nf; f += gridDim.x * blockDim.x) {
+    const int i0 = F[3 * f], i1 = F[3 * f + 1], i2 = F[3 * f + 2];
+    const float3 v0 = load3(V + 3 * i0), v1 = load3(V + 3 * i1), v2 = load3(V + 3 * i2);
+    const float3 e1 = v1 - v0, e2 = v2 - v0;
+    const float3 c = cross(e1, e2);
+    const float lc = len(c);
+    const float3 u = mk(c.x / lc, c.y / lc, c.z / lc);
+    const float3 du = (load3(dN + 3 * i0) + load3(dN + 3 * i1) + load3(dN + 3 * i2)) * (1.0f / 3.0f);
+    const float3 dc = (du - u * dot(u, du)) * (1.0f / lc);
+    const float3 de1 = cross(e2, dc), de2 = cross(dc, e1);
+    const float3 dv0 = -(de1 + de2);
+    atomicAdd(dV + 3 * i0 + 0, dv0.x); atomicAdd(dV + 3 * i0 + 1, dv0.y); atomicAdd(dV + 3 * i0 + 2, dv0.z);
+    atomicAdd(dV + 3 * i1 + 0, de1.x); atomicAdd(dV + 3 * i1 + 1, de1.y); atomicAdd(dV + 3 * i1 + 2, de1.z);
+    atomicAdd(dV + 3 * i2 + 0, de2.x); atomicAdd(dV + 3 * i2 + 1, de2.y); atomicAdd(dV + 3 * i2 + 2, de2.z);
+  }
+}
+
+size_t normals_scratch_bytes(int32_t nv) { return align_up((size_t)nv * 3 * sizeof(unsigned long long), 256); }
+
+void launch_vertex_normals(const float* V, int32_t nv, const int32_t* F, int32_t nf, float* N, void* scratch,
+                           cudaStream_t s) {
+  ProfScope ps("k_vertex_normals", s);
+  unsigned long long* acc = (unsigned long long*)scratch;
+  cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * 3 * (size_t)nv, s);
+  const int blocks = (int)((nf + 255) / 256) < 4 * num_sms() ? (int)((nf + 255) / 256) : 4 * num_sms();
+  k_face_normals_scatter<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(V, F, nf, acc);
+  const int64_t n3 = 3 * (int64_t)nv;
+  const int b2 = (int)((n3 + 255) / 256) < 4 * num_sms() ? (int)((n3 + 255) / 256) : 4 * num_sms();
+  k_normals_finish<<<b2 > 0 ? b2 : 1, 256, 0, s>>>(acc, n3, N);
+}
+
+void launch_vertex_normals_backward(const float* V, int32_t nv, const int32_t* F, int32_t nf, const float* dN,
+                                    float* dV, cudaStream_t s) {
+  (void)nv;
+  ProfScope ps("k_face_normals_backward", s);
+  const int blocks = (int)((nf + 255) / 256) < 4 * num_sms() ? (int)((nf + 255) / 256) : 4 * num_sms();
+  k_face_normals_backward<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(V, F, nf, dN, dV);
+}
+
+// ---------------------------------------------------------------------------
+// LBVH build
+// ---------------------------------------------------------------------------
+// float <-> order-preserving unsigned, for atomicMin/Max on floats
+__device__ __forceinline__ uint32_t f2ord(float f) {
+  uint32_t b = __float_as_uint(f);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float ord2f(uint32_t o) {
+  return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
+}
+
+// scratch: bounds of the centroids as ordered uints [lo xyz, hi xyz]
+__global__ void k_init_bounds(uint32_t* b) {
+  if (threadIdx.x < 3) b[threadIdx.x] = 0xffffffffu;
+  else if (threadIdx.x < 6) b[threadIdx.x] = 0u;
+}
+
+__device__ __forceinline__ float3 centroid_of(const float* V, const int32_t* F, int f) {
+  const float3 v0 = load3(V + 3 * F[3 * f]), v1 = load3(V + 3 * F[3 * f + 1]), v2 = load3(V + 3 * F[3 * f + 2]);
+  return (v0 + v1 + v2) * (1.0f / 3.0f);
+}
+
+__global__ void k_centroid_bounds(const float* __restrict__ V, const int32_t* __restrict__ F, int32_t nf,
+                                  uint32_t* __restrict__ b) {
+  float3 lo = mk(INFINITY, INFINITY, INFINITY), hi = mk(-INFINITY, -INFINITY, -INFINITY);
+  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nf; f += gridDim.x * blockDim.x) {
+    const float3 c = centroid_of(V, F, f);
+    lo = mk(fminf(lo.x, c.x), fminf(lo.y, c.y), fminf(lo.z, c.z));
+    hi = mk(fmaxf(hi.x, c.x), fmaxf(hi.y, c.y), fmaxf(hi.z, c.z));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    lo.x = fminf(lo.x, __shfl_xor_sync(kFull, lo.x, o));
+    lo.y = fminf(lo.y, __shfl_xor_sync(kFull, lo.y, o));
+    lo.z = fminf(lo.z, __shfl_xor_sync(kFull, lo.z, o));
+    hi.x = fmaxf(hi.x, __shfl_xor_sync(kFull, hi.x, o));
+    hi.y = fmaxf(hi.y, __shfl_xor_sync(kFull, hi.y, o));
+    hi.z = fmaxf(hi.z, __shfl_xor_sync(kFull, hi.z, o));
+  }
+  if ((threadIdx.x & 31) == 0 && lo.x <= hi.x) {
+    atomicMin(b + 0, f2ord(lo.x)); atomicMin(b + 1, f2ord(lo.y)); atomicMin(b + 2, f2ord(lo.z));
+    atomicMax(b + 3, f2ord(hi.x)); atomicMax(b + 4, f2ord(hi.y)); atomicMax(b + 5, f2ord(hi.z));
+  }
+}
+
+// 10 bits per axis interleaved into a 30-bit Morton code
+__device__ __forceinline__ uint32_t spread10(uint32_t v) {
+  v = (v | (v << 16)) & 0x030000FFu;
+  v = (v | (v << 8)) & 0x0300F00Fu;
+  v = (v | (v << 4)) & 0x030C30C3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+
+__global__ void k_morton(const float* __restrict__ V, const int32_t* __restrict__ F, int32_t nf,
+                         const uint32_t* __restrict__ b, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  const float3 lo = mk(ord2f(b[0]), ord2f(b[1]), ord2f(b[2]));
+  const float3 hi = mk(ord2f(b[3]), ord2f(b[4]), ord2f(b[5]));
+  const float3 ext = mk(fmaxf(hi.x - lo.x, 1e-30f), fmaxf(hi.y - lo.y, 1e-30f), fmaxf(hi.z - lo.z, 1e-30f));
+  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nf; f += gridDim.x * blockDim.x) {
+    const float3 c = centroid_of(V, F, f);
+    const uint32_t x = (uint32_t)fminf(fmaxf((c.x - lo.x) / ext.x * 1024.0f, 0.0f), 1023.0f);
+    const uint32_t y = (uint32_t)fminf(fmaxf((c.y - lo.y) / ext.y * 1024.0f, 0.0f), 1023.0f);
+    const uint32_t z = (uint32_t)fminf(fmaxf((c.z - lo.z) / ext.z * 1024.0f, 0.0f), 1023.0f);
+    keys[f] = (spread10(x) << 2) | (spread10(y) << 1) | spread10(z);
+    vals[f] = (uint32_t)f;
+  }
+}
+
+// ---- stable LSD radix sort, 8 bits per pass -------------------------------
+constexpr int kSortThreads = 256;
+constexpr int kSortIpt = 4;
+constexpr int kSortTile = kSortThreads * kSortIpt;
+constexpr int kSortWarps = kSortThreads / 32;
+
+// hist is digit-major: hist[d * nblocks + block]
+__global__ void k_radix_hist(const uint32_t* __restrict__ keys, int32_t n, int shift, uint32_t* __restrict__ hist) {
+  __shared__ uint32_t cnt[256];
+  cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const int base = blockIdx.x * kSortTile;
+  for (int j = 0; j < kSortIpt; ++j) {
+    const int i = base + j * kSortThreads + threadIdx.x;
+    if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & 0xffu], 1u);
+  }
+  __syncthreads();
+  hist[threadIdx.x * gridDim.x + blockIdx.x] = cnt[threadIdx.x];
+}
+
+// exclusive scan of m entries in one block of 1024 threads
+__global__ void k_scan_exclusive(uint32_t* __restrict__ a, int32_t m) {
+  __shared__ uint32_t part[1024];
+  const int per = (m + 1023) / 1024;
+  const int lo = threadIdx.x * per;
+  const int hi = min(lo + per, m);
+  uint32_t s = 0;
+  for (int i = lo; i < hi; ++i) s += a[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {  // Hillis-Steele inclusive scan of the partial sums
+    uint32_t v = threadIdx.x >= o ? part[threadIdx.x - o] : 0u;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  uint32_t run = threadIdx.x ? part[threadIdx.x - 1] : 0u;
+  for (int i = lo; i < hi; ++i) {
+    const uint32_t v = a[i];
+    a[i] = run;
+    run += v;
+  }
+}
+
+// Scatter a tile keeping the input order among equal digits: items are taken
+// in order j (stride kSortThreads), then warp, then lane; within a warp the
+// rank among equal digits comes from __match_any_sync, across warps from a
+// per-step prefix over per-warp digit counts.
+__global__ void k_radix_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, int32_t n,
+                                int shift, const uint32_t* __restrict__ hist, uint32_t* __restrict__ kout,
+                                uint32_t* __restrict__ vout) {
+  __shared__ uint32_t off[256];
+  __shared__ uint32_t wcnt[kSortWarps][256];
+  __shared__ uint32_t step_total[256];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  off[tid] = hist[tid * gridDim.x + blockIdx.x];
+  const int base = blockIdx.x * kSortTile;
+  const unsigned lanemask_lt = (1u << lane) - 1u;
+  for (int j = 0; j < kSortIpt; ++j) {
+    for (int w = 0; w < kSortWarps; ++w) wcnt[w][tid] = 0;
+    __syncthreads();
+    const int i = base + j * kSortThreads + tid;
+    const bool valid = i < n;
+    uint32_t key = 0, val = 0, dg = 256;
+    if (valid) {
+      key = kin[i];
+      val = vin[i];
+      dg = (key >> shift) & 0xffu;
+    }
+    const unsigned peers = __match_any_sync(kFull, dg);
+    const uint32_t rank = __popc(peers & lanemask_lt);
+    if (valid && rank == 0) wcnt[warp][dg] = __popc(peers);
+    __syncthreads();
+    {  // thread tid owns digit tid: prefix over warps
+      uint32_t run = 0;
+      for (int w = 0; w < kSortWarps; ++w) {
+        const uint32_t c = wcnt[w][tid];
+        wcnt[w][tid] = run;
+        run += c;
+      }
+      step_total[tid] = run;
+    }
+    __syncthreads();
+    if (valid) {
+      const uint32_t pos = off[dg] + wcnt[warp][dg] + rank;
+      if (pos < (uint32_t)n) {
+        kout[pos] = key;
+        vout[pos] = val;
+      }
+    }
+    __syncthreads();
+    off[tid] += step_total[tid];
+  }
+}
+
+// ---- Karras (2012) hierarchy ------------------------------------------------
+// delta(a, b): length of the common prefix of keys a and b, with the index
+// appended to break ties between equal keys; -1 outside [0, n).
+__device__ __forceinline__ int lcp(const uint32_t* keys, int n, int a, int b) {
+  if (b < 0 || b >= n) return -1;
+  const uint32_t ka = keys[a], kb = keys[b];
+  if (ka == kb) return 32 + __clz((uint32_t)a ^ (uint32_t)b);
+  return __clz(ka ^ kb);
+}
+
+__global__ void k_karras(const uint32_t* __restrict__ keys, int32_t n, float4* __restrict__ nodes,
+                         int32_t* __restrict__ parent) {
+  const int n_int = n - 1;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_int; i += gridDim.x * blockDim.x) {
+    const int d = (lcp(keys, n, i, i + 1) - lcp(keys, n, i, i - 1)) >= 0 ? 1 : -1;
+    const int dmin = lcp(keys, n, i, i - d);
+    int lmax = 2;
+    while (lcp(keys, n, i, i + lmax * d) > dmin) lmax *= 2;
+    int l = 0;
+    for (int t = lmax / 2; t >= 1; t /= 2)
+      if (lcp(keys, n, i, i + (l + t) * d) > dmin) l += t;
+    const int j = i + l * d;
+    const int dnode = lcp(keys, n, i, j);
+    int s = 0;
+    for (int div = 2;; div *= 2) {
+      const int t = (l + div - 1) / div;
+      if (lcp(keys, n, i, i + (s + t) * d) > dnode) s += t;
+      if (t <= 1) break;
+    }
+    const int gamma = i + s * d + (d < 0 ? -1 : 0);
+    const int lo = min(i, j), hi = max(i, j);
+    const int left = (lo == gamma) ? ~gamma : gamma;
+    const int right = (hi == gamma + 1) ? ~(gamma + 1) : gamma + 1;
+    reinterpret_cast<int4*>(nodes)[4 * i + 3] = make_int4(left, right, 0, 0);
+    parent[left < 0 ? n_int + gamma : gamma] = i;
+    parent[right < 0 ? n_int + gamma + 1 : gamma + 1] = i;
+    if (i == 0) parent[0] = -1;
+  }
+}
+
+// one triangle: a single internal node whose second child has an empty box
+__global__ void k_single_leaf(float4* nodes, int32_t* parent) {
+  const float inf = INFINITY;
+  nodes[1] = make_float4(inf, -inf, inf, -inf);
+  nodes[2] = make_float4(0.f, 0.f, inf, -inf);
+  reinterpret_cast<int4*>(nodes)[3] = make_int4(~0, ~0, 0, 0);
+  parent[0] = -1;
+  parent[1] = 0;
+}
+
+__global__ void k_gather_leaf_tri(const uint32_t* __restrict__ vals, int32_t n, int32_t* __restrict__ leaf_tri) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) leaf_tri[i] = (int32_t)vals[i];
+}
+
+// ---- bottom-up bounds --------------------------------------------------------
+__device__ __forceinline__ void store_child_box(float4* node, int slot, float3 lo, float3 hi) {
+  // slot 0: n0 = (lo.x, hi.x, lo.y, hi.y), n2.xy = (lo.z, hi.z); slot 1: n1, n2.zw
+  volatile float* n = reinterpret_cast<volatile float*>(node);
+  const int b = slot * 4;
+  n[b + 0] = lo.x; n[b + 1] = hi.x; n[b + 2] = lo.y; n[b + 3] = hi.y;
+  n[8 + 2 * slot] = lo.z; n[8 + 2 * slot + 1] = hi.z;
+}
+
+__device__ __forceinline__ void load_child_box(const float4* node, int slot, float3& lo, float3& hi) {
+  const volatile float* n = reinterpret_cast<const volatile float*>(node);
+  const int b = slot * 4;
+  lo = mk(n[b + 0], n[b + 2], n[8 + 2 * slot]);
+  hi = mk(n[b + 1], n[b + 3], n[8 + 2 * slot + 1]);
+}
+
+// Each leaf writes its triangle record and box, then climbs: the first of two
+// children to reach a node stops, the second merges both boxes and goes on.
+__global__ void k_refit(const float* __restrict__ V, const int32_t* __restrict__ F, int32_t nf, BvhView B,
+                        uint32_t* __restrict__ arrive) {
+  const int n_int = B.hdr->n_int;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += gridDim.x * blockDim.x) {
+    const int tri = B.leaf_tri[i];
+    const float3 v0 = load3(V + 3 * F[3 * tri]), v1 = load3(V + 3 * F[3 * tri + 1]), v2 = load3(V + 3 * F[3 * tri + 2]);
+    B.tris[3 * i + 0] = make_float4(v0.x, v0.y, v0.z, __int_as_float(tri));
+    const float3 e1 = v1 - v0, e2 = v2 - v0;
+    B.tris[3 * i + 1] = make_float4(e1.x, e1.y, e1.z, 0.f);
+    B.tris[3 * i + 2] = make_float4(e2.x, e2.y, e2.z, 0.f);
+    float3 lo = mk(fminf(v0.x, fminf(v1.x, v2.x)), fminf(v0.y, fminf(v1.y, v2.y)), fminf(v0.z, fminf(v1.z, v2.z)));
+    float3 hi = mk(fmaxf(v0.x, fmaxf(v1.x, v2.x)), fmaxf(v0.y, fmaxf(v1.y, v2.y)), fmaxf(v0.z, fmaxf(v1.z, v2.z)));
+    int me = ~i;
+    int node = B.parent[n_int + i];
+    // a path to the root has at most n_int nodes; the bound guards a corrupt tree
+    for (int hops = 0; node >= 0 && node < n_int && hops <= n_int; ++hops) {
+      float4* rec = B.nodes + 4 * node;
+      const int4 ch = reinterpret_cast<const int4*>(rec)[3];
+      const int slot = (ch.x == me) ? 0 : 1;
+      store_child_box(rec, slot, lo, hi);
+      __threadfence();
+      const uint32_t prev = atomicAdd(arrive + node, 1u);
+      if (prev == 0) break;  // the sibling is still on its way
+      __threadfence();
+      float3 olo, ohi;
+      load_child_box(rec, 1 - slot, olo, ohi);
+      lo = mk(fminf(lo.x, olo.x), fminf(lo.y, olo.y), fminf(lo.z, olo.z));
+      hi = mk(fmaxf(hi.x, ohi.x), fmaxf(hi.y, ohi.y), fmaxf(hi.z, ohi.z));
+      me = node;
+      node = B.parent[node];
+    }
+  }
+}
+
+__global__ void k_bvh_header(BvhHeader* h, int32_t nf) {
+  h->nf = nf;
+  h->n_int = nf > 1 ? nf - 1 : 1;
+  h->root = 0;
+  h->pad = 0;
+}
+
+// scratch layout for build/refit
+struct BuildScratch {
+  uint32_t *keys_a, *keys_b, *vals_a, *vals_b, *hist, *arrive, *bounds;
+  size_t total;
+  BuildScratch(void* base, int32_t nf) {
+    const int nblocks = (nf + kSortTile - 1) / kSortTile;
+    const size_t n_int = nf > 1 ? (size_t)nf - 1 : 1;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes, 256); return r; };
+    const size_t ka = take(sizeof(uint32_t) * nf), kb = take(sizeof(uint32_t) * nf);
+    const size_t va = take(sizeof(uint32_t) * nf), vb = take(sizeof(uint32_t) * nf);
+    const size_t hi = take(sizeof(uint32_t) * 256 * (size_t)nblocks);
+    const size_t ar = take(sizeof(uint32_t) * n_int);
+    const size_t bo = take(sizeof(uint32_t) * 8);
+    total = o;
+    char* b = (char*)base;
+    keys_a = (uint32_t*)(b + ka); keys_b = (uint32_t*)(b + kb);
+    vals_a = (uint32_t*)(b + va); vals_b = (uint32_t*)(b + vb);
+    hist = (uint32_t*)(b + hi); arrive = (uint32_t*)(b + ar); bounds = (uint32_t*)(b + bo);
+  }
+};
+
+size_t bvh_scratch_bytes(int32_t nf) { return BuildScratch(nullptr, nf).total; }
+
+static int grid_for(int64_t n, int threads) {
+  int64_t b = (n + threads - 1) / threads;
+  const int64_t cap = 8 * (int64_t)num_sms();
+  if (b > cap) b = cap;
+  return b < 1 ? 1 : (int)b;
+}
+
+void launch_refit(const float* V, const int32_t* F, int32_t nf, void* bvh, void* scratch, cudaStream_t s) {
+  BvhView B = bvh_view(bvh, nf);
+  BuildScratch S(scratch, nf);
+  const size_t n_int = nf > 1 ? (size_t)nf - 1 : 1;
+  ProfScope ps("k_refit", s);
+  cudaMemsetAsync(S.arrive, 0, sizeof(uint32_t) * n_int, s);
+  k_refit<<<grid_for(nf, 256), 256, 0, s>>>(V, F, nf, B, S.arrive);
+}
+
+void launch_build(const float* V, const int32_t* F, int32_t nf, void* bvh, void* scratch, cudaStream_t s) {
+  BvhView B = bvh_view(bvh, nf);
+  BuildScratch S(scratch, nf);
+  ProfScope ps("lbvh_build", s);
+  k_bvh_header<<<1, 1, 0, s>>>(B.hdr, nf);
+  k_init_bounds<<<1, 32, 0, s>>>(S.bounds);
+  k_centroid_bounds<<<grid_for(nf, 256), 256, 0, s>>>(V, F, nf, S.bounds);
+  k_morton<<<grid_for(nf, 256), 256, 0, s>>>(V, F, nf, S.bounds, S.keys_a, S.vals_a);
+  const int nblocks = (nf + kSortTile - 1) / kSortTile;
+  uint32_t *kin = S.keys_a, *vin = S.vals_a, *kout = S.keys_b, *vout = S.vals_b;
+  for (int shift = 0; shift < 32; shift += 8) {
+    k_radix_hist<<<nblocks, kSortThreads, 0, s>>>(kin, nf, shift, S.hist);
+    k_scan_exclusive<<<1, 1024, 0, s>>>(S.hist, 256 * nblocks);
+    k_radix_scatter<<<nblocks, kSortThreads, 0, s>>>(kin, vin, nf, shift, S.hist, kout, vout);
+    uint32_t* t = kin; kin = kout; kout = t;
+    t = vin; vin = vout; vout = t;
+  }
+  // after an even number of passes the sorted data is back in keys_a/vals_a
+  k_gather_leaf_tri<<<grid_for(nf, 256), 256, 0, s>>>(vin, nf, B.leaf_tri);
+  if (nf > 1) {
+    k_karras<<<grid_for(nf - 1, 256), 256, 0, s>>>(kin, nf, B.nodes, B.parent);
+  } else {
+    k_single_leaf<<<1, 1, 0, s>>>(B.nodes, B.parent);
+  }
+  launch_refit(V, F, nf, bvh, scratch, s);
+}
+
+}  // namespace dt

@@ -1,0 +1,208 @@
+// Internal definitions shared by the CUDA translation units of libdifftrans:
+// float3 arithmetic, the device layouts of the BVH buffer and of the render
+// workspace (the segment "tape"), segment and status flag bits, and the
+// launch helpers.  FP32 throughout; no fast-math approximations (divisions
+// and square roots are IEEE round-to-nearest).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/difftrans.h"
+
+namespace dt {
+
+// ---------------------------------------------------------------------------
+// float3 arithmetic
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ float3 mk(float x, float y, float z) { return make_float3(x, y, z); }
+__host__ __device__ __forceinline__ float3 operator+(float3 a, float3 b) { return mk(a.x + b.x, a.y + b.y, a.z + b.z); }
+__host__ __device__ __forceinline__ float3 operator-(float3 a, float3 b) { return mk(a.x - b.x, a.y - b.y, a.z - b.z); }
+__host__ __device__ __forceinline__ float3 operator-(float3 a) { return mk(-a.x, -a.y, -a.z); }
+__host__ __device__ __forceinline__ float3 operator*(float3 a, float s) { return mk(a.x * s, a.y * s, a.z * s); }
+__host__ __device__ __forceinline__ float3 operator*(float s, float3 a) { return mk(a.x * s, a.y * s, a.z * s); }
+__host__ __device__ __forceinline__ float3 mul(float3 a, float3 b) { return mk(a.x * b.x, a.y * b.y, a.z * b.z); }
+__host__ __device__ __forceinline__ float dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__host__ __device__ __forceinline__ float3 cross(float3 a, float3 b) {
+  return mk(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__host__ __device__ __forceinline__ float len(float3 a) { return sqrtf(dot(a, a)); }
+__host__ __device__ __forceinline__ float3 normalize(float3 a) {
+  float n = len(a);
+  return mk(a.x / n, a.y / n, a.z / n);
+}
+__device__ __forceinline__ float3 xyz(float4 v) { return mk(v.x, v.y, v.z); }
+__device__ __forceinline__ float3 load3(const float* p) { return mk(p[0], p[1], p[2]); }
+
+// ---------------------------------------------------------------------------
+// segment flags (same bit meaning as the parity dump in difftrans.h)
+// ---------------------------------------------------------------------------
+enum : uint32_t {
+  SF_INSIDE = 4u,
+  SF_TIR = 8u,
+  SF_BACKFACING = 16u,
+  SF_DISCARDED = 128u,
+  SF_MISS = 512u,
+};
+
+// device status bits (render workspace header)
+enum : uint32_t {
+  ST_QUEUE_OVERFLOW = 1u,
+  ST_STACK_OVERFLOW = 2u,
+};
+
+constexpr int kMaxLevels = 32;
+constexpr int kMaxDepth = 30;
+constexpr int kTraceStack = 64;
+
+// ---------------------------------------------------------------------------
+// BVH buffer: header, internal nodes, leaf-order triangles, leaf -> triangle
+// map, parent links.  Internal node j (0 <= j < n_int) is 4 float4:
+//   n0 = child0 (lo.x, hi.x, lo.y, hi.y), n1 = child1 (lo.x, hi.x, lo.y, hi.y),
+//   n2 = (child0 lo.z, hi.z, child1 lo.z, hi.z), n3 = (child0, child1) as int
+// where a child >= 0 is an internal node and a child < 0 is leaf ~child.
+// Leaf i (sorted position) is triangle leaf_tri[i], stored as 3 float4:
+//   (v0.xyz, triangle id), (e1 = v1 - v0, 0), (e2 = v2 - v0, 0).
+// parent[] holds the parent of internal node j at j and of leaf i at n_int+i.
+// ---------------------------------------------------------------------------
+struct BvhHeader {
+  int32_t nf;
+  int32_t n_int;  // number of internal nodes = max(nf - 1, 1)
+  int32_t root;   // 0
+  int32_t pad;
+};
+
+struct BvhView {
+  BvhHeader* hdr;
+  float4* nodes;     // [n_int * 4]
+  float4* tris;      // [nf * 3]
+  int32_t* leaf_tri; // [nf]
+  int32_t* parent;   // [n_int + nf]
+};
+
+__host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct BvhLayout {
+  size_t off_nodes, off_tris, off_leaf, off_parent, total;
+  __host__ __device__ explicit BvhLayout(int32_t nf) {
+    const size_t n_int = nf > 1 ? (size_t)nf - 1 : 1;
+    off_nodes = 256;
+    off_tris = align_up(off_nodes + n_int * 4 * sizeof(float4), 256);
+    off_leaf = align_up(off_tris + (size_t)nf * 3 * sizeof(float4), 256);
+    off_parent = align_up(off_leaf + (size_t)nf * sizeof(int32_t), 256);
+    total = align_up(off_parent + (n_int + (size_t)nf) * sizeof(int32_t), 256);
+  }
+};
+
+__host__ __device__ inline BvhView bvh_view(const void* base, int32_t nf) {
+  BvhLayout L(nf);
+  char* b = (char*)base;
+  return BvhView{(BvhHeader*)b, (float4*)(b + L.off_nodes), (float4*)(b + L.off_tris), (int32_t*)(b + L.off_leaf),
+                 (int32_t*)(b + L.off_parent)};
+}
+
+// ---------------------------------------------------------------------------
+// Render workspace: a header, then the segment arena.  Level k occupies
+// [level_start[k], level_start[k] + count(k)).  Per segment i:
+//   ray_o[i] = (origin xyz, sample index as int bits)
+//   ray_d[i] = (direction xyz, heap node id as int bits)
+//   ray_w[i] = (throughput rgb, triangle the ray leaves from, or -1)
+//   hit[i]   = (t, b1, b2, hit triangle or -1)
+//   child[i] = arena index of the first child (reflected; refracted at +1
+//              unless total internal reflection), -1 when it has none
+//   sflag[i] = SF_* bits
+// ---------------------------------------------------------------------------
+struct WsHeader {
+  uint32_t status;
+  uint32_t n_levels;
+  unsigned long long capacity;
+  unsigned long long seg_needed;
+  uint32_t level_count[kMaxLevels];  // appended (may exceed what fits)
+  uint32_t level_start[kMaxLevels];
+  uint32_t fetch[kMaxLevels];        // work-fetch cursors of the trace kernels
+  unsigned long long counters[16];   // see CNT_*
+  int32_t n_views, width, height, spp, max_depth, pad0;
+};
+
+enum { CNT_HITS = 0, CNT_MISSES, CNT_DISCARDED, CNT_BACKFACING, CNT_TIR, CNT_NODES, CNT_TRIS };
+
+struct WsView {
+  WsHeader* hdr;
+  float4* ray_o;
+  float4* ray_d;
+  float4* ray_w;
+  float4* hit;
+  int32_t* child;
+  uint32_t* sflag;
+  unsigned long long cap;
+};
+
+struct WsLayout {
+  size_t off_o, off_d, off_w, off_hit, off_child, off_flag, total;
+  __host__ __device__ explicit WsLayout(unsigned long long cap) {
+    off_o = 1024;
+    off_d = align_up(off_o + cap * sizeof(float4), 256);
+    off_w = align_up(off_d + cap * sizeof(float4), 256);
+    off_hit = align_up(off_w + cap * sizeof(float4), 256);
+    off_child = align_up(off_hit + cap * sizeof(float4), 256);
+    off_flag = align_up(off_child + cap * sizeof(int32_t), 256);
+    total = align_up(off_flag + cap * sizeof(uint32_t), 256);
+  }
+};
+static_assert(sizeof(WsHeader) <= 1024, "header must fit its slot");
+
+__host__ __device__ inline WsView ws_view(const void* base, unsigned long long cap) {
+  WsLayout L(cap);
+  char* b = (char*)base;
+  return WsView{(WsHeader*)b, (float4*)(b + L.off_o), (float4*)(b + L.off_d), (float4*)(b + L.off_w),
+                (float4*)(b + L.off_hit), (int32_t*)(b + L.off_child), (uint32_t*)(b + L.off_flag), cap};
+}
+
+// Segments of level k that fit in the arena.
+__device__ __forceinline__ uint32_t level_size(const WsHeader* h, int k) {
+  const unsigned long long start = h->level_start[k];
+  if (start >= h->capacity) return 0;
+  const unsigned long long room = h->capacity - start;
+  const unsigned long long n = h->level_count[k];
+  return (uint32_t)(n < room ? n : room);
+}
+
+// ---------------------------------------------------------------------------
+// warp helpers
+// ---------------------------------------------------------------------------
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ void warp_add_u64(unsigned long long* dst, unsigned v) {
+  unsigned s = __reduce_add_sync(kFull, v);
+  if ((threadIdx.x & 31) == 0 && s) atomicAdd(dst, (unsigned long long)s);
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+// PCG hash (Jarzynski & Olano, "Hash Functions for GPU Rendering", JCGT 2020)
+__host__ __device__ __forceinline__ uint32_t pcg_hash(uint32_t v) {
+  uint32_t state = v * 747796405u + 2891336453u;
+  uint32_t word = ((state >> ((state >> 28u) + 4u)) ^ state) * 277803737u;
+  return (word >> 22u) ^ word;
+}
+
+// ---------------------------------------------------------------------------
+// host-side helpers (defined in dt_api.cu)
+// ---------------------------------------------------------------------------
+dt_status set_error(dt_status code, const char* fmt, ...);
+dt_status check_launch(const char* what);
+int num_sms();
+
+// Per-kernel event timing (dt_profile_enable).  Scoped: records a start event
+// on construction and a stop event on destruction when profiling is on.
+struct ProfScope {
+  int slot;
+  cudaStream_t stream;
+  ProfScope(const char* name, cudaStream_t s);
+  ~ProfScope();
+};
+
+}  // namespace dt

@@ -1,0 +1,221 @@
+"""GPU forward path vs the FP64 oracle, element by element, through the C ABI.
+
+Hit triangle ids must agree bit for bit per (sample, heap node) and radiance
+within 1e-4 relative, on every pixel whose oracle path has no degenerate
+event (a hit or near miss within 1e-6 of an edge, a near tie, a TIR or
+inside/outside decision within 1e-6 of its threshold)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import paper_2603_00413_gb300 as dt
+from paper_2603_00413_gb300 import scenes as S
+from tests.gpu_util import GpuScene, assert_hit_id_parity, assert_radiance_parity, degenerate_pixels
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2603_00413_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+
+
+def test_vertex_normals_match_oracle():
+    for V, F in [S.icosphere(3), S.two_tori_mesh(40)]:
+        Vt = torch.from_numpy(V).cuda()
+        Ft = torch.from_numpy(F).cuda()
+        N = dt.vertex_normals(Vt, Ft).cpu().numpy()
+        No = O.vertex_normals(V, F)
+        np.testing.assert_allclose(N, No, rtol=0, atol=2e-5)
+
+
+def test_vertex_normals_backward_matches_finite_differences():
+    """<dN/dV u, w> by central differences of the (FP64) oracle normals."""
+    V, F = S.icosphere(2)
+    rng = np.random.default_rng(0)
+    w = rng.normal(size=V.shape).astype(np.float32)
+    u = rng.normal(size=V.shape)
+    dV = dt.vertex_normals_backward(torch.from_numpy(V).cuda(), torch.from_numpy(F).cuda(),
+                                    torch.from_numpy(w).cuda()).cpu().numpy().astype(np.float64)
+    h = 1e-6
+    Vd = V.astype(np.float64)
+    fd = ((O.vertex_normals(Vd + h * u, F) - O.vertex_normals(Vd - h * u, F)) / (2 * h) * w).sum()
+    assert (dV * u).sum() == pytest.approx(fd, rel=1e-4)
+
+
+def _random_rays(rng, m, inside_frac=0.5, radius=0.85):
+    k = int(m * inside_frac)
+    o = rng.uniform(-2.5, 2.5, size=(m, 3))
+    dirs = rng.normal(size=(k, 3))
+    o[:k] = dirs / np.linalg.norm(dirs, axis=1, keepdims=True) * rng.uniform(0, radius, size=(k, 1))
+    d = rng.normal(size=(m, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    return o.astype(np.float32), d.astype(np.float32)
+
+
+@pytest.mark.parametrize("mesh", ["icosphere", "tori", "blob", "box", "single"])
+def test_bvh_closest_hit_matches_brute_force(mesh):
+    rng = np.random.default_rng(1)
+    if mesh == "icosphere":
+        V, F = S.icosphere(3)
+    elif mesh == "tori":
+        V, F = S.two_tori_mesh(40)
+    elif mesh == "blob":
+        V, F = S.mesh_from_field(S.random_blob_field(rng), 6000)
+    elif mesh == "box":
+        V, F = S.box_grid(3, (1.0, 1.0, 0.2))
+    else:
+        V = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0]], np.float32)
+        F = np.array([[0, 1, 2]], np.int32)
+    o, d = _random_rays(rng, 3000)
+    if mesh == "single":
+        o = rng.uniform(-0.5, 1.0, size=(3000, 3)).astype(np.float32)
+        o[:, 2] = rng.choice([-1.0, 1.0], size=3000)
+        d = (np.stack([rng.uniform(0, 1, 3000), rng.uniform(0, 1, 3000), np.zeros(3000)], 1) - o)
+        d = (d / np.linalg.norm(d, axis=1, keepdims=True)).astype(np.float32)
+    src = rng.integers(-1, F.shape[0], size=o.shape[0]).astype(np.int32)
+    Vt, Ft = torch.from_numpy(V).cuda(), torch.from_numpy(F).cuda()
+    bvh = dt.build_bvh(Vt, Ft)
+    tri, tbb = dt.closest_hit(bvh, torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda(),
+                              torch.from_numpy(src).cuda(), 1e-5)
+    tri, tbb = tri.cpu().numpy(), tbb.cpu().numpy()
+    otri, ot, ob1, ob2, ofl = O.closest_hit(V, F, o.astype(np.float64), d.astype(np.float64), src, 1e-5)
+    ok = (ofl & (O.SEG_NEAR_EDGE | O.SEG_NEAR_TIE)) == 0
+    assert ok.mean() > 0.95
+    np.testing.assert_array_equal(tri[ok], otri[ok])
+    h = ok & (otri >= 0)
+    assert h.sum() > 100 or mesh == "single"
+    # FP32 Moller-Trumbore: t and the hit point carry relative error ~1e-7 |x|;
+    # the barycentrics carry ~eps |s||e| / |det|, large for grazing rays, so
+    # they are checked through the hit point they reconstruct
+    np.testing.assert_allclose(tbb[h, 0], ot[h], rtol=2e-5, atol=1e-6)
+    Vd = V.astype(np.float64)
+    tri_v = Vd[F[otri[h]]]
+    def point(b1, b2):
+        return tri_v[:, 0] * (1 - b1 - b2)[:, None] + tri_v[:, 1] * b1[:, None] + tri_v[:, 2] * b2[:, None]
+    err = np.linalg.norm(point(tbb[h, 1].astype(np.float64), tbb[h, 2].astype(np.float64)) - point(ob1[h], ob2[h]),
+                         axis=1)
+    assert err.max() < 2e-5, err.max()
+    np.testing.assert_allclose(tbb[h, 1], ob1[h], atol=2e-4)
+    np.testing.assert_allclose(tbb[h, 2], ob2[h], atol=2e-4)
+
+
+def test_refit_tracks_moved_vertices():
+    rng = np.random.default_rng(2)
+    V, F = S.two_tori_mesh(40)
+    Vt, Ft = torch.from_numpy(V).cuda(), torch.from_numpy(F).cuda()
+    bvh = dt.build_bvh(Vt, Ft)
+    V2 = (V.astype(np.float64) + rng.normal(0, 0.01, size=V.shape)).astype(np.float32)
+    dt.refit_bvh(bvh, torch.from_numpy(V2).cuda(), Ft)
+    o, d = _random_rays(rng, 2000, inside_frac=0.0)
+    tri, _ = dt.closest_hit(bvh, torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda(), None, 1e-5)
+    otri, *_, ofl = O.closest_hit(V2, F, o, d, None, 1e-5)
+    ok = (ofl & (O.SEG_NEAR_EDGE | O.SEG_NEAR_TIE)) == 0
+    np.testing.assert_array_equal(tri.cpu().numpy()[ok], otri[ok])
+
+
+def _parity(gs, view=0):
+    img, tape = gs.render()
+    torch.cuda.synchronize()
+    orc = gs.oracle(view, segments=True)
+    info = assert_radiance_parity(img[view], orc)
+    si, _ = dt.dump_segments(tape)
+    si = si.cpu().numpy()
+    npix = gs.width * gs.height
+    spp = gs.params.spp
+    lo, hi = view * npix * spp, (view + 1) * npix * spp
+    sel = (si[:, 0] >= lo) & (si[:, 0] < hi)
+    n = assert_hit_id_parity(si[sel], orc, spp, view_offset=lo)
+    return img, tape, orc, info, n
+
+
+def test_render_glass_icosphere_matches_oracle():
+    """The one-icosphere workload in full: subdivision 3, IoR 1.5, no
+    absorption, 64x64 at pixel centres, depth 4, 64x32 SH environment."""
+    gs = GpuScene.from_scene(S.glass_icosphere_scene())
+    img, tape, orc, info, n = _parity(gs)
+    st = tape.stats
+    oc = orc["counters"]
+    bad = degenerate_pixels(orc)
+    assert bad.sum() <= 0.02 * bad.size
+    if bad.sum() == 0:
+        assert st["segments"] == oc["segments"]
+        assert st["hits"] == oc["hits"] and st["misses"] == oc["misses"]
+        assert st["discarded"] == oc["discarded"] and st["tir"] == oc["tir"]
+
+
+@pytest.mark.parametrize("depth", [0, 1, 6])
+def test_render_absorbing_off_axis(depth):
+    sc = S.glass_icosphere_scene(width=48, height=40)
+    cam = S.camera((1.3, 0.9, 2.5), (0.05, -0.1, 0.0), (0, 1, 0), 50.0, 48, 40)
+    gs = GpuScene(sc.V, sc.F, 1.45, np.array([0.5, 1.0, 1.5], np.float32), sc.env, [cam], 48, 40, depth)
+    _parity(gs)
+
+
+def test_render_genus2_multi_view_jittered():
+    V, F = S.two_tori_mesh(36)
+    env = S.sh_env_map(64, 32, 1)
+    cams = S.fibonacci_views(3, 3.0, 40, 40)
+    gs = GpuScene(V, F, 1.52, np.array([0.3, 0.1, 0.05], np.float32), env, cams, 40, 40, 8, spp=2, jitter=1,
+                  seed=77)
+    img, tape = gs.render()
+    for v in range(3):
+        orc = gs.oracle(v, segments=True)
+        info = assert_radiance_parity(img[v], orc)
+        assert info["excluded_frac"] < 0.25, info
+        si, _ = dt.dump_segments(tape)
+        si = si.cpu().numpy()
+        npix = 40 * 40 * 2
+        sel = (si[:, 0] >= v * npix) & (si[:, 0] < (v + 1) * npix)
+        assert_hit_id_parity(si[sel], orc, 2, view_offset=v * npix)
+
+
+def test_all_miss_view_shows_environment():
+    sc = S.glass_icosphere_scene(width=16, height=16)
+    cam = S.camera((0.0, 0.0, 3.0), (0.0, 0.0, 6.0), (0, 1, 0), 45.0, 16, 16)  # looking away
+    gs = GpuScene(sc.V, sc.F, 1.5, np.zeros(3, np.float32), sc.env, [cam], 16, 16, 4)
+    img, tape = gs.render()
+    o, d = O.camera_rays(cam)
+    np.testing.assert_allclose(img[0].cpu().numpy().reshape(-1, 3), O.env_lookup(sc.env, d), rtol=1e-5, atol=1e-6)
+    assert tape.stats["hits"] == 0 and tape.stats["segments"] == 256
+
+
+def test_single_pixel_and_single_triangle():
+    V = np.array([[-1, -1, 0], [1, -1, 0], [0, 1, 0]], np.float32)
+    F = np.array([[0, 1, 2]], np.int32)
+    env = S.sh_env_map(16, 8, 3)
+    cam = S.camera((0.1, 0.1, 2.0), (0.1, 0.1, 0.0), (0, 1, 0), 30.0, 1, 1)
+    gs = GpuScene(V, F, 1.5, np.zeros(3, np.float32), env, [cam], 1, 1, 3)
+    _parity(gs)
+
+
+def test_arena_overflow_is_reported_and_retried():
+    sc = S.glass_icosphere_scene(width=32, height=32)
+    gs = GpuScene.from_scene(sc)
+    small = dt.Workspace(32 * 32 + 10, gs.V.device)
+    img_small, tape = dt.render(gs.V, gs.F, gs.bvh, gs.N, gs.ior, gs.sigma, gs.env, gs.cams, 32, 32, gs.params,
+                                ws=small, check=False)
+    st = dt.read_stats(small)
+    assert st["status"] == dt.DT_ERR_QUEUE_OVERFLOW
+    assert st["seg_needed"] > small.capacity
+    img, tape = dt.render(gs.V, gs.F, gs.bvh, gs.N, gs.ior, gs.sigma, gs.env, gs.cams, 32, 32, gs.params,
+                          ws=dt.Workspace(32 * 32 + 10, gs.V.device))
+    assert tape.stats["status"] == dt.DT_OK and tape.ws.capacity > small.capacity
+    assert_radiance_parity(img[0], gs.oracle(0))
+
+
+def test_host_rejects_bad_arguments():
+    sc = S.glass_icosphere_scene(width=8, height=8)
+    gs = GpuScene.from_scene(sc)
+    with pytest.raises(dt.DiffTransError):
+        dt.render(gs.V, gs.F, gs.bvh, gs.N, gs.ior, gs.sigma, gs.env, gs.cams, 8, 8, dt.Params(31))
+    with pytest.raises(dt.DiffTransError):
+        dt.render(gs.V, gs.F, gs.bvh, gs.N, gs.ior, gs.sigma, gs.env, gs.cams, 8, 8, dt.Params(4, spp=0))
+    with pytest.raises(dt.DiffTransError):
+        dt.render(gs.V, gs.F, gs.bvh, gs.N, gs.ior, gs.sigma, gs.env, gs.cams, 8, 8, dt.Params(4),
+                  ws=dt.Workspace(10, gs.V.device))
