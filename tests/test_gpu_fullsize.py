@@ -34,25 +34,42 @@ def full():
     return sc, img, tape
 
 
-def _sample(sc, n, seed, hits_only=False):
-    """n seeded (view, pixel) samples with their camera rays; with hits_only,
-    drawn among pixels whose path hits the object and is not edge-degenerate."""
-    rng = np.random.default_rng(seed)
-    m = 8 * n if hits_only else n
-    views = rng.integers(0, len(sc.cams), size=m)
-    pix = rng.integers(0, 512 * 512, size=m)
-    o = np.zeros((m, 3))
-    d = np.zeros((m, 3))
+def _rays(sc, views, pix):
+    o = np.zeros((len(views), 3))
+    d = np.zeros((len(views), 3))
     for i, (v, p) in enumerate(zip(views, pix)):
         oo, dd = O.camera_rays(sc.cams[v])
         o[i], d[i] = oo[p], dd[p]
-    if hits_only:
+    return o, d
+
+
+def _sample(sc, n, seed, hits_only=False):
+    """n seeded (view, pixel) samples with their camera rays; with hits_only,
+    drawn (in rounds of candidates) among pixels whose path hits the object
+    and is not edge-degenerate."""
+    rng = np.random.default_rng(seed)
+    if not hits_only:
+        views = rng.integers(0, len(sc.cams), size=n)
+        pix = rng.integers(0, 512 * 512, size=n)
+        o, d = _rays(sc, views, pix)
+        return views, pix, o, d
+    got_v, got_p = [], []
+    for _ in range(12):
+        m = 8 * n
+        views = rng.integers(0, len(sc.cams), size=m)
+        pix = rng.integers(0, 512 * 512, size=m)
+        o, d = _rays(sc, views, pix)
         r = O.render_rays(sc.V, sc.F, sc.ior, sc.sigma, sc.env, o, d, sc.max_depth, probe=PROBE, segments=True)
         hit = np.zeros(m, bool)
         hit[np.unique(r["seg_i"][r["seg_i"][:, 2] >= 0, 0])] = True
-        keep = np.nonzero(hit & ((r["pix_flags"] & O.SEG_DEGENERATE) == 0))[0][:n]
-        assert keep.size == n
-        views, pix, o, d = views[keep], pix[keep], o[keep], d[keep]
+        keep = np.nonzero(hit & ((r["pix_flags"] & O.SEG_DEGENERATE) == 0))[0]
+        got_v += list(views[keep])
+        got_p += list(pix[keep])
+        if len(got_v) >= n:
+            break
+    assert len(got_v) >= n
+    views, pix = np.array(got_v[:n]), np.array(got_p[:n])
+    o, d = _rays(sc, views, pix)
     return views, pix, o, d
 
 
