@@ -71,6 +71,27 @@ dt_status dt_vertex_normals_scratch_size(int32_t nv, size_t* bytes);
 dt_status dt_vertex_normals(const float* d_V, int32_t nv, const int32_t* d_F, int32_t nf, float* d_N,
                             void* d_scratch, dt_stream stream);
 
+/* dt_vertex_normals for callers that cannot allocate device memory: a
+ * plugin that only receives device pointers from a host application owning
+ * all device memory, or a serving loop that must not allocate after start-up
+ * (cudaMalloc/cudaFree can synchronise the device and fragment a pool).  The
+ * paper has no counterpart; it computes the same Eq. 13 normals, bit for bit,
+ * as dt_vertex_normals, but takes no scratch buffer: it uses one fixed array
+ * of 24 MiB of device memory inside the library (2^20 vertices x 3 x 8
+ * bytes), which every GPU that loads the library holds until the process
+ * exits.  It allocates nothing.
+ *  - nv > 1048576 (2^20) is rejected with DT_ERR_INVALID_ARG and a message;
+ *    use dt_vertex_normals then.
+ *  - The first call on each device looks up the array's device address
+ *    (with that device current) and keeps it; make that first call before
+ *    any stream capture.
+ *  - Every call on a device shares the one array and it keeps the last
+ *    call's contents (each call clears the part it uses first).  Calls whose
+ *    work overlaps on the GPU -- on different streams, or from different
+ *    host threads -- race on it: order them on one stream. */
+dt_status dt_vertex_normals_noalloc(const float* d_V, int32_t nv, const int32_t* d_F, int32_t nf, float* d_N,
+                                    dt_stream stream);
+
 /* Backward of dt_vertex_normals: d_dV[nv][3] += (dN/dV)^T d_dN, for a
  * gradient d_dN float[nv][3] with respect to the normals.  d_dV is
  * accumulated into, not overwritten. */

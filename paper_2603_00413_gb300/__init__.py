@@ -24,7 +24,7 @@ __all__ = [
     "DiffTransError", "load_library", "vertex_normals", "vertex_normals_backward", "Bvh", "build_bvh",
     "refit_bvh", "Params", "render", "render_backward", "read_stats", "dump_segments", "closest_hit",
     "render_workspace_size", "backward_workspace_size", "Tape", "DiffTransRender", "render_differentiable",
-    "l2_loss_grad", "profile_enable", "profile_read",
+    "l2_loss_grad", "profile_enable", "profile_read", "vertex_normals_noalloc",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -87,6 +87,7 @@ _PROTOS = {
     "dt_version": (c_char_p, []),
     "dt_vertex_normals_scratch_size": (c_int32, [c_int32, POINTER(c_size_t)]),
     "dt_vertex_normals": (c_int32, [c_void_p, c_int32, c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
+    "dt_vertex_normals_noalloc": (c_int32, [c_void_p, c_int32, c_void_p, c_int32, c_void_p, c_void_p]),
     "dt_vertex_normals_backward": (c_int32, [c_void_p, c_int32, c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
     "dt_bvh_size": (c_int32, [c_int32, POINTER(c_size_t), POINTER(c_size_t)]),
     "dt_build_bvh": (c_int32, [c_void_p, c_int32, c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
@@ -187,6 +188,22 @@ def vertex_normals(V, F, out=None, stream=None, scratch=None):
     _check(load_library().dt_vertex_normals(_ptr(V), V.shape[0], _ptr(F), F.shape[0], _ptr(N), _ptr(scratch),
                                             _stream(stream)))
     return N
+
+
+NOALLOC_MAX_VERTICES = 1 << 20
+
+
+def vertex_normals_noalloc(V, F, out, stream=None):
+    """Eq. 13 normals for callers that cannot allocate device memory: the
+    scratch lives in a fixed 24 MiB array inside the library (at most 2^20
+    vertices); `out` must be given.  Calls that overlap on the GPU share that
+    array and race: keep them on one stream."""
+    _need(V, torch.float32, (3,), "V")
+    _need(F, torch.int32, (3,), "F")
+    _need(out, torch.float32, (3,), "out")
+    _check(load_library().dt_vertex_normals_noalloc(_ptr(V), V.shape[0], _ptr(F), F.shape[0], _ptr(out),
+                                                    _stream(stream)))
+    return out
 
 
 def vertex_normals_backward(V, F, dN, dV=None, stream=None):
