@@ -61,17 +61,26 @@ def parse():
     return ap.parse_args()
 
 
-def kernel_sources_hash() -> str:
+# the source files that define each measured kernel
+KERNEL_FILES = {
+    "k_trace": ["dt_trace.cu", "dt_shade.cuh", "dt_internal.cuh"],
+    "k_shade": ["dt_trace.cu", "dt_shade.cuh", "dt_internal.cuh"],
+    "k_adjoint": ["dt_adjoint.cu", "dt_shade.cuh", "dt_internal.cuh"],
+}
+
+
+def kernel_sources_hash(kernel: str) -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2603_00413_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in KERNEL_FILES.get(kernel, sorted(os.listdir(csrc))):
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
-    was taken on the current kernel sources (else None)."""
+def ncu_traffic(kernel: str, units_per_launch: float):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary
+    (bytes per unit there, scaled to this launch's units), if it was taken on
+    the current sources of that kernel (else None)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(path):
         return None
@@ -80,9 +89,9 @@ def ncu_traffic(kernel: str):
     except Exception:
         return None
     e = d.get(kernel)
-    if not e or e.get("kernel_sources") != kernel_sources_hash():
+    if not e or e.get("kernel_sources") != kernel_sources_hash(kernel):
         return None
-    return e.get("dram_bytes_per_launch")
+    return e.get("dram_bytes_per_unit") * units_per_launch
 
 
 def genus2_workload(n_views, res, depth, seed=1):
@@ -321,25 +330,40 @@ def run_ours(args):
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
     kt = {k: v for k, v in prof.items()}
     dom = max(kt, key=lambda k: kt[k][1])
-    nl = stats["n_levels"]
     hits, misses = stats["hits"], stats["misses"]
     spawners = hits - stats["discarded"] - stats["backfacing"]
-    per_step_bytes = {
+    children = seg - nvw * res * res
+    bvh_bytes = (sc.F.shape[0] - 1) * NODE_BYTES + sc.F.shape[0] * TRI_BYTES
+    # bytes that must cross HBM per step (the BVH, the scene and the
+    # environment stay in L2; the tape, the image and its gradient do not)
+    hbm_step = {
+        "k_trace": seg * (RAY_RECORD + HIT_RECORD) + (D + 1) * bvh_bytes,
+        "k_shade": seg * (RAY_RECORD + HIT_RECORD + LINK_RECORD) + children * RAY_RECORD + misses * 2 * 12,
+        "k_adjoint": seg * (RAY_RECORD + HIT_RECORD + LINK_RECORD + 12) + (seg - nvw * res * res) * 48
+        + spawners * 2 * 48,
+    }
+    # bytes the kernel moves through L2 (on-chip reuse included)
+    l2_step = {
         "k_trace": seg * (RAY_RECORD + HIT_RECORD) + stats["nodes_visited"] * NODE_BYTES
         + stats["tris_tested"] * TRI_BYTES,
-        "k_shade": seg * (RAY_RECORD + HIT_RECORD + LINK_RECORD) + hits * HIT_SCENE + misses * ENV_MISS
-        + (stats["segments"] - nvw * res * res) * RAY_RECORD,
-        "k_adjoint": seg * (RAY_RECORD + HIT_RECORD + LINK_RECORD + ADJ_OUT) + misses * 48
-        + spawners * (HIT_SCENE + 2 * ADJ_OUT + ADJ_ATOMICS),
+        "k_shade": hbm_step["k_shade"] + hits * HIT_SCENE + misses * ENV_MISS,
+        "k_adjoint": hbm_step["k_adjoint"] + spawners * (HIT_SCENE + ADJ_ATOMICS) + misses * 48,
     }
     launches, dom_ms = kt[dom]
     per_launch_ms = dom_ms / launches
-    bytes_per_launch = per_step_bytes.get(dom, 0) * args.steps / launches
-    achieved = bytes_per_launch / (per_launch_ms / 1000.0) / 1e9
-    traffic = ncu_traffic(dom)
+    hbm_per_launch = hbm_step.get(dom, 0) * args.steps / launches
+    l2_per_launch = l2_step.get(dom, 0) * args.steps / launches
+    achieved = hbm_per_launch / (per_launch_ms / 1000.0) / 1e9
+    l2_peak = dt.measure_l2_read_bandwidth()
+    l2_achieved = l2_per_launch / (per_launch_ms / 1000.0) / 1e9
+    traffic = ncu_traffic(dom, seg * args.steps / launches)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": traffic, "kernel": dom,
-                "peak_source": peak_src, "bytes_per_launch": bytes_per_launch, "ms_per_launch": per_launch_ms}
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
+                "bytes_per_launch": hbm_per_launch, "ms_per_launch": per_launch_ms,
+                "l2": {"achieved": l2_achieved, "peak": l2_peak, "unit": "GB/s", "frac": l2_achieved / l2_peak,
+                       "bytes_per_launch": l2_per_launch,
+                       "peak_source": "measured in this run (dt_measure_l2_read_bandwidth, 32 MB, L1 bypassed)"}}
     gpu_launches = int(sum(v[0] * KERNELS_PER_SCOPE.get(k, 1) for k, v in kt.items()))
     kernel_share = {k: round(v[1] / sum(x[1] for x in kt.values()), 4) for k, v in kt.items()}
 

@@ -281,6 +281,16 @@ typedef struct dt_kernel_time {
 dt_status dt_profile_enable(int32_t enable);
 dt_status dt_profile_read(dt_kernel_time* out, int32_t cap, int32_t* n);
 
+/* ------------------------------------------------------------------------
+ * Measurement utility (no counterpart in the paper): L2 read bandwidth of
+ * the current GPU in GB/s, from float4 loads that bypass L1 over d_buf
+ * (bytes >= 4096, 16-byte aligned; choose it well below the L2 size) read
+ * iters times after one warming pass.  Synchronises the stream.  The value
+ * is the on-chip denominator for kernels whose working set stays in L2.
+ * ------------------------------------------------------------------------ */
+dt_status dt_measure_l2_read_bandwidth(const void* d_buf, size_t bytes, int32_t iters, double* gbps,
+                                       dt_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

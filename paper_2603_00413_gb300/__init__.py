@@ -105,6 +105,7 @@ _PROTOS = {
                                  c_void_p, c_void_p]),
     "dt_l2_loss_grad": (c_int32, [c_void_p, c_void_p, c_int64, c_float, c_void_p, c_void_p, c_void_p]),
     "dt_profile_enable": (c_int32, [c_int32]),
+    "dt_measure_l2_read_bandwidth": (c_int32, [c_void_p, c_size_t, c_int32, POINTER(ctypes.c_double), c_void_p]),
     "dt_profile_read": (c_int32, [POINTER(DtKernelTime), c_int32, POINTER(c_int32)]),
 }
 
@@ -409,6 +410,16 @@ def l2_loss_grad(img, target, grad=None, loss=None, stream=None):
     _check(load_library().dt_l2_loss_grad(_ptr(img), _ptr(target), n, 1.0 / max(n, 1), _ptr(grad), _ptr(loss),
                                           _stream(stream)))
     return grad, loss
+
+
+def measure_l2_read_bandwidth(nbytes: int = 32 << 20, iters: int = 50, device=None, stream=None) -> float:
+    """L2 read bandwidth (GB/s) of the current GPU, measured by the library."""
+    dev = device or torch.device("cuda", torch.cuda.current_device())
+    _, buf = _aligned_empty(nbytes, dev)
+    buf.zero_()
+    g = ctypes.c_double()
+    _check(load_library().dt_measure_l2_read_bandwidth(_ptr(buf), nbytes, iters, ctypes.byref(g), _stream(stream)))
+    return g.value
 
 
 def profile_enable(on: bool = True):
