@@ -267,6 +267,30 @@ dt_status dt_l2_loss_grad(const float* d_img, const float* d_target, int64_t n, 
                           float* d_loss, dt_stream stream);
 
 /* ------------------------------------------------------------------------
+ * Launch and scheduling knobs of the kernels (process-wide; a call takes
+ * the values current when it is made).  The traversal is persistent: each
+ * lane carries one ray, a warp runs trace_steps node visits per round and
+ * refills its idle lanes from the level's queue once trace_refill of them
+ * are idle; trace_blocks_per_sm CTAs of 256 threads run per SM.
+ * shade_blocks_per_sm sizes the grid of the shading and adjoint kernels.
+ * bvh_width selects the node format the traversal reads: 2 (binary nodes,
+ * 64 B) or 4 (4-wide nodes, 128 B: the binary nodes at even depth with
+ * their grandchildren as children); both are kept current by build/refit.
+ * Defaults {16, 8, 5, 8, 2}; results do not depend on them (the same closest
+ * hit is found).  dt_set_tuning rejects values outside steps 1..256, refill
+ * 1..32, trace 1..8, shade 1..16, width 2 or 4.
+ * ------------------------------------------------------------------------ */
+typedef struct dt_tuning {
+  int32_t trace_steps;
+  int32_t trace_refill;
+  int32_t trace_blocks_per_sm;
+  int32_t shade_blocks_per_sm;
+  int32_t bvh_width;
+} dt_tuning;
+dt_status dt_get_tuning(dt_tuning* out);
+dt_status dt_set_tuning(const dt_tuning* in);
+
+/* ------------------------------------------------------------------------
  * Per-kernel timing.  While enabled, every launch of the library's main
  * kernels is bracketed by CUDA events recorded on its launch stream.
  * dt_profile_read waits for those events, returns per kernel name the

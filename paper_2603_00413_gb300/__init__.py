@@ -77,6 +77,11 @@ class DtStats(ctypes.Structure):
         }
 
 
+class DtTuning(ctypes.Structure):
+    _fields_ = [("trace_steps", c_int32), ("trace_refill", c_int32), ("trace_blocks_per_sm", c_int32),
+                ("shade_blocks_per_sm", c_int32), ("bvh_width", c_int32)]
+
+
 class DtKernelTime(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 40), ("launches", c_int64), ("total_ms", ctypes.c_double)]
 
@@ -105,6 +110,8 @@ _PROTOS = {
                                  c_void_p, c_void_p]),
     "dt_l2_loss_grad": (c_int32, [c_void_p, c_void_p, c_int64, c_float, c_void_p, c_void_p, c_void_p]),
     "dt_profile_enable": (c_int32, [c_int32]),
+    "dt_get_tuning": (c_int32, [POINTER(DtTuning)]),
+    "dt_set_tuning": (c_int32, [POINTER(DtTuning)]),
     "dt_measure_l2_read_bandwidth": (c_int32, [c_void_p, c_size_t, c_int32, POINTER(ctypes.c_double), c_void_p]),
     "dt_profile_read": (c_int32, [POINTER(DtKernelTime), c_int32, POINTER(c_int32)]),
 }
@@ -420,6 +427,23 @@ def measure_l2_read_bandwidth(nbytes: int = 32 << 20, iters: int = 50, device=No
     g = ctypes.c_double()
     _check(load_library().dt_measure_l2_read_bandwidth(_ptr(buf), nbytes, iters, ctypes.byref(g), _stream(stream)))
     return g.value
+
+
+def get_tuning() -> dict:
+    t = DtTuning()
+    _check(load_library().dt_get_tuning(ctypes.byref(t)))
+    return {f: getattr(t, f) for f, _ in DtTuning._fields_}
+
+
+def set_tuning(**kw) -> dict:
+    """Set launch/scheduling knobs (trace_steps, trace_refill,
+    trace_blocks_per_sm, shade_blocks_per_sm); returns the previous values."""
+    old = get_tuning()
+    new = dict(old)
+    new.update(kw)
+    t = DtTuning(*[int(new[f]) for f, _ in DtTuning._fields_])
+    _check(load_library().dt_set_tuning(ctypes.byref(t)))
+    return old
 
 
 def profile_enable(on: bool = True):

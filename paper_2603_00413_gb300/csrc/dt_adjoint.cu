@@ -19,6 +19,7 @@ namespace dt {
 
 void launch_vertex_normals_backward(const float* V, int32_t nv, const int32_t* F, int32_t nf, const float* dN,
                                     float* dV, cudaStream_t s);
+extern dt_tuning g_tuning;
 
 // backward scratch: two level buffers of (L, obar, dbar) and dN
 struct BwsLayout {
@@ -245,7 +246,7 @@ void launch_backward(const dt_scene& sc, const dt_views& vw, const dt_params& p,
   cudaMemsetAsync(dsigma, 0, sizeof(float) * 3, s);
   AdjScene S{sc.d_V, sc.d_F, sc.d_N, sc.d_ior, sc.d_sigma, sc.d_env, sc.env_w, sc.env_h};
   const uint32_t n_pix = (uint32_t)vw.n_views * vw.width * vw.height;
-  const int blocks = 8 * num_sms();
+  const int blocks = g_tuning.shade_blocks_per_sm * num_sms();
   for (int k = p.max_depth; k >= 0; --k) {
     ProfScope ps("k_adjoint", s);
     k_adjoint<<<blocks, 256, 0, s>>>(W, S, k, p.spp, n_pix, grad_out, buf[(k + 1) & 1], buf[k & 1], dV, dN, dior,

@@ -31,6 +31,7 @@ void launch_dump(const void* ws, unsigned long long cap, int32_t* si, float* sf,
 void launch_closest_hit(const void* bvh, int32_t nf, const float* o, const float* d, const int32_t* src, int32_t n,
                         float tmin, int32_t* tri, float* tbb, cudaStream_t s);
 size_t backward_ws_bytes(unsigned long long max_level, int32_t nv);
+extern dt_tuning g_tuning;
 void launch_l2_loss_grad(const float* img, const float* target, int64_t n, float scale, float* grad, float* loss,
                          cudaStream_t s);
 void launch_backward(const dt_scene& sc, const dt_views& vw, const dt_params& p, const void* ws,
@@ -296,6 +297,23 @@ dt_status dt_dump_segments(const void* d_ws, size_t ws_bytes, int32_t* d_seg_i, 
   if (wcap == 0) return set_error(DT_ERR_INVALID_ARG, "workspace too small");
   launch_dump(d_ws, wcap, d_seg_i, d_seg_f, (unsigned long long)cap, (cudaStream_t)stream);
   return check_launch("dt_dump_segments");
+}
+
+dt_status dt_get_tuning(dt_tuning* out) {
+  if (!out) return set_error(DT_ERR_INVALID_ARG, "NULL pointer");
+  *out = g_tuning;
+  return DT_OK;
+}
+
+dt_status dt_set_tuning(const dt_tuning* in) {
+  if (!in) return set_error(DT_ERR_INVALID_ARG, "NULL pointer");
+  if (in->trace_steps < 1 || in->trace_steps > 256 || in->trace_refill < 1 || in->trace_refill > 32 ||
+      in->trace_blocks_per_sm < 1 || in->trace_blocks_per_sm > 8 || in->shade_blocks_per_sm < 1 ||
+      in->shade_blocks_per_sm > 16 || (in->bvh_width != 2 && in->bvh_width != 4))
+    return set_error(DT_ERR_INVALID_ARG, "tuning out of range (steps 1..256, refill 1..32, trace blocks/SM 1..8, "
+                                         "shade blocks/SM 1..16, width 2 or 4)");
+  g_tuning = *in;
+  return DT_OK;
 }
 
 dt_status dt_profile_enable(int32_t enable) {

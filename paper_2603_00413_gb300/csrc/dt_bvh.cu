@@ -259,7 +259,7 @@ __device__ __forceinline__ int lcp(const uint32_t* keys, int n, int a, int b) {
   return __clz(ka ^ kb);
 }
 
-__global__ void k_karras(const uint32_t* __restrict__ keys, int32_t n, float4* __restrict__ nodes,
+__global__ void k_karras(const uint32_t* __restrict__ keys, int32_t n, int2* __restrict__ bin_child,
                          int32_t* __restrict__ parent) {
   const int n_int = n - 1;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_int; i += gridDim.x * blockDim.x) {
@@ -282,19 +282,16 @@ __global__ void k_karras(const uint32_t* __restrict__ keys, int32_t n, float4* _
     const int lo = min(i, j), hi = max(i, j);
     const int left = (lo == gamma) ? ~gamma : gamma;
     const int right = (hi == gamma + 1) ? ~(gamma + 1) : gamma + 1;
-    reinterpret_cast<int4*>(nodes)[4 * i + 3] = make_int4(left, right, 0, 0);
+    bin_child[i] = make_int2(left, right);
     parent[left < 0 ? n_int + gamma : gamma] = i;
     parent[right < 0 ? n_int + gamma + 1 : gamma + 1] = i;
     if (i == 0) parent[0] = -1;
   }
 }
 
-// one triangle: a single internal node whose second child has an empty box
-__global__ void k_single_leaf(float4* nodes, int32_t* parent) {
-  const float inf = INFINITY;
-  nodes[1] = make_float4(inf, -inf, inf, -inf);
-  nodes[2] = make_float4(0.f, 0.f, inf, -inf);
-  reinterpret_cast<int4*>(nodes)[3] = make_int4(~0, ~0, 0, 0);
+// one triangle: a single internal node whose two children are both leaf 0
+__global__ void k_single_leaf(int2* bin_child, int32_t* parent) {
+  bin_child[0] = make_int2(~0, ~0);
   parent[0] = -1;
   parent[1] = 0;
 }
@@ -303,24 +300,23 @@ __global__ void k_gather_leaf_tri(const uint32_t* __restrict__ vals, int32_t n, 
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) leaf_tri[i] = (int32_t)vals[i];
 }
 
-// ---- bottom-up bounds --------------------------------------------------------
-__device__ __forceinline__ void store_child_box(float4* node, int slot, float3 lo, float3 hi) {
-  // slot 0: n0 = (lo.x, hi.x, lo.y, hi.y), n2.xy = (lo.z, hi.z); slot 1: n1, n2.zw
-  volatile float* n = reinterpret_cast<volatile float*>(node);
-  const int b = slot * 4;
-  n[b + 0] = lo.x; n[b + 1] = hi.x; n[b + 2] = lo.y; n[b + 3] = hi.y;
-  n[8 + 2 * slot] = lo.z; n[8 + 2 * slot + 1] = hi.z;
+// ---- bottom-up bounds of the binary tree -----------------------------------
+__device__ __forceinline__ void store_box(float4* box, float3 lo, float3 hi) {
+  volatile float* b = reinterpret_cast<volatile float*>(box);
+  b[0] = lo.x; b[1] = lo.y; b[2] = lo.z; b[3] = 0.f;
+  b[4] = hi.x; b[5] = hi.y; b[6] = hi.z; b[7] = 0.f;
 }
 
-__device__ __forceinline__ void load_child_box(const float4* node, int slot, float3& lo, float3& hi) {
-  const volatile float* n = reinterpret_cast<const volatile float*>(node);
-  const int b = slot * 4;
-  lo = mk(n[b + 0], n[b + 2], n[8 + 2 * slot]);
-  hi = mk(n[b + 1], n[b + 3], n[8 + 2 * slot + 1]);
+__device__ __forceinline__ void load_box(const float4* box, float3& lo, float3& hi) {
+  const volatile float* b = reinterpret_cast<const volatile float*>(box);
+  lo = mk(b[0], b[1], b[2]);
+  hi = mk(b[4], b[5], b[6]);
 }
 
 // Each leaf writes its triangle record and box, then climbs: the first of two
-// children to reach a node stops, the second merges both boxes and goes on.
+// children to reach a node stops, the second merges both boxes, stores the
+// node's box and goes on.  A path to the root has at most n_int nodes; the
+// bound guards a corrupt tree.
 __global__ void k_refit(const float* __restrict__ V, const int32_t* __restrict__ F, int32_t nf, BvhView B,
                         uint32_t* __restrict__ arrive) {
   const int n_int = B.hdr->n_int;
@@ -333,33 +329,170 @@ __global__ void k_refit(const float* __restrict__ V, const int32_t* __restrict__
     B.tris[3 * i + 2] = make_float4(e2.x, e2.y, e2.z, 0.f);
     float3 lo = mk(fminf(v0.x, fminf(v1.x, v2.x)), fminf(v0.y, fminf(v1.y, v2.y)), fminf(v0.z, fminf(v1.z, v2.z)));
     float3 hi = mk(fmaxf(v0.x, fmaxf(v1.x, v2.x)), fmaxf(v0.y, fmaxf(v1.y, v2.y)), fmaxf(v0.z, fmaxf(v1.z, v2.z)));
+    store_box(B.box_leaf + 2 * i, lo, hi);
     int me = ~i;
     int node = B.parent[n_int + i];
-    // a path to the root has at most n_int nodes; the bound guards a corrupt tree
     for (int hops = 0; node >= 0 && node < n_int && hops <= n_int; ++hops) {
-      float4* rec = B.nodes + 4 * node;
-      const int4 ch = reinterpret_cast<const int4*>(rec)[3];
-      const int slot = (ch.x == me) ? 0 : 1;
-      store_child_box(rec, slot, lo, hi);
-      __threadfence();
-      const uint32_t prev = atomicAdd(arrive + node, 1u);
-      if (prev == 0) break;  // the sibling is still on its way
-      __threadfence();
-      float3 olo, ohi;
-      load_child_box(rec, 1 - slot, olo, ohi);
-      lo = mk(fminf(lo.x, olo.x), fminf(lo.y, olo.y), fminf(lo.z, olo.z));
-      hi = mk(fmaxf(hi.x, ohi.x), fmaxf(hi.y, ohi.y), fmaxf(hi.z, ohi.z));
+      const int2 ch = B.bin_child[node];
+      const int sib = (ch.x == me) ? ch.y : ch.x;
+      if (sib != kNoChild) {
+        __threadfence();
+        const uint32_t prev = atomicAdd(arrive + node, 1u);
+        if (prev == 0) break;  // the sibling is still on its way
+        __threadfence();
+        float3 olo, ohi;
+        load_box(sib >= 0 ? B.box_int + 2 * sib : B.box_leaf + 2 * (~sib), olo, ohi);
+        lo = mk(fminf(lo.x, olo.x), fminf(lo.y, olo.y), fminf(lo.z, olo.z));
+        hi = mk(fmaxf(hi.x, ohi.x), fmaxf(hi.y, ohi.y), fmaxf(hi.z, ohi.z));
+      }
+      store_box(B.box_int + 2 * node, lo, hi);
       me = node;
       node = B.parent[node];
     }
   }
 }
 
+// ---- the 4-wide BVH ----------------------------------------------------------
+// flag[j] = 1 when binary node j sits at even depth (walks up to the root)
+__global__ void k_even_depth(BvhView B, uint32_t* __restrict__ flag) {
+  const int n_int = B.hdr->n_int;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n_int; j += gridDim.x * blockDim.x) {
+    int d = 0, p = j;
+    for (int hops = 0; hops <= n_int && p > 0; ++hops) {
+      p = B.parent[p];
+      ++d;
+    }
+    flag[j] = (d & 1) ? 0u : 1u;
+  }
+}
+
+// after an exclusive scan of the flags: node4 index per even-depth node, -1 else
+__global__ void k_bin_to4(BvhView B, const uint32_t* __restrict__ scanned) {
+  const int n_int = B.hdr->n_int;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n_int; j += gridDim.x * blockDim.x) {
+    int d = 0, p = j;
+    for (int hops = 0; hops <= n_int && p > 0; ++hops) {
+      p = B.parent[p];
+      ++d;
+    }
+    B.bin_to4[j] = (d & 1) ? -1 : (int)scanned[j];
+    if (j == n_int - 1) B.hdr->n4 = (int)scanned[j] + ((d & 1) ? 0 : 1);
+  }
+}
+
+// children of 4-wide node bin_to4[j] = the grandchildren of binary node j (a
+// leaf child stays as it is); refs in row 6, binary sources in row 7
+__global__ void k_node4_topology(BvhView B) {
+  const int n_int = B.hdr->n_int;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n_int; j += gridDim.x * blockDim.x) {
+    const int m = B.bin_to4[j];
+    if (m < 0) continue;
+    int ref[4] = {kNoChild, kNoChild, kNoChild, kNoChild};
+    int srcs[4] = {kNoChild, kNoChild, kNoChild, kNoChild};
+    int k = 0;
+    const int2 ch = B.bin_child[j];
+    const int c2[2] = {ch.x, ch.y};
+    for (int a = 0; a < 2; ++a) {
+      const int c = c2[a];
+      if (c == kNoChild) continue;
+      if (c < 0) {
+        ref[k] = c; srcs[k] = c; ++k;
+        continue;
+      }
+      const int2 g = B.bin_child[c];
+      const int gg[2] = {g.x, g.y};
+      for (int b = 0; b < 2; ++b) {
+        const int x = gg[b];
+        if (x == kNoChild) continue;
+        ref[k] = x < 0 ? x : B.bin_to4[x];
+        srcs[k] = x;
+        ++k;
+      }
+    }
+    reinterpret_cast<int4*>(B.node4)[8 * m + 6] = make_int4(ref[0], ref[1], ref[2], ref[3]);
+    reinterpret_cast<int4*>(B.node4)[8 * m + 7] = make_int4(srcs[0], srcs[1], srcs[2], srcs[3]);
+  }
+}
+
+// child boxes of every 4-wide node from the binary boxes (after each refit)
+__global__ void k_node4_boxes(BvhView B) {
+  const int n4 = B.hdr->n4;
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n4; m += gridDim.x * blockDim.x) {
+    const int4 sv = reinterpret_cast<const int4*>(B.node4)[8 * m + 7];
+    const int srcs[4] = {sv.x, sv.y, sv.z, sv.w};
+    float r[6][4];
+    for (int k = 0; k < 4; ++k) {
+      float3 lo = mk(INFINITY, INFINITY, INFINITY), hi = mk(-INFINITY, -INFINITY, -INFINITY);
+      const int x = srcs[k];
+      if (x != kNoChild) {
+        const float4* bx = x >= 0 ? B.box_int + 2 * x : B.box_leaf + 2 * (~x);
+        const float4 a = bx[0], b = bx[1];
+        lo = mk(a.x, a.y, a.z);
+        hi = mk(b.x, b.y, b.z);
+      }
+      r[0][k] = lo.x; r[1][k] = hi.x; r[2][k] = lo.y; r[3][k] = hi.y; r[4][k] = lo.z; r[5][k] = hi.z;
+    }
+    for (int row = 0; row < 6; ++row) B.node4[8 * m + row] = make_float4(r[row][0], r[row][1], r[row][2], r[row][3]);
+  }
+}
+
+// binary nodes for the 2-wide traversal, from the binary boxes (after each refit)
+__global__ void k_node2_boxes(BvhView B) {
+  const int n_int = B.hdr->n_int;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n_int; j += gridDim.x * blockDim.x) {
+    const int2 ch = B.bin_child[j];
+    float3 lo[2], hi[2];
+    const int c2[2] = {ch.x, ch.y};
+    for (int k = 0; k < 2; ++k) {
+      lo[k] = mk(INFINITY, INFINITY, INFINITY);
+      hi[k] = mk(-INFINITY, -INFINITY, -INFINITY);
+      const int x = c2[k];
+      if (x != kNoChild) {
+        const float4* bx = x >= 0 ? B.box_int + 2 * x : B.box_leaf + 2 * (~x);
+        const float4 a = bx[0], b = bx[1];
+        lo[k] = mk(a.x, a.y, a.z);
+        hi[k] = mk(b.x, b.y, b.z);
+      }
+    }
+    B.node2[4 * j + 0] = make_float4(lo[0].x, hi[0].x, lo[0].y, hi[0].y);
+    B.node2[4 * j + 1] = make_float4(lo[1].x, hi[1].x, lo[1].y, hi[1].y);
+    B.node2[4 * j + 2] = make_float4(lo[0].z, hi[0].z, lo[1].z, hi[1].z);
+    reinterpret_cast<int4*>(B.node2)[4 * j + 3] = make_int4(ch.x, ch.y, 0, 0);
+  }
+}
+
+// Validation of the built hierarchy: every reference in range, every parent
+// link consistent with the child lists.  The traversal reads `corrupt` once
+// and refuses to run on a tree that failed.
+__global__ void k_validate(BvhView B) {
+  const int n_int = B.hdr->n_int, n4 = B.hdr->n4, nf = B.hdr->nf;
+  bool bad = (n4 < 1 || n4 > n_int);
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n_int; j += gridDim.x * blockDim.x) {
+    const int2 ch = B.bin_child[j];
+    const int c2[2] = {ch.x, ch.y};
+    for (int k = 0; k < 2; ++k) {
+      const int c = c2[k];
+      if (c >= 0) bad |= c >= n_int || B.parent[c] != j;
+      else bad |= (uint32_t)(~c) >= (uint32_t)nf || (nf > 1 && B.parent[n_int + ~c] != j);
+    }
+    if (j < n4) {
+      const int4 r = reinterpret_cast<const int4*>(B.node4)[8 * j + 6];
+      const int rr[4] = {r.x, r.y, r.z, r.w};
+      for (int k = 0; k < 4; ++k) {
+        const int c = rr[k];
+        if (c == kNoChild) continue;
+        bad |= c >= 0 ? c >= n4 : (uint32_t)(~c) >= (uint32_t)nf;
+      }
+    }
+  }
+  if (bad) atomicExch(&B.hdr->corrupt, 1);
+}
+
 __global__ void k_bvh_header(BvhHeader* h, int32_t nf) {
   h->nf = nf;
   h->n_int = nf > 1 ? nf - 1 : 1;
-  h->root = 0;
-  h->pad = 0;
+  h->n4 = 0;
+  h->corrupt = 0;
 }
 
 // scratch layout for build/refit
@@ -400,31 +533,43 @@ void launch_refit(const float* V, const int32_t* F, int32_t nf, void* bvh, void*
   ProfScope ps("k_refit", s);
   cudaMemsetAsync(S.arrive, 0, sizeof(uint32_t) * n_int, s);
   k_refit<<<grid_for(nf, 256), 256, 0, s>>>(V, F, nf, B, S.arrive);
+  k_node2_boxes<<<grid_for((int64_t)n_int, 256), 256, 0, s>>>(B);
+  k_node4_boxes<<<grid_for((int64_t)n_int, 256), 256, 0, s>>>(B);
 }
 
 void launch_build(const float* V, const int32_t* F, int32_t nf, void* bvh, void* scratch, cudaStream_t s) {
   BvhView B = bvh_view(bvh, nf);
   BuildScratch S(scratch, nf);
-  ProfScope ps("lbvh_build", s);
-  k_bvh_header<<<1, 1, 0, s>>>(B.hdr, nf);
-  k_init_bounds<<<1, 32, 0, s>>>(S.bounds);
-  k_centroid_bounds<<<grid_for(nf, 256), 256, 0, s>>>(V, F, nf, S.bounds);
-  k_morton<<<grid_for(nf, 256), 256, 0, s>>>(V, F, nf, S.bounds, S.keys_a, S.vals_a);
-  const int nblocks = (nf + kSortTile - 1) / kSortTile;
-  uint32_t *kin = S.keys_a, *vin = S.vals_a, *kout = S.keys_b, *vout = S.vals_b;
-  for (int shift = 0; shift < 32; shift += 8) {
-    k_radix_hist<<<nblocks, kSortThreads, 0, s>>>(kin, nf, shift, S.hist);
-    k_scan_exclusive<<<1, 1024, 0, s>>>(S.hist, 256 * nblocks);
-    k_radix_scatter<<<nblocks, kSortThreads, 0, s>>>(kin, vin, nf, shift, S.hist, kout, vout);
-    uint32_t* t = kin; kin = kout; kout = t;
-    t = vin; vin = vout; vout = t;
-  }
-  // after an even number of passes the sorted data is back in keys_a/vals_a
-  k_gather_leaf_tri<<<grid_for(nf, 256), 256, 0, s>>>(vin, nf, B.leaf_tri);
-  if (nf > 1) {
-    k_karras<<<grid_for(nf - 1, 256), 256, 0, s>>>(kin, nf, B.nodes, B.parent);
-  } else {
-    k_single_leaf<<<1, 1, 0, s>>>(B.nodes, B.parent);
+  const int n_int = nf > 1 ? nf - 1 : 1;
+  {
+    ProfScope ps("lbvh_build", s);
+    k_bvh_header<<<1, 1, 0, s>>>(B.hdr, nf);
+    k_init_bounds<<<1, 32, 0, s>>>(S.bounds);
+    k_centroid_bounds<<<grid_for(nf, 256), 256, 0, s>>>(V, F, nf, S.bounds);
+    k_morton<<<grid_for(nf, 256), 256, 0, s>>>(V, F, nf, S.bounds, S.keys_a, S.vals_a);
+    const int nblocks = (nf + kSortTile - 1) / kSortTile;
+    uint32_t *kin = S.keys_a, *vin = S.vals_a, *kout = S.keys_b, *vout = S.vals_b;
+    for (int shift = 0; shift < 32; shift += 8) {
+      k_radix_hist<<<nblocks, kSortThreads, 0, s>>>(kin, nf, shift, S.hist);
+      k_scan_exclusive<<<1, 1024, 0, s>>>(S.hist, 256 * nblocks);
+      k_radix_scatter<<<nblocks, kSortThreads, 0, s>>>(kin, vin, nf, shift, S.hist, kout, vout);
+      uint32_t* t = kin; kin = kout; kout = t;
+      t = vin; vin = vout; vout = t;
+    }
+    // after an even number of passes the sorted data is back in keys_a/vals_a
+    k_gather_leaf_tri<<<grid_for(nf, 256), 256, 0, s>>>(vin, nf, B.leaf_tri);
+    if (nf > 1) {
+      k_karras<<<grid_for(nf - 1, 256), 256, 0, s>>>(kin, nf, B.bin_child, B.parent);
+    } else {
+      k_single_leaf<<<1, 1, 0, s>>>(B.bin_child, B.parent);
+    }
+    // 4-wide topology: even-depth nodes, numbered by a scan
+    uint32_t* flag = S.keys_b;  // free after the sort
+    k_even_depth<<<grid_for(n_int, 256), 256, 0, s>>>(B, flag);
+    k_scan_exclusive<<<1, 1024, 0, s>>>(flag, n_int);
+    k_bin_to4<<<grid_for(n_int, 256), 256, 0, s>>>(B, flag);
+    k_node4_topology<<<grid_for(n_int, 256), 256, 0, s>>>(B);
+    k_validate<<<grid_for(n_int, 256), 256, 0, s>>>(B);
   }
   launch_refit(V, F, nf, bvh, scratch, s);
 }

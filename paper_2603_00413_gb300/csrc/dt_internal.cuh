@@ -56,49 +56,78 @@ constexpr int kMaxDepth = 30;
 constexpr int kTraceStack = 64;
 
 // ---------------------------------------------------------------------------
-// BVH buffer: header, internal nodes, leaf-order triangles, leaf -> triangle
-// map, parent links.  Internal node j (0 <= j < n_int) is 4 float4:
-//   n0 = child0 (lo.x, hi.x, lo.y, hi.y), n1 = child1 (lo.x, hi.x, lo.y, hi.y),
-//   n2 = (child0 lo.z, hi.z, child1 lo.z, hi.z), n3 = (child0, child1) as int
-// where a child >= 0 is an internal node and a child < 0 is leaf ~child.
-// Leaf i (sorted position) is triangle leaf_tri[i], stored as 3 float4:
-//   (v0.xyz, triangle id), (e1 = v1 - v0, 0), (e2 = v2 - v0, 0).
-// parent[] holds the parent of internal node j at j and of leaf i at n_int+i.
+// BVH buffer.  A binary LBVH (Karras) is built and refitted; the traversal
+// reads a 4-wide BVH derived from it: every binary node at even depth is a
+// 4-wide node whose children are its grandchildren (a leaf child stays one
+// child, so a node has 2 to 4 children).
+//  - bin_child[j] = (left, right) of binary internal node j; a child >= 0 is
+//    internal, < 0 is leaf ~child (a one-triangle mesh has one node whose two
+//    children are both leaf 0).  parent[] holds the parent of internal
+//    node j at j and of leaf i at n_int + i.
+//  - box_int[2j], box_int[2j+1] = (lo, hi) of binary node j;
+//    box_leaf[2i], box_leaf[2i+1] = (lo, hi) of leaf i.
+//  - node4[8m .. 8m+7]: 4-wide node m as float4 rows (one component per
+//    child): lo.x, hi.x, lo.y, hi.y, lo.z, hi.z, child refs (int bits: >= 0
+//    node4 index, < 0 leaf ~i, kNoChild empty with an empty box), and the
+//    binary sources of the four boxes (same encoding, for the refit).
+//  - bin_to4[j] = node4 index of binary node j (even depth) or -1.
+//  - node2[4j .. 4j+3]: binary node j for the 2-wide traversal: child-0 box
+//    (lo.x, hi.x, lo.y, hi.y), child-1 box (same), (c0 lo.z, hi.z, c1 lo.z,
+//    hi.z), (child0, child1) as int bits (leaf ~i, kNoChild empty).
+//  - tris[3i..3i+2] = leaf i's triangle: (v0, id), (e1, 0), (e2, 0).
+//  - leaf_tri[i] = triangle of leaf i.
 // ---------------------------------------------------------------------------
+constexpr int kNoChild = (int)0x80000000;
+
 struct BvhHeader {
   int32_t nf;
-  int32_t n_int;  // number of internal nodes = max(nf - 1, 1)
-  int32_t root;   // 0
-  int32_t pad;
+  int32_t n_int;    // binary internal nodes = max(nf - 1, 1)
+  int32_t n4;       // 4-wide nodes (written on the device)
+  int32_t corrupt;  // set by the build's validation pass when a reference is out of range
 };
 
 struct BvhView {
   BvhHeader* hdr;
-  float4* nodes;     // [n_int * 4]
-  float4* tris;      // [nf * 3]
-  int32_t* leaf_tri; // [nf]
+  int2* bin_child;   // [n_int]
   int32_t* parent;   // [n_int + nf]
+  float4* box_int;   // [2 n_int]
+  float4* box_leaf;  // [2 nf]
+  float4* node4;     // [8 n_int] (at most n_int 4-wide nodes)
+  float4* node2;     // [4 n_int]
+  int32_t* bin_to4;  // [n_int]
+  float4* tris;      // [3 nf]
+  int32_t* leaf_tri; // [nf]
 };
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct BvhLayout {
-  size_t off_nodes, off_tris, off_leaf, off_parent, total;
+  size_t off_child, off_parent, off_box_int, off_box_leaf, off_node4, off_node2, off_bin_to4, off_tris, off_leaf,
+      total;
   __host__ __device__ explicit BvhLayout(int32_t nf) {
     const size_t n_int = nf > 1 ? (size_t)nf - 1 : 1;
-    off_nodes = 256;
-    off_tris = align_up(off_nodes + n_int * 4 * sizeof(float4), 256);
-    off_leaf = align_up(off_tris + (size_t)nf * 3 * sizeof(float4), 256);
-    off_parent = align_up(off_leaf + (size_t)nf * sizeof(int32_t), 256);
-    total = align_up(off_parent + (n_int + (size_t)nf) * sizeof(int32_t), 256);
+    size_t o = 256;
+    auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes, 256); return r; };
+    off_node4 = take(n_int * 8 * sizeof(float4));
+    off_node2 = take(n_int * 4 * sizeof(float4));
+    off_tris = take((size_t)nf * 3 * sizeof(float4));
+    off_child = take(n_int * sizeof(int2));
+    off_parent = take((n_int + (size_t)nf) * sizeof(int32_t));
+    off_box_int = take(n_int * 2 * sizeof(float4));
+    off_box_leaf = take((size_t)nf * 2 * sizeof(float4));
+    off_bin_to4 = take(n_int * sizeof(int32_t));
+    off_leaf = take((size_t)nf * sizeof(int32_t));
+    total = o;
   }
 };
 
 __host__ __device__ inline BvhView bvh_view(const void* base, int32_t nf) {
   BvhLayout L(nf);
   char* b = (char*)base;
-  return BvhView{(BvhHeader*)b, (float4*)(b + L.off_nodes), (float4*)(b + L.off_tris), (int32_t*)(b + L.off_leaf),
-                 (int32_t*)(b + L.off_parent)};
+  return BvhView{(BvhHeader*)b, (int2*)(b + L.off_child), (int32_t*)(b + L.off_parent),
+                 (float4*)(b + L.off_box_int), (float4*)(b + L.off_box_leaf), (float4*)(b + L.off_node4),
+                 (float4*)(b + L.off_node2), (int32_t*)(b + L.off_bin_to4), (float4*)(b + L.off_tris),
+                 (int32_t*)(b + L.off_leaf)};
 }
 
 // ---------------------------------------------------------------------------

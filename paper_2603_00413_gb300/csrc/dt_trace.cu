@@ -118,9 +118,90 @@ __device__ __forceinline__ void test_leaf(const float4* __restrict__ tris, int l
   }
 }
 
-// A tree traversal visits every internal node at most once, so more than
-// max_iter = 2 n_int + 8 steps means a corrupt hierarchy: give up and flag it.
-__device__ __forceinline__ ClosestHit closest_hit(const float4* __restrict__ nodes, const float4* __restrict__ tris,
+// One visit of 4-wide node `node`: slab tests on its four children, leaf
+// children intersected at once, internal children that were hit (and are not
+// beyond the closest hit so far) entered nearest first with the others pushed
+// farthest first.  Returns the next node, or -1 when the stack is empty.
+// Empty child slots (kNoChild) are masked explicitly: a slab test only
+// intersects intervals, so it would accept their inverted (+inf, -inf) box.
+// References need no range check here: the build validated them (k_validate)
+// and the traversal kernels refuse a tree that failed.
+__device__ __forceinline__ int visit_node4(const float4* __restrict__ node4, const float4* __restrict__ tris, int node,
+                                           float3 o, float3 d, float3 idir, int src, float tmin, ClosestHit& h,
+                                           int* stack, int& sp, bool& overflow, uint32_t& ntest) {
+  const float4* Np = node4 + 8 * node;
+  const float4 lx = __ldg(Np), hx = __ldg(Np + 1), ly = __ldg(Np + 2), hy = __ldg(Np + 3);
+  const float4 lz = __ldg(Np + 4), hz = __ldg(Np + 5);
+  const int4 ch = __ldg(reinterpret_cast<const int4*>(Np) + 6);
+  float t0, t1, t2, t3;
+  bool b0 = ch.x != kNoChild && slab(o, idir, lx.x, hx.x, ly.x, hy.x, lz.x, hz.x, tmin, h.t, t0);
+  bool b1 = ch.y != kNoChild && slab(o, idir, lx.y, hx.y, ly.y, hy.y, lz.y, hz.y, tmin, h.t, t1);
+  bool b2 = ch.z != kNoChild && slab(o, idir, lx.z, hx.z, ly.z, hy.z, lz.z, hz.z, tmin, h.t, t2);
+  bool b3 = ch.w != kNoChild && slab(o, idir, lx.w, hx.w, ly.w, hy.w, lz.w, hz.w, tmin, h.t, t3);
+  if (b0 && ch.x < 0) { test_leaf(tris, ~ch.x, o, d, src, tmin, h, ntest); b0 = false; }
+  if (b1 && ch.y < 0) { test_leaf(tris, ~ch.y, o, d, src, tmin, h, ntest); b1 = false; }
+  if (b2 && ch.z < 0) { test_leaf(tris, ~ch.z, o, d, src, tmin, h, ntest); b2 = false; }
+  if (b3 && ch.w < 0) { test_leaf(tris, ~ch.w, o, d, src, tmin, h, ntest); b3 = false; }
+  // internal children still in front of the closest hit, as (t, ref) pairs
+  float ta = (b0 && t0 <= h.t) ? t0 : INFINITY, tb = (b1 && t1 <= h.t) ? t1 : INFINITY;
+  float tc = (b2 && t2 <= h.t) ? t2 : INFINITY, td = (b3 && t3 <= h.t) ? t3 : INFINITY;
+  int ra = ch.x, rb = ch.y, rc = ch.z, rd = ch.w;
+  const int cnt = (ta < INFINITY) + (tb < INFINITY) + (tc < INFINITY) + (td < INFINITY);
+  if (cnt == 0) return sp > 0 ? stack[--sp] : -1;
+  // sort the four pairs by t (five compare-exchanges)
+#define DT_CSWAP(ta_, ra_, tb_, rb_)                     \
+  if (tb_ < ta_) {                                      \
+    const float tt = ta_; ta_ = tb_; tb_ = tt;          \
+    const int rr = ra_; ra_ = rb_; rb_ = rr;            \
+  }
+  DT_CSWAP(ta, ra, tb, rb) DT_CSWAP(tc, rc, td, rd) DT_CSWAP(ta, ra, tc, rc) DT_CSWAP(tb, rb, td, rd)
+  DT_CSWAP(tb, rb, tc, rc)
+#undef DT_CSWAP
+  if (sp + cnt - 1 > kTraceStack) {
+    overflow = true;
+    return ra;
+  }
+  if (cnt >= 4) stack[sp++] = rd;
+  if (cnt >= 3) stack[sp++] = rc;
+  if (cnt >= 2) stack[sp++] = rb;
+  return ra;
+}
+
+// One visit of binary node `node` (same contract as visit_node4; binary
+// nodes always have two children).
+__device__ __forceinline__ int visit_node2(const float4* __restrict__ node2, const float4* __restrict__ tris, int node,
+                                           float3 o, float3 d, float3 idir, int src, float tmin, ClosestHit& h,
+                                           int* stack, int& sp, bool& overflow, uint32_t& ntest) {
+  const float4* Np = node2 + 4 * node;
+  const float4 n0 = __ldg(Np), n1 = __ldg(Np + 1), n2 = __ldg(Np + 2);
+  const int4 n3 = __ldg(reinterpret_cast<const int4*>(Np) + 3);
+  float tn0, tn1;
+  bool h0 = slab(o, idir, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, tmin, h.t, tn0);
+  bool h1 = slab(o, idir, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, tmin, h.t, tn1);
+  if (h0 && n3.x < 0) { test_leaf(tris, ~n3.x, o, d, src, tmin, h, ntest); h0 = false; }
+  if (h1 && n3.y < 0) { test_leaf(tris, ~n3.y, o, d, src, tmin, h, ntest); h1 = false; }
+  if (h0 && h1) {
+    int nearc = n3.x, farc = n3.y;
+    if (tn1 < tn0) { nearc = n3.y; farc = n3.x; }
+    if (sp < kTraceStack) stack[sp++] = farc; else overflow = true;
+    return nearc;
+  }
+  if (h0) return n3.x;
+  if (h1) return n3.y;
+  return sp > 0 ? stack[--sp] : -1;
+}
+
+template <int kWidth>
+__device__ __forceinline__ int visit_node(const float4* __restrict__ nodes, const float4* __restrict__ tris, int node,
+                                          float3 o, float3 d, float3 idir, int src, float tmin, ClosestHit& h,
+                                          int* stack, int& sp, bool& overflow, uint32_t& ntest) {
+  if (kWidth == 4) return visit_node4(nodes, tris, node, o, d, idir, src, tmin, h, stack, sp, overflow, ntest);
+  return visit_node2(nodes, tris, node, o, d, idir, src, tmin, h, stack, sp, overflow, ntest);
+}
+
+// A tree traversal visits every node at most once, so more than max_iter
+// = 2 n_int + 8 visits means a corrupt hierarchy: give up and flag it.
+__device__ __forceinline__ ClosestHit closest_hit(const float4* __restrict__ node2, const float4* __restrict__ tris,
                                                   float3 o, float3 d, int src, float tmin, int max_iter,
                                                   uint32_t& nvis, uint32_t& ntest, bool& overflow) {
   ClosestHit h{INFINITY, 0.f, 0.f, -1};
@@ -128,60 +209,88 @@ __device__ __forceinline__ ClosestHit closest_hit(const float4* __restrict__ nod
   int stack[kTraceStack];
   int sp = 0;
   int node = 0;
-  for (int it = 0;; ++it) {
+  for (int it = 0; node >= 0; ++it) {
     if (it >= max_iter) {
       overflow = true;
       break;
     }
-    const float4* N = nodes + 4 * node;
-    const float4 n0 = __ldg(N), n1 = __ldg(N + 1), n2 = __ldg(N + 2);
-    const int4 n3 = __ldg(reinterpret_cast<const int4*>(N) + 3);
     ++nvis;
-    float tn0, tn1;
-    bool h0 = slab(o, idir, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, tmin, h.t, tn0);
-    bool h1 = slab(o, idir, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, tmin, h.t, tn1);
-    if (h0 && n3.x < 0) { test_leaf(tris, ~n3.x, o, d, src, tmin, h, ntest); h0 = false; }
-    if (h1 && n3.y < 0) { test_leaf(tris, ~n3.y, o, d, src, tmin, h, ntest); h1 = false; }
-    if (h0 && h1) {
-      int nearc = n3.x, farc = n3.y;
-      if (tn1 < tn0) { nearc = n3.y; farc = n3.x; }
-      if (sp < kTraceStack) stack[sp++] = farc; else overflow = true;
-      node = nearc;
-    } else if (h0) {
-      node = n3.x;
-    } else if (h1) {
-      node = n3.y;
-    } else {
-      if (sp == 0) break;
-      node = stack[--sp];
-    }
+    node = visit_node2(node2, tris, node, o, d, idir, src, tmin, h, stack, sp, overflow, ntest);
   }
   return h;
 }
 
-// Persistent traversal of level k: warps take 32 segments at a time from a
-// shared cursor until the level is exhausted.
-__global__ void __launch_bounds__(256) k_trace(WsView W, const float4* __restrict__ nodes,
-                                               const float4* __restrict__ tris, int k, float tmin, int max_iter) {
+// Persistent traversal of level k with dynamic refill.  Every lane carries
+// its own ray; a warp runs up to `steps` node visits per round, then, when
+// at least `refill` lanes have finished, pulls that many new segments from
+// the level's cursor with one atomic and hands them to the idle lanes.  A
+// warp therefore no longer waits for the slowest ray of a fixed batch of 32
+// (the divergence that left most lanes idle), and stops when the level is
+// exhausted and its last ray is done.
+template <int kMinBlocks, int kWidth>
+__global__ void __launch_bounds__(256, kMinBlocks) k_trace(WsView W, const float4* __restrict__ nodes,
+                                                           const float4* __restrict__ tris, const BvhHeader* bh,
+                                                           int k, float tmin, int max_iter, int steps, int refill) {
   WsHeader* H = W.hdr;
+  if (bh->corrupt) {  // the build's validation failed: trace nothing
+    if (threadIdx.x == 0) atomicOr(&H->status, ST_STACK_OVERFLOW);
+    return;
+  }
   const uint32_t n = level_size(H, k);
   const uint32_t start = H->level_start[k];
   const uint32_t lane = threadIdx.x & 31;
+  const unsigned lanes_below = (1u << lane) - 1u;
   uint32_t nvis = 0, ntest = 0;
   bool overflow = false;
+  bool active = false, exhausted = false;
+  uint32_t a = 0;
+  float3 o = mk(0.f, 0.f, 0.f), d = o, idir = o;
+  int src = -1, node = 0, sp = 0, iters = 0;
+  ClosestHit h{INFINITY, 0.f, 0.f, -1};
+  int stack[kTraceStack];
   while (true) {
-    uint32_t base = 0;
-    if (lane == 0) base = atomicAdd(&H->fetch[k], 32u);
-    base = __shfl_sync(kFull, base, 0);
-    if (base >= n) break;
-    const uint32_t i = base + lane;
-    if (i < n) {
-      const uint32_t a = start + i;
-      const float4 ro = W.ray_o[a], rd = W.ray_d[a], rw = W.ray_w[a];
-      const ClosestHit h = closest_hit(nodes, tris, xyz(ro), xyz(rd), __float_as_int(rw.w), tmin, max_iter, nvis,
-                                       ntest, overflow);
-      W.hit[a] = h.tri >= 0 ? make_float4(h.t, h.b1, h.b2, __int_as_float(h.tri))
-                            : make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+    const unsigned idle = __ballot_sync(kFull, !active);
+    const int n_idle = __popc(idle);
+    if (!exhausted && n_idle >= refill) {
+      uint32_t base = 0;
+      if (lane == 0) base = atomicAdd(&H->fetch[k], (uint32_t)n_idle);
+      base = __shfl_sync(kFull, base, 0);
+      if (base + (uint32_t)n_idle >= n) exhausted = true;
+      if (!active) {
+        const uint32_t i = base + __popc(idle & lanes_below);
+        if (i < n) {
+          a = start + i;
+          const float4 ro = W.ray_o[a], rd = W.ray_d[a], rw = W.ray_w[a];
+          o = xyz(ro);
+          d = xyz(rd);
+          idir = mk(safe_inv(d.x), safe_inv(d.y), safe_inv(d.z));
+          src = __float_as_int(rw.w);
+          h = ClosestHit{INFINITY, 0.f, 0.f, -1};
+          node = 0;
+          sp = 0;
+          iters = 0;
+          active = true;
+        }
+      }
+    }
+    if (!__any_sync(kFull, active)) break;
+    if (!active) continue;
+    for (int st = 0; st < steps; ++st) {
+      bool done = false;
+      if (++iters > max_iter) {
+        overflow = true;
+        done = true;
+      } else {
+        ++nvis;
+        node = visit_node<kWidth>(nodes, tris, node, o, d, idir, src, tmin, h, stack, sp, overflow, ntest);
+        done = node < 0;
+      }
+      if (done) {
+        W.hit[a] = h.tri >= 0 ? make_float4(h.t, h.b1, h.b2, __int_as_float(h.tri))
+                              : make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+        active = false;
+        break;
+      }
     }
   }
   warp_add_u64(&H->counters[CNT_NODES], nvis);
@@ -192,11 +301,16 @@ __global__ void __launch_bounds__(256) k_trace(WsView W, const float4* __restric
 // Closest hit of arbitrary rays (tooling and tests).
 __global__ void k_closest_hit_rays(const float4* __restrict__ nodes, const float4* __restrict__ tris,
                                    const float* __restrict__ o, const float* __restrict__ d,
-                                   const int32_t* __restrict__ src, int32_t n, float tmin, int max_iter,
-                                   int32_t* __restrict__ tri, float* __restrict__ tbb) {
+                                   const int32_t* __restrict__ src, int32_t n, const BvhHeader* bh, float tmin,
+                                   int max_iter, int32_t* __restrict__ tri, float* __restrict__ tbb) {
+  const bool corrupt = bh->corrupt != 0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     uint32_t nv = 0, nt = 0;
     bool ovf = false;
+    if (corrupt) {
+      tri[i] = -2;
+      continue;
+    }
     const ClosestHit h = closest_hit(nodes, tris, load3(o + 3 * i), load3(d + 3 * i), src ? src[i] : -1, tmin,
                                      max_iter, nv, nt, ovf);
     tri[i] = ovf ? -2 : h.tri;
@@ -356,8 +470,29 @@ __global__ void k_dump(WsView W, int32_t* __restrict__ si, float* __restrict__ s
 // ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
-static int persistent_blocks() { return 8 * num_sms(); }
-static int traversal_limit(int32_t nf) { return 2 * (nf > 1 ? nf - 1 : 1) + 8; }
+// Launch and scheduling knobs (dt_set_tuning); process-wide.
+dt_tuning g_tuning = {16, 8, 5, 8, 2};
+static int persistent_blocks() { return g_tuning.trace_blocks_per_sm * num_sms(); }
+static int shade_blocks() { return g_tuning.shade_blocks_per_sm * num_sms(); }
+static int n_int_of(int32_t nf) { return nf > 1 ? nf - 1 : 1; }
+
+// The traversal is compiled for 2..8 resident CTAs of 256 threads per SM (the
+// register budget per thread follows) and for the 2- and 4-wide node
+// formats; the tuning picks the variant and the persistent grid is
+// trace_blocks_per_sm CTAs per SM.
+template <int kWidth, typename... A>
+static void launch_trace_w(int bps, cudaStream_t s, A... a) {
+  const int g = bps * num_sms();
+  switch (bps) {
+    case 1: case 2: k_trace<2, kWidth><<<g, 256, 0, s>>>(a...); break;
+    case 3: k_trace<3, kWidth><<<g, 256, 0, s>>>(a...); break;
+    case 4: k_trace<4, kWidth><<<g, 256, 0, s>>>(a...); break;
+    case 5: k_trace<5, kWidth><<<g, 256, 0, s>>>(a...); break;
+    case 6: k_trace<6, kWidth><<<g, 256, 0, s>>>(a...); break;
+    default: k_trace<8, kWidth><<<g, 256, 0, s>>>(a...); break;
+  }
+}
+static int traversal_limit(int32_t nf) { return 2 * n_int_of(nf) + 8; }
 
 void launch_forward(const dt_scene& sc, const dt_views& vw, const dt_params& p, float* out, void* ws,
                     unsigned long long cap, cudaStream_t s) {
@@ -378,11 +513,18 @@ void launch_forward(const dt_scene& sc, const dt_views& vw, const dt_params& p, 
   for (int k = 0; k <= p.max_depth; ++k) {
     {
       ProfScope ps("k_trace", s);
-      k_trace<<<persistent_blocks(), 256, 0, s>>>(W, B.nodes, B.tris, k, p.t_min, traversal_limit(sc.nf));
+      if (g_tuning.bvh_width == 4)
+        launch_trace_w<4>(g_tuning.trace_blocks_per_sm, s, W, (const float4*)B.node4, (const float4*)B.tris,
+                          (const BvhHeader*)B.hdr, k, p.t_min, traversal_limit(sc.nf), g_tuning.trace_steps,
+                          g_tuning.trace_refill);
+      else
+        launch_trace_w<2>(g_tuning.trace_blocks_per_sm, s, W, (const float4*)B.node2, (const float4*)B.tris,
+                          (const BvhHeader*)B.hdr, k, p.t_min, traversal_limit(sc.nf), g_tuning.trace_steps,
+                          g_tuning.trace_refill);
     }
     {
       ProfScope ps("k_shade", s);
-      k_shade<<<persistent_blocks(), 256, 0, s>>>(W, S, k, p.max_depth, p.spp, n_pix, out);
+      k_shade<<<shade_blocks(), 256, 0, s>>>(W, S, k, p.max_depth, p.spp, n_pix, out);
     }
   }
 }
@@ -398,8 +540,8 @@ void launch_closest_hit(const void* bvh, int32_t nf, const float* o, const float
   BvhView B = bvh_view(bvh, nf);
   int b = (n + 127) / 128;
   if (b > 8 * num_sms()) b = 8 * num_sms();
-  k_closest_hit_rays<<<b > 0 ? b : 1, 128, 0, s>>>(B.nodes, B.tris, o, d, src, n, tmin, traversal_limit(nf), tri,
-                                                    tbb);
+  k_closest_hit_rays<<<b > 0 ? b : 1, 128, 0, s>>>(B.node2, B.tris, o, d, src, n, B.hdr, tmin,
+                                                    traversal_limit(nf), tri, tbb);
 }
 
 }  // namespace dt
