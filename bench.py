@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--cpu-sample", type=int, default=12, help="pixels in the CPU oracle sample")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-scene batching comparison")
+    ap.add_argument("--batch-scenes", type=int, default=64)
     return ap.parse_args()
 
 
@@ -210,8 +212,99 @@ def run_reference(args):
 # GPU leg
 # ---------------------------------------------------------------------------
 # kernels launched per profiled scope (a scope may hold more than one kernel)
-KERNELS_PER_SCOPE = {"k_vertex_normals": 2, "k_refit": 1, "k_camera": 1, "k_trace": 1, "k_shade": 1,
-                     "k_l2_loss_grad": 1, "k_adjoint": 1, "k_face_normals_backward": 1, "lbvh_build": 14}
+KERNELS_PER_SCOPE = {"k_vertex_normals": 2, "k_refit": 3, "k_camera": 1, "k_trace": 1, "k_shade": 1,
+                     "k_l2_loss_grad": 1, "k_adjoint": 1, "k_face_normals_backward": 1, "lbvh_build": 21,
+                     "k_write_table": 2, "k_zero_images": 1, "k_zero_grads": 1}
+
+
+def batch_leg(args, dt, dev, steps):
+    """64 scenes of uneven size (2k-200k faces, 128^2-800^2 images, depth
+    4-12), fwd+bwd with a fixed image gradient: the plain loop (each scene
+    rendered and differentiated by its own calls), one batched render +
+    backward, and the batched step replayed from a captured CUDA graph."""
+    import torch
+    from paper_2603_00413_gb300 import scenes as S
+    scs = S.batch_scenes(args.batch_scenes, 2)
+    items = []
+    for sc in scs:
+        V = torch.from_numpy(sc.V).to(dev)
+        F = torch.from_numpy(sc.F).to(dev)
+        c = sc.cams[0]
+        items.append(dt.BatchItem(V, F, dt.build_bvh(V, F), dt.vertex_normals(V, F),
+                                  torch.tensor([sc.ior], device=dev), torch.from_numpy(sc.sigma).to(dev),
+                                  torch.from_numpy(sc.env).to(dev), torch.from_numpy(c.as_array()[None]).to(dev),
+                                  c.width, c.height, dt.Params(sc.max_depth)))
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(5)
+    grads = [torch.randn(1, it.height, it.width, 3, device=dev, generator=gen) for it in items]
+    stream = torch.cuda.current_stream()
+    # batched
+    imgs, tape = dt.render_batch(items)
+    st = tape.stats
+    seg = st["segments"]
+    _, bws = dt._aligned_empty(dt.batch_backward_workspace_size(items, st["max_level"]), dev)
+    gouts = [(torch.empty_like(it.V), torch.empty(1, device=dev), torch.empty(3, device=dev)) for it in items]
+
+    def batched():
+        _, t = dt.render_batch(items, ws=tape.ws, outs=imgs, check=False)
+        t.stats = st
+        dt.render_batch_backward(t, grads, bws=bws, outs=gouts)
+
+    # plain: each scene on its own, with its own workspace sized by a first render
+    plain_ws = []
+    for it in items:
+        _, t = dt.render(it.V, it.F, it.bvh, it.N, it.ior, it.sigma, it.env, it.cams, it.width, it.height, it.params)
+        _, b = dt._aligned_empty(dt.backward_workspace_size(t.stats["max_level"], it.V.shape[0]), dev)
+        plain_ws.append((t, b))
+    plain_seg = sum(t.stats["segments"] for t, _ in plain_ws)
+
+    def plain():
+        for it, (t, b), img, g in zip(items, plain_ws, imgs, grads):
+            _, tp = dt.render(it.V, it.F, it.bvh, it.N, it.ior, it.sigma, it.env, it.cams, it.width, it.height,
+                              it.params, ws=t.ws, out=img, check=False)
+            tp.stats = t.stats
+            dt.render_backward(tp, g, bws=b)
+
+    def timed(fn, k):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    ms_batched = timed(batched, steps)
+    ms_plain = timed(plain, steps)
+    # the batched step captured once in a CUDA graph and replayed
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        batched()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(graph, stream=side):
+            batched()
+    ms_graph = timed(graph.replay, steps)
+    chk = dt.read_stats(tape.ws)
+    assert chk["status"] == dt.DT_OK and chk["segments"] == seg, chk
+    depth_max = max(it.params.max_depth for it in items)
+    return {
+        "workload": f"{len(items)} random-blob scenes, {sum(it.F.shape[0] for it in items)} faces in all "
+                    f"({min(it.F.shape[0] for it in items)}-{max(it.F.shape[0] for it in items)}), "
+                    f"{sum(it.width * it.height for it in items)} pixels ({min(it.width for it in items)}^2-"
+                    f"{max(it.width for it in items)}^2), depth {min(it.params.max_depth for it in items)}-"
+                    f"{depth_max}, fwd+bwd with a fixed image gradient",
+        "segments_per_step": int(seg),
+        "plain_segments_per_s": plain_seg / (ms_plain / 1e3), "plain_ms": ms_plain,
+        "batched_segments_per_s": seg / (ms_batched / 1e3), "batched_ms": ms_batched,
+        "graph_segments_per_s": seg / (ms_graph / 1e3), "graph_ms": ms_graph,
+        "launches_per_step_plain": int(sum(3 * (it.params.max_depth + 1) + 8 for it in items)),
+        "launches_per_step_batched": int(3 * (depth_max + 1) + 4 + 2 * (1 + (len(items) + 23) // 24)),
+    }
 
 
 def run_ours(args):
@@ -413,6 +506,12 @@ def run_ours(args):
                "sample": f"{args.cpu_sample} seeded pixels of the same workload ({nseg} segments), forward + "
                          f"gradient by forward mode over the parameters those paths touch, {secs:.1f} s"}
 
+    batch = None
+    if rank == 0 and world == 1 and not args.no_batch:
+        del ws, bws, tape
+        torch.cuda.empty_cache()
+        batch = batch_leg(args, dt, dev, max(3, args.steps // 4))
+
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -431,6 +530,7 @@ def run_ours(args):
             "clocks": clk.summary(),
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "batch": batch,
             "levels": stats["level_count"],
             "nodes_per_segment": stats["nodes_visited"] / seg,
             "tris_per_segment": stats["tris_tested"] / seg,

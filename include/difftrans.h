@@ -235,6 +235,37 @@ dt_status dt_render_backward(const dt_scene* scene, const dt_views* views, const
                              int64_t max_level, dt_stream stream);
 
 /* ------------------------------------------------------------------------
+ * Batching: many scenes of uneven size in one render.  One call traces the
+ * camera rays of every scene; then for each depth one persistent traversal
+ * launch and one shading launch cover the segments of all scenes together
+ * (each segment carries its scene through its sample index), so the number
+ * of launches depends on the largest depth only, not on the number of
+ * scenes.  Each entry is a scene as for dt_render with its own views,
+ * params and image; dt_render is the one-entry batch.  Sample indices are
+ * global across the batch (entry i's samples follow entry i-1's) for
+ * dt_dump_segments.  n in [1, 256]; the total of primary rays < 2^32.
+ * The backward takes d_grad_out, d_grad_V, d_grad_ior, d_grad_sigma of each
+ * entry (outputs overwritten) and a scratch sized by
+ * dt_batch_backward_workspace_size.  Entries are host memory read during
+ * the call; the library keeps no pointer to them.
+ * ------------------------------------------------------------------------ */
+typedef struct dt_batch_entry {
+  dt_scene scene;
+  dt_views views;
+  dt_params params;
+  float* d_out;              /* forward: float[n_views][height][width][3] */
+  const float* d_grad_out;   /* backward: dLoss/dImage, same shape */
+  float* d_grad_V;           /* backward outputs */
+  float* d_grad_ior;
+  float* d_grad_sigma;
+} dt_batch_entry;
+dt_status dt_render_batch(const dt_batch_entry* entries, int32_t n, void* d_ws, size_t ws_bytes, dt_stream stream);
+dt_status dt_batch_backward_workspace_size(const dt_batch_entry* entries, int32_t n, int64_t max_level,
+                                           size_t* bytes);
+dt_status dt_render_batch_backward(const dt_batch_entry* entries, int32_t n, const void* d_ws, size_t ws_bytes,
+                                   void* d_bws, size_t bws_bytes, int64_t max_level, dt_stream stream);
+
+/* ------------------------------------------------------------------------
  * Debug / parity: every segment of the tape in arena order (level by
  * level).  d_seg_i int32[cap][4] = (sample index, heap node id, hit triangle
  * or -1, flags); d_seg_f float[cap][9] = (t, b1, b2, origin xyz, direction

@@ -24,7 +24,9 @@ __all__ = [
     "DiffTransError", "load_library", "vertex_normals", "vertex_normals_backward", "Bvh", "build_bvh",
     "refit_bvh", "Params", "render", "render_backward", "read_stats", "dump_segments", "closest_hit",
     "render_workspace_size", "backward_workspace_size", "Tape", "DiffTransRender", "render_differentiable",
-    "l2_loss_grad", "profile_enable", "profile_read", "vertex_normals_noalloc",
+    "l2_loss_grad", "profile_enable", "profile_read", "vertex_normals_noalloc", "BatchItem", "render_batch",
+    "render_batch_backward", "batch_backward_workspace_size", "get_tuning", "set_tuning",
+    "measure_l2_read_bandwidth",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -77,6 +79,12 @@ class DtStats(ctypes.Structure):
         }
 
 
+class DtBatchEntry(ctypes.Structure):
+    _fields_ = [("scene", DtScene), ("views", DtViews), ("params", DtParams), ("d_out", c_void_p),
+                ("d_grad_out", c_void_p), ("d_grad_V", c_void_p), ("d_grad_ior", c_void_p),
+                ("d_grad_sigma", c_void_p)]
+
+
 class DtTuning(ctypes.Structure):
     _fields_ = [("trace_steps", c_int32), ("trace_refill", c_int32), ("trace_blocks_per_sm", c_int32),
                 ("shade_blocks_per_sm", c_int32), ("bvh_width", c_int32)]
@@ -108,6 +116,10 @@ _PROTOS = {
     "dt_dump_segments": (c_int32, [c_void_p, c_size_t, c_void_p, c_void_p, c_int64, c_void_p]),
     "dt_closest_hit": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_int32, c_float, c_void_p,
                                  c_void_p, c_void_p]),
+    "dt_render_batch": (c_int32, [POINTER(DtBatchEntry), c_int32, c_void_p, c_size_t, c_void_p]),
+    "dt_batch_backward_workspace_size": (c_int32, [POINTER(DtBatchEntry), c_int32, c_int64, POINTER(c_size_t)]),
+    "dt_render_batch_backward": (c_int32, [POINTER(DtBatchEntry), c_int32, c_void_p, c_size_t, c_void_p, c_size_t,
+                                           c_int64, c_void_p]),
     "dt_l2_loss_grad": (c_int32, [c_void_p, c_void_p, c_int64, c_float, c_void_p, c_void_p, c_void_p]),
     "dt_profile_enable": (c_int32, [c_int32]),
     "dt_get_tuning": (c_int32, [POINTER(DtTuning)]),
@@ -456,6 +468,99 @@ def profile_read() -> dict:
     n = c_int32()
     _check(load_library().dt_profile_read(buf, 64, ctypes.byref(n)))
     return {buf[i].name.decode(): (buf[i].launches, buf[i].total_ms) for i in range(min(n.value, 64))}
+
+
+# ---------------------------------------------------------------------------
+# batches
+# ---------------------------------------------------------------------------
+class BatchItem:
+    """One scene of a batched render: geometry, materials, environment, views
+    and parameters, with its own output image."""
+
+    def __init__(self, V, F, bvh: Bvh, N, ior, sigma, env, cams, width: int, height: int, params: Params):
+        self.V, self.F, self.bvh, self.N = V, F, bvh, N
+        self.ior, self.sigma, self.env, self.cams = ior, sigma, env, cams
+        self.width, self.height, self.params = int(width), int(height), params
+        self.out = None
+
+    @property
+    def n_primary(self):
+        return self.cams.shape[0] * self.width * self.height * self.params.spp
+
+    def entry(self, out=None, grad_out=None, dV=None, dior=None, dsig=None):
+        e = DtBatchEntry()
+        e.scene = _scene_struct(self.V, self.F, self.bvh, self.N, self.ior, self.sigma, self.env)
+        e.views = _views_struct(self.cams, self.width, self.height)
+        e.params = self.params.c()
+        e.d_out = out.data_ptr() if out is not None else None
+        e.d_grad_out = grad_out.data_ptr() if grad_out is not None else None
+        e.d_grad_V = dV.data_ptr() if dV is not None else None
+        e.d_grad_ior = dior.data_ptr() if dior is not None else None
+        e.d_grad_sigma = dsig.data_ptr() if dsig is not None else None
+        return e
+
+
+class BatchTape:
+    def __init__(self, ws, items, stats):
+        self.ws, self.items, self.stats = ws, items, stats
+
+
+def render_batch(items, ws: Workspace = None, outs=None, stream=None, check: bool = True):
+    """Forward render of a batch of scenes in one set of launches.  Returns
+    (list of images, BatchTape); with check=True the status is read back and
+    an arena overflow retried."""
+    lib = load_library()
+    n = len(items)
+    dev = items[0].V.device
+    n0 = sum(it.n_primary for it in items)
+    depth = max(it.params.max_depth for it in items)
+    if ws is None:
+        ws = Workspace(default_capacity(n0, depth), dev)
+    if outs is None:
+        outs = [torch.empty(it.cams.shape[0], it.height, it.width, 3, dtype=torch.float32, device=dev)
+                for it in items]
+    arr = (DtBatchEntry * n)(*[it.entry(out=o) for it, o in zip(items, outs)])
+    while True:
+        _check(lib.dt_render_batch(arr, n, _ptr(ws.buf), ws.bytes, _stream(stream)))
+        if not check:
+            return outs, BatchTape(ws, items, None)
+        stats = read_stats(ws, stream)
+        if stats["status"] == DT_ERR_QUEUE_OVERFLOW:
+            ws = Workspace(min(max(2 * ws.capacity, int(1.3 * stats["seg_needed"])), 2 ** 31 - 1), dev)
+            continue
+        if stats["status"] != DT_OK:
+            raise DiffTransError(stats["status"], "device-side error during render")
+        return outs, BatchTape(ws, items, stats)
+
+
+def batch_backward_workspace_size(items, max_level: int) -> int:
+    arr = (DtBatchEntry * len(items))(*[it.entry() for it in items])
+    b = c_size_t()
+    _check(load_library().dt_batch_backward_workspace_size(arr, len(items), int(max_level), ctypes.byref(b)))
+    return b.value
+
+
+def render_batch_backward(tape: BatchTape, grads, bws=None, outs=None, stream=None):
+    """Gradients of sum_i sum(grads[i] * image_i) for every scene of the
+    batch: list of (dV, dior, dsigma)."""
+    lib = load_library()
+    items = tape.items
+    stats = tape.stats if tape.stats is not None else read_stats(tape.ws, stream)
+    if stats["status"] != DT_OK:
+        raise DiffTransError(stats["status"], "the forward render did not finish cleanly")
+    max_level = max(1, stats["max_level"])
+    nbytes = batch_backward_workspace_size(items, max_level)
+    dev = items[0].V.device
+    if bws is None or bws.numel() < nbytes:
+        _, bws = _aligned_empty(nbytes, dev)
+    if outs is None:
+        outs = [(torch.empty_like(it.V), torch.empty(1, device=dev), torch.empty(3, device=dev)) for it in items]
+    grads = [_need(g.contiguous(), torch.float32, (3,), "grad") for g in grads]
+    arr = (DtBatchEntry * len(items))(*[it.entry(grad_out=g, dV=o[0], dior=o[1], dsig=o[2])
+                                        for it, g, o in zip(items, grads, outs)])
+    _check(lib.dt_render_batch_backward(arr, len(items), _ptr(tape.ws.buf), tape.ws.bytes, _ptr(bws), bws.numel(),
+                                        max_level, _stream(stream)))
+    return outs
 
 
 # ---------------------------------------------------------------------------

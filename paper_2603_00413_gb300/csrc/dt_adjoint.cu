@@ -17,8 +17,6 @@
 
 namespace dt {
 
-void launch_vertex_normals_backward(const float* V, int32_t nv, const int32_t* F, int32_t nf, const float* dN,
-                                    float* dV, cudaStream_t s);
 extern dt_tuning g_tuning;
 
 // backward scratch: two level buffers of (L, obar, dbar) and dN
@@ -33,66 +31,79 @@ struct BwsLayout {
   }
 };
 
-size_t backward_ws_bytes(unsigned long long max_level, int32_t nv) { return BwsLayout(max_level, nv).total; }
-
-struct AdjScene {
-  const float* V;
-  const int32_t* F;
-  const float* N;
-  const float* ior;
-  const float* sigma;
-  const float* env;
-  int env_w, env_h;
-};
-
 __device__ __forceinline__ void atomic_add3(float* p, float3 v) {
   atomicAdd(p, v.x);
   atomicAdd(p + 1, v.y);
   atomicAdd(p + 2, v.z);
 }
 
+// Per-block sums of the IoR and sigma gradients, one slot per scene; a thread
+// adds its running sums when its scene changes and at the end.
+struct SceneSums {
+  float* s;  // shared [n_scenes][4]
+  __device__ __forceinline__ void add(int scene, float ior, float3 sig) {
+    if (scene < 0) return;
+    if (ior != 0.f) atomicAdd(s + 4 * scene, ior);
+    if (sig.x != 0.f) atomicAdd(s + 4 * scene + 1, sig.x);
+    if (sig.y != 0.f) atomicAdd(s + 4 * scene + 2, sig.y);
+    if (sig.z != 0.f) atomicAdd(s + 4 * scene + 3, sig.z);
+  }
+};
+
 // out_next: (L, obar, dbar) of level k+1 indexed by position in that level;
 // out_cur: the same for level k (not written for k = 0: camera rays have no
 // parent).  Each entry is 3 float4 (xyz used).
-__global__ void __launch_bounds__(256) k_adjoint(WsView W, AdjScene S, int k, int spp, uint32_t n_pix,
-                                                 const float* __restrict__ grad_out,
-                                                 const float4* __restrict__ out_next, float4* __restrict__ out_cur,
-                                                 float* __restrict__ dV, float* __restrict__ dN,
-                                                 float* __restrict__ dior, float* __restrict__ dsigma) {
+// kBatch = false: one scene, whose entry E0 arrives as a kernel parameter;
+// true: each segment looks its scene up.
+template <bool kBatch>
+__global__ void __launch_bounds__(256) k_adjoint(WsView W, int k, const float4* __restrict__ out_next,
+                                                 float4* __restrict__ out_cur, const SceneEntry E0) {
+  extern __shared__ float sums_smem[];
   const WsHeader* H = W.hdr;
+  const int n_scenes = kBatch ? W.th->n : 1;
+  for (int i = threadIdx.x; i < 4 * n_scenes; i += blockDim.x) sums_smem[i] = 0.f;
+  __syncthreads();
+  SceneSums sums{sums_smem};
   const uint32_t n = level_size(H, k);
   const uint32_t start = H->level_start[k];
   const uint32_t next_start = H->level_start[k + 1];
   const uint32_t n_next = level_size(H, k + 1);
-  const float ior = __ldg(S.ior);
-  const float3 sigma = mk(__ldg(S.sigma), __ldg(S.sigma + 1), __ldg(S.sigma + 2));
-  const float inv_spp = 1.0f / (float)spp;
+  int cur = -1;
   float acc_ior = 0.f;
   float3 acc_sig = mk(0.f, 0.f, 0.f);
   const uint32_t stride = gridDim.x * blockDim.x;
-  const uint32_t nloop = (n + 31u) & ~31u;  // whole warps, for the reductions at the end
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nloop; i += stride) {
-    if (i >= n) continue;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const uint32_t a = start + i;
     const float4 ro = W.ray_o[a], rd = W.ray_d[a], rw = W.ray_w[a], hh = W.hit[a];
     const uint32_t fl = W.sflag[a];
-    const uint32_t pix = __float_as_uint(ro.w) / (uint32_t)spp;
+    const uint32_t sample = __float_as_uint(ro.w);
+    const int sc = kBatch ? find_scene(W.th->starts, n_scenes, sample) : 0;
+    const SceneEntry& E = kBatch ? W.ent[sc] : E0;
+    if (sc != cur) {
+      sums.add(cur, acc_ior, acc_sig);
+      cur = sc;
+      acc_ior = 0.f;
+      acc_sig = mk(0.f, 0.f, 0.f);
+    }
+    const uint32_t pix = (sample - E.sample_start) / (uint32_t)E.spp;
     float3 L = mk(0.f, 0.f, 0.f), obar = L, dbar = L;
-    if (pix < n_pix) {
-      const float3 g = mk(__ldg(grad_out + 3 * (size_t)pix), __ldg(grad_out + 3 * (size_t)pix + 1),
-                          __ldg(grad_out + 3 * (size_t)pix + 2));
-      const float3 gbar = mul(g, mk(rw.x, rw.y, rw.z)) * inv_spp;
+    if (sample >= E.sample_start && pix < E.pix_count) {
+      const float3 g = mk(__ldg(E.grad_out + 3 * (size_t)pix), __ldg(E.grad_out + 3 * (size_t)pix + 1),
+                          __ldg(E.grad_out + 3 * (size_t)pix + 2));
+      const float3 gbar = mul(g, mk(rw.x, rw.y, rw.z)) * (1.0f / (float)E.spp);
       const float3 o = xyz(ro), d = xyz(rd);
       const int32_t ch = W.child[a];
       if (fl & SF_MISS) {
-        L = env_lookup(S.env, S.env_w, S.env_h, d);
-        dbar = env_grad_dir(S.env, S.env_w, S.env_h, d, gbar);
+        L = env_lookup(E.env, E.env_w, E.env_h, d);
+        dbar = env_grad_dir(E.env, E.env_w, E.env_h, d, gbar);
       } else if (!(fl & (SF_DISCARDED | SF_BACKFACING)) && ch >= 0) {
         const int tri = __float_as_int(hh.w);
         const float t = hh.x, b1 = hh.y, b2 = hh.z, b0 = 1.0f - b1 - b2;
-        const int i0 = __ldg(S.F + 3 * tri), i1 = __ldg(S.F + 3 * tri + 1), i2 = __ldg(S.F + 3 * tri + 2);
-        const float3 v0 = load3(S.V + 3 * i0), v1 = load3(S.V + 3 * i1), v2 = load3(S.V + 3 * i2);
-        const float3 N0 = load3(S.N + 3 * i0), N1 = load3(S.N + 3 * i1), N2 = load3(S.N + 3 * i2);
+        const int i0 = __ldg(E.F + 3 * tri), i1 = __ldg(E.F + 3 * tri + 1), i2 = __ldg(E.F + 3 * tri + 2);
+        const float3 v0 = load3(E.V + 3 * i0), v1 = load3(E.V + 3 * i1), v2 = load3(E.V + 3 * i2);
+        const float3 N0 = load3(E.N + 3 * i0), N1 = load3(E.N + 3 * i1), N2 = load3(E.N + 3 * i2);
+        const float ior = __ldg(E.ior);
+        const float3 sigma = mk(__ldg(E.sigma), __ldg(E.sigma + 1), __ldg(E.sigma + 2));
         const bool tir = (fl & SF_TIR) != 0;
         HitShade h;
         shade_hit(o, d, t, b1, b2, v0, v1, v2, N0, N1, N2, ior, sigma, h, tir ? 1 : 0);
@@ -167,9 +178,9 @@ __global__ void __launch_bounds__(256) k_adjoint(WsView W, AdjScene S, int k, in
         const float3 nbar = h.entering ? nsbar : -nsbar;
         const float3 mbar = (nbar - h.n * dot(h.n, nbar)) * (1.0f / h.lm);
         // m = b0 N0 + b1 N1 + b2 N2
-        atomic_add3(dN + 3 * i0, mbar * b0);
-        atomic_add3(dN + 3 * i1, mbar * b1);
-        atomic_add3(dN + 3 * i2, mbar * b2);
+        atomic_add3(E.dN + 3 * i0, mbar * b0);
+        atomic_add3(E.dN + 3 * i1, mbar * b1);
+        atomic_add3(E.dN + 3 * i2, mbar * b2);
         const float b0b = dot(N0, mbar);
         const float b1b = dot(N1, mbar) - b0b;
         const float b2b = dot(N2, mbar) - b0b;
@@ -187,9 +198,9 @@ __global__ void __launch_bounds__(256) k_adjoint(WsView W, AdjScene S, int k, in
                                       : mk(0.f, 0.f, 0.f);
         obar = obar + lam;
         dbar = dbar + lam * t;
-        atomic_add3(dV + 3 * i0, lam * (-b0));
-        atomic_add3(dV + 3 * i1, lam * (-b1));
-        atomic_add3(dV + 3 * i2, lam * (-b2));
+        atomic_add3(E.dV + 3 * i0, lam * (-b0));
+        atomic_add3(E.dV + 3 * i1, lam * (-b1));
+        atomic_add3(E.dV + 3 * i2, lam * (-b2));
       }
     }
     if (k > 0) {
@@ -198,15 +209,35 @@ __global__ void __launch_bounds__(256) k_adjoint(WsView W, AdjScene S, int k, in
       out_cur[3 * i + 2] = make_float4(dbar.x, dbar.y, dbar.z, 0.f);
     }
   }
-  // one atomic per warp for the scalar parameters
-  const float si = warp_sum(acc_ior);
-  const float sx = warp_sum(acc_sig.x), sy = warp_sum(acc_sig.y), sz = warp_sum(acc_sig.z);
-  if ((threadIdx.x & 31) == 0) {
-    if (si != 0.f) atomicAdd(dior, si);
-    if (sx != 0.f) atomicAdd(dsigma, sx);
-    if (sy != 0.f) atomicAdd(dsigma + 1, sy);
-    if (sz != 0.f) atomicAdd(dsigma + 2, sz);
+  sums.add(cur, acc_ior, acc_sig);
+  __syncthreads();
+  for (int sc = threadIdx.x; sc < n_scenes; sc += blockDim.x) {
+    const SceneEntry& E = kBatch ? W.ent[sc] : E0;
+    if (sums_smem[4 * sc] != 0.f) atomicAdd(E.dior, sums_smem[4 * sc]);
+    for (int c = 0; c < 3; ++c)
+      if (sums_smem[4 * sc + 1 + c] != 0.f) atomicAdd(E.dsigma + c, sums_smem[4 * sc + 1 + c]);
   }
+}
+
+// zero every scene's dV, dN, dIoR, dsigma (blockIdx.y = scene)
+__global__ void k_zero_grads(const SceneEntry* __restrict__ ent) {
+  const SceneEntry& E = ent[blockIdx.y];
+  const size_t n = 3 * (size_t)E.nv;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    E.dV[i] = 0.f;
+    E.dN[i] = 0.f;
+  }
+  if (blockIdx.x == 0 && threadIdx.x < 4) {
+    if (threadIdx.x == 0) E.dior[0] = 0.f;
+    else E.dsigma[threadIdx.x - 1] = 0.f;
+  }
+}
+
+// Eq. 13 backward for every scene (blockIdx.y = scene): dN -> dV.
+__global__ void k_face_normals_backward_table(const SceneEntry* __restrict__ ent) {
+  const SceneEntry& E = ent[blockIdx.y];
+  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < E.nf; f += gridDim.x * blockDim.x)
+    face_normal_backward_one(E.V, E.F, f, E.dN, E.dV);
 }
 
 // L2 seed: grad = 2 scale (img - target); loss = scale sum (img - target)^2
@@ -232,27 +263,60 @@ void launch_l2_loss_grad(const float* img, const float* target, int64_t n, float
   k_l2_loss_grad<<<(int)b, 256, 0, s>>>(img, target, n, scale, grad, loss);
 }
 
-void launch_backward(const dt_scene& sc, const dt_views& vw, const dt_params& p, const void* ws,
-                     unsigned long long cap, const float* grad_out, float* dV, float* dior, float* dsigma, void* bws,
-                     unsigned long long max_level, cudaStream_t s) {
+void launch_write_table(const WsView& W, const TableHeader& th, const SceneEntry* entries, int n, cudaStream_t s);
+
+// Backward of a table of scenes over the tape in ws: rewrites the table with
+// the gradient pointers, zeroes the gradients, sweeps k = D..0, then the
+// vertex-normal adjoint of every scene.
+void launch_backward_table(const TableHeader& th, const SceneEntry* entries, const void* ws, unsigned long long cap,
+                           void* bws, unsigned long long max_level, cudaStream_t s) {
   WsView W = ws_view(ws, cap);
-  BwsLayout L(max_level, sc.nv);
+  BwsLayout L(max_level, 0);
   char* b = (char*)bws;
   float4* buf[2] = {(float4*)(b + L.off_buf0), (float4*)(b + L.off_buf1)};
-  float* dN = (float*)(b + L.off_dN);
-  cudaMemsetAsync(dN, 0, sizeof(float) * 3 * (size_t)sc.nv, s);
-  cudaMemsetAsync(dV, 0, sizeof(float) * 3 * (size_t)sc.nv, s);
-  cudaMemsetAsync(dior, 0, sizeof(float), s);
-  cudaMemsetAsync(dsigma, 0, sizeof(float) * 3, s);
-  AdjScene S{sc.d_V, sc.d_F, sc.d_N, sc.d_ior, sc.d_sigma, sc.d_env, sc.env_w, sc.env_h};
-  const uint32_t n_pix = (uint32_t)vw.n_views * vw.width * vw.height;
-  const int blocks = g_tuning.shade_blocks_per_sm * num_sms();
-  for (int k = p.max_depth; k >= 0; --k) {
-    ProfScope ps("k_adjoint", s);
-    k_adjoint<<<blocks, 256, 0, s>>>(W, S, k, p.spp, n_pix, grad_out, buf[(k + 1) & 1], buf[k & 1], dV, dN, dior,
-                                     dsigma);
+  const int n = th.n;
+  launch_write_table(W, th, entries, n, s);
+  int max_nv = 1, max_nf = 1;
+  for (int i = 0; i < n; ++i) {
+    if (entries[i].nv > max_nv) max_nv = entries[i].nv;
+    if (entries[i].nf > max_nf) max_nf = entries[i].nf;
   }
-  launch_vertex_normals_backward(sc.d_V, sc.nv, sc.d_F, sc.nf, dN, dV, s);
+  const int cap_blocks = 4 * num_sms();
+  int zb = (3 * max_nv + 255) / 256;
+  if (zb > cap_blocks) zb = cap_blocks;
+  {
+    ProfScope ps("k_zero_grads", s);
+    k_zero_grads<<<dim3(zb, n), 256, 0, s>>>(W.ent);
+  }
+  const int blocks = g_tuning.shade_blocks_per_sm * num_sms();
+  const size_t smem = sizeof(float) * 4 * (size_t)n;
+  for (int k = th.max_depth; k >= 0; --k) {
+    ProfScope ps("k_adjoint", s);
+    if (n > 1) k_adjoint<true><<<blocks, 256, smem, s>>>(W, k, buf[(k + 1) & 1], buf[k & 1], entries[0]);
+    else k_adjoint<false><<<blocks, 256, smem, s>>>(W, k, buf[(k + 1) & 1], buf[k & 1], entries[0]);
+  }
+  int fb = (max_nf + 255) / 256;
+  if (fb > cap_blocks) fb = cap_blocks;
+  ProfScope ps("k_face_normals_backward", s);
+  k_face_normals_backward_table<<<dim3(fb, n), 256, 0, s>>>(W.ent);
+}
+
+// The backward scratch of a table: the two level buffers, then every
+// scene's dN.  Fills the entries' dN pointers.
+size_t backward_ws_bytes_table(unsigned long long max_level, const SceneEntry* entries, int n) {
+  BwsLayout L(max_level, 0);
+  size_t o = L.off_dN;
+  for (int i = 0; i < n; ++i) o = align_up(o + (size_t)entries[i].nv * 3 * sizeof(float), 256);
+  return o;
+}
+
+void assign_dN(SceneEntry* entries, int n, void* bws, unsigned long long max_level) {
+  BwsLayout L(max_level, 0);
+  size_t o = L.off_dN;
+  for (int i = 0; i < n; ++i) {
+    entries[i].dN = (float*)((char*)bws + o);
+    o = align_up(o + (size_t)entries[i].nv * 3 * sizeof(float), 256);
+  }
 }
 
 }  // namespace dt

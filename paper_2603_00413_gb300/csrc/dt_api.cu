@@ -11,6 +11,8 @@
 #include <string>
 #include <vector>
 
+#include <string.h>
+
 #include "dt_internal.cuh"
 
 namespace dt {
@@ -24,8 +26,14 @@ void launch_vertex_normals_backward(const float* V, int32_t nv, const int32_t* F
 size_t bvh_scratch_bytes(int32_t nf);
 void launch_build(const float* V, const int32_t* F, int32_t nf, void* bvh, void* scratch, cudaStream_t s);
 void launch_refit(const float* V, const int32_t* F, int32_t nf, void* bvh, void* scratch, cudaStream_t s);
-void launch_forward(const dt_scene& sc, const dt_views& vw, const dt_params& p, float* out, void* ws,
-                    unsigned long long cap, cudaStream_t s);
+SceneEntry make_entry(const dt_scene& sc, const dt_views& vw, const dt_params& p, float* out);
+void finish_table(SceneEntry* entries, int n, TableHeader& th);
+void launch_forward_table(const TableHeader& th, const SceneEntry* entries, void* ws, unsigned long long cap,
+                          cudaStream_t s);
+void launch_backward_table(const TableHeader& th, const SceneEntry* entries, const void* ws, unsigned long long cap,
+                           void* bws, unsigned long long max_level, cudaStream_t s);
+size_t backward_ws_bytes_table(unsigned long long max_level, const SceneEntry* entries, int n);
+void assign_dN(SceneEntry* entries, int n, void* bws, unsigned long long max_level);
 void launch_dump(const void* ws, unsigned long long cap, int32_t* si, float* sf, unsigned long long n,
                  cudaStream_t s);
 void launch_closest_hit(const void* bvh, int32_t nf, const float* o, const float* d, const int32_t* src, int32_t n,
@@ -112,7 +120,8 @@ ProfScope::~ProfScope() {
 // the largest segment capacity whose layout fits in ws_bytes
 static unsigned long long cap_from_bytes(size_t ws_bytes) {
   if (ws_bytes < 4096) return 0;
-  unsigned long long cap = (ws_bytes - 1024) / 72;
+  if (ws_bytes < 1024 + kTableBytes + 4096) return 0;
+  unsigned long long cap = (ws_bytes - 1024 - kTableBytes) / 72;
   if (cap > 0x7fffffffull) cap = 0x7fffffffull;
   while (cap > 0 && WsLayout(cap).total > ws_bytes) --cap;
   return cap;
@@ -213,16 +222,59 @@ dt_status dt_render_workspace_size(int64_t seg_capacity, size_t* ws_bytes) {
 
 dt_status dt_render(const dt_scene* scene, const dt_views* views, const dt_params* params, float* d_out, void* d_ws,
                     size_t ws_bytes, dt_stream stream) {
-  dt_status st = check_scene(scene);
+  if (!scene || !views || !params) return set_error(DT_ERR_INVALID_ARG, "scene, views or params is NULL");
+  dt_batch_entry e;
+  memset(&e, 0, sizeof(e));
+  e.scene = *scene;
+  e.views = *views;
+  e.params = *params;
+  e.d_out = d_out;
+  return dt_render_batch(&e, 1, d_ws, ws_bytes, stream);
+}
+
+static dt_status check_entries(const dt_batch_entry* entries, int32_t n, bool backward,
+                               std::vector<SceneEntry>& out, TableHeader& th) {
+  if (!entries) return set_error(DT_ERR_INVALID_ARG, "entries is NULL");
+  if (n < 1 || n > kMaxBatch) return set_error(DT_ERR_INVALID_ARG, "batch size must be in [1, %d] (got %d)", kMaxBatch, n);
+  out.resize(n);
+  unsigned long long total = 0;
+  for (int i = 0; i < n; ++i) {
+    const dt_batch_entry& e = entries[i];
+    dt_status st = check_scene(&e.scene);
+    if (st == DT_OK) st = check_views_params(&e.views, &e.params);
+    if (st != DT_OK) {
+      char msg[sizeof(g_err)];
+      strncpy(msg, g_err, sizeof(msg) - 1);
+      msg[sizeof(msg) - 1] = 0;
+      return set_error(st, "entry %d: %s", i, msg);
+    }
+    if (!backward && !e.d_out) return set_error(DT_ERR_INVALID_ARG, "entry %d: d_out is NULL", i);
+    if (backward && (!e.d_grad_out || !e.d_grad_V || !e.d_grad_ior || !e.d_grad_sigma))
+      return set_error(DT_ERR_INVALID_ARG, "entry %d: a gradient pointer is NULL", i);
+    out[i] = make_entry(e.scene, e.views, e.params, e.d_out);
+    out[i].grad_out = e.d_grad_out;
+    out[i].dV = e.d_grad_V;
+    out[i].dior = e.d_grad_ior;
+    out[i].dsigma = e.d_grad_sigma;
+    total += (unsigned long long)out[i].pix_count * (unsigned long long)e.params.spp;
+  }
+  if (total >= 0xffffffffull) return set_error(DT_ERR_INVALID_ARG, "too many primary rays in one call (%llu)", total);
+  finish_table(out.data(), n, th);
+  return DT_OK;
+}
+
+dt_status dt_render_batch(const dt_batch_entry* entries, int32_t n, void* d_ws, size_t ws_bytes, dt_stream stream) {
+  std::vector<SceneEntry> ent;
+  TableHeader th;
+  dt_status st = check_entries(entries, n, false, ent, th);
   if (st) return st;
-  if ((st = check_views_params(views, params))) return st;
-  if (!d_out || !d_ws) return set_error(DT_ERR_INVALID_ARG, "NULL output or workspace");
+  if (!d_ws) return set_error(DT_ERR_INVALID_ARG, "workspace is NULL");
   if (!aligned(d_ws, 256)) return set_error(DT_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
   const unsigned long long cap = cap_from_bytes(ws_bytes);
-  const unsigned long long n0 = (unsigned long long)views->n_views * views->width * views->height * params->spp;
-  if (cap < n0)
-    return set_error(DT_ERR_INVALID_ARG, "workspace holds %llu segments, fewer than the %llu camera rays", cap, n0);
-  launch_forward(*scene, *views, *params, d_out, d_ws, cap, (cudaStream_t)stream);
+  if (cap < th.n_samples)
+    return set_error(DT_ERR_INVALID_ARG, "workspace holds %llu segments, fewer than the %u camera rays", cap,
+                     th.n_samples);
+  launch_forward_table(th, ent.data(), d_ws, cap, (cudaStream_t)stream);
   return check_launch("dt_render");
 }
 
@@ -266,28 +318,58 @@ dt_status dt_read_stats(const void* d_ws, size_t ws_bytes, dt_stats* out, dt_str
 
 dt_status dt_backward_workspace_size(int64_t max_level, int32_t nv, size_t* bytes) {
   if (max_level < 1 || nv < 1 || !bytes) return set_error(DT_ERR_INVALID_ARG, "need max_level >= 1, nv >= 1");
-  *bytes = backward_ws_bytes((unsigned long long)max_level, nv);
+  SceneEntry e;
+  memset(&e, 0, sizeof(e));
+  e.nv = nv;
+  *bytes = backward_ws_bytes_table((unsigned long long)max_level, &e, 1);
   return DT_OK;
+}
+
+dt_status dt_batch_backward_workspace_size(const dt_batch_entry* entries, int32_t n, int64_t max_level,
+                                           size_t* bytes) {
+  if (!entries || n < 1 || n > kMaxBatch || max_level < 1 || !bytes) return set_error(DT_ERR_INVALID_ARG, "bad argument");
+  std::vector<SceneEntry> e(n);
+  for (int i = 0; i < n; ++i) {
+    memset(&e[i], 0, sizeof(SceneEntry));
+    e[i].nv = entries[i].scene.nv;
+  }
+  *bytes = backward_ws_bytes_table((unsigned long long)max_level, e.data(), n);
+  return DT_OK;
+}
+
+dt_status dt_render_batch_backward(const dt_batch_entry* entries, int32_t n, const void* d_ws, size_t ws_bytes,
+                                   void* d_bws, size_t bws_bytes, int64_t max_level, dt_stream stream) {
+  std::vector<SceneEntry> ent;
+  TableHeader th;
+  dt_status st = check_entries(entries, n, true, ent, th);
+  if (st) return st;
+  if (!d_ws || !d_bws) return set_error(DT_ERR_INVALID_ARG, "NULL workspace");
+  const unsigned long long cap = cap_from_bytes(ws_bytes);
+  if (cap == 0) return set_error(DT_ERR_INVALID_ARG, "workspace too small");
+  if (max_level < 1) return set_error(DT_ERR_INVALID_ARG, "max_level must be >= 1");
+  if (bws_bytes < backward_ws_bytes_table((unsigned long long)max_level, ent.data(), n))
+    return set_error(DT_ERR_INVALID_ARG, "backward workspace smaller than its size query");
+  if (!aligned(d_bws, 256)) return set_error(DT_ERR_INVALID_ARG, "backward workspace must be 256-byte aligned");
+  assign_dN(ent.data(), n, d_bws, (unsigned long long)max_level);
+  launch_backward_table(th, ent.data(), d_ws, cap, d_bws, (unsigned long long)max_level, (cudaStream_t)stream);
+  return check_launch("dt_render_backward");
 }
 
 dt_status dt_render_backward(const dt_scene* scene, const dt_views* views, const dt_params* params, const void* d_ws,
                              size_t ws_bytes, const float* d_grad_out, float* d_grad_V, float* d_grad_ior,
                              float* d_grad_sigma, void* d_bws, size_t bws_bytes, int64_t max_level,
                              dt_stream stream) {
-  dt_status st = check_scene(scene);
-  if (st) return st;
-  if ((st = check_views_params(views, params))) return st;
-  if (!d_ws || !d_grad_out || !d_grad_V || !d_grad_ior || !d_grad_sigma || !d_bws)
-    return set_error(DT_ERR_INVALID_ARG, "NULL pointer");
-  const unsigned long long cap = cap_from_bytes(ws_bytes);
-  if (cap == 0) return set_error(DT_ERR_INVALID_ARG, "workspace too small");
-  if (max_level < 1) return set_error(DT_ERR_INVALID_ARG, "max_level must be >= 1");
-  if (bws_bytes < backward_ws_bytes((unsigned long long)max_level, scene->nv))
-    return set_error(DT_ERR_INVALID_ARG, "backward workspace smaller than dt_backward_workspace_size");
-  if (!aligned(d_bws, 256)) return set_error(DT_ERR_INVALID_ARG, "backward workspace must be 256-byte aligned");
-  launch_backward(*scene, *views, *params, d_ws, cap, d_grad_out, d_grad_V, d_grad_ior, d_grad_sigma, d_bws,
-                  (unsigned long long)max_level, (cudaStream_t)stream);
-  return check_launch("dt_render_backward");
+  if (!scene || !views || !params) return set_error(DT_ERR_INVALID_ARG, "scene, views or params is NULL");
+  dt_batch_entry e;
+  memset(&e, 0, sizeof(e));
+  e.scene = *scene;
+  e.views = *views;
+  e.params = *params;
+  e.d_grad_out = d_grad_out;
+  e.d_grad_V = d_grad_V;
+  e.d_grad_ior = d_grad_ior;
+  e.d_grad_sigma = d_grad_sigma;
+  return dt_render_batch_backward(&e, 1, d_ws, ws_bytes, d_bws, bws_bytes, max_level, stream);
 }
 
 dt_status dt_dump_segments(const void* d_ws, size_t ws_bytes, int32_t* d_seg_i, float* d_seg_f, int64_t cap,

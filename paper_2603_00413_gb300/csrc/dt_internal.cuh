@@ -155,8 +155,72 @@ struct WsHeader {
 
 enum { CNT_HITS = 0, CNT_MISSES, CNT_DISCARDED, CNT_BACKFACING, CNT_TIR, CNT_NODES, CNT_TRIS };
 
+// ---------------------------------------------------------------------------
+// Scene table: every render (one scene or a batch) reads its scenes from a
+// table in the workspace, written by a kernel whose parameters carry the
+// entries.  Segments find their scene by binary search of their sample index
+// in starts[] (faces by face_starts[] for the per-face kernels).
+// ---------------------------------------------------------------------------
+constexpr int kMaxBatch = 256;
+constexpr int kEntriesPerChunk = 24;  // table entries per writing launch (kernel-parameter space)
+
+struct SceneEntry {
+  const float* V;
+  const int32_t* F;
+  const float* N;
+  const float* ior;
+  const float* sigma;
+  const float* env;
+  const float4* node2;
+  const float4* node4;
+  const float4* tris;
+  const BvhHeader* bh;
+  const float* cams;
+  float* out;
+  const float* grad_out;  // backward only
+  float* dV;
+  float* dior;
+  float* dsigma;
+  float* dN;
+  unsigned long long seed;
+  int32_t nv, nf, env_w, env_h;
+  int32_t n_views, width, height, spp;
+  int32_t max_depth, jitter, max_iter, pad0;
+  float t_min;
+  uint32_t sample_start, face_start, pix_count;
+};
+
+struct TableHeader {
+  int32_t n;
+  int32_t max_depth;
+  uint32_t n_samples;
+  uint32_t n_faces;
+  uint32_t starts[kMaxBatch + 1];
+  uint32_t face_starts[kMaxBatch + 1];
+};
+
+struct TableView {
+  const TableHeader* th;
+  const SceneEntry* e;
+};
+
+constexpr size_t kTableBytes =
+    ((sizeof(TableHeader) + 255) / 256) * 256 + ((kMaxBatch * sizeof(SceneEntry) + 255) / 256) * 256;
+
+// index i with starts[i] <= x < starts[i+1] (n >= 1)
+__device__ __forceinline__ int find_scene(const uint32_t* starts, int n, uint32_t x) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(starts + mid) <= x) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
 struct WsView {
   WsHeader* hdr;
+  TableHeader* th;
+  SceneEntry* ent;
   float4* ray_o;
   float4* ray_d;
   float4* ray_w;
@@ -167,9 +231,10 @@ struct WsView {
 };
 
 struct WsLayout {
-  size_t off_o, off_d, off_w, off_hit, off_child, off_flag, total;
+  size_t off_table, off_o, off_d, off_w, off_hit, off_child, off_flag, total;
   __host__ __device__ explicit WsLayout(unsigned long long cap) {
-    off_o = 1024;
+    off_table = 1024;
+    off_o = off_table + kTableBytes;
     off_d = align_up(off_o + cap * sizeof(float4), 256);
     off_w = align_up(off_d + cap * sizeof(float4), 256);
     off_hit = align_up(off_w + cap * sizeof(float4), 256);
@@ -183,7 +248,9 @@ static_assert(sizeof(WsHeader) <= 1024, "header must fit its slot");
 __host__ __device__ inline WsView ws_view(const void* base, unsigned long long cap) {
   WsLayout L(cap);
   char* b = (char*)base;
-  return WsView{(WsHeader*)b, (float4*)(b + L.off_o), (float4*)(b + L.off_d), (float4*)(b + L.off_w),
+  TableHeader* th = (TableHeader*)(b + L.off_table);
+  SceneEntry* ent = (SceneEntry*)(b + L.off_table + ((sizeof(TableHeader) + 255) / 256) * 256);
+  return WsView{(WsHeader*)b, th, ent, (float4*)(b + L.off_o), (float4*)(b + L.off_d), (float4*)(b + L.off_w),
                 (float4*)(b + L.off_hit), (int32_t*)(b + L.off_child), (uint32_t*)(b + L.off_flag), cap};
 }
 

@@ -145,4 +145,25 @@ __device__ __forceinline__ void shade_hit(float3 o, float3 d, float t, float b1,
   }
 }
 
+// Backward of Eq. 13 for face f.  Its unit normal u = c/|c|, c = e1 x e2,
+// feeds (1/3) u to each of its vertices, so du = (1/3)(dN_v0 + dN_v1 +
+// dN_v2); dc = (du - u (u.du)) / |c|; c = e1 x e2 gives de1 = e2 x dc,
+// de2 = dc x e1; then dv1 += de1, dv2 += de2, dv0 -= de1 + de2 (atomics).
+__device__ __forceinline__ void face_normal_backward_one(const float* __restrict__ V, const int32_t* __restrict__ F,
+                                                         int f, const float* __restrict__ dN, float* __restrict__ dV) {
+  const int i0 = F[3 * f], i1 = F[3 * f + 1], i2 = F[3 * f + 2];
+  const float3 v0 = load3(V + 3 * i0), v1 = load3(V + 3 * i1), v2 = load3(V + 3 * i2);
+  const float3 e1 = v1 - v0, e2 = v2 - v0;
+  const float3 c = cross(e1, e2);
+  const float lc = len(c);
+  const float3 u = mk(c.x / lc, c.y / lc, c.z / lc);
+  const float3 du = (load3(dN + 3 * i0) + load3(dN + 3 * i1) + load3(dN + 3 * i2)) * (1.0f / 3.0f);
+  const float3 dc = (du - u * dot(u, du)) * (1.0f / lc);
+  const float3 de1 = cross(e2, dc), de2 = cross(dc, e1);
+  const float3 dv0 = -(de1 + de2);
+  atomicAdd(dV + 3 * i0 + 0, dv0.x); atomicAdd(dV + 3 * i0 + 1, dv0.y); atomicAdd(dV + 3 * i0 + 2, dv0.z);
+  atomicAdd(dV + 3 * i1 + 0, de1.x); atomicAdd(dV + 3 * i1 + 1, de1.y); atomicAdd(dV + 3 * i1 + 2, de1.z);
+  atomicAdd(dV + 3 * i2 + 0, de2.x); atomicAdd(dV + 3 * i2 + 1, de2.y); atomicAdd(dV + 3 * i2 + 2, de2.z);
+}
+
 }  // namespace dt

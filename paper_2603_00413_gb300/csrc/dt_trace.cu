@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string.h>
+
 #include "dt_internal.cuh"
 #include "dt_shade.cuh"
 
@@ -40,25 +42,56 @@ __device__ __forceinline__ void camera_ray(const float* cam, int width, int heig
   d = normalize(fwd + r * px + u * py);
 }
 
-__global__ void k_camera(WsView W, const float* __restrict__ cams, int n_views, int width, int height, int spp,
-                         int jitter, uint64_t seed, unsigned long long capacity, int max_depth) {
-  const uint32_t npix = (uint32_t)width * (uint32_t)height;
-  const uint32_t n0 = (uint32_t)n_views * npix * (uint32_t)spp;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    W.hdr->capacity = capacity;
-    W.hdr->level_count[0] = n0;
-    W.hdr->level_start[0] = 0;
-    W.hdr->n_views = n_views; W.hdr->width = width; W.hdr->height = height;
-    W.hdr->spp = spp; W.hdr->max_depth = max_depth;
+// Scene table: the header and the entries arrive as kernel parameters (no
+// host memcpy, so the writes are ordered on the stream and can be captured in
+// a graph) and are copied into the workspace.
+struct TableChunk {
+  int32_t first, count;
+  SceneEntry e[kEntriesPerChunk];
+};
+
+__global__ void k_write_table_header(TableHeader* dst, const TableHeader src) {
+  const uint32_t* a = reinterpret_cast<const uint32_t*>(&src);
+  uint32_t* b = reinterpret_cast<uint32_t*>(dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(TableHeader) / 4); i += blockDim.x) b[i] = a[i];
+}
+
+__global__ void k_write_table_entries(SceneEntry* dst, const TableChunk src) {
+  const int words = (int)(sizeof(SceneEntry) / 4);
+  for (int i = threadIdx.x; i < src.count * words; i += blockDim.x) {
+    const int k = i / words, w = i % words;
+    reinterpret_cast<uint32_t*>(dst + src.first + k)[w] = reinterpret_cast<const uint32_t*>(&src.e[k])[w];
   }
-  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < n0; g += gridDim.x * blockDim.x) {
-    const uint32_t s = g % (uint32_t)spp;
-    const uint32_t gp = g / (uint32_t)spp;
+}
+
+// zero every scene's image (blockIdx.y = scene)
+__global__ void k_zero_images(const SceneEntry* __restrict__ ent) {
+  const SceneEntry& E = ent[blockIdx.y];
+  const size_t n = (size_t)E.pix_count * 3;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    E.out[i] = 0.0f;
+}
+
+// Camera rays of every scene into level 0 (blockIdx.y = scene).  Sample
+// index g = sample_start + (view * H * W + py * W + px) * spp + s.
+__global__ void k_camera(WsView W, unsigned long long capacity) {
+  const SceneEntry& E = W.ent[blockIdx.y];
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+    W.hdr->capacity = capacity;
+    W.hdr->level_count[0] = W.th->n_samples;
+    W.hdr->level_start[0] = 0;
+  }
+  const uint32_t npix = (uint32_t)E.width * (uint32_t)E.height;
+  const uint32_t n0 = E.pix_count * (uint32_t)E.spp;
+  for (uint32_t l = blockIdx.x * blockDim.x + threadIdx.x; l < n0; l += gridDim.x * blockDim.x) {
+    const uint32_t s = l % (uint32_t)E.spp;
+    const uint32_t gp = l / (uint32_t)E.spp;
     const uint32_t view = gp / npix, p = gp % npix;
     float jx = 0.5f, jy = 0.5f;
-    if (jitter) jitter_offset(seed, view, p, s, jx, jy);
+    if (E.jitter) jitter_offset(E.seed, view, p, s, jx, jy);
     float3 o, d;
-    camera_ray(cams + 10 * view, width, height, (float)(p % width) + jx, (float)(p / width) + jy, o, d);
+    camera_ray(E.cams + 10 * view, E.width, E.height, (float)(p % E.width) + jx, (float)(p / E.width) + jy, o, d);
+    const uint32_t g = E.sample_start + l;
     W.ray_o[g] = make_float4(o.x, o.y, o.z, __uint_as_float(g));
     W.ray_d[g] = make_float4(d.x, d.y, d.z, __uint_as_float(1u));
     W.ray_w[g] = make_float4(1.f, 1.f, 1.f, __int_as_float(-1));
@@ -227,15 +260,13 @@ __device__ __forceinline__ ClosestHit closest_hit(const float4* __restrict__ nod
 // warp therefore no longer waits for the slowest ray of a fixed batch of 32
 // (the divergence that left most lanes idle), and stops when the level is
 // exhausted and its last ray is done.
-template <int kMinBlocks, int kWidth>
-__global__ void __launch_bounds__(256, kMinBlocks) k_trace(WsView W, const float4* __restrict__ nodes,
-                                                           const float4* __restrict__ tris, const BvhHeader* bh,
-                                                           int k, float tmin, int max_iter, int steps, int refill) {
+// kBatch = false: one scene, whose entry E0 arrives as a kernel parameter
+// (uniform constant-bank reads); true: each ray looks its scene up.
+template <int kMinBlocks, int kWidth, bool kBatch>
+__global__ void __launch_bounds__(256, kMinBlocks) k_trace(WsView W, int k, int steps, int refill,
+                                                           const SceneEntry E0) {
   WsHeader* H = W.hdr;
-  if (bh->corrupt) {  // the build's validation failed: trace nothing
-    if (threadIdx.x == 0) atomicOr(&H->status, ST_STACK_OVERFLOW);
-    return;
-  }
+  const int n_scenes = kBatch ? W.th->n : 1;
   const uint32_t n = level_size(H, k);
   const uint32_t start = H->level_start[k];
   const uint32_t lane = threadIdx.x & 31;
@@ -246,6 +277,10 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_trace(WsView W, const float
   uint32_t a = 0;
   float3 o = mk(0.f, 0.f, 0.f), d = o, idir = o;
   int src = -1, node = 0, sp = 0, iters = 0;
+  int max_iter = kBatch ? 0 : (E0.bh->corrupt ? 0 : E0.max_iter);  // a tree that failed validation is not traced
+  float tmin = E0.t_min;
+  const float4* nodes = kWidth == 4 ? E0.node4 : E0.node2;
+  const float4* tris = E0.tris;
   ClosestHit h{INFINITY, 0.f, 0.f, -1};
   int stack[kTraceStack];
   while (true) {
@@ -261,6 +296,13 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_trace(WsView W, const float
         if (i < n) {
           a = start + i;
           const float4 ro = W.ray_o[a], rd = W.ray_d[a], rw = W.ray_w[a];
+          if (kBatch) {
+            const SceneEntry& E = W.ent[find_scene(W.th->starts, n_scenes, __float_as_uint(ro.w))];
+            nodes = kWidth == 4 ? E.node4 : E.node2;
+            tris = E.tris;
+            max_iter = E.bh->corrupt ? 0 : E.max_iter;
+            tmin = E.t_min;
+          }
           o = xyz(ro);
           d = xyz(rd);
           idir = mk(safe_inv(d.x), safe_inv(d.y), safe_inv(d.z));
@@ -323,20 +365,13 @@ __global__ void k_closest_hit_rays(const float4* __restrict__ nodes, const float
 // ---------------------------------------------------------------------------
 // shading: Sec. 3.4 steps 1-5 for every segment of level k
 // ---------------------------------------------------------------------------
-struct SceneDev {
-  const float* V;
-  const int32_t* F;
-  const float* N;
-  const float* ior;
-  const float* sigma;
-  const float* env;
-  int env_w, env_h;
-};
-
-__global__ void __launch_bounds__(256) k_shade(WsView W, SceneDev S, int k, int max_depth, int spp,
-                                               uint32_t n_pix, float* __restrict__ img) {
-  const float inv_spp = 1.0f / (float)spp;
+// Shading of every segment of level k: Sec. 3.4 steps 1-5 with the
+// segment's own scene (depth limit, materials, environment, image); kBatch
+// as for k_trace.
+template <bool kBatch>
+__global__ void __launch_bounds__(256) k_shade(WsView W, int k, const SceneEntry E0) {
   WsHeader* H = W.hdr;
+  const int n_scenes = kBatch ? W.th->n : 1;
   const uint32_t n = level_size(H, k);
   const uint32_t start = H->level_start[k];
   const uint32_t next_start = start + n;
@@ -344,8 +379,6 @@ __global__ void __launch_bounds__(256) k_shade(WsView W, SceneDev S, int k, int 
     H->level_start[k + 1] = next_start;
     if (n) H->n_levels = (uint32_t)(k + 1);
   }
-  const float ior = __ldg(S.ior);
-  const float3 sigma = mk(__ldg(S.sigma), __ldg(S.sigma + 1), __ldg(S.sigma + 2));
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t warps = gridDim.x * blockDim.x / 32;
   uint32_t c_hit = 0, c_miss = 0, c_disc = 0, c_back = 0, c_tir = 0;
@@ -357,32 +390,37 @@ __global__ void __launch_bounds__(256) k_shade(WsView W, SceneDev S, int k, int 
     float4 co = make_float4(0.f, 0.f, 0.f, 0.f), cdr = co, cwr = co, cdt = co, cwt = co;
     if (i < n) {
       const float4 ro = W.ray_o[a], rd = W.ray_d[a], rw = W.ray_w[a], hh = W.hit[a];
+      const uint32_t sample = __float_as_uint(ro.w);
+      const SceneEntry& E = kBatch ? W.ent[find_scene(W.th->starts, n_scenes, sample)] : E0;
       const int tri = __float_as_int(hh.w);
       const float3 d = xyz(rd);
       uint32_t fl = 0;
       if (tri < 0) {  // step 3: no intersection -> environment
         fl = SF_MISS;
         ++c_miss;
-        const uint32_t pix = __float_as_uint(ro.w) / (uint32_t)spp;
-        if (pix < n_pix) {  // dead records (see below) carry an out-of-range sample index
-          const float3 E = env_lookup(S.env, S.env_w, S.env_h, d);
-          float* dst = img + 3 * (size_t)pix;
-          atomicAdd(dst + 0, rw.x * E.x * inv_spp);
-          atomicAdd(dst + 1, rw.y * E.y * inv_spp);
-          atomicAdd(dst + 2, rw.z * E.z * inv_spp);
+        const uint32_t pix = (sample - E.sample_start) / (uint32_t)E.spp;
+        if (sample >= E.sample_start && pix < E.pix_count) {  // dead records carry an out-of-range sample
+          const float3 Ev = env_lookup(E.env, E.env_w, E.env_h, d);
+          const float inv_spp = 1.0f / (float)E.spp;
+          float* dst = E.out + 3 * (size_t)pix;
+          atomicAdd(dst + 0, rw.x * Ev.x * inv_spp);
+          atomicAdd(dst + 1, rw.y * Ev.y * inv_spp);
+          atomicAdd(dst + 2, rw.z * Ev.z * inv_spp);
         }
       } else {
         ++c_hit;
-        const int i0 = __ldg(S.F + 3 * tri), i1 = __ldg(S.F + 3 * tri + 1), i2 = __ldg(S.F + 3 * tri + 2);
-        const float3 v0 = load3(S.V + 3 * i0), v1 = load3(S.V + 3 * i1), v2 = load3(S.V + 3 * i2);
-        if (k >= max_depth) {  // step 1: the depth limit: contributes nothing
+        const int i0 = __ldg(E.F + 3 * tri), i1 = __ldg(E.F + 3 * tri + 1), i2 = __ldg(E.F + 3 * tri + 2);
+        const float3 v0 = load3(E.V + 3 * i0), v1 = load3(E.V + 3 * i1), v2 = load3(E.V + 3 * i2);
+        if (k >= E.max_depth) {  // step 1: the depth limit: contributes nothing
           const float3 ng = cross(v1 - v0, v2 - v0);
           fl = SF_DISCARDED | (dot(d, ng) < 0.0f ? 0u : SF_INSIDE);
           ++c_disc;
         } else {
+          const float ior = __ldg(E.ior);
+          const float3 sigma = mk(__ldg(E.sigma), __ldg(E.sigma + 1), __ldg(E.sigma + 2));
           HitShade h;
-          shade_hit(xyz(ro), d, hh.x, hh.y, hh.z, v0, v1, v2, load3(S.N + 3 * i0), load3(S.N + 3 * i1),
-                    load3(S.N + 3 * i2), ior, sigma, h);
+          shade_hit(xyz(ro), d, hh.x, hh.y, hh.z, v0, v1, v2, load3(E.N + 3 * i0), load3(E.N + 3 * i1),
+                    load3(E.N + 3 * i2), ior, sigma, h);
           fl = h.entering ? 0u : SF_INSIDE;
           if (h.backfacing) {
             fl |= SF_BACKFACING;
@@ -472,7 +510,6 @@ __global__ void k_dump(WsView W, int32_t* __restrict__ si, float* __restrict__ s
 // ---------------------------------------------------------------------------
 // Launch and scheduling knobs (dt_set_tuning); process-wide.
 dt_tuning g_tuning = {16, 8, 5, 8, 2};
-static int persistent_blocks() { return g_tuning.trace_blocks_per_sm * num_sms(); }
 static int shade_blocks() { return g_tuning.shade_blocks_per_sm * num_sms(); }
 static int n_int_of(int32_t nf) { return nf > 1 ? nf - 1 : 1; }
 
@@ -480,53 +517,117 @@ static int n_int_of(int32_t nf) { return nf > 1 ? nf - 1 : 1; }
 // register budget per thread follows) and for the 2- and 4-wide node
 // formats; the tuning picks the variant and the persistent grid is
 // trace_blocks_per_sm CTAs per SM.
-template <int kWidth, typename... A>
+template <int kWidth, bool kBatch, typename... A>
 static void launch_trace_w(int bps, cudaStream_t s, A... a) {
   const int g = bps * num_sms();
   switch (bps) {
-    case 1: case 2: k_trace<2, kWidth><<<g, 256, 0, s>>>(a...); break;
-    case 3: k_trace<3, kWidth><<<g, 256, 0, s>>>(a...); break;
-    case 4: k_trace<4, kWidth><<<g, 256, 0, s>>>(a...); break;
-    case 5: k_trace<5, kWidth><<<g, 256, 0, s>>>(a...); break;
-    case 6: k_trace<6, kWidth><<<g, 256, 0, s>>>(a...); break;
-    default: k_trace<8, kWidth><<<g, 256, 0, s>>>(a...); break;
+    case 1: case 2: case 3: k_trace<3, kWidth, kBatch><<<g, 256, 0, s>>>(a...); break;
+    case 4: k_trace<4, kWidth, kBatch><<<g, 256, 0, s>>>(a...); break;
+    case 5: k_trace<5, kWidth, kBatch><<<g, 256, 0, s>>>(a...); break;
+    default: k_trace<6, kWidth, kBatch><<<g, 256, 0, s>>>(a...); break;
   }
 }
 static int traversal_limit(int32_t nf) { return 2 * n_int_of(nf) + 8; }
 
-void launch_forward(const dt_scene& sc, const dt_views& vw, const dt_params& p, float* out, void* ws,
-                    unsigned long long cap, cudaStream_t s) {
+// Writes the scene table (header + entries) into the workspace.
+void launch_write_table(const WsView& W, const TableHeader& th, const SceneEntry* entries, int n, cudaStream_t s) {
+  ProfScope ps("k_write_table", s);
+  k_write_table_header<<<1, 256, 0, s>>>(W.th, th);
+  for (int first = 0; first < n; first += kEntriesPerChunk) {
+    TableChunk c;
+    c.first = first;
+    c.count = n - first < kEntriesPerChunk ? n - first : kEntriesPerChunk;
+    for (int k = 0; k < c.count; ++k) c.e[k] = entries[first + k];
+    k_write_table_entries<<<1, 256, 0, s>>>(W.ent, c);
+  }
+}
+
+// Forward of a table of scenes: camera rays of all of them into level 0,
+// then per depth one persistent traversal and one shading pass over the
+// segments of every scene together.
+void launch_forward_table(const TableHeader& th, const SceneEntry* entries, void* ws, unsigned long long cap,
+                          cudaStream_t s) {
   WsView W = ws_view(ws, cap);
+  const int n = th.n;
   cudaMemsetAsync(ws, 0, 1024, s);
-  cudaMemsetAsync(out, 0, sizeof(float) * 3 * (size_t)vw.n_views * vw.width * vw.height, s);
-  const uint64_t n0 = (uint64_t)vw.n_views * vw.width * vw.height * p.spp;
-  int cb = (int)((n0 + 255) / 256);
-  if (cb > 16 * num_sms()) cb = 16 * num_sms();
+  launch_write_table(W, th, entries, n, s);
+  uint32_t max_pix = 0, max_s = 0;
+  for (int i = 0; i < n; ++i) {
+    if (entries[i].pix_count > max_pix) max_pix = entries[i].pix_count;
+    const uint32_t ns = entries[i].pix_count * (uint32_t)entries[i].spp;
+    if (ns > max_s) max_s = ns;
+  }
+  int zb = (int)((3ull * max_pix + 255) / 256);
+  if (zb > 4 * num_sms()) zb = 4 * num_sms();
+  {
+    ProfScope ps("k_zero_images", s);
+    k_zero_images<<<dim3(zb > 0 ? zb : 1, n), 256, 0, s>>>(W.ent);
+  }
+  int cb = (int)((max_s + 255) / 256);
+  if (cb > 4 * num_sms()) cb = 4 * num_sms();
   {
     ProfScope ps("k_camera", s);
-    k_camera<<<cb, 256, 0, s>>>(W, vw.d_cams, vw.n_views, vw.width, vw.height, p.spp, p.jitter, p.seed, cap,
-                                p.max_depth);
+    k_camera<<<dim3(cb > 0 ? cb : 1, n), 256, 0, s>>>(W, cap);
   }
-  BvhView B = bvh_view(sc.d_bvh, sc.nf);
-  SceneDev S{sc.d_V, sc.d_F, sc.d_N, sc.d_ior, sc.d_sigma, sc.d_env, sc.env_w, sc.env_h};
-  const uint32_t n_pix = (uint32_t)vw.n_views * vw.width * vw.height;
-  for (int k = 0; k <= p.max_depth; ++k) {
+  const bool batch = n > 1;
+  const SceneEntry& E0 = entries[0];
+  const int bps = g_tuning.trace_blocks_per_sm, st = g_tuning.trace_steps, rf = g_tuning.trace_refill;
+  for (int k = 0; k <= th.max_depth; ++k) {
     {
       ProfScope ps("k_trace", s);
-      if (g_tuning.bvh_width == 4)
-        launch_trace_w<4>(g_tuning.trace_blocks_per_sm, s, W, (const float4*)B.node4, (const float4*)B.tris,
-                          (const BvhHeader*)B.hdr, k, p.t_min, traversal_limit(sc.nf), g_tuning.trace_steps,
-                          g_tuning.trace_refill);
-      else
-        launch_trace_w<2>(g_tuning.trace_blocks_per_sm, s, W, (const float4*)B.node2, (const float4*)B.tris,
-                          (const BvhHeader*)B.hdr, k, p.t_min, traversal_limit(sc.nf), g_tuning.trace_steps,
-                          g_tuning.trace_refill);
+      if (g_tuning.bvh_width == 4) {
+        if (batch) launch_trace_w<4, true>(bps, s, W, k, st, rf, E0);
+        else launch_trace_w<4, false>(bps, s, W, k, st, rf, E0);
+      } else {
+        if (batch) launch_trace_w<2, true>(bps, s, W, k, st, rf, E0);
+        else launch_trace_w<2, false>(bps, s, W, k, st, rf, E0);
+      }
     }
     {
       ProfScope ps("k_shade", s);
-      k_shade<<<shade_blocks(), 256, 0, s>>>(W, S, k, p.max_depth, p.spp, n_pix, out);
+      if (batch) k_shade<true><<<shade_blocks(), 256, 0, s>>>(W, k, E0);
+      else k_shade<false><<<shade_blocks(), 256, 0, s>>>(W, k, E0);
     }
   }
+}
+
+// One table entry for a scene as given at the C ABI.
+SceneEntry make_entry(const dt_scene& sc, const dt_views& vw, const dt_params& p, float* out) {
+  SceneEntry e;
+  memset(&e, 0, sizeof(e));
+  BvhView B = bvh_view(sc.d_bvh, sc.nf);
+  e.V = sc.d_V; e.F = sc.d_F; e.N = sc.d_N; e.ior = sc.d_ior; e.sigma = sc.d_sigma; e.env = sc.d_env;
+  e.node2 = B.node2; e.node4 = B.node4; e.tris = B.tris; e.bh = B.hdr;
+  e.cams = vw.d_cams; e.out = out;
+  e.seed = p.seed;
+  e.nv = sc.nv; e.nf = sc.nf; e.env_w = sc.env_w; e.env_h = sc.env_h;
+  e.n_views = vw.n_views; e.width = vw.width; e.height = vw.height; e.spp = p.spp;
+  e.max_depth = p.max_depth; e.jitter = p.jitter; e.max_iter = traversal_limit(sc.nf);
+  e.t_min = p.t_min;
+  e.pix_count = (uint32_t)vw.n_views * (uint32_t)vw.width * (uint32_t)vw.height;
+  return e;
+}
+
+// Fills sample/face offsets of the entries and the table header.
+void finish_table(SceneEntry* entries, int n, TableHeader& th) {
+  memset(&th, 0, sizeof(th));
+  th.n = n;
+  uint32_t s = 0, f = 0;
+  int md = 0;
+  for (int i = 0; i < n; ++i) {
+    entries[i].sample_start = s;
+    entries[i].face_start = f;
+    th.starts[i] = s;
+    th.face_starts[i] = f;
+    s += entries[i].pix_count * (uint32_t)entries[i].spp;
+    f += (uint32_t)entries[i].nf;
+    if (entries[i].max_depth > md) md = entries[i].max_depth;
+  }
+  th.starts[n] = s;
+  th.face_starts[n] = f;
+  th.n_samples = s;
+  th.n_faces = f;
+  th.max_depth = md;
 }
 
 void launch_dump(const void* ws, unsigned long long cap, int32_t* si, float* sf, unsigned long long n,

@@ -21,6 +21,7 @@ from __future__ import annotations
 import dataclasses
 import itertools
 import math
+import os
 
 import numpy as np
 
@@ -379,9 +380,9 @@ def _random_rotation(rng):
         [2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)]])
 
 
-def random_blob_field(rng: np.random.Generator):
-    """A random SDF: union (min) of 1-6 ellipsoids or tori with random axes,
-    radii and centres in [-0.5, 0.5]^3.  Returns a callable on grids."""
+def blob_prims(rng: np.random.Generator) -> list:
+    """Parameters of a random SDF: 1-6 ellipsoids or tori with random axes,
+    radii and centres in [-0.5, 0.5]^3 (plain data, picklable)."""
     prims = []
     for _ in range(int(rng.integers(1, 7))):
         c = rng.uniform(-0.5, 0.5, size=3)
@@ -391,7 +392,16 @@ def random_blob_field(rng: np.random.Generator):
         else:
             R = rng.uniform(0.2, 0.45)
             prims.append(("t", c, (R, rng.uniform(0.06, 0.45 * R)), rot))
+    return prims
 
+
+def random_blob_field(rng: np.random.Generator):
+    """A random SDF: the union (min) of blob_prims(rng).  Returns a callable
+    on grids."""
+    return blob_field(blob_prims(rng))
+
+
+def blob_field(prims):
     def field(X, Y, Z):
         out = None
         for kind, c, prm, rot in prims:
@@ -402,6 +412,57 @@ def random_blob_field(rng: np.random.Generator):
             out = s if out is None else np.minimum(out, s)
         return out
     return field
+
+
+@dataclasses.dataclass
+class BatchSpec:
+    """One scene of the batching workload, as plain data."""
+    index: int
+    prims: list
+    faces: int
+    side: int
+    depth: int
+    ior: float
+    sigma: np.ndarray
+    env_seed: int
+    cam_seed: int
+
+
+def batch_specs(n: int = 64, seed: int = 2) -> list:
+    """n scenes: faces log-uniform in [2k, 200k], square images with side
+    log-uniform in [128, 800], depth uniform in 4..12, IoR ~ U[1.3, 1.7],
+    per-channel absorption ~ U[0, 2], a 256x128 SH environment each."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        out.append(BatchSpec(
+            index=i, prims=blob_prims(rng),
+            faces=int(round(math.exp(rng.uniform(math.log(2000), math.log(200000))))),
+            side=int(round(math.exp(rng.uniform(math.log(128), math.log(800))))),
+            depth=int(rng.integers(4, 13)), ior=float(F32(rng.uniform(1.3, 1.7))),
+            sigma=rng.uniform(0.0, 2.0, size=3).astype(F32), env_seed=int(rng.integers(0, 2 ** 31)),
+            cam_seed=int(rng.integers(0, 2 ** 31))))
+    return out
+
+
+def build_batch_scene(spec: BatchSpec) -> Scene:
+    """The scene of one BatchSpec (top-level, so a process pool can run it)."""
+    V, F = mesh_from_field(blob_field(spec.prims), spec.faces)
+    env = sh_env_map(256, 128, spec.env_seed)
+    cam = random_view(np.random.default_rng(spec.cam_seed), 3.0, spec.side, spec.side)
+    return Scene(V, F, spec.ior, spec.sigma, env, [cam], spec.depth, 1, 0, spec.index)
+
+
+def batch_scenes(n: int = 64, seed: int = 2, workers: int = None) -> list:
+    """The batching workload (see batch_specs), built in parallel processes
+    (spawned, so this is safe after CUDA has been initialised)."""
+    specs = batch_specs(n, seed)
+    workers = workers or min(len(specs), os.cpu_count() or 1)
+    if workers <= 1:
+        return [build_batch_scene(s) for s in specs]
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(workers) as pool:
+        return pool.map(build_batch_scene, specs, chunksize=1)
 
 
 def mesh_from_field(field, target_faces: int, lo: float = -1.2, hi: float = 1.2,

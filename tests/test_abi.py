@@ -83,6 +83,7 @@ int main(void) {
   printf("%zu %zu %zu %zu\n", sizeof(dt_scene), sizeof(dt_views), sizeof(dt_params), sizeof(dt_stats));
   printf("%zu %zu %zu %zu\n", offsetof(dt_scene, env_w), offsetof(dt_params, seed), offsetof(dt_params, t_min),
          offsetof(dt_stats, max_level));
+  printf("%zu %zu %zu\n", sizeof(dt_batch_entry), offsetof(dt_batch_entry, d_grad_sigma), sizeof(dt_tuning));
   return 0;
 }
 """
@@ -95,8 +96,10 @@ int main(void) {
     sizes = [int(x) for x in out]
     assert sizes[:4] == [ctypes.sizeof(dt.DtScene), ctypes.sizeof(dt.DtViews), ctypes.sizeof(dt.DtParams),
                          ctypes.sizeof(dt.DtStats)]
-    assert sizes[4:] == [dt.DtScene.env_w.offset, dt.DtParams.seed.offset, dt.DtParams.t_min.offset,
-                         dt.DtStats.max_level.offset]
+    assert sizes[4:8] == [dt.DtScene.env_w.offset, dt.DtParams.seed.offset, dt.DtParams.t_min.offset,
+                          dt.DtStats.max_level.offset]
+    assert sizes[8:] == [ctypes.sizeof(dt.DtBatchEntry), dt.DtBatchEntry.d_grad_sigma.offset,
+                         ctypes.sizeof(dt.DtTuning)]
 
 
 def test_python_calls_fail_loudly_without_the_library(tmp_path):
