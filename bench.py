@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=12, help="pixels in the CPU oracle sample")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-scene batching comparison")
     ap.add_argument("--batch-scenes", type=int, default=64)
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving comparison")
+    ap.add_argument("--serve-requests", type=int, default=200)
     return ap.parse_args()
 
 
@@ -217,6 +219,41 @@ KERNELS_PER_SCOPE = {"k_vertex_normals": 2, "k_refit": 3, "k_camera": 1, "k_trac
                      "k_write_table": 2, "k_zero_images": 1, "k_zero_grads": 1}
 
 
+def serve_leg(args, scs, dev):
+    """Poisson streams of render and gradient requests (50/50) over 32
+    resident meshes; square images with side log-uniform in [64, 1024],
+    depth uniform in 4..16.  The continuous-batching server against the same
+    loop serving one request per launch, at two arrival rates."""
+    import torch
+    from paper_2603_00413_gb300 import serve
+    from paper_2603_00413_gb300 import scenes as S
+    res = [serve.ResidentScene.from_arrays(sc.V, sc.F, sc.ior, sc.sigma, sc.env, dev) for sc in scs[:32]]
+    budget = int(0.5 * torch.cuda.mem_get_info(dev)[0])
+    out = {"workload": f"{len(res)} resident meshes ({min(r.F.shape[0] for r in res)}-"
+                       f"{max(r.F.shape[0] for r in res)} faces), {args.serve_requests} Poisson requests per rate, "
+                       f"50% render / 50% gradient, side 64-1024, depth 4-16", "rates": {}}
+
+    def view(rng, side):
+        return S.random_view(rng, 3.0, side, side).as_array()
+
+    for rate in (100.0, 1000.0):
+        row = {}
+        for name, mb, ns in (("batched", 32, 2), ("one_per_launch", 1, 1)):
+            rng = np.random.default_rng(int(rate))
+            trg = np.random.default_rng(int(rate) + 7)
+            reqs = serve.poisson_requests(rng, args.serve_requests, rate, len(res), sides=(64, 1024), depths=(4, 16),
+                                          grad_frac=0.5, view_fn=view,
+                                          target_fn=lambda r: trg.uniform(0, 2, size=(r.height, r.width, 3)).astype(
+                                              np.float32))
+            srv = serve.Server(res, budget, max_batch=mb, streams=ns)
+            done = srv.run(reqs, timeout=600)
+            wall = max(r.finish for r in done)
+            row[name] = serve.latency_summary(done, wall)
+            row[name]["launches"] = srv.launches
+        out["rates"][str(int(rate))] = row
+    return out
+
+
 def batch_leg(args, dt, dev, steps):
     """64 scenes of uneven size (2k-200k faces, 128^2-800^2 images, depth
     4-12), fwd+bwd with a fixed image gradient: the plain loop (each scene
@@ -277,6 +314,10 @@ def batch_leg(args, dt, dev, steps):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / k
 
+    from paper_2603_00413_gb300 import autotune
+    import tempfile
+    tuned = autotune.tune(batched, key=f"batch{len(items)}-seed2", reps=1, retune=True,
+                          cache_path=os.path.join(tempfile.gettempdir(), "difftrans_bench_tuning.json"))
     ms_batched = timed(batched, steps)
     ms_plain = timed(plain, steps)
     # the batched step captured once in a CUDA graph and replayed
@@ -292,7 +333,12 @@ def batch_leg(args, dt, dev, steps):
     chk = dt.read_stats(tape.ws)
     assert chk["status"] == dt.DT_OK and chk["segments"] == seg, chk
     depth_max = max(it.params.max_depth for it in items)
-    return {
+    serve_out = None
+    if not args.no_serve:
+        del graph, tape, bws, plain_ws
+        torch.cuda.empty_cache()
+        serve_out = serve_leg(args, scs, dev)
+    return serve_out, {
         "workload": f"{len(items)} random-blob scenes, {sum(it.F.shape[0] for it in items)} faces in all "
                     f"({min(it.F.shape[0] for it in items)}-{max(it.F.shape[0] for it in items)}), "
                     f"{sum(it.width * it.height for it in items)} pixels ({min(it.width for it in items)}^2-"
@@ -302,6 +348,7 @@ def batch_leg(args, dt, dev, steps):
         "plain_segments_per_s": plain_seg / (ms_plain / 1e3), "plain_ms": ms_plain,
         "batched_segments_per_s": seg / (ms_batched / 1e3), "batched_ms": ms_batched,
         "graph_segments_per_s": seg / (ms_graph / 1e3), "graph_ms": ms_graph,
+        "tuning": tuned["tuning"], "tuning_trials": len(tuned["trials"]),
         "launches_per_step_plain": int(sum(3 * (it.params.max_depth + 1) + 8 for it in items)),
         "launches_per_step_batched": int(3 * (depth_max + 1) + 4 + 2 * (1 + (len(items) + 23) // 24)),
     }
@@ -506,11 +553,11 @@ def run_ours(args):
                "sample": f"{args.cpu_sample} seeded pixels of the same workload ({nseg} segments), forward + "
                          f"gradient by forward mode over the parameters those paths touch, {secs:.1f} s"}
 
-    batch = None
+    batch = serving = None
     if rank == 0 and world == 1 and not args.no_batch:
         del ws, bws, tape
         torch.cuda.empty_cache()
-        batch = batch_leg(args, dt, dev, max(3, args.steps // 4))
+        serving, batch = batch_leg(args, dt, dev, max(3, args.steps // 4))
 
     if rank == 0:
         out = {
@@ -531,6 +578,7 @@ def run_ours(args):
             "e2e": e2e,
             "cpu_baseline": cpu,
             "batch": batch,
+            "serve": serving,
             "levels": stats["level_count"],
             "nodes_per_segment": stats["nodes_visited"] / seg,
             "tris_per_segment": stats["tris_tested"] / seg,
