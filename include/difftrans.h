@@ -158,15 +158,26 @@ typedef struct dt_views {
  *    pcg(seed_hi)) ^ v) ^ p) ^ s), pcg = the PCG hash of Jarzynski and Olano
  *    (JCGT 2020).
  *  t_min: hits need t > t_min (the triangle a ray leaves from is skipped
- *    as well).  1e-5 for meshes scaled to the unit sphere. */
+ *    as well).  1e-5 for meshes scaled to the unit sphere.
+ *  tape_mode: 0 keeps every segment's hit record for the backward; 1 is
+ *    per-bounce checkpointing: only the ray queues are kept, hit records
+ *    live in a ring of two levels of level_capacity segments each, and the
+ *    backward re-traces each level before differentiating it (one more
+ *    traversal, 16 bytes per segment less).  A level larger than
+ *    level_capacity is dropped past that size and reported as
+ *    DT_ERR_QUEUE_OVERFLOW with dt_stats.level_needed.
+ *  level_capacity: segments per ring level (tape_mode 1 only; else 0).
+ *  The workspace must be sized for the same tape_mode and level_capacity
+ *  (dt_render_workspace_size_ex) and the backward must be given the same
+ *  params as the forward; all entries of a batch share them. */
 typedef struct dt_params {
   int32_t max_depth;
   int32_t spp;
   int32_t jitter;
-  int32_t reserved0;
+  int32_t tape_mode;
   uint64_t seed;
   float t_min;
-  int32_t reserved1;
+  int32_t level_capacity;
 } dt_params;
 
 /* ------------------------------------------------------------------------
@@ -174,7 +185,8 @@ typedef struct dt_params {
  * then for k = 0..D a closest-hit pass over the level-k segments and a
  * shading pass that accumulates escaped rays into the image and appends the
  * reflected and refracted children to level k+1.  Every segment of every
- * level is kept in the workspace (the "tape") for dt_render_backward.
+ * level is kept in the workspace (the "tape") for dt_render_backward
+ * (tape_mode 1: the ray queues of every level, the hits of the last two).
  *
  * dt_render_workspace_size: bytes for a workspace holding seg_capacity
  *   segments (all levels together; seg_capacity <= 2^31 - 1).  A segment is
@@ -187,6 +199,10 @@ typedef struct dt_params {
  *   DT_ERR_QUEUE_OVERFLOW with a lower bound on the capacity needed.
  * ------------------------------------------------------------------------ */
 dt_status dt_render_workspace_size(int64_t seg_capacity, size_t* ws_bytes);
+/* The same for a tape_mode (see dt_params): tape_mode 1 needs
+ * 1 <= level_capacity <= seg_capacity. */
+dt_status dt_render_workspace_size_ex(int64_t seg_capacity, int32_t tape_mode, int64_t level_capacity,
+                                      size_t* ws_bytes);
 dt_status dt_render(const dt_scene* scene, const dt_views* views, const dt_params* params, float* d_out,
                     void* d_ws, size_t ws_bytes, dt_stream stream);
 
@@ -206,6 +222,7 @@ typedef struct dt_stats {
   int64_t nodes_visited;       /* BVH nodes whose child boxes were tested */
   int64_t tris_tested;         /* ray/triangle tests */
   int64_t max_level;           /* largest level_count */
+  int64_t level_needed;        /* largest level as generated (for tape_mode 1 level_capacity) */
 } dt_stats;
 dt_status dt_read_stats(const void* d_ws, size_t ws_bytes, dt_stats* out, dt_stream stream);
 
@@ -222,7 +239,11 @@ dt_status dt_read_stats(const void* d_ws, size_t ws_bytes, dt_stats* out, dt_str
  *
  * The scene, views and params must be those of the dt_render that filled
  * d_ws (ws_bytes as passed to it), and that render must have finished with
- * status DT_OK.  dt_backward_workspace_size: bytes of the backward scratch
+ * status DT_OK.  With tape_mode 0 the tape is only read; with tape_mode 1
+ * each level is traced again (Sec. 3.4 step 2, through the same BVH, which
+ * must not have changed since the forward) into the workspace's hit ring
+ * before its adjoint, so the ring and the re-trace cursors of d_ws are
+ * written.  dt_backward_workspace_size: bytes of the backward scratch
  * d_bws (256-byte aligned) for a render whose largest level held max_level
  * segments (dt_stats.max_level); pass the same max_level to
  * dt_render_backward.  Outputs are overwritten: d_grad_V float[nv][3],
@@ -230,7 +251,7 @@ dt_status dt_read_stats(const void* d_ws, size_t ws_bytes, dt_stats* out, dt_str
  * ------------------------------------------------------------------------ */
 dt_status dt_backward_workspace_size(int64_t max_level, int32_t nv, size_t* bytes);
 dt_status dt_render_backward(const dt_scene* scene, const dt_views* views, const dt_params* params,
-                             const void* d_ws, size_t ws_bytes, const float* d_grad_out, float* d_grad_V,
+                             void* d_ws, size_t ws_bytes, const float* d_grad_out, float* d_grad_V,
                              float* d_grad_ior, float* d_grad_sigma, void* d_bws, size_t bws_bytes,
                              int64_t max_level, dt_stream stream);
 
@@ -262,14 +283,15 @@ typedef struct dt_batch_entry {
 dt_status dt_render_batch(const dt_batch_entry* entries, int32_t n, void* d_ws, size_t ws_bytes, dt_stream stream);
 dt_status dt_batch_backward_workspace_size(const dt_batch_entry* entries, int32_t n, int64_t max_level,
                                            size_t* bytes);
-dt_status dt_render_batch_backward(const dt_batch_entry* entries, int32_t n, const void* d_ws, size_t ws_bytes,
+dt_status dt_render_batch_backward(const dt_batch_entry* entries, int32_t n, void* d_ws, size_t ws_bytes,
                                    void* d_bws, size_t bws_bytes, int64_t max_level, dt_stream stream);
 
 /* ------------------------------------------------------------------------
  * Debug / parity: every segment of the tape in arena order (level by
  * level).  d_seg_i int32[cap][4] = (sample index, heap node id, hit triangle
  * or -1, flags); d_seg_f float[cap][9] = (t, b1, b2, origin xyz, direction
- * xyz).  Sample index = (view*height*width + py*width + px)*spp + s; the
+ * xyz); available after a render with tape_mode 0 only (after tape_mode 1
+ * nothing is written).  Sample index = (view*height*width + py*width + px)*spp + s; the
  * heap node id of a camera ray is 1 and the children of node m are 2m
  * (reflected) and 2m+1 (refracted).  Flag bits: 4 inside (hit from inside),
  * 8 total internal reflection, 16 backfacing shading normal, 128 hit at

@@ -59,15 +59,16 @@ class DtViews(ctypes.Structure):
 
 
 class DtParams(ctypes.Structure):
-    _fields_ = [("max_depth", c_int32), ("spp", c_int32), ("jitter", c_int32), ("reserved0", c_int32),
-                ("seed", c_uint64), ("t_min", c_float), ("reserved1", c_int32)]
+    _fields_ = [("max_depth", c_int32), ("spp", c_int32), ("jitter", c_int32), ("tape_mode", c_int32),
+                ("seed", c_uint64), ("t_min", c_float), ("level_capacity", c_int32)]
 
 
 class DtStats(ctypes.Structure):
     _fields_ = [("status", c_int32), ("n_levels", c_int32), ("segments", c_int64), ("seg_needed", c_int64),
                 ("level_count", c_int64 * 32), ("level_start", c_int64 * 32), ("hits", c_int64),
                 ("misses", c_int64), ("discarded", c_int64), ("backfacing", c_int64), ("tir", c_int64),
-                ("nodes_visited", c_int64), ("tris_tested", c_int64), ("max_level", c_int64)]
+                ("nodes_visited", c_int64), ("tris_tested", c_int64), ("max_level", c_int64),
+                ("level_needed", c_int64)]
 
     def as_dict(self):
         n = self.n_levels
@@ -76,6 +77,7 @@ class DtStats(ctypes.Structure):
             "level_count": list(self.level_count[:max(n, 1)]), "hits": self.hits, "misses": self.misses,
             "discarded": self.discarded, "backfacing": self.backfacing, "tir": self.tir,
             "nodes_visited": self.nodes_visited, "tris_tested": self.tris_tested, "max_level": self.max_level,
+            "level_needed": self.level_needed,
         }
 
 
@@ -106,6 +108,7 @@ _PROTOS = {
     "dt_build_bvh": (c_int32, [c_void_p, c_int32, c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
     "dt_refit_bvh": (c_int32, [c_void_p, c_int32, c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
     "dt_render_workspace_size": (c_int32, [c_int64, POINTER(c_size_t)]),
+    "dt_render_workspace_size_ex": (c_int32, [c_int64, c_int32, c_int64, POINTER(c_size_t)]),
     "dt_render": (c_int32, [POINTER(DtScene), POINTER(DtViews), POINTER(DtParams), c_void_p, c_void_p, c_size_t,
                             c_void_p]),
     "dt_read_stats": (c_int32, [c_void_p, c_size_t, POINTER(DtStats), c_void_p]),
@@ -282,16 +285,31 @@ def closest_hit(bvh: Bvh, o, d, src=None, t_min: float = 1e-5, stream=None):
 # render / backward
 # ---------------------------------------------------------------------------
 class Params:
-    def __init__(self, max_depth: int, spp: int = 1, jitter: int = 0, seed: int = 0, t_min: float = 1e-5):
+    """Render parameters.  checkpoint=True keeps only the per-depth ray
+    queues on the tape and re-traces each level's hits in the backward
+    (tape_mode 1); the hit ring then holds level_capacity records per level
+    (0: chosen from the workspace, else twice the camera rays)."""
+
+    def __init__(self, max_depth: int, spp: int = 1, jitter: int = 0, seed: int = 0, t_min: float = 1e-5,
+                 checkpoint: bool = False, level_capacity: int = 0):
         self.max_depth, self.spp, self.jitter, self.seed, self.t_min = max_depth, spp, jitter, seed, t_min
+        self.checkpoint, self.level_capacity = bool(checkpoint), int(level_capacity)
 
-    def c(self):
-        return DtParams(self.max_depth, self.spp, self.jitter, 0, self.seed & (2 ** 64 - 1), self.t_min, 0)
+    def c(self, level_capacity: int = None):
+        ring = self.level_capacity if level_capacity is None else level_capacity
+        return DtParams(self.max_depth, self.spp, self.jitter, 1 if self.checkpoint else 0, self.seed & (2 ** 64 - 1),
+                        self.t_min, int(ring) if self.checkpoint else 0)
 
 
-def render_workspace_size(seg_capacity: int) -> int:
+def render_workspace_size(seg_capacity: int, level_capacity: int = 0) -> int:
+    """Bytes of a workspace for seg_capacity segments; level_capacity > 0
+    sizes a checkpointed one (hit ring of that many records per level)."""
     b = c_size_t()
-    _check(load_library().dt_render_workspace_size(int(seg_capacity), ctypes.byref(b)))
+    if level_capacity > 0:
+        _check(load_library().dt_render_workspace_size_ex(int(seg_capacity), 1, int(level_capacity),
+                                                          ctypes.byref(b)))
+    else:
+        _check(load_library().dt_render_workspace_size(int(seg_capacity), ctypes.byref(b)))
     return b.value
 
 
@@ -302,11 +320,13 @@ def backward_workspace_size(max_level: int, nv: int) -> int:
 
 
 class Workspace:
-    """A caller-owned segment arena (the tape) for dt_render."""
+    """A caller-owned segment arena (the tape) for dt_render; level_capacity
+    > 0 makes it a checkpointed one (hits of two levels only)."""
 
-    def __init__(self, seg_capacity: int, device):
+    def __init__(self, seg_capacity: int, device, level_capacity: int = 0):
         self.capacity = int(seg_capacity)
-        self.bytes = render_workspace_size(self.capacity)
+        self.level_capacity = int(min(level_capacity, self.capacity)) if level_capacity > 0 else 0
+        self.bytes = render_workspace_size(self.capacity, self.level_capacity)
         self._raw, self.buf = _aligned_empty(self.bytes, device)
 
 
@@ -335,17 +355,47 @@ def read_stats(ws: Workspace, stream=None) -> dict:
 
 
 class Tape:
-    """Everything dt_render_backward needs from a forward call."""
+    """Everything dt_render_backward needs from a forward call (params_c:
+    the dt_params the forward ran with)."""
 
-    def __init__(self, ws, scene_args, cams, width, height, params, stats):
+    def __init__(self, ws, scene_args, cams, width, height, params, stats, params_c=None):
         self.ws, self.scene_args, self.cams = ws, scene_args, cams
         self.width, self.height, self.params, self.stats = width, height, params, stats
+        self.params_c = params_c if params_c is not None else params.c()
 
 
 def default_capacity(n_primary: int, max_depth: int) -> int:
     """First guess of the segment arena: 2D + 3 segments per primary ray is
     what a convex object needs; the arena grows on overflow."""
     return int(min(2 ** 31 - 1, max(n_primary * (2 * max_depth + 3), 1024)))
+
+
+def _new_workspace(params: Params, n_primary: int, device, capacity: int = None, level_capacity: int = None):
+    cap = default_capacity(n_primary, params.max_depth) if capacity is None else capacity
+    if not params.checkpoint:
+        return Workspace(cap, device)
+    ring = level_capacity or params.level_capacity or 2 * n_primary
+    return Workspace(cap, device, level_capacity=max(ring, 1))
+
+
+def _grow_workspace(ws: Workspace, params: Params, stats: dict, device):
+    """A larger workspace after an overflow of the arena or of a checkpointed
+    level's hit ring."""
+    cap = ws.capacity
+    if stats["seg_needed"] > cap:
+        cap = min(max(2 * cap, int(1.3 * stats["seg_needed"])), 2 ** 31 - 1)
+    if not ws.level_capacity:
+        return Workspace(cap, device)
+    ring = ws.level_capacity
+    if stats["level_needed"] > ring:
+        ring = int(1.25 * stats["level_needed"])
+    return Workspace(max(cap, ring), device, level_capacity=ring)
+
+
+def _effective_params(params: Params, ws: Workspace):
+    if params.checkpoint and not ws.level_capacity:
+        raise ValueError("a checkpointed render needs a workspace made with level_capacity > 0")
+    return params.c(ws.level_capacity if params.checkpoint else 0)
 
 
 def render(V, F, bvh: Bvh, N, ior, sigma, env, cams, width: int, height: int, params: Params, ws: Workspace = None,
@@ -359,25 +409,24 @@ def render(V, F, bvh: Bvh, N, ior, sigma, env, cams, width: int, height: int, pa
     n_views = cams.shape[0]
     n0 = n_views * width * height * params.spp
     if ws is None:
-        ws = Workspace(default_capacity(n0, params.max_depth), V.device)
+        ws = _new_workspace(params, n0, V.device)
     if out is None:
         out = torch.empty(n_views, height, width, 3, dtype=torch.float32, device=V.device)
     sc = _scene_struct(V, F, bvh, N, ior, sigma, env)
     vw = _views_struct(cams, width, height)
-    pc = params.c()
     while True:
+        pc = _effective_params(params, ws)
         _check(lib.dt_render(ctypes.byref(sc), ctypes.byref(vw), ctypes.byref(pc), _ptr(out), _ptr(ws.buf),
                              ws.bytes, _stream(stream)))
         if not check:
-            return out, Tape(ws, (V, F, bvh, N, ior, sigma, env), cams, width, height, params, None)
+            return out, Tape(ws, (V, F, bvh, N, ior, sigma, env), cams, width, height, params, None, pc)
         stats = read_stats(ws, stream)
         if stats["status"] == DT_ERR_QUEUE_OVERFLOW:
-            grow = max(2 * ws.capacity, int(1.3 * stats["seg_needed"]))
-            ws = Workspace(min(grow, 2 ** 31 - 1), V.device)
+            ws = _grow_workspace(ws, params, stats, V.device)
             continue
         if stats["status"] != DT_OK:
             raise DiffTransError(stats["status"], "device-side error during render")
-        return out, Tape(ws, (V, F, bvh, N, ior, sigma, env), cams, width, height, params, stats)
+        return out, Tape(ws, (V, F, bvh, N, ior, sigma, env), cams, width, height, params, stats, pc)
 
 
 def render_backward(tape: Tape, grad_out, stream=None, bws=None):
@@ -398,7 +447,7 @@ def render_backward(tape: Tape, grad_out, stream=None, bws=None):
     dsig = torch.empty(3, dtype=torch.float32, device=V.device)
     sc = _scene_struct(V, F, bvh, N, ior, sigma, env)
     vw = _views_struct(tape.cams, tape.width, tape.height)
-    pc = tape.params.c()
+    pc = tape.params_c
     _check(lib.dt_render_backward(ctypes.byref(sc), ctypes.byref(vw), ctypes.byref(pc), _ptr(tape.ws.buf),
                                   tape.ws.bytes, _ptr(grad_out), _ptr(dV), _ptr(dior), _ptr(dsig), _ptr(bws),
                                   bws.numel(), max_level, _stream(stream)))
@@ -408,6 +457,8 @@ def render_backward(tape: Tape, grad_out, stream=None, bws=None):
 def dump_segments(tape: Tape, stream=None):
     """Every segment of the tape: (seg_i int32 [n,4] = (sample, heap node, tri,
     flags), seg_f float32 [n,9] = (t, b1, b2, origin, direction))."""
+    if tape.ws.level_capacity:
+        raise ValueError("a checkpointed tape keeps no hit records to dump")
     stats = tape.stats if tape.stats is not None else read_stats(tape.ws, stream)
     n = stats["segments"]
     dev = tape.ws.buf.device
@@ -487,11 +538,11 @@ class BatchItem:
     def n_primary(self):
         return self.cams.shape[0] * self.width * self.height * self.params.spp
 
-    def entry(self, out=None, grad_out=None, dV=None, dior=None, dsig=None):
+    def entry(self, out=None, grad_out=None, dV=None, dior=None, dsig=None, level_capacity: int = 0):
         e = DtBatchEntry()
         e.scene = _scene_struct(self.V, self.F, self.bvh, self.N, self.ior, self.sigma, self.env)
         e.views = _views_struct(self.cams, self.width, self.height)
-        e.params = self.params.c()
+        e.params = self.params.c(level_capacity)
         e.d_out = out.data_ptr() if out is not None else None
         e.d_grad_out = grad_out.data_ptr() if grad_out is not None else None
         e.d_grad_V = dV.data_ptr() if dV is not None else None
@@ -514,19 +565,24 @@ def render_batch(items, ws: Workspace = None, outs=None, stream=None, check: boo
     dev = items[0].V.device
     n0 = sum(it.n_primary for it in items)
     depth = max(it.params.max_depth for it in items)
+    p0 = items[0].params
+    if any(it.params.checkpoint != p0.checkpoint for it in items):
+        raise ValueError("all items of a batch are checkpointed or none is")
     if ws is None:
-        ws = Workspace(default_capacity(n0, depth), dev)
+        ws = _new_workspace(Params(depth, checkpoint=p0.checkpoint, level_capacity=p0.level_capacity), n0, dev)
     if outs is None:
         outs = [torch.empty(it.cams.shape[0], it.height, it.width, 3, dtype=torch.float32, device=dev)
                 for it in items]
-    arr = (DtBatchEntry * n)(*[it.entry(out=o) for it, o in zip(items, outs)])
     while True:
+        if p0.checkpoint and not ws.level_capacity:
+            raise ValueError("a checkpointed render needs a workspace made with level_capacity > 0")
+        arr = (DtBatchEntry * n)(*[it.entry(out=o, level_capacity=ws.level_capacity) for it, o in zip(items, outs)])
         _check(lib.dt_render_batch(arr, n, _ptr(ws.buf), ws.bytes, _stream(stream)))
         if not check:
             return outs, BatchTape(ws, items, None)
         stats = read_stats(ws, stream)
         if stats["status"] == DT_ERR_QUEUE_OVERFLOW:
-            ws = Workspace(min(max(2 * ws.capacity, int(1.3 * stats["seg_needed"])), 2 ** 31 - 1), dev)
+            ws = _grow_workspace(ws, p0, stats, dev)
             continue
         if stats["status"] != DT_OK:
             raise DiffTransError(stats["status"], "device-side error during render")
@@ -534,7 +590,7 @@ def render_batch(items, ws: Workspace = None, outs=None, stream=None, check: boo
 
 
 def batch_backward_workspace_size(items, max_level: int) -> int:
-    arr = (DtBatchEntry * len(items))(*[it.entry() for it in items])
+    arr = (DtBatchEntry * len(items))(*[it.entry(level_capacity=1) for it in items])
     b = c_size_t()
     _check(load_library().dt_batch_backward_workspace_size(arr, len(items), int(max_level), ctypes.byref(b)))
     return b.value
@@ -556,7 +612,8 @@ def render_batch_backward(tape: BatchTape, grads, bws=None, outs=None, stream=No
     if outs is None:
         outs = [(torch.empty_like(it.V), torch.empty(1, device=dev), torch.empty(3, device=dev)) for it in items]
     grads = [_need(g.contiguous(), torch.float32, (3,), "grad") for g in grads]
-    arr = (DtBatchEntry * len(items))(*[it.entry(grad_out=g, dV=o[0], dior=o[1], dsig=o[2])
+    arr = (DtBatchEntry * len(items))(*[it.entry(grad_out=g, dV=o[0], dior=o[1], dsig=o[2],
+                                                 level_capacity=tape.ws.level_capacity)
                                         for it, g, o in zip(items, grads, outs)])
     _check(lib.dt_render_batch_backward(arr, len(items), _ptr(tape.ws.buf), tape.ws.bytes, _ptr(bws), bws.numel(),
                                         max_level, _stream(stream)))

@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(256) k_adjoint(WsView W, int k, const float4* 
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const uint32_t a = start + i;
-    const float4 ro = W.ray_o[a], rd = W.ray_d[a], rw = W.ray_w[a], hh = W.hit[a];
+    const float4 ro = W.ray_o[a], rd = W.ray_d[a], rw = W.ray_w[a], hh = W.hit[hit_slot(W, k, a, i)];
     const uint32_t fl = W.sflag[a];
     const uint32_t sample = __float_as_uint(ro.w);
     const int sc = kBatch ? find_scene(W.th->starts, n_scenes, sample) : 0;
@@ -264,13 +264,14 @@ void launch_l2_loss_grad(const float* img, const float* target, int64_t n, float
 }
 
 void launch_write_table(const WsView& W, const TableHeader& th, const SceneEntry* entries, int n, cudaStream_t s);
+void launch_retrace(const WsView& W, int k, const SceneEntry& E0, bool batch, cudaStream_t s);
 
 // Backward of a table of scenes over the tape in ws: rewrites the table with
 // the gradient pointers, zeroes the gradients, sweeps k = D..0, then the
 // vertex-normal adjoint of every scene.
-void launch_backward_table(const TableHeader& th, const SceneEntry* entries, const void* ws, unsigned long long cap,
-                           void* bws, unsigned long long max_level, cudaStream_t s) {
-  WsView W = ws_view(ws, cap);
+void launch_backward_table(const TableHeader& th, const SceneEntry* entries, void* ws, unsigned long long cap,
+                           unsigned long long ring, void* bws, unsigned long long max_level, cudaStream_t s) {
+  WsView W = ws_view(ws, cap, ring);
   BwsLayout L(max_level, 0);
   char* b = (char*)bws;
   float4* buf[2] = {(float4*)(b + L.off_buf0), (float4*)(b + L.off_buf1)};
@@ -290,7 +291,9 @@ void launch_backward_table(const TableHeader& th, const SceneEntry* entries, con
   }
   const int blocks = g_tuning.shade_blocks_per_sm * num_sms();
   const size_t smem = sizeof(float) * 4 * (size_t)n;
+  if (ring) cudaMemsetAsync(W.hdr->fetch_bwd, 0, sizeof(W.hdr->fetch_bwd), s);
   for (int k = th.max_depth; k >= 0; --k) {
+    if (ring) launch_retrace(W, k, entries[0], n > 1, s);  // checkpointed: hits of level k again
     ProfScope ps("k_adjoint", s);
     if (n > 1) k_adjoint<true><<<blocks, 256, smem, s>>>(W, k, buf[(k + 1) & 1], buf[k & 1], entries[0]);
     else k_adjoint<false><<<blocks, 256, smem, s>>>(W, k, buf[(k + 1) & 1], buf[k & 1], entries[0]);

@@ -29,9 +29,9 @@ void launch_refit(const float* V, const int32_t* F, int32_t nf, void* bvh, void*
 SceneEntry make_entry(const dt_scene& sc, const dt_views& vw, const dt_params& p, float* out);
 void finish_table(SceneEntry* entries, int n, TableHeader& th);
 void launch_forward_table(const TableHeader& th, const SceneEntry* entries, void* ws, unsigned long long cap,
-                          cudaStream_t s);
-void launch_backward_table(const TableHeader& th, const SceneEntry* entries, const void* ws, unsigned long long cap,
-                           void* bws, unsigned long long max_level, cudaStream_t s);
+                          unsigned long long ring, cudaStream_t s);
+void launch_backward_table(const TableHeader& th, const SceneEntry* entries, void* ws, unsigned long long cap,
+                           unsigned long long ring, void* bws, unsigned long long max_level, cudaStream_t s);
 size_t backward_ws_bytes_table(unsigned long long max_level, const SceneEntry* entries, int n);
 void assign_dN(SceneEntry* entries, int n, void* bws, unsigned long long max_level);
 void launch_dump(const void* ws, unsigned long long cap, int32_t* si, float* sf, unsigned long long n,
@@ -117,13 +117,14 @@ ProfScope::~ProfScope() {
   if (slot < (int)g_prof.size()) cudaEventRecord(g_prof[slot].stop, stream);
 }
 
-// the largest segment capacity whose layout fits in ws_bytes
-static unsigned long long cap_from_bytes(size_t ws_bytes) {
-  if (ws_bytes < 4096) return 0;
-  if (ws_bytes < 1024 + kTableBytes + 4096) return 0;
-  unsigned long long cap = (ws_bytes - 1024 - kTableBytes) / 72;
+// the largest segment capacity whose layout fits in ws_bytes, with a hit ring
+// of `ring` records per level parity (ring = 0: one hit record per segment)
+static unsigned long long cap_from_bytes(size_t ws_bytes, unsigned long long ring = 0) {
+  const size_t fixed = 1024 + kTableBytes + 4096 + (ring ? 2 * ring * 16 : 0);
+  if (ws_bytes < fixed) return 0;
+  unsigned long long cap = (ws_bytes - fixed + 4096) / (ring ? 56 : 72);
   if (cap > 0x7fffffffull) cap = 0x7fffffffull;
-  while (cap > 0 && WsLayout(cap).total > ws_bytes) --cap;
+  while (cap > 0 && WsLayout(cap, ring).total > ws_bytes) --cap;
   return cap;
 }
 
@@ -147,6 +148,9 @@ static dt_status check_views_params(const dt_views* vw, const dt_params* p) {
     return set_error(DT_ERR_INVALID_ARG, "max_depth must be in [0, %d] (got %d)", kMaxDepth, p->max_depth);
   if (p->spp < 1) return set_error(DT_ERR_INVALID_ARG, "spp must be >= 1");
   if (!(p->t_min >= 0.0f)) return set_error(DT_ERR_INVALID_ARG, "t_min must be >= 0");
+  if (p->tape_mode != 0 && p->tape_mode != 1) return set_error(DT_ERR_INVALID_ARG, "tape_mode must be 0 or 1");
+  if (p->tape_mode == 1 && p->level_capacity < 1)
+    return set_error(DT_ERR_INVALID_ARG, "tape_mode 1 needs level_capacity >= 1");
   const unsigned long long n0 = (unsigned long long)vw->n_views * vw->width * vw->height * p->spp;
   if (n0 >= 0xffffffffull) return set_error(DT_ERR_INVALID_ARG, "too many primary rays in one call (%llu)", n0);
   return DT_OK;
@@ -220,6 +224,22 @@ dt_status dt_render_workspace_size(int64_t seg_capacity, size_t* ws_bytes) {
   return DT_OK;
 }
 
+dt_status dt_render_workspace_size_ex(int64_t seg_capacity, int32_t tape_mode, int64_t level_capacity,
+                                      size_t* ws_bytes) {
+  if (seg_capacity < 1 || seg_capacity > 0x7fffffffll)
+    return set_error(DT_ERR_INVALID_ARG, "seg_capacity must be in [1, 2^31-1]");
+  if (!ws_bytes) return set_error(DT_ERR_INVALID_ARG, "ws_bytes is NULL");
+  if (tape_mode == 0) {
+    *ws_bytes = WsLayout((unsigned long long)seg_capacity).total;
+    return DT_OK;
+  }
+  if (tape_mode != 1 || level_capacity < 1 || level_capacity > seg_capacity)
+    return set_error(DT_ERR_INVALID_ARG, "tape_mode must be 0 or 1, and tape_mode 1 needs 1 <= level_capacity "
+                                         "<= seg_capacity");
+  *ws_bytes = WsLayout((unsigned long long)seg_capacity, (unsigned long long)level_capacity).total;
+  return DT_OK;
+}
+
 dt_status dt_render(const dt_scene* scene, const dt_views* views, const dt_params* params, float* d_out, void* d_ws,
                     size_t ws_bytes, dt_stream stream) {
   if (!scene || !views || !params) return set_error(DT_ERR_INVALID_ARG, "scene, views or params is NULL");
@@ -259,8 +279,16 @@ static dt_status check_entries(const dt_batch_entry* entries, int32_t n, bool ba
     total += (unsigned long long)out[i].pix_count * (unsigned long long)e.params.spp;
   }
   if (total >= 0xffffffffull) return set_error(DT_ERR_INVALID_ARG, "too many primary rays in one call (%llu)", total);
+  for (int i = 1; i < n; ++i)
+    if (entries[i].params.tape_mode != entries[0].params.tape_mode ||
+        (entries[0].params.tape_mode == 1 && entries[i].params.level_capacity != entries[0].params.level_capacity))
+      return set_error(DT_ERR_INVALID_ARG, "entry %d: all entries of a batch share tape_mode and level_capacity", i);
   finish_table(out.data(), n, th);
   return DT_OK;
+}
+
+static unsigned long long ring_of(const dt_batch_entry* entries) {
+  return entries[0].params.tape_mode == 1 ? (unsigned long long)entries[0].params.level_capacity : 0ull;
 }
 
 dt_status dt_render_batch(const dt_batch_entry* entries, int32_t n, void* d_ws, size_t ws_bytes, dt_stream stream) {
@@ -270,11 +298,12 @@ dt_status dt_render_batch(const dt_batch_entry* entries, int32_t n, void* d_ws, 
   if (st) return st;
   if (!d_ws) return set_error(DT_ERR_INVALID_ARG, "workspace is NULL");
   if (!aligned(d_ws, 256)) return set_error(DT_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
-  const unsigned long long cap = cap_from_bytes(ws_bytes);
+  const unsigned long long ring = ring_of(entries);
+  const unsigned long long cap = cap_from_bytes(ws_bytes, ring);
   if (cap < th.n_samples)
     return set_error(DT_ERR_INVALID_ARG, "workspace holds %llu segments, fewer than the %u camera rays", cap,
                      th.n_samples);
-  launch_forward_table(th, ent.data(), d_ws, cap, (cudaStream_t)stream);
+  launch_forward_table(th, ent.data(), d_ws, cap, ring, (cudaStream_t)stream);
   return check_launch("dt_render");
 }
 
@@ -289,11 +318,13 @@ dt_status dt_read_stats(const void* d_ws, size_t ws_bytes, dt_stats* out, dt_str
   out->status = (h.status & ST_QUEUE_OVERFLOW) ? DT_ERR_QUEUE_OVERFLOW
               : (h.status & ST_STACK_OVERFLOW) ? DT_ERR_STACK_OVERFLOW : DT_OK;
   out->n_levels = (int32_t)h.n_levels;
-  long long seg = 0, need = 0, mx = 0;
+  long long seg = 0, need = 0, mx = 0, lvl_need = 0;
   for (int k = 0; k < kMaxLevels; ++k) {
     const unsigned long long start = h.level_start[k];
     unsigned long long n = h.level_count[k];
     need += (long long)n;
+    if ((long long)n > lvl_need) lvl_need = (long long)n;
+    if (h.ring && n > h.ring) n = h.ring;
     if (k >= (int)h.n_levels) n = 0;
     const unsigned long long room = start < h.capacity ? h.capacity - start : 0ull;
     if (n > room) n = room;
@@ -305,6 +336,8 @@ dt_status dt_read_stats(const void* d_ws, size_t ws_bytes, dt_stats* out, dt_str
   out->segments = seg;
   out->seg_needed = need;
   out->max_level = mx;
+  out->level_needed = lvl_need;
+  if (h.ring && lvl_need > (long long)h.ring && out->status == DT_OK) out->status = DT_ERR_QUEUE_OVERFLOW;
   out->hits = (int64_t)h.counters[CNT_HITS];
   out->misses = (int64_t)h.counters[CNT_MISSES];
   out->discarded = (int64_t)h.counters[CNT_DISCARDED];
@@ -337,25 +370,27 @@ dt_status dt_batch_backward_workspace_size(const dt_batch_entry* entries, int32_
   return DT_OK;
 }
 
-dt_status dt_render_batch_backward(const dt_batch_entry* entries, int32_t n, const void* d_ws, size_t ws_bytes,
+dt_status dt_render_batch_backward(const dt_batch_entry* entries, int32_t n, void* d_ws, size_t ws_bytes,
                                    void* d_bws, size_t bws_bytes, int64_t max_level, dt_stream stream) {
   std::vector<SceneEntry> ent;
   TableHeader th;
   dt_status st = check_entries(entries, n, true, ent, th);
   if (st) return st;
   if (!d_ws || !d_bws) return set_error(DT_ERR_INVALID_ARG, "NULL workspace");
-  const unsigned long long cap = cap_from_bytes(ws_bytes);
+  const unsigned long long ring = ring_of(entries);
+  const unsigned long long cap = cap_from_bytes(ws_bytes, ring);
   if (cap == 0) return set_error(DT_ERR_INVALID_ARG, "workspace too small");
   if (max_level < 1) return set_error(DT_ERR_INVALID_ARG, "max_level must be >= 1");
   if (bws_bytes < backward_ws_bytes_table((unsigned long long)max_level, ent.data(), n))
     return set_error(DT_ERR_INVALID_ARG, "backward workspace smaller than its size query");
   if (!aligned(d_bws, 256)) return set_error(DT_ERR_INVALID_ARG, "backward workspace must be 256-byte aligned");
   assign_dN(ent.data(), n, d_bws, (unsigned long long)max_level);
-  launch_backward_table(th, ent.data(), d_ws, cap, d_bws, (unsigned long long)max_level, (cudaStream_t)stream);
+  launch_backward_table(th, ent.data(), d_ws, cap, ring, d_bws, (unsigned long long)max_level,
+                        (cudaStream_t)stream);
   return check_launch("dt_render_backward");
 }
 
-dt_status dt_render_backward(const dt_scene* scene, const dt_views* views, const dt_params* params, const void* d_ws,
+dt_status dt_render_backward(const dt_scene* scene, const dt_views* views, const dt_params* params, void* d_ws,
                              size_t ws_bytes, const float* d_grad_out, float* d_grad_V, float* d_grad_ior,
                              float* d_grad_sigma, void* d_bws, size_t bws_bytes, int64_t max_level,
                              dt_stream stream) {
@@ -375,7 +410,7 @@ dt_status dt_render_backward(const dt_scene* scene, const dt_views* views, const
 dt_status dt_dump_segments(const void* d_ws, size_t ws_bytes, int32_t* d_seg_i, float* d_seg_f, int64_t cap,
                            dt_stream stream) {
   if (!d_ws || !d_seg_i || !d_seg_f || cap < 0) return set_error(DT_ERR_INVALID_ARG, "bad argument");
-  const unsigned long long wcap = cap_from_bytes(ws_bytes);
+  const unsigned long long wcap = cap_from_bytes(ws_bytes, 0);
   if (wcap == 0) return set_error(DT_ERR_INVALID_ARG, "workspace too small");
   launch_dump(d_ws, wcap, d_seg_i, d_seg_f, (unsigned long long)cap, (cudaStream_t)stream);
   return check_launch("dt_dump_segments");

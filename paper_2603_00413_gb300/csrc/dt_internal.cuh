@@ -149,8 +149,10 @@ struct WsHeader {
   uint32_t level_count[kMaxLevels];  // appended (may exceed what fits)
   uint32_t level_start[kMaxLevels];
   uint32_t fetch[kMaxLevels];        // work-fetch cursors of the trace kernels
+  uint32_t fetch_bwd[kMaxLevels];    // cursors of the backward's re-traces (tape_mode 1)
   unsigned long long counters[16];   // see CNT_*
-  int32_t n_views, width, height, spp, max_depth, pad0;
+  uint32_t ring;                     // level capacity of the hit ring (tape_mode 1), 0 = every hit kept
+  uint32_t pad0;
 };
 
 enum { CNT_HITS = 0, CNT_MISSES, CNT_DISCARDED, CNT_BACKFACING, CNT_TIR, CNT_NODES, CNT_TRIS };
@@ -228,39 +230,51 @@ struct WsView {
   int32_t* child;
   uint32_t* sflag;
   unsigned long long cap;
+  uint32_t ring;  // 0: hit[a] for arena index a; else hit[(k & 1) ring + i] for position i in level k
 };
 
+// Where the hit record of position i of level k (arena index a) lives.
+__device__ __forceinline__ size_t hit_slot(const WsView& W, int k, uint32_t a, uint32_t i) {
+  return W.ring ? (size_t)(k & 1) * W.ring + i : (size_t)a;
+}
+
+// Arena layout; the hit records come last, so every other offset depends on
+// the segment capacity only.  ring = 0: one hit per segment; else a ring of
+// two levels of `ring` hits.
 struct WsLayout {
-  size_t off_table, off_o, off_d, off_w, off_hit, off_child, off_flag, total;
-  __host__ __device__ explicit WsLayout(unsigned long long cap) {
+  size_t off_table, off_o, off_d, off_w, off_child, off_flag, off_hit, total;
+  __host__ __device__ explicit WsLayout(unsigned long long cap, unsigned long long ring = 0) {
     off_table = 1024;
     off_o = off_table + kTableBytes;
     off_d = align_up(off_o + cap * sizeof(float4), 256);
     off_w = align_up(off_d + cap * sizeof(float4), 256);
-    off_hit = align_up(off_w + cap * sizeof(float4), 256);
-    off_child = align_up(off_hit + cap * sizeof(float4), 256);
+    off_child = align_up(off_w + cap * sizeof(float4), 256);
     off_flag = align_up(off_child + cap * sizeof(int32_t), 256);
-    total = align_up(off_flag + cap * sizeof(uint32_t), 256);
+    off_hit = align_up(off_flag + cap * sizeof(uint32_t), 256);
+    total = align_up(off_hit + (ring ? 2 * ring : cap) * sizeof(float4), 256);
   }
 };
 static_assert(sizeof(WsHeader) <= 1024, "header must fit its slot");
 
-__host__ __device__ inline WsView ws_view(const void* base, unsigned long long cap) {
-  WsLayout L(cap);
+__host__ __device__ inline WsView ws_view(const void* base, unsigned long long cap, unsigned long long ring = 0) {
+  WsLayout L(cap, ring);
   char* b = (char*)base;
   TableHeader* th = (TableHeader*)(b + L.off_table);
   SceneEntry* ent = (SceneEntry*)(b + L.off_table + ((sizeof(TableHeader) + 255) / 256) * 256);
   return WsView{(WsHeader*)b, th, ent, (float4*)(b + L.off_o), (float4*)(b + L.off_d), (float4*)(b + L.off_w),
-                (float4*)(b + L.off_hit), (int32_t*)(b + L.off_child), (uint32_t*)(b + L.off_flag), cap};
+                (float4*)(b + L.off_hit), (int32_t*)(b + L.off_child), (uint32_t*)(b + L.off_flag), cap,
+                (uint32_t)ring};
 }
 
-// Segments of level k that fit in the arena.
+// Segments of level k that fit in the arena (and in the hit ring, if any).
 __device__ __forceinline__ uint32_t level_size(const WsHeader* h, int k) {
   const unsigned long long start = h->level_start[k];
   if (start >= h->capacity) return 0;
   const unsigned long long room = h->capacity - start;
-  const unsigned long long n = h->level_count[k];
-  return (uint32_t)(n < room ? n : room);
+  unsigned long long n = h->level_count[k];
+  if (n > room) n = room;
+  if (h->ring && n > h->ring) n = h->ring;
+  return (uint32_t)n;
 }
 
 // ---------------------------------------------------------------------------

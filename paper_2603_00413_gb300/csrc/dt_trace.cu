@@ -78,6 +78,7 @@ __global__ void k_camera(WsView W, unsigned long long capacity) {
   const SceneEntry& E = W.ent[blockIdx.y];
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
     W.hdr->capacity = capacity;
+    W.hdr->ring = W.ring;
     W.hdr->level_count[0] = W.th->n_samples;
     W.hdr->level_start[0] = 0;
   }
@@ -262,10 +263,13 @@ __device__ __forceinline__ ClosestHit closest_hit(const float4* __restrict__ nod
 // exhausted and its last ray is done.
 // kBatch = false: one scene, whose entry E0 arrives as a kernel parameter
 // (uniform constant-bank reads); true: each ray looks its scene up.
+// retrace = 1: the backward's re-trace of a checkpointed level (own cursor,
+// no statistics).
 template <int kMinBlocks, int kWidth, bool kBatch>
 __global__ void __launch_bounds__(256, kMinBlocks) k_trace(WsView W, int k, int steps, int refill,
-                                                           const SceneEntry E0) {
+                                                           const SceneEntry E0, int retrace) {
   WsHeader* H = W.hdr;
+  uint32_t* cursor = retrace ? &H->fetch_bwd[k] : &H->fetch[k];
   const int n_scenes = kBatch ? W.th->n : 1;
   const uint32_t n = level_size(H, k);
   const uint32_t start = H->level_start[k];
@@ -288,7 +292,7 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_trace(WsView W, int k, int 
     const int n_idle = __popc(idle);
     if (!exhausted && n_idle >= refill) {
       uint32_t base = 0;
-      if (lane == 0) base = atomicAdd(&H->fetch[k], (uint32_t)n_idle);
+      if (lane == 0) base = atomicAdd(cursor, (uint32_t)n_idle);
       base = __shfl_sync(kFull, base, 0);
       if (base + (uint32_t)n_idle >= n) exhausted = true;
       if (!active) {
@@ -328,15 +332,17 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_trace(WsView W, int k, int 
         done = node < 0;
       }
       if (done) {
-        W.hit[a] = h.tri >= 0 ? make_float4(h.t, h.b1, h.b2, __int_as_float(h.tri))
-                              : make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+        W.hit[hit_slot(W, k, a, a - start)] = h.tri >= 0 ? make_float4(h.t, h.b1, h.b2, __int_as_float(h.tri))
+                                                         : make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
         active = false;
         break;
       }
     }
   }
-  warp_add_u64(&H->counters[CNT_NODES], nvis);
-  warp_add_u64(&H->counters[CNT_TRIS], ntest);
+  if (!retrace) {
+    warp_add_u64(&H->counters[CNT_NODES], nvis);
+    warp_add_u64(&H->counters[CNT_TRIS], ntest);
+  }
   if (__any_sync(kFull, overflow) && lane == 0) atomicOr(&H->status, ST_STACK_OVERFLOW);
 }
 
@@ -389,7 +395,7 @@ __global__ void __launch_bounds__(256) k_shade(WsView W, int k, const SceneEntry
     int nchild = 0;
     float4 co = make_float4(0.f, 0.f, 0.f, 0.f), cdr = co, cwr = co, cdt = co, cwt = co;
     if (i < n) {
-      const float4 ro = W.ray_o[a], rd = W.ray_d[a], rw = W.ray_w[a], hh = W.hit[a];
+      const float4 ro = W.ray_o[a], rd = W.ray_d[a], rw = W.ray_w[a], hh = W.hit[hit_slot(W, k, a, i)];
       const uint32_t sample = __float_as_uint(ro.w);
       const SceneEntry& E = kBatch ? W.ent[find_scene(W.th->starts, n_scenes, sample)] : E0;
       const int tri = __float_as_int(hh.w);
@@ -488,6 +494,7 @@ __global__ void __launch_bounds__(256) k_shade(WsView W, int k, const SceneEntry
 // every segment of the arena, level by level, for parity checks
 __global__ void k_dump(WsView W, int32_t* __restrict__ si, float* __restrict__ sf, unsigned long long cap) {
   const WsHeader* H = W.hdr;
+  if (H->ring) return;  // hit records of checkpointed renders are not kept
   const int nl = (int)H->n_levels;
   const unsigned long long total = nl > 0 ? H->level_start[nl] : 0ull;
   const unsigned long long lim = total < cap ? total : cap;
@@ -546,8 +553,8 @@ void launch_write_table(const WsView& W, const TableHeader& th, const SceneEntry
 // then per depth one persistent traversal and one shading pass over the
 // segments of every scene together.
 void launch_forward_table(const TableHeader& th, const SceneEntry* entries, void* ws, unsigned long long cap,
-                          cudaStream_t s) {
-  WsView W = ws_view(ws, cap);
+                          unsigned long long ring, cudaStream_t s) {
+  WsView W = ws_view(ws, cap, ring);
   const int n = th.n;
   cudaMemsetAsync(ws, 0, 1024, s);
   launch_write_table(W, th, entries, n, s);
@@ -576,11 +583,11 @@ void launch_forward_table(const TableHeader& th, const SceneEntry* entries, void
     {
       ProfScope ps("k_trace", s);
       if (g_tuning.bvh_width == 4) {
-        if (batch) launch_trace_w<4, true>(bps, s, W, k, st, rf, E0);
-        else launch_trace_w<4, false>(bps, s, W, k, st, rf, E0);
+        if (batch) launch_trace_w<4, true>(bps, s, W, k, st, rf, E0, 0);
+        else launch_trace_w<4, false>(bps, s, W, k, st, rf, E0, 0);
       } else {
-        if (batch) launch_trace_w<2, true>(bps, s, W, k, st, rf, E0);
-        else launch_trace_w<2, false>(bps, s, W, k, st, rf, E0);
+        if (batch) launch_trace_w<2, true>(bps, s, W, k, st, rf, E0, 0);
+        else launch_trace_w<2, false>(bps, s, W, k, st, rf, E0, 0);
       }
     }
     {
@@ -588,6 +595,19 @@ void launch_forward_table(const TableHeader& th, const SceneEntry* entries, void
       if (batch) k_shade<true><<<shade_blocks(), 256, 0, s>>>(W, k, E0);
       else k_shade<false><<<shade_blocks(), 256, 0, s>>>(W, k, E0);
     }
+  }
+}
+
+// The backward's re-trace of level k of a checkpointed render (tape_mode 1).
+void launch_retrace(const WsView& W, int k, const SceneEntry& E0, bool batch, cudaStream_t s) {
+  ProfScope ps("k_trace_retrace", s);
+  const int bps = g_tuning.trace_blocks_per_sm, st = g_tuning.trace_steps, rf = g_tuning.trace_refill;
+  if (g_tuning.bvh_width == 4) {
+    if (batch) launch_trace_w<4, true>(bps, s, W, k, st, rf, E0, 1);
+    else launch_trace_w<4, false>(bps, s, W, k, st, rf, E0, 1);
+  } else {
+    if (batch) launch_trace_w<2, true>(bps, s, W, k, st, rf, E0, 1);
+    else launch_trace_w<2, false>(bps, s, W, k, st, rf, E0, 1);
   }
 }
 
@@ -632,7 +652,7 @@ void finish_table(SceneEntry* entries, int n, TableHeader& th) {
 
 void launch_dump(const void* ws, unsigned long long cap, int32_t* si, float* sf, unsigned long long n,
                  cudaStream_t s) {
-  WsView W = ws_view(ws, cap);
+  WsView W = ws_view(ws, cap, 0);  // a checkpointed render's dump returns at once (k_dump)
   k_dump<<<4 * num_sms(), 256, 0, s>>>(W, si, sf, n);
 }
 

@@ -84,6 +84,8 @@ int main(void) {
   printf("%zu %zu %zu %zu\n", offsetof(dt_scene, env_w), offsetof(dt_params, seed), offsetof(dt_params, t_min),
          offsetof(dt_stats, max_level));
   printf("%zu %zu %zu\n", sizeof(dt_batch_entry), offsetof(dt_batch_entry, d_grad_sigma), sizeof(dt_tuning));
+  printf("%zu %zu %zu\n", offsetof(dt_params, tape_mode), offsetof(dt_params, level_capacity),
+         offsetof(dt_stats, level_needed));
   return 0;
 }
 """
@@ -98,8 +100,26 @@ int main(void) {
                          ctypes.sizeof(dt.DtStats)]
     assert sizes[4:8] == [dt.DtScene.env_w.offset, dt.DtParams.seed.offset, dt.DtParams.t_min.offset,
                           dt.DtStats.max_level.offset]
-    assert sizes[8:] == [ctypes.sizeof(dt.DtBatchEntry), dt.DtBatchEntry.d_grad_sigma.offset,
-                         ctypes.sizeof(dt.DtTuning)]
+    assert sizes[8:11] == [ctypes.sizeof(dt.DtBatchEntry), dt.DtBatchEntry.d_grad_sigma.offset,
+                           ctypes.sizeof(dt.DtTuning)]
+    assert sizes[11:] == [dt.DtParams.tape_mode.offset, dt.DtParams.level_capacity.offset,
+                          dt.DtStats.level_needed.offset]
+
+
+def test_checkpointed_workspace_is_smaller_and_validated():
+    """A checkpointed workspace drops the per-segment hit records (16 of 72
+    bytes) for a two-level ring; bad tape modes and ring sizes are refused."""
+    import paper_2603_00413_gb300 as dt
+    L = dt.load_library()
+    cap, ring = 10_000_000, 1_000_000
+    full = dt.render_workspace_size(cap)
+    ck = dt.render_workspace_size(cap, ring)
+    assert full - ck == pytest.approx(16 * (cap - 2 * ring), abs=4096)
+    b = ctypes.c_size_t()
+    assert L.dt_render_workspace_size_ex(cap, 0, 0, ctypes.byref(b)) == dt.DT_OK and b.value == full
+    assert L.dt_render_workspace_size_ex(cap, 2, ring, ctypes.byref(b)) == dt.DT_ERR_INVALID_ARG
+    assert L.dt_render_workspace_size_ex(cap, 1, 0, ctypes.byref(b)) == dt.DT_ERR_INVALID_ARG
+    assert L.dt_render_workspace_size_ex(cap, 1, cap + 1, ctypes.byref(b)) == dt.DT_ERR_INVALID_ARG
 
 
 def test_python_calls_fail_loudly_without_the_library(tmp_path):
