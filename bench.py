@@ -62,6 +62,12 @@ def parse():
     ap.add_argument("--batch-scenes", type=int, default=64)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving comparison")
     ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--large", action="store_true",
+                    help="add the large optimisation step (about 1.1M-triangle noisy sphere, 800x800, 8 jittered "
+                         "spp, depth 16, per-bounce checkpointing, LBVH rebuild every step)")
+    ap.add_argument("--large-grid", type=int, default=240)
+    ap.add_argument("--large-res", type=int, default=800)
+    ap.add_argument("--large-steps", type=int, default=5)
     return ap.parse_args()
 
 
@@ -214,7 +220,8 @@ def run_reference(args):
 # GPU leg
 # ---------------------------------------------------------------------------
 # kernels launched per profiled scope (a scope may hold more than one kernel)
-KERNELS_PER_SCOPE = {"k_vertex_normals": 2, "k_refit": 3, "k_camera": 1, "k_trace": 1, "k_shade": 1,
+KERNELS_PER_SCOPE = {"k_vertex_normals": 2, "k_refit": 3, "k_camera": 1, "k_trace": 1, "k_trace_retrace": 1,
+                     "k_shade": 1,
                      "k_l2_loss_grad": 1, "k_adjoint": 1, "k_face_normals_backward": 1, "lbvh_build": 21,
                      "k_write_table": 2, "k_zero_images": 1, "k_zero_grads": 1}
 
@@ -251,6 +258,89 @@ def serve_leg(args, scs, dev):
             row[name] = serve.latency_summary(done, wall)
             row[name]["launches"] = srv.launches
         out["rates"][str(int(rate))] = row
+    return out
+
+
+def large_leg(args, dt, dev):
+    """The large optimisation step: sphere SDF (r = 1) plus 3 octaves of value
+    noise (amplitude 0.1) meshed by marching tetrahedra on a 240^3 grid over
+    [-1.3, 1.3]^3 (about 1.1M triangles), one 800x800 view with 8 jittered
+    samples per pixel (5.12M camera rays), depth 16, IoR 1.52, sigma (0.3,
+    0.1, 0.05), a 2048x1024 environment; L2 loss against a render of the
+    vertices perturbed by N(0, 0.001).  One step = LBVH rebuild + vertex
+    normals + checkpointed forward + loss seed + backward (re-trace per
+    level).  The same step with the full tape is timed beside it."""
+    import torch
+    from paper_2603_00413_gb300 import scenes as S
+    t0 = time.time()
+    Vn, Fn = S.noisy_sphere_mesh(args.large_grid, seed=3, amplitude=0.1, octaves=3)
+    env_np = S.sh_env_map(2048, 1024, 3)
+    gen_s = time.time() - t0
+    rng = np.random.default_rng(4)
+    res, D, spp = args.large_res, 16, 8
+    cam = S.camera((0.45, 0.35, 3.0), (0.0, 0.0, 0.0), (0.0, 1.0, 0.0), 45.0, res, res)
+    V = torch.from_numpy(Vn).to(dev)
+    F = torch.from_numpy(Fn).to(dev)
+    Vt = torch.from_numpy((Vn + rng.normal(scale=0.001, size=Vn.shape)).astype(np.float32)).to(dev)
+    ior = torch.tensor([1.52], device=dev)
+    sigma = torch.tensor([0.3, 0.1, 0.05], device=dev)
+    env = torch.from_numpy(env_np).to(dev)
+    cams = torch.from_numpy(cam.as_array()[None]).to(dev)
+    stream = torch.cuda.current_stream()
+    out = {"workload": f"noisy sphere ({Fn.shape[0]} triangles, marching tetrahedra {args.large_grid}^3), 1 view "
+                       f"{res}x{res}, {spp} jittered spp, depth {D}, IoR 1.52, sigma (0.3, 0.1, 0.05), env 2048x1024",
+           "triangles": int(Fn.shape[0]), "camera_rays": res * res * spp, "mesh_gen_s": round(gen_s, 1)}
+    bvh = dt.build_bvh(V, F)
+    N = dt.vertex_normals(V, F)
+    for mode in ("checkpoint", "full"):
+        params = dt.Params(D, spp=spp, jitter=1, seed=11, checkpoint=(mode == "checkpoint"))
+        bvh_t = dt.build_bvh(Vt, F)
+        target, _ = dt.render(Vt, F, bvh_t, dt.vertex_normals(Vt, F), ior, sigma, env, cams, res, res, params)
+        del bvh_t
+        img, tape = dt.render(V, F, bvh, N, ior, sigma, env, cams, res, res, params)
+        stats = tape.stats
+        ws = tape.ws
+        _, bws = dt._aligned_empty(dt.backward_workspace_size(stats["max_level"], V.shape[0]), dev)
+        grad = torch.empty_like(img)
+        loss = torch.empty(1, device=dev)
+
+        def step():
+            bvh.build(V, F)
+            dt.vertex_normals(V, F, out=N)
+            o, tp = dt.render(V, F, bvh, N, ior, sigma, env, cams, res, res, params, ws=ws, out=img, check=False)
+            tp.stats = stats
+            dt.l2_loss_grad(o, target, grad=grad, loss=loss)
+            return dt.render_backward(tp, grad, bws=bws)
+
+        for _ in range(max(args.warmup, 3)):
+            step()
+        torch.cuda.synchronize()
+        dt.profile_read()
+        dt.profile_enable(True)
+        ev = []
+        for _ in range(args.large_steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            ev.append((e0, e1))
+        torch.cuda.synchronize()
+        dt.profile_enable(False)
+        prof = dt.profile_read()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / args.large_steps
+        chk = dt.read_stats(ws)
+        assert chk["status"] == dt.DT_OK and chk["segments"] == stats["segments"], chk
+        seg = stats["segments"]
+        tot = sum(v[1] for v in prof.values())
+        out[mode] = {"ms_per_step": ms, "segments_per_step": int(seg), "segments_per_s": seg / (ms / 1e3),
+                     "tape_bytes": int(ws.bytes), "level_capacity": int(ws.level_capacity),
+                     "rebuild_ms": prof.get("lbvh_build", (1, 0.0))[1] / args.large_steps,
+                     "kernel_share": {k: round(v[1] / tot, 4) for k, v in prof.items()},
+                     "gpu_launches_per_step": int(sum(v[0] * KERNELS_PER_SCOPE.get(k, 1) for k, v in prof.items())
+                                                  / args.large_steps),
+                     "levels": stats["level_count"], "loss": float(loss.item())}
+        del ws, bws, tape, img, target, grad
+        torch.cuda.empty_cache()
     return out
 
 
@@ -553,6 +643,12 @@ def run_ours(args):
                "sample": f"{args.cpu_sample} seeded pixels of the same workload ({nseg} segments), forward + "
                          f"gradient by forward mode over the parameters those paths touch, {secs:.1f} s"}
 
+    large = None
+    if rank == 0 and world == 1 and args.large:
+        with ClockSampler(dev.index or 0) as clk_large:
+            large = large_leg(args, dt, dev)
+        large["clocks"] = clk_large.summary()
+
     batch = serving = None
     if rank == 0 and world == 1 and not args.no_batch:
         del ws, bws, tape
@@ -579,6 +675,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "batch": batch,
             "serve": serving,
+            "large": large,
             "levels": stats["level_count"],
             "nodes_per_segment": stats["nodes_visited"] / seg,
             "tris_per_segment": stats["tris_tested"] / seg,
