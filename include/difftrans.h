@@ -329,9 +329,14 @@ dt_status dt_l2_loss_grad(const float* d_img, const float* d_target, int64_t n, 
  * bvh_width selects the node format the traversal reads: 2 (binary nodes,
  * 64 B) or 4 (4-wide nodes, 128 B: the binary nodes at even depth with
  * their grandchildren as children); both are kept current by build/refit.
- * Defaults {16, 8, 5, 8, 2}; results do not depend on them (the same closest
- * hit is found).  dt_set_tuning rejects values outside steps 1..256, refill
- * 1..32, trace 1..8, shade 1..16, width 2 or 4.
+ * bvh_builder selects the topology dt_build_bvh builds: 0 = LBVH (Morton
+ * codes, radix sort, Karras 2012 hierarchy), 1 = top-down binned surface
+ * area heuristic (16 centroid bins per axis; fewer node visits per ray,
+ * slower to build); dt_refit_bvh keeps whichever topology was built.
+ * Defaults {16, 8, 5, 8, 2, 1}; results do not depend on them (the same
+ * closest hit is found).  dt_set_tuning rejects values outside steps
+ * 1..256, refill 1..32, trace 1..8, shade 1..16, width 2 or 4, builder 0
+ * or 1.
  * ------------------------------------------------------------------------ */
 typedef struct dt_tuning {
   int32_t trace_steps;
@@ -339,6 +344,7 @@ typedef struct dt_tuning {
   int32_t trace_blocks_per_sm;
   int32_t shade_blocks_per_sm;
   int32_t bvh_width;
+  int32_t bvh_builder;
 } dt_tuning;
 dt_status dt_get_tuning(dt_tuning* out);
 dt_status dt_set_tuning(const dt_tuning* in);

@@ -89,7 +89,7 @@ class DtBatchEntry(ctypes.Structure):
 
 class DtTuning(ctypes.Structure):
     _fields_ = [("trace_steps", c_int32), ("trace_refill", c_int32), ("trace_blocks_per_sm", c_int32),
-                ("shade_blocks_per_sm", c_int32), ("bvh_width", c_int32)]
+                ("shade_blocks_per_sm", c_int32), ("bvh_width", c_int32), ("bvh_builder", c_int32)]
 
 
 class DtKernelTime(ctypes.Structure):

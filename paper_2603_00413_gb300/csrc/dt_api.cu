@@ -426,9 +426,10 @@ dt_status dt_set_tuning(const dt_tuning* in) {
   if (!in) return set_error(DT_ERR_INVALID_ARG, "NULL pointer");
   if (in->trace_steps < 1 || in->trace_steps > 256 || in->trace_refill < 1 || in->trace_refill > 32 ||
       in->trace_blocks_per_sm < 1 || in->trace_blocks_per_sm > 8 || in->shade_blocks_per_sm < 1 ||
-      in->shade_blocks_per_sm > 16 || (in->bvh_width != 2 && in->bvh_width != 4))
+      in->shade_blocks_per_sm > 16 || (in->bvh_width != 2 && in->bvh_width != 4) ||
+      (in->bvh_builder != 0 && in->bvh_builder != 1))
     return set_error(DT_ERR_INVALID_ARG, "tuning out of range (steps 1..256, refill 1..32, trace blocks/SM 1..8, "
-                                         "shade blocks/SM 1..16, width 2 or 4)");
+                                         "shade blocks/SM 1..16, width 2 or 4, builder 0 or 1)");
   g_tuning = *in;
   return DT_OK;
 }

@@ -10,6 +10,8 @@
 
 namespace dt {
 
+extern dt_tuning g_tuning;
+
 // ---------------------------------------------------------------------------
 // Eq. 13: N_v = (1/3) sum_{f containing v} unit((v1 - v0) x (v2 - v0)).
 // One thread per face adds its unit normal, in 2^-40 fixed point, to its
@@ -336,6 +338,451 @@ __global__ void k_refit(const float* __restrict__ V, const int32_t* __restrict__
   }
 }
 
+// ---- binned SAH build (top-down) ---------------------------------------------
+// A second builder of the same binary layout.  Top-down: each task is a
+// contiguous range of a primitive permutation; its split is the one of 3 x 15
+// bin boundaries (16 centroid bins per axis) with the least surface area cost
+// area(left box) * left count + area(right box) * right count, and the range
+// is partitioned stably into [left | right].  Tasks larger than kSahSmall
+// take one launch per tree level, one CTA per task; smaller tasks are built
+// down to their leaves by one warp each, in shared memory.  An internal node
+// is numbered by its split position s (the last position of its left child),
+// which is unique in [0, nf - 2]; the root's number is swapped with 0 so the
+// root is node 0.  Splits deeper than kSahFreeDepth (large tasks) or
+// kSahSmallFreeDepth (small ones) take the median, which bounds the depth
+// (see launch_build).  Every decision is a deterministic function of the
+// geometry: bins are sums, minima and maxima, and partitions are stable.
+constexpr int kSahBins = 16;
+constexpr int kSahSmall = 128;
+constexpr int kSahFreeDepth = 24;
+constexpr int kSahSmallFreeDepth = 56;
+constexpr int kSahMaxLevels = 64;
+constexpr int kSahThreads = 512;
+constexpr int kSahSmallWarps = 4;
+
+struct SahTask {
+  int a, n, parent, sd;  // first position, count, parent node, side | depth << 1
+  float4 lo, hi;         // binning bounds (xyz), a superset of the centroids
+};
+struct SahState {
+  int n_large[kSahMaxLevels + 2];
+  int n_small;
+  int sroot;
+  int overflow;
+};
+struct SahView {
+  float4* cen;
+  float4* pbox;
+  uint32_t* idx[2];
+  SahTask* tasks[2];
+  int4* small;  // (a, n, parent, side | depth << 1 | buffer << 30)
+  SahState* st;
+  int max_large, max_small;
+};
+
+__device__ __forceinline__ int sah_bin(float c, float lo, float scale) {
+  const int b = (int)__fmul_rn(__fsub_rn(c, lo), scale);
+  return min(kSahBins - 1, max(0, b));
+}
+__device__ __forceinline__ float sah_scale(float lo, float hi) {
+  const float ext = __fsub_rn(hi, lo);
+  return ext > 0.0f ? __fdiv_rn((float)kSahBins, ext) : 0.0f;
+}
+__device__ __forceinline__ float sah_area(float3 lo, float3 hi) {
+  const float3 d = hi - lo;
+  return d.x * d.y + d.y * d.z + d.z * d.x;
+}
+__device__ __forceinline__ int sah_split_id(int s, int sroot) { return s == sroot ? 0 : (s == 0 ? sroot : s); }
+__device__ __forceinline__ void sah_set_child(BvhView& B, int node, int side, int ref) {
+  reinterpret_cast<int*>(B.bin_child + node)[side] = ref;
+}
+__device__ __forceinline__ float comp(const float4& v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
+__device__ __forceinline__ float comp3(const float3& v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
+
+// primitive boxes and centroids, the identity permutation, bin_child cleared
+// to kNoChild and internal parents to -1 (validation catches any link a build
+// leaves unset, and the depth walks stop at an unset parent)
+__global__ void k_sah_prims(const float* __restrict__ V, const int32_t* __restrict__ F, int32_t nf, SahView S,
+                            BvhView B) {
+  const int n_int = nf - 1;
+  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nf; f += gridDim.x * blockDim.x) {
+    const float3 v0 = load3(V + 3 * F[3 * f]), v1 = load3(V + 3 * F[3 * f + 1]), v2 = load3(V + 3 * F[3 * f + 2]);
+    const float3 c = (v0 + v1 + v2) * (1.0f / 3.0f);
+    S.cen[f] = make_float4(c.x, c.y, c.z, 0.f);
+    S.pbox[2 * f] =
+        make_float4(fminf(v0.x, fminf(v1.x, v2.x)), fminf(v0.y, fminf(v1.y, v2.y)), fminf(v0.z, fminf(v1.z, v2.z)), 0.f);
+    S.pbox[2 * f + 1] =
+        make_float4(fmaxf(v0.x, fmaxf(v1.x, v2.x)), fmaxf(v0.y, fmaxf(v1.y, v2.y)), fmaxf(v0.z, fmaxf(v1.z, v2.z)), 0.f);
+    S.idx[0][f] = (uint32_t)f;
+    if (f < n_int) {
+      B.bin_child[f] = make_int2(kNoChild, kNoChild);
+      B.parent[f] = -1;
+    }
+  }
+}
+
+// the root task: large (level 0) or, for at most kSahSmall triangles, small
+__global__ void k_sah_root(int32_t nf, const uint32_t* __restrict__ bounds, SahView S) {
+  for (int i = threadIdx.x; i < kSahMaxLevels + 2; i += blockDim.x) S.st->n_large[i] = 0;
+  if (threadIdx.x == 0) {
+    S.st->sroot = -1;
+    S.st->overflow = 0;
+    if (nf > kSahSmall) {
+      SahTask t;
+      t.a = 0; t.n = nf; t.parent = -1; t.sd = 0;
+      t.lo = make_float4(ord2f(bounds[0]), ord2f(bounds[1]), ord2f(bounds[2]), 0.f);
+      t.hi = make_float4(ord2f(bounds[3]), ord2f(bounds[4]), ord2f(bounds[5]), 0.f);
+      S.tasks[0][0] = t;
+      S.st->n_small = 0;
+      __threadfence();
+      S.st->n_large[0] = 1;
+    } else {
+      S.small[0] = make_int4(0, nf, -1, 0);
+      S.st->n_small = 1;
+    }
+  }
+}
+
+struct SahBinsSmem {
+  uint32_t cnt[3][kSahBins];
+  uint32_t lo[3][kSahBins][3];
+  uint32_t hi[3][kSahBins][3];
+};
+
+__device__ __forceinline__ void sah_flush(SahBinsSmem& sb, int k, int b, uint32_t n, float3 lo, float3 hi) {
+  atomicAdd(&sb.cnt[k][b], n);
+  atomicMin(&sb.lo[k][b][0], f2ord(lo.x)); atomicMin(&sb.lo[k][b][1], f2ord(lo.y)); atomicMin(&sb.lo[k][b][2], f2ord(lo.z));
+  atomicMax(&sb.hi[k][b][0], f2ord(hi.x)); atomicMax(&sb.hi[k][b][1], f2ord(hi.y)); atomicMax(&sb.hi[k][b][2], f2ord(hi.z));
+}
+
+// best split of one axis from its bins: boundary i puts bins 0..i left
+struct SahSplit {
+  float cost;
+  int axis, bin, nl;
+  float3 llo, lhi, rlo, rhi;
+};
+__device__ SahSplit sah_sweep(const SahBinsSmem& sb, int k) {
+  SahSplit best;
+  best.cost = INFINITY; best.axis = k; best.bin = -1; best.nl = 0;
+  float rarea[kSahBins];
+  uint32_t rcnt[kSahBins];
+  float3 rl = mk(INFINITY, INFINITY, INFINITY), rh = mk(-INFINITY, -INFINITY, -INFINITY);
+  uint32_t c = 0;
+  for (int i = kSahBins - 1; i >= 1; --i) {
+    if (sb.cnt[k][i]) {
+      rl = mk(fminf(rl.x, ord2f(sb.lo[k][i][0])), fminf(rl.y, ord2f(sb.lo[k][i][1])), fminf(rl.z, ord2f(sb.lo[k][i][2])));
+      rh = mk(fmaxf(rh.x, ord2f(sb.hi[k][i][0])), fmaxf(rh.y, ord2f(sb.hi[k][i][1])), fmaxf(rh.z, ord2f(sb.hi[k][i][2])));
+    }
+    c += sb.cnt[k][i];
+    rcnt[i] = c;
+    rarea[i] = c ? sah_area(rl, rh) : 0.f;
+  }
+  float3 ll = mk(INFINITY, INFINITY, INFINITY), lh = mk(-INFINITY, -INFINITY, -INFINITY);
+  uint32_t lc = 0;
+  for (int i = 0; i < kSahBins - 1; ++i) {
+    if (sb.cnt[k][i]) {
+      ll = mk(fminf(ll.x, ord2f(sb.lo[k][i][0])), fminf(ll.y, ord2f(sb.lo[k][i][1])), fminf(ll.z, ord2f(sb.lo[k][i][2])));
+      lh = mk(fmaxf(lh.x, ord2f(sb.hi[k][i][0])), fmaxf(lh.y, ord2f(sb.hi[k][i][1])), fmaxf(lh.z, ord2f(sb.hi[k][i][2])));
+    }
+    lc += sb.cnt[k][i];
+    const uint32_t rc = rcnt[i + 1];
+    if (lc == 0 || rc == 0) continue;
+    const float cost = sah_area(ll, lh) * (float)lc + rarea[i + 1] * (float)rc;
+    if (cost < best.cost) {
+      best.cost = cost; best.bin = i; best.nl = (int)lc;
+      best.llo = ll; best.lhi = lh;
+    }
+  }
+  if (best.bin >= 0) {  // the right box of the chosen boundary
+    float3 a = mk(INFINITY, INFINITY, INFINITY), b = mk(-INFINITY, -INFINITY, -INFINITY);
+    for (int i = best.bin + 1; i < kSahBins; ++i)
+      if (sb.cnt[k][i]) {
+        a = mk(fminf(a.x, ord2f(sb.lo[k][i][0])), fminf(a.y, ord2f(sb.lo[k][i][1])), fminf(a.z, ord2f(sb.lo[k][i][2])));
+        b = mk(fmaxf(b.x, ord2f(sb.hi[k][i][0])), fmaxf(b.y, ord2f(sb.hi[k][i][1])), fmaxf(b.z, ord2f(sb.hi[k][i][2])));
+      }
+    best.rlo = a; best.rhi = b;
+  }
+  return best;
+}
+
+// One tree level of the large tasks: one CTA per task.
+__global__ void __launch_bounds__(kSahThreads) k_sah_large(int level, SahView S, BvhView B) {
+  __shared__ SahBinsSmem sb;
+  __shared__ SahSplit s_best[3];
+  __shared__ uint32_t s_warp[kSahThreads / 32];
+  const int n_int = B.hdr->n_int;
+  const int ntask = min(S.st->n_large[level], S.max_large);
+  const SahTask* tasks = S.tasks[level & 1];
+  const uint32_t* __restrict__ in = S.idx[level & 1];
+  uint32_t* out = S.idx[(level + 1) & 1];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int t = blockIdx.x; t < ntask; t += gridDim.x) {
+    const SahTask T = tasks[t];
+    const int depth = T.sd >> 1;
+    const float3 blo = mk(T.lo.x, T.lo.y, T.lo.z), bhi = mk(T.hi.x, T.hi.y, T.hi.z);
+    const float sc[3] = {sah_scale(blo.x, bhi.x), sah_scale(blo.y, bhi.y), sah_scale(blo.z, bhi.z)};
+    const bool free_split = depth < kSahFreeDepth && (sc[0] > 0.f || sc[1] > 0.f || sc[2] > 0.f);
+    if (free_split) {
+      for (int i = tid; i < 3 * kSahBins; i += blockDim.x) {
+        (&sb.cnt[0][0])[i] = 0u;
+        for (int q = 0; q < 3; ++q) {
+          (&sb.lo[0][0][0])[3 * i + q] = 0xffffffffu;
+          (&sb.hi[0][0][0])[3 * i + q] = 0u;
+        }
+      }
+      __syncthreads();
+      // each thread bins a contiguous run, adding runs of equal bins at once
+      const int run = (T.n + blockDim.x - 1) / blockDim.x;
+      const int p0 = T.a + tid * run, p1 = min(T.a + T.n, p0 + run);
+      int cb[3] = {-1, -1, -1};
+      uint32_t cn[3] = {0u, 0u, 0u};
+      float3 clo[3], chi[3];
+      for (int pos = p0; pos < p1; ++pos) {
+        const uint32_t p = in[pos];
+        const float4 c = S.cen[p], lo = S.pbox[2 * p], hi = S.pbox[2 * p + 1];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          if (sc[k] <= 0.f) continue;
+          const int b = sah_bin(comp(c, k), comp3(blo, k), sc[k]);
+          if (b != cb[k]) {
+            if (cb[k] >= 0) sah_flush(sb, k, cb[k], cn[k], clo[k], chi[k]);
+            cb[k] = b; cn[k] = 0u;
+            clo[k] = mk(INFINITY, INFINITY, INFINITY);
+            chi[k] = mk(-INFINITY, -INFINITY, -INFINITY);
+          }
+          ++cn[k];
+          clo[k] = mk(fminf(clo[k].x, lo.x), fminf(clo[k].y, lo.y), fminf(clo[k].z, lo.z));
+          chi[k] = mk(fmaxf(chi[k].x, hi.x), fmaxf(chi[k].y, hi.y), fmaxf(chi[k].z, hi.z));
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        if (cb[k] >= 0) sah_flush(sb, k, cb[k], cn[k], clo[k], chi[k]);
+      __syncthreads();
+      if (tid < 3) {
+        SahSplit sp;
+        if (sc[tid] > 0.f) sp = sah_sweep(sb, tid);
+        else { sp.cost = INFINITY; sp.axis = tid; sp.bin = -1; sp.nl = 0; }
+        s_best[tid] = sp;
+      }
+      __syncthreads();
+    }
+    // choose: the cheapest axis (ties to the lower axis), else the median
+    int axis = -1, bin = -1, nl = T.n / 2;
+    float3 llo = blo, lhi = bhi, rlo = blo, rhi = bhi;
+    if (free_split) {
+      float bc = INFINITY;
+      for (int k = 0; k < 3; ++k)
+        if (s_best[k].bin >= 0 && s_best[k].cost < bc) { bc = s_best[k].cost; axis = k; }
+      if (axis >= 0) {
+        bin = s_best[axis].bin; nl = s_best[axis].nl;
+        llo = s_best[axis].llo; lhi = s_best[axis].lhi; rlo = s_best[axis].rlo; rhi = s_best[axis].rhi;
+      }
+    }
+    // stable partition into out[a, a + n)
+    int lbase = 0, rbase = 0;
+    for (int base = 0; base < T.n; base += blockDim.x) {
+      const int i = base + tid;
+      const bool valid = i < T.n;
+      uint32_t p = 0u;
+      bool left = false;
+      if (valid) {
+        p = in[T.a + i];
+        left = axis >= 0 ? sah_bin(comp(S.cen[p], axis), comp3(blo, axis), sc[axis]) <= bin : i < nl;
+      }
+      const unsigned bal = __ballot_sync(kFull, left);
+      if (lane == 0) s_warp[wid] = __popc(bal);
+      __syncthreads();
+      int woff = 0, tot = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        const int c = (int)s_warp[w];
+        if (w < wid) woff += c;
+        tot += c;
+      }
+      const int lrank = woff + __popc(bal & ((1u << lane) - 1u));
+      if (valid) {  // positions stay inside the task even if bins and partition disagreed
+        const int q = left ? lbase + lrank : nl + rbase + (i - base - lrank);
+        if (q < T.n) out[T.a + q] = p;
+      }
+      const int nvalid = min((int)blockDim.x, T.n - base);
+      lbase += tot;
+      rbase += nvalid - tot;
+      __syncthreads();
+    }
+    if (tid == 0) {
+      if (lbase != nl) atomicExch(&B.hdr->corrupt, 1);  // bins and partition disagree: never expected
+      const int s = T.a + nl - 1;
+      int sroot;
+      if (T.parent < 0) {
+        sroot = s;
+        S.st->sroot = s;
+      } else {
+        sroot = S.st->sroot;
+      }
+      const int id = sah_split_id(s, sroot);
+      B.parent[id] = T.parent;
+      if (T.parent >= 0) sah_set_child(B, T.parent, T.sd & 1, id);
+      for (int c = 0; c < 2; ++c) {
+        const int ca = c ? T.a + nl : T.a, cn = c ? T.n - nl : nl;
+        if (cn == 1) {
+          sah_set_child(B, id, c, ~ca);
+          B.parent[n_int + ca] = id;
+          B.leaf_tri[ca] = (int32_t)out[ca];
+        } else if (cn <= kSahSmall) {
+          const int slot = atomicAdd(&S.st->n_small, 1);
+          if (slot < S.max_small) S.small[slot] = make_int4(ca, cn, id, c | ((depth + 1) << 1) | (((level + 1) & 1) << 30));
+          else atomicExch(&B.hdr->corrupt, 1);  // more tasks than disjoint ranges: never expected
+        } else {
+          const int slot = atomicAdd(&S.st->n_large[level + 1], 1);
+          if (slot < S.max_large) {
+            SahTask ct;
+            ct.a = ca; ct.n = cn; ct.parent = id; ct.sd = c | ((depth + 1) << 1);
+            const float3 lo = c ? rlo : llo, hi = c ? rhi : lhi;
+            ct.lo = make_float4(lo.x, lo.y, lo.z, 0.f);
+            ct.hi = make_float4(hi.x, hi.y, hi.z, 0.f);
+            S.tasks[(level + 1) & 1][slot] = ct;
+          } else {
+            atomicExch(&B.hdr->corrupt, 1);
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Small tasks: one warp builds a whole subtree (at most kSahSmall triangles)
+// with the same binned SAH, the range held in shared memory.
+__global__ void __launch_bounds__(32 * kSahSmallWarps) k_sah_small(SahView S, BvhView B) {
+  __shared__ uint32_t s_ids[kSahSmallWarps][kSahSmall], s_tmp[kSahSmallWarps][kSahSmall];
+  __shared__ int4 s_stack[kSahSmallWarps][kSahSmall / 2 + 1];
+  __shared__ SahBinsSmem s_bins[kSahSmallWarps];
+  const int n_int = B.hdr->n_int;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t* ids = s_ids[w];
+  uint32_t* tmp = s_tmp[w];
+  int4* stack = s_stack[w];
+  SahBinsSmem& sb = s_bins[w];
+  const int nsmall = min(S.st->n_small, S.max_small);
+  for (int t = blockIdx.x * kSahSmallWarps + w; t < nsmall; t += gridDim.x * kSahSmallWarps) {
+    const int4 T = S.small[t];
+    const int a = T.x, n = T.y;
+    const uint32_t* in = S.idx[(T.w >> 30) & 1];
+    for (int i = lane; i < n; i += 32) ids[i] = in[a + i];
+    int sroot = T.z < 0 ? -1 : S.st->sroot;
+    int sp = 0;
+    if (lane == 0) stack[0] = make_int4(0, n, T.z, T.w & 0x3fffffff);
+    sp = 1;
+    __syncwarp();
+    while (sp > 0) {
+      --sp;
+      const int4 e = stack[sp];
+      __syncwarp();
+      const int ra = e.x, rn = e.y, par = e.z, side = e.w & 1, depth = e.w >> 1;
+      // centroid bounds of the range
+      float3 lo = mk(INFINITY, INFINITY, INFINITY), hi = mk(-INFINITY, -INFINITY, -INFINITY);
+      for (int i = lane; i < rn; i += 32) {
+        const float4 c = S.cen[ids[ra + i]];
+        lo = mk(fminf(lo.x, c.x), fminf(lo.y, c.y), fminf(lo.z, c.z));
+        hi = mk(fmaxf(hi.x, c.x), fmaxf(hi.y, c.y), fmaxf(hi.z, c.z));
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        lo.x = fminf(lo.x, __shfl_xor_sync(kFull, lo.x, o));
+        lo.y = fminf(lo.y, __shfl_xor_sync(kFull, lo.y, o));
+        lo.z = fminf(lo.z, __shfl_xor_sync(kFull, lo.z, o));
+        hi.x = fmaxf(hi.x, __shfl_xor_sync(kFull, hi.x, o));
+        hi.y = fmaxf(hi.y, __shfl_xor_sync(kFull, hi.y, o));
+        hi.z = fmaxf(hi.z, __shfl_xor_sync(kFull, hi.z, o));
+      }
+      const float sc[3] = {sah_scale(lo.x, hi.x), sah_scale(lo.y, hi.y), sah_scale(lo.z, hi.z)};
+      int axis = -1, bin = -1, nl = rn / 2;
+      if (depth < kSahSmallFreeDepth && (sc[0] > 0.f || sc[1] > 0.f || sc[2] > 0.f)) {
+        for (int i = lane; i < 3 * kSahBins; i += 32) {
+          (&sb.cnt[0][0])[i] = 0u;
+          for (int q = 0; q < 3; ++q) {
+            (&sb.lo[0][0][0])[3 * i + q] = 0xffffffffu;
+            (&sb.hi[0][0][0])[3 * i + q] = 0u;
+          }
+        }
+        __syncwarp();
+        for (int i = lane; i < rn; i += 32) {
+          const uint32_t p = ids[ra + i];
+          const float4 c = S.cen[p], plo = S.pbox[2 * p], phi = S.pbox[2 * p + 1];
+          for (int k = 0; k < 3; ++k) {
+            if (sc[k] <= 0.f) continue;
+            sah_flush(sb, k, sah_bin(comp(c, k), comp3(lo, k), sc[k]), 1u, mk(plo.x, plo.y, plo.z),
+                      mk(phi.x, phi.y, phi.z));
+          }
+        }
+        __syncwarp();
+        SahSplit sp3;
+        sp3.cost = INFINITY; sp3.bin = -1; sp3.axis = lane; sp3.nl = 0;
+        if (lane < 3 && sc[lane] > 0.f) sp3 = sah_sweep(sb, lane);
+        float bc = INFINITY;
+        for (int k = 0; k < 3; ++k) {
+          const float ck = __shfl_sync(kFull, sp3.cost, k);
+          const int bk = __shfl_sync(kFull, sp3.bin, k);
+          if (bk >= 0 && ck < bc) { bc = ck; axis = k; }
+        }
+        if (axis >= 0) {
+          bin = __shfl_sync(kFull, sp3.bin, axis);
+          nl = __shfl_sync(kFull, sp3.nl, axis);
+        }
+        __syncwarp();
+      }
+      // stable partition of ids[ra, ra + rn) through tmp
+      int lbase = 0;
+      int rbase = 0;
+      for (int base = 0; base < rn; base += 32) {
+        const int i = base + lane;
+        const bool valid = i < rn;
+        uint32_t p = 0u;
+        bool left = false;
+        if (valid) {
+          p = ids[ra + i];
+          left = axis >= 0 ? sah_bin(comp(S.cen[p], axis), comp3(lo, axis), sc[axis]) <= bin : i < nl;
+        }
+        const unsigned bal = __ballot_sync(kFull, left);
+        const int lr = __popc(bal & ((1u << lane) - 1u));
+        if (valid) {  // inside the range even if bins and partition disagreed
+          const int q = left ? lbase + lr : nl + rbase + (lane - lr);
+          if (q < rn) tmp[ra + q] = p;
+        }
+        const int tot = __popc(bal);
+        lbase += tot;
+        rbase += min(32, rn - base) - tot;
+      }
+      __syncwarp();
+      for (int i = lane; i < rn; i += 32) ids[ra + i] = tmp[ra + i];
+      __syncwarp();
+      if (lbase != nl && lane == 0) atomicExch(&B.hdr->corrupt, 1);
+      const int s = a + ra + nl - 1;
+      if (par < 0) sroot = s;  // the whole tree is this one task
+      const int id = sah_split_id(s, sroot);
+      if (lane == 0) {
+        B.parent[id] = par;
+        if (par >= 0) sah_set_child(B, par, side, id);
+        if (par < 0) S.st->sroot = s;
+      }
+      for (int c = 1; c >= 0; --c) {
+        const int ca = c ? ra + nl : ra, cn = c ? rn - nl : nl;
+        if (cn == 1) {
+          if (lane == 0) {
+            sah_set_child(B, id, c, ~(a + ca));
+            B.parent[n_int + a + ca] = id;
+          }
+        } else {
+          if (lane == 0) stack[sp] = make_int4(ca, cn, id, c | ((depth + 1) << 1));
+          ++sp;
+        }
+      }
+      __syncwarp();
+    }
+    for (int i = lane; i < n; i += 32) B.leaf_tri[a + i] = (int32_t)ids[i];
+    __syncwarp();
+  }
+}
+
 // ---- the 4-wide BVH ----------------------------------------------------------
 // flag[j] = 1 when binary node j sits at even depth (walks up to the root)
 __global__ void k_even_depth(BvhView B, uint32_t* __restrict__ flag) {
@@ -482,6 +929,7 @@ __global__ void k_bvh_header(BvhHeader* h, int32_t nf) {
 // scratch layout for build/refit
 struct BuildScratch {
   uint32_t *keys_a, *keys_b, *vals_a, *vals_b, *hist, *arrive, *bounds;
+  SahView sah;
   size_t total;
   BuildScratch(void* base, int32_t nf) {
     const int nblocks = (nf + kSortTile - 1) / kSortTile;
@@ -493,11 +941,25 @@ struct BuildScratch {
     const size_t hi = take(sizeof(uint32_t) * 256 * (size_t)nblocks);
     const size_t ar = take(sizeof(uint32_t) * n_int);
     const size_t bo = take(sizeof(uint32_t) * 8);
+    // binned SAH build: centroids, boxes, two task lists per level, small tasks
+    sah.max_large = nf / (kSahSmall + 1) + 1;
+    sah.max_small = nf / 2 + 1;
+    const size_t ce = take(sizeof(float4) * nf), pb = take(sizeof(float4) * 2 * (size_t)nf);
+    const size_t t0 = take(sizeof(SahTask) * sah.max_large), t1 = take(sizeof(SahTask) * sah.max_large);
+    const size_t sm = take(sizeof(int4) * sah.max_small), st = take(sizeof(SahState));
     total = o;
     char* b = (char*)base;
     keys_a = (uint32_t*)(b + ka); keys_b = (uint32_t*)(b + kb);
     vals_a = (uint32_t*)(b + va); vals_b = (uint32_t*)(b + vb);
     hist = (uint32_t*)(b + hi); arrive = (uint32_t*)(b + ar); bounds = (uint32_t*)(b + bo);
+    sah.cen = (float4*)(b + ce);
+    sah.pbox = (float4*)(b + pb);
+    sah.idx[0] = vals_a;
+    sah.idx[1] = vals_b;
+    sah.tasks[0] = (SahTask*)(b + t0);
+    sah.tasks[1] = (SahTask*)(b + t1);
+    sah.small = (int4*)(b + sm);
+    sah.st = (SahState*)(b + st);
   }
 };
 
@@ -521,34 +983,62 @@ void launch_refit(const float* V, const int32_t* F, int32_t nf, void* bvh, void*
   k_node4_boxes<<<grid_for((int64_t)n_int, 256), 256, 0, s>>>(B);
 }
 
+// Binned SAH topology (see above).  Large levels: kSahFreeDepth levels of
+// free splits, then median splits, which halve a task per level, so after
+// ceil(log2(nf / kSahSmall)) + 1 more levels every task is small; small
+// tasks take free splits to depth kSahSmallFreeDepth, then at most
+// log2(kSahSmall) median levels: the tree is at most 63 deep, within the
+// traversal's 64-entry stack.  Levels beyond the last large one launch and
+// return at once (the host does not wait to learn how many there were).
+static void launch_sah_topology(const float* V, const int32_t* F, int32_t nf, BvhView& B, BuildScratch& S,
+                                cudaStream_t s) {
+  k_sah_prims<<<grid_for(nf, 256), 256, 0, s>>>(V, F, nf, S.sah, B);
+  k_sah_root<<<1, 64, 0, s>>>(nf, S.bounds, S.sah);
+  int levels = 0;
+  if (nf > kSahSmall) {
+    int lg = 0;
+    while (((int64_t)kSahSmall << lg) < (int64_t)nf) ++lg;
+    levels = kSahFreeDepth + lg + 2;
+    if (levels > kSahMaxLevels) levels = kSahMaxLevels;
+  }
+  const int grid = 2 * num_sms();
+  for (int L = 0; L < levels; ++L) k_sah_large<<<grid, kSahThreads, 0, s>>>(L, S.sah, B);
+  k_sah_small<<<grid_for(nf / 2 + 1, 32 * kSahSmallWarps), 32 * kSahSmallWarps, 0, s>>>(S.sah, B);
+}
+
 void launch_build(const float* V, const int32_t* F, int32_t nf, void* bvh, void* scratch, cudaStream_t s) {
   BvhView B = bvh_view(bvh, nf);
   BuildScratch S(scratch, nf);
   const int n_int = nf > 1 ? nf - 1 : 1;
+  const bool sah = g_tuning.bvh_builder == 1 && nf > 1;
   {
-    ProfScope ps("lbvh_build", s);
+    ProfScope ps(sah ? "sah_build" : "lbvh_build", s);
     k_bvh_header<<<1, 1, 0, s>>>(B.hdr, nf);
     k_init_bounds<<<1, 32, 0, s>>>(S.bounds);
     k_centroid_bounds<<<grid_for(nf, 256), 256, 0, s>>>(V, F, nf, S.bounds);
-    k_morton<<<grid_for(nf, 256), 256, 0, s>>>(V, F, nf, S.bounds, S.keys_a, S.vals_a);
-    const int nblocks = (nf + kSortTile - 1) / kSortTile;
-    uint32_t *kin = S.keys_a, *vin = S.vals_a, *kout = S.keys_b, *vout = S.vals_b;
-    for (int shift = 0; shift < 32; shift += 8) {
-      k_radix_hist<<<nblocks, kSortThreads, 0, s>>>(kin, nf, shift, S.hist);
-      k_scan_exclusive<<<1, 1024, 0, s>>>(S.hist, 256 * nblocks);
-      k_radix_scatter<<<nblocks, kSortThreads, 0, s>>>(kin, vin, nf, shift, S.hist, kout, vout);
-      uint32_t* t = kin; kin = kout; kout = t;
-      t = vin; vin = vout; vout = t;
-    }
-    // after an even number of passes the sorted data is back in keys_a/vals_a
-    k_gather_leaf_tri<<<grid_for(nf, 256), 256, 0, s>>>(vin, nf, B.leaf_tri);
-    if (nf > 1) {
-      k_karras<<<grid_for(nf - 1, 256), 256, 0, s>>>(kin, nf, B.bin_child, B.parent);
+    if (sah) {
+      launch_sah_topology(V, F, nf, B, S, s);
     } else {
-      k_single_leaf<<<1, 1, 0, s>>>(B.bin_child, B.parent);
+      k_morton<<<grid_for(nf, 256), 256, 0, s>>>(V, F, nf, S.bounds, S.keys_a, S.vals_a);
+      const int nblocks = (nf + kSortTile - 1) / kSortTile;
+      uint32_t *kin = S.keys_a, *vin = S.vals_a, *kout = S.keys_b, *vout = S.vals_b;
+      for (int shift = 0; shift < 32; shift += 8) {
+        k_radix_hist<<<nblocks, kSortThreads, 0, s>>>(kin, nf, shift, S.hist);
+        k_scan_exclusive<<<1, 1024, 0, s>>>(S.hist, 256 * nblocks);
+        k_radix_scatter<<<nblocks, kSortThreads, 0, s>>>(kin, vin, nf, shift, S.hist, kout, vout);
+        uint32_t* t = kin; kin = kout; kout = t;
+        t = vin; vin = vout; vout = t;
+      }
+      // after an even number of passes the sorted data is back in keys_a/vals_a
+      k_gather_leaf_tri<<<grid_for(nf, 256), 256, 0, s>>>(vin, nf, B.leaf_tri);
+      if (nf > 1) {
+        k_karras<<<grid_for(nf - 1, 256), 256, 0, s>>>(kin, nf, B.bin_child, B.parent);
+      } else {
+        k_single_leaf<<<1, 1, 0, s>>>(B.bin_child, B.parent);
+      }
     }
     // 4-wide topology: even-depth nodes, numbered by a scan
-    uint32_t* flag = S.keys_b;  // free after the sort
+    uint32_t* flag = S.keys_b;  // free after the sort (unused by the SAH build)
     k_even_depth<<<grid_for(n_int, 256), 256, 0, s>>>(B, flag);
     k_scan_exclusive<<<1, 1024, 0, s>>>(flag, n_int);
     k_bin_to4<<<grid_for(n_int, 256), 256, 0, s>>>(B, flag);
