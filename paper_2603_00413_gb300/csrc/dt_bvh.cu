@@ -344,40 +344,53 @@ __global__ void k_refit(const float* __restrict__ V, const int32_t* __restrict__
 // bin boundaries (16 centroid bins per axis) with the least surface area cost
 // area(left box) * left count + area(right box) * right count, and the range
 // is partitioned stably into [left | right].  Tasks larger than kSahSmall
-// take one launch per tree level, one CTA per task; smaller tasks are built
+// take four launches per tree level, each spread over chunks of kSahChunk
+// positions so that the few huge tasks near the root use the whole GPU: bin
+// (per-chunk shared-memory bins added into the task's bins), split (one warp
+// per task), count (left primitives per chunk) and scatter (stable, each
+// chunk at the offset of the chunks before it).  Smaller tasks are built
 // down to their leaves by one warp each, in shared memory.  An internal node
 // is numbered by its split position s (the last position of its left child),
 // which is unique in [0, nf - 2]; the root's number is swapped with 0 so the
 // root is node 0.  Splits deeper than kSahFreeDepth (large tasks) or
 // kSahSmallFreeDepth (small ones) take the median, which bounds the depth
-// (see launch_build).  Every decision is a deterministic function of the
-// geometry: bins are sums, minima and maxima, and partitions are stable.
+// (see launch_sah_topology).  Every decision is a deterministic function of
+// the geometry: bins are integer sums, minima and maxima, and partitions are
+// stable.
 constexpr int kSahBins = 16;
 constexpr int kSahSmall = 128;
 constexpr int kSahFreeDepth = 24;
 constexpr int kSahSmallFreeDepth = 56;
 constexpr int kSahMaxLevels = 64;
-constexpr int kSahThreads = 512;
+constexpr int kSahChunk = 4096;
+constexpr int kSahThreads = 256;
 constexpr int kSahSmallWarps = 4;
 
 struct SahTask {
-  int a, n, parent, sd;  // first position, count, parent node, side | depth << 1
-  float4 lo, hi;         // binning bounds (xyz), a superset of the centroids
+  int a, n, parent, sd;       // range, parent node, side | depth << 1
+  int chunk0, axis, bin, nl;  // first chunk of the level; the split (axis < 0: median)
+  float4 lo, hi;              // binning bounds (xyz), a superset of the centroids
+};
+struct SahBins {  // order-preserving uints for the float bounds
+  uint32_t cnt[3][kSahBins];
+  uint32_t lo[3][kSahBins][3];
+  uint32_t hi[3][kSahBins][3];
 };
 struct SahState {
-  int n_large[kSahMaxLevels + 2];
+  unsigned long long packed[kSahMaxLevels + 2];  // per level: tasks << 32 | chunks
   int n_small;
   int sroot;
-  int overflow;
 };
 struct SahView {
   float4* cen;
   float4* pbox;
   uint32_t* idx[2];
   SahTask* tasks[2];
+  SahBins* bins[2];
+  uint32_t* chunk_left;
   int4* small;  // (a, n, parent, side | depth << 1 | buffer << 30)
   SahState* st;
-  int max_large, max_small;
+  int max_large, max_small, max_chunks;
 };
 
 __device__ __forceinline__ int sah_bin(float c, float lo, float scale) {
@@ -421,21 +434,38 @@ __global__ void k_sah_prims(const float* __restrict__ V, const int32_t* __restri
   }
 }
 
+__device__ __forceinline__ int sah_chunks(int n) { return (n + kSahChunk - 1) / kSahChunk; }
+
+// empty bins: zero counts, inverted bounds (threads i0, i0 + stride, ...)
+__device__ __forceinline__ void sah_zero_bins(SahBins* g, int i0, int stride) {
+  uint32_t* cnt = &g->cnt[0][0];
+  uint32_t* lo = &g->lo[0][0][0];
+  uint32_t* hi = &g->hi[0][0][0];
+  for (int i = i0; i < 3 * kSahBins; i += stride) {
+    cnt[i] = 0u;
+    for (int q = 0; q < 3; ++q) {
+      lo[3 * i + q] = 0xffffffffu;
+      hi[3 * i + q] = 0u;
+    }
+  }
+}
+
 // the root task: large (level 0) or, for at most kSahSmall triangles, small
 __global__ void k_sah_root(int32_t nf, const uint32_t* __restrict__ bounds, SahView S) {
-  for (int i = threadIdx.x; i < kSahMaxLevels + 2; i += blockDim.x) S.st->n_large[i] = 0;
+  for (int i = threadIdx.x; i < kSahMaxLevels + 2; i += blockDim.x) S.st->packed[i] = 0ull;
+  if (nf > kSahSmall) sah_zero_bins(&S.bins[0][0], threadIdx.x, blockDim.x);
+  __syncthreads();
   if (threadIdx.x == 0) {
     S.st->sroot = -1;
-    S.st->overflow = 0;
+    S.st->n_small = 0;
     if (nf > kSahSmall) {
       SahTask t;
       t.a = 0; t.n = nf; t.parent = -1; t.sd = 0;
+      t.chunk0 = 0; t.axis = -1; t.bin = -1; t.nl = 0;
       t.lo = make_float4(ord2f(bounds[0]), ord2f(bounds[1]), ord2f(bounds[2]), 0.f);
       t.hi = make_float4(ord2f(bounds[3]), ord2f(bounds[4]), ord2f(bounds[5]), 0.f);
       S.tasks[0][0] = t;
-      S.st->n_small = 0;
-      __threadfence();
-      S.st->n_large[0] = 1;
+      S.st->packed[0] = (1ull << 32) | (unsigned long long)sah_chunks(nf);
     } else {
       S.small[0] = make_int4(0, nf, -1, 0);
       S.st->n_small = 1;
@@ -443,13 +473,7 @@ __global__ void k_sah_root(int32_t nf, const uint32_t* __restrict__ bounds, SahV
   }
 }
 
-struct SahBinsSmem {
-  uint32_t cnt[3][kSahBins];
-  uint32_t lo[3][kSahBins][3];
-  uint32_t hi[3][kSahBins][3];
-};
-
-__device__ __forceinline__ void sah_flush(SahBinsSmem& sb, int k, int b, uint32_t n, float3 lo, float3 hi) {
+__device__ __forceinline__ void sah_flush(SahBins& sb, int k, int b, uint32_t n, float3 lo, float3 hi) {
   atomicAdd(&sb.cnt[k][b], n);
   atomicMin(&sb.lo[k][b][0], f2ord(lo.x)); atomicMin(&sb.lo[k][b][1], f2ord(lo.y)); atomicMin(&sb.lo[k][b][2], f2ord(lo.z));
   atomicMax(&sb.hi[k][b][0], f2ord(hi.x)); atomicMax(&sb.hi[k][b][1], f2ord(hi.y)); atomicMax(&sb.hi[k][b][2], f2ord(hi.z));
@@ -461,7 +485,7 @@ struct SahSplit {
   int axis, bin, nl;
   float3 llo, lhi, rlo, rhi;
 };
-__device__ SahSplit sah_sweep(const SahBinsSmem& sb, int k) {
+__device__ SahSplit sah_sweep(const SahBins& sb, int k) {
   SahSplit best;
   best.cost = INFINITY; best.axis = k; best.bin = -1; best.nl = 0;
   float rarea[kSahBins];
@@ -505,112 +529,138 @@ __device__ SahSplit sah_sweep(const SahBinsSmem& sb, int k) {
   return best;
 }
 
-// One tree level of the large tasks: one CTA per task.
-__global__ void __launch_bounds__(kSahThreads) k_sah_large(int level, SahView S, BvhView B) {
-  __shared__ SahBinsSmem sb;
-  __shared__ SahSplit s_best[3];
-  __shared__ uint32_t s_warp[kSahThreads / 32];
-  const int n_int = B.hdr->n_int;
-  const int ntask = min(S.st->n_large[level], S.max_large);
+// the task that owns chunk c (tasks are in chunk order: slot and chunks come
+// from one 64-bit atomic)
+__device__ __forceinline__ int sah_find_task(const SahTask* tasks, int ntask, int c) {
+  int lo = 0, hi = ntask - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tasks[mid].chunk0 <= c) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+struct SahLevel {
+  int ntask, nchunk;
+};
+__device__ __forceinline__ SahLevel sah_level(const SahView& S, int level) {
+  const unsigned long long pk = S.st->packed[level];
+  SahLevel l;
+  l.ntask = min((int)(pk >> 32), S.max_large);
+  l.nchunk = min((int)(pk & 0xffffffffull), S.max_chunks);
+  return l;
+}
+
+__device__ __forceinline__ bool sah_free(const SahTask& T, float sc[3]) {
+  sc[0] = sah_scale(T.lo.x, T.hi.x);
+  sc[1] = sah_scale(T.lo.y, T.hi.y);
+  sc[2] = sah_scale(T.lo.z, T.hi.z);
+  return (T.sd >> 1) < kSahFreeDepth && (sc[0] > 0.f || sc[1] > 0.f || sc[2] > 0.f);
+}
+
+__device__ __forceinline__ bool sah_goes_left(const SahView& S, const SahTask& T, const float sc[3], uint32_t p, int i) {
+  if (T.axis < 0) return i < T.nl;
+  const float4 c = S.cen[p];
+  return sah_bin(comp(c, T.axis), comp(T.lo, T.axis), sc[T.axis]) <= T.bin;
+}
+
+// 1/4 of a level: the bins of every task, chunk by chunk
+__global__ void __launch_bounds__(kSahThreads) k_sah_bin(int level, SahView S) {
+  __shared__ SahBins sb;
+  const SahLevel L = sah_level(S, level);
   const SahTask* tasks = S.tasks[level & 1];
   const uint32_t* __restrict__ in = S.idx[level & 1];
-  uint32_t* out = S.idx[(level + 1) & 1];
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  for (int t = blockIdx.x; t < ntask; t += gridDim.x) {
+  const int tid = threadIdx.x;
+  for (int c = blockIdx.x; c < L.nchunk; c += gridDim.x) {
+    const int t = sah_find_task(tasks, L.ntask, c);
     const SahTask T = tasks[t];
+    float sc[3];
+    if (!sah_free(T, sc)) continue;  // uniform over the block
+    sah_zero_bins(&sb, tid, blockDim.x);
+    __syncthreads();
+    const int q0 = T.a + (c - T.chunk0) * kSahChunk, q1 = min(T.a + T.n, q0 + kSahChunk);
+    // each thread bins a contiguous run, adding runs of equal bins at once
+    const int run = (q1 - q0 + blockDim.x - 1) / blockDim.x;
+    const int p0 = q0 + tid * run, p1 = min(q1, p0 + run);
+    int cb[3] = {-1, -1, -1};
+    uint32_t cn[3] = {0u, 0u, 0u};
+    float3 clo[3], chi[3];
+    for (int pos = p0; pos < p1; ++pos) {
+      const uint32_t p = in[pos];
+      const float4 c4 = S.cen[p], lo = S.pbox[2 * p], hi = S.pbox[2 * p + 1];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        if (sc[k] <= 0.f) continue;
+        const int b = sah_bin(comp(c4, k), comp(T.lo, k), sc[k]);
+        if (b != cb[k]) {
+          if (cb[k] >= 0) sah_flush(sb, k, cb[k], cn[k], clo[k], chi[k]);
+          cb[k] = b; cn[k] = 0u;
+          clo[k] = mk(INFINITY, INFINITY, INFINITY);
+          chi[k] = mk(-INFINITY, -INFINITY, -INFINITY);
+        }
+        ++cn[k];
+        clo[k] = mk(fminf(clo[k].x, lo.x), fminf(clo[k].y, lo.y), fminf(clo[k].z, lo.z));
+        chi[k] = mk(fmaxf(chi[k].x, hi.x), fmaxf(chi[k].y, hi.y), fmaxf(chi[k].z, hi.z));
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      if (cb[k] >= 0) sah_flush(sb, k, cb[k], cn[k], clo[k], chi[k]);
+    __syncthreads();
+    SahBins& G = S.bins[level & 1][t];
+    for (int i = tid; i < 3 * kSahBins; i += blockDim.x) {
+      const int k = i / kSahBins, b = i % kSahBins;
+      if (!sb.cnt[k][b]) continue;
+      atomicAdd(&G.cnt[k][b], sb.cnt[k][b]);
+      for (int q = 0; q < 3; ++q) {
+        atomicMin(&G.lo[k][b][q], sb.lo[k][b][q]);
+        atomicMax(&G.hi[k][b][q], sb.hi[k][b][q]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// 2/4: one warp per task chooses the split, numbers the node, links it to
+// its parent and queues the children (large ones for the next level with
+// cleared bins, the rest for the warp builder)
+__global__ void __launch_bounds__(128) k_sah_split(int level, SahView S, BvhView B) {
+  const SahLevel L = sah_level(S, level);
+  SahTask* tasks = S.tasks[level & 1];
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  for (int t = gw; t < L.ntask; t += nw) {
+    SahTask T = tasks[t];
     const int depth = T.sd >> 1;
-    const float3 blo = mk(T.lo.x, T.lo.y, T.lo.z), bhi = mk(T.hi.x, T.hi.y, T.hi.z);
-    const float sc[3] = {sah_scale(blo.x, bhi.x), sah_scale(blo.y, bhi.y), sah_scale(blo.z, bhi.z)};
-    const bool free_split = depth < kSahFreeDepth && (sc[0] > 0.f || sc[1] > 0.f || sc[2] > 0.f);
-    if (free_split) {
-      for (int i = tid; i < 3 * kSahBins; i += blockDim.x) {
-        (&sb.cnt[0][0])[i] = 0u;
-        for (int q = 0; q < 3; ++q) {
-          (&sb.lo[0][0][0])[3 * i + q] = 0xffffffffu;
-          (&sb.hi[0][0][0])[3 * i + q] = 0u;
-        }
-      }
-      __syncthreads();
-      // each thread bins a contiguous run, adding runs of equal bins at once
-      const int run = (T.n + blockDim.x - 1) / blockDim.x;
-      const int p0 = T.a + tid * run, p1 = min(T.a + T.n, p0 + run);
-      int cb[3] = {-1, -1, -1};
-      uint32_t cn[3] = {0u, 0u, 0u};
-      float3 clo[3], chi[3];
-      for (int pos = p0; pos < p1; ++pos) {
-        const uint32_t p = in[pos];
-        const float4 c = S.cen[p], lo = S.pbox[2 * p], hi = S.pbox[2 * p + 1];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          if (sc[k] <= 0.f) continue;
-          const int b = sah_bin(comp(c, k), comp3(blo, k), sc[k]);
-          if (b != cb[k]) {
-            if (cb[k] >= 0) sah_flush(sb, k, cb[k], cn[k], clo[k], chi[k]);
-            cb[k] = b; cn[k] = 0u;
-            clo[k] = mk(INFINITY, INFINITY, INFINITY);
-            chi[k] = mk(-INFINITY, -INFINITY, -INFINITY);
-          }
-          ++cn[k];
-          clo[k] = mk(fminf(clo[k].x, lo.x), fminf(clo[k].y, lo.y), fminf(clo[k].z, lo.z));
-          chi[k] = mk(fmaxf(chi[k].x, hi.x), fmaxf(chi[k].y, hi.y), fmaxf(chi[k].z, hi.z));
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < 3; ++k)
-        if (cb[k] >= 0) sah_flush(sb, k, cb[k], cn[k], clo[k], chi[k]);
-      __syncthreads();
-      if (tid < 3) {
-        SahSplit sp;
-        if (sc[tid] > 0.f) sp = sah_sweep(sb, tid);
-        else { sp.cost = INFINITY; sp.axis = tid; sp.bin = -1; sp.nl = 0; }
-        s_best[tid] = sp;
-      }
-      __syncthreads();
-    }
-    // choose: the cheapest axis (ties to the lower axis), else the median
+    float sc[3];
     int axis = -1, bin = -1, nl = T.n / 2;
-    float3 llo = blo, lhi = bhi, rlo = blo, rhi = bhi;
-    if (free_split) {
+    float3 llo = mk(T.lo.x, T.lo.y, T.lo.z), lhi = mk(T.hi.x, T.hi.y, T.hi.z), rlo = llo, rhi = lhi;
+    if (sah_free(T, sc)) {
+      const SahBins& G = S.bins[level & 1][t];
+      SahSplit sp;
+      sp.cost = INFINITY; sp.bin = -1; sp.axis = lane; sp.nl = 0;
+      if (lane < 3 && sc[lane] > 0.f) sp = sah_sweep(G, lane);
       float bc = INFINITY;
-      for (int k = 0; k < 3; ++k)
-        if (s_best[k].bin >= 0 && s_best[k].cost < bc) { bc = s_best[k].cost; axis = k; }
+      for (int k = 0; k < 3; ++k) {
+        const float ck = __shfl_sync(kFull, sp.cost, k);
+        const int bk = __shfl_sync(kFull, sp.bin, k);
+        if (bk >= 0 && ck < bc) { bc = ck; axis = k; }
+      }
       if (axis >= 0) {
-        bin = s_best[axis].bin; nl = s_best[axis].nl;
-        llo = s_best[axis].llo; lhi = s_best[axis].lhi; rlo = s_best[axis].rlo; rhi = s_best[axis].rhi;
+        bin = __shfl_sync(kFull, sp.bin, axis);
+        nl = __shfl_sync(kFull, sp.nl, axis);
+        llo = mk(__shfl_sync(kFull, sp.llo.x, axis), __shfl_sync(kFull, sp.llo.y, axis), __shfl_sync(kFull, sp.llo.z, axis));
+        lhi = mk(__shfl_sync(kFull, sp.lhi.x, axis), __shfl_sync(kFull, sp.lhi.y, axis), __shfl_sync(kFull, sp.lhi.z, axis));
+        rlo = mk(__shfl_sync(kFull, sp.rlo.x, axis), __shfl_sync(kFull, sp.rlo.y, axis), __shfl_sync(kFull, sp.rlo.z, axis));
+        rhi = mk(__shfl_sync(kFull, sp.rhi.x, axis), __shfl_sync(kFull, sp.rhi.y, axis), __shfl_sync(kFull, sp.rhi.z, axis));
       }
     }
-    // stable partition into out[a, a + n)
-    int lbase = 0, rbase = 0;
-    for (int base = 0; base < T.n; base += blockDim.x) {
-      const int i = base + tid;
-      const bool valid = i < T.n;
-      uint32_t p = 0u;
-      bool left = false;
-      if (valid) {
-        p = in[T.a + i];
-        left = axis >= 0 ? sah_bin(comp(S.cen[p], axis), comp3(blo, axis), sc[axis]) <= bin : i < nl;
-      }
-      const unsigned bal = __ballot_sync(kFull, left);
-      if (lane == 0) s_warp[wid] = __popc(bal);
-      __syncthreads();
-      int woff = 0, tot = 0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-        const int c = (int)s_warp[w];
-        if (w < wid) woff += c;
-        tot += c;
-      }
-      const int lrank = woff + __popc(bal & ((1u << lane) - 1u));
-      if (valid) {  // positions stay inside the task even if bins and partition disagreed
-        const int q = left ? lbase + lrank : nl + rbase + (i - base - lrank);
-        if (q < T.n) out[T.a + q] = p;
-      }
-      const int nvalid = min((int)blockDim.x, T.n - base);
-      lbase += tot;
-      rbase += nvalid - tot;
-      __syncthreads();
-    }
-    if (tid == 0) {
-      if (lbase != nl) atomicExch(&B.hdr->corrupt, 1);  // bins and partition disagree: never expected
+    int child_slot[2] = {-1, -1};
+    if (lane == 0) {
+      tasks[t].axis = axis;
+      tasks[t].bin = bin;
+      tasks[t].nl = nl;
       const int s = T.a + nl - 1;
       int sroot;
       if (T.parent < 0) {
@@ -624,30 +674,109 @@ __global__ void __launch_bounds__(kSahThreads) k_sah_large(int level, SahView S,
       if (T.parent >= 0) sah_set_child(B, T.parent, T.sd & 1, id);
       for (int c = 0; c < 2; ++c) {
         const int ca = c ? T.a + nl : T.a, cn = c ? T.n - nl : nl;
-        if (cn == 1) {
-          sah_set_child(B, id, c, ~ca);
-          B.parent[n_int + ca] = id;
-          B.leaf_tri[ca] = (int32_t)out[ca];
-        } else if (cn <= kSahSmall) {
+        if (cn <= kSahSmall) {  // (one triangle: the warp builder writes the leaf)
           const int slot = atomicAdd(&S.st->n_small, 1);
           if (slot < S.max_small) S.small[slot] = make_int4(ca, cn, id, c | ((depth + 1) << 1) | (((level + 1) & 1) << 30));
           else atomicExch(&B.hdr->corrupt, 1);  // more tasks than disjoint ranges: never expected
         } else {
-          const int slot = atomicAdd(&S.st->n_large[level + 1], 1);
-          if (slot < S.max_large) {
+          const unsigned long long old =
+              atomicAdd(&S.st->packed[level + 1], (1ull << 32) | (unsigned long long)sah_chunks(cn));
+          const int slot = (int)(old >> 32), chunk0 = (int)(old & 0xffffffffull);
+          if (slot < S.max_large && chunk0 + sah_chunks(cn) <= S.max_chunks) {
             SahTask ct;
             ct.a = ca; ct.n = cn; ct.parent = id; ct.sd = c | ((depth + 1) << 1);
+            ct.chunk0 = chunk0; ct.axis = -1; ct.bin = -1; ct.nl = 0;
             const float3 lo = c ? rlo : llo, hi = c ? rhi : lhi;
             ct.lo = make_float4(lo.x, lo.y, lo.z, 0.f);
             ct.hi = make_float4(hi.x, hi.y, hi.z, 0.f);
             S.tasks[(level + 1) & 1][slot] = ct;
+            child_slot[c] = slot;
           } else {
             atomicExch(&B.hdr->corrupt, 1);
           }
         }
       }
     }
+    for (int c = 0; c < 2; ++c) {
+      const int slot = __shfl_sync(kFull, child_slot[c], 0);
+      if (slot >= 0) sah_zero_bins(&S.bins[(level + 1) & 1][slot], lane, 32);
+    }
+  }
+}
+
+// 3/4: left primitives of every chunk
+__global__ void __launch_bounds__(kSahThreads) k_sah_count(int level, SahView S) {
+  __shared__ int s_sum;
+  const SahLevel L = sah_level(S, level);
+  const SahTask* tasks = S.tasks[level & 1];
+  const uint32_t* __restrict__ in = S.idx[level & 1];
+  for (int c = blockIdx.x; c < L.nchunk; c += gridDim.x) {
+    const SahTask T = tasks[sah_find_task(tasks, L.ntask, c)];
+    float sc[3];
+    sah_free(T, sc);
+    if (threadIdx.x == 0) s_sum = 0;
     __syncthreads();
+    const int i0 = (c - T.chunk0) * kSahChunk, i1 = min(T.n, i0 + kSahChunk);
+    int cnt = 0;
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) cnt += sah_goes_left(S, T, sc, in[T.a + i], i) ? 1 : 0;
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(kFull, cnt, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&s_sum, cnt);
+    __syncthreads();
+    if (threadIdx.x == 0) S.chunk_left[c] = (uint32_t)s_sum;
+    __syncthreads();
+  }
+}
+
+// 4/4: stable scatter of every chunk to [left | right] of its task
+__global__ void __launch_bounds__(kSahThreads) k_sah_scatter(int level, SahView S, BvhView B) {
+  __shared__ uint32_t s_warp[kSahThreads / 32];
+  __shared__ int s_prefix;
+  const SahLevel L = sah_level(S, level);
+  const SahTask* tasks = S.tasks[level & 1];
+  const uint32_t* __restrict__ in = S.idx[level & 1];
+  uint32_t* out = S.idx[(level + 1) & 1];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int c = blockIdx.x; c < L.nchunk; c += gridDim.x) {
+    const SahTask T = tasks[sah_find_task(tasks, L.ntask, c)];
+    float sc[3];
+    sah_free(T, sc);
+    if (tid == 0) s_prefix = 0;
+    __syncthreads();
+    int pre = 0;
+    for (int j = T.chunk0 + tid; j < c; j += blockDim.x) pre += (int)S.chunk_left[j];
+    for (int o = 16; o > 0; o >>= 1) pre += __shfl_xor_sync(kFull, pre, o);
+    if (lane == 0 && pre) atomicAdd(&s_prefix, pre);
+    __syncthreads();
+    const int i0 = (c - T.chunk0) * kSahChunk, i1 = min(T.n, i0 + kSahChunk);
+    int lbase = s_prefix, rbase = i0 - s_prefix;
+    for (int base = i0; base < i1; base += blockDim.x) {
+      const int i = base + tid;
+      const bool valid = i < i1;
+      uint32_t p = 0u;
+      bool left = false;
+      if (valid) {
+        p = in[T.a + i];
+        left = sah_goes_left(S, T, sc, p, i);
+      }
+      const unsigned bal = __ballot_sync(kFull, left);
+      if (lane == 0) s_warp[wid] = __popc(bal);
+      __syncthreads();
+      int woff = 0, tot = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        const int cw = (int)s_warp[w];
+        if (w < wid) woff += cw;
+        tot += cw;
+      }
+      const int lrank = woff + __popc(bal & ((1u << lane) - 1u));
+      if (valid) {  // positions stay inside the task even if bins and partition disagreed
+        const int q = left ? lbase + lrank : T.nl + rbase + (i - base - lrank);
+        if (q < T.n) out[T.a + q] = p;
+      }
+      lbase += tot;
+      rbase += min((int)blockDim.x, i1 - base) - tot;
+      __syncthreads();
+    }
+    if (tid == 0 && i1 == T.n && lbase != T.nl) atomicExch(&B.hdr->corrupt, 1);  // never expected
   }
 }
 
@@ -656,18 +785,26 @@ __global__ void __launch_bounds__(kSahThreads) k_sah_large(int level, SahView S,
 __global__ void __launch_bounds__(32 * kSahSmallWarps) k_sah_small(SahView S, BvhView B) {
   __shared__ uint32_t s_ids[kSahSmallWarps][kSahSmall], s_tmp[kSahSmallWarps][kSahSmall];
   __shared__ int4 s_stack[kSahSmallWarps][kSahSmall / 2 + 1];
-  __shared__ SahBinsSmem s_bins[kSahSmallWarps];
+  __shared__ SahBins s_bins[kSahSmallWarps];
   const int n_int = B.hdr->n_int;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint32_t* ids = s_ids[w];
   uint32_t* tmp = s_tmp[w];
   int4* stack = s_stack[w];
-  SahBinsSmem& sb = s_bins[w];
+  SahBins& sb = s_bins[w];
   const int nsmall = min(S.st->n_small, S.max_small);
   for (int t = blockIdx.x * kSahSmallWarps + w; t < nsmall; t += gridDim.x * kSahSmallWarps) {
     const int4 T = S.small[t];
     const int a = T.x, n = T.y;
     const uint32_t* in = S.idx[(T.w >> 30) & 1];
+    if (n == 1) {  // a one-triangle child of a large task
+      if (lane == 0) {
+        sah_set_child(B, T.z, T.w & 1, ~a);
+        B.parent[n_int + a] = T.z;
+        B.leaf_tri[a] = (int32_t)in[a];
+      }
+      continue;
+    }
     for (int i = lane; i < n; i += 32) ids[i] = in[a + i];
     int sroot = T.z < 0 ? -1 : S.st->sroot;
     int sp = 0;
@@ -697,13 +834,7 @@ __global__ void __launch_bounds__(32 * kSahSmallWarps) k_sah_small(SahView S, Bv
       const float sc[3] = {sah_scale(lo.x, hi.x), sah_scale(lo.y, hi.y), sah_scale(lo.z, hi.z)};
       int axis = -1, bin = -1, nl = rn / 2;
       if (depth < kSahSmallFreeDepth && (sc[0] > 0.f || sc[1] > 0.f || sc[2] > 0.f)) {
-        for (int i = lane; i < 3 * kSahBins; i += 32) {
-          (&sb.cnt[0][0])[i] = 0u;
-          for (int q = 0; q < 3; ++q) {
-            (&sb.lo[0][0][0])[3 * i + q] = 0xffffffffu;
-            (&sb.hi[0][0][0])[3 * i + q] = 0u;
-          }
-        }
+        sah_zero_bins(&sb, lane, 32);
         __syncwarp();
         for (int i = lane; i < rn; i += 32) {
           const uint32_t p = ids[ra + i];
@@ -941,11 +1072,15 @@ struct BuildScratch {
     const size_t hi = take(sizeof(uint32_t) * 256 * (size_t)nblocks);
     const size_t ar = take(sizeof(uint32_t) * n_int);
     const size_t bo = take(sizeof(uint32_t) * 8);
-    // binned SAH build: centroids, boxes, two task lists per level, small tasks
+    // binned SAH build: centroids, boxes, task lists and bins of two levels,
+    // left counts per chunk, small tasks
     sah.max_large = nf / (kSahSmall + 1) + 1;
-    sah.max_small = nf / 2 + 1;
+    sah.max_small = nf + 1;
+    sah.max_chunks = nf / kSahChunk + sah.max_large + 1;
     const size_t ce = take(sizeof(float4) * nf), pb = take(sizeof(float4) * 2 * (size_t)nf);
     const size_t t0 = take(sizeof(SahTask) * sah.max_large), t1 = take(sizeof(SahTask) * sah.max_large);
+    const size_t b0 = take(sizeof(SahBins) * sah.max_large), b1 = take(sizeof(SahBins) * sah.max_large);
+    const size_t cl = take(sizeof(uint32_t) * sah.max_chunks);
     const size_t sm = take(sizeof(int4) * sah.max_small), st = take(sizeof(SahState));
     total = o;
     char* b = (char*)base;
@@ -958,6 +1093,9 @@ struct BuildScratch {
     sah.idx[1] = vals_b;
     sah.tasks[0] = (SahTask*)(b + t0);
     sah.tasks[1] = (SahTask*)(b + t1);
+    sah.bins[0] = (SahBins*)(b + b0);
+    sah.bins[1] = (SahBins*)(b + b1);
+    sah.chunk_left = (uint32_t*)(b + cl);
     sah.small = (int4*)(b + sm);
     sah.st = (SahState*)(b + st);
   }
@@ -1001,8 +1139,17 @@ static void launch_sah_topology(const float* V, const int32_t* F, int32_t nf, Bv
     levels = kSahFreeDepth + lg + 2;
     if (levels > kSahMaxLevels) levels = kSahMaxLevels;
   }
-  const int grid = 2 * num_sms();
-  for (int L = 0; L < levels; ++L) k_sah_large<<<grid, kSahThreads, 0, s>>>(L, S.sah, B);
+  const int grid = 4 * num_sms();
+  {
+    ProfScope ps("sah_large_levels", s);
+    for (int L = 0; L < levels; ++L) {
+      k_sah_bin<<<grid, kSahThreads, 0, s>>>(L, S.sah);
+      k_sah_split<<<grid_for(S.sah.max_large * 32, 128), 128, 0, s>>>(L, S.sah, B);
+      k_sah_count<<<grid, kSahThreads, 0, s>>>(L, S.sah);
+      k_sah_scatter<<<grid, kSahThreads, 0, s>>>(L, S.sah, B);
+    }
+  }
+  ProfScope ps("sah_small", s);
   k_sah_small<<<grid_for(nf / 2 + 1, 32 * kSahSmallWarps), 32 * kSahSmallWarps, 0, s>>>(S.sah, B);
 }
 
