@@ -27,15 +27,18 @@ struct BwsLayout {
     off_buf0 = 0;
     off_buf1 = align_up(off_buf0 + lvl, 256);
     off_dN = align_up(off_buf1 + lvl, 256);
-    total = align_up(off_dN + (size_t)nv * 3 * sizeof(float), 256);
+    total = align_up(off_dN + (size_t)nv * 2 * sizeof(float4), 256);
   }
 };
 
-__device__ __forceinline__ void atomic_add3(float* p, float3 v) {
-  atomicAdd(p, v.x);
-  atomicAdd(p + 1, v.y);
-  atomicAdd(p + 2, v.z);
-}
+// one 128-bit vector atomic per vertex (the accumulators are float4 per
+// vertex, w unused)
+__device__ __forceinline__ void atomic_add4(float4* p, float3 v) { atomicAdd(p, make_float4(v.x, v.y, v.z, 0.f)); }
+
+// Per-scene gradient accumulators in the backward scratch: dN4 then dV4, nv
+// float4 each; the entry's dN pointer holds their start.
+__device__ __forceinline__ float4* acc_dN4(const SceneEntry& E) { return reinterpret_cast<float4*>(E.dN); }
+__device__ __forceinline__ float4* acc_dV4(const SceneEntry& E) { return reinterpret_cast<float4*>(E.dN) + E.nv; }
 
 // Per-block sums of the IoR and sigma gradients, one slot per scene; a thread
 // adds its running sums when its scene changes and at the end.
@@ -55,8 +58,10 @@ struct SceneSums {
 // parent).  Each entry is 3 float4 (xyz used).
 // kBatch = false: one scene, whose entry E0 arrives as a kernel parameter;
 // true: each segment looks its scene up.
+constexpr int kAdjointMinBlocks = 3;  // CTAs of 256 per SM the register budget is sized for
+
 template <bool kBatch>
-__global__ void __launch_bounds__(256) k_adjoint(WsView W, int k, const float4* __restrict__ out_next,
+__global__ void __launch_bounds__(256, kAdjointMinBlocks) k_adjoint(WsView W, int k, const float4* __restrict__ out_next,
                                                  float4* __restrict__ out_cur, const SceneEntry E0) {
   extern __shared__ float sums_smem[];
   const WsHeader* H = W.hdr;
@@ -178,9 +183,10 @@ __global__ void __launch_bounds__(256) k_adjoint(WsView W, int k, const float4* 
         const float3 nbar = h.entering ? nsbar : -nsbar;
         const float3 mbar = (nbar - h.n * dot(h.n, nbar)) * (1.0f / h.lm);
         // m = b0 N0 + b1 N1 + b2 N2
-        atomic_add3(E.dN + 3 * i0, mbar * b0);
-        atomic_add3(E.dN + 3 * i1, mbar * b1);
-        atomic_add3(E.dN + 3 * i2, mbar * b2);
+        float4* dN4 = acc_dN4(E);
+        atomic_add4(dN4 + i0, mbar * b0);
+        atomic_add4(dN4 + i1, mbar * b1);
+        atomic_add4(dN4 + i2, mbar * b2);
         const float b0b = dot(N0, mbar);
         const float b1b = dot(N1, mbar) - b0b;
         const float b2b = dot(N2, mbar) - b0b;
@@ -198,9 +204,10 @@ __global__ void __launch_bounds__(256) k_adjoint(WsView W, int k, const float4* 
                                       : mk(0.f, 0.f, 0.f);
         obar = obar + lam;
         dbar = dbar + lam * t;
-        atomic_add3(E.dV + 3 * i0, lam * (-b0));
-        atomic_add3(E.dV + 3 * i1, lam * (-b1));
-        atomic_add3(E.dV + 3 * i2, lam * (-b2));
+        float4* dV4 = acc_dV4(E);
+        atomic_add4(dV4 + i0, lam * (-b0));
+        atomic_add4(dV4 + i1, lam * (-b1));
+        atomic_add4(dV4 + i2, lam * (-b2));
       }
     }
     if (k > 0) {
@@ -219,25 +226,51 @@ __global__ void __launch_bounds__(256) k_adjoint(WsView W, int k, const float4* 
   }
 }
 
-// zero every scene's dV, dN, dIoR, dsigma (blockIdx.y = scene)
+// zero every scene's accumulators, dIoR and dsigma (blockIdx.y = scene)
 __global__ void k_zero_grads(const SceneEntry* __restrict__ ent) {
   const SceneEntry& E = ent[blockIdx.y];
-  const size_t n = 3 * (size_t)E.nv;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    E.dV[i] = 0.f;
-    E.dN[i] = 0.f;
-  }
+  const size_t n = 2 * (size_t)E.nv;
+  float4* acc = acc_dN4(E);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   if (blockIdx.x == 0 && threadIdx.x < 4) {
     if (threadIdx.x == 0) E.dior[0] = 0.f;
     else E.dsigma[threadIdx.x - 1] = 0.f;
   }
 }
 
-// Eq. 13 backward for every scene (blockIdx.y = scene): dN -> dV.
+// Eq. 13 backward for every scene (blockIdx.y = scene): dN -> dV, on the
+// float4 accumulators (the same arithmetic as face_normal_backward_one)
 __global__ void k_face_normals_backward_table(const SceneEntry* __restrict__ ent) {
   const SceneEntry& E = ent[blockIdx.y];
-  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < E.nf; f += gridDim.x * blockDim.x)
-    face_normal_backward_one(E.V, E.F, f, E.dN, E.dV);
+  const float4* dN4 = acc_dN4(E);
+  float4* dV4 = acc_dV4(E);
+  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < E.nf; f += gridDim.x * blockDim.x) {
+    const int i0 = E.F[3 * f], i1 = E.F[3 * f + 1], i2 = E.F[3 * f + 2];
+    const float3 v0 = load3(E.V + 3 * i0), v1 = load3(E.V + 3 * i1), v2 = load3(E.V + 3 * i2);
+    const float3 e1 = v1 - v0, e2 = v2 - v0;
+    const float3 c = cross(e1, e2);
+    const float lc = len(c);
+    const float3 u = mk(c.x / lc, c.y / lc, c.z / lc);
+    const float3 du = (xyz(dN4[i0]) + xyz(dN4[i1]) + xyz(dN4[i2])) * (1.0f / 3.0f);
+    const float3 dc = (du - u * dot(u, du)) * (1.0f / lc);
+    const float3 de1 = cross(e2, dc), de2 = cross(dc, e1);
+    atomic_add4(dV4 + i0, -(de1 + de2));
+    atomic_add4(dV4 + i1, de1);
+    atomic_add4(dV4 + i2, de2);
+  }
+}
+
+// the caller's dV [nv][3] from the accumulator (blockIdx.y = scene)
+__global__ void k_finish_grads_table(const SceneEntry* __restrict__ ent) {
+  const SceneEntry& E = ent[blockIdx.y];
+  const float4* dV4 = acc_dV4(E);
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < E.nv; v += gridDim.x * blockDim.x) {
+    const float4 g = dV4[v];
+    E.dV[3 * v] = g.x;
+    E.dV[3 * v + 1] = g.y;
+    E.dV[3 * v + 2] = g.z;
+  }
 }
 
 // L2 seed: grad = 2 scale (img - target); loss = scale sum (img - target)^2
@@ -283,7 +316,7 @@ void launch_backward_table(const TableHeader& th, const SceneEntry* entries, voi
     if (entries[i].nf > max_nf) max_nf = entries[i].nf;
   }
   const int cap_blocks = 4 * num_sms();
-  int zb = (3 * max_nv + 255) / 256;
+  int zb = (2 * max_nv + 255) / 256;
   if (zb > cap_blocks) zb = cap_blocks;
   {
     ProfScope ps("k_zero_grads", s);
@@ -302,14 +335,18 @@ void launch_backward_table(const TableHeader& th, const SceneEntry* entries, voi
   if (fb > cap_blocks) fb = cap_blocks;
   ProfScope ps("k_face_normals_backward", s);
   k_face_normals_backward_table<<<dim3(fb, n), 256, 0, s>>>(W.ent);
+  int vb = (max_nv + 255) / 256;
+  if (vb > cap_blocks) vb = cap_blocks;
+  k_finish_grads_table<<<dim3(vb, n), 256, 0, s>>>(W.ent);
 }
 
 // The backward scratch of a table: the two level buffers, then every
-// scene's dN.  Fills the entries' dN pointers.
+// scene's dN and dV accumulators (float4 per vertex each).  assign_dN
+// points each entry's dN at its pair.
 size_t backward_ws_bytes_table(unsigned long long max_level, const SceneEntry* entries, int n) {
   BwsLayout L(max_level, 0);
   size_t o = L.off_dN;
-  for (int i = 0; i < n; ++i) o = align_up(o + (size_t)entries[i].nv * 3 * sizeof(float), 256);
+  for (int i = 0; i < n; ++i) o = align_up(o + (size_t)entries[i].nv * 2 * sizeof(float4), 256);
   return o;
 }
 
@@ -318,7 +355,7 @@ void assign_dN(SceneEntry* entries, int n, void* bws, unsigned long long max_lev
   size_t o = L.off_dN;
   for (int i = 0; i < n; ++i) {
     entries[i].dN = (float*)((char*)bws + o);
-    o = align_up(o + (size_t)entries[i].nv * 3 * sizeof(float), 256);
+    o = align_up(o + (size_t)entries[i].nv * 2 * sizeof(float4), 256);
   }
 }
 

@@ -265,6 +265,8 @@ __device__ __forceinline__ ClosestHit closest_hit(const float4* __restrict__ nod
 // (uniform constant-bank reads); true: each ray looks its scene up.
 // retrace = 1: the backward's re-trace of a checkpointed level (own cursor,
 // no statistics).
+constexpr int kTraceClaim = 64;  // segments a warp claims from the level cursor at once
+
 template <int kMinBlocks, int kWidth, bool kBatch>
 __global__ void __launch_bounds__(256, kMinBlocks) k_trace(WsView W, int k, int steps, int refill,
                                                            const SceneEntry E0, int retrace) {
@@ -287,16 +289,35 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_trace(WsView W, int k, int 
   const float4* tris = E0.tris;
   ClosestHit h{INFINITY, 0.f, 0.f, -1};
   int stack[kTraceStack];
+  // the warp's claimed batch [qb, qe) of the level's segments: one atomic on
+  // the level cursor per kTraceClaim segments, not one per refill
+  uint32_t qb = 0, qe = 0;
+  bool cursor_done = false;
   while (true) {
     const unsigned idle = __ballot_sync(kFull, !active);
     const int n_idle = __popc(idle);
     if (!exhausted && n_idle >= refill) {
-      uint32_t base = 0;
-      if (lane == 0) base = atomicAdd(cursor, (uint32_t)n_idle);
-      base = __shfl_sync(kFull, base, 0);
-      if (base + (uint32_t)n_idle >= n) exhausted = true;
+      const uint32_t have = qe - qb;
+      uint32_t nb = 0;
+      const bool claim = have < (uint32_t)n_idle && !cursor_done;
+      if (claim) {
+        if (lane == 0) nb = atomicAdd(cursor, (uint32_t)kTraceClaim);
+        nb = __shfl_sync(kFull, nb, 0);
+      }
+      const uint32_t r = __popc(idle & lanes_below);
+      const uint32_t i = r < have ? qb + r : (claim ? nb + (r - have) : 0xffffffffu);
+      if (claim) {
+        const uint32_t used = (uint32_t)n_idle - have;
+        qb = nb + used;
+        qe = nb + (uint32_t)kTraceClaim;
+        if (nb + (uint32_t)kTraceClaim >= n) cursor_done = true;
+      } else {
+        qb += min((uint32_t)n_idle, have);
+      }
+      if (qe > n) qe = n;
+      if (qb > qe) qb = qe;
+      if (cursor_done && qb >= qe) exhausted = true;
       if (!active) {
-        const uint32_t i = base + __popc(idle & lanes_below);
         if (i < n) {
           a = start + i;
           const float4 ro = W.ray_o[a], rd = W.ray_d[a], rw = W.ray_w[a];
@@ -374,8 +395,10 @@ __global__ void k_closest_hit_rays(const float4* __restrict__ nodes, const float
 // Shading of every segment of level k: Sec. 3.4 steps 1-5 with the
 // segment's own scene (depth limit, materials, environment, image); kBatch
 // as for k_trace.
+constexpr int kShadeThreads = 256;
+
 template <bool kBatch>
-__global__ void __launch_bounds__(256) k_shade(WsView W, int k, const SceneEntry E0) {
+__global__ void __launch_bounds__(kShadeThreads) k_shade(WsView W, int k, const SceneEntry E0) {
   WsHeader* H = W.hdr;
   const int n_scenes = kBatch ? W.th->n : 1;
   const uint32_t n = level_size(H, k);
@@ -385,12 +408,15 @@ __global__ void __launch_bounds__(256) k_shade(WsView W, int k, const SceneEntry
     H->level_start[k + 1] = next_start;
     if (n) H->n_levels = (uint32_t)(k + 1);
   }
-  const uint32_t lane = threadIdx.x & 31;
-  const uint32_t warps = gridDim.x * blockDim.x / 32;
+  __shared__ uint32_t s_woff[kShadeThreads / 32];
+  __shared__ uint32_t s_base;
+  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   uint32_t c_hit = 0, c_miss = 0, c_disc = 0, c_back = 0, c_tir = 0;
   bool overflow = false;
-  for (uint32_t wb = (blockIdx.x * blockDim.x + threadIdx.x) / 32 * 32; wb < n; wb += warps * 32) {
-    const uint32_t i = wb + lane;
+  // CTA-wide tiles, so that the children of a tile are appended with one
+  // atomic on the level counter per CTA rather than per warp
+  for (uint32_t tile = blockIdx.x * kShadeThreads; tile < n; tile += gridDim.x * kShadeThreads) {
+    const uint32_t i = tile + threadIdx.x;
     const uint32_t a = start + i;
     int nchild = 0;
     float4 co = make_float4(0.f, 0.f, 0.f, 0.f), cdr = co, cwr = co, cdt = co, cwt = co;
@@ -449,17 +475,28 @@ __global__ void __launch_bounds__(256) k_shade(WsView W, int k, const SceneEntry
       }
       W.sflag[a] = fl;
     }
-    // warp-aggregated append of the children to level k+1
+    // CTA-aggregated append of the children to level k+1: warp scans, a
+    // prefix over the warps, one atomic
     int incl = nchild;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const int v = __shfl_up_sync(kFull, incl, o);
       if ((int)lane >= o) incl += v;
     }
-    const int total = __shfl_sync(kFull, incl, 31);
-    uint32_t base = 0;
-    if (lane == 0 && total > 0) base = atomicAdd(&H->level_count[k + 1], (uint32_t)total);
-    base = __shfl_sync(kFull, base, 0);
+    if (lane == 31) s_woff[wid] = (uint32_t)incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t run = 0;
+      for (int w = 0; w < kShadeThreads / 32; ++w) {
+        const uint32_t t = s_woff[w];
+        s_woff[w] = run;
+        run += t;
+      }
+      s_base = run ? atomicAdd(&H->level_count[k + 1], run) : 0u;
+    }
+    __syncthreads();
+    const uint32_t base = s_base + s_woff[wid];
+    __syncthreads();  // s_woff and s_base are rewritten by the next tile
     if (i < n) {
       int32_t ch = -1;
       if (nchild > 0) {
@@ -592,8 +629,8 @@ void launch_forward_table(const TableHeader& th, const SceneEntry* entries, void
     }
     {
       ProfScope ps("k_shade", s);
-      if (batch) k_shade<true><<<shade_blocks(), 256, 0, s>>>(W, k, E0);
-      else k_shade<false><<<shade_blocks(), 256, 0, s>>>(W, k, E0);
+      if (batch) k_shade<true><<<shade_blocks(), kShadeThreads, 0, s>>>(W, k, E0);
+      else k_shade<false><<<shade_blocks(), kShadeThreads, 0, s>>>(W, k, E0);
     }
   }
 }
