@@ -67,7 +67,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
             if err.strip():
                 print(err, file=sys.stderr)
     tmp = LIB_PATH + ".tmp%d" % os.getpid()
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *[o for o, _ in results]]
+    # --no-undefined: a symbol declared in one unit and defined nowhere fails here, not at load time
+    cmd = [nvcc, *ARCH, "-shared", "-Xlinker", "--no-undefined", "-o", tmp, *[o for o, _ in results]]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")

@@ -552,8 +552,8 @@ __global__ void k_dump(WsView W, int32_t* __restrict__ si, float* __restrict__ s
 // ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
-// Launch and scheduling knobs (dt_set_tuning); process-wide.
-dt_tuning g_tuning = {16, 8, 5, 8, 2, 1};
+// Launch and scheduling knobs (dt_set_tuning; defined with the C ABI).
+extern dt_tuning g_tuning;
 static int shade_blocks() { return g_tuning.shade_blocks_per_sm * num_sms(); }
 static int n_int_of(int32_t nf) { return nf > 1 ? nf - 1 : 1; }
 
