@@ -444,6 +444,29 @@ def batch_leg(args, dt, dev, steps):
     }
 
 
+def rank_cameras(n_views: int, world: int, rank: int, res: int):
+    """The views of one rank: every world-th view of a Fibonacci set of
+    n_views * world, so ranks hold disjoint sets of the same size (weak
+    scaling) and their union is the whole set."""
+    from paper_2603_00413_gb300 import scenes as S
+    allc = S.fibonacci_views(n_views * world, 3.0, res, res)
+    return allc[rank::world]
+
+
+def reduce_over_ranks(times, units, device):
+    """(max over ranks of each time, sum over ranks of units): the whole-job
+    time is the slowest rank's, the work is everyone's."""
+    import torch
+    import torch.distributed as tdist
+    if not (tdist.is_available() and tdist.is_initialized()):
+        return [float(x) for x in times], float(units)
+    t = torch.tensor([float(x) for x in times], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    tdist.all_reduce(u, op=tdist.ReduceOp.SUM)
+    return [float(x) for x in t.tolist()], float(u.item())
+
+
 def run_ours(args):
     import torch
     import torch.distributed as tdist
@@ -462,11 +485,9 @@ def run_ours(args):
     import paper_2603_00413_gb300 as dt
 
     sc, Vt_np = genus2_workload(args.views, args.res, args.depth)
-    # disjoint view sets per rank (weak scaling): rotate the Fibonacci set
+    # disjoint view sets per rank (weak scaling)
     if world > 1:
-        from paper_2603_00413_gb300 import scenes as S
-        allc = S.fibonacci_views(args.views * world, 3.0, args.res, args.res)
-        sc.cams = allc[rank::world]
+        sc.cams = rank_cameras(args.views, world, rank, args.res)
     res, D = args.res, args.depth
     nvw = len(sc.cams)
     V = torch.from_numpy(sc.V).to(dev)
@@ -540,14 +561,10 @@ def run_ours(args):
     with ClockSampler(dev.index or 0) as clk:
         ms, prof = timed(False, args.steps, profile=True)
     ms_fwd, _ = timed(True, args.steps)
-    total_ms = float(sum(ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        total_ms = float(t.item())
     seg = stats["segments"]
-    value = seg * world * args.steps / (total_ms / 1000.0)
-    fwd_value = seg * world * args.steps / (sum(ms_fwd) / 1000.0)
+    (total_ms, fwd_ms), seg_all = reduce_over_ranks([sum(ms), sum(ms_fwd)], seg, dev)
+    value = seg_all * args.steps / (total_ms / 1000.0)
+    fwd_value = seg_all * args.steps / (fwd_ms / 1000.0)
     chk = dt.read_stats(ws)
     assert chk["status"] == dt.DT_OK and chk["segments"] == seg, chk
 
@@ -633,7 +650,8 @@ def run_ours(args):
             e2e_step()
             torch.cuda.synchronize()
             tt.append(time.perf_counter() - t0)
-        e2e = {"value": seg * world * args.steps / sum(tt), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+        (e2e_s,), _ = reduce_over_ranks([sum(tt)], seg, dev)
+        e2e = {"value": seg_all * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
     cpu = None
@@ -665,11 +683,11 @@ def run_ours(args):
             "config": {"workload": f"genus-2 two-tori mesh ({sc.F.shape[0]} triangles), {nvw} views {res}x{res}, "
                                    f"depth {D}, 1 spp, IoR {sc.ior:.4f}, fwd+bwd of an L2 image loss",
                        "views": nvw, "width": res, "height": res, "max_depth": D, "triangles": int(sc.F.shape[0]),
-                       "segments_per_step": int(seg), "l2": "flushed by a 512 MB write before every timed step",
+                       "segments_per_step": int(seg_all), "l2": "flushed by a 512 MB write before every timed step",
                        "bvh": "binned SAH" if dt.get_tuning()["bvh_builder"] == 1 else "LBVH",
                        "parallelism": f"replicas over disjoint views x{world}"},
             "fwd_segments_per_s": fwd_value,
-            "ms_per_step_fwd": float(sum(ms_fwd)) / args.steps,
+            "ms_per_step_fwd": fwd_ms / args.steps,
             "roofline": roofline,
             "kernel_share": kernel_share,
             "gpu_launches": gpu_launches,
