@@ -340,9 +340,10 @@ __global__ void k_refit(const float* __restrict__ V, const int32_t* __restrict__
 
 // ---- binned SAH build (top-down) ---------------------------------------------
 // A second builder of the same binary layout.  Top-down: each task is a
-// contiguous range of a primitive permutation; its split is the one of 3 x 15
-// bin boundaries (16 centroid bins per axis) with the least surface area cost
-// area(left box) * left count + area(right box) * right count, and the range
+// contiguous range of a primitive permutation; its split is the bin boundary
+// (of 32 centroid bins per axis; 16 in the warp builder) with the least
+// surface area cost area(left box) * left count + area(right box) * right
+// count, and the range
 // is partitioned stably into [left | right].  Tasks larger than kSahSmall
 // take four launches per tree level, each spread over chunks of kSahChunk
 // positions so that the few huge tasks near the root use the whole GPU: bin
@@ -357,7 +358,8 @@ __global__ void k_refit(const float* __restrict__ V, const int32_t* __restrict__
 // (see launch_sah_topology).  Every decision is a deterministic function of
 // the geometry: bins are integer sums, minima and maxima, and partitions are
 // stable.
-constexpr int kSahBins = 16;
+constexpr int kSahBins = 32;       // bins per axis of the large-task levels
+constexpr int kSahSmallBins = 16;  // of the warp builder
 constexpr int kSahSmall = 128;
 constexpr int kSahFreeDepth = 24;
 constexpr int kSahSmallFreeDepth = 56;
@@ -371,11 +373,14 @@ struct SahTask {
   int chunk0, axis, bin, nl;  // first chunk of the level; the split (axis < 0: median)
   float4 lo, hi;              // binning bounds (xyz), a superset of the centroids
 };
-struct SahBins {  // order-preserving uints for the float bounds
-  uint32_t cnt[3][kSahBins];
-  uint32_t lo[3][kSahBins][3];
-  uint32_t hi[3][kSahBins][3];
+template <int kB>
+struct SahBinsT {  // order-preserving uints for the float bounds
+  uint32_t cnt[3][kB];
+  uint32_t lo[3][kB][3];
+  uint32_t hi[3][kB][3];
 };
+using SahBins = SahBinsT<kSahBins>;
+using SahSmallBins = SahBinsT<kSahSmallBins>;
 struct SahState {
   unsigned long long packed[kSahMaxLevels + 2];  // per level: tasks << 32 | chunks
   int n_small;
@@ -393,13 +398,15 @@ struct SahView {
   int max_large, max_small, max_chunks;
 };
 
+template <int kB = kSahBins>
 __device__ __forceinline__ int sah_bin(float c, float lo, float scale) {
   const int b = (int)__fmul_rn(__fsub_rn(c, lo), scale);
-  return min(kSahBins - 1, max(0, b));
+  return min(kB - 1, max(0, b));
 }
+template <int kB = kSahBins>
 __device__ __forceinline__ float sah_scale(float lo, float hi) {
   const float ext = __fsub_rn(hi, lo);
-  return ext > 0.0f ? __fdiv_rn((float)kSahBins, ext) : 0.0f;
+  return ext > 0.0f ? __fdiv_rn((float)kB, ext) : 0.0f;
 }
 __device__ __forceinline__ float sah_area(float3 lo, float3 hi) {
   const float3 d = hi - lo;
@@ -437,11 +444,12 @@ __global__ void k_sah_prims(const float* __restrict__ V, const int32_t* __restri
 __device__ __forceinline__ int sah_chunks(int n) { return (n + kSahChunk - 1) / kSahChunk; }
 
 // empty bins: zero counts, inverted bounds (threads i0, i0 + stride, ...)
-__device__ __forceinline__ void sah_zero_bins(SahBins* g, int i0, int stride) {
+template <int kB>
+__device__ __forceinline__ void sah_zero_bins(SahBinsT<kB>* g, int i0, int stride) {
   uint32_t* cnt = &g->cnt[0][0];
   uint32_t* lo = &g->lo[0][0][0];
   uint32_t* hi = &g->hi[0][0][0];
-  for (int i = i0; i < 3 * kSahBins; i += stride) {
+  for (int i = i0; i < 3 * kB; i += stride) {
     cnt[i] = 0u;
     for (int q = 0; q < 3; ++q) {
       lo[3 * i + q] = 0xffffffffu;
@@ -473,7 +481,8 @@ __global__ void k_sah_root(int32_t nf, const uint32_t* __restrict__ bounds, SahV
   }
 }
 
-__device__ __forceinline__ void sah_flush(SahBins& sb, int k, int b, uint32_t n, float3 lo, float3 hi) {
+template <int kB>
+__device__ __forceinline__ void sah_flush(SahBinsT<kB>& sb, int k, int b, uint32_t n, float3 lo, float3 hi) {
   atomicAdd(&sb.cnt[k][b], n);
   atomicMin(&sb.lo[k][b][0], f2ord(lo.x)); atomicMin(&sb.lo[k][b][1], f2ord(lo.y)); atomicMin(&sb.lo[k][b][2], f2ord(lo.z));
   atomicMax(&sb.hi[k][b][0], f2ord(hi.x)); atomicMax(&sb.hi[k][b][1], f2ord(hi.y)); atomicMax(&sb.hi[k][b][2], f2ord(hi.z));
@@ -485,14 +494,15 @@ struct SahSplit {
   int axis, bin, nl;
   float3 llo, lhi, rlo, rhi;
 };
-__device__ SahSplit sah_sweep(const SahBins& sb, int k) {
+template <int kB>
+__device__ SahSplit sah_sweep(const SahBinsT<kB>& sb, int k) {
   SahSplit best;
   best.cost = INFINITY; best.axis = k; best.bin = -1; best.nl = 0;
-  float rarea[kSahBins];
-  uint32_t rcnt[kSahBins];
+  float rarea[kB];
+  uint32_t rcnt[kB];
   float3 rl = mk(INFINITY, INFINITY, INFINITY), rh = mk(-INFINITY, -INFINITY, -INFINITY);
   uint32_t c = 0;
-  for (int i = kSahBins - 1; i >= 1; --i) {
+  for (int i = kB - 1; i >= 1; --i) {
     if (sb.cnt[k][i]) {
       rl = mk(fminf(rl.x, ord2f(sb.lo[k][i][0])), fminf(rl.y, ord2f(sb.lo[k][i][1])), fminf(rl.z, ord2f(sb.lo[k][i][2])));
       rh = mk(fmaxf(rh.x, ord2f(sb.hi[k][i][0])), fmaxf(rh.y, ord2f(sb.hi[k][i][1])), fmaxf(rh.z, ord2f(sb.hi[k][i][2])));
@@ -503,7 +513,7 @@ __device__ SahSplit sah_sweep(const SahBins& sb, int k) {
   }
   float3 ll = mk(INFINITY, INFINITY, INFINITY), lh = mk(-INFINITY, -INFINITY, -INFINITY);
   uint32_t lc = 0;
-  for (int i = 0; i < kSahBins - 1; ++i) {
+  for (int i = 0; i < kB - 1; ++i) {
     if (sb.cnt[k][i]) {
       ll = mk(fminf(ll.x, ord2f(sb.lo[k][i][0])), fminf(ll.y, ord2f(sb.lo[k][i][1])), fminf(ll.z, ord2f(sb.lo[k][i][2])));
       lh = mk(fmaxf(lh.x, ord2f(sb.hi[k][i][0])), fmaxf(lh.y, ord2f(sb.hi[k][i][1])), fmaxf(lh.z, ord2f(sb.hi[k][i][2])));
@@ -519,7 +529,7 @@ __device__ SahSplit sah_sweep(const SahBins& sb, int k) {
   }
   if (best.bin >= 0) {  // the right box of the chosen boundary
     float3 a = mk(INFINITY, INFINITY, INFINITY), b = mk(-INFINITY, -INFINITY, -INFINITY);
-    for (int i = best.bin + 1; i < kSahBins; ++i)
+    for (int i = best.bin + 1; i < kB; ++i)
       if (sb.cnt[k][i]) {
         a = mk(fminf(a.x, ord2f(sb.lo[k][i][0])), fminf(a.y, ord2f(sb.lo[k][i][1])), fminf(a.z, ord2f(sb.lo[k][i][2])));
         b = mk(fmaxf(b.x, ord2f(sb.hi[k][i][0])), fmaxf(b.y, ord2f(sb.hi[k][i][1])), fmaxf(b.z, ord2f(sb.hi[k][i][2])));
@@ -785,13 +795,13 @@ __global__ void __launch_bounds__(kSahThreads) k_sah_scatter(int level, SahView 
 __global__ void __launch_bounds__(32 * kSahSmallWarps) k_sah_small(SahView S, BvhView B) {
   __shared__ uint32_t s_ids[kSahSmallWarps][kSahSmall], s_tmp[kSahSmallWarps][kSahSmall];
   __shared__ int4 s_stack[kSahSmallWarps][kSahSmall / 2 + 1];
-  __shared__ SahBins s_bins[kSahSmallWarps];
+  __shared__ SahSmallBins s_bins[kSahSmallWarps];
   const int n_int = B.hdr->n_int;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint32_t* ids = s_ids[w];
   uint32_t* tmp = s_tmp[w];
   int4* stack = s_stack[w];
-  SahBins& sb = s_bins[w];
+  SahSmallBins& sb = s_bins[w];
   const int nsmall = min(S.st->n_small, S.max_small);
   for (int t = blockIdx.x * kSahSmallWarps + w; t < nsmall; t += gridDim.x * kSahSmallWarps) {
     const int4 T = S.small[t];
@@ -831,7 +841,8 @@ __global__ void __launch_bounds__(32 * kSahSmallWarps) k_sah_small(SahView S, Bv
         hi.y = fmaxf(hi.y, __shfl_xor_sync(kFull, hi.y, o));
         hi.z = fmaxf(hi.z, __shfl_xor_sync(kFull, hi.z, o));
       }
-      const float sc[3] = {sah_scale(lo.x, hi.x), sah_scale(lo.y, hi.y), sah_scale(lo.z, hi.z)};
+      const float sc[3] = {sah_scale<kSahSmallBins>(lo.x, hi.x), sah_scale<kSahSmallBins>(lo.y, hi.y),
+                           sah_scale<kSahSmallBins>(lo.z, hi.z)};
       int axis = -1, bin = -1, nl = rn / 2;
       if (depth < kSahSmallFreeDepth && (sc[0] > 0.f || sc[1] > 0.f || sc[2] > 0.f)) {
         sah_zero_bins(&sb, lane, 32);
@@ -841,7 +852,7 @@ __global__ void __launch_bounds__(32 * kSahSmallWarps) k_sah_small(SahView S, Bv
           const float4 c = S.cen[p], plo = S.pbox[2 * p], phi = S.pbox[2 * p + 1];
           for (int k = 0; k < 3; ++k) {
             if (sc[k] <= 0.f) continue;
-            sah_flush(sb, k, sah_bin(comp(c, k), comp3(lo, k), sc[k]), 1u, mk(plo.x, plo.y, plo.z),
+            sah_flush(sb, k, sah_bin<kSahSmallBins>(comp(c, k), comp3(lo, k), sc[k]), 1u, mk(plo.x, plo.y, plo.z),
                       mk(phi.x, phi.y, phi.z));
           }
         }
@@ -871,7 +882,7 @@ __global__ void __launch_bounds__(32 * kSahSmallWarps) k_sah_small(SahView S, Bv
         bool left = false;
         if (valid) {
           p = ids[ra + i];
-          left = axis >= 0 ? sah_bin(comp(S.cen[p], axis), comp3(lo, axis), sc[axis]) <= bin : i < nl;
+          left = axis >= 0 ? sah_bin<kSahSmallBins>(comp(S.cen[p], axis), comp3(lo, axis), sc[axis]) <= bin : i < nl;
         }
         const unsigned bal = __ballot_sync(kFull, left);
         const int lr = __popc(bal & ((1u << lane) - 1u));

@@ -342,22 +342,29 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_trace(WsView W, int k, int 
     }
     if (!__any_sync(kFull, active)) break;
     if (!active) continue;
-    for (int st = 0; st < steps; ++st) {
-      bool done = false;
-      if (++iters > max_iter) {
-        overflow = true;
-        done = true;
-      } else {
-        ++nvis;
+    // A valid tree is visited at most once per node (max_iter = 2 n_int + 8);
+    // the guard is checked once per round, so a corrupt tree (max_iter 0) is
+    // never entered and a runaway ray stops within one round of the bound.
+    int st = 0;
+    bool done = iters >= max_iter;
+    if (!done) {
+      for (; st < steps; ++st) {
         node = visit_node<kWidth>(nodes, tris, node, o, d, idir, src, tmin, h, stack, sp, overflow, ntest);
-        done = node < 0;
+        if (node < 0) {
+          ++st;
+          done = true;
+          break;
+        }
       }
-      if (done) {
-        W.hit[hit_slot(W, k, a, a - start)] = h.tri >= 0 ? make_float4(h.t, h.b1, h.b2, __int_as_float(h.tri))
-                                                         : make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
-        active = false;
-        break;
-      }
+      nvis += (uint32_t)st;
+      iters += st;
+      if (!done && iters >= max_iter) done = true;
+    }
+    if (done) {
+      if (node >= 0) overflow = true;  // stopped by the guard
+      W.hit[hit_slot(W, k, a, a - start)] = h.tri >= 0 ? make_float4(h.t, h.b1, h.b2, __int_as_float(h.tri))
+                                                       : make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+      active = false;
     }
   }
   if (!retrace) {
@@ -396,9 +403,10 @@ __global__ void k_closest_hit_rays(const float4* __restrict__ nodes, const float
 // segment's own scene (depth limit, materials, environment, image); kBatch
 // as for k_trace.
 constexpr int kShadeThreads = 256;
+constexpr int kShadeMinBlocks = 4;  // CTAs per SM the register budget is sized for
 
 template <bool kBatch>
-__global__ void __launch_bounds__(kShadeThreads) k_shade(WsView W, int k, const SceneEntry E0) {
+__global__ void __launch_bounds__(kShadeThreads, kShadeMinBlocks) k_shade(WsView W, int k, const SceneEntry E0) {
   WsHeader* H = W.hdr;
   const int n_scenes = kBatch ? W.th->n : 1;
   const uint32_t n = level_size(H, k);
