@@ -225,6 +225,40 @@ __device__ __forceinline__ int visit_node2(const float4* __restrict__ node2, con
   return sp > 0 ? stack[--sp] : -1;
 }
 
+// The binary visit of the persistent traversal: the same node test as
+// visit_node2, but a hit leaf is queued in the lane's pending slots rather
+// than intersected at once.  The kernel intersects every lane's pending
+// triangles together after a few visits, so the triangle test runs as one
+// block per few visits for the warp instead of one or two blocks per visit
+// in which a few lanes work while the rest wait.  The caller visits only
+// while fewer than two triangles are pending, so three slots always suffice.
+__device__ __forceinline__ void push_pending(int leaf, int& p0, int& p1, int& p2) {
+  if (p0 < 0) p0 = leaf;
+  else if (p1 < 0) p1 = leaf;
+  else p2 = leaf;
+}
+__device__ __forceinline__ int visit_node2_deferred(const float4* __restrict__ node2, int node, float3 o, float3 idir,
+                                                    float tmin, float tmax, int* stack, int& sp, bool& overflow,
+                                                    int& p0, int& p1, int& p2) {
+  const float4* Np = node2 + 4 * node;
+  const float4 n0 = __ldg(Np), n1 = __ldg(Np + 1), n2 = __ldg(Np + 2);
+  const int4 n3 = __ldg(reinterpret_cast<const int4*>(Np) + 3);
+  float tn0, tn1;
+  bool h0 = slab(o, idir, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, tmin, tmax, tn0);
+  bool h1 = slab(o, idir, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, tmin, tmax, tn1);
+  if (h0 && n3.x < 0) { push_pending(~n3.x, p0, p1, p2); h0 = false; }
+  if (h1 && n3.y < 0) { push_pending(~n3.y, p0, p1, p2); h1 = false; }
+  if (h0 && h1) {
+    int nearc = n3.x, farc = n3.y;
+    if (tn1 < tn0) { nearc = n3.y; farc = n3.x; }
+    if (sp < kTraceStack) stack[sp++] = farc; else overflow = true;
+    return nearc;
+  }
+  if (h0) return n3.x;
+  if (h1) return n3.y;
+  return sp > 0 ? stack[--sp] : -1;
+}
+
 template <int kWidth>
 __device__ __forceinline__ int visit_node(const float4* __restrict__ nodes, const float4* __restrict__ tris, int node,
                                           float3 o, float3 d, float3 idir, int src, float tmin, ClosestHit& h,
@@ -266,6 +300,7 @@ __device__ __forceinline__ ClosestHit closest_hit(const float4* __restrict__ nod
 // retrace = 1: the backward's re-trace of a checkpointed level (own cursor,
 // no statistics).
 constexpr int kTraceClaim = 64;  // segments a warp claims from the level cursor at once
+constexpr int kLeafEvery = 4;    // node visits between the warp's batched triangle tests
 
 template <int kMinBlocks, int kWidth, bool kBatch>
 __global__ void __launch_bounds__(256, kMinBlocks) k_trace(WsView W, int k, int steps, int refill,
@@ -348,12 +383,30 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_trace(WsView W, int k, int 
     int st = 0;
     bool done = iters >= max_iter;
     if (!done) {
-      for (; st < steps; ++st) {
-        node = visit_node<kWidth>(nodes, tris, node, o, d, idir, src, tmin, h, stack, sp, overflow, ntest);
-        if (node < 0) {
-          ++st;
-          done = true;
-          break;
+      if (kWidth == 2) {
+        // visits in groups of kLeafEvery, then the pending triangles of the
+        // whole warp at once (see visit_node2_deferred)
+        int p0 = -1, p1 = -1, p2 = -1;
+        while (st < steps) {
+          for (int j = 0; j < kLeafEvery && node >= 0 && p1 < 0; ++j, ++st)
+            node = visit_node2_deferred(nodes, node, o, idir, tmin, h.t, stack, sp, overflow, p0, p1, p2);
+          if (p0 >= 0) test_leaf(tris, p0, o, d, src, tmin, h, ntest);
+          if (p1 >= 0) test_leaf(tris, p1, o, d, src, tmin, h, ntest);
+          if (p2 >= 0) test_leaf(tris, p2, o, d, src, tmin, h, ntest);
+          p0 = p1 = p2 = -1;
+          if (node < 0) {
+            done = true;
+            break;
+          }
+        }
+      } else {
+        for (; st < steps; ++st) {
+          node = visit_node<kWidth>(nodes, tris, node, o, d, idir, src, tmin, h, stack, sp, overflow, ntest);
+          if (node < 0) {
+            ++st;
+            done = true;
+            break;
+          }
         }
       }
       nvis += (uint32_t)st;
