@@ -22,7 +22,7 @@ from . import get_tuning, set_tuning
 DEFAULT_SPACE = {
     "bvh_width": (2, 4),
     "trace_blocks_per_sm": (4, 5, 6),
-    "trace_steps": (8, 16, 32),
+    "trace_steps": (16, 32, 64, 128),
     "trace_refill": (4, 8, 16),
     "shade_blocks_per_sm": (4, 8, 16),
 }

@@ -40,9 +40,9 @@ void launch_closest_hit(const void* bvh, int32_t nf, const float* o, const float
                         float tmin, int32_t* tri, float* tbb, cudaStream_t s);
 size_t backward_ws_bytes(unsigned long long max_level, int32_t nv);
 // Launch and scheduling knobs (dt_set_tuning); process-wide.  Node visits
-// per round 24, refill at 8 idle lanes, 5 traversal and 8 shading CTAs per
+// per round 64, refill at 8 idle lanes, 5 traversal and 8 shading CTAs per
 // SM, binary nodes, binned SAH builder.
-dt_tuning g_tuning = {24, 8, 5, 8, 2, 1};
+dt_tuning g_tuning = {64, 8, 5, 8, 2, 1};
 void launch_l2_loss_grad(const float* img, const float* target, int64_t n, float scale, float* grad, float* loss,
                          cudaStream_t s);
 void launch_backward(const dt_scene& sc, const dt_views& vw, const dt_params& p, const void* ws,
