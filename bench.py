@@ -220,7 +220,7 @@ def run_reference(args):
 # GPU leg
 # ---------------------------------------------------------------------------
 # kernels launched per profiled scope (a scope may hold more than one kernel)
-KERNELS_PER_SCOPE = {"k_vertex_normals": 2, "k_refit": 3, "k_camera": 1, "k_trace": 1, "k_trace_retrace": 1,
+KERNELS_PER_SCOPE = {"k_vertex_normals": 2, "k_refit": 3, "k_camera": 1, "k_trace": 1,
                      "k_shade": 1,
                      "k_l2_loss_grad": 1, "k_adjoint": 1, "k_face_normals_backward": 1, "lbvh_build": 21,
                      "k_write_table": 2, "k_zero_images": 1, "k_zero_grads": 1}
@@ -268,8 +268,8 @@ def large_leg(args, dt, dev):
     samples per pixel (5.12M camera rays), depth 16, IoR 1.52, sigma (0.3,
     0.1, 0.05), a 2048x1024 environment; L2 loss against a render of the
     vertices perturbed by N(0, 0.001).  One step = LBVH rebuild + vertex
-    normals + checkpointed forward + loss seed + backward (re-trace per
-    level).  The same step with the full tape is timed beside it."""
+    normals + checkpointed forward + loss seed + backward (hits recovered
+    from the children's source triangles).  The same step with the full tape is timed beside it."""
     import torch
     from paper_2603_00413_gb300 import scenes as S
     t0 = time.time()

@@ -160,12 +160,14 @@ typedef struct dt_views {
  *  t_min: hits need t > t_min (the triangle a ray leaves from is skipped
  *    as well).  1e-5 for meshes scaled to the unit sphere.
  *  tape_mode: 0 keeps every segment's hit record for the backward; 1 is
- *    per-bounce checkpointing: only the ray queues are kept, hit records
- *    live in a ring of two levels of level_capacity segments each, and the
- *    backward re-traces each level before differentiating it (one more
- *    traversal, 16 bytes per segment less).  A level larger than
- *    level_capacity is dropped past that size and reported as
- *    DT_ERR_QUEUE_OVERFLOW with dt_stats.level_needed.
+ *    per-bounce checkpointing: only the ray queues are kept, the hit
+ *    records of the forward live in a ring of two levels of level_capacity
+ *    segments each, and the backward recovers the hit of every segment
+ *    that spawned children from the source triangle those children carry,
+ *    intersecting that one triangle again with the traversal's arithmetic
+ *    (16 bytes per segment less, one triangle test per spawning segment
+ *    more).  A level larger than level_capacity is dropped past that size
+ *    and reported as DT_ERR_QUEUE_OVERFLOW with dt_stats.level_needed.
  *  level_capacity: segments per ring level (tape_mode 1 only; else 0).
  *  The workspace must be sized for the same tape_mode and level_capacity
  *  (dt_render_workspace_size_ex) and the backward must be given the same
@@ -239,11 +241,8 @@ dt_status dt_read_stats(const void* d_ws, size_t ws_bytes, dt_stats* out, dt_str
  *
  * The scene, views and params must be those of the dt_render that filled
  * d_ws (ws_bytes as passed to it), and that render must have finished with
- * status DT_OK.  With tape_mode 0 the tape is only read; with tape_mode 1
- * each level is traced again (Sec. 3.4 step 2, through the same BVH, which
- * must not have changed since the forward) into the workspace's hit ring
- * before its adjoint, so the ring and the re-trace cursors of d_ws are
- * written.  dt_backward_workspace_size: bytes of the backward scratch
+ * status DT_OK; d_ws is only read, and the vertices must not have changed
+ * since the forward.  dt_backward_workspace_size: bytes of the backward scratch
  * d_bws (256-byte aligned) for a render whose largest level held max_level
  * segments (dt_stats.max_level); pass the same max_level to
  * dt_render_backward.  Outputs are overwritten: d_grad_V float[nv][3],
@@ -251,7 +250,7 @@ dt_status dt_read_stats(const void* d_ws, size_t ws_bytes, dt_stats* out, dt_str
  * ------------------------------------------------------------------------ */
 dt_status dt_backward_workspace_size(int64_t max_level, int32_t nv, size_t* bytes);
 dt_status dt_render_backward(const dt_scene* scene, const dt_views* views, const dt_params* params,
-                             void* d_ws, size_t ws_bytes, const float* d_grad_out, float* d_grad_V,
+                             const void* d_ws, size_t ws_bytes, const float* d_grad_out, float* d_grad_V,
                              float* d_grad_ior, float* d_grad_sigma, void* d_bws, size_t bws_bytes,
                              int64_t max_level, dt_stream stream);
 
@@ -283,7 +282,7 @@ typedef struct dt_batch_entry {
 dt_status dt_render_batch(const dt_batch_entry* entries, int32_t n, void* d_ws, size_t ws_bytes, dt_stream stream);
 dt_status dt_batch_backward_workspace_size(const dt_batch_entry* entries, int32_t n, int64_t max_level,
                                            size_t* bytes);
-dt_status dt_render_batch_backward(const dt_batch_entry* entries, int32_t n, void* d_ws, size_t ws_bytes,
+dt_status dt_render_batch_backward(const dt_batch_entry* entries, int32_t n, const void* d_ws, size_t ws_bytes,
                                    void* d_bws, size_t bws_bytes, int64_t max_level, dt_stream stream);
 
 /* ------------------------------------------------------------------------

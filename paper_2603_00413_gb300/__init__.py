@@ -286,7 +286,8 @@ def closest_hit(bvh: Bvh, o, d, src=None, t_min: float = 1e-5, stream=None):
 # ---------------------------------------------------------------------------
 class Params:
     """Render parameters.  checkpoint=True keeps only the per-depth ray
-    queues on the tape and re-traces each level's hits in the backward
+    queues on the tape and recovers the hits in the backward from the
+    source triangle each spawned child carries
     (tape_mode 1); the hit ring then holds level_capacity records per level
     (0: chosen from the workspace, else twice the camera rays)."""
 

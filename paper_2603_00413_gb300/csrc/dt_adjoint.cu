@@ -79,7 +79,10 @@ __global__ void __launch_bounds__(256, kAdjointMinBlocks) k_adjoint(WsView W, in
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const uint32_t a = start + i;
-    const float4 ro = W.ray_o[a], rd = W.ray_d[a], rw = W.ray_w[a], hh = W.hit[hit_slot(W, k, a, i)];
+    const float4 ro = W.ray_o[a], rd = W.ray_d[a], rw = W.ray_w[a];
+    // the full tape keeps every hit record; a checkpointed one does not (see
+    // the spawning branch below)
+    const float4 hh = W.ring ? make_float4(0.f, 0.f, 0.f, 0.f) : W.hit[a];
     const uint32_t fl = W.sflag[a];
     const uint32_t sample = __float_as_uint(ro.w);
     const int sc = kBatch ? find_scene(W.th->starts, n_scenes, sample) : 0;
@@ -102,10 +105,15 @@ __global__ void __launch_bounds__(256, kAdjointMinBlocks) k_adjoint(WsView W, in
         L = env_lookup(E.env, E.env_w, E.env_h, d);
         dbar = env_grad_dir(E.env, E.env_w, E.env_h, d, gbar);
       } else if (!(fl & (SF_DISCARDED | SF_BACKFACING)) && ch >= 0) {
-        const int tri = __float_as_int(hh.w);
-        const float t = hh.x, b1 = hh.y, b2 = hh.z, b0 = 1.0f - b1 - b2;
+        // checkpointed tape: the hit triangle is the source triangle its
+        // children carry, and (t, b1, b2) come from intersecting it again
+        // with the same arithmetic as the traversal's leaf test
+        const int tri = W.ring ? __float_as_int(W.ray_w[ch].w) : __float_as_int(hh.w);
         const int i0 = __ldg(E.F + 3 * tri), i1 = __ldg(E.F + 3 * tri + 1), i2 = __ldg(E.F + 3 * tri + 2);
         const float3 v0 = load3(E.V + 3 * i0), v1 = load3(E.V + 3 * i1), v2 = load3(E.V + 3 * i2);
+        float t = hh.x, b1 = hh.y, b2 = hh.z;
+        if (W.ring) intersect_known(o, d, v0, v1 - v0, v2 - v0, t, b1, b2);
+        const float b0 = 1.0f - b1 - b2;
         const float3 N0 = load3(E.N + 3 * i0), N1 = load3(E.N + 3 * i1), N2 = load3(E.N + 3 * i2);
         const float ior = __ldg(E.ior);
         const float3 sigma = mk(__ldg(E.sigma), __ldg(E.sigma + 1), __ldg(E.sigma + 2));
@@ -297,12 +305,11 @@ void launch_l2_loss_grad(const float* img, const float* target, int64_t n, float
 }
 
 void launch_write_table(const WsView& W, const TableHeader& th, const SceneEntry* entries, int n, cudaStream_t s);
-void launch_retrace(const WsView& W, int k, const SceneEntry& E0, bool batch, cudaStream_t s);
 
 // Backward of a table of scenes over the tape in ws: rewrites the table with
 // the gradient pointers, zeroes the gradients, sweeps k = D..0, then the
 // vertex-normal adjoint of every scene.
-void launch_backward_table(const TableHeader& th, const SceneEntry* entries, void* ws, unsigned long long cap,
+void launch_backward_table(const TableHeader& th, const SceneEntry* entries, const void* ws, unsigned long long cap,
                            unsigned long long ring, void* bws, unsigned long long max_level, cudaStream_t s) {
   WsView W = ws_view(ws, cap, ring);
   BwsLayout L(max_level, 0);
@@ -324,9 +331,7 @@ void launch_backward_table(const TableHeader& th, const SceneEntry* entries, voi
   }
   const int blocks = g_tuning.shade_blocks_per_sm * num_sms();
   const size_t smem = sizeof(float) * 4 * (size_t)n;
-  if (ring) cudaMemsetAsync(W.hdr->fetch_bwd, 0, sizeof(W.hdr->fetch_bwd), s);
   for (int k = th.max_depth; k >= 0; --k) {
-    if (ring) launch_retrace(W, k, entries[0], n > 1, s);  // checkpointed: hits of level k again
     ProfScope ps("k_adjoint", s);
     if (n > 1) k_adjoint<true><<<blocks, 256, smem, s>>>(W, k, buf[(k + 1) & 1], buf[k & 1], entries[0]);
     else k_adjoint<false><<<blocks, 256, smem, s>>>(W, k, buf[(k + 1) & 1], buf[k & 1], entries[0]);

@@ -30,7 +30,7 @@ SceneEntry make_entry(const dt_scene& sc, const dt_views& vw, const dt_params& p
 void finish_table(SceneEntry* entries, int n, TableHeader& th);
 void launch_forward_table(const TableHeader& th, const SceneEntry* entries, void* ws, unsigned long long cap,
                           unsigned long long ring, cudaStream_t s);
-void launch_backward_table(const TableHeader& th, const SceneEntry* entries, void* ws, unsigned long long cap,
+void launch_backward_table(const TableHeader& th, const SceneEntry* entries, const void* ws, unsigned long long cap,
                            unsigned long long ring, void* bws, unsigned long long max_level, cudaStream_t s);
 size_t backward_ws_bytes_table(unsigned long long max_level, const SceneEntry* entries, int n);
 void assign_dN(SceneEntry* entries, int n, void* bws, unsigned long long max_level);
@@ -373,7 +373,7 @@ dt_status dt_batch_backward_workspace_size(const dt_batch_entry* entries, int32_
   return DT_OK;
 }
 
-dt_status dt_render_batch_backward(const dt_batch_entry* entries, int32_t n, void* d_ws, size_t ws_bytes,
+dt_status dt_render_batch_backward(const dt_batch_entry* entries, int32_t n, const void* d_ws, size_t ws_bytes,
                                    void* d_bws, size_t bws_bytes, int64_t max_level, dt_stream stream) {
   std::vector<SceneEntry> ent;
   TableHeader th;
@@ -393,7 +393,7 @@ dt_status dt_render_batch_backward(const dt_batch_entry* entries, int32_t n, voi
   return check_launch("dt_render_backward");
 }
 
-dt_status dt_render_backward(const dt_scene* scene, const dt_views* views, const dt_params* params, void* d_ws,
+dt_status dt_render_backward(const dt_scene* scene, const dt_views* views, const dt_params* params, const void* d_ws,
                              size_t ws_bytes, const float* d_grad_out, float* d_grad_V, float* d_grad_ior,
                              float* d_grad_sigma, void* d_bws, size_t bws_bytes, int64_t max_level,
                              dt_stream stream) {

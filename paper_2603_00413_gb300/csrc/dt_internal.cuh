@@ -149,7 +149,6 @@ struct WsHeader {
   uint32_t level_count[kMaxLevels];  // appended (may exceed what fits)
   uint32_t level_start[kMaxLevels];
   uint32_t fetch[kMaxLevels];        // work-fetch cursors of the trace kernels
-  uint32_t fetch_bwd[kMaxLevels];    // cursors of the backward's re-traces (tape_mode 1)
   unsigned long long counters[16];   // see CNT_*
   uint32_t ring;                     // level capacity of the hit ring (tape_mode 1), 0 = every hit kept
   uint32_t pad0;

@@ -149,6 +149,25 @@ __device__ __forceinline__ void shade_hit(float3 o, float3 d, float t, float b1,
 // feeds (1/3) u to each of its vertices, so du = (1/3)(dN_v0 + dN_v1 +
 // dN_v2); dc = (du - u (u.du)) / |c|; c = e1 x e2 gives de1 = e2 x dc,
 // de2 = dc x e1; then dv1 += de1, dv2 += de2, dv0 -= de1 + de2 (atomics).
+// Moller-Trumbore of one triangle (v0, e1 = v1 - v0, e2 = v2 - v0): (t, b1,
+// b2) with o + t d = v0 + b1 e1 + b2 e2; false when d is parallel to the
+// plane.  The traversal's leaf test evaluates the same expressions in the
+// same order on the same inputs (e1, e2 as the refit stores them), so the
+// checkpointed backward recovers the forward's hit.
+__device__ __forceinline__ bool intersect_known(float3 o, float3 d, float3 v0, float3 e1, float3 e2, float& t,
+                                                float& b1, float& b2) {
+  const float3 p = cross(d, e2);
+  const float det = dot(e1, p);
+  if (det == 0.0f) return false;
+  const float inv = 1.0f / det;
+  const float3 s = o - v0;
+  b1 = dot(s, p) * inv;
+  const float3 q = cross(s, e1);
+  b2 = dot(d, q) * inv;
+  t = dot(e2, q) * inv;
+  return true;
+}
+
 __device__ __forceinline__ void face_normal_backward_one(const float* __restrict__ V, const int32_t* __restrict__ F,
                                                          int f, const float* __restrict__ dN, float* __restrict__ dV) {
   const int i0 = F[3 * f], i1 = F[3 * f + 1], i2 = F[3 * f + 2];

@@ -134,6 +134,8 @@ __device__ __forceinline__ void test_leaf(const float4* __restrict__ tris, int l
   const int id = __float_as_int(a.w);
   if (id == src) return;
   ++ntest;
+  // the arithmetic of intersect_known, written out (the checkpointed
+  // backward calls that function on the same inputs and gets the same bits)
   const float3 v0 = xyz(a), e1 = xyz(b), e2 = xyz(c);
   const float3 p = cross(d, e2);
   const float det = dot(e1, p);
@@ -297,16 +299,14 @@ __device__ __forceinline__ ClosestHit closest_hit(const float4* __restrict__ nod
 // exhausted and its last ray is done.
 // kBatch = false: one scene, whose entry E0 arrives as a kernel parameter
 // (uniform constant-bank reads); true: each ray looks its scene up.
-// retrace = 1: the backward's re-trace of a checkpointed level (own cursor,
-// no statistics).
 constexpr int kTraceClaim = 64;  // segments a warp claims from the level cursor at once
 constexpr int kLeafEvery = 4;    // node visits between the warp's batched triangle tests
 
 template <int kMinBlocks, int kWidth, bool kBatch>
 __global__ void __launch_bounds__(256, kMinBlocks) k_trace(WsView W, int k, int steps, int refill,
-                                                           const SceneEntry E0, int retrace) {
+                                                           const SceneEntry E0) {
   WsHeader* H = W.hdr;
-  uint32_t* cursor = retrace ? &H->fetch_bwd[k] : &H->fetch[k];
+  uint32_t* cursor = &H->fetch[k];
   const int n_scenes = kBatch ? W.th->n : 1;
   const uint32_t n = level_size(H, k);
   const uint32_t start = H->level_start[k];
@@ -420,10 +420,8 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_trace(WsView W, int k, int 
       active = false;
     }
   }
-  if (!retrace) {
-    warp_add_u64(&H->counters[CNT_NODES], nvis);
-    warp_add_u64(&H->counters[CNT_TRIS], ntest);
-  }
+  warp_add_u64(&H->counters[CNT_NODES], nvis);
+  warp_add_u64(&H->counters[CNT_TRIS], ntest);
   if (__any_sync(kFull, overflow) && lane == 0) atomicOr(&H->status, ST_STACK_OVERFLOW);
 }
 
@@ -681,11 +679,11 @@ void launch_forward_table(const TableHeader& th, const SceneEntry* entries, void
     {
       ProfScope ps("k_trace", s);
       if (g_tuning.bvh_width == 4) {
-        if (batch) launch_trace_w<4, true>(bps, s, W, k, st, rf, E0, 0);
-        else launch_trace_w<4, false>(bps, s, W, k, st, rf, E0, 0);
+        if (batch) launch_trace_w<4, true>(bps, s, W, k, st, rf, E0);
+        else launch_trace_w<4, false>(bps, s, W, k, st, rf, E0);
       } else {
-        if (batch) launch_trace_w<2, true>(bps, s, W, k, st, rf, E0, 0);
-        else launch_trace_w<2, false>(bps, s, W, k, st, rf, E0, 0);
+        if (batch) launch_trace_w<2, true>(bps, s, W, k, st, rf, E0);
+        else launch_trace_w<2, false>(bps, s, W, k, st, rf, E0);
       }
     }
     {
@@ -693,19 +691,6 @@ void launch_forward_table(const TableHeader& th, const SceneEntry* entries, void
       if (batch) k_shade<true><<<shade_blocks(), kShadeThreads, 0, s>>>(W, k, E0);
       else k_shade<false><<<shade_blocks(), kShadeThreads, 0, s>>>(W, k, E0);
     }
-  }
-}
-
-// The backward's re-trace of level k of a checkpointed render (tape_mode 1).
-void launch_retrace(const WsView& W, int k, const SceneEntry& E0, bool batch, cudaStream_t s) {
-  ProfScope ps("k_trace_retrace", s);
-  const int bps = g_tuning.trace_blocks_per_sm, st = g_tuning.trace_steps, rf = g_tuning.trace_refill;
-  if (g_tuning.bvh_width == 4) {
-    if (batch) launch_trace_w<4, true>(bps, s, W, k, st, rf, E0, 1);
-    else launch_trace_w<4, false>(bps, s, W, k, st, rf, E0, 1);
-  } else {
-    if (batch) launch_trace_w<2, true>(bps, s, W, k, st, rf, E0, 1);
-    else launch_trace_w<2, false>(bps, s, W, k, st, rf, E0, 1);
   }
 }
 
