@@ -38,16 +38,13 @@ void launch_dump(const void* ws, unsigned long long cap, int32_t* si, float* sf,
                  cudaStream_t s);
 void launch_closest_hit(const void* bvh, int32_t nf, const float* o, const float* d, const int32_t* src, int32_t n,
                         float tmin, int32_t* tri, float* tbb, cudaStream_t s);
-size_t backward_ws_bytes(unsigned long long max_level, int32_t nv);
+void launch_l2_loss_grad(const float* img, const float* target, int64_t n, float scale, float* grad, float* loss,
+                         cudaStream_t s);
+
 // Launch and scheduling knobs (dt_set_tuning); process-wide.  Node visits
 // per round 64, refill at 8 idle lanes, 5 traversal and 8 shading CTAs per
 // SM, binary nodes, binned SAH builder.
 dt_tuning g_tuning = {64, 8, 5, 8, 2, 1};
-void launch_l2_loss_grad(const float* img, const float* target, int64_t n, float scale, float* grad, float* loss,
-                         cudaStream_t s);
-void launch_backward(const dt_scene& sc, const dt_views& vw, const dt_params& p, const void* ws,
-                     unsigned long long cap, const float* grad_out, float* dV, float* dior, float* dsigma, void* bws,
-                     unsigned long long max_level, cudaStream_t s);
 
 static thread_local char g_err[512] = "";
 
