@@ -360,6 +360,7 @@ __global__ void k_refit(const float* __restrict__ V, const int32_t* __restrict__
 // stable.
 constexpr int kSahBins = 32;       // bins per axis of the large-task levels
 constexpr int kSahSmallBins = 16;  // of the warp builder
+constexpr int kSahTiny = 4;        // ranges up to this size split at the centroid median
 constexpr int kSahSmall = 128;
 constexpr int kSahFreeDepth = 24;
 constexpr int kSahSmallFreeDepth = 56;
@@ -844,7 +845,20 @@ __global__ void __launch_bounds__(32 * kSahSmallWarps) k_sah_small(SahView S, Bv
       const float sc[3] = {sah_scale<kSahSmallBins>(lo.x, hi.x), sah_scale<kSahSmallBins>(lo.y, hi.y),
                            sah_scale<kSahSmallBins>(lo.z, hi.z)};
       int axis = -1, bin = -1, nl = rn / 2;
-      if (depth < kSahSmallFreeDepth && (sc[0] > 0.f || sc[1] > 0.f || sc[2] > 0.f)) {
+      // a range of at most kSahTiny triangles splits at the median of its
+      // centroids along their longest extent (ties by position): binning
+      // would cost far more than it can gain on a handful of triangles
+      const bool tiny = rn <= kSahTiny;
+      int tiny_rank = 0;
+      if (tiny) {
+        const float3 ext = hi - lo;
+        const int la = (ext.x >= ext.y && ext.x >= ext.z) ? 0 : (ext.y >= ext.z ? 1 : 2);
+        const float c = lane < rn ? comp(S.cen[ids[ra + lane]], la) : 0.f;
+        for (int j = 0; j < rn; ++j) {
+          const float cj = __shfl_sync(kFull, c, j);
+          tiny_rank += (cj < c || (cj == c && j < (int)lane)) ? 1 : 0;
+        }
+      } else if (depth < kSahSmallFreeDepth && (sc[0] > 0.f || sc[1] > 0.f || sc[2] > 0.f)) {
         sah_zero_bins(&sb, lane, 32);
         __syncwarp();
         for (int i = lane; i < rn; i += 32) {
@@ -882,7 +896,9 @@ __global__ void __launch_bounds__(32 * kSahSmallWarps) k_sah_small(SahView S, Bv
         bool left = false;
         if (valid) {
           p = ids[ra + i];
-          left = axis >= 0 ? sah_bin<kSahSmallBins>(comp(S.cen[p], axis), comp3(lo, axis), sc[axis]) <= bin : i < nl;
+          left = tiny ? tiny_rank < nl
+                      : (axis >= 0 ? sah_bin<kSahSmallBins>(comp(S.cen[p], axis), comp3(lo, axis), sc[axis]) <= bin
+                                   : i < nl);
         }
         const unsigned bal = __ballot_sync(kFull, left);
         const int lr = __popc(bal & ((1u << lane) - 1u));
