@@ -19,15 +19,44 @@ namespace dt {
 
 extern dt_tuning g_tuning;
 
-// backward scratch: two level buffers of (L, obar, dbar) and dN
+// An adjoint record (L, obar, dbar) of one segment: 9 floats in 36 bytes,
+// as two float4 arrays (L.xyz obar.x | obar.yz dbar.xy) and one float array
+// (dbar.z) of the level's length.
+struct AdjRecords {
+  float4* a;
+  float4* b;
+  float* c;
+  __device__ __forceinline__ void load(uint32_t i, float3& L, float3& ob, float3& db) const {
+    const float4 x = a[i], y = b[i];
+    L = mk(x.x, x.y, x.z);
+    ob = mk(x.w, y.x, y.y);
+    db = mk(y.z, y.w, c[i]);
+  }
+  __device__ __forceinline__ void store(uint32_t i, float3 L, float3 ob, float3 db) const {
+    a[i] = make_float4(L.x, L.y, L.z, ob.x);
+    b[i] = make_float4(ob.y, ob.z, db.x, db.y);
+    c[i] = db.z;
+  }
+};
+
+// backward scratch: two level buffers of adjoint records and the dN/dV
+// accumulators
 struct BwsLayout {
-  size_t off_buf0, off_buf1, off_dN, total;
+  size_t off_buf[2][3], off_dN, total;
   BwsLayout(unsigned long long max_level, int32_t nv) {
-    const size_t lvl = (size_t)max_level * 3 * sizeof(float4);
-    off_buf0 = 0;
-    off_buf1 = align_up(off_buf0 + lvl, 256);
-    off_dN = align_up(off_buf1 + lvl, 256);
+    size_t o = 0;
+    for (int k = 0; k < 2; ++k) {
+      off_buf[k][0] = o;
+      off_buf[k][1] = align_up(o + (size_t)max_level * sizeof(float4), 256);
+      off_buf[k][2] = align_up(off_buf[k][1] + (size_t)max_level * sizeof(float4), 256);
+      o = align_up(off_buf[k][2] + (size_t)max_level * sizeof(float), 256);
+    }
+    off_dN = o;
     total = align_up(off_dN + (size_t)nv * 2 * sizeof(float4), 256);
+  }
+  AdjRecords records(void* base, int k) const {
+    char* b = (char*)base;
+    return AdjRecords{(float4*)(b + off_buf[k][0]), (float4*)(b + off_buf[k][1]), (float*)(b + off_buf[k][2])};
   }
 };
 
@@ -55,14 +84,14 @@ struct SceneSums {
 
 // out_next: (L, obar, dbar) of level k+1 indexed by position in that level;
 // out_cur: the same for level k (not written for k = 0: camera rays have no
-// parent).  Each entry is 3 float4 (xyz used).
+// parent); see AdjRecords.
 // kBatch = false: one scene, whose entry E0 arrives as a kernel parameter;
 // true: each segment looks its scene up.
 constexpr int kAdjointMinBlocks = 3;  // CTAs of 256 per SM the register budget is sized for
 
 template <bool kBatch>
-__global__ void __launch_bounds__(256, kAdjointMinBlocks) k_adjoint(WsView W, int k, const float4* __restrict__ out_next,
-                                                 float4* __restrict__ out_cur, const SceneEntry E0) {
+__global__ void __launch_bounds__(256, kAdjointMinBlocks) k_adjoint(WsView W, int k, const AdjRecords out_next,
+                                                                   const AdjRecords out_cur, const SceneEntry E0) {
   extern __shared__ float sums_smem[];
   const WsHeader* H = W.hdr;
   const int n_scenes = kBatch ? W.th->n : 1;
@@ -124,10 +153,10 @@ __global__ void __launch_bounds__(256, kAdjointMinBlocks) k_adjoint(WsView W, in
         float3 Lr = mk(0.f, 0.f, 0.f), orb = Lr, drb = Lr, Lt = Lr, otb = Lr, dtb = Lr;
         const uint32_t jr = (uint32_t)ch - next_start;
         if (jr < n_next) {
-          Lr = xyz(out_next[3 * jr]); orb = xyz(out_next[3 * jr + 1]); drb = xyz(out_next[3 * jr + 2]);
+          out_next.load(jr, Lr, orb, drb);
         }
         if (!tir && jr + 1 < n_next) {
-          Lt = xyz(out_next[3 * (jr + 1)]); otb = xyz(out_next[3 * (jr + 1) + 1]); dtb = xyz(out_next[3 * (jr + 1) + 2]);
+          out_next.load(jr + 1, Lt, otb, dtb);
         }
         const float R = tir ? 1.0f : h.R, T = tir ? 0.0f : h.T;
         const float3 mix = Lr * R + Lt * T;
@@ -219,9 +248,7 @@ __global__ void __launch_bounds__(256, kAdjointMinBlocks) k_adjoint(WsView W, in
       }
     }
     if (k > 0) {
-      out_cur[3 * i] = make_float4(L.x, L.y, L.z, 0.f);
-      out_cur[3 * i + 1] = make_float4(obar.x, obar.y, obar.z, 0.f);
-      out_cur[3 * i + 2] = make_float4(dbar.x, dbar.y, dbar.z, 0.f);
+      out_cur.store(i, L, obar, dbar);
     }
   }
   sums.add(cur, acc_ior, acc_sig);
@@ -313,8 +340,7 @@ void launch_backward_table(const TableHeader& th, const SceneEntry* entries, con
                            unsigned long long ring, void* bws, unsigned long long max_level, cudaStream_t s) {
   WsView W = ws_view(ws, cap, ring);
   BwsLayout L(max_level, 0);
-  char* b = (char*)bws;
-  float4* buf[2] = {(float4*)(b + L.off_buf0), (float4*)(b + L.off_buf1)};
+  const AdjRecords buf[2] = {L.records(bws, 0), L.records(bws, 1)};
   const int n = th.n;
   launch_write_table(W, th, entries, n, s);
   int max_nv = 1, max_nf = 1;
