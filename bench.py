@@ -177,6 +177,14 @@ def oracle_sample(sc, Vt, n_pix, seed=12345):
     return nseg, dt
 
 
+def workload_config(sc, views_per_rank, res, depth, world):
+    """The config object both arms print for the genus-2 workload."""
+    return {"workload": f"genus-2 two-tori mesh ({sc.F.shape[0]} triangles), {views_per_rank * world} views "
+                        f"{res}x{res}, depth {depth}, 1 spp, IoR {sc.ior:.4f}, fwd+bwd of an L2 image loss",
+            "views": views_per_rank * world, "width": res, "height": res, "max_depth": depth,
+            "triangles": int(sc.F.shape[0])}
+
+
 def cpu_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -208,8 +216,7 @@ def run_reference(args):
         "warmup": args.warmup, "ms_per_step": 1000.0 * secs / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "impl": "reference",
-        "config": {"workload": f"genus-2 two-tori mesh {sc.F.shape[0]} triangles, {args.views} views "
-                               f"{args.res}x{args.res}, depth {args.depth}, fwd+bwd; CPU sample", "spp": 1},
+        "config": workload_config(sc, args.views, args.res, args.depth, 1),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -680,9 +687,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"genus-2 two-tori mesh ({sc.F.shape[0]} triangles), {nvw} views {res}x{res}, "
-                                   f"depth {D}, 1 spp, IoR {sc.ior:.4f}, fwd+bwd of an L2 image loss",
-                       "views": nvw, "width": res, "height": res, "max_depth": D, "triangles": int(sc.F.shape[0]),
+            "config": {**workload_config(sc, nvw, res, D, world),
                        "segments_per_step": int(seg_all), "l2": "flushed by a 512 MB write before every timed step",
                        "bvh": "binned SAH" if dt.get_tuning()["bvh_builder"] == 1 else "LBVH",
                        "parallelism": f"replicas over disjoint views x{world}"},
