@@ -261,6 +261,53 @@ __device__ __forceinline__ int visit_node2_deferred(const float4* __restrict__ n
   return sp > 0 ? stack[--sp] : -1;
 }
 
+// The 4-wide visit of the persistent traversal, with hit leaves queued as
+// in visit_node2_deferred (the caller visits only while nothing is pending,
+// so four slots suffice).
+__device__ __forceinline__ void push_pending4(int leaf, int& p0, int& p1, int& p2, int& p3) {
+  if (p0 < 0) p0 = leaf;
+  else if (p1 < 0) p1 = leaf;
+  else if (p2 < 0) p2 = leaf;
+  else p3 = leaf;
+}
+__device__ __forceinline__ int visit_node4_deferred(const float4* __restrict__ node4, int node, float3 o, float3 idir,
+                                                    float tmin, float tmax, int* stack, int& sp, bool& overflow,
+                                                    int& p0, int& p1, int& p2, int& p3) {
+  const float4* Np = node4 + 8 * node;
+  const float4 lx = __ldg(Np), hx = __ldg(Np + 1), ly = __ldg(Np + 2), hy = __ldg(Np + 3);
+  const float4 lz = __ldg(Np + 4), hz = __ldg(Np + 5);
+  const int4 ch = __ldg(reinterpret_cast<const int4*>(Np) + 6);
+  float t0, t1, t2, t3;
+  bool b0 = ch.x != kNoChild && slab(o, idir, lx.x, hx.x, ly.x, hy.x, lz.x, hz.x, tmin, tmax, t0);
+  bool b1 = ch.y != kNoChild && slab(o, idir, lx.y, hx.y, ly.y, hy.y, lz.y, hz.y, tmin, tmax, t1);
+  bool b2 = ch.z != kNoChild && slab(o, idir, lx.z, hx.z, ly.z, hy.z, lz.z, hz.z, tmin, tmax, t2);
+  bool b3 = ch.w != kNoChild && slab(o, idir, lx.w, hx.w, ly.w, hy.w, lz.w, hz.w, tmin, tmax, t3);
+  if (b0 && ch.x < 0) { push_pending4(~ch.x, p0, p1, p2, p3); b0 = false; }
+  if (b1 && ch.y < 0) { push_pending4(~ch.y, p0, p1, p2, p3); b1 = false; }
+  if (b2 && ch.z < 0) { push_pending4(~ch.z, p0, p1, p2, p3); b2 = false; }
+  if (b3 && ch.w < 0) { push_pending4(~ch.w, p0, p1, p2, p3); b3 = false; }
+  float ta = b0 ? t0 : INFINITY, tb = b1 ? t1 : INFINITY, tc = b2 ? t2 : INFINITY, td = b3 ? t3 : INFINITY;
+  int ra = ch.x, rb = ch.y, rc = ch.z, rd = ch.w;
+  const int cnt = b0 + b1 + b2 + b3;
+  if (cnt == 0) return sp > 0 ? stack[--sp] : -1;
+#define DT_CSWAP(ta_, ra_, tb_, rb_)                     \
+  if (tb_ < ta_) {                                      \
+    const float tt = ta_; ta_ = tb_; tb_ = tt;          \
+    const int rr = ra_; ra_ = rb_; rb_ = rr;            \
+  }
+  DT_CSWAP(ta, ra, tb, rb) DT_CSWAP(tc, rc, td, rd) DT_CSWAP(ta, ra, tc, rc) DT_CSWAP(tb, rb, td, rd)
+  DT_CSWAP(tb, rb, tc, rc)
+#undef DT_CSWAP
+  if (sp + cnt - 1 > kTraceStack) {
+    overflow = true;
+    return ra;
+  }
+  if (cnt >= 4) stack[sp++] = rd;
+  if (cnt >= 3) stack[sp++] = rc;
+  if (cnt >= 2) stack[sp++] = rb;
+  return ra;
+}
+
 template <int kWidth>
 __device__ __forceinline__ int visit_node(const float4* __restrict__ nodes, const float4* __restrict__ tris, int node,
                                           float3 o, float3 d, float3 idir, int src, float tmin, ClosestHit& h,
@@ -400,10 +447,16 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_trace(WsView W, int k, int 
           }
         }
       } else {
-        for (; st < steps; ++st) {
-          node = visit_node<kWidth>(nodes, tris, node, o, d, idir, src, tmin, h, stack, sp, overflow, ntest);
+        int p0 = -1, p1 = -1, p2 = -1, p3 = -1;
+        while (st < steps) {
+          for (int j = 0; j < kLeafEvery && node >= 0 && p0 < 0; ++j, ++st)
+            node = visit_node4_deferred(nodes, node, o, idir, tmin, h.t, stack, sp, overflow, p0, p1, p2, p3);
+          if (p0 >= 0) test_leaf(tris, p0, o, d, src, tmin, h, ntest);
+          if (p1 >= 0) test_leaf(tris, p1, o, d, src, tmin, h, ntest);
+          if (p2 >= 0) test_leaf(tris, p2, o, d, src, tmin, h, ntest);
+          if (p3 >= 0) test_leaf(tris, p3, o, d, src, tmin, h, ntest);
+          p0 = p1 = p2 = p3 = -1;
           if (node < 0) {
-            ++st;
             done = true;
             break;
           }
