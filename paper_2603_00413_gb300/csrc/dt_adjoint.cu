@@ -149,14 +149,15 @@ __global__ void __launch_bounds__(256, kAdjointMinBlocks) k_adjoint(WsView W, in
         const bool tir = (fl & SF_TIR) != 0;
         HitShade h;
         shade_hit(o, d, t, b1, b2, v0, v1, v2, N0, N1, N2, ior, sigma, h, tir ? 1 : 0);
-        // children: reflected at ch, refracted at ch + 1
+        // children: reflected at ch, refracted at ch + (flags >> kRefractShift)
         float3 Lr = mk(0.f, 0.f, 0.f), orb = Lr, drb = Lr, Lt = Lr, otb = Lr, dtb = Lr;
         const uint32_t jr = (uint32_t)ch - next_start;
+        const uint32_t jt = jr + (fl >> kRefractShift);
         if (jr < n_next) {
           out_next.load(jr, Lr, orb, drb);
         }
-        if (!tir && jr + 1 < n_next) {
-          out_next.load(jr + 1, Lt, otb, dtb);
+        if (!tir && jt < n_next) {
+          out_next.load(jt, Lt, otb, dtb);
         }
         const float R = tir ? 1.0f : h.R, T = tir ? 0.0f : h.T;
         const float3 mix = Lr * R + Lt * T;

@@ -43,7 +43,9 @@ enum : uint32_t {
   SF_BACKFACING = 16u,
   SF_DISCARDED = 128u,
   SF_MISS = 512u,
+  SF_FLAG_BITS = 0xffffu,  // the event bits; above them the refracted child's offset
 };
+constexpr int kRefractShift = 16;  // sflag >> 16 = refracted child index - reflected child index
 
 // device status bits (render workspace header)
 enum : uint32_t {
@@ -137,9 +139,9 @@ __host__ __device__ inline BvhView bvh_view(const void* base, int32_t nf) {
 //   ray_d[i] = (direction xyz, heap node id as int bits)
 //   ray_w[i] = (throughput rgb, triangle the ray leaves from, or -1)
 //   hit[i]   = (t, b1, b2, hit triangle or -1)
-//   child[i] = arena index of the first child (reflected; refracted at +1
-//              unless total internal reflection), -1 when it has none
-//   sflag[i] = SF_* bits
+//   child[i] = arena index of the reflected child, -1 when it has none
+//   sflag[i] = SF_* bits; bits 16-31: the refracted child's index minus
+//              child[i] (0 when there is none: total internal reflection)
 // ---------------------------------------------------------------------------
 struct WsHeader {
   uint32_t status;

@@ -520,8 +520,8 @@ __global__ void __launch_bounds__(kShadeThreads, kShadeMinBlocks) k_shade(WsView
     H->level_start[k + 1] = next_start;
     if (n) H->n_levels = (uint32_t)(k + 1);
   }
-  __shared__ uint32_t s_woff[kShadeThreads / 32];
-  __shared__ uint32_t s_base;
+  __shared__ uint32_t s_wr[kShadeThreads / 32], s_wt[kShadeThreads / 32];
+  __shared__ uint32_t s_base, s_nr;
   const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   uint32_t c_hit = 0, c_miss = 0, c_disc = 0, c_back = 0, c_tir = 0;
   bool overflow = false;
@@ -531,6 +531,7 @@ __global__ void __launch_bounds__(kShadeThreads, kShadeMinBlocks) k_shade(WsView
     const uint32_t i = tile + threadIdx.x;
     const uint32_t a = start + i;
     int nchild = 0;
+    uint32_t fl = 0;
     float4 co = make_float4(0.f, 0.f, 0.f, 0.f), cdr = co, cwr = co, cdt = co, cwt = co;
     if (i < n) {
       const float4 ro = W.ray_o[a], rd = W.ray_d[a], rw = W.ray_w[a], hh = W.hit[hit_slot(W, k, a, i)];
@@ -538,7 +539,6 @@ __global__ void __launch_bounds__(kShadeThreads, kShadeMinBlocks) k_shade(WsView
       const SceneEntry& E = kBatch ? W.ent[find_scene(W.th->starts, n_scenes, sample)] : E0;
       const int tri = __float_as_int(hh.w);
       const float3 d = xyz(rd);
-      uint32_t fl = 0;
       if (tri < 0) {  // step 3: no intersection -> environment
         fl = SF_MISS;
         ++c_miss;
@@ -585,51 +585,60 @@ __global__ void __launch_bounds__(kShadeThreads, kShadeMinBlocks) k_shade(WsView
           }
         }
       }
-      W.sflag[a] = fl;
     }
-    // CTA-aggregated append of the children to level k+1: warp scans, a
-    // prefix over the warps, one atomic
-    int incl = nchild;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int v = __shfl_up_sync(kFull, incl, o);
-      if ((int)lane >= o) incl += v;
+    // CTA-aggregated append of the children to level k+1, the tile's
+    // reflected children first and its refracted ones after them: rays of
+    // one kind from neighbouring parents take similar paths, so the next
+    // level's warps diverge less than with the two kinds interleaved.  Warp
+    // ballots, a prefix over the warps, one atomic per tile.
+    const unsigned br = __ballot_sync(kFull, nchild > 0), bt = __ballot_sync(kFull, nchild == 2);
+    if (lane == 0) {
+      s_wr[wid] = __popc(br);
+      s_wt[wid] = __popc(bt);
     }
-    if (lane == 31) s_woff[wid] = (uint32_t)incl;
     __syncthreads();
     if (threadIdx.x == 0) {
-      uint32_t run = 0;
+      uint32_t rr = 0, tt = 0;
       for (int w = 0; w < kShadeThreads / 32; ++w) {
-        const uint32_t t = s_woff[w];
-        s_woff[w] = run;
-        run += t;
+        const uint32_t x = s_wr[w], y = s_wt[w];
+        s_wr[w] = rr;
+        s_wt[w] = tt;
+        rr += x;
+        tt += y;
       }
-      s_base = run ? atomicAdd(&H->level_count[k + 1], run) : 0u;
+      s_base = (rr + tt) ? atomicAdd(&H->level_count[k + 1], rr + tt) : 0u;
+      s_nr = rr;
     }
     __syncthreads();
-    const uint32_t base = s_base + s_woff[wid];
-    __syncthreads();  // s_woff and s_base are rewritten by the next tile
+    const uint32_t tile_base = s_base, tile_nr = s_nr, off_r = s_wr[wid], off_t = s_wt[wid];
+    __syncthreads();  // the shared offsets are rewritten by the next tile
     if (i < n) {
       int32_t ch = -1;
+      uint32_t delta = 0;
       if (nchild > 0) {
-        const unsigned long long j = (unsigned long long)next_start + base + (uint32_t)(incl - nchild);
-        if (j + (unsigned long long)nchild <= H->capacity) {
-          ch = (int32_t)j;
-          W.ray_o[j] = co; W.ray_d[j] = cdr; W.ray_w[j] = cwr;
-          if (nchild == 2) { W.ray_o[j + 1] = co; W.ray_d[j + 1] = cdt; W.ray_w[j + 1] = cwt; }
+        // every allocated position below the capacity is written by exactly
+        // one child; a child past the capacity is dropped (overflow)
+        const uint32_t below = (1u << lane) - 1u;
+        const unsigned long long jr = (unsigned long long)next_start + tile_base + off_r + __popc(br & below);
+        if (jr < H->capacity) {
+          ch = (int32_t)jr;
+          W.ray_o[jr] = co; W.ray_d[jr] = cdr; W.ray_w[jr] = cwr;
         } else {
           overflow = true;
-          // a pair that straddles the end of the arena: the slot that still
-          // fits gets an inert record (zero direction, no pixel) so nothing
-          // below the capacity is ever left unwritten
-          if (j < H->capacity) {
-            W.ray_o[j] = make_float4(0.f, 0.f, 0.f, __uint_as_float(0xffffffffu));
-            W.ray_d[j] = make_float4(0.f, 0.f, 0.f, __uint_as_float(0u));
-            W.ray_w[j] = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+        }
+        if (nchild == 2) {
+          const unsigned long long jt =
+              (unsigned long long)next_start + tile_base + tile_nr + off_t + __popc(bt & below);
+          delta = (uint32_t)(jt - jr);
+          if (jt < H->capacity) {
+            W.ray_o[jt] = co; W.ray_d[jt] = cdt; W.ray_w[jt] = cwt;
+          } else {
+            overflow = true;
           }
         }
       }
       W.child[a] = ch;
+      W.sflag[a] = fl | (delta << kRefractShift);
     }
   }
   warp_add_u64(&H->counters[CNT_HITS], c_hit);
@@ -653,7 +662,7 @@ __global__ void k_dump(WsView W, int32_t* __restrict__ si, float* __restrict__ s
     si[4 * a + 0] = __float_as_int(ro.w);
     si[4 * a + 1] = __float_as_int(rd.w);
     si[4 * a + 2] = __float_as_int(hh.w);
-    si[4 * a + 3] = (int32_t)W.sflag[a];
+    si[4 * a + 3] = (int32_t)(W.sflag[a] & SF_FLAG_BITS);
     float* f = sf + 9 * a;
     f[0] = hh.x; f[1] = hh.y; f[2] = hh.z;
     f[3] = ro.x; f[4] = ro.y; f[5] = ro.z;
