@@ -123,7 +123,8 @@ using V3d = V3<double>;
 
 // ---------------------------------------------------------------------------
 // Eq. 13: vertex normal = (1/3) * sum over incident faces of the unit normal
-// (v1 - v0) x (v2 - v0) / |(v1 - v0) x (v2 - v0)|.
+// (v1 - v0) x (v2 - v0) / |(v1 - v0) x (v2 - v0)|.  A zero-area face has no
+// unit normal and adds nothing.
 // ---------------------------------------------------------------------------
 template <class T>
 void vertex_normals(const std::vector<V3<T>>& V, const int* F, int nf, std::vector<V3<T>>& N) {
@@ -131,6 +132,7 @@ void vertex_normals(const std::vector<V3<T>>& V, const int* F, int nf, std::vect
   for (int f = 0; f < nf; ++f) {
     const int i0 = F[3 * f], i1 = F[3 * f + 1], i2 = F[3 * f + 2];
     V3<T> c = cross(V[i1] - V[i0], V[i2] - V[i0]);
+    if (!(val(dot(c, c)) > 0.0)) continue;
     V3<T> u = normalize(c);
     N[i0] = N[i0] + u; N[i1] = N[i1] + u; N[i2] = N[i2] + u;
   }

@@ -287,6 +287,7 @@ __global__ void k_face_normals_backward_table(const SceneEntry* __restrict__ ent
     const float3 e1 = v1 - v0, e2 = v2 - v0;
     const float3 c = cross(e1, e2);
     const float lc = len(c);
+    if (!(lc > 0.0f)) continue;  // a zero-area face added nothing to the normals
     const float3 u = mk(c.x / lc, c.y / lc, c.z / lc);
     const float3 du = (xyz(dN4[i0]) + xyz(dN4[i1]) + xyz(dN4[i2])) * (1.0f / 3.0f);
     const float3 dc = (du - u * dot(u, du)) * (1.0f / lc);

@@ -175,6 +175,7 @@ __device__ __forceinline__ void face_normal_backward_one(const float* __restrict
   const float3 e1 = v1 - v0, e2 = v2 - v0;
   const float3 c = cross(e1, e2);
   const float lc = len(c);
+  if (!(lc > 0.0f)) return;  // a zero-area face added nothing to the normals
   const float3 u = mk(c.x / lc, c.y / lc, c.z / lc);
   const float3 du = (load3(dN + 3 * i0) + load3(dN + 3 * i1) + load3(dN + 3 * i2)) * (1.0f / 3.0f);
   const float3 dc = (du - u * dot(u, du)) * (1.0f / lc);

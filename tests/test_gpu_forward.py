@@ -34,6 +34,36 @@ def test_vertex_normals_match_oracle():
         np.testing.assert_allclose(N, No, rtol=0, atol=2e-5)
 
 
+def test_zero_area_faces_render_and_differentiate():
+    """Faces of zero area (a repeated vertex) add nothing to the Eq. 13
+    normals, are never hit (Moller-Trumbore's determinant is 0) and add no
+    gradient: normals, image and gradients stay finite and match the oracle
+    and the same mesh without them."""
+    V, F = S.icosphere(3)
+    Fd = np.concatenate([F, F[:40, [0, 0, 2]], F[40:80, [1, 2, 2]]]).astype(np.int32)
+    env = S.sh_env_map(64, 32, 0)
+    cam = S.camera((0.4, 0.7, 2.8), (0, 0, 0), (0, 1, 0), 45.0, 32, 32)
+    sigma = np.array([0.5, 1.0, 1.5], np.float32)
+    Vt = torch.from_numpy(V).cuda()
+    N = dt.vertex_normals(Vt, torch.from_numpy(Fd).cuda())
+    assert torch.isfinite(N).all()
+    np.testing.assert_allclose(N.cpu().numpy(), O.vertex_normals(V, Fd), rtol=0, atol=2e-5)
+    np.testing.assert_array_equal(N.cpu().numpy(), dt.vertex_normals(Vt, torch.from_numpy(F).cuda()).cpu().numpy())
+    gd = GpuScene(V, Fd, 1.45, sigma, env, [cam], 32, 32, 4)
+    g0 = GpuScene(V, F, 1.45, sigma, env, [cam], 32, 32, 4)
+    img_d, tape_d = gd.render()
+    img_0, tape_0 = g0.render()
+    assert tape_d.stats["segments"] == tape_0.stats["segments"]
+    np.testing.assert_allclose(img_d.cpu().numpy(), img_0.cpu().numpy(), rtol=1e-6, atol=1e-7)
+    assert_radiance_parity(img_d[0], gd.oracle(0))
+    g = torch.randn_like(img_d)
+    dVd, diord, dsigd = dt.render_backward(tape_d, g)
+    dV0, dior0, dsig0 = dt.render_backward(tape_0, g)
+    assert torch.isfinite(dVd).all()
+    np.testing.assert_allclose(dVd.cpu().numpy(), dV0.cpu().numpy(), rtol=1e-4, atol=1e-5)
+    assert float(diord) == pytest.approx(float(dior0), rel=1e-4, abs=1e-6)
+
+
 def test_vertex_normals_backward_matches_finite_differences():
     """<dN/dV u, w> by central differences of the (FP64) oracle normals."""
     V, F = S.icosphere(2)

@@ -492,3 +492,19 @@ def test_forward_mode_matches_central_differences():
         scale = np.abs(jvp).max()
         assert scale > 0
         np.testing.assert_allclose(jvp[stable], fd[stable], rtol=0, atol=2e-6 * scale)
+
+
+def test_zero_area_faces_add_nothing_to_vertex_normals():
+    """Eq. 13 averages unit face normals; a face of zero area has none, so
+    adding degenerate faces (a repeated vertex, three collinear vertices)
+    leaves every vertex normal as it was and nothing becomes NaN."""
+    V, F = S.icosphere(1)
+    base = O.vertex_normals(V, F)
+    m = V.shape[0]
+    line = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [2.0, 0.0, 0.0]], V.dtype)  # exactly collinear
+    V2 = np.concatenate([V, line])
+    F2 = np.concatenate([F, [[F[0, 0], F[0, 0], F[0, 2]], [F[3, 1], F[3, 2], F[3, 2]], [m, m + 1, m + 2]]])
+    n2 = O.vertex_normals(V2, F2.astype(np.int32))
+    assert np.isfinite(n2).all()
+    np.testing.assert_array_equal(n2[:m], base)
+    np.testing.assert_array_equal(n2[m:], 0.0)
