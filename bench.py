@@ -185,6 +185,20 @@ def workload_config(sc, views_per_rank, res, depth, world):
             "triangles": int(sc.F.shape[0])}
 
 
+def cpu_model():
+    """The host CPU's model string (x86 'model name', Arm implementer/part)."""
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+    except OSError:
+        return None
+    for key in ("model name", "Model", "Hardware"):
+        for line in info:
+            if line.startswith(key) and ":" in line:
+                return line.split(":", 1)[1].strip()
+    parts = sorted({line.split(":", 1)[1].strip() for line in info if line.startswith("CPU part")})
+    return "CPU part " + ",".join(parts) if parts else None
+
+
 def cpu_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -217,7 +231,8 @@ def run_reference(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "impl": "reference",
         "config": workload_config(sc, args.views, args.res, args.depth, 1),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "cpu": cpu_model(),
+                         "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out))
@@ -666,7 +681,8 @@ def run_ours(args):
         import oracle as O
         O.build()
         nseg, secs = oracle_sample(sc, Vt_np, args.cpu_sample)
-        cpu = {"value": nseg / secs, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+        cpu = {"value": nseg / secs, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "cpu": cpu_model(),
+               "triangle_tests_per_s": nseg * sc.F.shape[0] / secs,
                "sample": f"{args.cpu_sample} seeded pixels of the same workload ({nseg} segments), forward + "
                          f"gradient by forward mode over the parameters those paths touch, {secs:.1f} s"}
 
@@ -693,6 +709,7 @@ def run_ours(args):
                        "parallelism": f"replicas over disjoint views x{world}"},
             "fwd_segments_per_s": fwd_value,
             "ms_per_step_fwd": fwd_ms / args.steps,
+            "ms_per_step_p50": float(np.percentile(ms, 50)), "ms_per_step_p90": float(np.percentile(ms, 90)),
             "roofline": roofline,
             "kernel_share": kernel_share,
             "gpu_launches": gpu_launches,
