@@ -285,7 +285,7 @@ __global__ void k_face_normals_backward_table(const SceneEntry* __restrict__ ent
     const int i0 = E.F[3 * f], i1 = E.F[3 * f + 1], i2 = E.F[3 * f + 2];
     const float3 v0 = load3(E.V + 3 * i0), v1 = load3(E.V + 3 * i1), v2 = load3(E.V + 3 * i2);
     const float3 e1 = v1 - v0, e2 = v2 - v0;
-    const float3 c = cross(e1, e2);
+    const float3 c = cross_rn(e1, e2);
     const float lc = len(c);
     if (!(lc > 0.0f)) continue;  // a zero-area face added nothing to the normals
     const float3 u = mk(c.x / lc, c.y / lc, c.z / lc);

@@ -27,7 +27,7 @@ __global__ void k_face_normals_scatter(const float* __restrict__ V, const int32_
   for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nf; f += gridDim.x * blockDim.x) {
     const int i0 = F[3 * f], i1 = F[3 * f + 1], i2 = F[3 * f + 2];
     const float3 v0 = load3(V + 3 * i0), v1 = load3(V + 3 * i1), v2 = load3(V + 3 * i2);
-    const float3 c = cross(v1 - v0, v2 - v0);
+    const float3 c = cross_rn(v1 - v0, v2 - v0);
     const float lc = len(c);
     if (!(lc > 0.0f)) continue;  // a zero-area face has no unit normal and adds nothing
     const float3 u = mk(c.x / lc, c.y / lc, c.z / lc);

@@ -27,6 +27,13 @@ __host__ __device__ __forceinline__ float3 cross(float3 a, float3 b) {
   return mk(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
 }
 __host__ __device__ __forceinline__ float len(float3 a) { return sqrtf(dot(a, a)); }
+// cross product with every product rounded before the subtraction (no fused
+// multiply-add): exactly zero for parallel inputs such as a x a, which a
+// contracted form is not (it keeps one product's rounding error)
+__device__ __forceinline__ float3 cross_rn(float3 a, float3 b) {
+  return mk(__fsub_rn(__fmul_rn(a.y, b.z), __fmul_rn(a.z, b.y)), __fsub_rn(__fmul_rn(a.z, b.x), __fmul_rn(a.x, b.z)),
+            __fsub_rn(__fmul_rn(a.x, b.y), __fmul_rn(a.y, b.x)));
+}
 __host__ __device__ __forceinline__ float3 normalize(float3 a) {
   float n = len(a);
   return mk(a.x / n, a.y / n, a.z / n);

@@ -173,7 +173,7 @@ __device__ __forceinline__ void face_normal_backward_one(const float* __restrict
   const int i0 = F[3 * f], i1 = F[3 * f + 1], i2 = F[3 * f + 2];
   const float3 v0 = load3(V + 3 * i0), v1 = load3(V + 3 * i1), v2 = load3(V + 3 * i2);
   const float3 e1 = v1 - v0, e2 = v2 - v0;
-  const float3 c = cross(e1, e2);
+  const float3 c = cross_rn(e1, e2);
   const float lc = len(c);
   if (!(lc > 0.0f)) return;  // a zero-area face added nothing to the normals
   const float3 u = mk(c.x / lc, c.y / lc, c.z / lc);
