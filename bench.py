@@ -195,8 +195,9 @@ def cpu_model():
         for line in info:
             if line.startswith(key) and ":" in line:
                 return line.split(":", 1)[1].strip()
+    arm = {"0xd4f": "Arm Neoverse V2", "0xd40": "Arm Neoverse V1", "0xd0c": "Arm Neoverse N1", "0xd49": "Arm Neoverse N2"}
     parts = sorted({line.split(":", 1)[1].strip() for line in info if line.startswith("CPU part")})
-    return "CPU part " + ",".join(parts) if parts else None
+    return ", ".join(arm.get(p, "CPU part " + p) for p in parts) if parts else None
 
 
 def cpu_cores():
@@ -682,7 +683,6 @@ def run_ours(args):
         O.build()
         nseg, secs = oracle_sample(sc, Vt_np, args.cpu_sample)
         cpu = {"value": nseg / secs, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "cpu": cpu_model(),
-               "triangle_tests_per_s": nseg * sc.F.shape[0] / secs,
                "sample": f"{args.cpu_sample} seeded pixels of the same workload ({nseg} segments), forward + "
                          f"gradient by forward mode over the parameters those paths touch, {secs:.1f} s"}
 
