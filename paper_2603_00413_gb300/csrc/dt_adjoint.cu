@@ -87,7 +87,7 @@ struct SceneSums {
 // parent); see AdjRecords.
 // kBatch = false: one scene, whose entry E0 arrives as a kernel parameter;
 // true: each segment looks its scene up.
-constexpr int kAdjointMinBlocks = 3;  // CTAs of 256 per SM the register budget is sized for
+constexpr int kAdjointMinBlocks = 4;  // CTAs of 256 per SM the register budget is sized for
 
 template <bool kBatch>
 __global__ void __launch_bounds__(256, kAdjointMinBlocks) k_adjoint(WsView W, int k, const AdjRecords out_next,
