@@ -333,7 +333,7 @@ dt_status dt_l2_loss_grad(const float* d_img, const float* d_target, int64_t n, 
  * area heuristic (32 centroid bins per axis, 16 for ranges of at most 128
  * triangles; fewer node visits per ray, slower to build); dt_refit_bvh
  * keeps whichever topology was built.
- * Defaults {64, 8, 5, 8, 2, 1}; results do not depend on them (the same
+ * Defaults {64, 8, 5, 4, 2, 1}; results do not depend on them (the same
  * closest hit is found).  dt_set_tuning rejects values outside steps
  * 1..256, refill 1..32, trace 1..8, shade 1..16, width 2 or 4, builder 0
  * or 1.
