@@ -154,57 +154,11 @@ __device__ __forceinline__ void test_leaf(const float4* __restrict__ tris, int l
   }
 }
 
-// One visit of 4-wide node `node`: slab tests on its four children, leaf
-// children intersected at once, internal children that were hit (and are not
-// beyond the closest hit so far) entered nearest first with the others pushed
-// farthest first.  Returns the next node, or -1 when the stack is empty.
-// Empty child slots (kNoChild) are masked explicitly: a slab test only
-// intersects intervals, so it would accept their inverted (+inf, -inf) box.
-// References need no range check here: the build validated them (k_validate)
-// and the traversal kernels refuse a tree that failed.
-__device__ __forceinline__ int visit_node4(const float4* __restrict__ node4, const float4* __restrict__ tris, int node,
-                                           float3 o, float3 d, float3 idir, int src, float tmin, ClosestHit& h,
-                                           int* stack, int& sp, bool& overflow, uint32_t& ntest) {
-  const float4* Np = node4 + 8 * node;
-  const float4 lx = __ldg(Np), hx = __ldg(Np + 1), ly = __ldg(Np + 2), hy = __ldg(Np + 3);
-  const float4 lz = __ldg(Np + 4), hz = __ldg(Np + 5);
-  const int4 ch = __ldg(reinterpret_cast<const int4*>(Np) + 6);
-  float t0, t1, t2, t3;
-  bool b0 = ch.x != kNoChild && slab(o, idir, lx.x, hx.x, ly.x, hy.x, lz.x, hz.x, tmin, h.t, t0);
-  bool b1 = ch.y != kNoChild && slab(o, idir, lx.y, hx.y, ly.y, hy.y, lz.y, hz.y, tmin, h.t, t1);
-  bool b2 = ch.z != kNoChild && slab(o, idir, lx.z, hx.z, ly.z, hy.z, lz.z, hz.z, tmin, h.t, t2);
-  bool b3 = ch.w != kNoChild && slab(o, idir, lx.w, hx.w, ly.w, hy.w, lz.w, hz.w, tmin, h.t, t3);
-  if (b0 && ch.x < 0) { test_leaf(tris, ~ch.x, o, d, src, tmin, h, ntest); b0 = false; }
-  if (b1 && ch.y < 0) { test_leaf(tris, ~ch.y, o, d, src, tmin, h, ntest); b1 = false; }
-  if (b2 && ch.z < 0) { test_leaf(tris, ~ch.z, o, d, src, tmin, h, ntest); b2 = false; }
-  if (b3 && ch.w < 0) { test_leaf(tris, ~ch.w, o, d, src, tmin, h, ntest); b3 = false; }
-  // internal children still in front of the closest hit, as (t, ref) pairs
-  float ta = (b0 && t0 <= h.t) ? t0 : INFINITY, tb = (b1 && t1 <= h.t) ? t1 : INFINITY;
-  float tc = (b2 && t2 <= h.t) ? t2 : INFINITY, td = (b3 && t3 <= h.t) ? t3 : INFINITY;
-  int ra = ch.x, rb = ch.y, rc = ch.z, rd = ch.w;
-  const int cnt = (ta < INFINITY) + (tb < INFINITY) + (tc < INFINITY) + (td < INFINITY);
-  if (cnt == 0) return sp > 0 ? stack[--sp] : -1;
-  // sort the four pairs by t (five compare-exchanges)
-#define DT_CSWAP(ta_, ra_, tb_, rb_)                     \
-  if (tb_ < ta_) {                                      \
-    const float tt = ta_; ta_ = tb_; tb_ = tt;          \
-    const int rr = ra_; ra_ = rb_; rb_ = rr;            \
-  }
-  DT_CSWAP(ta, ra, tb, rb) DT_CSWAP(tc, rc, td, rd) DT_CSWAP(ta, ra, tc, rc) DT_CSWAP(tb, rb, td, rd)
-  DT_CSWAP(tb, rb, tc, rc)
-#undef DT_CSWAP
-  if (sp + cnt - 1 > kTraceStack) {
-    overflow = true;
-    return ra;
-  }
-  if (cnt >= 4) stack[sp++] = rd;
-  if (cnt >= 3) stack[sp++] = rc;
-  if (cnt >= 2) stack[sp++] = rb;
-  return ra;
-}
-
-// One visit of binary node `node` (same contract as visit_node4; binary
-// nodes always have two children).
+// One visit of binary node `node`: slab tests on its two children, leaf
+// children intersected at once, internal children that were hit entered
+// nearest first with the other pushed.  Returns the next node, or -1 when the
+// stack is empty.  (Used by the closest-hit tool; the persistent traversal
+// uses visit_node2_deferred.)
 __device__ __forceinline__ int visit_node2(const float4* __restrict__ node2, const float4* __restrict__ tris, int node,
                                            float3 o, float3 d, float3 idir, int src, float tmin, ClosestHit& h,
                                            int* stack, int& sp, bool& overflow, uint32_t& ntest) {
@@ -308,13 +262,6 @@ __device__ __forceinline__ int visit_node4_deferred(const float4* __restrict__ n
   return ra;
 }
 
-template <int kWidth>
-__device__ __forceinline__ int visit_node(const float4* __restrict__ nodes, const float4* __restrict__ tris, int node,
-                                          float3 o, float3 d, float3 idir, int src, float tmin, ClosestHit& h,
-                                          int* stack, int& sp, bool& overflow, uint32_t& ntest) {
-  if (kWidth == 4) return visit_node4(nodes, tris, node, o, d, idir, src, tmin, h, stack, sp, overflow, ntest);
-  return visit_node2(nodes, tris, node, o, d, idir, src, tmin, h, stack, sp, overflow, ntest);
-}
 
 // A tree traversal visits every node at most once, so more than max_iter
 // = 2 n_int + 8 visits means a corrupt hierarchy: give up and flag it.
@@ -339,11 +286,11 @@ __device__ __forceinline__ ClosestHit closest_hit(const float4* __restrict__ nod
 
 // Persistent traversal of level k with dynamic refill.  Every lane carries
 // its own ray; a warp runs up to `steps` node visits per round, then, when
-// at least `refill` lanes have finished, pulls that many new segments from
-// the level's cursor with one atomic and hands them to the idle lanes.  A
-// warp therefore no longer waits for the slowest ray of a fixed batch of 32
-// (the divergence that left most lanes idle), and stops when the level is
-// exhausted and its last ray is done.
+// at least `refill` lanes have finished, hands them new segments from a
+// batch of kTraceClaim it claimed from the level's cursor with one atomic.
+// Within a round, leaves hit by a visit are queued per lane and intersected
+// for the whole warp every kLeafEvery visits.  A warp stops when the level
+// is exhausted and its last ray is done.
 // kBatch = false: one scene, whose entry E0 arrives as a kernel parameter
 // (uniform constant-bank reads); true: each ray looks its scene up.
 constexpr int kTraceClaim = 64;  // segments a warp claims from the level cursor at once
