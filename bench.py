@@ -539,13 +539,15 @@ def run_ours(args):
     loss = torch.empty(1, device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
 
-    def step(fwd_only=False):
+    def step(fwd_only=False, target_ready=None):
         dt.vertex_normals(V, F, out=N)
         bvh.refit(V, F)
         out, tp = dt.render(V, F, bvh, N, ior, sigma, env, cams, res, res, params, ws=ws, out=img, check=False)
         if fwd_only:
             return None
         tp.stats = stats
+        if target_ready is not None:  # the target arrives on another stream
+            stream.wait_event(target_ready)
         dt.l2_loss_grad(out, target, grad=grad, loss=loss)
         return dt.render_backward(tp, grad, bws=bws)
 
@@ -651,12 +653,21 @@ def run_ours(args):
         h2d = hV.numel() * 4 + 4 + 12 + htarget.numel() * 4
         d2h = outV.numel() * 4 + 5 * 4
 
+        copy_stream = torch.cuda.Stream(device=dev)
+
         def e2e_step():
+            # the inputs the forward needs first on the compute stream; the
+            # target images (the bulk of the bytes) on a copy stream, overlapped
+            # with the forward and waited for before the loss
             V.copy_(hV, non_blocking=True)
             ior.copy_(hior, non_blocking=True)
             sigma.copy_(hsig, non_blocking=True)
-            target.copy_(htarget, non_blocking=True)
-            dV, dior, dsig = step()
+            copy_stream.wait_stream(stream)
+            with torch.cuda.stream(copy_stream):
+                target.copy_(htarget, non_blocking=True)
+                ready = torch.cuda.Event()
+                ready.record(copy_stream)
+            dV, dior, dsig = step(target_ready=ready)
             outV.copy_(dV, non_blocking=True)
             outs[0:1].copy_(dior, non_blocking=True)
             outs[1:4].copy_(dsig, non_blocking=True)
