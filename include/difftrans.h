@@ -333,10 +333,16 @@ dt_status dt_l2_loss_grad(const float* d_img, const float* d_target, int64_t n, 
  * area heuristic (32 centroid bins per axis, 16 for ranges of at most 128
  * triangles; fewer node visits per ray, slower to build); dt_refit_bvh
  * keeps whichever topology was built.
- * Defaults {64, 8, 5, 4, 2, 1}; results do not depend on them (the same
+ * trace_order 1 traces every level after the camera rays in the order of
+ * a per-segment key (direction octant, then the Morton code of the origin
+ * in the scene's bounding box; the scene index first in a batch), sorted on
+ * the device in the level's own not-yet-written hit, child and flag words:
+ * a warp's rays then take similar paths through the BVH.  0 traces the
+ * segments in arena order.
+ * Defaults {64, 8, 5, 4, 2, 1, 0}; results do not depend on them (the same
  * closest hit is found).  dt_set_tuning rejects values outside steps
  * 1..256, refill 1..32, trace 1..8, shade 1..16, width 2 or 4, builder 0
- * or 1.
+ * or 1, order 0 or 1.
  * ------------------------------------------------------------------------ */
 typedef struct dt_tuning {
   int32_t trace_steps;
@@ -345,6 +351,7 @@ typedef struct dt_tuning {
   int32_t shade_blocks_per_sm;
   int32_t bvh_width;
   int32_t bvh_builder;
+  int32_t trace_order;
 } dt_tuning;
 dt_status dt_get_tuning(dt_tuning* out);
 dt_status dt_set_tuning(const dt_tuning* in);

@@ -217,6 +217,11 @@ struct TableView {
 constexpr size_t kTableBytes =
     ((sizeof(TableHeader) + 255) / 256) * 256 + ((kMaxBatch * sizeof(SceneEntry) + 255) / 256) * 256;
 
+// Traversal-order sort of a level (dt_order.cu): at most kOrderMaxBlocks
+// CTAs, whose per-digit counts and the 256 digit totals take a fixed region.
+constexpr int kOrderMaxBlocks = 1024;
+constexpr size_t kOrderBytes = ((((size_t)256 * kOrderMaxBlocks + 256) * sizeof(uint32_t) + 255) / 256) * 256;
+
 // index i with starts[i] <= x < starts[i+1] (n >= 1)
 __device__ __forceinline__ int find_scene(const uint32_t* starts, int n, uint32_t x) {
   int lo = 0, hi = n - 1;
@@ -239,6 +244,7 @@ struct WsView {
   uint32_t* sflag;
   unsigned long long cap;
   uint32_t ring;  // 0: hit[a] for arena index a; else hit[(k & 1) ring + i] for position i in level k
+  uint32_t* order_hist;  // traversal-order sort: [256 digits][grid] block counts, then 256 digit totals
 };
 
 // Where the hit record of position i of level k (arena index a) lives.
@@ -246,14 +252,51 @@ __device__ __forceinline__ size_t hit_slot(const WsView& W, int k, uint32_t a, u
   return W.ring ? (size_t)(k & 1) * W.ring + i : (size_t)a;
 }
 
+// The hit records of level k (arena start `start`) seen as four arrays of
+// 32-bit words.  Until level k is traced they hold its traversal-order keys
+// (written with each segment by the shading pass of level k-1) and the
+// temporaries of the order sort.
+__device__ __forceinline__ uint32_t* level_words(const WsView& W, int k, uint32_t start) {
+  return reinterpret_cast<uint32_t*>(W.hit + (W.ring ? (size_t)(k & 1) * W.ring : (size_t)start));
+}
+
+// Traversal-order key of a ray: the direction octant in bits 21-23 above the
+// 21-bit Morton code of its origin on a 128^3 grid over the scene's bounding
+// box (lo, and 128 / extent per axis).  Rays that share the octant and leave
+// nearby points take similar paths through the BVH.
+__device__ __forceinline__ uint32_t spread7(uint32_t v) {
+  v = (v | (v << 8)) & 0x0000F00Fu;
+  v = (v | (v << 4)) & 0x000C30C3u;
+  v = (v | (v << 2)) & 0x00249249u;
+  return v;
+}
+__device__ __forceinline__ uint32_t cell7(float x, float lo, float scale) {
+  return (uint32_t)fminf(fmaxf((x - lo) * scale, 0.0f), 127.0f);
+}
+__device__ __forceinline__ uint32_t ray_order_key(float3 o, float3 d, float3 lo, float3 scale) {
+  const uint32_t oct = ((d.x < 0.0f) ? 4u : 0u) | ((d.y < 0.0f) ? 2u : 0u) | ((d.z < 0.0f) ? 1u : 0u);
+  return (oct << 21) | (spread7(cell7(o.x, lo.x, scale.x)) << 2) | (spread7(cell7(o.y, lo.y, scale.y)) << 1) |
+         spread7(cell7(o.z, lo.z, scale.z));
+}
+// Bounding box of a scene from its binary BVH root (node 0): lo and the
+// 128-cells-per-axis scale of ray_order_key.
+__device__ __forceinline__ void scene_order_box(const float4* __restrict__ node2, float3& lo, float3& scale) {
+  const float4 a = __ldg(node2), b = __ldg(node2 + 1), c = __ldg(node2 + 2);
+  lo = mk(fminf(a.x, b.x), fminf(a.z, b.z), fminf(c.x, c.z));
+  const float3 hi = mk(fmaxf(a.y, b.y), fmaxf(a.w, b.w), fmaxf(c.y, c.w));
+  scale = mk(128.0f / fmaxf(hi.x - lo.x, 1e-30f), 128.0f / fmaxf(hi.y - lo.y, 1e-30f),
+             128.0f / fmaxf(hi.z - lo.z, 1e-30f));
+}
+
 // Arena layout; the hit records come last, so every other offset depends on
 // the segment capacity only.  ring = 0: one hit per segment; else a ring of
 // two levels of `ring` hits.
 struct WsLayout {
-  size_t off_table, off_o, off_d, off_w, off_child, off_flag, off_hit, total;
+  size_t off_table, off_order, off_o, off_d, off_w, off_child, off_flag, off_hit, total;
   __host__ __device__ explicit WsLayout(unsigned long long cap, unsigned long long ring = 0) {
     off_table = 1024;
-    off_o = off_table + kTableBytes;
+    off_order = off_table + kTableBytes;
+    off_o = off_order + kOrderBytes;
     off_d = align_up(off_o + cap * sizeof(float4), 256);
     off_w = align_up(off_d + cap * sizeof(float4), 256);
     off_child = align_up(off_w + cap * sizeof(float4), 256);
@@ -271,7 +314,7 @@ __host__ __device__ inline WsView ws_view(const void* base, unsigned long long c
   SceneEntry* ent = (SceneEntry*)(b + L.off_table + ((sizeof(TableHeader) + 255) / 256) * 256);
   return WsView{(WsHeader*)b, th, ent, (float4*)(b + L.off_o), (float4*)(b + L.off_d), (float4*)(b + L.off_w),
                 (float4*)(b + L.off_hit), (int32_t*)(b + L.off_child), (uint32_t*)(b + L.off_flag), cap,
-                (uint32_t)ring};
+                (uint32_t)ring, (uint32_t*)(b + L.off_order)};
 }
 
 // Segments of level k that fit in the arena (and in the hit ring, if any).

@@ -290,7 +290,9 @@ __device__ __forceinline__ ClosestHit closest_hit(const float4* __restrict__ nod
 // batch of kTraceClaim it claimed from the level's cursor with one atomic.
 // Within a round, leaves hit by a visit are queued per lane and intersected
 // for the whole warp every kLeafEvery visits.  A warp stops when the level
-// is exhausted and its last ray is done.
+// is exhausted and its last ray is done.  sorted != 0: position i of the
+// level is the segment the order sort put there (its flag word holds it
+// until the shading pass rewrites it).
 // kBatch = false: one scene, whose entry E0 arrives as a kernel parameter
 // (uniform constant-bank reads); true: each ray looks its scene up.
 constexpr int kTraceClaim = 64;  // segments a warp claims from the level cursor at once
@@ -298,12 +300,14 @@ constexpr int kLeafEvery = 4;    // node visits between the warp's batched trian
 
 template <int kMinBlocks, int kWidth, bool kBatch>
 __global__ void __launch_bounds__(256, kMinBlocks) k_trace(WsView W, int k, int steps, int refill,
-                                                           const SceneEntry E0) {
+                                                           const SceneEntry E0, int sorted) {
   WsHeader* H = W.hdr;
   uint32_t* cursor = &H->fetch[k];
   const int n_scenes = kBatch ? W.th->n : 1;
   const uint32_t n = level_size(H, k);
   const uint32_t start = H->level_start[k];
+  // the level's traversal order (dt_order.cu), or its arena order
+  const uint32_t* order = sorted ? W.sflag + start : nullptr;
   const uint32_t lane = threadIdx.x & 31;
   const unsigned lanes_below = (1u << lane) - 1u;
   uint32_t nvis = 0, ntest = 0;
@@ -346,9 +350,11 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_trace(WsView W, int k, int 
       if (qe > n) qe = n;
       if (qb > qe) qb = qe;
       if (cursor_done && qb >= qe) exhausted = true;
-      if (!active) {
-        if (i < n) {
-          a = start + i;
+      if (!active && i < n) {
+        const uint32_t pos = order ? __ldg(order + i) : i;
+        if (pos >= n) overflow = true;  // not a permutation of the level: reported, not traced
+        else {
+          a = start + pos;
           const float4 ro = W.ray_o[a], rd = W.ray_d[a], rw = W.ray_w[a];
           if (kBatch) {
             const SceneEntry& E = W.ent[find_scene(W.th->starts, n_scenes, __float_as_uint(ro.w))];
@@ -456,8 +462,12 @@ __global__ void k_closest_hit_rays(const float4* __restrict__ nodes, const float
 constexpr int kShadeThreads = 256;
 constexpr int kShadeMinBlocks = 4;  // CTAs per SM the register budget is sized for
 
+// keys != 0: each child also gets its traversal-order key (ray_order_key,
+// with the scene index in bits 24-31 in a batch) in the level-(k+1) words
+// that the order sort reads.
 template <bool kBatch>
-__global__ void __launch_bounds__(kShadeThreads, kShadeMinBlocks) k_shade(WsView W, int k, const SceneEntry E0) {
+__global__ void __launch_bounds__(kShadeThreads, kShadeMinBlocks) k_shade(WsView W, int k, const SceneEntry E0,
+                                                                         int keys) {
   WsHeader* H = W.hdr;
   const int n_scenes = kBatch ? W.th->n : 1;
   const uint32_t n = level_size(H, k);
@@ -470,6 +480,11 @@ __global__ void __launch_bounds__(kShadeThreads, kShadeMinBlocks) k_shade(WsView
   __shared__ uint32_t s_wr[kShadeThreads / 32], s_wt[kShadeThreads / 32];
   __shared__ uint32_t s_base, s_nr;
   const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t* next_keys = keys ? level_words(W, k + 1, next_start) : nullptr;
+  // positions of level k+1 that can hold a key (its ring half, or the arena)
+  const unsigned long long key_room = W.ring ? (unsigned long long)W.ring : H->capacity - next_start;
+  float3 box_lo = mk(0.f, 0.f, 0.f), box_scale = box_lo;
+  if (!kBatch && keys) scene_order_box(E0.node2, box_lo, box_scale);
   uint32_t c_hit = 0, c_miss = 0, c_disc = 0, c_back = 0, c_tir = 0;
   bool overflow = false;
   // CTA-wide tiles, so that the children of a tile are appended with one
@@ -478,12 +493,13 @@ __global__ void __launch_bounds__(kShadeThreads, kShadeMinBlocks) k_shade(WsView
     const uint32_t i = tile + threadIdx.x;
     const uint32_t a = start + i;
     int nchild = 0;
-    uint32_t fl = 0;
+    uint32_t fl = 0, key_hi = 0;
     float4 co = make_float4(0.f, 0.f, 0.f, 0.f), cdr = co, cwr = co, cdt = co, cwt = co;
     if (i < n) {
       const float4 ro = W.ray_o[a], rd = W.ray_d[a], rw = W.ray_w[a], hh = W.hit[hit_slot(W, k, a, i)];
       const uint32_t sample = __float_as_uint(ro.w);
-      const SceneEntry& E = kBatch ? W.ent[find_scene(W.th->starts, n_scenes, sample)] : E0;
+      const int scene = kBatch ? find_scene(W.th->starts, n_scenes, sample) : 0;
+      const SceneEntry& E = kBatch ? W.ent[scene] : E0;
       const int tri = __float_as_int(hh.w);
       const float3 d = xyz(rd);
       if (tri < 0) {  // step 3: no intersection -> environment
@@ -524,6 +540,10 @@ __global__ void __launch_bounds__(kShadeThreads, kShadeMinBlocks) k_shade(WsView
             cdr = make_float4(h.wr.x, h.wr.y, h.wr.z, __uint_as_float(2u * node));
             cwr = make_float4(Wt.x * h.R, Wt.y * h.R, Wt.z * h.R, __int_as_float(tri));
             nchild = 1;
+            if (kBatch && keys) {
+              scene_order_box(E.node2, box_lo, box_scale);
+              key_hi = (uint32_t)scene << 24;
+            }
             if (!h.tir) {
               cdt = make_float4(h.wt.x, h.wt.y, h.wt.z, __uint_as_float(2u * node + 1u));
               cwt = make_float4(Wt.x * h.T, Wt.y * h.T, Wt.z * h.T, __int_as_float(tri));
@@ -570,6 +590,8 @@ __global__ void __launch_bounds__(kShadeThreads, kShadeMinBlocks) k_shade(WsView
         if (jr < H->capacity) {
           ch = (int32_t)jr;
           W.ray_o[jr] = co; W.ray_d[jr] = cdr; W.ray_w[jr] = cwr;
+          if (next_keys && jr - next_start < key_room)
+            next_keys[jr - next_start] = key_hi | ray_order_key(xyz(co), xyz(cdr), box_lo, box_scale);
         } else {
           overflow = true;
         }
@@ -579,6 +601,8 @@ __global__ void __launch_bounds__(kShadeThreads, kShadeMinBlocks) k_shade(WsView
           delta = (uint32_t)(jt - jr);
           if (jt < H->capacity) {
             W.ray_o[jt] = co; W.ray_d[jt] = cdt; W.ray_w[jt] = cwt;
+            if (next_keys && jt - next_start < key_room)
+              next_keys[jt - next_start] = key_hi | ray_order_key(xyz(co), xyz(cdt), box_lo, box_scale);
           } else {
             overflow = true;
           }
@@ -622,6 +646,8 @@ __global__ void k_dump(WsView W, int32_t* __restrict__ si, float* __restrict__ s
 // ---------------------------------------------------------------------------
 // Launch and scheduling knobs (dt_set_tuning; defined with the C ABI).
 extern dt_tuning g_tuning;
+// Sorts level k into its traversal order (dt_order.cu).
+void launch_order(const WsView& W, int k, int npass, cudaStream_t s);
 static int shade_blocks() { return g_tuning.shade_blocks_per_sm * num_sms(); }
 static int n_int_of(int32_t nf) { return nf > 1 ? nf - 1 : 1; }
 
@@ -684,21 +710,27 @@ void launch_forward_table(const TableHeader& th, const SceneEntry* entries, void
   const bool batch = n > 1;
   const SceneEntry& E0 = entries[0];
   const int bps = g_tuning.trace_blocks_per_sm, st = g_tuning.trace_steps, rf = g_tuning.trace_refill;
+  // levels after the camera rays are traced in the order of their keys
+  // (dt_order.cu); the camera rays keep pixel order, which is coherent
+  const bool order = g_tuning.trace_order != 0;
   for (int k = 0; k <= th.max_depth; ++k) {
+    const int sorted = order && k > 0;
+    if (sorted) launch_order(W, k, batch ? 4 : 3, s);
     {
       ProfScope ps("k_trace", s);
       if (g_tuning.bvh_width == 4) {
-        if (batch) launch_trace_w<4, true>(bps, s, W, k, st, rf, E0);
-        else launch_trace_w<4, false>(bps, s, W, k, st, rf, E0);
+        if (batch) launch_trace_w<4, true>(bps, s, W, k, st, rf, E0, sorted);
+        else launch_trace_w<4, false>(bps, s, W, k, st, rf, E0, sorted);
       } else {
-        if (batch) launch_trace_w<2, true>(bps, s, W, k, st, rf, E0);
-        else launch_trace_w<2, false>(bps, s, W, k, st, rf, E0);
+        if (batch) launch_trace_w<2, true>(bps, s, W, k, st, rf, E0, sorted);
+        else launch_trace_w<2, false>(bps, s, W, k, st, rf, E0, sorted);
       }
     }
     {
       ProfScope ps("k_shade", s);
-      if (batch) k_shade<true><<<shade_blocks(), kShadeThreads, 0, s>>>(W, k, E0);
-      else k_shade<false><<<shade_blocks(), kShadeThreads, 0, s>>>(W, k, E0);
+      const int keys = order && k < th.max_depth;
+      if (batch) k_shade<true><<<shade_blocks(), kShadeThreads, 0, s>>>(W, k, E0, keys);
+      else k_shade<false><<<shade_blocks(), kShadeThreads, 0, s>>>(W, k, E0, keys);
     }
   }
 }

@@ -73,6 +73,23 @@ def test_host_side_argument_checks_fire_before_any_launch(lib):
     assert b"NULL" in L.dt_last_error()
 
 
+def test_tuning_round_trips_and_is_validated(lib):
+    """dt_get_tuning / dt_set_tuning are host-only; a rejected set changes
+    nothing."""
+    import paper_2603_00413_gb300 as dt
+    old = dt.get_tuning()
+    assert old["trace_order"] in (0, 1) and old["bvh_width"] in (2, 4)
+    try:
+        dt.set_tuning(trace_order=0)
+        assert dt.get_tuning()["trace_order"] == 0
+        for bad in (dict(trace_order=2), dict(bvh_width=3), dict(trace_steps=0), dict(bvh_builder=-1)):
+            with pytest.raises(dt.DiffTransError):
+                dt.set_tuning(**bad)
+        assert dt.get_tuning() == dict(old, trace_order=0)
+    finally:
+        dt.set_tuning(**old)
+
+
 def test_struct_layouts_match_header():
     import paper_2603_00413_gb300 as dt
     probe = r"""
