@@ -333,16 +333,19 @@ dt_status dt_l2_loss_grad(const float* d_img, const float* d_target, int64_t n, 
  * area heuristic (32 centroid bins per axis, 16 for ranges of at most 128
  * triangles; fewer node visits per ray, slower to build); dt_refit_bvh
  * keeps whichever topology was built.
- * trace_order 1 traces every level after the camera rays in the order of
- * a per-segment key (direction octant, then the Morton code of the origin
- * in the scene's bounding box; the scene index first in a batch), sorted on
- * the device in the level's own not-yet-written hit, child and flag words:
- * a warp's rays then take similar paths through the BVH.  0 traces the
- * segments in arena order.
- * Defaults {64, 8, 5, 4, 2, 1, 0}; results do not depend on them (the same
+ * trace_order b (12..22) traces every level after the camera rays bucket
+ * by bucket: the bucket is the top b bits of a 24-bit key (direction octant,
+ * then the Morton code of the ray origin on a 128^3 grid over the scene's
+ * bounding box; in a batch the scene index and the top b-8 bits), counted
+ * while the level's segments are shaded into existence and turned into an
+ * order by one scan (a counting sort in the level's own not-yet-written
+ * hit and flag words), so that a warp's rays take similar paths through the
+ * BVH.  0 traces the segments in the order they were appended.  Camera
+ * rays are laid out in 8x4 pixel blocks.
+ * Defaults {64, 8, 5, 4, 2, 1, 20}; results do not depend on them (the same
  * closest hit is found).  dt_set_tuning rejects values outside steps
  * 1..256, refill 1..32, trace 1..8, shade 1..16, width 2 or 4, builder 0
- * or 1, order 0 or 1.
+ * or 1, order 0 or 12..22.
  * ------------------------------------------------------------------------ */
 typedef struct dt_tuning {
   int32_t trace_steps;

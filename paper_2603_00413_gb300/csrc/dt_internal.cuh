@@ -217,10 +217,12 @@ struct TableView {
 constexpr size_t kTableBytes =
     ((sizeof(TableHeader) + 255) / 256) * 256 + ((kMaxBatch * sizeof(SceneEntry) + 255) / 256) * 256;
 
-// Traversal-order sort of a level (dt_order.cu): at most kOrderMaxBlocks
-// CTAs, whose per-digit counts and the 256 digit totals take a fixed region.
-constexpr int kOrderMaxBlocks = 1024;
-constexpr size_t kOrderBytes = ((((size_t)256 * kOrderMaxBlocks + 256) * sizeof(uint32_t) + 255) / 256) * 256;
+// Traversal order of a level (dt_order.cu): a counting sort over at most
+// 2^kOrderBits buckets, whose counters (and at most 1024 span totals of
+// their scan) take a fixed region of the workspace.
+constexpr int kOrderBits = 22;
+constexpr uint32_t kOrderCounters = 1u << kOrderBits;
+constexpr size_t kOrderBytes = (((size_t)kOrderCounters + 1024) * sizeof(uint32_t) + 255) / 256 * 256;
 
 // index i with starts[i] <= x < starts[i+1] (n >= 1)
 __device__ __forceinline__ int find_scene(const uint32_t* starts, int n, uint32_t x) {
@@ -244,7 +246,7 @@ struct WsView {
   uint32_t* sflag;
   unsigned long long cap;
   uint32_t ring;  // 0: hit[a] for arena index a; else hit[(k & 1) ring + i] for position i in level k
-  uint32_t* order_hist;  // traversal-order sort: [256 digits][grid] block counts, then 256 digit totals
+  uint32_t* order_count;  // traversal order: kOrderCounters bucket counters, then the scan's span totals
 };
 
 // Where the hit record of position i of level k (arena index a) lives.
@@ -252,12 +254,12 @@ __device__ __forceinline__ size_t hit_slot(const WsView& W, int k, uint32_t a, u
   return W.ring ? (size_t)(k & 1) * W.ring + i : (size_t)a;
 }
 
-// The hit records of level k (arena start `start`) seen as four arrays of
-// 32-bit words.  Until level k is traced they hold its traversal-order keys
-// (written with each segment by the shading pass of level k-1) and the
-// temporaries of the order sort.
-__device__ __forceinline__ uint32_t* level_words(const WsView& W, int k, uint32_t start) {
-  return reinterpret_cast<uint32_t*>(W.hit + (W.ring ? (size_t)(k & 1) * W.ring : (size_t)start));
+// The hit records of level k (arena start `start`).  Until level k is
+// traced they hold, per position, the segment's traversal-order bucket and
+// its rank in the bucket (written with each segment by the shading pass of
+// level k-1).
+__device__ __forceinline__ uint2* level_buckets(const WsView& W, int k, uint32_t start) {
+  return reinterpret_cast<uint2*>(W.hit + (W.ring ? (size_t)(k & 1) * W.ring : (size_t)start));
 }
 
 // Traversal-order key of a ray: the direction octant in bits 21-23 above the
@@ -278,6 +280,17 @@ __device__ __forceinline__ uint32_t ray_order_key(float3 o, float3 d, float3 lo,
   return (oct << 21) | (spread7(cell7(o.x, lo.x, scale.x)) << 2) | (spread7(cell7(o.y, lo.y, scale.y)) << 1) |
          spread7(cell7(o.z, lo.z, scale.z));
 }
+// Bucket of a key with `bits` bits (12..kOrderBits): its top bits, below the
+// scene index (8 bits) in a batch.
+__device__ __forceinline__ uint32_t order_bucket(uint32_t key24, int bits, bool batch, uint32_t scene) {
+  return batch ? (scene << (bits - 8)) | (key24 >> (32 - bits)) : key24 >> (24 - bits);
+}
+// Counts a child in its bucket and stores (bucket, rank in the bucket: the
+// count before it) at its position p of the next level; b == ~0u: no child.
+__device__ __forceinline__ void order_count_child(uint32_t* count, uint2* kr, uint32_t b, uint32_t p) {
+  if (b != ~0u) kr[p] = make_uint2(b, atomicAdd(count + b, 1u));
+}
+
 // Bounding box of a scene from its binary BVH root (node 0): lo and the
 // 128-cells-per-axis scale of ray_order_key.
 __device__ __forceinline__ void scene_order_box(const float4* __restrict__ node2, float3& lo, float3& scale) {

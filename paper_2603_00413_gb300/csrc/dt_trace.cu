@@ -72,8 +72,22 @@ __global__ void k_zero_images(const SceneEntry* __restrict__ ent) {
     E.out[i] = 0.0f;
 }
 
+// Pixel of position q of a view's pixels in traversal order: bands of four
+// rows (the last one shorter when H is not a multiple of four), each taken
+// column by column, so that 32 consecutive positions of a full band cover
+// an 8x4 pixel block; a bijection of [0, W H).
+__device__ __forceinline__ uint32_t tiled_pixel(uint32_t q, uint32_t w, uint32_t h) {
+  const uint32_t band = q / (4u * w);
+  const uint32_t hb = min(4u, h - 4u * band);
+  const uint32_t r = q - band * 4u * w;
+  return (4u * band + r % hb) * w + r / hb;
+}
+
 // Camera rays of every scene into level 0 (blockIdx.y = scene).  Sample
-// index g = sample_start + (view * H * W + py * W + px) * spp + s.
+// index g = sample_start + (view * H * W + py * W + px) * spp + s; the
+// samples of a view are laid out in the arena in tiled_pixel order (the
+// samples of a pixel together), so that a warp's camera rays are an 8x4
+// block of pixels rather than a row of 32.
 __global__ void k_camera(WsView W, unsigned long long capacity) {
   const SceneEntry& E = W.ent[blockIdx.y];
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
@@ -87,15 +101,17 @@ __global__ void k_camera(WsView W, unsigned long long capacity) {
   for (uint32_t l = blockIdx.x * blockDim.x + threadIdx.x; l < n0; l += gridDim.x * blockDim.x) {
     const uint32_t s = l % (uint32_t)E.spp;
     const uint32_t gp = l / (uint32_t)E.spp;
-    const uint32_t view = gp / npix, p = gp % npix;
+    const uint32_t view = gp / npix;
+    const uint32_t p = tiled_pixel(gp % npix, (uint32_t)E.width, (uint32_t)E.height);
     float jx = 0.5f, jy = 0.5f;
     if (E.jitter) jitter_offset(E.seed, view, p, s, jx, jy);
     float3 o, d;
     camera_ray(E.cams + 10 * view, E.width, E.height, (float)(p % E.width) + jx, (float)(p / E.width) + jy, o, d);
-    const uint32_t g = E.sample_start + l;
-    W.ray_o[g] = make_float4(o.x, o.y, o.z, __uint_as_float(g));
-    W.ray_d[g] = make_float4(d.x, d.y, d.z, __uint_as_float(1u));
-    W.ray_w[g] = make_float4(1.f, 1.f, 1.f, __int_as_float(-1));
+    const uint32_t g = E.sample_start + (view * npix + p) * (uint32_t)E.spp + s;
+    const uint32_t a = E.sample_start + l;
+    W.ray_o[a] = make_float4(o.x, o.y, o.z, __uint_as_float(g));
+    W.ray_d[a] = make_float4(d.x, d.y, d.z, __uint_as_float(1u));
+    W.ray_w[a] = make_float4(1.f, 1.f, 1.f, __int_as_float(-1));
   }
 }
 
@@ -291,8 +307,8 @@ __device__ __forceinline__ ClosestHit closest_hit(const float4* __restrict__ nod
 // Within a round, leaves hit by a visit are queued per lane and intersected
 // for the whole warp every kLeafEvery visits.  A warp stops when the level
 // is exhausted and its last ray is done.  sorted != 0: position i of the
-// level is the segment the order sort put there (its flag word holds it
-// until the shading pass rewrites it).
+// level is the segment the traversal order put there (its flag word holds
+// it until the shading pass rewrites it).
 // kBatch = false: one scene, whose entry E0 arrives as a kernel parameter
 // (uniform constant-bank reads); true: each ray looks its scene up.
 constexpr int kTraceClaim = 64;  // segments a warp claims from the level cursor at once
@@ -462,12 +478,12 @@ __global__ void k_closest_hit_rays(const float4* __restrict__ nodes, const float
 constexpr int kShadeThreads = 256;
 constexpr int kShadeMinBlocks = 4;  // CTAs per SM the register budget is sized for
 
-// keys != 0: each child also gets its traversal-order key (ray_order_key,
-// with the scene index in bits 24-31 in a batch) in the level-(k+1) words
-// that the order sort reads.
+// order_bits != 0: each child is also counted in its traversal-order
+// bucket (order_bucket of ray_order_key with that many bits; dt_order.cu)
+// and its bucket and rank are stored with the next level.
 template <bool kBatch>
 __global__ void __launch_bounds__(kShadeThreads, kShadeMinBlocks) k_shade(WsView W, int k, const SceneEntry E0,
-                                                                         int keys) {
+                                                                         int order_bits) {
   WsHeader* H = W.hdr;
   const int n_scenes = kBatch ? W.th->n : 1;
   const uint32_t n = level_size(H, k);
@@ -480,11 +496,11 @@ __global__ void __launch_bounds__(kShadeThreads, kShadeMinBlocks) k_shade(WsView
   __shared__ uint32_t s_wr[kShadeThreads / 32], s_wt[kShadeThreads / 32];
   __shared__ uint32_t s_base, s_nr;
   const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  uint32_t* next_keys = keys ? level_words(W, k + 1, next_start) : nullptr;
-  // positions of level k+1 that can hold a key (its ring half, or the arena)
+  uint2* next_kr = order_bits ? level_buckets(W, k + 1, next_start) : nullptr;
+  // positions of level k+1 that can hold a bucket (its ring half, or the arena)
   const unsigned long long key_room = W.ring ? (unsigned long long)W.ring : H->capacity - next_start;
   float3 box_lo = mk(0.f, 0.f, 0.f), box_scale = box_lo;
-  if (!kBatch && keys) scene_order_box(E0.node2, box_lo, box_scale);
+  if (!kBatch && order_bits) scene_order_box(E0.node2, box_lo, box_scale);
   uint32_t c_hit = 0, c_miss = 0, c_disc = 0, c_back = 0, c_tir = 0;
   bool overflow = false;
   // CTA-wide tiles, so that the children of a tile are appended with one
@@ -493,7 +509,8 @@ __global__ void __launch_bounds__(kShadeThreads, kShadeMinBlocks) k_shade(WsView
     const uint32_t i = tile + threadIdx.x;
     const uint32_t a = start + i;
     int nchild = 0;
-    uint32_t fl = 0, key_hi = 0;
+    uint32_t fl = 0, scene_id = 0;
+    uint32_t b_r = ~0u, p_r = 0, b_t = ~0u, p_t = 0;  // order buckets and next-level positions of the children
     float4 co = make_float4(0.f, 0.f, 0.f, 0.f), cdr = co, cwr = co, cdt = co, cwt = co;
     if (i < n) {
       const float4 ro = W.ray_o[a], rd = W.ray_d[a], rw = W.ray_w[a], hh = W.hit[hit_slot(W, k, a, i)];
@@ -540,9 +557,9 @@ __global__ void __launch_bounds__(kShadeThreads, kShadeMinBlocks) k_shade(WsView
             cdr = make_float4(h.wr.x, h.wr.y, h.wr.z, __uint_as_float(2u * node));
             cwr = make_float4(Wt.x * h.R, Wt.y * h.R, Wt.z * h.R, __int_as_float(tri));
             nchild = 1;
-            if (kBatch && keys) {
+            if (kBatch && order_bits) {
               scene_order_box(E.node2, box_lo, box_scale);
-              key_hi = (uint32_t)scene << 24;
+              scene_id = (uint32_t)scene;
             }
             if (!h.tir) {
               cdt = make_float4(h.wt.x, h.wt.y, h.wt.z, __uint_as_float(2u * node + 1u));
@@ -590,8 +607,10 @@ __global__ void __launch_bounds__(kShadeThreads, kShadeMinBlocks) k_shade(WsView
         if (jr < H->capacity) {
           ch = (int32_t)jr;
           W.ray_o[jr] = co; W.ray_d[jr] = cdr; W.ray_w[jr] = cwr;
-          if (next_keys && jr - next_start < key_room)
-            next_keys[jr - next_start] = key_hi | ray_order_key(xyz(co), xyz(cdr), box_lo, box_scale);
+          if (next_kr && jr - next_start < key_room) {
+            p_r = (uint32_t)(jr - next_start);
+            b_r = order_bucket(ray_order_key(xyz(co), xyz(cdr), box_lo, box_scale), order_bits, kBatch, scene_id);
+          }
         } else {
           overflow = true;
         }
@@ -601,8 +620,10 @@ __global__ void __launch_bounds__(kShadeThreads, kShadeMinBlocks) k_shade(WsView
           delta = (uint32_t)(jt - jr);
           if (jt < H->capacity) {
             W.ray_o[jt] = co; W.ray_d[jt] = cdt; W.ray_w[jt] = cwt;
-            if (next_keys && jt - next_start < key_room)
-              next_keys[jt - next_start] = key_hi | ray_order_key(xyz(co), xyz(cdt), box_lo, box_scale);
+            if (next_kr && jt - next_start < key_room) {
+              p_t = (uint32_t)(jt - next_start);
+              b_t = order_bucket(ray_order_key(xyz(co), xyz(cdt), box_lo, box_scale), order_bits, kBatch, scene_id);
+            }
           } else {
             overflow = true;
           }
@@ -610,6 +631,10 @@ __global__ void __launch_bounds__(kShadeThreads, kShadeMinBlocks) k_shade(WsView
       }
       W.child[a] = ch;
       W.sflag[a] = fl | (delta << kRefractShift);
+    }
+    if (next_kr) {
+      order_count_child(W.order_count, next_kr, b_r, p_r);
+      order_count_child(W.order_count, next_kr, b_t, p_t);
     }
   }
   warp_add_u64(&H->counters[CNT_HITS], c_hit);
@@ -646,8 +671,10 @@ __global__ void k_dump(WsView W, int32_t* __restrict__ si, float* __restrict__ s
 // ---------------------------------------------------------------------------
 // Launch and scheduling knobs (dt_set_tuning; defined with the C ABI).
 extern dt_tuning g_tuning;
-// Sorts level k into its traversal order (dt_order.cu).
-void launch_order(const WsView& W, int k, int npass, cudaStream_t s);
+// Traversal order of level k from the buckets counted while it was shaded
+// into existence, and the clearing of the bucket counters (dt_order.cu).
+void launch_order(const WsView& W, int k, cudaStream_t s);
+void launch_order_clear(const WsView& W, cudaStream_t s);
 static int shade_blocks() { return g_tuning.shade_blocks_per_sm * num_sms(); }
 static int n_int_of(int32_t nf) { return nf > 1 ? nf - 1 : 1; }
 
@@ -710,12 +737,12 @@ void launch_forward_table(const TableHeader& th, const SceneEntry* entries, void
   const bool batch = n > 1;
   const SceneEntry& E0 = entries[0];
   const int bps = g_tuning.trace_blocks_per_sm, st = g_tuning.trace_steps, rf = g_tuning.trace_refill;
-  // levels after the camera rays are traced in the order of their keys
-  // (dt_order.cu); the camera rays keep pixel order, which is coherent
-  const bool order = g_tuning.trace_order != 0;
+  // levels after the camera rays are traced bucket by bucket (dt_order.cu);
+  // the camera rays keep pixel order, which is coherent
+  const int order_bits = g_tuning.trace_order;
   for (int k = 0; k <= th.max_depth; ++k) {
-    const int sorted = order && k > 0;
-    if (sorted) launch_order(W, k, batch ? 4 : 3, s);
+    const int sorted = order_bits && k > 0;
+    if (sorted) launch_order(W, k, s);
     {
       ProfScope ps("k_trace", s);
       if (g_tuning.bvh_width == 4) {
@@ -727,10 +754,11 @@ void launch_forward_table(const TableHeader& th, const SceneEntry* entries, void
       }
     }
     {
+      const int bits = k < th.max_depth ? order_bits : 0;
+      if (bits) launch_order_clear(W, s);
       ProfScope ps("k_shade", s);
-      const int keys = order && k < th.max_depth;
-      if (batch) k_shade<true><<<shade_blocks(), kShadeThreads, 0, s>>>(W, k, E0, keys);
-      else k_shade<false><<<shade_blocks(), kShadeThreads, 0, s>>>(W, k, E0, keys);
+      if (batch) k_shade<true><<<shade_blocks(), kShadeThreads, 0, s>>>(W, k, E0, bits);
+      else k_shade<false><<<shade_blocks(), kShadeThreads, 0, s>>>(W, k, E0, bits);
     }
   }
 }

@@ -78,11 +78,12 @@ def test_tuning_round_trips_and_is_validated(lib):
     nothing."""
     import paper_2603_00413_gb300 as dt
     old = dt.get_tuning()
-    assert old["trace_order"] in (0, 1) and old["bvh_width"] in (2, 4)
+    assert (old["trace_order"] == 0 or 12 <= old["trace_order"] <= 22) and old["bvh_width"] in (2, 4)
     try:
         dt.set_tuning(trace_order=0)
         assert dt.get_tuning()["trace_order"] == 0
-        for bad in (dict(trace_order=2), dict(bvh_width=3), dict(trace_steps=0), dict(bvh_builder=-1)):
+        for bad in (dict(trace_order=1), dict(trace_order=23), dict(bvh_width=3), dict(trace_steps=0),
+                    dict(bvh_builder=-1)):
             with pytest.raises(dt.DiffTransError):
                 dt.set_tuning(**bad)
         assert dt.get_tuning() == dict(old, trace_order=0)

@@ -1,11 +1,13 @@
-"""Traversal order (tuning trace_order): every level after the camera rays is
-traced in the order of a per-segment key (direction octant, then the Morton
-code of the origin; the scene index first in a batch), sorted on the device
-in the level's own not-yet-written hit, child and flag words.  The order
-changes nothing that is traced: the same segments, hits, flags and node
-visits as in arena order, and the same images and gradients, for one scene
-(three 8-bit passes), a batch (four, with the scene index), a checkpointed
-tape, and levels far smaller than the sort's grid."""
+"""Traversal order (tuning trace_order = b key bits): every level after the
+camera rays is traced bucket by bucket, the bucket being the top b bits of a
+per-segment key (direction octant, then the Morton code of the origin; the
+scene index first in a batch), counted while the level is shaded into
+existence and turned into an order by one scan in the level's own
+not-yet-written hit and flag words.  The order changes nothing that is
+traced: the same segments, hits, flags and node visits as in append order,
+and the same images and gradients, for one scene at several key widths, a
+batch (scene index in the bucket), a checkpointed tape, and levels of a few
+segments."""
 import numpy as np
 import pytest
 import torch
@@ -15,6 +17,7 @@ from paper_2603_00413_gb300 import scenes as S
 from tests.gpu_util import GpuScene, assert_radiance_parity
 
 pytestmark = pytest.mark.gpu
+ORDER = 20  # key bits of the traversal-order buckets (the default)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -64,10 +67,11 @@ def _sorted_dump(tape):
     return si[key], sf[key]
 
 
-def test_order_finds_the_same_hits():
+@pytest.mark.parametrize("bits", [12, ORDER, 22])
+def test_order_finds_the_same_hits(bits):
     gs = _genus2()
     img0, tape0, _, prof0 = _run(gs, 0)
-    img1, tape1, _, prof1 = _run(gs, 1)
+    img1, tape1, _, prof1 = _run(gs, bits)
     s0, s1 = tape0.stats, tape1.stats
     assert s0["status"] == s1["status"] == dt.DT_OK
     for key in ("segments", "level_count", "hits", "misses", "tir", "nodes_visited", "tris_tested"):
@@ -88,7 +92,7 @@ def test_order_gives_the_same_gradients():
     rng = np.random.default_rng(3)
     g = torch.from_numpy(rng.normal(size=(2, 40, 48, 3)).astype(np.float32)).cuda()
     _, _, (dV0, di0, ds0), _ = _run(gs, 0, g)
-    _, _, (dV1, di1, ds1), _ = _run(gs, 1, g)
+    _, _, (dV1, di1, ds1), _ = _run(gs, ORDER, g)
     a, b = dV0.cpu().numpy().astype(np.float64), dV1.cpu().numpy().astype(np.float64)
     assert np.linalg.norm(a - b) <= 1e-5 * np.linalg.norm(a)
     assert float(di1) == pytest.approx(float(di0), rel=1e-5, abs=1e-8)
@@ -100,7 +104,7 @@ def test_order_in_a_checkpointed_tape():
     rng = np.random.default_rng(4)
     g = torch.from_numpy(rng.normal(size=(2, 40, 48, 3)).astype(np.float32)).cuda()
     img0, tape0, (dV0, di0, _), _ = _run(gs, 0, g)
-    img1, tape1, (dV1, di1, _), prof = _run(gs, 1, g)
+    img1, tape1, (dV1, di1, _), prof = _run(gs, ORDER, g)
     assert tape1.ws.level_capacity > 0 and _sorts(prof, gs.params.max_depth)
     assert tape0.stats["nodes_visited"] == tape1.stats["nodes_visited"]
     np.testing.assert_allclose(img1.cpu().numpy(), img0.cpu().numpy(), rtol=1e-6, atol=1e-7)
@@ -120,11 +124,11 @@ def test_order_in_a_batch():
     grads = [torch.from_numpy(rng.normal(size=(g.cams.shape[0], g.height, g.width, 3)).astype(np.float32)).cuda()
              for g in scenes]
     out = {}
-    for order in (0, 1):
+    for order in (0, ORDER):
         dt.set_tuning(trace_order=order)
         imgs, tape = dt.render_batch(items)
         out[order] = ([i.cpu().numpy() for i in imgs], tape.stats, dt.render_batch_backward(tape, grads))
-    (i0, s0, g0), (i1, s1, g1) = out[0], out[1]
+    (i0, s0, g0), (i1, s1, g1) = out[0], out[ORDER]
     assert s0["segments"] == s1["segments"] and s0["nodes_visited"] == s1["nodes_visited"]
     for a, b in zip(i0, i1):
         np.testing.assert_allclose(b, a, rtol=1e-6, atol=1e-7)
@@ -139,7 +143,7 @@ def test_order_with_tiny_levels():
     sc = S.glass_icosphere_scene(width=3, height=2)
     gs = GpuScene.from_scene(sc, max_depth=6)
     img0, tape0, _, _ = _run(gs, 0)
-    img1, tape1, _, prof = _run(gs, 1)
+    img1, tape1, _, prof = _run(gs, ORDER)
     assert _sorts(prof, 6) and tape1.stats["status"] == dt.DT_OK
     np.testing.assert_array_equal(_sorted_dump(tape0)[0], _sorted_dump(tape1)[0])
     assert_radiance_parity(img1[0], gs.oracle(0))
