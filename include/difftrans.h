@@ -342,7 +342,7 @@ dt_status dt_l2_loss_grad(const float* d_img, const float* d_target, int64_t n, 
  * hit and flag words), so that a warp's rays take similar paths through the
  * BVH.  0 traces the segments in the order they were appended.  Camera
  * rays are laid out in 8x4 pixel blocks.
- * Defaults {64, 8, 5, 4, 2, 1, 20}; results do not depend on them (the same
+ * Defaults {192, 8, 5, 4, 2, 1, 20}; results do not depend on them (the same
  * closest hit is found).  dt_set_tuning rejects values outside steps
  * 1..256, refill 1..32, trace 1..8, shade 1..16, width 2 or 4, builder 0
  * or 1, order 0 or 12..22.

@@ -2,7 +2,8 @@
 
 The kernels' results do not depend on the knobs (the same closest hits are
 found), only their speed does: node format of the traversal (binary or
-4-wide), resident traversal CTAs per SM (its register budget), node visits
+4-wide), the width of the traversal-order buckets (0: append order),
+resident traversal CTAs per SM (its register budget), node visits
 per scheduling round and the idle-lane count that triggers a refill, and the
 grid of the shading and adjoint kernels.  `tune` times a caller's step
 function under a grid of settings with CUDA events and keeps the fastest;
@@ -21,8 +22,9 @@ from . import get_tuning, set_tuning
 
 DEFAULT_SPACE = {
     "bvh_width": (2, 4),
+    "trace_order": (0, 16, 20, 22),
     "trace_blocks_per_sm": (4, 5, 6),
-    "trace_steps": (16, 32, 64, 128),
+    "trace_steps": (32, 64, 128, 192, 256),
     "trace_refill": (4, 8, 16),
     "shade_blocks_per_sm": (4, 8, 16),
 }

@@ -254,12 +254,12 @@ __device__ __forceinline__ size_t hit_slot(const WsView& W, int k, uint32_t a, u
   return W.ring ? (size_t)(k & 1) * W.ring + i : (size_t)a;
 }
 
-// The hit records of level k (arena start `start`).  Until level k is
-// traced they hold, per position, the segment's traversal-order bucket and
-// its rank in the bucket (written with each segment by the shading pass of
+// The hit records of level k (arena start `start`) seen as 32-bit words.
+// Until level k is traced the first n words hold each segment's
+// traversal-order bucket (written with the segment by the shading pass of
 // level k-1).
-__device__ __forceinline__ uint2* level_buckets(const WsView& W, int k, uint32_t start) {
-  return reinterpret_cast<uint2*>(W.hit + (W.ring ? (size_t)(k & 1) * W.ring : (size_t)start));
+__device__ __forceinline__ uint32_t* level_buckets(const WsView& W, int k, uint32_t start) {
+  return reinterpret_cast<uint32_t*>(W.hit + (W.ring ? (size_t)(k & 1) * W.ring : (size_t)start));
 }
 
 // Traversal-order key of a ray: the direction octant in bits 21-23 above the
@@ -285,10 +285,13 @@ __device__ __forceinline__ uint32_t ray_order_key(float3 o, float3 d, float3 lo,
 __device__ __forceinline__ uint32_t order_bucket(uint32_t key24, int bits, bool batch, uint32_t scene) {
   return batch ? (scene << (bits - 8)) | (key24 >> (32 - bits)) : key24 >> (24 - bits);
 }
-// Counts a child in its bucket and stores (bucket, rank in the bucket: the
-// count before it) at its position p of the next level; b == ~0u: no child.
-__device__ __forceinline__ void order_count_child(uint32_t* count, uint2* kr, uint32_t b, uint32_t p) {
-  if (b != ~0u) kr[p] = make_uint2(b, atomicAdd(count + b, 1u));
+// Counts a child in its bucket and stores the bucket at its position p of
+// the next level; b == ~0u: no child.
+__device__ __forceinline__ void order_count_child(uint32_t* count, uint32_t* kb, uint32_t b, uint32_t p) {
+  if (b != ~0u) {
+    kb[p] = b;
+    atomicAdd(count + b, 1u);
+  }
 }
 
 // Bounding box of a scene from its binary BVH root (node 0): lo and the

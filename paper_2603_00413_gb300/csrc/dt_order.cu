@@ -10,36 +10,42 @@
 // the same in any order.
 //
 // A counting sort by bucket.  The shading pass of level k-1 writes each
-// child's bucket and counts it in a table of 2^kOrderBits counters with an
-// atomic whose return value is the child's rank in its bucket.  One scan turns the counts into bucket starts, and each segment's
-// position in the order is then its bucket's start plus its rank: no sort
-// passes.  The order within a bucket is the atomics' order; only the bucket
-// sequence matters for coherence.  Keys and ranks live in the level's hit
-// records (written only when the level is traced), the order in its flag
-// words (written only by the shading pass after the trace), the table in a
-// fixed region of the workspace.  Level sizes are read on the device, so
-// the launches need no host synchronisation.
+// child's bucket and counts it in a table of 2^kOrderBits counters.  One
+// scan turns the counts into bucket starts, and a placement pass gives each
+// segment the next free place of its bucket (an atomic on the start): no
+// sort passes.  The order within a bucket is the atomics' order; only the
+// bucket sequence matters for coherence.  The buckets live in the level's
+// hit records (written only when the level is traced), the order in its
+// flag words (written only by the shading pass after the trace), the table
+// in a fixed region of the workspace.  Level sizes are read on the device,
+// so the launches need no host synchronisation.
 #include "dt_internal.cuh"
 
 namespace dt {
 
 constexpr int kOrderThreads = 256;
-constexpr int kScanPerThread = 32;                           // counters per thread of the scan
-constexpr int kScanSpan = kOrderThreads * kScanPerThread;    // counters per CTA of the scan
+constexpr int kScanIters = 8;                                   // uint4 loads per lane
+constexpr int kScanWarpSpan = kScanIters * 32 * 4;              // counters per warp of the scan
+constexpr int kScanSpan = (kOrderThreads / 32) * kScanWarpSpan;  // counters per CTA of the scan (8192)
 
 static_assert(kOrderCounters % kScanSpan == 0, "the counter table is a whole number of scan spans");
-constexpr int kScanBlocks = kOrderCounters / kScanSpan;
-static_assert(kScanBlocks <= 1024, "one CTA scans the span totals");
+static_assert(kOrderCounters / kScanSpan <= 1024, "a CTA scans the span totals in shared memory");
 
-// Block-wide exclusive sum over kOrderThreads values; *total gets the sum.
-__device__ __forceinline__ uint32_t block_exclusive_sum(uint32_t v, uint32_t* s_warp, uint32_t* total) {
-  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  uint32_t x = v;
+// Inclusive warp sum of v over lanes 0..lane.
+__device__ __forceinline__ uint32_t warp_inclusive_sum(uint32_t v) {
+  const uint32_t lane = threadIdx.x & 31;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(kFull, x, o);
-    if (lane >= (uint32_t)o) x += y;
+    const uint32_t y = __shfl_up_sync(kFull, v, o);
+    if (lane >= (uint32_t)o) v += y;
   }
+  return v;
+}
+
+// Block-wide exclusive sum over the block's threads; *total gets the sum.
+__device__ __forceinline__ uint32_t block_exclusive_sum(uint32_t v, uint32_t* s_warp, uint32_t* total) {
+  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const uint32_t x = warp_inclusive_sum(v);
   if (lane == 31) s_warp[wid] = x;
   __syncthreads();
   uint32_t before = 0, all = 0;
@@ -52,73 +58,114 @@ __device__ __forceinline__ uint32_t block_exclusive_sum(uint32_t v, uint32_t* s_
   return before + x - v;
 }
 
-// Counts -> exclusive starts within each span of kScanSpan counters; the
-// span totals go to span_sum[].
+// Counts -> exclusive starts within each span of kScanSpan counters (each
+// warp an eighth of the span, read with coalesced 16-byte loads); the span
+// totals go to span_sum[].
 __global__ void __launch_bounds__(kOrderThreads) k_order_scan_spans(uint32_t* __restrict__ count,
                                                                     uint32_t* __restrict__ span_sum) {
   __shared__ uint32_t s_warp[kOrderThreads / 32];
-  uint4* c4 = reinterpret_cast<uint4*>(count + (size_t)blockIdx.x * kScanSpan + threadIdx.x * kScanPerThread);
-  uint4 v[kScanPerThread / 4];
-  uint32_t s = 0;
+  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint4* c4 = reinterpret_cast<uint4*>(count + (size_t)blockIdx.x * kScanSpan + wid * kScanWarpSpan) + lane;
+  uint4 v[kScanIters];
+  uint32_t ex[kScanIters];
+  uint32_t run = 0;  // the warp's sum so far
 #pragma unroll
-  for (int q = 0; q < kScanPerThread / 4; ++q) {
-    v[q] = c4[q];
-    s += v[q].x + v[q].y + v[q].z + v[q].w;
+  for (int it = 0; it < kScanIters; ++it) v[it] = c4[it * 32];
+#pragma unroll
+  for (int it = 0; it < kScanIters; ++it) {
+    const uint32_t s = v[it].x + v[it].y + v[it].z + v[it].w;
+    const uint32_t inc = warp_inclusive_sum(s);
+    ex[it] = run + inc - s;
+    run += __shfl_sync(kFull, inc, 31);
   }
   uint32_t total;
-  uint32_t run = block_exclusive_sum(s, s_warp, &total);
+  const uint32_t warp_base = block_exclusive_sum(lane == 0 ? run : 0u, s_warp, &total);
+  const uint32_t base = __shfl_sync(kFull, warp_base, 0);
 #pragma unroll
-  for (int q = 0; q < kScanPerThread / 4; ++q) {
+  for (int it = 0; it < kScanIters; ++it) {
+    uint32_t r = base + ex[it];
     uint4 o;
-    o.x = run; run += v[q].x;
-    o.y = run; run += v[q].y;
-    o.z = run; run += v[q].z;
-    o.w = run; run += v[q].w;
-    c4[q] = o;
+    o.x = r; r += v[it].x;
+    o.y = r; r += v[it].y;
+    o.z = r; r += v[it].z;
+    o.w = r;
+    c4[it * 32] = o;
   }
   if (threadIdx.x == 0) span_sum[blockIdx.x] = total;
 }
 
-// Exclusive scan of the span totals in place (one CTA).
-__global__ void __launch_bounds__(1024) k_order_scan_totals(uint32_t* __restrict__ span_sum) {
-  __shared__ uint32_t s_warp[32];
-  const uint32_t v = threadIdx.x < (unsigned)kScanBlocks ? span_sum[threadIdx.x] : 0u;
-  uint32_t total;
-  const uint32_t e = block_exclusive_sum(v, s_warp, &total);
-  if (threadIdx.x < (unsigned)kScanBlocks) span_sum[threadIdx.x] = e;
-}
-
-// Position of every segment of level k in the traversal order: its
-// bucket's start plus its rank in the bucket.
-__global__ void __launch_bounds__(kOrderThreads) k_order_place(WsView W, int k) {
+// Position of every segment of level k in the traversal order: the next
+// free place of its bucket (an atomic on the bucket's start in its span)
+// plus the totals of the spans before it (scanned by each CTA in shared
+// memory).  Four independent segments per thread and step keep several
+// atomics in flight.
+constexpr int kPlaceUnroll = 4;
+__global__ void __launch_bounds__(kOrderThreads) k_order_place(WsView W, int k, int spans) {
+  __shared__ uint32_t s_span[1024];
+  __shared__ uint32_t s_warp[kOrderThreads / 32];
   const WsHeader* H = W.hdr;
   const uint32_t n = level_size(H, k);
+  if (n == 0) return;
   const uint32_t start = H->level_start[k];
-  const uint2* kr = level_buckets(W, k, start);
+  {
+    const uint32_t* tot = W.order_count + kOrderCounters;
+    uint32_t v[4], sum = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = threadIdx.x * 4 + q;
+      v[q] = j < spans ? tot[j] : 0u;
+      sum += v[q];
+    }
+    uint32_t all;
+    uint32_t run = block_exclusive_sum(sum, s_warp, &all);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      s_span[threadIdx.x * 4 + q] = run;
+      run += v[q];
+    }
+  }
+  __syncthreads();
+  const uint32_t* kb = level_buckets(W, k, start);
   uint32_t* order = W.sflag + start;
-  const uint32_t* count = W.order_count;
-  const uint32_t* span_sum = W.order_count + kOrderCounters;
-  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-    const uint2 br = kr[p];
-    const uint32_t b = br.x & (kOrderCounters - 1);
-    const uint32_t pos = __ldg(count + b) + __ldg(span_sum + b / kScanSpan) + br.y;
-    if (pos < n) order[pos] = p;
+  uint32_t* count = W.order_count;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t p0 = blockIdx.x * blockDim.x + threadIdx.x; p0 < n; p0 += kPlaceUnroll * stride) {
+    uint32_t b[kPlaceUnroll], c[kPlaceUnroll];
+#pragma unroll
+    for (int j = 0; j < kPlaceUnroll; ++j) {
+      const uint32_t p = p0 + j * stride;
+      b[j] = p < n ? kb[p] & (kOrderCounters - 1) : ~0u;
+    }
+#pragma unroll
+    for (int j = 0; j < kPlaceUnroll; ++j) c[j] = b[j] != ~0u ? atomicAdd(count + b[j], 1u) : 0u;
+#pragma unroll
+    for (int j = 0; j < kPlaceUnroll; ++j) {
+      if (b[j] == ~0u) continue;
+      const uint32_t pos = c[j] + s_span[b[j] / kScanSpan];
+      if (pos < n) order[pos] = p0 + j * stride;
+    }
   }
 }
 
-void launch_order_clear(const WsView& W, cudaStream_t s) {
+// Buckets in use for `bits`-bit keys: whole scan spans.
+static uint32_t order_buckets(int bits) {
+  const uint32_t nb = 1u << bits;
+  return nb < (uint32_t)kScanSpan ? (uint32_t)kScanSpan : nb;
+}
+
+void launch_order_clear(const WsView& W, int bits, cudaStream_t s) {
   ProfScope ps("order_clear", s);
-  cudaMemsetAsync(W.order_count, 0, (size_t)kOrderCounters * sizeof(uint32_t), s);
+  cudaMemsetAsync(W.order_count, 0, (size_t)order_buckets(bits) * sizeof(uint32_t), s);
 }
 
 // Level k (k >= 1) into its traversal order, from the buckets and ranks the
-// shading pass of level k-1 wrote.
-void launch_order(const WsView& W, int k, cudaStream_t s) {
+// shading pass of level k-1 wrote with `bits`-bit keys.
+void launch_order(const WsView& W, int k, int bits, cudaStream_t s) {
   ProfScope ps("k_order", s);
+  const int spans = (int)(order_buckets(bits) / kScanSpan);
   uint32_t* span_sum = W.order_count + kOrderCounters;
-  k_order_scan_spans<<<kScanBlocks, kOrderThreads, 0, s>>>(W.order_count, span_sum);
-  k_order_scan_totals<<<1, 1024, 0, s>>>(span_sum);
-  k_order_place<<<4 * num_sms(), kOrderThreads, 0, s>>>(W, k);
+  k_order_scan_spans<<<spans, kOrderThreads, 0, s>>>(W.order_count, span_sum);
+  k_order_place<<<8 * num_sms(), kOrderThreads, 0, s>>>(W, k, spans);
 }
 
 }  // namespace dt

@@ -496,7 +496,7 @@ __global__ void __launch_bounds__(kShadeThreads, kShadeMinBlocks) k_shade(WsView
   __shared__ uint32_t s_wr[kShadeThreads / 32], s_wt[kShadeThreads / 32];
   __shared__ uint32_t s_base, s_nr;
   const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  uint2* next_kr = order_bits ? level_buckets(W, k + 1, next_start) : nullptr;
+  uint32_t* next_kr = order_bits ? level_buckets(W, k + 1, next_start) : nullptr;
   // positions of level k+1 that can hold a bucket (its ring half, or the arena)
   const unsigned long long key_room = W.ring ? (unsigned long long)W.ring : H->capacity - next_start;
   float3 box_lo = mk(0.f, 0.f, 0.f), box_scale = box_lo;
@@ -673,8 +673,8 @@ __global__ void k_dump(WsView W, int32_t* __restrict__ si, float* __restrict__ s
 extern dt_tuning g_tuning;
 // Traversal order of level k from the buckets counted while it was shaded
 // into existence, and the clearing of the bucket counters (dt_order.cu).
-void launch_order(const WsView& W, int k, cudaStream_t s);
-void launch_order_clear(const WsView& W, cudaStream_t s);
+void launch_order(const WsView& W, int k, int bits, cudaStream_t s);
+void launch_order_clear(const WsView& W, int bits, cudaStream_t s);
 static int shade_blocks() { return g_tuning.shade_blocks_per_sm * num_sms(); }
 static int n_int_of(int32_t nf) { return nf > 1 ? nf - 1 : 1; }
 
@@ -742,7 +742,7 @@ void launch_forward_table(const TableHeader& th, const SceneEntry* entries, void
   const int order_bits = g_tuning.trace_order;
   for (int k = 0; k <= th.max_depth; ++k) {
     const int sorted = order_bits && k > 0;
-    if (sorted) launch_order(W, k, s);
+    if (sorted) launch_order(W, k, order_bits, s);
     {
       ProfScope ps("k_trace", s);
       if (g_tuning.bvh_width == 4) {
@@ -755,7 +755,7 @@ void launch_forward_table(const TableHeader& th, const SceneEntry* entries, void
     }
     {
       const int bits = k < th.max_depth ? order_bits : 0;
-      if (bits) launch_order_clear(W, s);
+      if (bits) launch_order_clear(W, bits, s);
       ProfScope ps("k_shade", s);
       if (batch) k_shade<true><<<shade_blocks(), kShadeThreads, 0, s>>>(W, k, E0, bits);
       else k_shade<false><<<shade_blocks(), kShadeThreads, 0, s>>>(W, k, E0, bits);
