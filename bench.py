@@ -40,6 +40,7 @@ HIT_RECORD = 16          # t, b1, b2, tri
 LINK_RECORD = 8          # child index + flags
 NODE_BYTES = 64          # one internal node: two child boxes + child ids
 TRI_BYTES = 48           # v0, e1, e2 of a leaf triangle
+ORDER_ENTRY = 4          # a level's traversal-order entry / a child's order bucket
 HIT_SCENE = 84           # 3 indices + 3 positions + 3 vertex normals
 ENV_MISS = 4 * 12 + 12   # 4 texels + pixel accumulation
 ADJ_OUT = 36             # (L, obar, dbar) handed to the parent
@@ -249,6 +250,31 @@ KERNELS_PER_SCOPE = {"k_vertex_normals": 2, "k_refit": 3, "k_camera": 1, "k_trac
                      "k_write_table": 2, "k_zero_images": 1, "k_zero_grads": 1}
 
 
+def sah_levels(nf: int) -> int:
+    """Large-task levels the binned-SAH builder launches for nf triangles:
+    tasks above 128 triangles are split level by level, with 24 levels of
+    free splits plus the median levels below them, at most 64."""
+    if nf <= 128:
+        return 0
+    lg = 0
+    while (128 << lg) < nf:
+        lg += 1
+    return min(24 + lg + 2, 64)
+
+
+def scope_kernels(scope: str, nf: int) -> int:
+    """Kernels launched per entry of a profiled scope; the SAH build's scopes
+    nest (sah_build holds sah_large_levels and sah_small), so each counts only
+    its own launches."""
+    if scope == "sah_build":
+        return 10  # header, bounds x2, primitives, root, 4-wide topology x4, validation
+    if scope == "sah_large_levels":
+        return 4 * sah_levels(nf)
+    if scope == "sah_small":
+        return 1
+    return KERNELS_PER_SCOPE.get(scope, 1)
+
+
 def serve_leg(args, scs, dev):
     """Poisson streams of render and gradient requests (50/50) over 32
     resident meshes; square images with side log-uniform in [64, 1024],
@@ -290,9 +316,10 @@ def large_leg(args, dt, dev):
     [-1.3, 1.3]^3 (about 1.1M triangles), one 800x800 view with 8 jittered
     samples per pixel (5.12M camera rays), depth 16, IoR 1.52, sigma (0.3,
     0.1, 0.05), a 2048x1024 environment; L2 loss against a render of the
-    vertices perturbed by N(0, 0.001).  One step = LBVH rebuild + vertex
-    normals + checkpointed forward + loss seed + backward (hits recovered
-    from the children's source triangles).  The same step with the full tape is timed beside it."""
+    vertices perturbed by N(0, 0.001).  One step = BVH rebuild (the tuned
+    builder: binned SAH by default) + vertex normals + checkpointed forward
+    + loss seed + backward (hits recovered from the children's source
+    triangles).  The same step with the full tape is timed beside it."""
     import torch
     from paper_2603_00413_gb300 import scenes as S
     t0 = time.time()
@@ -357,9 +384,10 @@ def large_leg(args, dt, dev):
         tot = sum(v[1] for v in prof.values())
         out[mode] = {"ms_per_step": ms, "segments_per_step": int(seg), "segments_per_s": seg / (ms / 1e3),
                      "tape_bytes": int(ws.bytes), "level_capacity": int(ws.level_capacity),
-                     "rebuild_ms": prof.get("lbvh_build", (1, 0.0))[1] / args.large_steps,
+                     "rebuild_ms": (prof.get("lbvh_build", (1, 0.0))[1] + prof.get("sah_build", (1, 0.0))[1])
+                     / args.large_steps,
                      "kernel_share": {k: round(v[1] / tot, 4) for k, v in prof.items()},
-                     "gpu_launches_per_step": int(sum(v[0] * KERNELS_PER_SCOPE.get(k, 1) for k, v in prof.items())
+                     "gpu_launches_per_step": int(sum(v[0] * scope_kernels(k, Fn.shape[0]) for k, v in prof.items())
                                                   / args.large_steps),
                      "levels": stats["level_count"], "loss": float(loss.item())}
         del ws, bws, tape, img, target, grad
@@ -608,15 +636,19 @@ def run_ours(args):
     bvh_bytes = (sc.F.shape[0] - 1) * NODE_BYTES + sc.F.shape[0] * TRI_BYTES
     # bytes that must cross HBM per step (the BVH, the scene and the
     # environment stay in L2; the tape, the image and its gradient do not)
+    # (levels after the camera rays, when traced in bucket order: + the
+    # order entry the traversal reads, + the bucket the shading pass writes)
+    ordered = children if dt.get_tuning()["trace_order"] else 0
     hbm_step = {
-        "k_trace": seg * (RAY_RECORD + HIT_RECORD) + (D + 1) * bvh_bytes,
-        "k_shade": seg * (RAY_RECORD + HIT_RECORD + LINK_RECORD) + children * RAY_RECORD + misses * 2 * 12,
+        "k_trace": seg * (RAY_RECORD + HIT_RECORD) + ordered * ORDER_ENTRY + (D + 1) * bvh_bytes,
+        "k_shade": seg * (RAY_RECORD + HIT_RECORD + LINK_RECORD) + children * RAY_RECORD + ordered * ORDER_ENTRY
+        + misses * 2 * 12,
         "k_adjoint": seg * (RAY_RECORD + HIT_RECORD + LINK_RECORD + 12) + (seg - nvw * res * res) * 48
         + spawners * 2 * 48,
     }
     # bytes the kernel moves through L2 (on-chip reuse included)
     l2_step = {
-        "k_trace": seg * (RAY_RECORD + HIT_RECORD) + stats["nodes_visited"] * NODE_BYTES
+        "k_trace": seg * (RAY_RECORD + HIT_RECORD) + ordered * ORDER_ENTRY + stats["nodes_visited"] * NODE_BYTES
         + stats["tris_tested"] * TRI_BYTES,
         "k_shade": hbm_step["k_shade"] + hits * HIT_SCENE + misses * ENV_MISS,
         "k_adjoint": hbm_step["k_adjoint"] + spawners * (HIT_SCENE + ADJ_ATOMICS) + misses * 48,

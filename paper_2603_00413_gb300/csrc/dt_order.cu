@@ -95,10 +95,10 @@ __global__ void __launch_bounds__(kOrderThreads) k_order_scan_spans(uint32_t* __
 }
 
 // Position of every segment of level k in the traversal order: the next
-// free place of its bucket (an atomic on the bucket's start in its span)
-// plus the totals of the spans before it (scanned by each CTA in shared
-// memory).  Four independent segments per thread and step keep several
-// atomics in flight.
+// free place of its bucket (an atomic on the bucket's start in its span,
+// one per bucket per warp) plus the totals of the spans before it (scanned
+// by each CTA in shared memory).  Four independent steps per warp keep
+// several atomics in flight.
 constexpr int kPlaceUnroll = 4;
 __global__ void __launch_bounds__(kOrderThreads) k_order_place(WsView W, int k, int spans) {
   __shared__ uint32_t s_span[1024];
@@ -128,21 +128,32 @@ __global__ void __launch_bounds__(kOrderThreads) k_order_place(WsView W, int k, 
   const uint32_t* kb = level_buckets(W, k, start);
   uint32_t* order = W.sflag + start;
   uint32_t* count = W.order_count;
+  const uint32_t lane = threadIdx.x & 31;
+  const unsigned lanes_below = (1u << lane) - 1u;
   const uint32_t stride = gridDim.x * blockDim.x;
-  for (uint32_t p0 = blockIdx.x * blockDim.x + threadIdx.x; p0 < n; p0 += kPlaceUnroll * stride) {
-    uint32_t b[kPlaceUnroll], c[kPlaceUnroll];
+  // warp-uniform loop: neighbouring segments often share a bucket, so the
+  // lanes of one bucket take their places with one atomic
+  for (uint32_t w0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); w0 < n; w0 += kPlaceUnroll * stride) {
+    uint32_t b[kPlaceUnroll], base[kPlaceUnroll];
+    unsigned peers[kPlaceUnroll];
 #pragma unroll
     for (int j = 0; j < kPlaceUnroll; ++j) {
-      const uint32_t p = p0 + j * stride;
+      const uint32_t p = w0 + j * stride + lane;
       b[j] = p < n ? kb[p] & (kOrderCounters - 1) : ~0u;
     }
 #pragma unroll
-    for (int j = 0; j < kPlaceUnroll; ++j) c[j] = b[j] != ~0u ? atomicAdd(count + b[j], 1u) : 0u;
+    for (int j = 0; j < kPlaceUnroll; ++j) {
+      peers[j] = __match_any_sync(kFull, b[j]);
+      base[j] = 0;
+      if (b[j] != ~0u && lane == (uint32_t)(__ffs(peers[j]) - 1))
+        base[j] = atomicAdd(count + b[j], (uint32_t)__popc(peers[j]));
+    }
 #pragma unroll
     for (int j = 0; j < kPlaceUnroll; ++j) {
+      const uint32_t c = __shfl_sync(kFull, base[j], __ffs(peers[j]) - 1) + __popc(peers[j] & lanes_below);
       if (b[j] == ~0u) continue;
-      const uint32_t pos = c[j] + s_span[b[j] / kScanSpan];
-      if (pos < n) order[pos] = p0 + j * stride;
+      const uint32_t pos = c + s_span[b[j] / kScanSpan];
+      if (pos < n) order[pos] = w0 + j * stride + lane;
     }
   }
 }
