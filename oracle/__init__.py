@@ -71,19 +71,63 @@ def _load():
         lib.orc_camera_rays.argtypes = [P, I, I, I, I, U64, I, P, P]
         lib.orc_pcg_hash.argtypes = [ctypes.c_uint32]
         lib.orc_pcg_hash.restype = ctypes.c_uint32
+        M = ctypes.POINTER(_OrcMedium)
         lib.orc_render.argtypes = [P, I, P, I, D, P, P, I, I, P, I, I, I, I, I, U64, I, D, D,
-                                   P, P, P, P, P, P, I64, P, P]
+                                   P, P, P, P, P, P, I64, P, P, M]
         lib.orc_render_rays.argtypes = [P, I, P, I, D, P, P, I, I, P, P, I, I, D, D,
-                                        P, P, P, P, P, P, I64, P, P]
+                                        P, P, P, P, P, P, I64, P, P, M]
         lib.orc_render_jvp.argtypes = [P, I, P, I, D, P, P, I, I, P, I, I, I, I, I, U64, I, D,
-                                       I, P, P, P, P, P]
-        lib.orc_render_rays_jvp.argtypes = [P, I, P, I, D, P, P, I, I, P, P, I, I, D, I, P, P, P, P, P]
+                                       I, P, P, P, P, P, M, P]
+        lib.orc_render_rays_jvp.argtypes = [P, I, P, I, D, P, P, I, I, P, P, I, I, D, I, P, P, P, P, P, M, P]
+        lib.orc_medium_depth.argtypes = [M, P, P, P, I, P]
         _lib = lib
     return _lib
 
 
+class _OrcMedium(ctypes.Structure):
+    _fields_ = [("mu", ctypes.c_void_p), ("n", ctypes.c_int * 3), ("lo", ctypes.c_double * 3),
+                ("hi", ctypes.c_double * 3), ("step", ctypes.c_double)]
+
+
 def _d(a):
     return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _medium(medium):
+    """(struct, keep-alive array) for a medium dict(mu [nz, ny, nx, 3], lo
+    (3,), hi (3,), step) or (None, None)."""
+    if medium is None:
+        return None, None
+    mu = _d(medium["mu"])
+    assert mu.ndim == 4 and mu.shape[3] == 3 and min(mu.shape[:3]) >= 2
+    m = _OrcMedium()
+    m.mu = mu.ctypes.data_as(ctypes.c_void_p)
+    m.n[0], m.n[1], m.n[2] = mu.shape[2], mu.shape[1], mu.shape[0]
+    for a in range(3):
+        m.lo[a] = float(medium["lo"][a])
+        m.hi[a] = float(medium["hi"][a])
+    m.step = float(medium["step"])
+    return m, mu
+
+
+def _mp(m):
+    return ctypes.byref(m) if m is not None else None
+
+
+def medium_depth(medium, o, d, t) -> np.ndarray:
+    """Optical depth of an absorption grid over segments o + s d, s in
+    [0, t] (Eq. 11 with the spatially varying rate of the grid): steps of
+    length `step` from the start, the last one partial, each sampled at its
+    midpoint with trilinear interpolation of the node values (positions
+    clamped to the grid's box).  medium = dict(mu [nz, ny, nx, 3], lo, hi,
+    step).  Returns [n, 3]."""
+    o, d = _d(o).reshape(-1, 3), _d(d).reshape(-1, 3)
+    t = _d(t).reshape(-1)
+    out = np.zeros_like(o)
+    m, keep = _medium(medium)
+    _load().orc_medium_depth(_mp(m), _p(o), _p(d), _p(t), o.shape[0], _p(out))
+    del keep
+    return out
 
 
 def _i(a):
@@ -158,7 +202,7 @@ def _common(V, F, ior, sigma, env, cam):
 
 
 def render(V, F, ior, sigma, env, cam, max_depth: int, spp: int = 1, jitter: int = 0, seed: int = 0,
-           view: int = 0, t_min: float = 1e-5, segments: bool = False, probe: float = 0.0) -> dict:
+           view: int = 0, t_min: float = 1e-5, segments: bool = False, probe: float = 0.0, medium=None) -> dict:
     """FP64 render of one view: the recursive ray tree of Sec. 3.4 steps 1-5.
 
     Returns dict(img [H,W,3], discard [H,W,3], pix_flags [H,W], pix_sig [H,W],
@@ -167,8 +211,10 @@ def render(V, F, ior, sigma, env, cam, max_depth: int, spp: int = 1, jitter: int
     discard is the path weight lost to the depth limit or to a backfacing
     shading normal.  probe > 0 re-traces every primary ray tilted by probe
     radians four ways and flags pixels whose path events change
-    (SEG_UNSTABLE in pix_flags)."""
+    (SEG_UNSTABLE in pix_flags).  medium: an absorption grid (see
+    medium_depth) added to sigma on interior segments."""
     V, F, ior, sigma, env, c = _common(V, F, ior, sigma, env, cam)
+    m, keep = _medium(medium)
     H, W = cam.height, cam.width
     img = np.zeros((H * W, 3))
     disc = np.zeros((H * W, 3))
@@ -180,7 +226,8 @@ def render(V, F, ior, sigma, env, cam, max_depth: int, spp: int = 1, jitter: int
     args = (_p(V), V.shape[0], _p(F), F.shape[0], ior, _p(sigma), _p(env), env.shape[1], env.shape[0],
             _p(c), W, H, int(max_depth), int(spp), int(jitter), int(seed), int(view), float(t_min), float(probe),
             _p(img), _p(disc), _p(pf), _p(sig))
-    seg_i, seg_f = _run_with_segments(lib.orc_render, args, segments, nseg, cnt)
+    seg_i, seg_f = _run_with_segments(lib.orc_render, args, segments, nseg, cnt, m)
+    del keep
     out = dict(img=img.reshape(H, W, 3), discard=disc.reshape(H, W, 3), pix_flags=pf.reshape(H, W),
                pix_sig=sig.reshape(H, W), counters=dict(zip(COUNTER_NAMES, cnt.tolist())))
     if segments:
@@ -188,20 +235,20 @@ def render(V, F, ior, sigma, env, cam, max_depth: int, spp: int = 1, jitter: int
     return out
 
 
-def _run_with_segments(fn, args, segments, nseg, cnt):
+def _run_with_segments(fn, args, segments, nseg, cnt, m=None):
     if not segments:
-        fn(*args, None, None, 0, None, _p(cnt))
+        fn(*args, None, None, 0, None, _p(cnt), _mp(m))
         return None, None
-    fn(*args, None, None, 0, _p(nseg), _p(cnt))
+    fn(*args, None, None, 0, _p(nseg), _p(cnt), _mp(m))
     n = int(nseg[0])
     seg_i = np.zeros((max(n, 1), 4), np.int32)
     seg_f = np.zeros((max(n, 1), 9))
-    fn(*args, _p(seg_i), _p(seg_f), n, _p(nseg), _p(cnt))
+    fn(*args, _p(seg_i), _p(seg_f), n, _p(nseg), _p(cnt), _mp(m))
     return seg_i[:n], seg_f[:n]
 
 
 def render_rays(V, F, ior, sigma, env, o, d, max_depth: int, t_min: float = 1e-5,
-                segments: bool = False, probe: float = 0.0) -> dict:
+                segments: bool = False, probe: float = 0.0, medium=None) -> dict:
     """The same FP64 ray tree for arbitrary primary rays (o, d: [n,3], d
     unit), one sample each.  Outputs as render() with pixels = rays."""
     V, F = _d(V), _i(F)
@@ -217,7 +264,9 @@ def render_rays(V, F, ior, sigma, env, o, d, max_depth: int, t_min: float = 1e-5
     lib = _load()
     args = (_p(V), V.shape[0], _p(F), F.shape[0], float(ior), _p(sigma), _p(env), env.shape[1], env.shape[0],
             _p(o), _p(d), n, int(max_depth), float(t_min), float(probe), _p(img), _p(disc), _p(pf), _p(sig))
-    seg_i, seg_f = _run_with_segments(lib.orc_render_rays, args, segments, nseg, cnt)
+    m, keep = _medium(medium)
+    seg_i, seg_f = _run_with_segments(lib.orc_render_rays, args, segments, nseg, cnt, m)
+    del keep
     out = dict(img=img, discard=disc, pix_flags=pf, pix_sig=sig, counters=dict(zip(COUNTER_NAMES, cnt.tolist())))
     if segments:
         out["seg_i"], out["seg_f"] = seg_i, seg_f
@@ -225,13 +274,17 @@ def render_rays(V, F, ior, sigma, env, o, d, max_depth: int, t_min: float = 1e-5
 
 
 def render_jvp(V, F, ior, sigma, env, cam, max_depth: int, tV=None, tior=None, tsigma=None,
-               spp: int = 1, jitter: int = 0, seed: int = 0, view: int = 0, t_min: float = 1e-5):
+               spp: int = 1, jitter: int = 0, seed: int = 0, view: int = 0, t_min: float = 1e-5,
+               medium=None, tmu=None):
     """Forward-mode derivative of the FP64 render along ntan directions at
-    fixed events.  tV: [ntan, nv, 3], tior: [ntan], tsigma: [ntan, 3].
+    fixed events.  tV: [ntan, nv, 3], tior: [ntan], tsigma: [ntan, 3], tmu:
+    [ntan, nz, ny, nx, 3] (tangents of the absorption grid's node values).
     Returns (img [H,W,3], dimg [ntan,H,W,3])."""
     V, F, ior, sigma, env, c = _common(V, F, ior, sigma, env, cam)
+    m, keep = _medium(medium)
+    tmu = _d(tmu) if tmu is not None else None
     nt = None
-    for a in (tV, tior, tsigma):
+    for a in (tV, tior, tsigma, tmu):
         if a is not None:
             nt = np.asarray(a).shape[0]
     assert nt is not None and nt > 0
@@ -243,20 +296,25 @@ def render_jvp(V, F, ior, sigma, env, cam, max_depth: int, tV=None, tior=None, t
     dimg = np.zeros((nt, H * W, 3))
     _load().orc_render_jvp(_p(V), V.shape[0], _p(F), F.shape[0], ior, _p(sigma), _p(env), env.shape[1],
                            env.shape[0], _p(c), W, H, int(max_depth), int(spp), int(jitter), int(seed),
-                           int(view), float(t_min), nt, _p(tV), _p(tior), _p(tsigma), _p(img), _p(dimg))
+                           int(view), float(t_min), nt, _p(tV), _p(tior), _p(tsigma), _p(img), _p(dimg),
+                           _mp(m), _p(tmu))
+    del keep
     return img.reshape(H, W, 3), dimg.reshape(nt, H, W, 3)
 
 
 def render_rays_jvp(V, F, ior, sigma, env, o, d, max_depth: int, tV=None, tior=None, tsigma=None,
-                    t_min: float = 1e-5):
-    """Forward-mode derivative of the FP64 tree of arbitrary primary rays.
-    Returns (radiance [n,3], d radiance [ntan,n,3])."""
+                    t_min: float = 1e-5, medium=None, tmu=None):
+    """Forward-mode derivative of the FP64 tree of arbitrary primary rays
+    (tangents as render_jvp).  Returns (radiance [n,3], d radiance
+    [ntan,n,3])."""
     V, F = _d(V), _i(F)
     sigma, env = _d(sigma).reshape(3), _d(env)
     o, d = _d(o).reshape(-1, 3), _d(d).reshape(-1, 3)
     n = o.shape[0]
+    m, keep = _medium(medium)
+    tmu = _d(tmu) if tmu is not None else None
     nt = None
-    for a in (tV, tior, tsigma):
+    for a in (tV, tior, tsigma, tmu):
         if a is not None:
             nt = np.asarray(a).shape[0]
     assert nt is not None and nt > 0
@@ -267,7 +325,8 @@ def render_rays_jvp(V, F, ior, sigma, env, o, d, max_depth: int, tV=None, tior=N
     dimg = np.zeros((nt, n, 3))
     _load().orc_render_rays_jvp(_p(V), V.shape[0], _p(F), F.shape[0], float(ior), _p(sigma), _p(env), env.shape[1],
                                 env.shape[0], _p(o), _p(d), n, int(max_depth), float(t_min), nt, _p(tV), _p(tior),
-                                _p(tsigma), _p(img), _p(dimg))
+                                _p(tsigma), _p(img), _p(dimg), _mp(m), _p(tmu))
+    del keep
     return img, dimg
 
 

@@ -35,6 +35,12 @@
 //    Intersection").
 //  * absorption with a constant per-channel rate: exp(-sigma * t) over an
 //    interior segment of length t (Eq. 11 with one exact step).
+//  * optional spatially varying absorption (Eq. 11 with mu_t = sigma + G):
+//    G is a dense grid of per-channel node values over a box, trilinear,
+//    positions clamped to the box; the segment is cut from its start into
+//    steps of length h (the last one partial: t - m h, m = floor(t / h), at
+//    most 8192 full steps), each contributing G at its midpoint times its
+//    length.  It applies where sigma does: on interior segments.
 //  * self-intersection: the triangle a ray leaves from is skipped and hits need
 //    t > t_min.  Ties on t go to the smaller triangle id.
 //  * environment: equirectangular, y up, bilinear, wrap in u, clamp in v.
@@ -320,6 +326,17 @@ inline void camera_ray(const double* cam, int width, int height, double sx, doub
 // ---------------------------------------------------------------------------
 // the recursive tracer (Sec. 3.4 steps 1-5)
 // ---------------------------------------------------------------------------
+// Dense absorption grid (Eq. 11 with a spatially varying rate): node values
+// mu[((k ny + j) nx + i) 3 + c] at lo + (i, j, k) (hi - lo) / (n - 1).
+struct orc_medium {
+  const double* mu;
+  int n[3];
+  double lo[3], hi[3];
+  double step;
+};
+
+constexpr long kMaxMediumSteps = 8192;
+
 template <class T>
 struct Scene {
   int nv = 0, nf = 0;
@@ -333,7 +350,58 @@ struct Scene {
   int env_w = 0, env_h = 0;
   int max_depth = 0;
   double t_min = 0.0;
+  // absorption grid (has_medium false: sigma only)
+  bool has_medium = false;
+  int gn[3] = {0, 0, 0};
+  double glo[3] = {0, 0, 0}, ghi[3] = {0, 0, 0}, gstep = 0.0;
+  std::vector<T> gmu;  // [nz][ny][nx][3]
 };
+
+// G(x): trilinear interpolation of the grid's node values at x, each
+// coordinate clamped to the box (the clamped coordinate is a constant, so
+// it carries no derivative).
+template <class T>
+V3<T> grid_eval(const Scene<T>& S, const V3<T>& x) {
+  const T xs[3] = {x.x, x.y, x.z};
+  T f[3];
+  int i0[3];
+  for (int a = 0; a < 3; ++a) {
+    const double span = (double)(S.gn[a] - 1);
+    T u = (xs[a] - S.glo[a]) / (S.ghi[a] - S.glo[a]) * span;
+    if (val(u) < 0.0) u = T(0.0);
+    if (val(u) > span) u = T(span);
+    int i = (int)std::floor(val(u));
+    if (i > S.gn[a] - 2) i = S.gn[a] - 2;
+    i0[a] = i;
+    f[a] = u - (double)i;
+  }
+  V3<T> acc;
+  for (int dz = 0; dz < 2; ++dz)
+    for (int dy = 0; dy < 2; ++dy)
+      for (int dx = 0; dx < 2; ++dx) {
+        const T w = (dx ? f[0] : 1.0 - f[0]) * (dy ? f[1] : 1.0 - f[1]) * (dz ? f[2] : 1.0 - f[2]);
+        const size_t node = ((size_t)(i0[2] + dz) * S.gn[1] + (i0[1] + dy)) * S.gn[0] + (i0[0] + dx);
+        acc = acc + V3<T>(S.gmu[3 * node], S.gmu[3 * node + 1], S.gmu[3 * node + 2]) * w;
+      }
+  return acc;
+}
+
+// Optical depth of the grid over the segment o + s d, s in [0, t]: the sum
+// of Eq. 11 over steps of length h from the segment's start, the last one
+// partial, each sampled at its midpoint.
+template <class T>
+V3<T> medium_depth(const Scene<T>& S, const V3<T>& o, const V3<T>& d, const T& t) {
+  V3<T> sum;
+  if (!S.has_medium) return sum;
+  const double h = S.gstep;
+  long m = (long)std::floor(val(t) / h);
+  if (m < 0) m = 0;
+  if (m > kMaxMediumSteps) m = kMaxMediumSteps;
+  for (long i = 0; i < m; ++i) sum = sum + grid_eval(S, o + d * T((i + 0.5) * h)) * T(h);
+  const T r = t - (double)m * h;
+  sum = sum + grid_eval(S, o + d * ((double)m * h + 0.5 * r)) * r;
+  return sum;
+}
 
 struct SegRec {
   int32_t ray, node, tri, flags;
@@ -405,10 +473,17 @@ V3<T> radiance(const Scene<T>& S, const V3<T>& o, const V3<T>& d, int k, uint32_
         bool tir = interface_terms(d, ns, eta1, eta2, wr, wt, R, Tt, &kappa);
         if (std::fabs(kappa) < 1e-6) rec.flags |= SEG_NEAR_CRITICAL;
         if (tir) { rec.flags |= SEG_TIR; P.counters[6]++; }
-        // step 5: absorption over this interior segment (Eq. 11, constant sigma)
+        // step 5: absorption over this interior segment (Eq. 11: constant sigma,
+        // plus the grid's optical depth when there is one)
         V3<T> A(T(1.0), T(1.0), T(1.0));
         if (!entering) {
-          A = V3<T>(exp(-1.0 * S.sigma[0] * t), exp(-1.0 * S.sigma[1] * t), exp(-1.0 * S.sigma[2] * t));
+          if (S.has_medium) {
+            const V3<T> G = medium_depth(S, o, d, t);
+            A = V3<T>(exp(-1.0 * (S.sigma[0] * t + G.x)), exp(-1.0 * (S.sigma[1] * t + G.y)),
+                      exp(-1.0 * (S.sigma[2] * t + G.z)));
+          } else {
+            A = V3<T>(exp(-1.0 * S.sigma[0] * t), exp(-1.0 * S.sigma[1] * t), exp(-1.0 * S.sigma[2] * t));
+          }
         }
         V3d Ad = val3(A);
         const double Rd = val(R), Td = val(Tt);
@@ -449,6 +524,7 @@ struct Inputs {
   const double* env; int env_w; int env_h;
   const double* cam; int width; int height;
   int max_depth; int spp; int jitter; uint64_t seed; int view; double t_min;
+  const orc_medium* medium;
 };
 
 template <class T>
@@ -463,6 +539,15 @@ void setup_scene(const Inputs& in, Scene<T>& S) {
   for (int c = 0; c < 3; ++c) S.sigma[c] = T(in.sigma[c]);
   S.env = in.env; S.env_w = in.env_w; S.env_h = in.env_h;
   S.max_depth = in.max_depth; S.t_min = in.t_min;
+  if (in.medium && in.medium->mu) {
+    const orc_medium& M = *in.medium;
+    S.has_medium = true;
+    for (int a = 0; a < 3; ++a) { S.gn[a] = M.n[a]; S.glo[a] = M.lo[a]; S.ghi[a] = M.hi[a]; }
+    S.gstep = M.step;
+    const size_t nn = (size_t)M.n[0] * M.n[1] * M.n[2] * 3;
+    S.gmu.resize(nn);
+    for (size_t i = 0; i < nn; ++i) S.gmu[i] = T(M.mu[i]);
+  }
 }
 
 // Render a set of pixels.  Pixel p has `spp` primary rays; ray_od(p, s, o, d)
@@ -670,9 +755,10 @@ int orc_render(const double* V, int nv, const int* F, int nf, double ior, const 
                const double* env, int env_w, int env_h, const double* cam, int width, int height,
                int max_depth, int spp, int jitter, uint64_t seed, int view, double t_min, double probe_delta,
                double* img, double* discard, int* pix_flags, uint64_t* pix_sig,
-               int32_t* seg_i, double* seg_f, int64_t cap, int64_t* n_seg, int64_t* counters) {
+               int32_t* seg_i, double* seg_f, int64_t cap, int64_t* n_seg, int64_t* counters,
+               const orc_medium* medium) {
   Inputs in{V, nv, F, nf, ior, sigma, env, env_w, env_h, cam, width, height, max_depth, spp, jitter, seed,
-            view, t_min};
+            view, t_min, medium};
   Scene<double> S;
   setup_scene(in, S);
   vertex_normals(S.V, F, nf, S.N);
@@ -699,8 +785,8 @@ int orc_render_rays(const double* V, int nv, const int* F, int nf, double ior, c
                     const double* env, int env_w, int env_h, const double* o, const double* d, int n,
                     int max_depth, double t_min, double probe_delta, double* img, double* discard, int* pix_flags,
                     uint64_t* pix_sig, int32_t* seg_i, double* seg_f, int64_t cap, int64_t* n_seg,
-                    int64_t* counters) {
-  Inputs in{V, nv, F, nf, ior, sigma, env, env_w, env_h, nullptr, n, 1, max_depth, 1, 0, 0, 0, t_min};
+                    int64_t* counters, const orc_medium* medium) {
+  Inputs in{V, nv, F, nf, ior, sigma, env, env_w, env_h, nullptr, n, 1, max_depth, 1, 0, 0, 0, t_min, medium};
   Scene<double> S;
   setup_scene(in, S);
   vertex_normals(S.V, F, nf, S.N);
@@ -725,7 +811,7 @@ namespace orc {
 // pass re-runs the tree with dual numbers.  ray_od gives the primary rays.
 template <class RayFn>
 void jvp_passes(const Inputs& in, int npix, int spp, RayFn ray_od, int ntan, const double* tV,
-                       const double* tior, const double* tsigma, double* img, double* dimg) {
+                       const double* tior, const double* tsigma, const double* tmu, double* img, double* dimg) {
   constexpr int K = 32;
   const int nv = in.nv;
   for (int base = 0; base < ntan; base += K) {
@@ -741,6 +827,10 @@ void jvp_passes(const Inputs& in, int npix, int spp, RayFn ray_od, int ntan, con
       }
       if (tior) S.ior.d[j] = tior[g];
       if (tsigma) for (int c = 0; c < 3; ++c) S.sigma[c].d[j] = tsigma[3 * g + c];
+      if (tmu && S.has_medium) {
+        const size_t nn = S.gmu.size();
+        for (size_t i = 0; i < nn; ++i) S.gmu[i].d[j] = tmu[(size_t)g * nn + i];
+      }
     }
     vertex_normals(S.V, in.F, in.nf, S.N);
     std::vector<V3<Dual<K>>> im;
@@ -761,21 +851,22 @@ void jvp_passes(const Inputs& in, int npix, int spp, RayFn ray_od, int ntan, con
 extern "C" {
 
 // Forward-mode derivative of one view's image along ntan directions at once.
-// tV: [ntan][nv][3], tior: [ntan], tsigma: [ntan][3] (each nullable = 0).
+// tV: [ntan][nv][3], tior: [ntan], tsigma: [ntan][3], tmu: [ntan][grid nodes][3]
+// (each nullable = 0; medium nullable = no absorption grid).
 // img: [H*W][3] (the same values as orc_render); dimg: [ntan][H*W][3].
 int orc_render_jvp(const double* V, int nv, const int* F, int nf, double ior, const double* sigma,
                    const double* env, int env_w, int env_h, const double* cam, int width, int height,
                    int max_depth, int spp, int jitter, uint64_t seed, int view, double t_min,
                    int ntan, const double* tV, const double* tior, const double* tsigma,
-                   double* img, double* dimg) {
+                   double* img, double* dimg, const orc_medium* medium, const double* tmu) {
   Inputs in{V, nv, F, nf, ior, sigma, env, env_w, env_h, cam, width, height, max_depth, spp, jitter, seed,
-            view, t_min};
+            view, t_min, medium};
   auto cam_ray = [&](int p, int s, V3d& o, V3d& d) {
     double jx = 0.5, jy = 0.5;
     if (jitter) jitter_offset(seed, (uint32_t)view, (uint32_t)p, (uint32_t)s, jx, jy);
     camera_ray(cam, width, height, (p % width) + jx, (p / width) + jy, o, d);
   };
-  jvp_passes(in, width * height, spp, cam_ray, ntan, tV, tior, tsigma, img, dimg);
+  jvp_passes(in, width * height, spp, cam_ray, ntan, tV, tior, tsigma, tmu, img, dimg);
   return 0;
 }
 
@@ -784,13 +875,35 @@ int orc_render_jvp(const double* V, int nv, const int* F, int nf, double ior, co
 int orc_render_rays_jvp(const double* V, int nv, const int* F, int nf, double ior, const double* sigma,
                         const double* env, int env_w, int env_h, const double* o, const double* d, int n,
                         int max_depth, double t_min, int ntan, const double* tV, const double* tior,
-                        const double* tsigma, double* img, double* dimg) {
-  Inputs in{V, nv, F, nf, ior, sigma, env, env_w, env_h, nullptr, n, 1, max_depth, 1, 0, 0, 0, t_min};
+                        const double* tsigma, double* img, double* dimg, const orc_medium* medium,
+                        const double* tmu) {
+  Inputs in{V, nv, F, nf, ior, sigma, env, env_w, env_h, nullptr, n, 1, max_depth, 1, 0, 0, 0, t_min, medium};
   auto given = [&](int p, int, V3d& oo, V3d& dd) {
     oo = V3d(o[3 * p], o[3 * p + 1], o[3 * p + 2]);
     dd = V3d(d[3 * p], d[3 * p + 1], d[3 * p + 2]);
   };
-  jvp_passes(in, n, 1, given, ntan, tV, tior, tsigma, img, dimg);
+  jvp_passes(in, n, 1, given, ntan, tV, tior, tsigma, tmu, img, dimg);
+  return 0;
+}
+
+// Optical depth of the absorption grid over n segments o + s d, s in [0, t]
+// (o, d: [n][3], t: [n]); out: [n][3].  The quadrature of Eq. 11 the
+// renderer applies to interior segments.
+int orc_medium_depth(const orc_medium* medium, const double* o, const double* d, const double* t, int n,
+                     double* out) {
+  Scene<double> S;
+  if (medium && medium->mu) {
+    S.has_medium = true;
+    for (int a = 0; a < 3; ++a) { S.gn[a] = medium->n[a]; S.glo[a] = medium->lo[a]; S.ghi[a] = medium->hi[a]; }
+    S.gstep = medium->step;
+    const size_t nn = (size_t)medium->n[0] * medium->n[1] * medium->n[2] * 3;
+    S.gmu.assign(medium->mu, medium->mu + nn);
+  }
+  for (int r = 0; r < n; ++r) {
+    const V3d G = medium_depth(S, V3d(o[3 * r], o[3 * r + 1], o[3 * r + 2]), V3d(d[3 * r], d[3 * r + 1], d[3 * r + 2]),
+                               t[r]);
+    out[3 * r] = G.x; out[3 * r + 1] = G.y; out[3 * r + 2] = G.z;
+  }
   return 0;
 }
 

@@ -572,6 +572,43 @@ def constant_env(width: int, height: int, rgb=(1.0, 1.0, 1.0)) -> np.ndarray:
 
 
 # --------------------------------------------------------------------------
+# absorption grids (a spatially varying absorption rate inside the object)
+# --------------------------------------------------------------------------
+def grid_nodes(n, lo, hi):
+    """Node coordinates (X, Y, Z), each [nz, ny, nx], of a grid with n =
+    (nx, ny, nz) nodes spanning the box [lo, hi]."""
+    ax = [np.linspace(lo[a], hi[a], n[a]) for a in range(3)]
+    Z, Y, X = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+    return X, Y, Z
+
+
+def linear_absorption_grid(n, lo, hi, a, b, step: float) -> dict:
+    """Node values of the per-channel field a_c + b_c . x (a: [3], b: [3, 3]
+    with b[c] the gradient of channel c) on an (nx, ny, nz) grid over
+    [lo, hi].  float64 node values; dict(mu [nz, ny, nx, 3], lo, hi, step)."""
+    X, Y, Z = grid_nodes(n, lo, hi)
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    mu = np.stack([a[c] + b[c, 0] * X + b[c, 1] * Y + b[c, 2] * Z for c in range(3)], axis=-1)
+    return dict(mu=mu, lo=tuple(map(float, lo)), hi=tuple(map(float, hi)), step=float(step))
+
+
+def random_absorption_grid(n, lo, hi, seed: int, scale: float = 1.0, step: float = None) -> dict:
+    """Smooth non-negative random absorption rates on an (nx, ny, nz) grid
+    over [lo, hi]: value noise of two octaves per channel from the seed,
+    softplus, times scale.  float32 node values; step defaults to half the
+    smallest cell."""
+    rng = np.random.default_rng(seed)
+    X, Y, Z = grid_nodes(n, lo, hi)
+    mu = np.zeros(X.shape + (3,))
+    for c in range(3):
+        v = _value_noise_3d(rng, X, Y, Z, 2.0) + 0.5 * _value_noise_3d(rng, X, Y, Z, 4.0)
+        mu[..., c] = np.logaddexp(0.0, 2.0 * v - 0.5)
+    cell = min((hi[a] - lo[a]) / (n[a] - 1) for a in range(3))
+    return dict(mu=(scale * mu).astype(F32), lo=tuple(map(float, lo)), hi=tuple(map(float, hi)),
+                step=float(F32(0.5 * cell if step is None else step)))
+
+
+# --------------------------------------------------------------------------
 # the benchmark workloads
 # --------------------------------------------------------------------------
 @dataclasses.dataclass

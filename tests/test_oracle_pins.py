@@ -508,3 +508,134 @@ def test_zero_area_faces_add_nothing_to_vertex_normals():
     assert np.isfinite(n2).all()
     np.testing.assert_array_equal(n2[:m], base)
     np.testing.assert_array_equal(n2[m:], 0.0)
+
+
+# ---------------------------------------------------------------------------
+# Eq. 11 with a spatially varying absorption rate: a dense grid added to
+# sigma on interior segments (trilinear, clamped to its box; steps of length
+# h from the segment's start, the last one partial, sampled at midpoints)
+# ---------------------------------------------------------------------------
+def _segments_in_box(rng, n, lo, hi, t_max):
+    """Random segments that stay inside [lo, hi]: start and end points drawn
+    inside, t = their distance (capped at t_max by moving the end)."""
+    lo, hi = np.asarray(lo), np.asarray(hi)
+    a = lo + (hi - lo) * rng.uniform(0.05, 0.95, size=(n, 3))
+    b = lo + (hi - lo) * rng.uniform(0.05, 0.95, size=(n, 3))
+    d = _unit(b - a)
+    t = np.minimum(np.linalg.norm(b - a, axis=1), t_max)
+    return a, d, t
+
+
+def test_medium_depth_of_a_linear_field_is_its_integral():
+    """Trilinear interpolation reproduces a field linear in x exactly and the
+    midpoint rule integrates a linear function exactly, so the optical depth
+    is the closed form t (a + b . (o + d t / 2)) per channel, whatever the
+    step (full steps, a partial last step, or a segment shorter than h)."""
+    rng = np.random.default_rng(11)
+    lo, hi = (-1.0, -0.8, -1.2), (1.1, 0.9, 1.0)
+    a = np.array([0.3, 1.2, 0.05])
+    b = rng.normal(size=(3, 3))
+    for n, h in [((2, 2, 2), 0.1), ((5, 4, 6), 0.037), ((3, 7, 2), 1.5)]:
+        med = S.linear_absorption_grid(n, lo, hi, a, b, h)
+        o, d, t = _segments_in_box(rng, 200, lo, hi, 2.0)
+        got = O.medium_depth(med, o, d, t)
+        mid = o + d * (t / 2)[:, None]
+        want = t[:, None] * (a[None, :] + mid @ b.T)
+        np.testing.assert_allclose(got, want, rtol=1e-11, atol=1e-12)
+
+
+def test_medium_depth_midpoint_error_of_a_bilinear_field():
+    """mu = x y is reproduced exactly by trilinear interpolation; along a
+    segment from the origin it is (dx dy) s^2, for which the midpoint rule
+    over steps h_i errs by exactly -(dx dy) sum h_i^3 / 12.  With m full
+    steps of length h and a last one of length r = t - m h this pins the
+    step layout: t^3/3 - (m h^3 + r^3)/12, times dx dy."""
+    rng = np.random.default_rng(12)
+    lo, hi = (-2.0, -2.0, -2.0), (2.0, 2.0, 2.0)
+    X, Y, Z = S.grid_nodes((3, 3, 3), lo, hi)
+    mu = np.stack([X * Y, 2.0 * X * Y, -X * Y], axis=-1)
+    for h in (0.05, 0.13, 0.7):
+        med = dict(mu=mu, lo=lo, hi=hi, step=h)
+        d = _unit(rng.normal(size=(50, 3)))
+        t = rng.uniform(0.01, 1.9, size=50)
+        o = np.zeros((50, 3))
+        got = O.medium_depth(med, o, d, t)
+        m = np.floor(t / h)
+        r = t - m * h
+        base = d[:, 0] * d[:, 1] * (t ** 3 / 3.0 - (m * h ** 3 + r ** 3) / 12.0)
+        np.testing.assert_allclose(got, base[:, None] * np.array([1.0, 2.0, -1.0]), rtol=1e-10, atol=1e-13)
+
+
+def test_medium_is_clamped_to_its_box():
+    """Beyond the box each clamped coordinate sees the boundary value: a
+    field linear in x read past hi_x is the constant a + b hi_x."""
+    lo, hi = (-1.0, -1.0, -1.0), (1.0, 1.0, 1.0)
+    b = np.zeros((3, 3))
+    b[:, 0] = [0.5, 1.0, 2.0]
+    med = S.linear_absorption_grid((4, 3, 5), lo, hi, [0.1, 0.2, 0.3], b, 0.05)
+    o = np.array([[1.5, 0.2, -0.3], [3.0, -2.0, 5.0]])
+    d = _unit(np.array([[1.0, 0.3, 0.2], [0.2, -1.0, 0.1]]))
+    t = np.array([0.8, 1.3])
+    got = O.medium_depth(med, o, d, t)
+    want = t[:, None] * (np.array([0.1, 0.2, 0.3]) + b[:, 0] * 1.0)[None, :]
+    np.testing.assert_allclose(got, want, rtol=1e-12)
+
+
+def test_medium_depth_is_continuous_across_step_boundaries():
+    """The partial last step makes the sum continuous in t: just below and
+    just above a multiple of h it differs by O(epsilon)."""
+    med = S.random_absorption_grid((6, 5, 7), (-1.2, -1.2, -1.2), (1.2, 1.2, 1.2), seed=3)
+    med["mu"] = med["mu"].astype(np.float64)
+    h = med["step"]
+    o = np.array([[-0.5, 0.1, 0.2]] * 2)
+    d = _unit(np.array([[0.8, 0.3, -0.2]] * 2))
+    for k in (1, 3, 7):
+        eps = 1e-9
+        got = O.medium_depth(med, o, d, np.array([k * h - eps, k * h + eps]))
+        assert np.abs(got[1] - got[0]).max() < 1e-7
+
+
+def test_constant_medium_is_a_sigma_shift():
+    """A grid of constant node values c adds c t to the optical depth of
+    every interior segment: the render equals the one with sigma + c."""
+    sc = S.glass_icosphere_scene(width=12, height=10, max_depth=5)
+    cam = sc.cams[0]
+    sigma = np.array([0.2, 0.1, 0.4])
+    c = np.array([0.5, 0.05, 1.1])
+    mu = np.broadcast_to(c, (3, 4, 2, 3)).copy()
+    med = dict(mu=mu, lo=(-1.5, -1.5, -1.5), hi=(1.5, 1.5, 1.5), step=0.07)
+    a = O.render(sc.V, sc.F, 1.5, sigma, sc.env, cam, 5, medium=med)
+    b = O.render(sc.V, sc.F, 1.5, sigma + c, sc.env, cam, 5)
+    np.testing.assert_allclose(a["img"], b["img"], rtol=1e-11, atol=1e-14)
+    assert a["counters"] == b["counters"]
+
+
+def test_medium_jvp_matches_central_differences():
+    """Forward-mode derivatives with respect to the grid's node values (and
+    the vertices, whose moves change every interior segment's length and
+    sample positions) against central differences of the FP64 render."""
+    sc = S.glass_icosphere_scene(width=8, height=8, max_depth=4)
+    cam = sc.cams[0]
+    sigma = np.array([0.1, 0.2, 0.3])
+    med = S.random_absorption_grid((4, 5, 3), (-1.1, -1.1, -1.1), (1.1, 1.1, 1.1), seed=7, scale=0.8)
+    med["mu"] = med["mu"].astype(np.float64)
+    rng = np.random.default_rng(13)
+    tmu = rng.normal(size=(1,) + med["mu"].shape)
+    tV = 0.01 * rng.normal(size=(1,) + sc.V.shape)
+    V = sc.V.astype(np.float64)
+    _, dm = O.render_jvp(V, sc.F, 1.5, sigma, sc.env, cam, 4, medium=med, tmu=tmu)
+    _, dv = O.render_jvp(V, sc.F, 1.5, sigma, sc.env, cam, 4, tV=tV, medium=med)
+    eps = 1e-6
+
+    def img(mu=None, VV=V):
+        m = dict(med, mu=med["mu"] if mu is None else mu)
+        return O.render(VV, sc.F, 1.5, sigma, sc.env, cam, 4, medium=m)["img"]
+
+    fd_m = (img(med["mu"] + eps * tmu[0]) - img(med["mu"] - eps * tmu[0])) / (2 * eps)
+    fd_v = (img(VV=V + eps * tV[0]) - img(VV=V - eps * tV[0])) / (2 * eps)
+    np.testing.assert_allclose(dm[0], fd_m, rtol=1e-5, atol=1e-8)
+    # a vertex move can shift a sample across a cell face (where the
+    # trilinear gradient jumps) only on a set of measure zero; compare
+    # pixelwise with a small absolute floor
+    np.testing.assert_allclose(dv[0], fd_v, rtol=1e-4, atol=1e-6)
+    assert np.abs(dm[0]).max() > 1e-3 and np.abs(dv[0]).max() > 1e-3
