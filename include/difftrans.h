@@ -122,6 +122,27 @@ dt_status dt_refit_bvh(const float* d_V, int32_t nv, const int32_t* d_F, int32_t
 /* ------------------------------------------------------------------------
  * Scene, views and parameters of a render.
  * ------------------------------------------------------------------------ */
+/* Spatially varying absorption (Eq. 11 with mu_t(x) = sigma + G(x)): G is a
+ * dense grid of per-channel rates at the nodes of an nx x ny x nz lattice
+ * spanning the box [lo, hi] (node (i, j, k) at lo + (i, j, k) (hi - lo) /
+ * (n - 1)), read with trilinear interpolation at positions clamped to the
+ * box.  On an interior segment (where sigma applies) of length t the
+ * optical depth sigma t gains the sum of G over steps of length `step` from
+ * the segment's start: m = floor(t / step) full steps (at most 8192) and a
+ * last one of length t - m step, each sampled at its midpoint and weighted
+ * by its length.
+ *  d_mu: float[nz][ny][nx][4], 16-byte aligned (the 4th float is unused);
+ *  d_grad_mu: where dt_render_backward writes dLoss/d(node values), same
+ *    layout (overwritten; NULL: not computed).
+ * nx, ny, nz >= 2; hi > lo on every axis; step > 0. */
+typedef struct dt_medium {
+  const float* d_mu;
+  float* d_grad_mu;
+  int32_t nx, ny, nz;
+  float lo[3], hi[3];
+  float step;
+} dt_medium;
+
 typedef struct dt_scene {
   const float* d_V;     /* float[nv][3] vertex positions */
   const int32_t* d_F;   /* int32[nf][3] */
@@ -132,6 +153,7 @@ typedef struct dt_scene {
   const float* d_sigma; /* float[3]: absorption rate per channel inside the object */
   const float* d_env;   /* float[env_h][env_w][3] environment */
   int32_t env_w, env_h;
+  const dt_medium* medium; /* NULL: the constant sigma only */
 } dt_scene;
 
 /* n_views pinhole cameras sharing one image size.  d_cams float[n_views][10]

@@ -48,10 +48,15 @@ class DiffTransError(RuntimeError):
         self.code = code
 
 
+class DtMedium(ctypes.Structure):
+    _fields_ = [("d_mu", c_void_p), ("d_grad_mu", c_void_p), ("nx", c_int32), ("ny", c_int32), ("nz", c_int32),
+                ("lo", ctypes.c_float * 3), ("hi", ctypes.c_float * 3), ("step", ctypes.c_float)]
+
+
 class DtScene(ctypes.Structure):
     _fields_ = [("d_V", c_void_p), ("d_F", c_void_p), ("nv", c_int32), ("nf", c_int32), ("d_bvh", c_void_p),
                 ("d_N", c_void_p), ("d_ior", c_void_p), ("d_sigma", c_void_p), ("d_env", c_void_p),
-                ("env_w", c_int32), ("env_h", c_int32)]
+                ("env_w", c_int32), ("env_h", c_int32), ("medium", ctypes.POINTER(DtMedium))]
 
 
 class DtViews(ctypes.Structure):
@@ -332,7 +337,41 @@ class Workspace:
         self._raw, self.buf = _aligned_empty(self.bytes, device)
 
 
-def _scene_struct(V, F, bvh, N, ior, sigma, env):
+class Medium:
+    """Spatially varying absorption (Eq. 11 with mu_t(x) = sigma + G(x)): a
+    grid of per-channel rates at the nodes of a lattice over the box [lo,
+    hi], trilinear, positions clamped to the box; interior segments add the
+    sum of G over steps of length `step` (the last one partial), each
+    sampled at its midpoint.  mu: float32 device tensor [nz, ny, nx, 3] or
+    [nz, ny, nx, 4] (stored with a 4th unused channel)."""
+
+    def __init__(self, mu, lo, hi, step: float):
+        if mu.dim() != 4 or mu.shape[3] not in (3, 4) or min(mu.shape[:3]) < 2:
+            raise ValueError("mu must be [nz, ny, nx, 3 or 4] with at least 2 nodes per axis")
+        if mu.shape[3] == 3:
+            mu = torch.cat([mu, torch.zeros_like(mu[..., :1])], dim=3)
+        self.mu = _need(mu.contiguous(), torch.float32, (4,), "mu")
+        self.lo = tuple(float(x) for x in lo)
+        self.hi = tuple(float(x) for x in hi)
+        self.step = float(step)
+
+    @property
+    def shape(self):
+        return tuple(self.mu.shape[:3])
+
+    def struct(self, grad=None) -> DtMedium:
+        m = DtMedium()
+        m.d_mu = self.mu.data_ptr()
+        m.d_grad_mu = grad.data_ptr() if grad is not None else None
+        m.nz, m.ny, m.nx = self.mu.shape[0], self.mu.shape[1], self.mu.shape[2]
+        for a in range(3):
+            m.lo[a] = self.lo[a]
+            m.hi[a] = self.hi[a]
+        m.step = self.step
+        return m
+
+
+def _scene_struct(V, F, bvh, N, ior, sigma, env, medium_c=None):
     _need(V, torch.float32, (3,), "V")
     _need(F, torch.int32, (3,), "F")
     _need(N, torch.float32, (3,), "N")
@@ -341,8 +380,11 @@ def _scene_struct(V, F, bvh, N, ior, sigma, env):
     _need(sigma, torch.float32, None, "sigma")
     if ior.numel() != 1 or sigma.numel() != 3:
         raise ValueError("ior needs 1 element and sigma 3")
-    return DtScene(V.data_ptr(), F.data_ptr(), V.shape[0], F.shape[0], bvh.buf.data_ptr(), N.data_ptr(),
-                   ior.data_ptr(), sigma.data_ptr(), env.data_ptr(), env.shape[1], env.shape[0])
+    sc = DtScene(V.data_ptr(), F.data_ptr(), V.shape[0], F.shape[0], bvh.buf.data_ptr(), N.data_ptr(),
+                 ior.data_ptr(), sigma.data_ptr(), env.data_ptr(), env.shape[1], env.shape[0])
+    if medium_c is not None:
+        sc.medium = ctypes.pointer(medium_c)
+    return sc
 
 
 def _views_struct(cams, width, height):
@@ -360,10 +402,11 @@ class Tape:
     """Everything dt_render_backward needs from a forward call (params_c:
     the dt_params the forward ran with)."""
 
-    def __init__(self, ws, scene_args, cams, width, height, params, stats, params_c=None):
+    def __init__(self, ws, scene_args, cams, width, height, params, stats, params_c=None, medium=None):
         self.ws, self.scene_args, self.cams = ws, scene_args, cams
         self.width, self.height, self.params, self.stats = width, height, params, stats
         self.params_c = params_c if params_c is not None else params.c()
+        self.medium = medium
 
 
 def default_capacity(n_primary: int, max_depth: int) -> int:
@@ -401,8 +444,9 @@ def _effective_params(params: Params, ws: Workspace):
 
 
 def render(V, F, bvh: Bvh, N, ior, sigma, env, cams, width: int, height: int, params: Params, ws: Workspace = None,
-           out=None, stream=None, check: bool = True):
-    """Forward render (Sec. 3.4 steps 1-5) of cams.shape[0] views.
+           out=None, stream=None, check: bool = True, medium: Medium = None):
+    """Forward render (Sec. 3.4 steps 1-5) of cams.shape[0] views; medium:
+    an absorption grid added to sigma on interior segments.
 
     Returns (image [n_views, height, width, 3], Tape).  With check=True the
     device status is read back (one synchronisation) and an arena overflow is
@@ -414,26 +458,28 @@ def render(V, F, bvh: Bvh, N, ior, sigma, env, cams, width: int, height: int, pa
         ws = _new_workspace(params, n0, V.device)
     if out is None:
         out = torch.empty(n_views, height, width, 3, dtype=torch.float32, device=V.device)
-    sc = _scene_struct(V, F, bvh, N, ior, sigma, env)
+    mc = medium.struct() if medium is not None else None
+    sc = _scene_struct(V, F, bvh, N, ior, sigma, env, mc)
     vw = _views_struct(cams, width, height)
     while True:
         pc = _effective_params(params, ws)
         _check(lib.dt_render(ctypes.byref(sc), ctypes.byref(vw), ctypes.byref(pc), _ptr(out), _ptr(ws.buf),
                              ws.bytes, _stream(stream)))
         if not check:
-            return out, Tape(ws, (V, F, bvh, N, ior, sigma, env), cams, width, height, params, None, pc)
+            return out, Tape(ws, (V, F, bvh, N, ior, sigma, env), cams, width, height, params, None, pc, medium)
         stats = read_stats(ws, stream)
         if stats["status"] == DT_ERR_QUEUE_OVERFLOW:
             ws = _grow_workspace(ws, params, stats, V.device)
             continue
         if stats["status"] != DT_OK:
             raise DiffTransError(stats["status"], "device-side error during render")
-        return out, Tape(ws, (V, F, bvh, N, ior, sigma, env), cams, width, height, params, stats, pc)
+        return out, Tape(ws, (V, F, bvh, N, ior, sigma, env), cams, width, height, params, stats, pc, medium)
 
 
 def render_backward(tape: Tape, grad_out, stream=None, bws=None):
     """Gradient of sum(grad_out * image) w.r.t. (V, ior, sigma) at the
-    forward's fixed events.  Returns (dV [nv,3], dior [1], dsigma [3])."""
+    forward's fixed events.  Returns (dV [nv,3], dior [1], dsigma [3]), and
+    with an absorption grid also dmu [nz, ny, nx, 3]."""
     lib = load_library()
     V, F, bvh, N, ior, sigma, env = tape.scene_args
     stats = tape.stats if tape.stats is not None else read_stats(tape.ws, stream)
@@ -447,12 +493,17 @@ def render_backward(tape: Tape, grad_out, stream=None, bws=None):
     dV = torch.empty_like(V)
     dior = torch.empty(1, dtype=torch.float32, device=V.device)
     dsig = torch.empty(3, dtype=torch.float32, device=V.device)
-    sc = _scene_struct(V, F, bvh, N, ior, sigma, env)
+    med = tape.medium
+    dmu = torch.empty_like(med.mu) if med is not None else None
+    mc = med.struct(dmu) if med is not None else None
+    sc = _scene_struct(V, F, bvh, N, ior, sigma, env, mc)
     vw = _views_struct(tape.cams, tape.width, tape.height)
     pc = tape.params_c
     _check(lib.dt_render_backward(ctypes.byref(sc), ctypes.byref(vw), ctypes.byref(pc), _ptr(tape.ws.buf),
                                   tape.ws.bytes, _ptr(grad_out), _ptr(dV), _ptr(dior), _ptr(dsig), _ptr(bws),
                                   bws.numel(), max_level, _stream(stream)))
+    if med is not None:
+        return dV, dior, dsig, dmu[..., :3]
     return dV, dior, dsig
 
 
@@ -531,19 +582,23 @@ class BatchItem:
     """One scene of a batched render: geometry, materials, environment, views
     and parameters, with its own output image."""
 
-    def __init__(self, V, F, bvh: Bvh, N, ior, sigma, env, cams, width: int, height: int, params: Params):
+    def __init__(self, V, F, bvh: Bvh, N, ior, sigma, env, cams, width: int, height: int, params: Params,
+                 medium: Medium = None):
         self.V, self.F, self.bvh, self.N = V, F, bvh, N
         self.ior, self.sigma, self.env, self.cams = ior, sigma, env, cams
         self.width, self.height, self.params = int(width), int(height), params
+        self.medium = medium
         self.out = None
 
     @property
     def n_primary(self):
         return self.cams.shape[0] * self.width * self.height * self.params.spp
 
-    def entry(self, out=None, grad_out=None, dV=None, dior=None, dsig=None, level_capacity: int = 0):
+    def entry(self, out=None, grad_out=None, dV=None, dior=None, dsig=None, level_capacity: int = 0, dmu=None):
         e = DtBatchEntry()
-        e.scene = _scene_struct(self.V, self.F, self.bvh, self.N, self.ior, self.sigma, self.env)
+        # the medium struct must outlive the call: keep it on the item
+        self._medium_c = self.medium.struct(dmu) if self.medium is not None else None
+        e.scene = _scene_struct(self.V, self.F, self.bvh, self.N, self.ior, self.sigma, self.env, self._medium_c)
         e.views = _views_struct(self.cams, self.width, self.height)
         e.params = self.params.c(level_capacity)
         e.d_out = out.data_ptr() if out is not None else None
@@ -601,7 +656,8 @@ def batch_backward_workspace_size(items, max_level: int) -> int:
 
 def render_batch_backward(tape: BatchTape, grads, bws=None, outs=None, stream=None):
     """Gradients of sum_i sum(grads[i] * image_i) for every scene of the
-    batch: list of (dV, dior, dsigma)."""
+    batch: list of (dV, dior, dsigma), with dmu [nz, ny, nx, 3] appended for
+    an item with an absorption grid."""
     lib = load_library()
     items = tape.items
     stats = tape.stats if tape.stats is not None else read_stats(tape.ws, stream)
@@ -614,13 +670,14 @@ def render_batch_backward(tape: BatchTape, grads, bws=None, outs=None, stream=No
         _, bws = _aligned_empty(nbytes, dev)
     if outs is None:
         outs = [(torch.empty_like(it.V), torch.empty(1, device=dev), torch.empty(3, device=dev)) for it in items]
+    dmus = [torch.empty_like(it.medium.mu) if it.medium is not None else None for it in items]
     grads = [_need(g.contiguous(), torch.float32, (3,), "grad") for g in grads]
     arr = (DtBatchEntry * len(items))(*[it.entry(grad_out=g, dV=o[0], dior=o[1], dsig=o[2],
-                                                 level_capacity=tape.ws.level_capacity)
-                                        for it, g, o in zip(items, grads, outs)])
+                                                 level_capacity=tape.ws.level_capacity, dmu=m)
+                                        for it, g, o, m in zip(items, grads, outs, dmus)])
     _check(lib.dt_render_batch_backward(arr, len(items), _ptr(tape.ws.buf), tape.ws.bytes, _ptr(bws), bws.numel(),
                                         max_level, _stream(stream)))
-    return outs
+    return [tuple(o) + ((m[..., :3],) if m is not None else ()) for o, m in zip(outs, dmus)]
 
 
 # ---------------------------------------------------------------------------

@@ -13,6 +13,7 @@
 #include <stdint.h>
 
 #include "dt_internal.cuh"
+#include "dt_medium.cuh"
 #include "dt_shade.cuh"
 
 namespace dt {
@@ -86,10 +87,11 @@ struct SceneSums {
 // out_cur: the same for level k (not written for k = 0: camera rays have no
 // parent); see AdjRecords.
 // kBatch = false: one scene, whose entry E0 arrives as a kernel parameter;
-// true: each segment looks its scene up.
+// true: each segment looks its scene up.  kGrid: some scene has an
+// absorption grid (dt_medium.cuh), whose optical depth interior segments add.
 constexpr int kAdjointMinBlocks = 4;  // CTAs of 256 per SM the register budget is sized for
 
-template <bool kBatch>
+template <bool kBatch, bool kGrid>
 __global__ void __launch_bounds__(256, kAdjointMinBlocks) k_adjoint(WsView W, int k, const AdjRecords out_next,
                                                                    const AdjRecords out_cur, const SceneEntry E0) {
   extern __shared__ float sums_smem[];
@@ -149,6 +151,8 @@ __global__ void __launch_bounds__(256, kAdjointMinBlocks) k_adjoint(WsView W, in
         const bool tir = (fl & SF_TIR) != 0;
         HitShade h;
         shade_hit(o, d, t, b1, b2, v0, v1, v2, N0, N1, N2, ior, sigma, h, tir ? 1 : 0);
+        const bool med = kGrid && E.mu && !h.entering;
+        if (med) h.A = absorption_with_depth(sigma, t, medium_depth(medium_view(E), o, d, t));
         // children: reflected at ch, refracted at ch + (flags >> kRefractShift)
         float3 Lr = mk(0.f, 0.f, 0.f), orb = Lr, drb = Lr, Lt = Lr, otb = Lr, dtb = Lr;
         const uint32_t jr = (uint32_t)ch - next_start;
@@ -167,10 +171,15 @@ __global__ void __launch_bounds__(256, kAdjointMinBlocks) k_adjoint(WsView W, in
         const float3 gA = mul(gbar, h.A);
         const float Rbar = dot(gA, Lr), Tbar = dot(gA, Lt);
         float tbar = 0.f;
-        if (!h.entering) {  // A_c = exp(-sigma_c t)
+        float3 sbar = mk(0.f, 0.f, 0.f);  // dJ/dS of the grid's optical depth
+        if (!h.entering) {  // A_c = exp(-sigma_c t - S_c)
           const float3 aa = mul(Abar, h.A);
           acc_sig = acc_sig + aa * (-t);
           tbar -= dot(aa, sigma);
+          if (med) {
+            sbar = -aa;
+            tbar += dot(sbar, medium_depth_dt(medium_view(E), o, d, t));
+          }
         }
         float cbar = 0.f, etabar = 0.f, eta1bar = 0.f, eta2bar = 0.f;
         float3 nsbar = mk(0.f, 0.f, 0.f), wibar = nsbar;
@@ -246,6 +255,9 @@ __global__ void __launch_bounds__(256, kAdjointMinBlocks) k_adjoint(WsView W, in
         atomic_add4(dV4 + i0, lam * (-b0));
         atomic_add4(dV4 + i1, lam * (-b1));
         atomic_add4(dV4 + i2, lam * (-b2));
+        // the grid's samples move with o and d at fixed t (the t dependence
+        // went into tbar above)
+        if (med) medium_backward(medium_view(E), E.dmu, o, d, t, sbar, obar, dbar);
       }
     }
     if (k > 0) {
@@ -262,13 +274,19 @@ __global__ void __launch_bounds__(256, kAdjointMinBlocks) k_adjoint(WsView W, in
   }
 }
 
-// zero every scene's accumulators, dIoR and dsigma (blockIdx.y = scene)
+// zero every scene's accumulators, dIoR, dsigma and absorption-grid
+// gradient (blockIdx.y = scene)
 __global__ void k_zero_grads(const SceneEntry* __restrict__ ent) {
   const SceneEntry& E = ent[blockIdx.y];
   const size_t n = 2 * (size_t)E.nv;
   float4* acc = acc_dN4(E);
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (E.mu && E.dmu) {
+    const size_t nn = (size_t)E.gnx * E.gny * E.gnz;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nn; i += (size_t)gridDim.x * blockDim.x)
+      E.dmu[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
   if (blockIdx.x == 0 && threadIdx.x < 4) {
     if (threadIdx.x == 0) E.dior[0] = 0.f;
     else E.dsigma[threadIdx.x - 1] = 0.f;
@@ -361,8 +379,14 @@ void launch_backward_table(const TableHeader& th, const SceneEntry* entries, con
   const size_t smem = sizeof(float) * 4 * (size_t)n;
   for (int k = th.max_depth; k >= 0; --k) {
     ProfScope ps("k_adjoint", s);
-    if (n > 1) k_adjoint<true><<<blocks, 256, smem, s>>>(W, k, buf[(k + 1) & 1], buf[k & 1], entries[0]);
-    else k_adjoint<false><<<blocks, 256, smem, s>>>(W, k, buf[(k + 1) & 1], buf[k & 1], entries[0]);
+    const AdjRecords nx = buf[(k + 1) & 1], cu = buf[k & 1];
+    if (th.any_medium) {
+      if (n > 1) k_adjoint<true, true><<<blocks, 256, smem, s>>>(W, k, nx, cu, entries[0]);
+      else k_adjoint<false, true><<<blocks, 256, smem, s>>>(W, k, nx, cu, entries[0]);
+    } else {
+      if (n > 1) k_adjoint<true, false><<<blocks, 256, smem, s>>>(W, k, nx, cu, entries[0]);
+      else k_adjoint<false, false><<<blocks, 256, smem, s>>>(W, k, nx, cu, entries[0]);
+    }
   }
   int fb = (max_nf + 255) / 256;
   if (fb > cap_blocks) fb = cap_blocks;

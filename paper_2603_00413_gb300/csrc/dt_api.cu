@@ -7,6 +7,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <cmath>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -137,6 +138,18 @@ static dt_status check_scene(const dt_scene* sc) {
                                                  sc->nv, sc->nf);
   if (sc->env_w < 1 || sc->env_h < 1) return set_error(DT_ERR_INVALID_ARG, "environment size must be positive");
   if (!aligned(sc->d_bvh, 256)) return set_error(DT_ERR_INVALID_ARG, "BVH buffer must be 256-byte aligned");
+  if (sc->medium) {
+    const dt_medium& M = *sc->medium;
+    if (!M.d_mu || !aligned(M.d_mu, 16) || (M.d_grad_mu && !aligned(M.d_grad_mu, 16)))
+      return set_error(DT_ERR_INVALID_ARG, "medium node values (and gradient) need 16-byte aligned device pointers");
+    if (M.nx < 2 || M.ny < 2 || M.nz < 2 || (long long)M.nx * M.ny * M.nz > (1ll << 31))
+      return set_error(DT_ERR_INVALID_ARG, "medium needs at least 2 nodes per axis (got %d x %d x %d)", M.nx, M.ny,
+                       M.nz);
+    for (int a = 0; a < 3; ++a)
+      if (!(M.hi[a] > M.lo[a]) || !std::isfinite(M.hi[a] - M.lo[a]))
+        return set_error(DT_ERR_INVALID_ARG, "medium box needs hi > lo on every axis");
+    if (!(M.step > 0.0f) || !std::isfinite(M.step)) return set_error(DT_ERR_INVALID_ARG, "medium step must be > 0");
+  }
   return DT_OK;
 }
 

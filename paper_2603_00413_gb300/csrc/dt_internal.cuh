@@ -198,11 +198,22 @@ struct SceneEntry {
   int32_t max_depth, jitter, max_iter, pad0;
   float t_min;
   uint32_t sample_start, face_start, pix_count;
+  // absorption grid (dt_medium; mu == nullptr: none): node values, their
+  // gradient (backward, may be nullptr), node counts, box origin, nodes per
+  // unit length minus the fencepost ((n - 1) / (hi - lo)), step length
+  const float4* mu;
+  float4* dmu;
+  int32_t gnx, gny, gnz;
+  float glo_x, glo_y, glo_z;
+  float gscale_x, gscale_y, gscale_z;
+  float gstep;
 };
 
 struct TableHeader {
   int32_t n;
   int32_t max_depth;
+  int32_t any_medium;  // some scene of the table has an absorption grid
+  int32_t pad0;
   uint32_t n_samples;
   uint32_t n_faces;
   uint32_t starts[kMaxBatch + 1];

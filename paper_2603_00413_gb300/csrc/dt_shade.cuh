@@ -88,7 +88,7 @@ struct HitShade {
   float kappa, sk, cos_t;
   float as_, bs_, rs, ap_, bp_, rp;
   float R, T;         // Eqs. 7-8
-  float3 A;           // absorption over this segment (Eq. 11, constant sigma)
+  float3 A;           // absorption over this segment (Eq. 11)
   bool entering, backfacing, tir;
 };
 
@@ -143,6 +143,12 @@ __device__ __forceinline__ void shade_hit(float3 o, float3 d, float t, float b1,
   } else {                                             // Sec. 3.4 step 5
     h.A = mk(expf(-sigma.x * t), expf(-sigma.y * t), expf(-sigma.z * t));
   }
+}
+
+// Absorption of an interior segment whose optical depth sigma t gains the
+// depth S of an absorption grid (Eq. 11 with a spatially varying rate).
+__device__ __forceinline__ float3 absorption_with_depth(float3 sigma, float t, float3 S) {
+  return mk(expf(-(sigma.x * t + S.x)), expf(-(sigma.y * t + S.y)), expf(-(sigma.z * t + S.z)));
 }
 
 // Backward of Eq. 13 for face f.  Its unit normal u = c/|c|, c = e1 x e2,

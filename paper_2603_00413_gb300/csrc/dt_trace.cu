@@ -10,6 +10,7 @@
 
 #include "dt_internal.cuh"
 #include "dt_shade.cuh"
+#include "dt_medium.cuh"
 
 namespace dt {
 
@@ -480,8 +481,9 @@ constexpr int kShadeMinBlocks = 4;  // CTAs per SM the register budget is sized 
 
 // order_bits != 0: each child is also counted in its traversal-order
 // bucket (order_bucket of ray_order_key with that many bits; dt_order.cu)
-// and its bucket and rank are stored with the next level.
-template <bool kBatch>
+// and its bucket is stored with the next level.  kGrid: some scene has an
+// absorption grid, whose optical depth interior segments add (dt_medium.cuh).
+template <bool kBatch, bool kGrid>
 __global__ void __launch_bounds__(kShadeThreads, kShadeMinBlocks) k_shade(WsView W, int k, const SceneEntry E0,
                                                                          int order_bits) {
   WsHeader* H = W.hdr;
@@ -545,6 +547,8 @@ __global__ void __launch_bounds__(kShadeThreads, kShadeMinBlocks) k_shade(WsView
           HitShade h;
           shade_hit(xyz(ro), d, hh.x, hh.y, hh.z, v0, v1, v2, load3(E.N + 3 * i0), load3(E.N + 3 * i1),
                     load3(E.N + 3 * i2), ior, sigma, h);
+          if (kGrid && E.mu && !h.entering)  // Sec. 3.4 step 5 with the grid's optical depth
+            h.A = absorption_with_depth(sigma, hh.x, medium_depth(medium_view(E), xyz(ro), d, hh.x));
           fl = h.entering ? 0u : SF_INSIDE;
           if (h.backfacing) {
             fl |= SF_BACKFACING;
@@ -757,8 +761,13 @@ void launch_forward_table(const TableHeader& th, const SceneEntry* entries, void
       const int bits = k < th.max_depth ? order_bits : 0;
       if (bits) launch_order_clear(W, bits, s);
       ProfScope ps("k_shade", s);
-      if (batch) k_shade<true><<<shade_blocks(), kShadeThreads, 0, s>>>(W, k, E0, bits);
-      else k_shade<false><<<shade_blocks(), kShadeThreads, 0, s>>>(W, k, E0, bits);
+      if (th.any_medium) {
+        if (batch) k_shade<true, true><<<shade_blocks(), kShadeThreads, 0, s>>>(W, k, E0, bits);
+        else k_shade<false, true><<<shade_blocks(), kShadeThreads, 0, s>>>(W, k, E0, bits);
+      } else {
+        if (batch) k_shade<true, false><<<shade_blocks(), kShadeThreads, 0, s>>>(W, k, E0, bits);
+        else k_shade<false, false><<<shade_blocks(), kShadeThreads, 0, s>>>(W, k, E0, bits);
+      }
     }
   }
 }
@@ -777,6 +786,17 @@ SceneEntry make_entry(const dt_scene& sc, const dt_views& vw, const dt_params& p
   e.max_depth = p.max_depth; e.jitter = p.jitter; e.max_iter = traversal_limit(sc.nf);
   e.t_min = p.t_min;
   e.pix_count = (uint32_t)vw.n_views * (uint32_t)vw.width * (uint32_t)vw.height;
+  if (sc.medium && sc.medium->d_mu) {
+    const dt_medium& M = *sc.medium;
+    e.mu = reinterpret_cast<const float4*>(M.d_mu);
+    e.dmu = reinterpret_cast<float4*>(M.d_grad_mu);
+    e.gnx = M.nx; e.gny = M.ny; e.gnz = M.nz;
+    e.glo_x = M.lo[0]; e.glo_y = M.lo[1]; e.glo_z = M.lo[2];
+    e.gscale_x = (float)(M.nx - 1) / (M.hi[0] - M.lo[0]);
+    e.gscale_y = (float)(M.ny - 1) / (M.hi[1] - M.lo[1]);
+    e.gscale_z = (float)(M.nz - 1) / (M.hi[2] - M.lo[2]);
+    e.gstep = M.step;
+  }
   return e;
 }
 
@@ -794,6 +814,7 @@ void finish_table(SceneEntry* entries, int n, TableHeader& th) {
     s += entries[i].pix_count * (uint32_t)entries[i].spp;
     f += (uint32_t)entries[i].nf;
     if (entries[i].max_depth > md) md = entries[i].max_depth;
+    if (entries[i].mu) th.any_medium = 1;
   }
   th.starts[n] = s;
   th.face_starts[n] = f;
