@@ -69,6 +69,10 @@ def parse():
     ap.add_argument("--large-grid", type=int, default=240)
     ap.add_argument("--large-res", type=int, default=800)
     ap.add_argument("--large-steps", type=int, default=5)
+    ap.add_argument("--no-medium", action="store_true", help="skip the spatially varying absorption leg")
+    ap.add_argument("--medium-grid", type=int, default=64, help="nodes per axis of the absorption grid")
+    ap.add_argument("--medium-views", type=int, default=100)
+    ap.add_argument("--medium-steps", type=int, default=5)
     return ap.parse_args()
 
 
@@ -391,6 +395,81 @@ def large_leg(args, dt, dev):
                                                   / args.large_steps),
                      "levels": stats["level_count"], "loss": float(loss.item())}
         del ws, bws, tape, img, target, grad
+        torch.cuda.empty_cache()
+    return out
+
+
+def medium_leg(args, dt, dev):
+    """The bench workload (genus-2 mesh, n views 512x512, depth 8, the same
+    IoR and sigma) with a spatially varying absorption rate on top of sigma
+    (Eq. 11): a grid^3 lattice of smooth random rates over [-1.25, 1.25]^3,
+    trilinear, sampled every half cell along interior segments.  One step =
+    normals + refit + forward + backward seeded by a fixed random image
+    gradient, with the node-value gradient; the same step without the grid
+    is timed beside it."""
+    import torch
+    from paper_2603_00413_gb300 import scenes as S
+    sc, _ = genus2_workload(args.medium_views, args.res, args.depth)
+    V = torch.from_numpy(sc.V).to(dev)
+    F = torch.from_numpy(sc.F).to(dev)
+    ior = torch.tensor([sc.ior], device=dev)
+    sigma = torch.from_numpy(sc.sigma).to(dev)
+    env = torch.from_numpy(sc.env).to(dev)
+    cams = torch.from_numpy(np.stack([c.as_array() for c in sc.cams])).to(dev)
+    g = args.medium_grid
+    lo, hi = (-1.25, -1.25, -1.25), (1.25, 1.25, 1.25)
+    med = S.random_absorption_grid((g, g, g), lo, hi, seed=6, scale=1.0)
+    medium = dt.Medium(torch.from_numpy(med["mu"]).to(dev), lo, hi, med["step"])
+    bvh = dt.build_bvh(V, F)
+    N = dt.vertex_normals(V, F)
+    params = dt.Params(args.depth)
+    res = args.res
+    stream = torch.cuda.current_stream()
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(7)
+    out = {"workload": f"genus-2 two-tori mesh ({sc.F.shape[0]} triangles), {args.medium_views} views {res}x{res}, "
+                       f"depth {args.depth}, IoR {sc.ior:.4f}, sigma {tuple(round(float(x), 4) for x in sc.sigma)} "
+                       f"plus a {g}^3 grid of smooth random absorption rates over [-1.25, 1.25]^3 sampled every "
+                       f"{med['step']:.4f} (half a cell) along interior segments; fwd+bwd with a fixed image gradient",
+           "grid_nodes": g ** 3, "step": med["step"]}
+    for mode in ("medium", "sigma_only"):
+        m = medium if mode == "medium" else None
+        img, tape = dt.render(V, F, bvh, N, ior, sigma, env, cams, res, res, params, medium=m)
+        stats = tape.stats
+        _, bws = dt._aligned_empty(dt.backward_workspace_size(stats["max_level"], V.shape[0]), dev)
+        grad = torch.randn(img.shape, device=dev, generator=gen)
+
+        def step():
+            dt.vertex_normals(V, F, out=N)
+            bvh.refit(V, F)
+            _, tp = dt.render(V, F, bvh, N, ior, sigma, env, cams, res, res, params, ws=tape.ws, out=img,
+                              check=False, medium=m)
+            tp.stats = stats
+            return dt.render_backward(tp, grad, bws=bws)
+
+        for _ in range(3):
+            step()
+        torch.cuda.synchronize()
+        dt.profile_read()
+        dt.profile_enable(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.medium_steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dt.profile_enable(False)
+        prof = dt.profile_read()
+        ms = e0.elapsed_time(e1) / args.medium_steps
+        chk = dt.read_stats(tape.ws)
+        assert chk["status"] == dt.DT_OK and chk["segments"] == stats["segments"], chk
+        tot = sum(v[1] for v in prof.values())
+        out[mode] = {"ms_per_step": ms, "segments_per_step": int(stats["segments"]),
+                     "segments_per_s": stats["segments"] / (ms / 1e3),
+                     "grid_samples_per_step": int(stats["medium_samples"]),
+                     "kernel_ms": {k: round(v[1] / args.medium_steps, 3) for k, v in prof.items()},
+                     "kernel_share": {k: round(v[1] / tot, 4) for k, v in prof.items()}}
+        del tape, bws, img, grad
         torch.cuda.empty_cache()
     return out
 
@@ -735,6 +814,12 @@ def run_ours(args):
             large = large_leg(args, dt, dev)
         large["clocks"] = clk_large.summary()
 
+    medium = None
+    if rank == 0 and world == 1 and not args.no_medium:
+        with ClockSampler(dev.index or 0) as clk_med:
+            medium = medium_leg(args, dt, dev)
+        medium["clocks"] = clk_med.summary()
+
     batch = serving = None
     if rank == 0 and world == 1 and not args.no_batch:
         del ws, bws, tape
@@ -762,6 +847,7 @@ def run_ours(args):
             "batch": batch,
             "serve": serving,
             "large": large,
+            "medium": medium,
             "levels": stats["level_count"],
             "nodes_per_segment": stats["nodes_visited"] / seg,
             "tris_per_segment": stats["tris_tested"] / seg,

@@ -247,6 +247,7 @@ typedef struct dt_stats {
   int64_t tris_tested;         /* ray/triangle tests */
   int64_t max_level;           /* largest level_count */
   int64_t level_needed;        /* largest level as generated (for tape_mode 1 level_capacity) */
+  int64_t medium_samples;      /* absorption-grid samples of the forward (dt_medium) */
 } dt_stats;
 dt_status dt_read_stats(const void* d_ws, size_t ws_bytes, dt_stats* out, dt_stream stream);
 

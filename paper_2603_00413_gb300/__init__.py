@@ -73,7 +73,7 @@ class DtStats(ctypes.Structure):
                 ("level_count", c_int64 * 32), ("level_start", c_int64 * 32), ("hits", c_int64),
                 ("misses", c_int64), ("discarded", c_int64), ("backfacing", c_int64), ("tir", c_int64),
                 ("nodes_visited", c_int64), ("tris_tested", c_int64), ("max_level", c_int64),
-                ("level_needed", c_int64)]
+                ("level_needed", c_int64), ("medium_samples", c_int64)]
 
     def as_dict(self):
         n = self.n_levels
@@ -82,7 +82,7 @@ class DtStats(ctypes.Structure):
             "level_count": list(self.level_count[:max(n, 1)]), "hits": self.hits, "misses": self.misses,
             "discarded": self.discarded, "backfacing": self.backfacing, "tir": self.tir,
             "nodes_visited": self.nodes_visited, "tris_tested": self.tris_tested, "max_level": self.max_level,
-            "level_needed": self.level_needed,
+            "level_needed": self.level_needed, "medium_samples": self.medium_samples,
         }
 
 

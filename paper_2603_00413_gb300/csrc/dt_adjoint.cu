@@ -43,7 +43,7 @@ struct AdjRecords {
 // backward scratch: two level buffers of adjoint records and the dN/dV
 // accumulators
 struct BwsLayout {
-  size_t off_buf[2][3], off_dN, total;
+  size_t off_buf[2][3], off_med, off_dN, total;
   BwsLayout(unsigned long long max_level, int32_t nv) {
     size_t o = 0;
     for (int k = 0; k < 2; ++k) {
@@ -52,6 +52,10 @@ struct BwsLayout {
       off_buf[k][2] = align_up(off_buf[k][1] + (size_t)max_level * sizeof(float4), 256);
       o = align_up(off_buf[k][2] + (size_t)max_level * sizeof(float), 256);
     }
+    // per segment of the level being swept: (dJ/dS, t) of an interior
+    // segment with an absorption grid, zeros otherwise
+    off_med = o;
+    o = align_up(o + (size_t)max_level * sizeof(float4), 256);
     off_dN = o;
     total = align_up(off_dN + (size_t)nv * 2 * sizeof(float4), 256);
   }
@@ -93,7 +97,8 @@ constexpr int kAdjointMinBlocks = 4;  // CTAs of 256 per SM the register budget 
 
 template <bool kBatch, bool kGrid>
 __global__ void __launch_bounds__(256, kAdjointMinBlocks) k_adjoint(WsView W, int k, const AdjRecords out_next,
-                                                                   const AdjRecords out_cur, const SceneEntry E0) {
+                                                                   const AdjRecords out_cur, const SceneEntry E0,
+                                                                   float4* __restrict__ med_side) {
   extern __shared__ float sums_smem[];
   const WsHeader* H = W.hdr;
   const int n_scenes = kBatch ? W.th->n : 1;
@@ -126,6 +131,7 @@ __global__ void __launch_bounds__(256, kAdjointMinBlocks) k_adjoint(WsView W, in
     }
     const uint32_t pix = (sample - E.sample_start) / (uint32_t)E.spp;
     float3 L = mk(0.f, 0.f, 0.f), obar = L, dbar = L;
+    float4 side = make_float4(0.f, 0.f, 0.f, 0.f);  // (dJ/dS, t) for the grid pass
     if (sample >= E.sample_start && pix < E.pix_count) {
       const float3 g = mk(__ldg(E.grad_out + 3 * (size_t)pix), __ldg(E.grad_out + 3 * (size_t)pix + 1),
                           __ldg(E.grad_out + 3 * (size_t)pix + 2));
@@ -179,6 +185,7 @@ __global__ void __launch_bounds__(256, kAdjointMinBlocks) k_adjoint(WsView W, in
           if (med) {
             sbar = -aa;
             tbar += dot(sbar, medium_depth_dt(medium_view(E), o, d, t));
+            side = make_float4(sbar.x, sbar.y, sbar.z, t);
           }
         }
         float cbar = 0.f, etabar = 0.f, eta1bar = 0.f, eta2bar = 0.f;
@@ -255,14 +262,12 @@ __global__ void __launch_bounds__(256, kAdjointMinBlocks) k_adjoint(WsView W, in
         atomic_add4(dV4 + i0, lam * (-b0));
         atomic_add4(dV4 + i1, lam * (-b1));
         atomic_add4(dV4 + i2, lam * (-b2));
-        // the grid's samples move with o and d at fixed t (the t dependence
-        // went into tbar above)
-        if (med) medium_backward(medium_view(E), E.dmu, o, d, t, sbar, obar, dbar);
       }
     }
     if (k > 0) {
       out_cur.store(i, L, obar, dbar);
     }
+    if (kGrid) med_side[i] = side;
   }
   sums.add(cur, acc_ior, acc_sig);
   __syncthreads();
@@ -271,6 +276,36 @@ __global__ void __launch_bounds__(256, kAdjointMinBlocks) k_adjoint(WsView W, in
     if (sums_smem[4 * sc] != 0.f) atomicAdd(E.dior, sums_smem[4 * sc]);
     for (int c = 0; c < 3; ++c)
       if (sums_smem[4 * sc + 1 + c] != 0.f) atomicAdd(E.dsigma + c, sums_smem[4 * sc + 1 + c]);
+  }
+}
+
+// The absorption grid's share of the adjoint of level k, after k_adjoint:
+// for each interior segment with a grid (side = (dJ/dS, t), t > 0) the
+// samples of its optical depth move with the segment's o and d at fixed t,
+// which adds to its adjoint record (read by the parent level next), and
+// dJ/dS goes to the grid's nodes.  A pass of its own, so the march and the
+// node atomics run at the occupancy of a small kernel.
+template <bool kBatch>
+__global__ void __launch_bounds__(256, 3) k_medium_adjoint(WsView W, int k, const AdjRecords out_cur,
+                                                        const float4* __restrict__ med_side, const SceneEntry E0) {
+  const WsHeader* H = W.hdr;
+  const int n_scenes = kBatch ? W.th->n : 1;
+  const uint32_t n = level_size(H, k);
+  const uint32_t start = H->level_start[k];
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float4 sv = med_side[i];
+    if (!(sv.w > 0.f) || (sv.x == 0.f && sv.y == 0.f && sv.z == 0.f)) continue;  // no grid, or no gradient
+    const uint32_t a = start + i;
+    const float4 ro = W.ray_o[a], rd = W.ray_d[a];
+    const SceneEntry& E = kBatch ? W.ent[find_scene(W.th->starts, n_scenes, __float_as_uint(ro.w))] : E0;
+    if (!E.mu) continue;
+    float3 ob = mk(0.f, 0.f, 0.f), db = ob;
+    medium_backward(medium_view(E), E.dmu, xyz(ro), xyz(rd), sv.w, mk(sv.x, sv.y, sv.z), ob, db);
+    if (k > 0) {  // camera rays have no parent to hand (obar, dbar) to
+      float3 L, o0, d0;
+      out_cur.load(i, L, o0, d0);
+      out_cur.store(i, L, o0 + ob, d0 + db);
+    }
   }
 }
 
@@ -377,15 +412,23 @@ void launch_backward_table(const TableHeader& th, const SceneEntry* entries, con
   }
   const int blocks = g_tuning.shade_blocks_per_sm * num_sms();
   const size_t smem = sizeof(float) * 4 * (size_t)n;
+  float4* side = reinterpret_cast<float4*>((char*)bws + L.off_med);
   for (int k = th.max_depth; k >= 0; --k) {
-    ProfScope ps("k_adjoint", s);
     const AdjRecords nx = buf[(k + 1) & 1], cu = buf[k & 1];
+    {
+      ProfScope ps("k_adjoint", s);
+      if (th.any_medium) {
+        if (n > 1) k_adjoint<true, true><<<blocks, 256, smem, s>>>(W, k, nx, cu, entries[0], side);
+        else k_adjoint<false, true><<<blocks, 256, smem, s>>>(W, k, nx, cu, entries[0], side);
+      } else {
+        if (n > 1) k_adjoint<true, false><<<blocks, 256, smem, s>>>(W, k, nx, cu, entries[0], side);
+        else k_adjoint<false, false><<<blocks, 256, smem, s>>>(W, k, nx, cu, entries[0], side);
+      }
+    }
     if (th.any_medium) {
-      if (n > 1) k_adjoint<true, true><<<blocks, 256, smem, s>>>(W, k, nx, cu, entries[0]);
-      else k_adjoint<false, true><<<blocks, 256, smem, s>>>(W, k, nx, cu, entries[0]);
-    } else {
-      if (n > 1) k_adjoint<true, false><<<blocks, 256, smem, s>>>(W, k, nx, cu, entries[0]);
-      else k_adjoint<false, false><<<blocks, 256, smem, s>>>(W, k, nx, cu, entries[0]);
+      ProfScope ps("k_medium_adjoint", s);
+      if (n > 1) k_medium_adjoint<true><<<8 * num_sms(), 256, 0, s>>>(W, k, cu, side, entries[0]);
+      else k_medium_adjoint<false><<<8 * num_sms(), 256, 0, s>>>(W, k, cu, side, entries[0]);
     }
   }
   int fb = (max_nf + 255) / 256;

@@ -359,6 +359,7 @@ dt_status dt_read_stats(const void* d_ws, size_t ws_bytes, dt_stats* out, dt_str
   out->tir = (int64_t)h.counters[CNT_TIR];
   out->nodes_visited = (int64_t)h.counters[CNT_NODES];
   out->tris_tested = (int64_t)h.counters[CNT_TRIS];
+  out->medium_samples = (int64_t)h.counters[CNT_MEDIUM];
   g_err[0] = 0;
   return DT_OK;
 }

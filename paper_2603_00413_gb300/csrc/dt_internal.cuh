@@ -163,7 +163,7 @@ struct WsHeader {
   uint32_t pad0;
 };
 
-enum { CNT_HITS = 0, CNT_MISSES, CNT_DISCARDED, CNT_BACKFACING, CNT_TIR, CNT_NODES, CNT_TRIS };
+enum { CNT_HITS = 0, CNT_MISSES, CNT_DISCARDED, CNT_BACKFACING, CNT_TIR, CNT_NODES, CNT_TRIS, CNT_MEDIUM };
 
 // ---------------------------------------------------------------------------
 // Scene table: every render (one scene or a batch) reads its scenes from a

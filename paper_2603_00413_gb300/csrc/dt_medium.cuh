@@ -11,8 +11,10 @@
 //   dS/dt = G(x_m) + (r / 2) dG/dx(x_m) d,
 // and at fixed t every sample moves with o and d:
 //   dS/do = sum_i w_i dG/dx(x_i),  dS/dd = sum_i w_i s_i dG/dx(x_i).
-// The forward shading pass and the adjoint both evaluate these; the adjoint
-// also scatters dJ/dS w_i into the eight nodes of each sample's cell.
+// The forward shading pass and the adjoint evaluate S and dS/dt; a separate
+// pass over the interior segments of each level adds the o and d terms to
+// their adjoint records and scatters dJ/dS w_i into the eight nodes of each
+// sample's cell.
 #pragma once
 
 #include "dt_internal.cuh"
@@ -143,38 +145,71 @@ __device__ __forceinline__ void medium_atomic4(float4* p, float3 v) {
   atomicAdd(p, make_float4(v.x, v.y, v.z, 0.f));
 }
 
-// Adjoint of the optical depth at fixed t: sbar = dJ/dS (per channel).
-// Adds dJ/do and dJ/dd to obar and dbar and, when dmu is given, dJ/dG at the
-// nodes (sbar w_i times each corner's trilinear weight).
+// Adjoint of the optical depth at fixed t: sbar = dJ/dS (per channel, one
+// value for the whole segment).  Adds dJ/do and dJ/dd to obar and dbar and,
+// when dmu is given, dJ/dG at the nodes: sbar times the sum over samples of
+// w_i times the corner's trilinear weight.  Since sbar is constant along the
+// segment, only those scalar sums are kept per corner, over consecutive
+// samples in the same cell (a step of half a cell puts about two samples in
+// each cell a ray crosses), and added with one atomic per node when the ray
+// leaves the cell.  The sample gradient needs only sbar . G at the corners.
+__device__ __forceinline__ void medium_flush(float4* p, int sx, int sy, float3 sbar, const float* acc) {
+  medium_atomic4(p, sbar * acc[0]);
+  medium_atomic4(p + 1, sbar * acc[1]);
+  medium_atomic4(p + sx, sbar * acc[2]);
+  medium_atomic4(p + sx + 1, sbar * acc[3]);
+  medium_atomic4(p + sy, sbar * acc[4]);
+  medium_atomic4(p + sy + 1, sbar * acc[5]);
+  medium_atomic4(p + sy + sx, sbar * acc[6]);
+  medium_atomic4(p + sy + sx + 1, sbar * acc[7]);
+}
+
 __device__ __forceinline__ void medium_backward(const MediumView& g, float4* dmu, float3 o, float3 d, float t,
                                                 float3 sbar, float3& obar, float3& dbar) {
   const float h = g.step;
   const int m = medium_full_steps(t, h);
   const float r = t - (float)m * h;
+  const int sx = g.nx, sy = g.nx * g.ny;
+  float acc[8];
+  size_t cur = ~(size_t)0;
   for (int i = 0; i <= m; ++i) {
     const float w = i < m ? h : r;
     const float s = i < m ? ((float)i + 0.5f) * h : (float)m * h + 0.5f * r;
     const GridCell c = grid_cell(g, o + d * s);
-    const CellNodes q = cell_nodes(g, c);
-    float3 gx, gy, gz;
-    trilinear_grad(q, c, g.scale, gx, gy, gz);
-    const float3 gp = mk(dot(sbar, gx), dot(sbar, gy), dot(sbar, gz)) * w;  // w dJ/dx at this sample
+    const float4* p = g.mu + c.base;
+    // sbar . G at the eight corners
+    const float s000 = dot(sbar, xyz(__ldg(p))), s100 = dot(sbar, xyz(__ldg(p + 1)));
+    const float s010 = dot(sbar, xyz(__ldg(p + sx))), s110 = dot(sbar, xyz(__ldg(p + sx + 1)));
+    const float s001 = dot(sbar, xyz(__ldg(p + sy))), s101 = dot(sbar, xyz(__ldg(p + sy + 1)));
+    const float s011 = dot(sbar, xyz(__ldg(p + sy + sx))), s111 = dot(sbar, xyz(__ldg(p + sy + sx + 1)));
+    const float ux = 1.0f - c.fx, uy = 1.0f - c.fy, uz = 1.0f - c.fz;
+    const float3 gp =
+        mk(((s100 - s000) * (uy * uz) + (s110 - s010) * (c.fy * uz) + (s101 - s001) * (uy * c.fz) +
+            (s111 - s011) * (c.fy * c.fz)) * (c.free_x ? g.scale.x : 0.0f),
+           ((s010 - s000) * (ux * uz) + (s110 - s100) * (c.fx * uz) + (s011 - s001) * (ux * c.fz) +
+            (s111 - s101) * (c.fx * c.fz)) * (c.free_y ? g.scale.y : 0.0f),
+           ((s001 - s000) * (ux * uy) + (s101 - s100) * (c.fx * uy) + (s011 - s010) * (ux * c.fy) +
+            (s111 - s110) * (c.fx * c.fy)) * (c.free_z ? g.scale.z : 0.0f)) * w;  // w dJ/dx at this sample
     obar = obar + gp;
     dbar = dbar + gp * s;
     if (dmu) {
-      const float3 v = sbar * w;
-      const float ux = 1.0f - c.fx, uy = 1.0f - c.fy, uz = 1.0f - c.fz;
-      float4* p = dmu + c.base;
-      medium_atomic4(p, v * (ux * uy * uz));
-      medium_atomic4(p + 1, v * (c.fx * uy * uz));
-      medium_atomic4(p + c.sx, v * (ux * c.fy * uz));
-      medium_atomic4(p + c.sx + 1, v * (c.fx * c.fy * uz));
-      medium_atomic4(p + c.sy, v * (ux * uy * c.fz));
-      medium_atomic4(p + c.sy + 1, v * (c.fx * uy * c.fz));
-      medium_atomic4(p + c.sy + c.sx, v * (ux * c.fy * c.fz));
-      medium_atomic4(p + c.sy + c.sx + 1, v * (c.fx * c.fy * c.fz));
+      if (c.base != cur) {
+        if (cur != ~(size_t)0) medium_flush(dmu + cur, sx, sy, sbar, acc);
+        cur = c.base;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[q] = 0.f;
+      }
+      acc[0] += w * (ux * uy * uz);
+      acc[1] += w * (c.fx * uy * uz);
+      acc[2] += w * (ux * c.fy * uz);
+      acc[3] += w * (c.fx * c.fy * uz);
+      acc[4] += w * (ux * uy * c.fz);
+      acc[5] += w * (c.fx * uy * c.fz);
+      acc[6] += w * (ux * c.fy * c.fz);
+      acc[7] += w * (c.fx * c.fy * c.fz);
     }
   }
+  if (dmu && cur != ~(size_t)0) medium_flush(dmu + cur, sx, sy, sbar, acc);
 }
 
 }  // namespace dt

@@ -503,7 +503,7 @@ __global__ void __launch_bounds__(kShadeThreads, kShadeMinBlocks) k_shade(WsView
   const unsigned long long key_room = W.ring ? (unsigned long long)W.ring : H->capacity - next_start;
   float3 box_lo = mk(0.f, 0.f, 0.f), box_scale = box_lo;
   if (!kBatch && order_bits) scene_order_box(E0.node2, box_lo, box_scale);
-  uint32_t c_hit = 0, c_miss = 0, c_disc = 0, c_back = 0, c_tir = 0;
+  uint32_t c_hit = 0, c_miss = 0, c_disc = 0, c_back = 0, c_tir = 0, c_med = 0;
   bool overflow = false;
   // CTA-wide tiles, so that the children of a tile are appended with one
   // atomic on the level counter per CTA rather than per warp
@@ -547,8 +547,10 @@ __global__ void __launch_bounds__(kShadeThreads, kShadeMinBlocks) k_shade(WsView
           HitShade h;
           shade_hit(xyz(ro), d, hh.x, hh.y, hh.z, v0, v1, v2, load3(E.N + 3 * i0), load3(E.N + 3 * i1),
                     load3(E.N + 3 * i2), ior, sigma, h);
-          if (kGrid && E.mu && !h.entering)  // Sec. 3.4 step 5 with the grid's optical depth
+          if (kGrid && E.mu && !h.entering) {  // Sec. 3.4 step 5 with the grid's optical depth
             h.A = absorption_with_depth(sigma, hh.x, medium_depth(medium_view(E), xyz(ro), d, hh.x));
+            c_med += (uint32_t)medium_full_steps(hh.x, E.gstep) + 1u;
+          }
           fl = h.entering ? 0u : SF_INSIDE;
           if (h.backfacing) {
             fl |= SF_BACKFACING;
@@ -646,6 +648,7 @@ __global__ void __launch_bounds__(kShadeThreads, kShadeMinBlocks) k_shade(WsView
   warp_add_u64(&H->counters[CNT_DISCARDED], c_disc);
   warp_add_u64(&H->counters[CNT_BACKFACING], c_back);
   warp_add_u64(&H->counters[CNT_TIR], c_tir);
+  if (kGrid) warp_add_u64(&H->counters[CNT_MEDIUM], c_med);
   if (__any_sync(kFull, overflow) && lane == 0) atomicOr(&H->status, ST_QUEUE_OVERFLOW);
 }
 

@@ -104,8 +104,8 @@ int main(void) {
   printf("%zu %zu %zu\n", sizeof(dt_batch_entry), offsetof(dt_batch_entry, d_grad_sigma), sizeof(dt_tuning));
   printf("%zu %zu %zu\n", offsetof(dt_params, tape_mode), offsetof(dt_params, level_capacity),
          offsetof(dt_stats, level_needed));
-  printf("%zu %zu %zu %zu\n", sizeof(dt_medium), offsetof(dt_medium, lo), offsetof(dt_medium, step),
-         offsetof(dt_scene, medium));
+  printf("%zu %zu %zu %zu %zu\n", sizeof(dt_medium), offsetof(dt_medium, lo), offsetof(dt_medium, step),
+         offsetof(dt_scene, medium), offsetof(dt_stats, medium_samples));
   return 0;
 }
 """
@@ -125,7 +125,7 @@ int main(void) {
     assert sizes[11:14] == [dt.DtParams.tape_mode.offset, dt.DtParams.level_capacity.offset,
                             dt.DtStats.level_needed.offset]
     assert sizes[14:] == [ctypes.sizeof(dt.DtMedium), dt.DtMedium.lo.offset, dt.DtMedium.step.offset,
-                          dt.DtScene.medium.offset]
+                          dt.DtScene.medium.offset, dt.DtStats.medium_samples.offset]
 
 
 def test_checkpointed_workspace_is_smaller_and_validated():

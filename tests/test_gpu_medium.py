@@ -62,12 +62,14 @@ def test_medium_render_matches_oracle():
     med = S.random_absorption_grid((9, 8, 10), LO, HI, seed=5, scale=1.5)
     img, tape = gs.render(medium=_gpu_medium(med))
     assert tape.stats["status"] == dt.DT_OK
+    assert tape.stats["medium_samples"] > 0
     for v in range(2):
         info = assert_radiance_parity(img[v], _oracle(gs, med, v))
         assert info["excluded_frac"] < 0.25, info
     # the grid absorbs: darker than sigma alone wherever light crossed the object
-    plain, _ = gs.render()
+    plain, ptape = gs.render()
     assert (img <= plain * (1 + 1e-5) + 1e-7).all() and (img < plain * 0.999).any()
+    assert ptape.stats["medium_samples"] == 0
 
 
 def test_constant_medium_equals_sigma_shift():
