@@ -639,3 +639,19 @@ def test_medium_jvp_matches_central_differences():
     # pixelwise with a small absolute floor
     np.testing.assert_allclose(dv[0], fd_v, rtol=1e-4, atol=1e-6)
     assert np.abs(dm[0]).max() > 1e-3 and np.abs(dv[0]).max() > 1e-3
+
+
+def test_image_is_linear_in_the_environment():
+    """Escaped radiance is read from the map and weighted by a throughput
+    that does not depend on it (Sec. 3.4 steps 3-5), so the image is linear
+    in the texels: render(a E1 + b E2) = a render(E1) + b render(E2).  (This
+    is what makes render(env = u) the directional derivative of the image
+    along u, the reference for the environment gradient.)"""
+    sc = S.glass_icosphere_scene(width=10, height=8, max_depth=4)
+    cam = sc.cams[0]
+    sigma = np.array([0.3, 0.1, 0.2])
+    rng = np.random.default_rng(17)
+    E1, E2 = rng.normal(size=(2,) + sc.env.shape)
+    a, b = 0.7, -1.3
+    r = lambda E: O.render(sc.V, sc.F, 1.5, sigma, E, cam, 4)["img"]
+    np.testing.assert_allclose(r(a * E1 + b * E2), a * r(E1) + b * r(E2), rtol=1e-10, atol=1e-12)
