@@ -406,7 +406,7 @@ def medium_leg(args, dt, dev):
     trilinear, sampled every half cell along interior segments.  One step =
     normals + refit + forward + backward seeded by a fixed random image
     gradient, with the node-value gradient; the same step without the grid
-    is timed beside it."""
+    is timed beside it, and once more with the environment-texel gradient."""
     import torch
     from paper_2603_00413_gb300 import scenes as S
     sc, _ = genus2_workload(args.medium_views, args.res, args.depth)
@@ -432,8 +432,9 @@ def medium_leg(args, dt, dev):
                        f"plus a {g}^3 grid of smooth random absorption rates over [-1.25, 1.25]^3 sampled every "
                        f"{med['step']:.4f} (half a cell) along interior segments; fwd+bwd with a fixed image gradient",
            "grid_nodes": g ** 3, "step": med["step"]}
-    for mode in ("medium", "sigma_only"):
+    for mode in ("medium", "sigma_only", "sigma_only_env_grad"):
         m = medium if mode == "medium" else None
+        want_env = mode == "sigma_only_env_grad"
         img, tape = dt.render(V, F, bvh, N, ior, sigma, env, cams, res, res, params, medium=m)
         stats = tape.stats
         _, bws = dt._aligned_empty(dt.backward_workspace_size(stats["max_level"], V.shape[0]), dev)
@@ -445,7 +446,7 @@ def medium_leg(args, dt, dev):
             _, tp = dt.render(V, F, bvh, N, ior, sigma, env, cams, res, res, params, ws=tape.ws, out=img,
                               check=False, medium=m)
             tp.stats = stats
-            return dt.render_backward(tp, grad, bws=bws)
+            return dt.render_backward(tp, grad, bws=bws, env_grad=want_env)
 
         for _ in range(3):
             step()

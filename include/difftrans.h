@@ -154,6 +154,8 @@ typedef struct dt_scene {
   const float* d_env;   /* float[env_h][env_w][3] environment */
   int32_t env_w, env_h;
   const dt_medium* medium; /* NULL: the constant sigma only */
+  float* d_grad_env;       /* backward: dLoss/d(environment texels), float[env_h][env_w][3], overwritten;
+                              NULL: not computed (the forward ignores it) */
 } dt_scene;
 
 /* n_views pinhole cameras sharing one image size.  d_cams float[n_views][10]

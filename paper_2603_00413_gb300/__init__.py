@@ -56,7 +56,8 @@ class DtMedium(ctypes.Structure):
 class DtScene(ctypes.Structure):
     _fields_ = [("d_V", c_void_p), ("d_F", c_void_p), ("nv", c_int32), ("nf", c_int32), ("d_bvh", c_void_p),
                 ("d_N", c_void_p), ("d_ior", c_void_p), ("d_sigma", c_void_p), ("d_env", c_void_p),
-                ("env_w", c_int32), ("env_h", c_int32), ("medium", ctypes.POINTER(DtMedium))]
+                ("env_w", c_int32), ("env_h", c_int32), ("medium", ctypes.POINTER(DtMedium)),
+                ("d_grad_env", c_void_p)]
 
 
 class DtViews(ctypes.Structure):
@@ -371,7 +372,7 @@ class Medium:
         return m
 
 
-def _scene_struct(V, F, bvh, N, ior, sigma, env, medium_c=None):
+def _scene_struct(V, F, bvh, N, ior, sigma, env, medium_c=None, denv=None):
     _need(V, torch.float32, (3,), "V")
     _need(F, torch.int32, (3,), "F")
     _need(N, torch.float32, (3,), "N")
@@ -384,6 +385,8 @@ def _scene_struct(V, F, bvh, N, ior, sigma, env, medium_c=None):
                  ior.data_ptr(), sigma.data_ptr(), env.data_ptr(), env.shape[1], env.shape[0])
     if medium_c is not None:
         sc.medium = ctypes.pointer(medium_c)
+    if denv is not None:
+        sc.d_grad_env = _need(denv, torch.float32, (3,), "d_grad_env").data_ptr()
     return sc
 
 
@@ -476,10 +479,11 @@ def render(V, F, bvh: Bvh, N, ior, sigma, env, cams, width: int, height: int, pa
         return out, Tape(ws, (V, F, bvh, N, ior, sigma, env), cams, width, height, params, stats, pc, medium)
 
 
-def render_backward(tape: Tape, grad_out, stream=None, bws=None):
+def render_backward(tape: Tape, grad_out, stream=None, bws=None, env_grad: bool = False):
     """Gradient of sum(grad_out * image) w.r.t. (V, ior, sigma) at the
-    forward's fixed events.  Returns (dV [nv,3], dior [1], dsigma [3]), and
-    with an absorption grid also dmu [nz, ny, nx, 3]."""
+    forward's fixed events.  Returns (dV [nv,3], dior [1], dsigma [3]),
+    then dmu [nz, ny, nx, 3] when the render had an absorption grid, then
+    denv [env_h, env_w, 3] when env_grad is set."""
     lib = load_library()
     V, F, bvh, N, ior, sigma, env = tape.scene_args
     stats = tape.stats if tape.stats is not None else read_stats(tape.ws, stream)
@@ -496,15 +500,19 @@ def render_backward(tape: Tape, grad_out, stream=None, bws=None):
     med = tape.medium
     dmu = torch.empty_like(med.mu) if med is not None else None
     mc = med.struct(dmu) if med is not None else None
-    sc = _scene_struct(V, F, bvh, N, ior, sigma, env, mc)
+    denv = torch.empty_like(env) if env_grad else None
+    sc = _scene_struct(V, F, bvh, N, ior, sigma, env, mc, denv)
     vw = _views_struct(tape.cams, tape.width, tape.height)
     pc = tape.params_c
     _check(lib.dt_render_backward(ctypes.byref(sc), ctypes.byref(vw), ctypes.byref(pc), _ptr(tape.ws.buf),
                                   tape.ws.bytes, _ptr(grad_out), _ptr(dV), _ptr(dior), _ptr(dsig), _ptr(bws),
                                   bws.numel(), max_level, _stream(stream)))
+    out = (dV, dior, dsig)
     if med is not None:
-        return dV, dior, dsig, dmu[..., :3]
-    return dV, dior, dsig
+        out += (dmu[..., :3],)
+    if env_grad:
+        out += (denv,)
+    return out
 
 
 def dump_segments(tape: Tape, stream=None):
@@ -594,11 +602,13 @@ class BatchItem:
     def n_primary(self):
         return self.cams.shape[0] * self.width * self.height * self.params.spp
 
-    def entry(self, out=None, grad_out=None, dV=None, dior=None, dsig=None, level_capacity: int = 0, dmu=None):
+    def entry(self, out=None, grad_out=None, dV=None, dior=None, dsig=None, level_capacity: int = 0, dmu=None,
+              denv=None):
         e = DtBatchEntry()
         # the medium struct must outlive the call: keep it on the item
         self._medium_c = self.medium.struct(dmu) if self.medium is not None else None
-        e.scene = _scene_struct(self.V, self.F, self.bvh, self.N, self.ior, self.sigma, self.env, self._medium_c)
+        e.scene = _scene_struct(self.V, self.F, self.bvh, self.N, self.ior, self.sigma, self.env, self._medium_c,
+                                denv)
         e.views = _views_struct(self.cams, self.width, self.height)
         e.params = self.params.c(level_capacity)
         e.d_out = out.data_ptr() if out is not None else None
@@ -654,10 +664,11 @@ def batch_backward_workspace_size(items, max_level: int) -> int:
     return b.value
 
 
-def render_batch_backward(tape: BatchTape, grads, bws=None, outs=None, stream=None):
+def render_batch_backward(tape: BatchTape, grads, bws=None, outs=None, stream=None, env_grad: bool = False):
     """Gradients of sum_i sum(grads[i] * image_i) for every scene of the
     batch: list of (dV, dior, dsigma), with dmu [nz, ny, nx, 3] appended for
-    an item with an absorption grid."""
+    an item with an absorption grid and denv [env_h, env_w, 3] when
+    env_grad is set."""
     lib = load_library()
     items = tape.items
     stats = tape.stats if tape.stats is not None else read_stats(tape.ws, stream)
@@ -671,13 +682,15 @@ def render_batch_backward(tape: BatchTape, grads, bws=None, outs=None, stream=No
     if outs is None:
         outs = [(torch.empty_like(it.V), torch.empty(1, device=dev), torch.empty(3, device=dev)) for it in items]
     dmus = [torch.empty_like(it.medium.mu) if it.medium is not None else None for it in items]
+    denvs = [torch.empty_like(it.env) if env_grad else None for it in items]
     grads = [_need(g.contiguous(), torch.float32, (3,), "grad") for g in grads]
     arr = (DtBatchEntry * len(items))(*[it.entry(grad_out=g, dV=o[0], dior=o[1], dsig=o[2],
-                                                 level_capacity=tape.ws.level_capacity, dmu=m)
-                                        for it, g, o, m in zip(items, grads, outs, dmus)])
+                                                 level_capacity=tape.ws.level_capacity, dmu=m, denv=de)
+                                        for it, g, o, m, de in zip(items, grads, outs, dmus, denvs)])
     _check(lib.dt_render_batch_backward(arr, len(items), _ptr(tape.ws.buf), tape.ws.bytes, _ptr(bws), bws.numel(),
                                         max_level, _stream(stream)))
-    return [tuple(o) + ((m[..., :3],) if m is not None else ()) for o, m in zip(outs, dmus)]
+    return [tuple(o) + ((m[..., :3],) if m is not None else ()) + ((de,) if de is not None else ())
+            for o, m, de in zip(outs, dmus, denvs)]
 
 
 # ---------------------------------------------------------------------------

@@ -309,6 +309,81 @@ __global__ void __launch_bounds__(256, 3) k_medium_adjoint(WsView W, int k, cons
   }
 }
 
+// Gradient of the environment texels (Sec. 3.4 step 3 read with a bilinear
+// lookup, linear in the texels): every segment that missed adds gbar =
+// g_pixel W / spp times its four bilinear weights to four texels.  It needs
+// no adjoint of other segments, so one pass covers every level of the tape.
+// kShared: one scene whose environment fits a CTA's shared memory; its texels
+// are summed there first and added to the output with one atomic per texel
+// per CTA (the bench's 64x32 environment takes tens of millions of misses
+// per step, which global atomics on 2048 texels would serialise).  Each
+// thread takes a contiguous chunk of the tape, so a warp's lanes read rays
+// far apart (other pixels, other directions) and rarely add to the same
+// texel in one instruction, as arena neighbours (coherent rays) would.
+constexpr int kEnvSharedTexels = 4096;  // 48 KB of float sums
+
+template <bool kBatch, bool kShared>
+__global__ void __launch_bounds__(256) k_env_adjoint(WsView W, const SceneEntry E0) {
+  extern __shared__ float env_acc[];
+  const WsHeader* H = W.hdr;
+  const int n_scenes = kBatch ? W.th->n : 1;
+  const int nl = (int)H->n_levels;
+  const unsigned long long total = nl > 0 ? H->level_start[nl] : 0ull;
+  const unsigned long long lim = total < W.cap ? total : W.cap;
+  const int ntex3 = kShared ? 3 * E0.env_w * E0.env_h : 0;
+  if (kShared) {
+    for (int i = threadIdx.x; i < ntex3; i += blockDim.x) env_acc[i] = 0.f;
+    __syncthreads();
+  }
+  const unsigned long long nthreads = (unsigned long long)gridDim.x * blockDim.x;
+  const unsigned long long chunk = (lim + nthreads - 1) / nthreads;
+  const unsigned long long a0 = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) * chunk;
+  const unsigned long long a1 = a0 + chunk < lim ? a0 + chunk : lim;
+  constexpr int kU = 4;  // segments in flight per thread
+  for (unsigned long long a = a0; a < a1; a += kU) {
+    bool miss[kU];
+    float4 ro[kU], rd[kU], rw[kU];
+#pragma unroll
+    for (int j = 0; j < kU; ++j) miss[j] = a + j < a1 && (W.sflag[a + j] & SF_MISS);
+#pragma unroll
+    for (int j = 0; j < kU; ++j)
+      if (miss[j]) {
+        ro[j] = W.ray_o[a + j];
+        rd[j] = W.ray_d[a + j];
+        rw[j] = W.ray_w[a + j];
+      }
+#pragma unroll
+    for (int j = 0; j < kU; ++j) {
+      if (!miss[j]) continue;
+      const uint32_t sample = __float_as_uint(ro[j].w);
+      const SceneEntry& E = kBatch ? W.ent[find_scene(W.th->starts, n_scenes, sample)] : E0;
+      if (!E.denv) continue;
+      const uint32_t pix = (sample - E.sample_start) / (uint32_t)E.spp;
+      if (sample < E.sample_start || pix >= E.pix_count) continue;  // a dead record
+      const float3 g = mk(__ldg(E.grad_out + 3 * (size_t)pix), __ldg(E.grad_out + 3 * (size_t)pix + 1),
+                          __ldg(E.grad_out + 3 * (size_t)pix + 2));
+      const float3 gbar = mul(g, mk(rw[j].x, rw[j].y, rw[j].z)) * (1.0f / (float)E.spp);
+      const EnvSample es = env_coords(xyz(rd[j]), E.env_w, E.env_h);
+      const int tex[4] = {es.y0 * E.env_w + es.x0, es.y0 * E.env_w + es.x1, es.y1 * E.env_w + es.x0,
+                          es.y1 * E.env_w + es.x1};
+      const float wt[4] = {(1.0f - es.ax) * (1.0f - es.ay), es.ax * (1.0f - es.ay), (1.0f - es.ax) * es.ay,
+                           es.ax * es.ay};
+      float* dst = kShared ? env_acc : E.denv;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        atomicAdd(dst + 3 * tex[q], gbar.x * wt[q]);
+        atomicAdd(dst + 3 * tex[q] + 1, gbar.y * wt[q]);
+        atomicAdd(dst + 3 * tex[q] + 2, gbar.z * wt[q]);
+      }
+    }
+  }
+  if (kShared) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < ntex3; i += blockDim.x)
+      if (env_acc[i] != 0.f) atomicAdd(E0.denv + i, env_acc[i]);
+  }
+}
+
 // zero every scene's accumulators, dIoR, dsigma and absorption-grid
 // gradient (blockIdx.y = scene)
 __global__ void k_zero_grads(const SceneEntry* __restrict__ ent) {
@@ -321,6 +396,11 @@ __global__ void k_zero_grads(const SceneEntry* __restrict__ ent) {
     const size_t nn = (size_t)E.gnx * E.gny * E.gnz;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nn; i += (size_t)gridDim.x * blockDim.x)
       E.dmu[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  if (E.denv) {
+    const size_t ne = 3 * (size_t)E.env_w * E.env_h;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < ne; i += (size_t)gridDim.x * blockDim.x)
+      E.denv[i] = 0.f;
   }
   if (blockIdx.x == 0 && threadIdx.x < 4) {
     if (threadIdx.x == 0) E.dior[0] = 0.f;
@@ -430,6 +510,15 @@ void launch_backward_table(const TableHeader& th, const SceneEntry* entries, con
       if (n > 1) k_medium_adjoint<true><<<8 * num_sms(), 256, 0, s>>>(W, k, cu, side, entries[0]);
       else k_medium_adjoint<false><<<8 * num_sms(), 256, 0, s>>>(W, k, cu, side, entries[0]);
     }
+  }
+  if (th.any_env_grad) {
+    ProfScope ps("k_env_adjoint", s);
+    const SceneEntry& E0 = entries[0];
+    const int tex = E0.env_w * E0.env_h;
+    if (n > 1) k_env_adjoint<true, false><<<4 * num_sms(), 256, 0, s>>>(W, E0);
+    else if (tex <= kEnvSharedTexels)
+      k_env_adjoint<false, true><<<4 * num_sms(), 256, 3 * sizeof(float) * (size_t)tex, s>>>(W, E0);
+    else k_env_adjoint<false, false><<<4 * num_sms(), 256, 0, s>>>(W, E0);
   }
   int fb = (max_nf + 255) / 256;
   if (fb > cap_blocks) fb = cap_blocks;

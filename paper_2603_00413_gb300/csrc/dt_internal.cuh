@@ -207,13 +207,14 @@ struct SceneEntry {
   float glo_x, glo_y, glo_z;
   float gscale_x, gscale_y, gscale_z;
   float gstep;
+  float* denv;  // backward: gradient of the environment texels (nullptr: not computed)
 };
 
 struct TableHeader {
   int32_t n;
   int32_t max_depth;
   int32_t any_medium;  // some scene of the table has an absorption grid
-  int32_t pad0;
+  int32_t any_env_grad;  // some scene of the table wants its environment gradient
   uint32_t n_samples;
   uint32_t n_faces;
   uint32_t starts[kMaxBatch + 1];

@@ -789,6 +789,7 @@ SceneEntry make_entry(const dt_scene& sc, const dt_views& vw, const dt_params& p
   e.max_depth = p.max_depth; e.jitter = p.jitter; e.max_iter = traversal_limit(sc.nf);
   e.t_min = p.t_min;
   e.pix_count = (uint32_t)vw.n_views * (uint32_t)vw.width * (uint32_t)vw.height;
+  e.denv = sc.d_grad_env;
   if (sc.medium && sc.medium->d_mu) {
     const dt_medium& M = *sc.medium;
     e.mu = reinterpret_cast<const float4*>(M.d_mu);
@@ -818,6 +819,7 @@ void finish_table(SceneEntry* entries, int n, TableHeader& th) {
     f += (uint32_t)entries[i].nf;
     if (entries[i].max_depth > md) md = entries[i].max_depth;
     if (entries[i].mu) th.any_medium = 1;
+    if (entries[i].denv) th.any_env_grad = 1;
   }
   th.starts[n] = s;
   th.face_starts[n] = f;

@@ -106,6 +106,7 @@ int main(void) {
          offsetof(dt_stats, level_needed));
   printf("%zu %zu %zu %zu %zu\n", sizeof(dt_medium), offsetof(dt_medium, lo), offsetof(dt_medium, step),
          offsetof(dt_scene, medium), offsetof(dt_stats, medium_samples));
+  printf("%zu\n", offsetof(dt_scene, d_grad_env));
   return 0;
 }
 """
@@ -124,8 +125,9 @@ int main(void) {
                            ctypes.sizeof(dt.DtTuning)]
     assert sizes[11:14] == [dt.DtParams.tape_mode.offset, dt.DtParams.level_capacity.offset,
                             dt.DtStats.level_needed.offset]
-    assert sizes[14:] == [ctypes.sizeof(dt.DtMedium), dt.DtMedium.lo.offset, dt.DtMedium.step.offset,
-                          dt.DtScene.medium.offset, dt.DtStats.medium_samples.offset]
+    assert sizes[14:19] == [ctypes.sizeof(dt.DtMedium), dt.DtMedium.lo.offset, dt.DtMedium.step.offset,
+                            dt.DtScene.medium.offset, dt.DtStats.medium_samples.offset]
+    assert sizes[19:] == [dt.DtScene.d_grad_env.offset]
 
 
 def test_checkpointed_workspace_is_smaller_and_validated():
