@@ -399,3 +399,38 @@ def grad_full(V, F, ior, sigma, env, cam, max_depth: int, g, vert_subset=None, c
         for j, (v, a) in enumerate(part):
             dV[v, a] = J[j]
     return dV, float(dior), dsig
+
+
+def paper_losses(img, target, lambda_color: float = 1.0, lambda_tone: float = 1.0):
+    """The training losses of the tracer stage, in FP64, with their gradient
+    with respect to the rendered image (an array [..., 3] of pixel colours
+    c_hat; target: the ground-truth colours c of the same shape).
+
+    Eq. 14 (GT-weighted L2): L_color = (1/|B|) sum_i ||(c_hat_i - c_i) * c_i||^2
+    over the |B| pixels, the product channel-wise.
+    Eq. 15 (tone): L_tone = (1 - c_hat . c / (||c_hat|| ||c||))^2 - var(c),
+    read per pixel (var = the population variance of the pixel's three
+    ground-truth channels) and averaged over the pixels like Eq. 14; a pixel
+    whose rendered or true colour is zero has no defined cosine and counts it
+    as 0 (its term 1 - var(c), no gradient).
+    Returns (total = lambda_color L_color + lambda_tone L_tone, L_color,
+    L_tone, dTotal/dc_hat)."""
+    ch = np.asarray(img, np.float64).reshape(-1, 3)
+    c = np.asarray(target, np.float64).reshape(-1, 3)
+    P = ch.shape[0]
+    r = (ch - c) * c
+    l_color = float((r * r).sum() / P)
+    g_color = 2.0 * r * c / P
+    nh = np.linalg.norm(ch, axis=1)
+    nc = np.linalg.norm(c, axis=1)
+    ok = (nh > 0) & (nc > 0)
+    s = np.zeros(P)
+    s[ok] = (ch[ok] * c[ok]).sum(axis=1) / (nh[ok] * nc[ok])
+    var = c.var(axis=1)
+    l_tone = float(((1.0 - s) ** 2 - var).sum() / P)
+    ds = np.zeros_like(ch)
+    ds[ok] = c[ok] / (nh[ok] * nc[ok])[:, None] - s[ok, None] * ch[ok] / (nh[ok] ** 2)[:, None]
+    g_tone = (-2.0 * (1.0 - s))[:, None] * ds / P
+    total = lambda_color * l_color + lambda_tone * l_tone
+    grad = (lambda_color * g_color + lambda_tone * g_tone).reshape(np.shape(img))
+    return total, l_color, l_tone, grad

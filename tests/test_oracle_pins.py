@@ -655,3 +655,40 @@ def test_image_is_linear_in_the_environment():
     a, b = 0.7, -1.3
     r = lambda E: O.render(sc.V, sc.F, 1.5, sigma, E, cam, 4)["img"]
     np.testing.assert_allclose(r(a * E1 + b * E2), a * r(E1) + b * r(E2), rtol=1e-10, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Eqs. 14-15: the tracer stage's colour and tone losses
+# ---------------------------------------------------------------------------
+def test_paper_losses_closed_forms():
+    """At c_hat = c both losses have zero gradient, L_color = 0 and
+    L_tone = -mean var(c); at c_hat = k c (k > 0) the tone is exact (cosine
+    1) and L_color = (k - 1)^2 mean sum c^4; for orthogonal colours the
+    cosine is 0 and the tone term is 1 - var(c)."""
+    rng = np.random.default_rng(61)
+    c = rng.uniform(0.05, 1.0, size=(50, 3))
+    var = c.var(axis=1)
+    t, lc, lt, g = O.paper_losses(c, c, 0.7, 1.3)
+    assert lc == 0.0 and lt == pytest.approx(-var.mean(), rel=1e-12) and np.abs(g).max() < 1e-15
+    t, lc, lt, g = O.paper_losses(2.5 * c, c, 1.0, 1.0)
+    assert lc == pytest.approx(1.5 ** 2 * (c ** 4).sum(axis=1).mean(), rel=1e-12)
+    assert lt == pytest.approx(-var.mean(), rel=1e-12)
+    a = np.array([[1.0, 0.0, 0.0], [0.0, 2.0, 0.0]])
+    b = np.array([[0.0, 3.0, 0.0], [0.0, 0.0, 0.5]])
+    _, _, lt, _ = O.paper_losses(a, b, 1.0, 1.0)
+    assert lt == pytest.approx(np.mean(1.0 - b.var(axis=1)), rel=1e-12)
+
+
+def test_paper_losses_gradient_matches_central_differences():
+    rng = np.random.default_rng(62)
+    ch = rng.uniform(0.0, 1.2, size=(4, 5, 3))
+    c = rng.uniform(0.05, 1.0, size=(4, 5, 3))
+    _, _, _, g = O.paper_losses(ch, c, 0.8, 1.7)
+    eps = 1e-6
+    fd = np.zeros_like(ch)
+    for idx in np.ndindex(ch.shape):
+        p, m = ch.copy(), ch.copy()
+        p[idx] += eps
+        m[idx] -= eps
+        fd[idx] = (O.paper_losses(p, c, 0.8, 1.7)[0] - O.paper_losses(m, c, 0.8, 1.7)[0]) / (2 * eps)
+    np.testing.assert_allclose(g, fd, rtol=1e-6, atol=1e-9)
