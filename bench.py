@@ -753,6 +753,21 @@ def run_ours(args):
     gpu_launches = int(sum(v[0] * KERNELS_PER_SCOPE.get(k, 1) for k, v in kt.items()))
     kernel_share = {k: round(v[1] / sum(x[1] for x in kt.values()), 4) for k, v in kt.items()}
 
+    # ---- the paper's losses (Eqs. 14-15) as the seed, on the same image ----
+    pgrad = torch.empty_like(img)
+    ploss = torch.empty(3, device=dev)
+    for _ in range(3):
+        dt.paper_loss_grad(img, target, 1.0, 1.0, grad=pgrad, loss=ploss)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(10):
+        dt.paper_loss_grad(img, target, 1.0, 1.0, grad=pgrad, loss=ploss)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    paper_loss = {"ms": e0.elapsed_time(e1) / 10, "pixels": img.numel() // 3,
+                  "l2_seed_ms": kt.get("k_l2_loss_grad", (1, 0.0))[1] / max(1, kt.get("k_l2_loss_grad", (1, 0.0))[0])}
+    del pgrad, ploss
+
     # ---- end to end through the public API with host buffers -------------
     e2e = None
     if not args.no_e2e:
@@ -849,6 +864,7 @@ def run_ours(args):
             "serve": serving,
             "large": large,
             "medium": medium,
+            "paper_loss": paper_loss,
             "levels": stats["level_count"],
             "nodes_per_segment": stats["nodes_visited"] / seg,
             "tris_per_segment": stats["tris_tested"] / seg,

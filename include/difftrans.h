@@ -343,6 +343,20 @@ dt_status dt_closest_hit(const void* d_bvh, int32_t nf, const float* d_o, const 
 dt_status dt_l2_loss_grad(const float* d_img, const float* d_target, int64_t n, float scale, float* d_grad,
                           float* d_loss, dt_stream stream);
 
+/* The tracer stage's own losses (Sec. 3.4 "Optimization") fused into the
+ * backward seed, over n_pix RGB pixels c_hat (rendered) and c (true):
+ *   L_color = (1/n_pix) sum_i ||(c_hat_i - c_i) * c_i||^2, the product
+ *             channel-wise (Eq. 14);
+ *   L_tone  = (1/n_pix) sum_i [(1 - cos(c_hat_i, c_i))^2 - var(c_i)]
+ *             (Eq. 15, per pixel: cos of the RGB vectors, 0 when either is
+ *             zero; var the population variance of the three true channels).
+ * d_img, d_target, d_grad float[n_pix][3]; d_grad = d(total)/d(c_hat) is
+ * overwritten; d_loss float[3] = (lambda_color L_color + lambda_tone L_tone,
+ * L_color, L_tone) is overwritten.  n_pix = 0 gives zeros (the image
+ * pointers may then be NULL). */
+dt_status dt_paper_loss_grad(const float* d_img, const float* d_target, int64_t n_pix, float lambda_color,
+                             float lambda_tone, float* d_grad, float* d_loss, dt_stream stream);
+
 /* ------------------------------------------------------------------------
  * Launch and scheduling knobs of the kernels (process-wide; a call takes
  * the values current when it is made).  The traversal is persistent: each

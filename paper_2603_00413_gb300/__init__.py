@@ -131,6 +131,7 @@ _PROTOS = {
     "dt_render_batch_backward": (c_int32, [POINTER(DtBatchEntry), c_int32, c_void_p, c_size_t, c_void_p, c_size_t,
                                            c_int64, c_void_p]),
     "dt_l2_loss_grad": (c_int32, [c_void_p, c_void_p, c_int64, c_float, c_void_p, c_void_p, c_void_p]),
+    "dt_paper_loss_grad": (c_int32, [c_void_p, c_void_p, c_int64, c_float, c_float, c_void_p, c_void_p, c_void_p]),
     "dt_profile_enable": (c_int32, [c_int32]),
     "dt_get_tuning": (c_int32, [POINTER(DtTuning)]),
     "dt_set_tuning": (c_int32, [POINTER(DtTuning)]),
@@ -540,6 +541,23 @@ def l2_loss_grad(img, target, grad=None, loss=None, stream=None):
     loss = torch.empty(1, dtype=torch.float32, device=img.device) if loss is None else loss
     _check(load_library().dt_l2_loss_grad(_ptr(img), _ptr(target), n, 1.0 / max(n, 1), _ptr(grad), _ptr(loss),
                                           _stream(stream)))
+    return grad, loss
+
+
+def paper_loss_grad(img, target, lambda_color: float = 1.0, lambda_tone: float = 1.0, grad=None, loss=None,
+                    stream=None):
+    """The tracer stage's losses on the device (Eq. 14, GT-weighted L2, and
+    Eq. 15, tone, per pixel and averaged): returns (d total / d img, loss
+    [3] = (lambda_color L_color + lambda_tone L_tone, L_color, L_tone))."""
+    _need(img, torch.float32, (3,), "img")
+    _need(target, torch.float32, (3,), "target")
+    if img.shape != target.shape:
+        raise ValueError("img and target need the same shape")
+    n = img.numel() // 3
+    grad = torch.empty_like(img) if grad is None else grad
+    loss = torch.empty(3, dtype=torch.float32, device=img.device) if loss is None else loss
+    _check(load_library().dt_paper_loss_grad(_ptr(img), _ptr(target), n, float(lambda_color), float(lambda_tone),
+                                             _ptr(grad), _ptr(loss), _stream(stream)))
     return grad, loss
 
 

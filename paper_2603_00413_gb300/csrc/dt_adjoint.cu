@@ -456,6 +456,52 @@ __global__ void k_l2_loss_grad(const float* __restrict__ img, const float* __res
   if ((threadIdx.x & 31) == 0 && acc != 0.f) atomicAdd(loss, acc * scale);
 }
 
+// Eqs. 14-15 per pixel and their gradient; loss[0..2] gather (total,
+// L_color, L_tone) with one atomic each per warp.
+__global__ void k_paper_loss_grad(const float* __restrict__ img, const float* __restrict__ target, int64_t n,
+                                  float inv_n, float lc, float lt, float* __restrict__ grad,
+                                  float* __restrict__ loss) {
+  float acc_c = 0.f, acc_t = 0.f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float3 ch = load3(img + 3 * i), c = load3(target + 3 * i);
+    const float3 r = mul(ch - c, c);
+    acc_c += dot(r, r);
+    float3 g = mul(r, c) * (2.0f * inv_n * lc);
+    const float mean = (c.x + c.y + c.z) * (1.0f / 3.0f);
+    const float var = ((c.x - mean) * (c.x - mean) + (c.y - mean) * (c.y - mean) + (c.z - mean) * (c.z - mean)) *
+                      (1.0f / 3.0f);
+    const float nh = len(ch), nc = len(c);
+    if (nh > 0.0f && nc > 0.0f) {
+      const float s = dot(ch, c) / (nh * nc);
+      const float3 ds = c * (1.0f / (nh * nc)) - ch * (s / (nh * nh));
+      g = g + ds * (-2.0f * (1.0f - s) * inv_n * lt);
+      acc_t += (1.0f - s) * (1.0f - s) - var;
+    } else {
+      acc_t += 1.0f - var;
+    }
+    grad[3 * i] = g.x;
+    grad[3 * i + 1] = g.y;
+    grad[3 * i + 2] = g.z;
+  }
+  acc_c = warp_sum(acc_c) * inv_n;
+  acc_t = warp_sum(acc_t) * inv_n;
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(loss, lc * acc_c + lt * acc_t);
+    atomicAdd(loss + 1, acc_c);
+    atomicAdd(loss + 2, acc_t);
+  }
+}
+
+void launch_paper_loss_grad(const float* img, const float* target, int64_t n, float lc, float lt, float* grad,
+                            float* loss, cudaStream_t s) {
+  cudaMemsetAsync(loss, 0, 3 * sizeof(float), s);
+  if (n == 0) return;
+  int64_t b = (n + 255) / 256;
+  if (b > 8 * num_sms()) b = 8 * num_sms();
+  ProfScope ps("k_paper_loss_grad", s);
+  k_paper_loss_grad<<<(int)b, 256, 0, s>>>(img, target, n, 1.0f / (float)n, lc, lt, grad, loss);
+}
+
 void launch_l2_loss_grad(const float* img, const float* target, int64_t n, float scale, float* grad, float* loss,
                          cudaStream_t s) {
   cudaMemsetAsync(loss, 0, sizeof(float), s);

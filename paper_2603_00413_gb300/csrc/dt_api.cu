@@ -39,6 +39,8 @@ void launch_dump(const void* ws, unsigned long long cap, int32_t* si, float* sf,
                  cudaStream_t s);
 void launch_closest_hit(const void* bvh, int32_t nf, const float* o, const float* d, const int32_t* src, int32_t n,
                         float tmin, int32_t* tri, float* tbb, cudaStream_t s);
+void launch_paper_loss_grad(const float* img, const float* target, int64_t n, float lc, float lt, float* grad,
+                            float* loss, cudaStream_t s);
 void launch_l2_loss_grad(const float* img, const float* target, int64_t n, float scale, float* grad, float* loss,
                          cudaStream_t s);
 
@@ -490,6 +492,14 @@ dt_status dt_l2_loss_grad(const float* d_img, const float* d_target, int64_t n, 
   if (!d_img || !d_target || !d_grad || !d_loss || n < 0) return set_error(DT_ERR_INVALID_ARG, "bad argument");
   launch_l2_loss_grad(d_img, d_target, n, scale, d_grad, d_loss, (cudaStream_t)stream);
   return check_launch("dt_l2_loss_grad");
+}
+
+dt_status dt_paper_loss_grad(const float* d_img, const float* d_target, int64_t n_pix, float lambda_color,
+                             float lambda_tone, float* d_grad, float* d_loss, dt_stream stream) {
+  if (!d_loss || n_pix < 0 || (n_pix > 0 && (!d_img || !d_target || !d_grad)))
+    return set_error(DT_ERR_INVALID_ARG, "bad argument");
+  launch_paper_loss_grad(d_img, d_target, n_pix, lambda_color, lambda_tone, d_grad, d_loss, (cudaStream_t)stream);
+  return check_launch("dt_paper_loss_grad");
 }
 
 dt_status dt_closest_hit(const void* d_bvh, int32_t nf, const float* d_o, const float* d_d, const int32_t* d_src,
