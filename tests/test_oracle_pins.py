@@ -692,3 +692,109 @@ def test_paper_losses_gradient_matches_central_differences():
         m[idx] -= eps
         fd[idx] = (O.paper_losses(p, c, 0.8, 1.7)[0] - O.paper_losses(m, c, 0.8, 1.7)[0]) / (2 * eps)
     np.testing.assert_allclose(g, fd, rtol=1e-6, atol=1e-9)
+
+
+# ---------------------------------------------------------------------------
+# the step after the gradient (App. A): Laplacian, large-steps solve,
+# AdamUniform, L_edge
+# ---------------------------------------------------------------------------
+from oracle import mesh_update as MU  # noqa: E402
+
+
+def _octahedron():
+    V = np.array([[1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]], np.float64)
+    F = np.array([(sx, sy, sz) for sx in (0, 1) for sy in (2, 3) for sz in (4, 5)], np.int64)
+    a, b, c = V[F[:, 0]], V[F[:, 1]], V[F[:, 2]]
+    flip = np.einsum("ij,ij->i", np.cross(b - a, c - a), a + b + c) < 0
+    F[flip] = F[flip][:, [0, 2, 1]]
+    return V, F
+
+
+def _tetrahedron():
+    V = np.array([[1, 1, 1], [1, -1, -1], [-1, 1, -1], [-1, -1, 1]], np.float64)
+    F = np.array([[0, 1, 2], [0, 3, 1], [0, 2, 3], [1, 3, 2]], np.int64)
+    a, b, c = V[F[:, 0]], V[F[:, 1]], V[F[:, 2]]
+    flip = np.einsum("ij,ij->i", np.cross(b - a, c - a), a + b + c) < 0
+    F[flip] = F[flip][:, [0, 2, 1]]
+    return V, F
+
+
+def test_laplacian_of_regular_solids_and_euler():
+    """Degrees 5 (icosahedron), 4 (octahedron), 3 (tetrahedron); rows sum to
+    zero; symmetric; a closed genus-0 mesh has V - E + F = 2, E = 3F/2."""
+    for (V, F), deg, ne in [(S.icosphere(0), 5, 30), (_octahedron(), 4, 12), (_tetrahedron(), 3, 6)]:
+        nv = len(V)
+        L = MU.laplacian(F, nv)
+        assert len(MU.edges(F)) == ne
+        np.testing.assert_array_equal(L.diagonal(), np.full(nv, deg))
+        np.testing.assert_allclose(np.asarray(L.sum(axis=1)).ravel(), 0.0)
+        assert abs(L - L.T).max() == 0
+    V, F = S.icosphere(3)
+    assert len(V) - len(MU.edges(F)) + len(F) == 2 and 2 * len(MU.edges(F)) == 3 * len(F)
+
+
+def test_smooth_solve_keeps_constants_and_the_mean():
+    """(I + lam L)^-1 fixes constant fields (L 1 = 0), keeps the mean of any
+    field (1^T L = 0), is the identity at lam = 0 and shrinks the rest
+    (eigenvalues 1 / (1 + lam mu) <= 1)."""
+    V, F = S.icosphere(2)
+    nv = len(V)
+    rng = np.random.default_rng(81)
+    c = np.array([0.3, -1.2, 2.0])
+    np.testing.assert_allclose(MU.smooth_solve(F, nv, 7.0, np.tile(c, (nv, 1))), np.tile(c, (nv, 1)), rtol=1e-12)
+    b = rng.normal(size=(nv, 3))
+    x = MU.smooth_solve(F, nv, 7.0, b)
+    np.testing.assert_allclose(x.mean(axis=0), b.mean(axis=0), rtol=1e-10, atol=1e-13)
+    assert np.linalg.norm(x - x.mean(axis=0)) < np.linalg.norm(b - b.mean(axis=0))
+    np.testing.assert_allclose(MU.smooth_solve(F, nv, 0.0, b), b, rtol=1e-14)
+
+
+def test_adam_uniform_constant_gradient_closed_form():
+    """With the same gradient every step the bias-corrected moments are g and
+    max g^2, so every step is lr g / (max |g| + eps)."""
+    rng = np.random.default_rng(82)
+    g = rng.normal(size=(40, 3))
+    st = None
+    for _ in range(5):
+        step, st = MU.adam_uniform(st, g, lr=0.01)
+        np.testing.assert_allclose(step, 0.01 * g / (np.abs(g).max() + 1e-8), rtol=1e-12)
+
+
+def test_large_steps_update_translates_under_a_constant_gradient():
+    """A constant gradient c is a fixed point of the solve, so the update is
+    the translation -lr c / (max |c| + eps) of every vertex."""
+    V, F = S.icosphere(2)
+    V = V.astype(np.float64)
+    c = np.array([0.5, -2.0, 1.0])
+    V1, st = MU.large_steps_update(F, V, np.tile(c, (len(V), 1)), None, lam=12.0, lr=0.01)
+    np.testing.assert_allclose(V1, V - 0.01 * c / (2.0 + 1e-8), rtol=1e-10, atol=1e-12)
+
+
+def test_edge_loss_closed_forms():
+    """Unit vertex normals of a regular solid are radial: adjacent octahedron
+    vertices are 90 degrees apart (each edge (1 - 0)^2 = 1), adjacent
+    tetrahedron vertices have cos = -1/3 (each edge (4/3)^2 = 16/9); a flat
+    patch has one normal (0)."""
+    V, F = _octahedron()
+    assert MU.edge_loss(V, F)[0] == pytest.approx(1.0, abs=1e-14)
+    V, F = _tetrahedron()
+    assert MU.edge_loss(V, F)[0] == pytest.approx(16.0 / 9.0, rel=1e-13)
+    P = np.array([[x, y, 0.0] for y in range(4) for x in range(4)])
+    F = np.array([[y * 4 + x, y * 4 + x + 1, (y + 1) * 4 + x] for y in range(3) for x in range(3)] +
+                 [[y * 4 + x + 1, (y + 1) * 4 + x + 1, (y + 1) * 4 + x] for y in range(3) for x in range(3)])
+    assert MU.edge_loss(P, F)[0] == pytest.approx(0.0, abs=1e-28)
+
+
+def test_edge_loss_gradient_matches_central_differences():
+    V, F = S.icosphere(1)
+    rng = np.random.default_rng(83)
+    V = V.astype(np.float64) * (1.0 + 0.1 * rng.uniform(size=(len(V), 1)))
+    _, g = MU.edge_loss(V, F)
+    eps = 1e-6
+    fd = np.zeros_like(V)
+    for idx in np.ndindex(V.shape):
+        p, m = V.copy(), V.copy()
+        p[idx] += eps
+        m[idx] -= eps
+        fd[idx] = (MU.edge_loss(p, F)[0] - MU.edge_loss(m, F)[0]) / (2 * eps)
+    np.testing.assert_allclose(g, fd, rtol=1e-6, atol=1e-9)
