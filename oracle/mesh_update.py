@@ -29,10 +29,12 @@ import scipy.sparse.linalg as spl
 
 
 def edges(F) -> np.ndarray:
-    """Distinct undirected edges (i < j) of the triangles F, sorted."""
+    """Distinct undirected edges (i < j) of the triangles F, sorted; a face
+    with a repeated vertex contributes no edge from a vertex to itself."""
     F = np.asarray(F, np.int64)
     e = np.concatenate([F[:, [0, 1]], F[:, [1, 2]], F[:, [2, 0]]])
     e = np.sort(e, axis=1)
+    e = e[e[:, 0] != e[:, 1]]
     return np.unique(e, axis=0)
 
 

@@ -798,3 +798,9 @@ def test_edge_loss_gradient_matches_central_differences():
         m[idx] -= eps
         fd[idx] = (MU.edge_loss(p, F)[0] - MU.edge_loss(m, F)[0]) / (2 * eps)
     np.testing.assert_allclose(g, fd, rtol=1e-6, atol=1e-9)
+
+
+def test_edges_ignore_repeated_vertices_and_faces():
+    """A repeated face adds no edge and a face (a, a, b) adds only {a, b}."""
+    F = np.array([[0, 1, 2], [0, 1, 2], [3, 3, 1]])
+    np.testing.assert_array_equal(MU.edges(F), [[0, 1], [0, 2], [1, 2], [1, 3]])
