@@ -358,6 +358,54 @@ dt_status dt_paper_loss_grad(const float* d_img, const float* d_target, int64_t 
                              float lambda_tone, float* d_grad, float* d_loss, dt_stream stream);
 
 /* ------------------------------------------------------------------------
+ * The step after the gradient (App. A): the paper optimises the mesh with
+ * AdamUniform (the optimiser of Nicolet et al. 2021, "Large Steps in
+ * Inverse Rendering of Geometry", learning rate 1e-3) and regularises it
+ * with the edge term L_edge.
+ *
+ * Topology: the distinct neighbours of every vertex of a triangle mesh in
+ * CSR form, built on the device.  dt_topology_size gives the bytes of the
+ * caller buffer (256-byte aligned) for nv vertices and nf triangles;
+ * dt_build_topology fills it (indices outside [0, nv) and self-pairs are
+ * ignored); dt_topology_info copies the number of distinct edges and the
+ * largest neighbour count to the host (synchronising) and, when row/col are
+ * given, the device pointers of the CSR arrays (int32 row[nv + 1], col[2 E]).
+ *
+ * M = I + lambda L with L = D - A the graph Laplacian of those edges
+ * (uniform weights).  dt_smooth_solve solves M x = b for b, x float[nv][3]
+ * (x holds the start on entry) by conjugate gradients with the diagonal as
+ * preconditioner, `iters` iterations, all scalars on the device; scratch
+ * of dt_smooth_scratch_size bytes.
+ *
+ * dt_large_steps_update: one mesh update.  u = M V; g_u = M^-1 dJ/dV (the
+ * matrix is symmetric); AdamUniform on u: m = beta1 m + (1 - beta1) g_u,
+ * v = beta2 v + (1 - beta2) max_i g_u,i^2 (one second moment for all
+ * coordinates), u -= lr (m / (1 - beta1^t)) / (sqrt(v / (1 - beta2^t)) +
+ * eps); then V = M^-1 u (started from the old V).  d_V float[nv][3] is
+ * updated in place; d_state (state_bytes, zeroed by the caller for a fresh
+ * optimiser) carries m, v and t between calls; d_scratch of scratch_bytes.
+ *
+ * dt_edge_loss_grad: L_edge = (1/|E|) sum over distinct edges {i, j} of
+ * (1 - n_i . n_j)^2, n the unit vertex normals of d_N (Eq. 13's normals,
+ * dt_vertex_normals); d_loss float[1] and d_grad_N = dL_edge/dN float[nv][3]
+ * are overwritten (dt_vertex_normals_backward takes it to the vertices).
+ * ------------------------------------------------------------------------ */
+dt_status dt_topology_size(int32_t nv, int32_t nf, size_t* bytes);
+dt_status dt_build_topology(const int32_t* d_F, int32_t nf, int32_t nv, void* d_topo, size_t topo_bytes,
+                            dt_stream stream);
+dt_status dt_topology_info(const void* d_topo, int32_t nv, int32_t nf, int64_t* n_edges, int32_t* max_degree,
+                           const int32_t** d_row, const int32_t** d_col, dt_stream stream);
+dt_status dt_smooth_scratch_size(int32_t nv, int32_t iters, size_t* bytes);
+dt_status dt_smooth_solve(const void* d_topo, int32_t nv, int32_t nf, float lambda, const float* d_b, float* d_x,
+                          int32_t iters, void* d_scratch, size_t scratch_bytes, dt_stream stream);
+dt_status dt_large_steps_sizes(int32_t nv, int32_t iters, size_t* state_bytes, size_t* scratch_bytes);
+dt_status dt_large_steps_update(const void* d_topo, int32_t nv, int32_t nf, float lambda, float lr, float beta1,
+                                float beta2, float eps, int32_t iters, float* d_V, const float* d_grad_V,
+                                void* d_state, void* d_scratch, size_t scratch_bytes, dt_stream stream);
+dt_status dt_edge_loss_grad(const void* d_topo, int32_t nv, int32_t nf, const float* d_N, float* d_grad_N,
+                            float* d_loss, dt_stream stream);
+
+/* ------------------------------------------------------------------------
  * Launch and scheduling knobs of the kernels (process-wide; a call takes
  * the values current when it is made).  The traversal is persistent: each
  * lane carries one ray, a warp runs trace_steps node visits per round and

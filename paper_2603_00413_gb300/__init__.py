@@ -132,6 +132,17 @@ _PROTOS = {
                                            c_int64, c_void_p]),
     "dt_l2_loss_grad": (c_int32, [c_void_p, c_void_p, c_int64, c_float, c_void_p, c_void_p, c_void_p]),
     "dt_paper_loss_grad": (c_int32, [c_void_p, c_void_p, c_int64, c_float, c_float, c_void_p, c_void_p, c_void_p]),
+    "dt_topology_size": (c_int32, [c_int32, c_int32, POINTER(c_size_t)]),
+    "dt_build_topology": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, c_size_t, c_void_p]),
+    "dt_topology_info": (c_int32, [c_void_p, c_int32, c_int32, POINTER(c_int64), POINTER(c_int32),
+                                   POINTER(c_void_p), POINTER(c_void_p), c_void_p]),
+    "dt_smooth_scratch_size": (c_int32, [c_int32, c_int32, POINTER(c_size_t)]),
+    "dt_smooth_solve": (c_int32, [c_void_p, c_int32, c_int32, c_float, c_void_p, c_void_p, c_int32, c_void_p, c_size_t,
+                                  c_void_p]),
+    "dt_large_steps_sizes": (c_int32, [c_int32, c_int32, POINTER(c_size_t), POINTER(c_size_t)]),
+    "dt_large_steps_update": (c_int32, [c_void_p, c_int32, c_int32, c_float, c_float, c_float, c_float, c_float,
+                                        c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "dt_edge_loss_grad": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
     "dt_profile_enable": (c_int32, [c_int32]),
     "dt_get_tuning": (c_int32, [POINTER(DtTuning)]),
     "dt_set_tuning": (c_int32, [POINTER(DtTuning)]),
@@ -559,6 +570,93 @@ def paper_loss_grad(img, target, lambda_color: float = 1.0, lambda_tone: float =
     _check(load_library().dt_paper_loss_grad(_ptr(img), _ptr(target), n, float(lambda_color), float(lambda_tone),
                                              _ptr(grad), _ptr(loss), _stream(stream)))
     return grad, loss
+
+
+# ---------------------------------------------------------------------------
+# the step after the gradient (App. A)
+# ---------------------------------------------------------------------------
+class Topology:
+    """The distinct neighbours of every vertex of a triangle mesh (CSR, on
+    the device), for the large-steps update and L_edge."""
+
+    def __init__(self, F, nv: int, stream=None):
+        _need(F, torch.int32, (3,), "F")
+        self.nv, self.nf = int(nv), F.shape[0]
+        b = c_size_t()
+        lib = load_library()
+        _check(lib.dt_topology_size(self.nv, self.nf, ctypes.byref(b)))
+        self.bytes = b.value
+        self._raw, self.buf = _aligned_empty(self.bytes, F.device)
+        _check(lib.dt_build_topology(_ptr(F), self.nf, self.nv, _ptr(self.buf), self.bytes, _stream(stream)))
+        self._info = None
+
+    def info(self, stream=None):
+        """(distinct edges, largest neighbour count, row [nv + 1], col
+        [2 edges]) -- synchronises once."""
+        if self._info is None:
+            ne, md = c_int64(), c_int32()
+            rp, cp = c_void_p(), c_void_p()
+            _check(load_library().dt_topology_info(_ptr(self.buf), self.nv, self.nf, ctypes.byref(ne),
+                                                   ctypes.byref(md), ctypes.byref(rp), ctypes.byref(cp),
+                                                   _stream(stream)))
+            base = self.buf.data_ptr()
+            row = self.buf[rp.value - base: rp.value - base + 4 * (self.nv + 1)].view(torch.int32)
+            col = self.buf[cp.value - base: cp.value - base + 8 * ne.value].view(torch.int32)
+            self._info = (ne.value, md.value, row, col)
+        return self._info
+
+
+def smooth_solve(topo: Topology, lam: float, b, x=None, iters: int = 100, stream=None):
+    """x = (I + lam L)^-1 b (b [nv, 3]; x the start, overwritten) by
+    preconditioned conjugate gradients on the device."""
+    _need(b, torch.float32, (3,), "b")
+    x = torch.zeros_like(b) if x is None else x
+    s = c_size_t()
+    lib = load_library()
+    _check(lib.dt_smooth_scratch_size(topo.nv, int(iters), ctypes.byref(s)))
+    _, scratch = _aligned_empty(s.value, b.device)
+    _check(lib.dt_smooth_solve(_ptr(topo.buf), topo.nv, topo.nf, float(lam), _ptr(b), _ptr(x), int(iters),
+                               _ptr(scratch), s.value, _stream(stream)))
+    return x
+
+
+class LargeStepsOptimizer:
+    """The mesh update of the tracer stage: AdamUniform on u = (I + lam L) V
+    with the gradient taken through the same matrix (Nicolet et al. 2021;
+    learning rate 1e-3 in App. A).  step(dJ/dV) updates V in place."""
+
+    def __init__(self, V, F, lam: float = 10.0, lr: float = 1e-3, betas=(0.9, 0.999), eps: float = 1e-8,
+                 iters: int = 100, topo: Topology = None):
+        _need(V, torch.float32, (3,), "V")
+        self.V, self.F = V, F
+        self.topo = topo if topo is not None else Topology(F, V.shape[0])
+        self.lam, self.lr, self.betas, self.eps, self.iters = float(lam), float(lr), betas, float(eps), int(iters)
+        st, sc = c_size_t(), c_size_t()
+        _check(load_library().dt_large_steps_sizes(V.shape[0], self.iters, ctypes.byref(st), ctypes.byref(sc)))
+        self._sraw, self.state = _aligned_empty(st.value, V.device)
+        self.state.zero_()
+        self._craw, self.scratch = _aligned_empty(sc.value, V.device)
+
+    def step(self, grad, stream=None):
+        _need(grad, torch.float32, (3,), "grad")
+        _check(load_library().dt_large_steps_update(
+            _ptr(self.topo.buf), self.topo.nv, self.topo.nf, self.lam, self.lr, float(self.betas[0]),
+            float(self.betas[1]), self.eps, self.iters, _ptr(self.V), _ptr(grad.contiguous()), _ptr(self.state),
+            _ptr(self.scratch), self.scratch.numel(), _stream(stream)))
+        return self.V
+
+
+def edge_loss_grad(V, F, topo: Topology = None, stream=None):
+    """L_edge of App. A and its gradient with respect to the vertices
+    (through the unit normals, Eq. 13 and the face cross products): returns
+    (loss [1], dV [nv, 3])."""
+    topo = topo if topo is not None else Topology(F, V.shape[0])
+    N = vertex_normals(V, F, stream=stream)
+    dN = torch.empty_like(N)
+    loss = torch.empty(1, dtype=torch.float32, device=V.device)
+    _check(load_library().dt_edge_loss_grad(_ptr(topo.buf), topo.nv, topo.nf, _ptr(N), _ptr(dN), _ptr(loss),
+                                            _stream(stream)))
+    return loss, vertex_normals_backward(V, F, dN, stream=stream)
 
 
 def measure_l2_read_bandwidth(nbytes: int = 32 << 20, iters: int = 50, device=None, stream=None) -> float:

@@ -18,7 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(HERE, "libdifftrans.so")
-SOURCES = ["dt_api.cu", "dt_bvh.cu", "dt_trace.cu", "dt_order.cu", "dt_adjoint.cu", "dt_noalloc.cu", "dt_tools.cu"]
+SOURCES = ["dt_api.cu", "dt_bvh.cu", "dt_trace.cu", "dt_order.cu", "dt_adjoint.cu", "dt_mesh.cu", "dt_noalloc.cu",
+           "dt_tools.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I", INCLUDE]

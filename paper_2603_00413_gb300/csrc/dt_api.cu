@@ -43,6 +43,20 @@ void launch_paper_loss_grad(const float* img, const float* target, int64_t n, fl
                             float* loss, cudaStream_t s);
 void launch_l2_loss_grad(const float* img, const float* target, int64_t n, float scale, float* grad, float* loss,
                          cudaStream_t s);
+size_t topology_bytes(int32_t nv, int32_t nf);
+void launch_build_topology(const int32_t* F, int32_t nf, int32_t nv, void* topo, cudaStream_t s);
+void read_topology_header(const void* topo, int32_t* nnz, int32_t* max_deg, cudaStream_t s);
+void topology_csr(const void* topo, int32_t nv, int32_t nf, const int32_t** row, const int32_t** col);
+size_t smooth_scratch_bytes(int32_t nv, int32_t iters);
+void launch_smooth_solve(const void* topo, int32_t nv, int32_t nf, float lam, const float* b, float* x, int iters,
+                         void* scratch, cudaStream_t s);
+size_t large_steps_state_bytes(int32_t nv);
+size_t large_steps_scratch_bytes(int32_t nv, int32_t iters);
+void launch_large_steps_update(const void* topo, int32_t nv, int32_t nf, float lam, float lr, float b1, float b2,
+                               float eps, int iters, float* V, const float* grad, void* state, void* scratch,
+                               cudaStream_t s);
+void launch_edge_loss_grad(const void* topo, int32_t nv, int32_t nf, const float* N, float* dN, float* loss,
+                           cudaStream_t s);
 
 // Launch and scheduling knobs (dt_set_tuning); process-wide.  Node visits
 // per round 192, refill at 8 idle lanes, 5 traversal and 4 shading CTAs per
@@ -492,6 +506,87 @@ dt_status dt_l2_loss_grad(const float* d_img, const float* d_target, int64_t n, 
   if (!d_img || !d_target || !d_grad || !d_loss || n < 0) return set_error(DT_ERR_INVALID_ARG, "bad argument");
   launch_l2_loss_grad(d_img, d_target, n, scale, d_grad, d_loss, (cudaStream_t)stream);
   return check_launch("dt_l2_loss_grad");
+}
+
+
+static dt_status check_mesh(int32_t nv, int32_t nf) {
+  if (nv < 3 || nf < 1 || (int64_t)nf * 6 > 0x7fffffffll) return set_error(DT_ERR_INVALID_ARG, "need nv >= 3, nf >= 1");
+  return DT_OK;
+}
+
+dt_status dt_topology_size(int32_t nv, int32_t nf, size_t* bytes) {
+  if (!bytes) return set_error(DT_ERR_INVALID_ARG, "NULL pointer");
+  if (dt_status st = check_mesh(nv, nf)) return st;
+  *bytes = topology_bytes(nv, nf);
+  return DT_OK;
+}
+
+dt_status dt_build_topology(const int32_t* d_F, int32_t nf, int32_t nv, void* d_topo, size_t topo_bytes,
+                            dt_stream stream) {
+  if (dt_status st = check_mesh(nv, nf)) return st;
+  if (!d_F || !d_topo || !aligned(d_topo, 256) || topo_bytes < topology_bytes(nv, nf))
+    return set_error(DT_ERR_INVALID_ARG, "bad topology buffer");
+  launch_build_topology(d_F, nf, nv, d_topo, (cudaStream_t)stream);
+  return check_launch("dt_build_topology");
+}
+
+dt_status dt_topology_info(const void* d_topo, int32_t nv, int32_t nf, int64_t* n_edges, int32_t* max_degree,
+                           const int32_t** d_row, const int32_t** d_col, dt_stream stream) {
+  if (dt_status st = check_mesh(nv, nf)) return st;
+  if (!d_topo) return set_error(DT_ERR_INVALID_ARG, "NULL topology");
+  int32_t nnz = 0, md = 0;
+  read_topology_header(d_topo, &nnz, &md, (cudaStream_t)stream);
+  if (n_edges) *n_edges = nnz / 2;
+  if (max_degree) *max_degree = md;
+  const int32_t *row = nullptr, *col = nullptr;
+  topology_csr(d_topo, nv, nf, &row, &col);
+  if (d_row) *d_row = row;
+  if (d_col) *d_col = col;
+  return check_launch("dt_topology_info");
+}
+
+dt_status dt_smooth_scratch_size(int32_t nv, int32_t iters, size_t* bytes) {
+  if (!bytes || nv < 1 || iters < 1) return set_error(DT_ERR_INVALID_ARG, "bad argument");
+  *bytes = smooth_scratch_bytes(nv, iters);
+  return DT_OK;
+}
+
+dt_status dt_smooth_solve(const void* d_topo, int32_t nv, int32_t nf, float lambda, const float* d_b, float* d_x,
+                          int32_t iters, void* d_scratch, size_t scratch_bytes, dt_stream stream) {
+  if (dt_status st = check_mesh(nv, nf)) return st;
+  if (!d_topo || !d_b || !d_x || !d_scratch || iters < 1 || iters > 100000 || !(lambda >= 0.0f) ||
+      scratch_bytes < smooth_scratch_bytes(nv, iters) || !aligned(d_scratch, 256))
+    return set_error(DT_ERR_INVALID_ARG, "bad argument");
+  launch_smooth_solve(d_topo, nv, nf, lambda, d_b, d_x, iters, d_scratch, (cudaStream_t)stream);
+  return check_launch("dt_smooth_solve");
+}
+
+dt_status dt_large_steps_sizes(int32_t nv, int32_t iters, size_t* state_bytes, size_t* scratch_bytes) {
+  if (!state_bytes || !scratch_bytes || nv < 1 || iters < 1) return set_error(DT_ERR_INVALID_ARG, "bad argument");
+  *state_bytes = large_steps_state_bytes(nv);
+  *scratch_bytes = large_steps_scratch_bytes(nv, iters);
+  return DT_OK;
+}
+
+dt_status dt_large_steps_update(const void* d_topo, int32_t nv, int32_t nf, float lambda, float lr, float beta1,
+                                float beta2, float eps, int32_t iters, float* d_V, const float* d_grad_V,
+                                void* d_state, void* d_scratch, size_t scratch_bytes, dt_stream stream) {
+  if (dt_status st = check_mesh(nv, nf)) return st;
+  if (!d_topo || !d_V || !d_grad_V || !d_state || !d_scratch || iters < 1 || iters > 100000 || !(lambda >= 0.0f) ||
+      !(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps > 0.0f) ||
+      scratch_bytes < large_steps_scratch_bytes(nv, iters) || !aligned(d_scratch, 256) || !aligned(d_state, 16))
+    return set_error(DT_ERR_INVALID_ARG, "bad argument");
+  launch_large_steps_update(d_topo, nv, nf, lambda, lr, beta1, beta2, eps, iters, d_V, d_grad_V, d_state, d_scratch,
+                            (cudaStream_t)stream);
+  return check_launch("dt_large_steps_update");
+}
+
+dt_status dt_edge_loss_grad(const void* d_topo, int32_t nv, int32_t nf, const float* d_N, float* d_grad_N,
+                            float* d_loss, dt_stream stream) {
+  if (dt_status st = check_mesh(nv, nf)) return st;
+  if (!d_topo || !d_N || !d_grad_N || !d_loss) return set_error(DT_ERR_INVALID_ARG, "bad argument");
+  launch_edge_loss_grad(d_topo, nv, nf, d_N, d_grad_N, d_loss, (cudaStream_t)stream);
+  return check_launch("dt_edge_loss_grad");
 }
 
 dt_status dt_paper_loss_grad(const float* d_img, const float* d_target, int64_t n_pix, float lambda_color,

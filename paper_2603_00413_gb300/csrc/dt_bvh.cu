@@ -1183,6 +1183,9 @@ static void launch_sah_topology(const float* V, const int32_t* F, int32_t nf, Bv
   k_sah_small<<<grid_for(nf / 2 + 1, 32 * kSahSmallWarps), 32 * kSahSmallWarps, 0, s>>>(S.sah, B);
 }
 
+// Exclusive scan of m entries in place (one CTA; used by the mesh topology).
+void launch_scan_exclusive(uint32_t* a, int32_t m, cudaStream_t s) { k_scan_exclusive<<<1, 1024, 0, s>>>(a, m); }
+
 void launch_build(const float* V, const int32_t* F, int32_t nf, void* bvh, void* scratch, cudaStream_t s) {
   BvhView B = bvh_view(bvh, nf);
   BuildScratch S(scratch, nf);

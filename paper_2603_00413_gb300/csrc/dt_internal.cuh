@@ -384,6 +384,7 @@ __host__ __device__ __forceinline__ uint32_t pcg_hash(uint32_t v) {
 dt_status set_error(dt_status code, const char* fmt, ...);
 dt_status check_launch(const char* what);
 int num_sms();
+void launch_scan_exclusive(uint32_t* a, int32_t m, cudaStream_t s);  // dt_bvh.cu
 
 // Per-kernel event timing (dt_profile_enable).  Scoped: records a start event
 // on construction and a stop event on destruction when profiling is on.
