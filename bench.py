@@ -323,7 +323,9 @@ def large_leg(args, dt, dev):
     vertices perturbed by N(0, 0.001).  One step = BVH rebuild (the tuned
     builder: binned SAH by default) + vertex normals + checkpointed forward
     + loss seed + backward (hits recovered from the children's source
-    triangles).  The same step with the full tape is timed beside it."""
+    triangles).  The same step with the full tape is timed beside it, and
+    the mesh update that closes the loop (L_edge gradient + large-steps
+    AdamUniform, App. A) after them."""
     import torch
     from paper_2603_00413_gb300 import scenes as S
     t0 = time.time()
@@ -396,6 +398,31 @@ def large_leg(args, dt, dev):
                      "levels": stats["level_count"], "loss": float(loss.item())}
         del ws, bws, tape, img, target, grad
         torch.cuda.empty_cache()
+    # the step after the gradient (App. A): L_edge's gradient added to a
+    # vertex gradient and the large-steps AdamUniform update, on a copy of
+    # the mesh; with the checkpointed step it closes the optimisation loop
+    Vc = V.clone()
+    topo = dt.Topology(F, V.shape[0])
+    opt = dt.LargeStepsOptimizer(Vc, F, lam=10.0, lr=1e-3, topo=topo)
+    gV = torch.randn(V.shape, device=dev, generator=torch.Generator(device=dev).manual_seed(9)) * 1e-3
+
+    def update():
+        _, dVe = dt.edge_loss_grad(Vc, F, topo)
+        opt.step(gV + 1e-3 * dVe)
+
+    for _ in range(2):
+        update()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.large_steps):
+        update()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    upd = e0.elapsed_time(e1) / args.large_steps
+    out["mesh_update"] = {"ms": upd, "vertices": int(V.shape[0]), "edges": int(topo.info()[0]),
+                          "cg_iterations_max": opt.iters,
+                          "optimisation_step_ms": out["checkpoint"]["ms_per_step"] + upd}
     return out
 
 

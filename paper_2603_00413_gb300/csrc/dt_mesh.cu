@@ -183,13 +183,27 @@ __device__ __forceinline__ void store3(float* p, float3 v) {
   p[2] = v.z;
 }
 
-// one atomic per warp for each of three column sums
-__device__ __forceinline__ void warp_add3(float* dst, float3 v) {
+// one atomic per CTA for each of three column sums (a warp-level atomic on
+// three addresses from every warp of a large mesh serialises); called by
+// every thread of the CTA after its loop
+__device__ __forceinline__ void block_add3(float* dst, float3 v) {
+  __shared__ float part[3][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
   v = mk(warp_sum(v.x), warp_sum(v.y), warp_sum(v.z));
-  if ((threadIdx.x & 31) == 0) {
-    atomicAdd(dst, v.x);
-    atomicAdd(dst + 1, v.y);
-    atomicAdd(dst + 2, v.z);
+  if (lane == 0) {
+    part[0][wid] = v.x;
+    part[1][wid] = v.y;
+    part[2][wid] = v.z;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    float3 t = lane < nw ? mk(part[0][lane], part[1][lane], part[2][lane]) : mk(0.f, 0.f, 0.f);
+    t = mk(warp_sum(t.x), warp_sum(t.y), warp_sum(t.z));
+    if (lane == 0) {
+      atomicAdd(dst, t.x);
+      atomicAdd(dst + 1, t.y);
+      atomicAdd(dst + 2, t.z);
+    }
   }
 }
 
@@ -236,32 +250,28 @@ static CgView cg_view(void* base, int32_t nv, int32_t iters) {
 // r = b - M x, z = r / diag, p = z, rz[0] = r . z
 __global__ void k_cg_init(const int32_t* __restrict__ row, const int32_t* __restrict__ col, int32_t nv, float lam,
                           const float* __restrict__ b, const float* __restrict__ x, CgView c) {
-  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < ((nv + 31) & ~31); v += gridDim.x * blockDim.x) {
-    float3 acc = mk(0.f, 0.f, 0.f);
-    if (v < nv) {
-      const float3 r = load3(b + 3 * v) - apply_m(row, col, x, lam, v);
-      const float3 z = r * (1.0f / (1.0f + lam * (float)(row[v + 1] - row[v])));
-      store3(c.r + 3 * v, r);
-      store3(c.z + 3 * v, z);
-      store3(c.p + 3 * v, z);
-      acc = mul(r, z);
-    }
-    warp_add3(c.rz, acc);
+  float3 acc = mk(0.f, 0.f, 0.f);
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += gridDim.x * blockDim.x) {
+    const float3 r = load3(b + 3 * v) - apply_m(row, col, x, lam, v);
+    const float3 z = r * (1.0f / (1.0f + lam * (float)(row[v + 1] - row[v])));
+    store3(c.r + 3 * v, r);
+    store3(c.z + 3 * v, z);
+    store3(c.p + 3 * v, z);
+    acc = acc + mul(r, z);
   }
+  block_add3(c.rz, acc);
 }
 
 // Ap = M p, pAp[it] = p . Ap
 __global__ void k_cg_ap(const int32_t* __restrict__ row, const int32_t* __restrict__ col, int32_t nv, float lam,
                         CgView c, int it) {
-  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < ((nv + 31) & ~31); v += gridDim.x * blockDim.x) {
-    float3 acc = mk(0.f, 0.f, 0.f);
-    if (v < nv) {
-      const float3 ap = apply_m(row, col, c.p, lam, v);
-      store3(c.ap + 3 * v, ap);
-      acc = mul(load3(c.p + 3 * v), ap);
-    }
-    warp_add3(c.pap + 3 * it, acc);
+  float3 acc = mk(0.f, 0.f, 0.f);
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += gridDim.x * blockDim.x) {
+    const float3 ap = apply_m(row, col, c.p, lam, v);
+    store3(c.ap + 3 * v, ap);
+    acc = acc + mul(load3(c.p + 3 * v), ap);
   }
+  block_add3(c.pap + 3 * it, acc);
 }
 
 // alpha = rz[it] / pAp[it]; x += alpha p; r -= alpha Ap; z = r / diag;
@@ -269,18 +279,16 @@ __global__ void k_cg_ap(const int32_t* __restrict__ row, const int32_t* __restri
 __global__ void k_cg_step(const int32_t* __restrict__ row, int32_t nv, float lam, float* __restrict__ x, CgView c,
                           int it) {
   const float3 alpha = mk(cg_alpha(c, it, 0), cg_alpha(c, it, 1), cg_alpha(c, it, 2));
-  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < ((nv + 31) & ~31); v += gridDim.x * blockDim.x) {
-    float3 acc = mk(0.f, 0.f, 0.f);
-    if (v < nv) {
-      store3(x + 3 * v, load3(x + 3 * v) + mul(alpha, load3(c.p + 3 * v)));
-      const float3 r = load3(c.r + 3 * v) - mul(alpha, load3(c.ap + 3 * v));
-      const float3 z = r * (1.0f / (1.0f + lam * (float)(row[v + 1] - row[v])));
-      store3(c.r + 3 * v, r);
-      store3(c.z + 3 * v, z);
-      acc = mul(r, z);
-    }
-    warp_add3(c.rz + 3 * (it + 1), acc);
+  float3 acc = mk(0.f, 0.f, 0.f);
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += gridDim.x * blockDim.x) {
+    store3(x + 3 * v, load3(x + 3 * v) + mul(alpha, load3(c.p + 3 * v)));
+    const float3 r = load3(c.r + 3 * v) - mul(alpha, load3(c.ap + 3 * v));
+    const float3 z = r * (1.0f / (1.0f + lam * (float)(row[v + 1] - row[v])));
+    store3(c.r + 3 * v, r);
+    store3(c.z + 3 * v, z);
+    acc = acc + mul(r, z);
   }
+  block_add3(c.rz + 3 * (it + 1), acc);
 }
 
 // beta = rz[it + 1] / rz[it]; p = z + beta p
@@ -350,7 +358,15 @@ __global__ void k_max_sq(const float* __restrict__ g, int64_t n, AdamScalars* sc
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     mx = fmaxf(mx, g[i] * g[i]);
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, o));
-  if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int*>(&sc->max_g2), __float_as_int(mx));
+  __shared__ float part[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) part[wid] = mx;
+  __syncthreads();
+  if (wid == 0) {  // one atomic per CTA
+    mx = lane < (int)((blockDim.x + 31) >> 5) ? part[lane] : 0.f;
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, o));
+    if (lane == 0) atomicMax(reinterpret_cast<int*>(&sc->max_g2), __float_as_int(mx));
+  }
 }
 
 // m = b1 m + (1 - b1) g; v = b2 v + (1 - b2) max g^2 (one thread does v);
