@@ -313,7 +313,7 @@ __device__ __forceinline__ ClosestHit closest_hit(const float4* __restrict__ nod
 // kBatch = false: one scene, whose entry E0 arrives as a kernel parameter
 // (uniform constant-bank reads); true: each ray looks its scene up.
 constexpr int kTraceClaim = 64;  // segments a warp claims from the level cursor at once
-constexpr int kLeafEvery = 4;    // node visits between the warp's batched triangle tests
+constexpr int kLeafEvery = 6;    // node visits between the warp's batched triangle tests
 
 template <int kMinBlocks, int kWidth, bool kBatch>
 __global__ void __launch_bounds__(256, kMinBlocks) k_trace(WsView W, int k, int steps, int refill,
