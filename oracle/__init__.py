@@ -84,9 +84,13 @@ def _load():
     return _lib
 
 
+MAX_HASH_LEVELS = 16
+
+
 class _OrcMedium(ctypes.Structure):
     _fields_ = [("mu", ctypes.c_void_p), ("n", ctypes.c_int * 3), ("lo", ctypes.c_double * 3),
-                ("hi", ctypes.c_double * 3), ("step", ctypes.c_double)]
+                ("hi", ctypes.c_double * 3), ("step", ctypes.c_double), ("levels", ctypes.c_int),
+                ("log2_table", ctypes.c_int), ("res", ctypes.c_int * MAX_HASH_LEVELS)]
 
 
 def _d(a):
@@ -94,15 +98,27 @@ def _d(a):
 
 
 def _medium(medium):
-    """(struct, keep-alive array) for a medium dict(mu [nz, ny, nx, 3], lo
-    (3,), hi (3,), step) or (None, None)."""
+    """(struct, keep-alive array) for a medium, or (None, None).  A dense
+    grid is dict(mu [nz, ny, nx, 3], lo (3,), hi (3,), step); a hash texture
+    is dict(table [L, T, 3] with T a power of two, res (L,) nodes per axis
+    of each level, lo, hi, step)."""
     if medium is None:
         return None, None
-    mu = _d(medium["mu"])
-    assert mu.ndim == 4 and mu.shape[3] == 3 and min(mu.shape[:3]) >= 2
     m = _OrcMedium()
+    if "table" in medium:
+        mu = _d(medium["table"])
+        res = [int(r) for r in medium["res"]]
+        L, T = mu.shape[0], mu.shape[1]
+        assert mu.ndim == 3 and mu.shape[2] == 3 and 1 <= L <= MAX_HASH_LEVELS and len(res) == L
+        assert T >= 2 and T & (T - 1) == 0 and min(res) >= 2
+        m.levels, m.log2_table = L, T.bit_length() - 1
+        for l, r in enumerate(res):
+            m.res[l] = r
+    else:
+        mu = _d(medium["mu"])
+        assert mu.ndim == 4 and mu.shape[3] == 3 and min(mu.shape[:3]) >= 2
+        m.n[0], m.n[1], m.n[2] = mu.shape[2], mu.shape[1], mu.shape[0]
     m.mu = mu.ctypes.data_as(ctypes.c_void_p)
-    m.n[0], m.n[1], m.n[2] = mu.shape[2], mu.shape[1], mu.shape[0]
     for a in range(3):
         m.lo[a] = float(medium["lo"][a])
         m.hi[a] = float(medium["hi"][a])
@@ -115,12 +131,13 @@ def _mp(m):
 
 
 def medium_depth(medium, o, d, t) -> np.ndarray:
-    """Optical depth of an absorption grid over segments o + s d, s in
-    [0, t] (Eq. 11 with the spatially varying rate of the grid): steps of
-    length `step` from the start, the last one partial, each sampled at its
-    midpoint with trilinear interpolation of the node values (positions
-    clamped to the grid's box).  medium = dict(mu [nz, ny, nx, 3], lo, hi,
-    step).  Returns [n, 3]."""
+    """Optical depth of an absorption field over segments o + s d, s in
+    [0, t] (Eq. 11 with the spatially varying rate): steps of length `step`
+    from the start, the last one partial, each sampled at its midpoint with
+    trilinear interpolation of the node values (positions clamped to the
+    box); a hash texture sums its levels' interpolations (Sec. 3.3's 3D
+    texture after Instant-NGP).  medium: a dense grid or a hash texture (see
+    _medium).  Returns [n, 3]."""
     o, d = _d(o).reshape(-1, 3), _d(d).reshape(-1, 3)
     t = _d(t).reshape(-1)
     out = np.zeros_like(o)
@@ -278,7 +295,8 @@ def render_jvp(V, F, ior, sigma, env, cam, max_depth: int, tV=None, tior=None, t
                medium=None, tmu=None):
     """Forward-mode derivative of the FP64 render along ntan directions at
     fixed events.  tV: [ntan, nv, 3], tior: [ntan], tsigma: [ntan, 3], tmu:
-    [ntan, nz, ny, nx, 3] (tangents of the absorption grid's node values).
+    [ntan, nz, ny, nx, 3] (tangents of the absorption grid's node values;
+    [ntan, L, T, 3] for a hash texture's table entries).
     Returns (img [H,W,3], dimg [ntan,H,W,3])."""
     V, F, ior, sigma, env, c = _common(V, F, ior, sigma, env, cam)
     m, keep = _medium(medium)

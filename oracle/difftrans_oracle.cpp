@@ -41,6 +41,15 @@
 //    steps of length h (the last one partial: t - m h, m = floor(t / h), at
 //    most 8192 full steps), each contributing G at its midpoint times its
 //    length.  It applies where sigma does: on interior segments.
+//  * G may instead be a multi-resolution hash texture (the "differentiable
+//    3D texture" of Sec. 3.3, after Instant-NGP, Mueller et al. 2022): L
+//    lattices over the same box with n_l nodes per axis, each level's values
+//    in its own table of T entries, the corner (i, j, k) of level l stored at
+//    ((k n_l + j) n_l + i) when n_l^3 <= T and otherwise at Instant-NGP's
+//    spatial hash (i * 1 XOR j * 2654435761 XOR k * 805459861, in 32-bit
+//    unsigned arithmetic) modulo T; G is the sum over the levels of their
+//    trilinear interpolations, each with three features, the rates
+//    themselves (no decoder network).
 //  * self-intersection: the triangle a ray leaves from is skipped and hits need
 //    t > t_min.  Ties on t go to the smaller triangle id.
 //  * environment: equirectangular, y up, bilinear, wrap in u, clamp in v.
@@ -326,13 +335,21 @@ inline void camera_ray(const double* cam, int width, int height, double sx, doub
 // ---------------------------------------------------------------------------
 // the recursive tracer (Sec. 3.4 steps 1-5)
 // ---------------------------------------------------------------------------
-// Dense absorption grid (Eq. 11 with a spatially varying rate): node values
-// mu[((k ny + j) nx + i) 3 + c] at lo + (i, j, k) (hi - lo) / (n - 1).
+// Absorption field (Eq. 11 with a spatially varying rate) over the box
+// [lo, hi].  levels == 0: a dense grid, node values mu[((k ny + j) nx + i) 3
+// + c] at lo + (i, j, k) (hi - lo) / (n - 1).  levels = L >= 1: a hash
+// texture whose level l has res[l] nodes per axis (node (i, j, k) at lo +
+// (i, j, k) (hi - lo) / (res[l] - 1)) and the table mu[(l T + e) 3 + c],
+// T = 2^log2_table, e the corner's entry (dense or hashed, see the header).
+constexpr int kMaxHashLevels = 16;
 struct orc_medium {
   const double* mu;
   int n[3];
   double lo[3], hi[3];
   double step;
+  int levels;
+  int log2_table;
+  int res[kMaxHashLevels];
 };
 
 constexpr long kMaxMediumSteps = 8192;
@@ -350,28 +367,58 @@ struct Scene {
   int env_w = 0, env_h = 0;
   int max_depth = 0;
   double t_min = 0.0;
-  // absorption grid (has_medium false: sigma only)
+  // absorption field (has_medium false: sigma only)
   bool has_medium = false;
   int gn[3] = {0, 0, 0};
   double glo[3] = {0, 0, 0}, ghi[3] = {0, 0, 0}, gstep = 0.0;
-  std::vector<T> gmu;  // [nz][ny][nx][3]
+  int glevels = 0;                   // 0: dense grid; L: hash texture
+  uint32_t gtable = 0;               // hash texture: entries per level
+  int gres[kMaxHashLevels] = {0};    // hash texture: nodes per axis per level
+  std::vector<T> gmu;  // dense: [nz][ny][nx][3]; hash texture: [L][T][3]
 };
 
-// G(x): trilinear interpolation of the grid's node values at x, each
-// coordinate clamped to the box (the clamped coordinate is a constant, so
-// it carries no derivative).
+// Instant-NGP's spatial hash of an integer lattice point (Mueller et al.
+// 2022, Eq. 4, d = 3): XOR of the coordinates times the primes 1,
+// 2654435761 and 805459861, wrapping in 32 bits; the caller reduces it
+// modulo the table size.
+inline uint32_t ingp_hash(uint32_t i, uint32_t j, uint32_t k) {
+  return (i * 1u) ^ (j * 2654435761u) ^ (k * 805459861u);
+}
+
 template <class T>
-V3<T> grid_eval(const Scene<T>& S, const V3<T>& x) {
+void set_medium(const orc_medium& M, Scene<T>& S) {
+  S.has_medium = true;
+  for (int a = 0; a < 3; ++a) { S.gn[a] = M.n[a]; S.glo[a] = M.lo[a]; S.ghi[a] = M.hi[a]; }
+  S.gstep = M.step;
+  S.glevels = M.levels;
+  size_t nn;
+  if (M.levels > 0) {
+    S.gtable = 1u << M.log2_table;
+    for (int l = 0; l < M.levels; ++l) S.gres[l] = M.res[l];
+    nn = (size_t)M.levels * S.gtable * 3;
+  } else {
+    nn = (size_t)M.n[0] * M.n[1] * M.n[2] * 3;
+  }
+  S.gmu.resize(nn);
+  for (size_t i = 0; i < nn; ++i) S.gmu[i] = T(M.mu[i]);
+}
+
+// Trilinear interpolation at x of one lattice of n[0] x n[1] x n[2] nodes
+// over the box, each coordinate clamped to the box (the clamped coordinate
+// is a constant, so it carries no derivative).  entry(i, j, k) is the index
+// of node (i, j, k)'s three values in S.gmu (divided by 3).
+template <class T, class Entry>
+V3<T> lattice_eval(const Scene<T>& S, const int n[3], Entry entry, const V3<T>& x) {
   const T xs[3] = {x.x, x.y, x.z};
   T f[3];
   int i0[3];
   for (int a = 0; a < 3; ++a) {
-    const double span = (double)(S.gn[a] - 1);
+    const double span = (double)(n[a] - 1);
     T u = (xs[a] - S.glo[a]) / (S.ghi[a] - S.glo[a]) * span;
     if (val(u) < 0.0) u = T(0.0);
     if (val(u) > span) u = T(span);
     int i = (int)std::floor(val(u));
-    if (i > S.gn[a] - 2) i = S.gn[a] - 2;
+    if (i > n[a] - 2) i = n[a] - 2;
     i0[a] = i;
     f[a] = u - (double)i;
   }
@@ -380,9 +427,33 @@ V3<T> grid_eval(const Scene<T>& S, const V3<T>& x) {
     for (int dy = 0; dy < 2; ++dy)
       for (int dx = 0; dx < 2; ++dx) {
         const T w = (dx ? f[0] : 1.0 - f[0]) * (dy ? f[1] : 1.0 - f[1]) * (dz ? f[2] : 1.0 - f[2]);
-        const size_t node = ((size_t)(i0[2] + dz) * S.gn[1] + (i0[1] + dy)) * S.gn[0] + (i0[0] + dx);
+        const size_t node = entry(i0[0] + dx, i0[1] + dy, i0[2] + dz);
         acc = acc + V3<T>(S.gmu[3 * node], S.gmu[3 * node + 1], S.gmu[3 * node + 2]) * w;
       }
+  return acc;
+}
+
+// G(x): the dense grid's trilinear interpolation, or the sum over the hash
+// texture's levels of theirs.
+template <class T>
+V3<T> grid_eval(const Scene<T>& S, const V3<T>& x) {
+  if (S.glevels == 0) {
+    const int nx = S.gn[0], ny = S.gn[1];
+    return lattice_eval(S, S.gn, [&](int i, int j, int k) { return ((size_t)k * ny + j) * nx + i; }, x);
+  }
+  V3<T> acc;
+  const uint32_t tsize = S.gtable;
+  for (int l = 0; l < S.glevels; ++l) {
+    const int r = S.gres[l];
+    const int n[3] = {r, r, r};
+    const size_t first = (size_t)l * tsize;
+    const bool hashed = (double)r * r * r > (double)tsize;
+    acc = acc + lattice_eval(S, n, [&](int i, int j, int k) {
+      const size_t e = hashed ? (size_t)(ingp_hash((uint32_t)i, (uint32_t)j, (uint32_t)k) % tsize)
+                              : ((size_t)k * r + j) * r + i;
+      return first + e;
+    }, x);
+  }
   return acc;
 }
 
@@ -539,15 +610,7 @@ void setup_scene(const Inputs& in, Scene<T>& S) {
   for (int c = 0; c < 3; ++c) S.sigma[c] = T(in.sigma[c]);
   S.env = in.env; S.env_w = in.env_w; S.env_h = in.env_h;
   S.max_depth = in.max_depth; S.t_min = in.t_min;
-  if (in.medium && in.medium->mu) {
-    const orc_medium& M = *in.medium;
-    S.has_medium = true;
-    for (int a = 0; a < 3; ++a) { S.gn[a] = M.n[a]; S.glo[a] = M.lo[a]; S.ghi[a] = M.hi[a]; }
-    S.gstep = M.step;
-    const size_t nn = (size_t)M.n[0] * M.n[1] * M.n[2] * 3;
-    S.gmu.resize(nn);
-    for (size_t i = 0; i < nn; ++i) S.gmu[i] = T(M.mu[i]);
-  }
+  if (in.medium && in.medium->mu) set_medium(*in.medium, S);
 }
 
 // Render a set of pixels.  Pixel p has `spp` primary rays; ray_od(p, s, o, d)
@@ -851,7 +914,7 @@ void jvp_passes(const Inputs& in, int npix, int spp, RayFn ray_od, int ntan, con
 extern "C" {
 
 // Forward-mode derivative of one view's image along ntan directions at once.
-// tV: [ntan][nv][3], tior: [ntan], tsigma: [ntan][3], tmu: [ntan][grid nodes][3]
+// tV: [ntan][nv][3], tior: [ntan], tsigma: [ntan][3], tmu: [ntan][grid nodes or table entries][3]
 // (each nullable = 0; medium nullable = no absorption grid).
 // img: [H*W][3] (the same values as orc_render); dimg: [ntan][H*W][3].
 int orc_render_jvp(const double* V, int nv, const int* F, int nf, double ior, const double* sigma,
@@ -892,13 +955,7 @@ int orc_render_rays_jvp(const double* V, int nv, const int* F, int nf, double io
 int orc_medium_depth(const orc_medium* medium, const double* o, const double* d, const double* t, int n,
                      double* out) {
   Scene<double> S;
-  if (medium && medium->mu) {
-    S.has_medium = true;
-    for (int a = 0; a < 3; ++a) { S.gn[a] = medium->n[a]; S.glo[a] = medium->lo[a]; S.ghi[a] = medium->hi[a]; }
-    S.gstep = medium->step;
-    const size_t nn = (size_t)medium->n[0] * medium->n[1] * medium->n[2] * 3;
-    S.gmu.assign(medium->mu, medium->mu + nn);
-  }
+  if (medium && medium->mu) set_medium(*medium, S);
   for (int r = 0; r < n; ++r) {
     const V3d G = medium_depth(S, V3d(o[3 * r], o[3 * r + 1], o[3 * r + 2]), V3d(d[3 * r], d[3 * r + 1], d[3 * r + 2]),
                                t[r]);

@@ -608,6 +608,31 @@ def random_absorption_grid(n, lo, hi, seed: int, scale: float = 1.0, step: float
                 step=float(F32(0.5 * cell if step is None else step)))
 
 
+def hash_texture_resolutions(levels: int, n_min: int, n_max: int) -> list:
+    """Nodes per axis of the levels of a multi-resolution hash texture,
+    growing geometrically from n_min to n_max (Instant-NGP's level scale:
+    factor b = exp((ln n_max - ln n_min) / (L - 1)), n_l = floor(n_min b^l))."""
+    if levels == 1:
+        return [int(n_min)]
+    b = math.exp((math.log(n_max) - math.log(n_min)) / (levels - 1))
+    return [int(math.floor(n_min * b ** l + 1e-6)) for l in range(levels)]
+
+
+def random_hash_texture(levels: int, log2_table: int, n_min: int, n_max: int, lo, hi, seed: int,
+                        scale: float = 1.0, step: float = None) -> dict:
+    """A multi-resolution hash texture of per-channel absorption rates over
+    [lo, hi]: table [levels, 2^log2_table, 3] of rates drawn uniformly from
+    [0, 2 scale / levels) (so G, the sum of the levels, averages `scale`),
+    float32; res from hash_texture_resolutions; step defaults to half the
+    finest cell."""
+    rng = np.random.default_rng(seed)
+    res = hash_texture_resolutions(levels, n_min, n_max)
+    table = rng.uniform(0.0, 2.0 * scale / levels, size=(levels, 1 << log2_table, 3)).astype(F32)
+    cell = min((hi[a] - lo[a]) / (res[-1] - 1) for a in range(3))
+    return dict(table=table, res=res, lo=tuple(map(float, lo)), hi=tuple(map(float, hi)),
+                step=float(F32(0.5 * cell if step is None else step)))
+
+
 # --------------------------------------------------------------------------
 # the benchmark workloads
 # --------------------------------------------------------------------------

@@ -641,6 +641,116 @@ def test_medium_jvp_matches_central_differences():
     assert np.abs(dm[0]).max() > 1e-3 and np.abs(dv[0]).max() > 1e-3
 
 
+def _point_values(med, P):
+    """G at points P ([n, 3]) from the optical depth of a segment of length
+    t = 2^-10 centred on each point with one (partial) step: S = G(p) t,
+    exact in binary arithmetic for the points used here."""
+    t = 2.0 ** -10
+    d = np.tile([1.0, 0.0, 0.0], (len(P), 1))
+    o = np.asarray(P, np.float64) - d * (t / 2)
+    return O.medium_depth(dict(med, step=1.0), o, d, np.full(len(P), t)) / t
+
+
+def test_hash_texture_of_dense_levels_reproduces_a_linear_field():
+    """Levels with n^3 <= T index their nodes densely, (k n + j) n + i in
+    their own slice [l T, (l + 1) T) of the table.  With level l holding
+    the linear field a_l + b_l . x at its nodes (and garbage in the entries
+    it does not use) the texture is the linear field sum_l a_l + b_l . x,
+    whose optical depth is the closed form of the dense-grid pin."""
+    rng = np.random.default_rng(21)
+    lo, hi = (-1.0, -0.7, -1.3), (0.9, 1.2, 1.1)
+    T, res = 512, [2, 5, 8]
+    table = np.full((3, T, 3), 1e6)
+    a_sum, b_sum = np.zeros(3), np.zeros((3, 3))
+    for l, n in enumerate(res):
+        a, b = rng.normal(size=3), rng.normal(size=(3, 3))
+        lev = S.linear_absorption_grid((n, n, n), lo, hi, a, b, 0.1)["mu"]  # [n, n, n, 3], x fastest
+        table[l, :n ** 3] = lev.reshape(-1, 3)
+        a_sum, b_sum = a_sum + a, b_sum + b
+    for h in (0.043, 0.31):
+        med = dict(table=table, res=res, lo=lo, hi=hi, step=h)
+        o, d, t = _segments_in_box(rng, 150, lo, hi, 2.0)
+        got = O.medium_depth(med, o, d, t)
+        want = t[:, None] * (a_sum[None, :] + (o + d * (t / 2)[:, None]) @ b_sum.T)
+        np.testing.assert_allclose(got, want, rtol=1e-10, atol=1e-11)
+
+
+def test_hash_texture_hashed_level_reads_the_spatial_hash():
+    """A level with n^3 > T stores corner (i, j, k) at (i XOR 2654435761 j
+    XOR 805459861 k) mod T (Instant-NGP, Eq. 4).  With T = 64 only the low
+    six bits of the products count: 2654435761 = 0x9E3779B1 = 49 and
+    805459861 = 0x30025795 = 21 (mod 64), so by hand (5,0,0) -> 5,
+    (0,1,0) -> 49, (0,0,1) -> 21, (1,1,0) -> 1^49 = 48, (1,1,1) -> 1^49^21
+    = 37, (0,2,0) -> 98 mod 64 = 34, (3,5,7) -> 3^53^19 = 37, (8,8,8) ->
+    8^8^40 = 40, (2,0,3) -> 2^63 = 61.  A table holding its own entry index
+    (times 1, 2, -1 per channel) returns these at the lattice points (the
+    box [0, 8]^3 with 9 nodes puts node (i, j, k) at (i, j, k)), and the
+    mean of the two corners halfway between (0,1,0) and (1,1,0)."""
+    T = 64
+    e = np.arange(T, dtype=np.float64)
+    med = dict(table=np.stack([e, 2 * e, -e], axis=-1)[None], res=[9], lo=(0.0, 0.0, 0.0), hi=(8.0, 8.0, 8.0))
+    pts = [(5, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 0), (1, 1, 1), (0, 2, 0), (3, 5, 7), (8, 8, 8), (2, 0, 3),
+           (0.5, 1, 0)]
+    want = np.array([5, 49, 21, 48, 37, 34, 37, 40, 61, 48.5])
+    got = _point_values(med, np.array(pts, np.float64))
+    np.testing.assert_array_equal(got, want[:, None] * np.array([1.0, 2.0, -1.0]))
+
+
+def test_hash_texture_levels_superpose():
+    """The texture is the sum of its levels: a dense, a dense and a hashed
+    level together give the sum of the three one-level textures' optical
+    depths (each with its own table slice and node count)."""
+    rng = np.random.default_rng(22)
+    lo, hi = (-1.2, -1.1, -1.0), (1.0, 1.3, 1.1)
+    med = S.random_hash_texture(3, 9, 4, 16, lo, hi, seed=5, scale=1.3)
+    assert med["res"] == [4, 8, 16] and 16 ** 3 > 512 >= 8 ** 3
+    med["table"] = med["table"].astype(np.float64)
+    o, d, t = _segments_in_box(rng, 100, lo, hi, 2.0)
+    got = O.medium_depth(med, o, d, t)
+    parts = sum(O.medium_depth(dict(med, table=med["table"][l:l + 1], res=[med["res"][l]]), o, d, t)
+                for l in range(3))
+    np.testing.assert_allclose(got, parts, rtol=1e-12, atol=1e-13)
+    assert np.abs(got).min() > 0
+
+
+def test_constant_hash_texture_is_a_sigma_shift():
+    """Every entry of every level c / L: the texture is the constant c (the
+    trilinear weights sum to one at each level), so the render equals the
+    one with sigma + c."""
+    sc = S.glass_icosphere_scene(width=12, height=10, max_depth=5)
+    cam = sc.cams[0]
+    sigma = np.array([0.2, 0.1, 0.4])
+    c = np.array([0.5, 0.05, 1.1])
+    table = np.broadcast_to(c / 4.0, (4, 64, 3)).copy()
+    med = dict(table=table, res=[2, 3, 5, 9], lo=(-1.5, -1.5, -1.5), hi=(1.5, 1.5, 1.5), step=0.07)
+    a = O.render(sc.V, sc.F, 1.5, sigma, sc.env, cam, 5, medium=med)
+    b = O.render(sc.V, sc.F, 1.5, sigma + c, sc.env, cam, 5)
+    np.testing.assert_allclose(a["img"], b["img"], rtol=1e-11, atol=1e-14)
+    assert a["counters"] == b["counters"]
+
+
+def test_hash_texture_jvp_matches_central_differences():
+    """Forward-mode derivatives with respect to the table entries (hashed
+    collisions included) against central differences of the FP64 render."""
+    sc = S.glass_icosphere_scene(width=8, height=8, max_depth=4)
+    cam = sc.cams[0]
+    sigma = np.array([0.1, 0.2, 0.3])
+    med = S.random_hash_texture(3, 6, 3, 9, (-1.1, -1.1, -1.1), (1.1, 1.1, 1.1), seed=8, scale=0.8)
+    med["table"] = med["table"].astype(np.float64)
+    rng = np.random.default_rng(23)
+    tmu = rng.normal(size=(1,) + med["table"].shape)
+    V = sc.V.astype(np.float64)
+    _, dm = O.render_jvp(V, sc.F, 1.5, sigma, sc.env, cam, 4, medium=med, tmu=tmu)
+    eps = 1e-6
+
+    def img(tab):
+        return O.render(V, sc.F, 1.5, sigma, sc.env, cam, 4, medium=dict(med, table=tab))["img"]
+
+    fd = (img(med["table"] + eps * tmu[0]) - img(med["table"] - eps * tmu[0])) / (2 * eps)
+    np.testing.assert_allclose(dm[0], fd, rtol=1e-5, atol=1e-8)
+    assert np.abs(dm[0]).max() > 1e-3
+
+
 def test_image_is_linear_in_the_environment():
     """Escaped radiance is read from the map and weighted by a throughput
     that does not depend on it (Sec. 3.4 steps 3-5), so the image is linear
