@@ -73,6 +73,9 @@ def parse():
     ap.add_argument("--medium-grid", type=int, default=64, help="nodes per axis of the absorption grid")
     ap.add_argument("--medium-views", type=int, default=100)
     ap.add_argument("--medium-steps", type=int, default=5)
+    ap.add_argument("--hash-levels", type=int, default=8, help="levels of the hash-texture absorption mode")
+    ap.add_argument("--hash-log2-table", type=int, default=19, help="log2 of the entries per hash-texture level")
+    ap.add_argument("--hash-res", type=str, default="16,128", help="nodes per axis of the coarsest,finest level")
     return ap.parse_args()
 
 
@@ -433,7 +436,10 @@ def medium_leg(args, dt, dev):
     trilinear, sampled every half cell along interior segments.  One step =
     normals + refit + forward + backward seeded by a fixed random image
     gradient, with the node-value gradient; the same step without the grid
-    is timed beside it, and once more with the environment-texel gradient."""
+    is timed beside it, and once more with the environment-texel gradient.
+    The hash_texture mode replaces the grid by a multi-resolution hash
+    texture (levels from n_min to n_max nodes per axis, 2^k entries per
+    level, random rates averaging 1) sampled with the same step."""
     import torch
     from paper_2603_00413_gb300 import scenes as S
     sc, _ = genus2_workload(args.medium_views, args.res, args.depth)
@@ -447,6 +453,10 @@ def medium_leg(args, dt, dev):
     lo, hi = (-1.25, -1.25, -1.25), (1.25, 1.25, 1.25)
     med = S.random_absorption_grid((g, g, g), lo, hi, seed=6, scale=1.0)
     medium = dt.Medium(torch.from_numpy(med["mu"]).to(dev), lo, hi, med["step"])
+    n_min, n_max = (int(x) for x in args.hash_res.split(","))
+    tex = S.random_hash_texture(args.hash_levels, args.hash_log2_table, n_min, n_max, lo, hi, seed=8, scale=1.0,
+                                step=med["step"])
+    texture = dt.HashTexture(torch.from_numpy(tex["table"]).to(dev), tex["res"], lo, hi, tex["step"])
     bvh = dt.build_bvh(V, F)
     N = dt.vertex_normals(V, F)
     params = dt.Params(args.depth)
@@ -458,9 +468,11 @@ def medium_leg(args, dt, dev):
                        f"depth {args.depth}, IoR {sc.ior:.4f}, sigma {tuple(round(float(x), 4) for x in sc.sigma)} "
                        f"plus a {g}^3 grid of smooth random absorption rates over [-1.25, 1.25]^3 sampled every "
                        f"{med['step']:.4f} (half a cell) along interior segments; fwd+bwd with a fixed image gradient",
-           "grid_nodes": g ** 3, "step": med["step"]}
-    for mode in ("medium", "sigma_only", "sigma_only_env_grad"):
-        m = medium if mode == "medium" else None
+           "grid_nodes": g ** 3, "step": med["step"],
+           "hash_texture_config": {"levels": args.hash_levels, "entries_per_level": 1 << args.hash_log2_table,
+                                   "res": tex["res"], "table_bytes": int(texture.mu.numel() * 4)}}
+    for mode in ("medium", "hash_texture", "sigma_only", "sigma_only_env_grad"):
+        m = {"medium": medium, "hash_texture": texture}.get(mode)
         want_env = mode == "sigma_only_env_grad"
         img, tape = dt.render(V, F, bvh, N, ior, sigma, env, cams, res, res, params, medium=m)
         stats = tape.stats

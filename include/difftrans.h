@@ -122,25 +122,43 @@ dt_status dt_refit_bvh(const float* d_V, int32_t nv, const int32_t* d_F, int32_t
 /* ------------------------------------------------------------------------
  * Scene, views and parameters of a render.
  * ------------------------------------------------------------------------ */
-/* Spatially varying absorption (Eq. 11 with mu_t(x) = sigma + G(x)): G is a
- * dense grid of per-channel rates at the nodes of an nx x ny x nz lattice
- * spanning the box [lo, hi] (node (i, j, k) at lo + (i, j, k) (hi - lo) /
- * (n - 1)), read with trilinear interpolation at positions clamped to the
- * box.  On an interior segment (where sigma applies) of length t the
- * optical depth sigma t gains the sum of G over steps of length `step` from
- * the segment's start: m = floor(t / step) full steps (at most 8192) and a
- * last one of length t - m step, each sampled at its midpoint and weighted
- * by its length.
+/* Spatially varying absorption (Eq. 11 with mu_t(x) = sigma + G(x)).  On an
+ * interior segment (where sigma applies) of length t the optical depth
+ * sigma t gains the sum of G over steps of length `step` from the segment's
+ * start: m = floor(t / step) full steps (at most 8192) and a last one of
+ * length t - m step, each sampled at its midpoint and weighted by its
+ * length.  Every lattice below spans the box [lo, hi] and is read with
+ * trilinear interpolation at positions clamped to the box.
+ *
+ * levels == 0: G is a dense grid of per-channel rates at the nodes of an
+ * nx x ny x nz lattice (node (i, j, k) at lo + (i, j, k) (hi - lo) / (n - 1)).
  *  d_mu: float[nz][ny][nx][4], 16-byte aligned (the 4th float is unused);
- *  d_grad_mu: where dt_render_backward writes dLoss/d(node values), same
- *    layout (overwritten; NULL: not computed).
- * nx, ny, nz >= 2; hi > lo on every axis; step > 0. */
+ *  nx, ny, nz >= 2.
+ *
+ * levels = L in 1..DT_MAX_HASH_LEVELS: G is a multi-resolution hash texture
+ * (Sec. 3.3's differentiable 3D texture after Instant-NGP, Mueller et al.
+ * 2022): level l is a lattice of res[l] nodes per axis whose values live in
+ * the table slice [l T, (l + 1) T), T = 2^log2_table; its corner (i, j, k)
+ * is entry (k res + j) res + i when res^3 <= T and otherwise entry
+ * (i XOR 2654435761 j XOR 805459861 k) mod T (32-bit unsigned products).
+ * G is the sum over the levels of their trilinear interpolations.
+ *  d_mu: float[L][T][4], 16-byte aligned (the 4th float is unused);
+ *  4 <= log2_table <= 24; 2 <= res[l] <= 2^20; nx, ny, nz ignored.
+ *
+ *  d_grad_mu: where dt_render_backward writes dLoss/d(node values or table
+ *    entries), the layout of d_mu (overwritten; NULL: not computed).  Hash
+ *    corners that share an entry add their contributions.
+ * hi > lo on every axis; step > 0. */
+#define DT_MAX_HASH_LEVELS 16
 typedef struct dt_medium {
   const float* d_mu;
   float* d_grad_mu;
   int32_t nx, ny, nz;
   float lo[3], hi[3];
   float step;
+  int32_t levels;     /* 0: dense grid; L: hash texture with L levels */
+  int32_t log2_table; /* hash texture: log2 of the entries per level */
+  int32_t res[DT_MAX_HASH_LEVELS]; /* hash texture: nodes per axis of each level */
 } dt_medium;
 
 typedef struct dt_scene {

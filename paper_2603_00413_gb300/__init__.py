@@ -48,9 +48,13 @@ class DiffTransError(RuntimeError):
         self.code = code
 
 
+MAX_HASH_LEVELS = 16  # DT_MAX_HASH_LEVELS
+
+
 class DtMedium(ctypes.Structure):
     _fields_ = [("d_mu", c_void_p), ("d_grad_mu", c_void_p), ("nx", c_int32), ("ny", c_int32), ("nz", c_int32),
-                ("lo", ctypes.c_float * 3), ("hi", ctypes.c_float * 3), ("step", ctypes.c_float)]
+                ("lo", ctypes.c_float * 3), ("hi", ctypes.c_float * 3), ("step", ctypes.c_float),
+                ("levels", c_int32), ("log2_table", c_int32), ("res", c_int32 * MAX_HASH_LEVELS)]
 
 
 class DtScene(ctypes.Structure):
@@ -384,6 +388,49 @@ class Medium:
         return m
 
 
+class HashTexture:
+    """Spatially varying absorption given as a multi-resolution hash texture
+    (Sec. 3.3's differentiable 3D texture, after Instant-NGP): L <= 16
+    lattices over the box [lo, hi], level l with res[l] nodes per axis and
+    its values in table[l] (T entries, T a power of two, 16 <= T <= 2^24):
+    corner (i, j, k) at entry (k res + j) res + i when res^3 <= T, else at
+    (i XOR 2654435761 j XOR 805459861 k) mod T.  G(x) is the sum of the
+    levels' trilinear interpolations; steps along interior segments as for
+    Medium.  table: float32 device tensor [L, T, 3] or [L, T, 4]; the
+    gradient comes back as [L, T, 3]."""
+
+    def __init__(self, table, res, lo, hi, step: float):
+        res = [int(r) for r in res]
+        if table.dim() != 3 or table.shape[2] not in (3, 4) or not 1 <= table.shape[0] <= MAX_HASH_LEVELS:
+            raise ValueError(f"table must be [L, T, 3 or 4] with 1 <= L <= {MAX_HASH_LEVELS}")
+        T = table.shape[1]
+        if T < 16 or T > (1 << 24) or T & (T - 1):
+            raise ValueError("the table size per level must be a power of two in 16..2^24")
+        if len(res) != table.shape[0] or min(res) < 2 or max(res) > (1 << 20):
+            raise ValueError("res needs one node count in 2..2^20 per level")
+        if table.shape[2] == 3:
+            table = torch.cat([table, torch.zeros_like(table[..., :1])], dim=2)
+        self.mu = _need(table.contiguous(), torch.float32, (4,), "table")
+        self.res = res
+        self.lo = tuple(float(x) for x in lo)
+        self.hi = tuple(float(x) for x in hi)
+        self.step = float(step)
+
+    def struct(self, grad=None) -> DtMedium:
+        m = DtMedium()
+        m.d_mu = self.mu.data_ptr()
+        m.d_grad_mu = grad.data_ptr() if grad is not None else None
+        for a in range(3):
+            m.lo[a] = self.lo[a]
+            m.hi[a] = self.hi[a]
+        m.step = self.step
+        m.levels = len(self.res)
+        m.log2_table = self.mu.shape[1].bit_length() - 1
+        for l, r in enumerate(self.res):
+            m.res[l] = r
+        return m
+
+
 def _scene_struct(V, F, bvh, N, ior, sigma, env, medium_c=None, denv=None):
     _need(V, torch.float32, (3,), "V")
     _need(F, torch.int32, (3,), "F")
@@ -459,9 +506,10 @@ def _effective_params(params: Params, ws: Workspace):
 
 
 def render(V, F, bvh: Bvh, N, ior, sigma, env, cams, width: int, height: int, params: Params, ws: Workspace = None,
-           out=None, stream=None, check: bool = True, medium: Medium = None):
+           out=None, stream=None, check: bool = True, medium=None):
     """Forward render (Sec. 3.4 steps 1-5) of cams.shape[0] views; medium:
-    an absorption grid added to sigma on interior segments.
+    an absorption grid (Medium) or hash texture (HashTexture) added to sigma
+    on interior segments.
 
     Returns (image [n_views, height, width, 3], Tape).  With check=True the
     device status is read back (one synchronisation) and an arena overflow is
@@ -707,7 +755,7 @@ class BatchItem:
     and parameters, with its own output image."""
 
     def __init__(self, V, F, bvh: Bvh, N, ior, sigma, env, cams, width: int, height: int, params: Params,
-                 medium: Medium = None):
+                 medium=None):
         self.V, self.F, self.bvh, self.N = V, F, bvh, N
         self.ior, self.sigma, self.env, self.cams = ior, sigma, env, cams
         self.width, self.height, self.params = int(width), int(height), params

@@ -91,11 +91,12 @@ struct SceneSums {
 // out_cur: the same for level k (not written for k = 0: camera rays have no
 // parent); see AdjRecords.
 // kBatch = false: one scene, whose entry E0 arrives as a kernel parameter;
-// true: each segment looks its scene up.  kGrid: some scene has an
-// absorption grid (dt_medium.cuh), whose optical depth interior segments add.
+// true: each segment looks its scene up.  kGrid: 1 = some scene has an
+// absorption grid (dt_medium.cuh), whose optical depth interior segments add;
+// 2 = some scene's is a hash texture.
 constexpr int kAdjointMinBlocks = 4;  // CTAs of 256 per SM the register budget is sized for
 
-template <bool kBatch, bool kGrid>
+template <bool kBatch, int kGrid>
 __global__ void __launch_bounds__(256, kAdjointMinBlocks) k_adjoint(WsView W, int k, const AdjRecords out_next,
                                                                    const AdjRecords out_cur, const SceneEntry E0,
                                                                    float4* __restrict__ med_side) {
@@ -158,7 +159,7 @@ __global__ void __launch_bounds__(256, kAdjointMinBlocks) k_adjoint(WsView W, in
         HitShade h;
         shade_hit(o, d, t, b1, b2, v0, v1, v2, N0, N1, N2, ior, sigma, h, tir ? 1 : 0);
         const bool med = kGrid && E.mu && !h.entering;
-        if (med) h.A = absorption_with_depth(sigma, t, medium_depth(medium_view(E), o, d, t));
+        if (med) h.A = absorption_with_depth(sigma, t, medium_depth<kGrid == 2>(medium_view(E, W.ent + sc), o, d, t));
         // children: reflected at ch, refracted at ch + (flags >> kRefractShift)
         float3 Lr = mk(0.f, 0.f, 0.f), orb = Lr, drb = Lr, Lt = Lr, otb = Lr, dtb = Lr;
         const uint32_t jr = (uint32_t)ch - next_start;
@@ -184,7 +185,7 @@ __global__ void __launch_bounds__(256, kAdjointMinBlocks) k_adjoint(WsView W, in
           tbar -= dot(aa, sigma);
           if (med) {
             sbar = -aa;
-            tbar += dot(sbar, medium_depth_dt(medium_view(E), o, d, t));
+            tbar += dot(sbar, medium_depth_dt<kGrid == 2>(medium_view(E, W.ent + sc), o, d, t));
             side = make_float4(sbar.x, sbar.y, sbar.z, t);
           }
         }
@@ -284,8 +285,9 @@ __global__ void __launch_bounds__(256, kAdjointMinBlocks) k_adjoint(WsView W, in
 // samples of its optical depth move with the segment's o and d at fixed t,
 // which adds to its adjoint record (read by the parent level next), and
 // dJ/dS goes to the grid's nodes.  A pass of its own, so the march and the
-// node atomics run at the occupancy of a small kernel.
-template <bool kBatch>
+// node atomics run at the occupancy of a small kernel.  kHash: some scene's
+// grid is a hash texture.
+template <bool kBatch, bool kHash>
 __global__ void __launch_bounds__(256, 3) k_medium_adjoint(WsView W, int k, const AdjRecords out_cur,
                                                         const float4* __restrict__ med_side, const SceneEntry E0) {
   const WsHeader* H = W.hdr;
@@ -297,10 +299,11 @@ __global__ void __launch_bounds__(256, 3) k_medium_adjoint(WsView W, int k, cons
     if (!(sv.w > 0.f) || (sv.x == 0.f && sv.y == 0.f && sv.z == 0.f)) continue;  // no grid, or no gradient
     const uint32_t a = start + i;
     const float4 ro = W.ray_o[a], rd = W.ray_d[a];
-    const SceneEntry& E = kBatch ? W.ent[find_scene(W.th->starts, n_scenes, __float_as_uint(ro.w))] : E0;
+    const int sc = kBatch ? find_scene(W.th->starts, n_scenes, __float_as_uint(ro.w)) : 0;
+    const SceneEntry& E = kBatch ? W.ent[sc] : E0;
     if (!E.mu) continue;
     float3 ob = mk(0.f, 0.f, 0.f), db = ob;
-    medium_backward(medium_view(E), E.dmu, xyz(ro), xyz(rd), sv.w, mk(sv.x, sv.y, sv.z), ob, db);
+    medium_backward<kHash>(medium_view(E, W.ent + sc), E.dmu, xyz(ro), xyz(rd), sv.w, mk(sv.x, sv.y, sv.z), ob, db);
     if (k > 0) {  // camera rays have no parent to hand (obar, dbar) to
       float3 L, o0, d0;
       out_cur.load(i, L, o0, d0);
@@ -393,7 +396,7 @@ __global__ void k_zero_grads(const SceneEntry* __restrict__ ent) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   if (E.mu && E.dmu) {
-    const size_t nn = (size_t)E.gnx * E.gny * E.gnz;
+    const size_t nn = E.gentries;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nn; i += (size_t)gridDim.x * blockDim.x)
       E.dmu[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
@@ -543,18 +546,27 @@ void launch_backward_table(const TableHeader& th, const SceneEntry* entries, con
     const AdjRecords nx = buf[(k + 1) & 1], cu = buf[k & 1];
     {
       ProfScope ps("k_adjoint", s);
-      if (th.any_medium) {
-        if (n > 1) k_adjoint<true, true><<<blocks, 256, smem, s>>>(W, k, nx, cu, entries[0], side);
-        else k_adjoint<false, true><<<blocks, 256, smem, s>>>(W, k, nx, cu, entries[0], side);
+      if (th.any_medium == 2) {
+        if (n > 1) k_adjoint<true, 2><<<blocks, 256, smem, s>>>(W, k, nx, cu, entries[0], side);
+        else k_adjoint<false, 2><<<blocks, 256, smem, s>>>(W, k, nx, cu, entries[0], side);
+      } else if (th.any_medium) {
+        if (n > 1) k_adjoint<true, 1><<<blocks, 256, smem, s>>>(W, k, nx, cu, entries[0], side);
+        else k_adjoint<false, 1><<<blocks, 256, smem, s>>>(W, k, nx, cu, entries[0], side);
       } else {
-        if (n > 1) k_adjoint<true, false><<<blocks, 256, smem, s>>>(W, k, nx, cu, entries[0], side);
-        else k_adjoint<false, false><<<blocks, 256, smem, s>>>(W, k, nx, cu, entries[0], side);
+        if (n > 1) k_adjoint<true, 0><<<blocks, 256, smem, s>>>(W, k, nx, cu, entries[0], side);
+        else k_adjoint<false, 0><<<blocks, 256, smem, s>>>(W, k, nx, cu, entries[0], side);
       }
     }
     if (th.any_medium) {
       ProfScope ps("k_medium_adjoint", s);
-      if (n > 1) k_medium_adjoint<true><<<8 * num_sms(), 256, 0, s>>>(W, k, cu, side, entries[0]);
-      else k_medium_adjoint<false><<<8 * num_sms(), 256, 0, s>>>(W, k, cu, side, entries[0]);
+      const int mb = 8 * num_sms();
+      if (th.any_medium == 2) {
+        if (n > 1) k_medium_adjoint<true, true><<<mb, 256, 0, s>>>(W, k, cu, side, entries[0]);
+        else k_medium_adjoint<false, true><<<mb, 256, 0, s>>>(W, k, cu, side, entries[0]);
+      } else {
+        if (n > 1) k_medium_adjoint<true, false><<<mb, 256, 0, s>>>(W, k, cu, side, entries[0]);
+        else k_medium_adjoint<false, false><<<mb, 256, 0, s>>>(W, k, cu, side, entries[0]);
+      }
     }
   }
   if (th.any_env_grad) {

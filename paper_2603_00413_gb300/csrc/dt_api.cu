@@ -158,9 +158,21 @@ static dt_status check_scene(const dt_scene* sc) {
     const dt_medium& M = *sc->medium;
     if (!M.d_mu || !aligned(M.d_mu, 16) || (M.d_grad_mu && !aligned(M.d_grad_mu, 16)))
       return set_error(DT_ERR_INVALID_ARG, "medium node values (and gradient) need 16-byte aligned device pointers");
-    if (M.nx < 2 || M.ny < 2 || M.nz < 2 || (long long)M.nx * M.ny * M.nz > (1ll << 31))
-      return set_error(DT_ERR_INVALID_ARG, "medium needs at least 2 nodes per axis (got %d x %d x %d)", M.nx, M.ny,
-                       M.nz);
+    if (M.levels < 0 || M.levels > DT_MAX_HASH_LEVELS)
+      return set_error(DT_ERR_INVALID_ARG, "medium levels must be 0 (dense grid) or 1..%d (got %d)",
+                       DT_MAX_HASH_LEVELS, M.levels);
+    if (M.levels == 0) {
+      if (M.nx < 2 || M.ny < 2 || M.nz < 2 || (long long)M.nx * M.ny * M.nz > (1ll << 31))
+        return set_error(DT_ERR_INVALID_ARG, "medium needs at least 2 nodes per axis (got %d x %d x %d)", M.nx, M.ny,
+                         M.nz);
+    } else {
+      if (M.log2_table < 4 || M.log2_table > 24)
+        return set_error(DT_ERR_INVALID_ARG, "hash texture log2_table must be in 4..24 (got %d)", M.log2_table);
+      for (int l = 0; l < M.levels; ++l)
+        if (M.res[l] < 2 || M.res[l] > (1 << 20))
+          return set_error(DT_ERR_INVALID_ARG, "hash texture level %d needs 2..2^20 nodes per axis (got %d)", l,
+                           M.res[l]);
+    }
     for (int a = 0; a < 3; ++a)
       if (!(M.hi[a] > M.lo[a]) || !std::isfinite(M.hi[a] - M.lo[a]))
         return set_error(DT_ERR_INVALID_ARG, "medium box needs hi > lo on every axis");

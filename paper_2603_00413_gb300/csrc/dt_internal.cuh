@@ -174,6 +174,17 @@ enum { CNT_HITS = 0, CNT_MISSES, CNT_DISCARDED, CNT_BACKFACING, CNT_TIR, CNT_NOD
 constexpr int kMaxBatch = 256;
 constexpr int kEntriesPerChunk = 24;  // table entries per writing launch (kernel-parameter space)
 
+// One level of a hash texture (dt_medium levels > 0).
+constexpr int kMaxGridLevels = 16;
+struct alignas(16) GridLevel {
+  int32_t n;         // nodes per axis
+  uint32_t mask;     // hashed level: entries per level - 1; 0: dense indexing (k n + j) n + i
+  uint32_t off;      // first table entry of the level
+  float sx, sy, sz;  // nodes per unit length minus the fencepost ((n - 1) / (hi - lo))
+  int32_t pad[2];
+};
+static_assert(sizeof(GridLevel) == 32, "levels are read as two 16-byte vectors");
+
 struct SceneEntry {
   const float* V;
   const int32_t* F;
@@ -208,12 +219,17 @@ struct SceneEntry {
   float gscale_x, gscale_y, gscale_z;
   float gstep;
   float* denv;  // backward: gradient of the environment texels (nullptr: not computed)
+  // hash texture (glevels > 0; mu then holds the levels' tables and the
+  // dense fields above are unused); gentries = float4 entries of mu
+  int32_t glevels;
+  uint32_t gentries;
+  GridLevel glev[kMaxGridLevels];
 };
 
 struct TableHeader {
   int32_t n;
   int32_t max_depth;
-  int32_t any_medium;  // some scene of the table has an absorption grid
+  int32_t any_medium;  // some scene of the table has an absorption grid (2: a hash texture)
   int32_t any_env_grad;  // some scene of the table wants its environment gradient
   uint32_t n_samples;
   uint32_t n_faces;

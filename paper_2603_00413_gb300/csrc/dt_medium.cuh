@@ -15,6 +15,13 @@
 // pass over the interior segments of each level adds the o and d terms to
 // their adjoint records and scatters dJ/dS w_i into the eight nodes of each
 // sample's cell.
+//
+// G may instead be a multi-resolution hash texture (Sec. 3.3's 3D texture
+// after Instant-NGP): the sum over up to 16 levels of the trilinear
+// interpolation of a cubic lattice over the same box, whose corners are
+// entries of the level's table slice, dense when the lattice fits it and
+// otherwise at Instant-NGP's spatial hash.  Every sum above then runs level
+// by level: the same steps, each level's cell and weights, its own scale.
 #pragma once
 
 #include "dt_internal.cuh"
@@ -28,11 +35,16 @@ struct MediumView {
   int nx, ny, nz;
   float3 lo, scale;
   float step;
+  int levels;             // hash texture levels (0: the dense grid)
+  const GridLevel* lev;   // their descriptors, in the workspace's copy of the scene entry
 };
 
-__device__ __forceinline__ MediumView medium_view(const SceneEntry& E) {
+// E: the scene entry as the kernel reads it (a kernel parameter or the
+// table); Eg: the same entry in the workspace table, whose level array is
+// indexed at run time.
+__device__ __forceinline__ MediumView medium_view(const SceneEntry& E, const SceneEntry* Eg) {
   return MediumView{E.mu, E.gnx, E.gny, E.gnz, mk(E.glo_x, E.glo_y, E.glo_z),
-                    mk(E.gscale_x, E.gscale_y, E.gscale_z), E.gstep};
+                    mk(E.gscale_x, E.gscale_y, E.gscale_z), E.gstep, E.glevels, Eg->glev};
 }
 
 // Cell of x: per axis u = (x - lo) scale clamped to [0, n - 1], cell index
@@ -88,7 +100,8 @@ __device__ __forceinline__ CellNodes cell_nodes(const MediumView& g, const GridC
 __device__ __forceinline__ float3 lerp3(float3 a, float3 b, float f) { return a + (b - a) * f; }
 
 // G at the cell position.
-__device__ __forceinline__ float3 trilinear(const CellNodes& q, const GridCell& c) {
+template <class Cell>
+__device__ __forceinline__ float3 trilinear(const CellNodes& q, const Cell& c) {
   const float3 x00 = lerp3(q.c000, q.c100, c.fx), x10 = lerp3(q.c010, q.c110, c.fx);
   const float3 x01 = lerp3(q.c001, q.c101, c.fx), x11 = lerp3(q.c011, q.c111, c.fx);
   return lerp3(lerp3(x00, x10, c.fy), lerp3(x01, x11, c.fy), c.fz);
@@ -96,7 +109,8 @@ __device__ __forceinline__ float3 trilinear(const CellNodes& q, const GridCell& 
 
 // dG_c/dx_a for the three channels c: columns gx, gy, gz (each a float3 over
 // the channels), zero along clamped axes.
-__device__ __forceinline__ void trilinear_grad(const CellNodes& q, const GridCell& c, float3 scale, float3& gx,
+template <class Cell>
+__device__ __forceinline__ void trilinear_grad(const CellNodes& q, const Cell& c, float3 scale, float3& gx,
                                                float3& gy, float3& gz) {
   const float ux = 1.0f - c.fx, uy = 1.0f - c.fy, uz = 1.0f - c.fz;
   gx = ((q.c100 - q.c000) * (uy * uz) + (q.c110 - q.c010) * (c.fy * uz) + (q.c101 - q.c001) * (uy * c.fz) +
@@ -114,8 +128,115 @@ __device__ __forceinline__ int medium_full_steps(float t, float h) {
   return m >= (float)kMaxMediumSteps ? kMaxMediumSteps : (int)m;
 }
 
-// Optical depth of the grid over o + s d, s in [0, t].
+// ---------------------------------------------------------------------------
+// hash texture
+// ---------------------------------------------------------------------------
+// Instant-NGP's spatial hash of a lattice point (Mueller et al. 2022, Eq. 4
+// with d = 3): XOR of the coordinates times 1, 2654435761 and 805459861 in
+// 32-bit arithmetic; the level keeps its low bits (tables are powers of two).
+__device__ __forceinline__ uint32_t ingp_hash(uint32_t i, uint32_t j, uint32_t k) {
+  return i ^ (j * 2654435761u) ^ (k * 805459861u);
+}
+
+// A level's cell containing x: fractions and clamping as grid_cell, and the
+// lattice coordinates of its (0, 0, 0) corner.
+struct LevelCell {
+  uint32_t i, j, k;
+  float fx, fy, fz;
+  bool free_x, free_y, free_z;
+};
+
+__device__ __forceinline__ LevelCell level_cell(const GridLevel& L, float3 lo, float3 x) {
+  LevelCell c;
+  int i, j, k;
+  c.fx = grid_axis(x.x, lo.x, L.sx, L.n, i, c.free_x);
+  c.fy = grid_axis(x.y, lo.y, L.sy, L.n, j, c.free_y);
+  c.fz = grid_axis(x.z, lo.z, L.sz, L.n, k, c.free_z);
+  c.i = (uint32_t)i;
+  c.j = (uint32_t)j;
+  c.k = (uint32_t)k;
+  return c;
+}
+
+// Table entry of the level's lattice point (i, j, k).
+__device__ __forceinline__ uint32_t level_entry(const GridLevel& L, uint32_t i, uint32_t j, uint32_t k) {
+  const uint32_t n = (uint32_t)L.n;
+  return L.off + (L.mask ? (ingp_hash(i, j, k) & L.mask) : ((k * n + j) * n + i));
+}
+
+// Corner q (x fastest, then y, then z) of the cell at (i, j, k).
+__device__ __forceinline__ uint32_t corner_entry(const GridLevel& L, uint32_t i, uint32_t j, uint32_t k, int q) {
+  return level_entry(L, i + (uint32_t)(q & 1), j + (uint32_t)((q >> 1) & 1), k + (uint32_t)(q >> 2));
+}
+
+__device__ __forceinline__ CellNodes level_nodes(const float4* mu, const GridLevel& L, const LevelCell& c) {
+  CellNodes q;
+  q.c000 = xyz(__ldg(mu + corner_entry(L, c.i, c.j, c.k, 0)));
+  q.c100 = xyz(__ldg(mu + corner_entry(L, c.i, c.j, c.k, 1)));
+  q.c010 = xyz(__ldg(mu + corner_entry(L, c.i, c.j, c.k, 2)));
+  q.c110 = xyz(__ldg(mu + corner_entry(L, c.i, c.j, c.k, 3)));
+  q.c001 = xyz(__ldg(mu + corner_entry(L, c.i, c.j, c.k, 4)));
+  q.c101 = xyz(__ldg(mu + corner_entry(L, c.i, c.j, c.k, 5)));
+  q.c011 = xyz(__ldg(mu + corner_entry(L, c.i, c.j, c.k, 6)));
+  q.c111 = xyz(__ldg(mu + corner_entry(L, c.i, c.j, c.k, 7)));
+  return q;
+}
+
+__device__ __forceinline__ GridLevel load_level(const GridLevel* p) {
+  GridLevel L;
+  const int4 a = __ldg(reinterpret_cast<const int4*>(p));
+  const int4 b = __ldg(reinterpret_cast<const int4*>(p) + 1);
+  L.n = a.x;
+  L.mask = (uint32_t)a.y;
+  L.off = (uint32_t)a.z;
+  L.sx = __int_as_float(a.w);
+  L.sy = __int_as_float(b.x);
+  L.sz = __int_as_float(b.y);
+  L.pad[0] = L.pad[1] = 0;
+  return L;
+}
+
+// Optical depth of the hash texture over o + s d, s in [0, t]: the steps of
+// medium_depth, level by level.
+__device__ __forceinline__ float3 hash_depth(const MediumView& g, float3 o, float3 d, float t) {
+  const float h = g.step;
+  const int m = medium_full_steps(t, h);
+  const float r = t - (float)m * h;
+  float3 sum = mk(0.f, 0.f, 0.f);
+  for (int l = 0; l < g.levels; ++l) {
+    const GridLevel L = load_level(g.lev + l);
+    for (int i = 0; i <= m; ++i) {
+      const float w = i < m ? h : r;
+      const float s = i < m ? ((float)i + 0.5f) * h : (float)m * h + 0.5f * r;
+      const LevelCell c = level_cell(L, g.lo, o + d * s);
+      sum = sum + trilinear(level_nodes(g.mu, L, c), c) * w;
+    }
+  }
+  return sum;
+}
+
+__device__ __forceinline__ float3 hash_depth_dt(const MediumView& g, float3 o, float3 d, float t) {
+  const float h = g.step;
+  const int m = medium_full_steps(t, h);
+  const float r = t - (float)m * h;
+  const float3 x = o + d * ((float)m * h + 0.5f * r);
+  float3 sum = mk(0.f, 0.f, 0.f);
+  for (int l = 0; l < g.levels; ++l) {
+    const GridLevel L = load_level(g.lev + l);
+    const LevelCell c = level_cell(L, g.lo, x);
+    const CellNodes q = level_nodes(g.mu, L, c);
+    float3 gx, gy, gz;
+    trilinear_grad(q, c, mk(L.sx, L.sy, L.sz), gx, gy, gz);
+    sum = sum + trilinear(q, c) + (gx * d.x + gy * d.y + gz * d.z) * (0.5f * r);
+  }
+  return sum;
+}
+
+// Optical depth of the grid over o + s d, s in [0, t] (kHash: the scene may
+// hold a hash texture instead; without it that code is not compiled).
+template <bool kHash>
 __device__ __forceinline__ float3 medium_depth(const MediumView& g, float3 o, float3 d, float t) {
+  if (kHash && g.levels) return hash_depth(g, o, d, t);
   const float h = g.step;
   const int m = medium_full_steps(t, h);
   float3 sum = mk(0.f, 0.f, 0.f);
@@ -129,7 +250,9 @@ __device__ __forceinline__ float3 medium_depth(const MediumView& g, float3 o, fl
 }
 
 // dS/dt per channel (only the partial last step depends on t).
+template <bool kHash>
 __device__ __forceinline__ float3 medium_depth_dt(const MediumView& g, float3 o, float3 d, float t) {
+  if (kHash && g.levels) return hash_depth_dt(g, o, d, t);
   const float h = g.step;
   const int m = medium_full_steps(t, h);
   const float r = t - (float)m * h;
@@ -164,8 +287,72 @@ __device__ __forceinline__ void medium_flush(float4* p, int sx, int sy, float3 s
   medium_atomic4(p + sy + sx + 1, sbar * acc[7]);
 }
 
+// The adjoint of hash_depth, level by level as medium_backward below: per
+// sample the gradient of sbar . G_l from sbar . (corner values), per cell
+// the scalar weight sums, flushed into the cell's eight entries (hashed
+// corners that share an entry add) when the ray leaves the cell.
+__device__ __forceinline__ void hash_flush(float4* dmu, const GridLevel& L, uint32_t i, uint32_t j, uint32_t k,
+                                           float3 sbar, const float* acc) {
+#pragma unroll
+  for (int q = 0; q < 8; ++q) medium_atomic4(dmu + corner_entry(L, i, j, k, q), sbar * acc[q]);
+}
+
+__device__ __forceinline__ void hash_backward(const MediumView& g, float4* dmu, float3 o, float3 d, float t,
+                                              float3 sbar, float3& obar, float3& dbar) {
+  const float h = g.step;
+  const int m = medium_full_steps(t, h);
+  const float r = t - (float)m * h;
+  for (int l = 0; l < g.levels; ++l) {
+    const GridLevel L = load_level(g.lev + l);
+    float acc[8];
+    uint32_t pi = ~0u, pj = 0, pk = 0;  // the cell whose sums are pending (pi = ~0: none)
+    for (int i = 0; i <= m; ++i) {
+      const float w = i < m ? h : r;
+      const float s = i < m ? ((float)i + 0.5f) * h : (float)m * h + 0.5f * r;
+      const LevelCell c = level_cell(L, g.lo, o + d * s);
+      float sv[8];  // sbar . G at the eight corners
+#pragma unroll
+      for (int q = 0; q < 8; ++q) sv[q] = dot(sbar, xyz(__ldg(g.mu + corner_entry(L, c.i, c.j, c.k, q))));
+      const float ux = 1.0f - c.fx, uy = 1.0f - c.fy, uz = 1.0f - c.fz;
+      const float3 gp =
+          mk(((sv[1] - sv[0]) * (uy * uz) + (sv[3] - sv[2]) * (c.fy * uz) + (sv[5] - sv[4]) * (uy * c.fz) +
+              (sv[7] - sv[6]) * (c.fy * c.fz)) * (c.free_x ? L.sx : 0.0f),
+             ((sv[2] - sv[0]) * (ux * uz) + (sv[3] - sv[1]) * (c.fx * uz) + (sv[6] - sv[4]) * (ux * c.fz) +
+              (sv[7] - sv[5]) * (c.fx * c.fz)) * (c.free_y ? L.sy : 0.0f),
+             ((sv[4] - sv[0]) * (ux * uy) + (sv[5] - sv[1]) * (c.fx * uy) + (sv[6] - sv[2]) * (ux * c.fy) +
+              (sv[7] - sv[3]) * (c.fx * c.fy)) * (c.free_z ? L.sz : 0.0f)) * w;
+      obar = obar + gp;
+      dbar = dbar + gp * s;
+      if (dmu) {
+        if (c.i != pi || c.j != pj || c.k != pk) {
+          if (pi != ~0u) hash_flush(dmu, L, pi, pj, pk, sbar, acc);
+          pi = c.i;
+          pj = c.j;
+          pk = c.k;
+#pragma unroll
+          for (int q = 0; q < 8; ++q) acc[q] = 0.f;
+        }
+        acc[0] += w * (ux * uy * uz);
+        acc[1] += w * (c.fx * uy * uz);
+        acc[2] += w * (ux * c.fy * uz);
+        acc[3] += w * (c.fx * c.fy * uz);
+        acc[4] += w * (ux * uy * c.fz);
+        acc[5] += w * (c.fx * uy * c.fz);
+        acc[6] += w * (ux * c.fy * c.fz);
+        acc[7] += w * (c.fx * c.fy * c.fz);
+      }
+    }
+    if (dmu && pi != ~0u) hash_flush(dmu, L, pi, pj, pk, sbar, acc);
+  }
+}
+
+template <bool kHash>
 __device__ __forceinline__ void medium_backward(const MediumView& g, float4* dmu, float3 o, float3 d, float t,
                                                 float3 sbar, float3& obar, float3& dbar) {
+  if (kHash && g.levels) {
+    hash_backward(g, dmu, o, d, t, sbar, obar, dbar);
+    return;
+  }
   const float h = g.step;
   const int m = medium_full_steps(t, h);
   const float r = t - (float)m * h;

@@ -50,6 +50,7 @@ struct TableChunk {
   int32_t first, count;
   SceneEntry e[kEntriesPerChunk];
 };
+static_assert(sizeof(TableChunk) <= 32764, "a table chunk must fit the kernel-parameter space");
 
 __global__ void k_write_table_header(TableHeader* dst, const TableHeader src) {
   const uint32_t* a = reinterpret_cast<const uint32_t*>(&src);
@@ -481,9 +482,10 @@ constexpr int kShadeMinBlocks = 4;  // CTAs per SM the register budget is sized 
 
 // order_bits != 0: each child is also counted in its traversal-order
 // bucket (order_bucket of ray_order_key with that many bits; dt_order.cu)
-// and its bucket is stored with the next level.  kGrid: some scene has an
-// absorption grid, whose optical depth interior segments add (dt_medium.cuh).
-template <bool kBatch, bool kGrid>
+// and its bucket is stored with the next level.  kGrid: 1 = some scene has
+// an absorption grid, whose optical depth interior segments add
+// (dt_medium.cuh); 2 = some scene's is a hash texture.
+template <bool kBatch, int kGrid>
 __global__ void __launch_bounds__(kShadeThreads, kShadeMinBlocks) k_shade(WsView W, int k, const SceneEntry E0,
                                                                          int order_bits) {
   WsHeader* H = W.hdr;
@@ -548,7 +550,7 @@ __global__ void __launch_bounds__(kShadeThreads, kShadeMinBlocks) k_shade(WsView
           shade_hit(xyz(ro), d, hh.x, hh.y, hh.z, v0, v1, v2, load3(E.N + 3 * i0), load3(E.N + 3 * i1),
                     load3(E.N + 3 * i2), ior, sigma, h);
           if (kGrid && E.mu && !h.entering) {  // Sec. 3.4 step 5 with the grid's optical depth
-            h.A = absorption_with_depth(sigma, hh.x, medium_depth(medium_view(E), xyz(ro), d, hh.x));
+            h.A = absorption_with_depth(sigma, hh.x, medium_depth<kGrid == 2>(medium_view(E, W.ent + scene), xyz(ro), d, hh.x));
             c_med += (uint32_t)medium_full_steps(hh.x, E.gstep) + 1u;
           }
           fl = h.entering ? 0u : SF_INSIDE;
@@ -764,12 +766,15 @@ void launch_forward_table(const TableHeader& th, const SceneEntry* entries, void
       const int bits = k < th.max_depth ? order_bits : 0;
       if (bits) launch_order_clear(W, bits, s);
       ProfScope ps("k_shade", s);
-      if (th.any_medium) {
-        if (batch) k_shade<true, true><<<shade_blocks(), kShadeThreads, 0, s>>>(W, k, E0, bits);
-        else k_shade<false, true><<<shade_blocks(), kShadeThreads, 0, s>>>(W, k, E0, bits);
+      if (th.any_medium == 2) {
+        if (batch) k_shade<true, 2><<<shade_blocks(), kShadeThreads, 0, s>>>(W, k, E0, bits);
+        else k_shade<false, 2><<<shade_blocks(), kShadeThreads, 0, s>>>(W, k, E0, bits);
+      } else if (th.any_medium) {
+        if (batch) k_shade<true, 1><<<shade_blocks(), kShadeThreads, 0, s>>>(W, k, E0, bits);
+        else k_shade<false, 1><<<shade_blocks(), kShadeThreads, 0, s>>>(W, k, E0, bits);
       } else {
-        if (batch) k_shade<true, false><<<shade_blocks(), kShadeThreads, 0, s>>>(W, k, E0, bits);
-        else k_shade<false, false><<<shade_blocks(), kShadeThreads, 0, s>>>(W, k, E0, bits);
+        if (batch) k_shade<true, 0><<<shade_blocks(), kShadeThreads, 0, s>>>(W, k, E0, bits);
+        else k_shade<false, 0><<<shade_blocks(), kShadeThreads, 0, s>>>(W, k, E0, bits);
       }
     }
   }
@@ -800,6 +805,23 @@ SceneEntry make_entry(const dt_scene& sc, const dt_views& vw, const dt_params& p
     e.gscale_y = (float)(M.ny - 1) / (M.hi[1] - M.lo[1]);
     e.gscale_z = (float)(M.nz - 1) / (M.hi[2] - M.lo[2]);
     e.gstep = M.step;
+    if (M.levels > 0) {  // hash texture: the dense fields stay unused
+      const uint32_t T = 1u << M.log2_table;
+      e.glevels = M.levels;
+      e.gentries = (uint32_t)M.levels * T;
+      for (int l = 0; l < M.levels; ++l) {
+        const int r = M.res[l];
+        GridLevel& L = e.glev[l];
+        L.n = r;
+        L.mask = (double)r * r * r > (double)T ? T - 1u : 0u;
+        L.off = (uint32_t)l * T;
+        L.sx = (float)(r - 1) / (M.hi[0] - M.lo[0]);
+        L.sy = (float)(r - 1) / (M.hi[1] - M.lo[1]);
+        L.sz = (float)(r - 1) / (M.hi[2] - M.lo[2]);
+      }
+    } else {
+      e.gentries = (uint32_t)((size_t)M.nx * M.ny * M.nz);
+    }
   }
   return e;
 }
@@ -818,7 +840,7 @@ void finish_table(SceneEntry* entries, int n, TableHeader& th) {
     s += entries[i].pix_count * (uint32_t)entries[i].spp;
     f += (uint32_t)entries[i].nf;
     if (entries[i].max_depth > md) md = entries[i].max_depth;
-    if (entries[i].mu) th.any_medium = 1;
+    if (entries[i].mu && th.any_medium < 2) th.any_medium = entries[i].glevels > 0 ? 2 : 1;
     if (entries[i].denv) th.any_env_grad = 1;
   }
   th.starts[n] = s;

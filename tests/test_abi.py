@@ -107,6 +107,8 @@ int main(void) {
   printf("%zu %zu %zu %zu %zu\n", sizeof(dt_medium), offsetof(dt_medium, lo), offsetof(dt_medium, step),
          offsetof(dt_scene, medium), offsetof(dt_stats, medium_samples));
   printf("%zu\n", offsetof(dt_scene, d_grad_env));
+  printf("%zu %zu %zu %d\n", offsetof(dt_medium, levels), offsetof(dt_medium, log2_table), offsetof(dt_medium, res),
+         DT_MAX_HASH_LEVELS);
   return 0;
 }
 """
@@ -127,7 +129,9 @@ int main(void) {
                             dt.DtStats.level_needed.offset]
     assert sizes[14:19] == [ctypes.sizeof(dt.DtMedium), dt.DtMedium.lo.offset, dt.DtMedium.step.offset,
                             dt.DtScene.medium.offset, dt.DtStats.medium_samples.offset]
-    assert sizes[19:] == [dt.DtScene.d_grad_env.offset]
+    assert sizes[19:20] == [dt.DtScene.d_grad_env.offset]
+    assert sizes[20:] == [dt.DtMedium.levels.offset, dt.DtMedium.log2_table.offset, dt.DtMedium.res.offset,
+                          dt.MAX_HASH_LEVELS]
 
 
 def test_checkpointed_workspace_is_smaller_and_validated():
