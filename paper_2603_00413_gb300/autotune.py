@@ -74,8 +74,9 @@ def tune(step, key: str, space: dict = None, reps: int = 2, cache_path: str = CA
     trials.append((dict(best), best_ms))
     if coordinate:
         for knob, options in space.items():
+            start = best[knob]  # the incumbent, already timed
             for v in options:
-                if v == best[knob]:
+                if v == start:
                     continue
                 cand = dict(best)
                 cand[knob] = v
