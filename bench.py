@@ -32,9 +32,9 @@ sys.path.insert(0, ROOT)
 METRIC = "ray-segments/s fwd and fwd+bwd vs plain kernel; p50/p99 request latency"
 UNIT = "segments/s"
 
-# Algorithmic bytes each kernel must move per unit of work (see the design doc,
-# "Roofline"): the tape and ray records it reads and writes once, the scene
-# data of the hit, and the BVH nodes / triangles the traversal visits.
+# Algorithmic bytes each kernel must move per unit of work: the tape and ray
+# records it reads and writes once, the scene data of the hit, and the BVH
+# nodes / triangles the traversal visits.
 RAY_RECORD = 48          # origin+sample, direction+node, throughput+source tri
 HIT_RECORD = 16          # t, b1, b2, tri
 LINK_RECORD = 8          # child index + flags

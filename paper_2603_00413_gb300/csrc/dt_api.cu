@@ -59,9 +59,9 @@ void launch_edge_loss_grad(const void* topo, int32_t nv, int32_t nf, const float
                            cudaStream_t s);
 
 // Launch and scheduling knobs (dt_set_tuning); process-wide.  Node visits
-// per round 192, refill at 8 idle lanes, 5 traversal and 4 shading CTAs per
-// SM, binary nodes, binned SAH builder, levels after the camera rays traced
-// in the order of 20-bit buckets.
+// per scheduling round 192, refill at 8 idle lanes, 5 traversal and 4
+// shading CTAs per SM, binary nodes, binned SAH builder, levels after the
+// camera rays traced in the order of 20-bit buckets.
 dt_tuning g_tuning = {192, 8, 5, 4, 2, 1, 20};
 
 static thread_local char g_err[512] = "";

@@ -8,7 +8,8 @@ import oracle as O
 import paper_2603_00413_gb300 as dt
 from paper_2603_00413_gb300 import scenes as S
 
-# tolerances of the parity bar (derived in DESIGN.md "Tolerances")
+# tolerances of the parity bar: FP32 against FP64 along paths of up to
+# eight interactions (radiance), and the adjoint's FP32 accumulation (gradients)
 RAD_RTOL = 1e-4
 RAD_ATOL = 1e-6
 GRAD_RTOL = 1e-3

@@ -1,5 +1,5 @@
-"""Gradient with respect to the environment texels (the SURVEY's next row 2:
-the bilinear lookup of Sec. 3.4 step 3, differentiated in its texels).  The
+"""Gradient with respect to the environment texels (the bilinear lookup of
+Sec. 3.4 step 3, differentiated in its texels).  The
 image is linear in the texels (pinned on the oracle), so the oracle's render
 with the environment replaced by a direction u is the image's derivative
 along u; the device's dJ/dE, projected on u, must match it.  Checked with
