@@ -542,8 +542,9 @@ def render(V, F, bvh: Bvh, N, ior, sigma, env, cams, width: int, height: int, pa
 def render_backward(tape: Tape, grad_out, stream=None, bws=None, env_grad: bool = False):
     """Gradient of sum(grad_out * image) w.r.t. (V, ior, sigma) at the
     forward's fixed events.  Returns (dV [nv,3], dior [1], dsigma [3]),
-    then dmu [nz, ny, nx, 3] when the render had an absorption grid, then
-    denv [env_h, env_w, 3] when env_grad is set."""
+    then dmu [nz, ny, nx, 3] when the render had an absorption grid (the
+    table's [L, T, 3] for a hash texture), then denv [env_h, env_w, 3] when
+    env_grad is set."""
     lib = load_library()
     V, F, bvh, N, ior, sigma, env = tape.scene_args
     stats = tape.stats if tape.stats is not None else read_stats(tape.ws, stream)
@@ -831,8 +832,8 @@ def batch_backward_workspace_size(items, max_level: int) -> int:
 def render_batch_backward(tape: BatchTape, grads, bws=None, outs=None, stream=None, env_grad: bool = False):
     """Gradients of sum_i sum(grads[i] * image_i) for every scene of the
     batch: list of (dV, dior, dsigma), with dmu [nz, ny, nx, 3] appended for
-    an item with an absorption grid and denv [env_h, env_w, 3] when
-    env_grad is set."""
+    an item with an absorption grid ([L, T, 3] for a hash texture) and denv
+    [env_h, env_w, 3] when env_grad is set."""
     lib = load_library()
     items = tape.items
     stats = tape.stats if tape.stats is not None else read_stats(tape.ws, stream)
