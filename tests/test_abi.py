@@ -159,3 +159,49 @@ def test_python_calls_fail_loudly_without_the_library(tmp_path):
             dt.load_library(str(tmp_path / "missing.so"))
     finally:
         dt._lib = saved
+
+
+def test_absorption_fields_are_validated_on_the_host(lib):
+    """dt_render checks a scene's absorption field (dense grid or hash
+    texture) before it builds the scene table or launches anything: the
+    device pointers here are never dereferenced.  A valid field lets the
+    check move on to the views."""
+    import paper_2603_00413_gb300 as dt
+    L = dt.load_library()
+    fake = 0x10000  # 256-byte aligned, never read
+
+    def scene_with(**kw):
+        m = dt.DtMedium()
+        m.d_mu = fake
+        m.nx = m.ny = m.nz = 4
+        for a in range(3):
+            m.lo[a], m.hi[a] = -1.0, 1.0
+        m.step = 0.05
+        for k, v in kw.items():
+            if k == "res":
+                for i, r in enumerate(v):
+                    m.res[i] = r
+            else:
+                setattr(m, k, v)
+        sc = dt.DtScene(fake, fake, 3, 1, fake, fake, fake, fake, fake, 8, 4)
+        sc.medium = ctypes.pointer(m)
+        return sc, m
+
+    def status(**kw):
+        sc, m = scene_with(**kw)
+        st = L.dt_render(ctypes.byref(sc), ctypes.byref(dt.DtViews()), ctypes.byref(dt.DtParams()), None, None,
+                         0, None)
+        return st, L.dt_last_error().decode()
+
+    for kw, words in [(dict(nx=1), "2 nodes per axis"), (dict(step=0.0), "step"), (dict(levels=17), "levels"),
+                      (dict(levels=-1), "levels"), (dict(levels=2, log2_table=3, res=[4, 8]), "log2_table"),
+                      (dict(levels=2, log2_table=25, res=[4, 8]), "log2_table"),
+                      (dict(levels=2, log2_table=10, res=[4, 1]), "level 1"),
+                      (dict(levels=1, log2_table=10, res=[(1 << 20) + 1]), "level 0"),
+                      (dict(d_mu=fake + 8), "aligned")]:
+        st, msg = status(**kw)
+        assert st == dt.DT_ERR_INVALID_ARG and words in msg, (kw, msg)
+    # valid fields: the dense grid, and a hash texture whose dense-grid sizes are ignored
+    for kw in (dict(), dict(levels=3, log2_table=12, res=[4, 16, 64], nx=0, ny=0, nz=0)):
+        st, msg = status(**kw)
+        assert st == dt.DT_ERR_INVALID_ARG and "d_cams" in msg, (kw, msg)
