@@ -205,3 +205,48 @@ def test_absorption_fields_are_validated_on_the_host(lib):
     for kw in (dict(), dict(levels=3, log2_table=12, res=[4, 16, 64], nx=0, ny=0, nz=0)):
         st, msg = status(**kw)
         assert st == dt.DT_ERR_INVALID_ARG and "d_cams" in msg, (kw, msg)
+
+
+def test_views_params_and_batches_are_validated_on_the_host(lib):
+    """The views, the parameters, the batch size, the output and the
+    workspace are checked before anything is launched (the device pointers
+    here are never dereferenced); the message names the entry."""
+    import paper_2603_00413_gb300 as dt
+    L = dt.load_library()
+    fake = 0x10000
+
+    def entry(**kw):
+        e = dt.DtBatchEntry()
+        e.scene = dt.DtScene(fake, fake, 3, 1, fake, fake, fake, fake, fake, 8, 4)
+        e.views = dt.DtViews(fake, 1, 4, 4)
+        e.params = dt.DtParams(4, 1, 0, 0, 0, 1e-5, 0)
+        e.d_out = fake
+        for k, v in kw.items():
+            owner, name = k.split("__")
+            setattr(getattr(e, owner) if owner != "e" else e, name, v)
+        return e
+
+    def status(entries, ws=fake, ws_bytes=1 << 30):
+        arr = (dt.DtBatchEntry * len(entries))(*entries)
+        st = L.dt_render_batch(arr, len(entries), ws, ws_bytes, None)
+        return st, L.dt_last_error().decode()
+
+    cases = [(dict(views__n_views=0), "n_views"), (dict(views__width=0), "n_views"),
+             (dict(params__max_depth=31), "max_depth"), (dict(params__max_depth=-1), "max_depth"),
+             (dict(params__spp=0), "spp"), (dict(params__t_min=-1.0), "t_min"),
+             (dict(params__tape_mode=2), "tape_mode"), (dict(params__tape_mode=1), "level_capacity"),
+             (dict(views__n_views=1 << 12, views__width=1 << 10, views__height=1 << 10), "too many primary rays"),
+             (dict(e__d_out=None), "d_out"), (dict(scene__nf=0), "nf >= 1")]
+    for kw, words in cases:
+        st, msg = status([entry(), entry(**kw)])
+        assert st == dt.DT_ERR_INVALID_ARG and words in msg and "entry 1" in msg, (kw, msg)
+    st, msg = status([])
+    assert st == dt.DT_ERR_INVALID_ARG and "batch size" in msg
+    st, msg = status([entry()] * 257)
+    assert st == dt.DT_ERR_INVALID_ARG and "batch size" in msg
+    st, msg = status([entry()], ws=None)
+    assert st == dt.DT_ERR_INVALID_ARG and "workspace is NULL" in msg
+    st, msg = status([entry()], ws=fake + 16)
+    assert st == dt.DT_ERR_INVALID_ARG and "256-byte aligned" in msg
+    st, msg = status([entry(views__n_views=64)], ws_bytes=dt.render_workspace_size(100))
+    assert st == dt.DT_ERR_INVALID_ARG and "fewer than the 1024 camera rays" in msg
