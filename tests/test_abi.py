@@ -250,3 +250,50 @@ def test_views_params_and_batches_are_validated_on_the_host(lib):
     assert st == dt.DT_ERR_INVALID_ARG and "256-byte aligned" in msg
     st, msg = status([entry(views__n_views=64)], ws_bytes=dt.render_workspace_size(100))
     assert st == dt.DT_ERR_INVALID_ARG and "fewer than the 1024 camera rays" in msg
+
+
+def test_mesh_update_and_loss_entries_check_their_arguments_on_the_host(lib):
+    """Size queries of the mesh update grow with the mesh and the iteration
+    count; the entry points refuse bad meshes, NULL or misaligned buffers,
+    short scratch and out-of-range hyper-parameters before any launch (the
+    device pointers here are never dereferenced)."""
+    import paper_2603_00413_gb300 as dt
+    L = dt.load_library()
+    fake = 0x10000
+    b, s = ctypes.c_size_t(), ctypes.c_size_t()
+    assert L.dt_topology_size(642, 1280, ctypes.byref(b)) == dt.DT_OK
+    small = b.value
+    assert L.dt_topology_size(2562, 5120, ctypes.byref(b)) == dt.DT_OK and b.value > small
+    for nv, nf in ((2, 1), (3, 0), (3, 1 << 29)):
+        assert L.dt_topology_size(nv, nf, ctypes.byref(b)) == dt.DT_ERR_INVALID_ARG
+    assert L.dt_smooth_scratch_size(642, 100, ctypes.byref(s)) == dt.DT_OK
+    s100 = s.value
+    assert L.dt_smooth_scratch_size(642, 200, ctypes.byref(s)) == dt.DT_OK and s.value >= s100
+    assert L.dt_smooth_scratch_size(0, 100, ctypes.byref(s)) == dt.DT_ERR_INVALID_ARG
+    st_b = ctypes.c_size_t()
+    assert L.dt_large_steps_sizes(642, 100, ctypes.byref(st_b), ctypes.byref(s)) == dt.DT_OK
+    assert st_b.value >= 642 * 3 * 4 and s.value >= s100
+    assert L.dt_large_steps_sizes(642, 0, ctypes.byref(st_b), ctypes.byref(s)) == dt.DT_ERR_INVALID_ARG
+    L.dt_topology_size(642, 1280, ctypes.byref(b))
+    topo_bytes = b.value
+    assert L.dt_build_topology(fake, 1280, 642, fake + 16, topo_bytes, None) == dt.DT_ERR_INVALID_ARG
+    assert L.dt_build_topology(fake, 1280, 642, fake, topo_bytes - 1, None) == dt.DT_ERR_INVALID_ARG
+    assert L.dt_build_topology(None, 1280, 642, fake, topo_bytes, None) == dt.DT_ERR_INVALID_ARG
+    L.dt_smooth_scratch_size(642, 100, ctypes.byref(s))
+    sb = s.value
+    for lam, iters, scratch, nbytes in ((-1.0, 100, fake, sb), (float("nan"), 100, fake, sb), (10.0, 0, fake, sb),
+                                        (10.0, 100, fake, sb - 1), (10.0, 100, fake + 16, sb)):
+        assert L.dt_smooth_solve(fake, 642, 1280, lam, fake, fake, iters, scratch, nbytes, None) == \
+            dt.DT_ERR_INVALID_ARG
+    L.dt_large_steps_sizes(642, 100, ctypes.byref(st_b), ctypes.byref(s))
+    good = dict(lam=10.0, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8, iters=100, state=fake, scratch=fake, nbytes=s.value)
+    for bad in (dict(b1=1.0), dict(b2=-0.1), dict(eps=0.0), dict(lam=-1.0), dict(state=fake + 8),
+                dict(nbytes=s.value - 1), dict(iters=100001)):
+        a = dict(good, **bad)
+        assert L.dt_large_steps_update(fake, 642, 1280, a["lam"], a["lr"], a["b1"], a["b2"], a["eps"], a["iters"],
+                                       fake, fake, a["state"], a["scratch"], a["nbytes"], None) == \
+            dt.DT_ERR_INVALID_ARG, bad
+    assert L.dt_edge_loss_grad(fake, 642, 1280, fake, None, fake, None) == dt.DT_ERR_INVALID_ARG
+    assert L.dt_paper_loss_grad(fake, fake, -1, 1.0, 1.0, fake, fake, None) == dt.DT_ERR_INVALID_ARG
+    assert L.dt_paper_loss_grad(None, fake, 10, 1.0, 1.0, fake, fake, None) == dt.DT_ERR_INVALID_ARG
+    assert L.dt_paper_loss_grad(fake, fake, 10, 1.0, 1.0, fake, None, None) == dt.DT_ERR_INVALID_ARG
