@@ -2,6 +2,7 @@
 outward-oriented meshes of the stated size and genus; smooth positive
 environment maps; deterministic output per seed."""
 import numpy as np
+import pytest
 
 from paper_2603_00413_gb300 import scenes as S
 
@@ -65,3 +66,20 @@ def test_fibonacci_views_on_sphere():
     E = np.array([c.eye for c in cams])
     np.testing.assert_allclose(np.linalg.norm(E, axis=1), 3.0, rtol=1e-6)
     assert abs(E.mean(axis=0)).max() < 0.1
+
+
+def test_hash_texture_inputs():
+    """Level sizes grow geometrically from n_min to n_max (Instant-NGP's level
+    scale); the table is seeded, non-negative and averages the requested
+    rate over the levels; the step defaults to half the finest cell."""
+    assert S.hash_texture_resolutions(1, 16, 128) == [16]
+    res = S.hash_texture_resolutions(8, 16, 128)
+    assert res[0] == 16 and res[-1] == 128 and all(b > a for a, b in zip(res, res[1:]))
+    ratios = np.array(res[1:], float) / np.array(res[:-1], float)
+    assert np.allclose(ratios, 2 ** (3 / 7), atol=0.06)
+    a = S.random_hash_texture(4, 10, 4, 32, (-1, -1, -1), (1, 1, 1), seed=3, scale=2.0)
+    b = S.random_hash_texture(4, 10, 4, 32, (-1, -1, -1), (1, 1, 1), seed=3, scale=2.0)
+    assert a["table"].shape == (4, 1024, 3) and a["table"].dtype == np.float32
+    assert np.array_equal(a["table"], b["table"]) and a["res"] == b["res"] == [4, 8, 16, 32]
+    assert a["table"].min() >= 0 and abs(a["table"].sum(axis=0).mean() - 2.0) < 0.1
+    assert a["step"] == pytest.approx(0.5 * 2.0 / 31, rel=1e-6)
