@@ -80,6 +80,8 @@ def _load():
                                        I, P, P, P, P, P, M, P]
         lib.orc_render_rays_jvp.argtypes = [P, I, P, I, D, P, P, I, I, P, P, I, I, D, I, P, P, P, P, P, M, P]
         lib.orc_medium_depth.argtypes = [M, P, P, P, I, P]
+        lib.orc_field_eval.argtypes = [M, P, I, P]
+        lib.orc_field_corners.argtypes = [M, P, I, P, P]
         _lib = lib
     return _lib
 
@@ -145,6 +147,33 @@ def medium_depth(medium, o, d, t) -> np.ndarray:
     _load().orc_medium_depth(_mp(m), _p(o), _p(d), _p(t), o.shape[0], _p(out))
     del keep
     return out
+
+
+def field_eval(medium, x) -> np.ndarray:
+    """G at points x ([n, 3]) of a dense grid or hash texture: the value the
+    optical-depth sum of Eq. 11 samples.  Returns [n, 3]."""
+    x = _d(x).reshape(-1, 3)
+    out = np.zeros_like(x)
+    m, keep = _medium(medium)
+    _load().orc_field_eval(_mp(m), _p(x), x.shape[0], _p(out))
+    del keep
+    return out
+
+
+def field_corners(medium, x):
+    """G at points x as a linear map of the values: (idx [n, K] int64, w
+    [n, K]) with K = 8 corners per level (8 for a dense grid), idx the row of
+    the flattened [entries, 3] values, so G(x_p) = sum_k w[p, k] *
+    values[idx[p, k]]."""
+    x = _d(x).reshape(-1, 3)
+    levels = len(medium["res"]) if "table" in medium else 1
+    K = 8 * levels
+    idx = np.zeros((x.shape[0], K), np.int64)
+    w = np.zeros((x.shape[0], K))
+    m, keep = _medium(medium)
+    _load().orc_field_corners(_mp(m), _p(x), x.shape[0], _p(idx), _p(w))
+    del keep
+    return idx, w
 
 
 def _i(a):
@@ -452,3 +481,28 @@ def paper_losses(img, target, lambda_color: float = 1.0, lambda_tone: float = 1.
     total = lambda_color * l_color + lambda_tone * l_tone
     grad = (lambda_color * g_color + lambda_tone * g_tone).reshape(np.shape(img))
     return total, l_color, l_tone, grad
+
+
+def mat_smooth_loss(medium, v, xi):
+    """L_mat-smooth of Sec. 3.4 (Eq. 16): (1/N) sum_i |mu_t(v_i) - mu_t(v_i +
+    xi_i)| over N points v_i with perturbations xi_i (both drawn by the
+    caller), |.| read as the sum of the three channels' absolute values;
+    sigma cancels, so only the field G counts.  Returns (loss, dL/d(values))
+    with the gradient in the shape of the medium's values ([nz, ny, nx, 3]
+    or [L, T, 3]); a channel whose difference is exactly 0 contributes no
+    gradient (the subgradient 0)."""
+    v = _d(v).reshape(-1, 3)
+    xi = _d(xi).reshape(-1, 3)
+    N = v.shape[0]
+    values = _d(medium["table"] if "table" in medium else medium["mu"])
+    flat = values.reshape(-1, 3)
+    ia, wa = field_corners(medium, v)
+    ib, wb = field_corners(medium, v + xi)
+    D = (wa[..., None] * flat[ia]).sum(axis=1) - (wb[..., None] * flat[ib]).sum(axis=1)
+    loss = float(np.abs(D).sum() / max(N, 1))
+    s = np.sign(D) / max(N, 1)
+    g = np.zeros_like(flat)
+    for c in range(3):
+        np.add.at(g[:, c], ia.ravel(), (wa * s[:, c:c + 1]).ravel())
+        np.add.at(g[:, c], ib.ravel(), -(wb * s[:, c:c + 1]).ravel())
+    return loss, g.reshape(values.shape)

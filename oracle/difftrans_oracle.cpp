@@ -403,15 +403,13 @@ void set_medium(const orc_medium& M, Scene<T>& S) {
   for (size_t i = 0; i < nn; ++i) S.gmu[i] = T(M.mu[i]);
 }
 
-// Trilinear interpolation at x of one lattice of n[0] x n[1] x n[2] nodes
-// over the box, each coordinate clamped to the box (the clamped coordinate
-// is a constant, so it carries no derivative).  entry(i, j, k) is the index
-// of node (i, j, k)'s three values in S.gmu (divided by 3).
-template <class T, class Entry>
-V3<T> lattice_eval(const Scene<T>& S, const int n[3], Entry entry, const V3<T>& x) {
+// The cell of one lattice of n[0] x n[1] x n[2] nodes over the box that
+// holds x: its lowest corner i0 and the fractions f, each coordinate clamped
+// to the box (the clamped coordinate is a constant, so it carries no
+// derivative).
+template <class T>
+void lattice_cell(const Scene<T>& S, const int n[3], const V3<T>& x, int i0[3], T f[3]) {
   const T xs[3] = {x.x, x.y, x.z};
-  T f[3];
-  int i0[3];
   for (int a = 0; a < 3; ++a) {
     const double span = (double)(n[a] - 1);
     T u = (xs[a] - S.glo[a]) / (S.ghi[a] - S.glo[a]) * span;
@@ -422,6 +420,15 @@ V3<T> lattice_eval(const Scene<T>& S, const int n[3], Entry entry, const V3<T>& 
     i0[a] = i;
     f[a] = u - (double)i;
   }
+}
+
+// Trilinear interpolation at x of one lattice.  entry(i, j, k) is the index
+// of node (i, j, k)'s three values in S.gmu (divided by 3).
+template <class T, class Entry>
+V3<T> lattice_eval(const Scene<T>& S, const int n[3], Entry entry, const V3<T>& x) {
+  T f[3];
+  int i0[3];
+  lattice_cell(S, n, x, i0, f);
   V3<T> acc;
   for (int dz = 0; dz < 2; ++dz)
     for (int dy = 0; dy < 2; ++dy)
@@ -433,26 +440,41 @@ V3<T> lattice_eval(const Scene<T>& S, const int n[3], Entry entry, const V3<T>& 
   return acc;
 }
 
+// The same lattice as a linear map: the eight corners' entries and weights.
+template <class Entry>
+void lattice_corners(const Scene<double>& S, const int n[3], Entry entry, const V3d& x, int64_t* idx, double* w) {
+  double f[3];
+  int i0[3];
+  lattice_cell(S, n, x, i0, f);
+  int q = 0;
+  for (int dz = 0; dz < 2; ++dz)
+    for (int dy = 0; dy < 2; ++dy)
+      for (int dx = 0; dx < 2; ++dx, ++q) {
+        w[q] = (dx ? f[0] : 1.0 - f[0]) * (dy ? f[1] : 1.0 - f[1]) * (dz ? f[2] : 1.0 - f[2]);
+        idx[q] = (int64_t)entry(i0[0] + dx, i0[1] + dy, i0[2] + dz);
+      }
+}
+
+// Entry of the dense grid's node (i, j, k), and of a hash-texture level's.
+inline size_t dense_entry(const int n[3], int i, int j, int k) { return ((size_t)k * n[1] + j) * n[0] + i; }
+inline size_t level_entry(uint32_t tsize, int l, int r, int i, int j, int k) {
+  const bool hashed = (double)r * r * r > (double)tsize;
+  const size_t e = hashed ? (size_t)(ingp_hash((uint32_t)i, (uint32_t)j, (uint32_t)k) % tsize)
+                          : ((size_t)k * r + j) * r + i;
+  return (size_t)l * tsize + e;
+}
+
 // G(x): the dense grid's trilinear interpolation, or the sum over the hash
 // texture's levels of theirs.
 template <class T>
 V3<T> grid_eval(const Scene<T>& S, const V3<T>& x) {
-  if (S.glevels == 0) {
-    const int nx = S.gn[0], ny = S.gn[1];
-    return lattice_eval(S, S.gn, [&](int i, int j, int k) { return ((size_t)k * ny + j) * nx + i; }, x);
-  }
+  if (S.glevels == 0)
+    return lattice_eval(S, S.gn, [&](int i, int j, int k) { return dense_entry(S.gn, i, j, k); }, x);
   V3<T> acc;
-  const uint32_t tsize = S.gtable;
   for (int l = 0; l < S.glevels; ++l) {
     const int r = S.gres[l];
     const int n[3] = {r, r, r};
-    const size_t first = (size_t)l * tsize;
-    const bool hashed = (double)r * r * r > (double)tsize;
-    acc = acc + lattice_eval(S, n, [&](int i, int j, int k) {
-      const size_t e = hashed ? (size_t)(ingp_hash((uint32_t)i, (uint32_t)j, (uint32_t)k) % tsize)
-                              : ((size_t)k * r + j) * r + i;
-      return first + e;
-    }, x);
+    acc = acc + lattice_eval(S, n, [&](int i, int j, int k) { return level_entry(S.gtable, l, r, i, j, k); }, x);
   }
   return acc;
 }
@@ -946,6 +968,46 @@ int orc_render_rays_jvp(const double* V, int nv, const int* F, int nf, double io
     dd = V3d(d[3 * p], d[3 * p + 1], d[3 * p + 2]);
   };
   jvp_passes(in, n, 1, given, ntan, tV, tior, tsigma, tmu, img, dimg);
+  return 0;
+}
+
+// The absorption field at n points x ([n][3]): G(x) into out ([n][3]), the
+// value the renderer's sum samples.
+int orc_field_eval(const orc_medium* medium, const double* x, int n, double* out) {
+  Scene<double> S;
+  if (!medium || !medium->mu) return 1;
+  set_medium(*medium, S);
+  for (int p = 0; p < n; ++p) {
+    const V3d G = grid_eval(S, V3d(x[3 * p], x[3 * p + 1], x[3 * p + 2]));
+    out[3 * p] = G.x; out[3 * p + 1] = G.y; out[3 * p + 2] = G.z;
+  }
+  return 0;
+}
+
+// G as a linear map of the node values or table entries: for each of n
+// points, K = 8 max(1, levels) corners (level by level, x fastest within a
+// cell) with their entry (a row of the [entries][3] values) and trilinear
+// weight: idx, w [n][K].
+int orc_field_corners(const orc_medium* medium, const double* x, int n, int64_t* idx, double* w) {
+  Scene<double> S;
+  if (!medium || !medium->mu) return 1;
+  set_medium(*medium, S);
+  const int K = 8 * std::max(1, S.glevels);
+  for (int p = 0; p < n; ++p) {
+    const V3d xp(x[3 * p], x[3 * p + 1], x[3 * p + 2]);
+    int64_t* ip = idx + (size_t)p * K;
+    double* wp = w + (size_t)p * K;
+    if (S.glevels == 0) {
+      lattice_corners(S, S.gn, [&](int i, int j, int k) { return dense_entry(S.gn, i, j, k); }, xp, ip, wp);
+      continue;
+    }
+    for (int l = 0; l < S.glevels; ++l) {
+      const int r = S.gres[l];
+      const int nn[3] = {r, r, r};
+      lattice_corners(S, nn, [&](int i, int j, int k) { return level_entry(S.gtable, l, r, i, j, k); }, xp,
+                      ip + 8 * l, wp + 8 * l);
+    }
+  }
   return 0;
 }
 

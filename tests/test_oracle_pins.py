@@ -751,6 +751,78 @@ def test_hash_texture_jvp_matches_central_differences():
     assert np.abs(dm[0]).max() > 1e-3
 
 
+def test_field_corners_are_the_renderers_field():
+    """The oracle's linear map of the field (entries and trilinear weights of
+    each level's cell) reproduces the field the optical-depth sum samples:
+    G at lattice-aligned points read through a one-step segment (the path
+    the renderer takes) equals sum_k w_k values[idx_k]; every level's eight
+    weights form a partition of unity, and points past the box read the
+    boundary."""
+    rng = np.random.default_rng(31)
+    lo, hi = (0.0, 0.0, 0.0), (8.0, 8.0, 8.0)
+    for med in (S.random_hash_texture(3, 6, 3, 9, lo, hi, seed=2),
+                dict(mu=rng.uniform(size=(6, 4, 5, 3)), lo=lo, hi=hi, step=0.1)):
+        key = "table" if "table" in med else "mu"
+        med[key] = med[key].astype(np.float64)
+        flat = med[key].reshape(-1, 3)
+        x = rng.uniform(-1.0, 9.0, size=(200, 3))
+        idx, w = O.field_corners(med, x)
+        G = (w[..., None] * flat[idx]).sum(axis=1)
+        np.testing.assert_allclose(O.field_eval(med, x), G, rtol=1e-13, atol=1e-14)
+        np.testing.assert_allclose(w.reshape(len(x), -1, 8).sum(axis=2), 1.0, atol=1e-14)
+        assert (w >= 0).all() and idx.min() >= 0 and idx.max() < len(flat)
+        pts = np.array([[1.0, 2.0, 3.0], [8.0, 0.0, 5.0], [4.0, 4.0, 4.0]])
+        np.testing.assert_allclose(_point_values(med, pts), O.field_eval(med, pts), rtol=1e-12, atol=1e-14)
+        far = np.array([[12.0, 3.0, -4.0]])
+        np.testing.assert_allclose(O.field_eval(med, far), O.field_eval(med, [[8.0, 3.0, 0.0]]), rtol=1e-14)
+
+
+def test_mat_smooth_loss_of_a_linear_field_is_closed_form():
+    """Eq. 16 on a field linear in x, a + B x (reproduced exactly by a dense
+    grid and by dense hash levels): mu_t(v) - mu_t(v + xi) = -B xi, so the
+    loss is (1/N) sum_i ||B xi_i||_1 for points and perturbations inside the
+    box; a zero perturbation and a constant field give 0 with no gradient."""
+    rng = np.random.default_rng(32)
+    lo, hi = (-1.0, -1.2, -0.9), (1.1, 1.0, 1.3)
+    a, B = rng.normal(size=3), rng.normal(size=(3, 3))
+    grid = S.linear_absorption_grid((4, 5, 3), lo, hi, a, B, 0.1)
+    table = np.full((2, 512, 3), 7.0)
+    for l, n in enumerate((3, 8)):
+        table[l, :n ** 3] = S.linear_absorption_grid((n, n, n), lo, hi, a / 2, B / 2, 0.1)["mu"].reshape(-1, 3)
+    tex = dict(table=table, res=[3, 8], lo=lo, hi=hi, step=0.1)
+    v = np.asarray(lo) + 0.1 + (np.asarray(hi) - np.asarray(lo) - 0.2) * rng.uniform(size=(300, 3))
+    xi = 0.05 * rng.normal(size=(300, 3))
+    xi = np.clip(v + xi, np.asarray(lo), np.asarray(hi)) - v
+    want = np.abs(xi @ B.T).sum() / 300
+    for med in (grid, tex):
+        loss, g = O.mat_smooth_loss(med, v, xi)
+        assert loss == pytest.approx(want, rel=1e-11)
+        assert g.shape == (med["table"] if "table" in med else med["mu"]).shape
+        loss0, g0 = O.mat_smooth_loss(med, v, np.zeros_like(v))
+        assert loss0 == 0.0 and not g0.any()
+    const = dict(grid, mu=np.broadcast_to([0.3, 0.1, 0.2], grid["mu"].shape).copy())
+    loss, g = O.mat_smooth_loss(const, v, xi)
+    assert loss < 1e-14
+
+
+def test_mat_smooth_gradient_matches_central_differences():
+    """The loss is piecewise linear in the values: away from a channel
+    difference of zero, central differences along a random direction of
+    the table match the gradient (hashed levels included)."""
+    rng = np.random.default_rng(33)
+    tex = S.random_hash_texture(3, 6, 3, 9, (-1.0, -1.0, -1.0), (1.0, 1.0, 1.0), seed=4)
+    tex["table"] = tex["table"].astype(np.float64)
+    v = rng.uniform(-1.0, 1.0, size=(80, 3))
+    xi = 0.1 * rng.normal(size=(80, 3))
+    loss, g = O.mat_smooth_loss(tex, v, xi)
+    for _ in range(3):
+        u = rng.normal(size=tex["table"].shape)
+        eps = 1e-7
+        lp = O.mat_smooth_loss(dict(tex, table=tex["table"] + eps * u), v, xi)[0]
+        lm = O.mat_smooth_loss(dict(tex, table=tex["table"] - eps * u), v, xi)[0]
+        assert (lp - lm) / (2 * eps) == pytest.approx(float((g * u).sum()), rel=1e-6)
+
+
 def test_image_is_linear_in_the_environment():
     """Escaped radiance is read from the map and weighted by a throughput
     that does not depend on it (Sec. 3.4 steps 3-5), so the image is linear
