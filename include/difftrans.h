@@ -55,7 +55,9 @@ typedef void* dt_stream; /* cudaStream_t */
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* dt_last_error(void);
-/* Library version string. */
+/* Library version string, "difftrans-gb300 <major>.<minor> (sm_103a)"; the
+ * minor number changes with every change of a struct's layout (0.2: dt_medium
+ * gained the hash-texture fields). */
 const char* dt_version(void);
 
 /* ------------------------------------------------------------------------
