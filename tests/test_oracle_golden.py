@@ -23,3 +23,14 @@ def test_oracle_matches_golden(name, fn):
     np.testing.assert_allclose(now["image_sum"], gold["image_sum"], rtol=1e-12)
     for k, v in gold["pixels"].items():
         np.testing.assert_allclose(now["pixels"][k], v, rtol=1e-12, atol=1e-15)
+
+
+def test_oracle_matches_golden_with_absorption_fields():
+    with open(os.path.join(HERE, "golden", "oracle_icosphere.json")) as f:
+        gold = json.load(f)["icosphere_textured"]
+    now = G.textured_fixture()
+    for name in ("grid", "hash_texture"):
+        assert now[name]["counters"] == gold[name]["counters"]
+        np.testing.assert_allclose(now[name]["image_sum"], gold[name]["image_sum"], rtol=1e-12)
+        for k, v in gold[name]["pixels"].items():
+            np.testing.assert_allclose(now[name]["pixels"][k], v, rtol=1e-12, atol=1e-15)
