@@ -28,7 +28,10 @@
  *    float[n_views][height][width][3] with row 0 at the top.
  *  - Return value: DT_OK, or an error code with a message in dt_last_error()
  *    (thread-local).  Argument errors are detected on the host before any
- *    work is enqueued.  Errors that only the GPU can see (a full segment
+ *    work is enqueued.  The contents of device arrays are not inspected on
+ *    the host: every entry of F must lie in [0, nv) and V must be finite
+ *    (the kernels index V, N and the gradients with F unchecked, so an
+ *    out-of-range entry is undefined behaviour).  Errors that only the GPU can see (a full segment
  *    arena, a traversal stack overflow) are recorded in the workspace's
  *    device status word and reported by dt_read_stats; the affected work is
  *    dropped, never written out of bounds.
