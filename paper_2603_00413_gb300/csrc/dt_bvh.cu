@@ -18,9 +18,13 @@ extern dt_tuning g_tuning;
 // three vertices with 64-bit integer atomics: integer addition is
 // associative, so the sums -- and every ray that depends on them -- are the
 // same bits on every run whatever order the atomics land in.  A second pass
-// converts to float and applies the 1/3.
+// converts to float and applies the 1/3.  Both conversions are FP32: the
+// scale is a power of two, so u * 2^40 is exact in float (|u| <= 1) and the
+// integer is u's value rounded to 2^-40; the finish rounds the sum to float
+// once and divides by 3 with IEEE rounding.
 // ---------------------------------------------------------------------------
-constexpr double kNormalFix = 1099511627776.0;  // 2^40
+constexpr float kNormalFix = 0x1p40f;
+constexpr float kNormalUnfix = 0x1p-40f;
 
 __global__ void k_face_normals_scatter(const float* __restrict__ V, const int32_t* __restrict__ F, int32_t nf,
                                        unsigned long long* __restrict__ acc) {
@@ -31,8 +35,8 @@ __global__ void k_face_normals_scatter(const float* __restrict__ V, const int32_
     const float lc = len(c);
     if (!(lc > 0.0f)) continue;  // a zero-area face has no unit normal and adds nothing
     const float3 u = mk(c.x / lc, c.y / lc, c.z / lc);
-    const long long q[3] = {__double2ll_rn((double)u.x * kNormalFix), __double2ll_rn((double)u.y * kNormalFix),
-                            __double2ll_rn((double)u.z * kNormalFix)};
+    const long long q[3] = {__float2ll_rn(u.x * kNormalFix), __float2ll_rn(u.y * kNormalFix),
+                            __float2ll_rn(u.z * kNormalFix)};
     const int idx[3] = {i0, i1, i2};
 #pragma unroll
     for (int k = 0; k < 3; ++k)
@@ -43,7 +47,7 @@ __global__ void k_face_normals_scatter(const float* __restrict__ V, const int32_
 
 __global__ void k_normals_finish(const unsigned long long* __restrict__ acc, int64_t n3, float* __restrict__ N) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x)
-    N[i] = (float)((double)(long long)acc[i] * (1.0 / kNormalFix) / 3.0);
+    N[i] = __fdiv_rn(__ll2float_rn((long long)acc[i]) * kNormalUnfix, 3.0f);
 }
 
 __global__ void k_face_normals_backward(const float* __restrict__ V, const int32_t* __restrict__ F, int32_t nf,

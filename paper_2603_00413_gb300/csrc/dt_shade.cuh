@@ -151,10 +151,6 @@ __device__ __forceinline__ float3 absorption_with_depth(float3 sigma, float t, f
   return mk(expf(-(sigma.x * t + S.x)), expf(-(sigma.y * t + S.y)), expf(-(sigma.z * t + S.z)));
 }
 
-// Backward of Eq. 13 for face f.  Its unit normal u = c/|c|, c = e1 x e2,
-// feeds (1/3) u to each of its vertices, so du = (1/3)(dN_v0 + dN_v1 +
-// dN_v2); dc = (du - u (u.du)) / |c|; c = e1 x e2 gives de1 = e2 x dc,
-// de2 = dc x e1; then dv1 += de1, dv2 += de2, dv0 -= de1 + de2 (atomics).
 // Moller-Trumbore of one triangle (v0, e1 = v1 - v0, e2 = v2 - v0): (t, b1,
 // b2) with o + t d = v0 + b1 e1 + b2 e2; false when d is parallel to the
 // plane.  The traversal's leaf test evaluates the same expressions in the
@@ -174,6 +170,10 @@ __device__ __forceinline__ bool intersect_known(float3 o, float3 d, float3 v0, f
   return true;
 }
 
+// Backward of Eq. 13 for face f.  Its unit normal u = c/|c|, c = e1 x e2,
+// feeds (1/3) u to each of its vertices, so du = (1/3)(dN_v0 + dN_v1 +
+// dN_v2); dc = (du - u (u.du)) / |c|; c = e1 x e2 gives de1 = e2 x dc,
+// de2 = dc x e1; then dv1 += de1, dv2 += de2, dv0 -= de1 + de2 (atomics).
 __device__ __forceinline__ void face_normal_backward_one(const float* __restrict__ V, const int32_t* __restrict__ F,
                                                          int f, const float* __restrict__ dN, float* __restrict__ dV) {
   const int i0 = F[3 * f], i1 = F[3 * f + 1], i2 = F[3 * f + 2];
