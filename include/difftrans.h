@@ -70,7 +70,8 @@ const char* dt_version(void);
  * float[nv][3] is overwritten.  The sums are accumulated in 64-bit fixed
  * point (2^-40) in d_scratch (>= dt_vertex_normals_scratch_size bytes,
  * 8-byte aligned, contents undefined afterwards), so the result is the same
- * bits on every run.  A face of zero area yields NaN normals.
+ * bits on every run.  A face of zero area has no unit normal and adds
+ * nothing to its vertices' normals.
  * ------------------------------------------------------------------------ */
 dt_status dt_vertex_normals_scratch_size(int32_t nv, size_t* bytes);
 dt_status dt_vertex_normals(const float* d_V, int32_t nv, const int32_t* d_F, int32_t nf, float* d_N,
@@ -87,9 +88,11 @@ dt_status dt_vertex_normals(const float* d_V, int32_t nv, const int32_t* d_F, in
  * exits.  It allocates nothing.
  *  - nv > 1048576 (2^20) is rejected with DT_ERR_INVALID_ARG and a message;
  *    use dt_vertex_normals then.
- *  - The first call on each device looks up the array's device address
- *    (with that device current) and keeps it; make that first call before
- *    any stream capture.
+ *  - The first call in each CUDA context (normally one per device: its
+ *    primary context) looks up the array's device address, with that device
+ *    current, and keeps it for that context; make that first call before any
+ *    stream capture.  A context made anew (after cudaDeviceReset) gets its
+ *    own lookup on its first call.
  *  - Every call on a device shares the one array and it keeps the last
  *    call's contents (each call clears the part it uses first).  Calls whose
  *    work overlaps on the GPU -- on different streams, or from different

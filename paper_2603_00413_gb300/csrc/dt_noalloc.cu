@@ -12,8 +12,11 @@
 // The array is a file-scope static __device__ variable of kNoAllocMaxVertices
 // * 3 64-bit words (24 MiB).  Every GPU that loads the library holds it until
 // the process exits.  Host code cannot use the array's name as a device
-// address, so the first call on each device looks the address up with
-// cudaGetSymbolAddress (with that device current) and keeps it.
+// address, so the first call in each CUDA context (one per device, unless
+// the context is destroyed and made again, as cudaDeviceReset does) looks the
+// address up with cudaGetSymbolAddress, with that device current, and keeps
+// it for that context.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -34,25 +37,93 @@ constexpr int32_t kNoAllocMaxVertices = 1 << 20;
 static __device__ __align__(256) unsigned long long g_normals_scratch[(size_t)kNoAllocMaxVertices * 3];
 
 namespace {
-std::mutex g_noalloc_mu;
-unsigned long long* g_noalloc_ptr[64] = {nullptr};
+// The array's address is a property of the module loaded into one CUDA
+// context: a context made anew (cudaDeviceReset, then any call) loads the
+// module again, possibly elsewhere.  So the cache is keyed on the context's
+// id, which the driver never gives to another context in this process.  The
+// two driver calls are reached through the runtime's entry-point query, so
+// the library does not link the driver library itself.
+typedef CUresult (*PfnCtxGetCurrent)(CUcontext*);
+typedef CUresult (*PfnCtxGetId)(CUcontext, unsigned long long*);
 
-// Device address of the array on the current device (looked up once per
-// device).
+constexpr int kCacheSlots = 64;
+struct CacheSlot {
+  unsigned long long ctx_id;
+  unsigned long long* ptr;
+};
+
+std::mutex g_noalloc_mu;
+CacheSlot g_noalloc_cache[kCacheSlots] = {};
+int g_noalloc_used = 0;
+PfnCtxGetCurrent g_ctx_get_current = nullptr;
+PfnCtxGetId g_ctx_get_id = nullptr;
+
+dt_status resolve_driver_calls() {
+  if (g_ctx_get_current && g_ctx_get_id) return DT_OK;
+  void* f1 = nullptr;
+  void* f2 = nullptr;
+  cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = cudaDriverEntryPointSymbolNotFound;
+  cudaError_t e1 = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1);
+  cudaError_t e2 = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+  if (e1 != cudaSuccess || e2 != cudaSuccess || q1 != cudaDriverEntryPointSuccess ||
+      q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+    return set_error(DT_ERR_CUDA, "looking up cuCtxGetCurrent/cuCtxGetId: %s",
+                     cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
+  g_ctx_get_current = (PfnCtxGetCurrent)f1;
+  g_ctx_get_id = (PfnCtxGetId)f2;
+  return DT_OK;
+}
+
+// Id of the current context; *id = 0 when no context is current yet.
+dt_status current_context_id(unsigned long long* id) {
+  CUcontext ctx = nullptr;
+  CUresult r = g_ctx_get_current(&ctx);
+  if (r != CUDA_SUCCESS) return set_error(DT_ERR_CUDA, "cuCtxGetCurrent failed (%d)", (int)r);
+  *id = 0;
+  if (!ctx) return DT_OK;
+  r = g_ctx_get_id(ctx, id);
+  if (r != CUDA_SUCCESS) return set_error(DT_ERR_CUDA, "cuCtxGetId failed (%d)", (int)r);
+  return DT_OK;
+}
+
+// Device address of the array in the current context (looked up once per
+// context, with the context's device current).
 dt_status noalloc_scratch(unsigned long long** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return set_error(DT_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
-  if (dev < 0 || dev >= 64) return set_error(DT_ERR_INVALID_ARG, "device index %d out of range", dev);
   std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_normals_scratch);
-    if (e != cudaSuccess || !p)
-      return set_error(DT_ERR_CUDA, "cudaGetSymbolAddress of the normals scratch: %s", cudaGetErrorString(e));
-    g_noalloc_ptr[dev] = (unsigned long long*)p;
+  dt_status st = resolve_driver_calls();
+  if (st != DT_OK) return st;
+  unsigned long long id = 0;
+  st = current_context_id(&id);
+  if (st != DT_OK) return st;
+  if (id) {
+    for (int i = 0; i < g_noalloc_used; ++i)
+      if (g_noalloc_cache[i].ctx_id == id) {
+        *out = g_noalloc_cache[i].ptr;
+        return DT_OK;
+      }
   }
-  *out = g_noalloc_ptr[dev];
+  // set-up for this context: the symbol lookup also makes the device's
+  // primary context current if no context was yet
+  void* p = nullptr;
+  e = cudaGetSymbolAddress(&p, g_normals_scratch);
+  if (e != cudaSuccess || !p)
+    return set_error(DT_ERR_CUDA, "cudaGetSymbolAddress of the normals scratch: %s", cudaGetErrorString(e));
+  if (!id) {
+    st = current_context_id(&id);
+    if (st != DT_OK) return st;
+  }
+  if (id) {
+    if (g_noalloc_used < kCacheSlots) {
+      g_noalloc_cache[g_noalloc_used++] = CacheSlot{id, (unsigned long long*)p};
+    } else {  // more contexts than slots in one process: reuse the oldest slot
+      for (int i = 1; i < kCacheSlots; ++i) g_noalloc_cache[i - 1] = g_noalloc_cache[i];
+      g_noalloc_cache[kCacheSlots - 1] = CacheSlot{id, (unsigned long long*)p};
+    }
+  }
+  *out = (unsigned long long*)p;
   return DT_OK;
 }
 }  // namespace
