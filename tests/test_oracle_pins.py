@@ -316,6 +316,55 @@ def test_jitter_offsets_are_uniform_and_deterministic():
     assert chi2 < 40.0  # 15 dof, p ~ 5e-4
 
 
+def test_pcg_hash_matches_values_worked_from_its_definition():
+    """The PCG hash of Jarzynski & Olano (JCGT 2020): state = v * 747796405 +
+    2891336453; word = ((state >> ((state >> 28) + 4)) ^ state) * 277803737;
+    out = (word >> 22) ^ word, all modulo 2^32.  Values worked out step by
+    step (hex):
+      v = 0:          state ac564b05, shift 10 + 4 = 14, xor ac54fa5c,
+                      word 07bb2ffc, out 07bb2fe2 = 129708002
+      v = 1:          state d8e8c2ba, shift 13 + 4 = 17, xor d8e8aece,
+                      word a8bee89e, out a8beea3c = 2831084092
+      v = ffffffff:   state 7fc3d350, shift 7 + 4 = 11, xor 7fcc2b2a,
+                      word e62a4a9a, out e62a4902 = 3861530882
+      v = 3039 (12345): state 0f64e252, shift 0 + 4 = 4, xor 0f92ac77,
+                      word f45eaedf, out f45ead0e = 4099845390
+    A wrong multiplier, increment, shift or final xor changes every one."""
+    assert O.pcg_hash(0) == 129708002
+    assert O.pcg_hash(1) == 2831084092
+    assert O.pcg_hash(0xFFFFFFFF) == 3861530882
+    assert O.pcg_hash(12345) == 4099845390
+
+
+def test_jitter_offset_matches_the_chained_hash_worked_by_hand():
+    """The jitter of sample s of pixel p in view v with seed S chains the hash
+    as h = pcg(pcg(pcg(pcg(S_lo ^ pcg(S_hi)) ^ v) ^ p) ^ s) and offsets the
+    sample by ((pcg(h) >> 8) 2^-24, (pcg(h ^ 9e3779b9) >> 8) 2^-24) inside
+    its pixel.  For S = 77, v = 2, p = 5, s = 1 (worked with the values of the
+    hash above): pcg(0) = 07bb2fe2, 77 ^ that = 07bb2faf -> 86bc5bbc; ^ 2 ->
+    7ac1f45f; ^ 5 -> bea75399; ^ 1 -> 9cad4b68 = h; pcg(h) = 308feb49 ->
+    3182571 / 2^24 = 0.18969601392745972; pcg(h ^ 9e3779b9) = 2d5c41a1 ->
+    2972737 / 2^24 = 0.1771889328956604.  The offset is read back from the
+    oracle's jittered camera ray by inverting the pinhole projection."""
+    W = H = 8
+    cam = S.camera((0.3, -0.2, 3.0), (0.0, 0.1, 0.0), (0, 1, 0), 40.0, W, H)
+    _, d = O.camera_rays(cam, spp=2, jitter=1, seed=77, view=2)
+    ray = (0 * W + 5) * 2 + 1                     # pixel (5, 0), sample 1
+    fwd = _unit(np.asarray(cam.at, float) - np.asarray(cam.eye, float))
+    right = _unit(np.cross(fwd, cam.up))
+    up = np.cross(right, fwd)
+    th = math.tan(math.radians(cam.fov_y_deg) / 2)
+    v = d[ray] / (d[ray] @ fwd)
+    sx = ((v @ right) / (th * W / H) + 1.0) * W / 2  # px + jx
+    sy = (1.0 - (v @ up) / th) * H / 2               # py + jy
+    assert sx - 5 == pytest.approx(3182571 / 2.0 ** 24, abs=1e-9)
+    assert sy - 0 == pytest.approx(2972737 / 2.0 ** 24, abs=1e-9)
+    # 77 ^ pcg(0) worked above
+    assert 77 ^ 0x07BB2FE2 == 0x07BB2FAF and O.pcg_hash(0x07BB2FAF) == 0x86BC5BBC
+    assert O.pcg_hash(0x86BC5BBC ^ 2) == 0x7AC1F45F and O.pcg_hash(0x7AC1F45F ^ 5) == 0xBEA75399
+    assert O.pcg_hash(0xBEA75399 ^ 1) == 0x9CAD4B68
+
+
 # ---------------------------------------------------------------------------
 # the whole ray tree (Sec. 3.4 steps 1-5)
 # ---------------------------------------------------------------------------
