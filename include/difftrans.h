@@ -339,8 +339,10 @@ dt_status dt_render_batch_backward(const dt_batch_entry* entries, int32_t n, con
 /* ------------------------------------------------------------------------
  * Debug / parity: every segment of the tape in arena order (level by
  * level).  d_seg_i int32[cap][4] = (sample index, heap node id, hit triangle
- * or -1, flags); d_seg_f float[cap][9] = (t, b1, b2, origin xyz, direction
- * xyz); available after a render with tape_mode 0 only (after tape_mode 1
+ * or -1, flags); d_seg_f float[cap][15] = (t, b1, b2, origin xyz, direction
+ * xyz, throughput W rgb, contribution W * E(d) rgb of a segment that escaped
+ * -- Sec. 3.4 step 3 before the 1/spp of the pixel average -- and 0 for a
+ * hit); available after a render with tape_mode 0 only (after tape_mode 1
  * nothing is written).  Sample index = (view*height*width + py*width + px)*spp + s; the
  * heap node id of a camera ray is 1 and the children of node m are 2m
  * (reflected) and 2m+1 (refracted).  Flag bits: 4 inside (hit from inside),

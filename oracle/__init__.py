@@ -38,6 +38,7 @@ SEG_MISS = 512
 SEG_UNSTABLE = 1024
 SEG_DEGENERATE = SEG_NEAR_EDGE | SEG_NEAR_TIE | SEG_NEAR_CRITICAL | SEG_GRAZING | SEG_NEAR_POLE | SEG_UNSTABLE
 
+SEG_F = 15  # doubles per segment record (see render)
 COUNTER_NAMES = ("segments", "hits", "misses", "discarded", "leaks", "backfacing", "tir", "degenerate")
 
 
@@ -79,6 +80,7 @@ def _load():
         lib.orc_render_jvp.argtypes = [P, I, P, I, D, P, P, I, I, P, I, I, I, I, I, U64, I, D,
                                        I, P, P, P, P, P, M, P]
         lib.orc_render_rays_jvp.argtypes = [P, I, P, I, D, P, P, I, I, P, P, I, I, D, I, P, P, P, P, P, M, P]
+        lib.orc_trace_steps.argtypes = [P, I, P, I, D, P, P, I, I, P, P, P, P, I, I, D, P, P, M]
         lib.orc_medium_depth.argtypes = [M, P, P, P, I, P]
         lib.orc_field_eval.argtypes = [M, P, I, P]
         lib.orc_field_corners.argtypes = [M, P, I, P, P]
@@ -253,7 +255,11 @@ def render(V, F, ior, sigma, env, cam, max_depth: int, spp: int = 1, jitter: int
 
     Returns dict(img [H,W,3], discard [H,W,3], pix_flags [H,W], pix_sig [H,W],
     counters {...}) and, with segments=True, seg_i [n,4] = (ray, heap node,
-    tri, flags) and seg_f [n,9] = (t, b1, b2, origin xyz, direction xyz).
+    tri, flags) and seg_f [n,15] = (t, b1, b2, origin xyz, direction xyz,
+    throughput W rgb, contribution W * E(d) rgb of an escaped segment, 0 for
+    a hit); W is the product of the A R or A T factors of Sec. 3.4 steps 4-5
+    over the segment's ancestors, so the sample's radiance is the sum of the
+    contributions.
     discard is the path weight lost to the depth limit or to a backfacing
     shading normal.  probe > 0 re-traces every primary ray tilted by probe
     radians four ways and flags pixels whose path events change
@@ -288,7 +294,7 @@ def _run_with_segments(fn, args, segments, nseg, cnt, m=None):
     fn(*args, None, None, 0, _p(nseg), _p(cnt), _mp(m))
     n = int(nseg[0])
     seg_i = np.zeros((max(n, 1), 4), np.int32)
-    seg_f = np.zeros((max(n, 1), 9))
+    seg_f = np.zeros((max(n, 1), SEG_F))
     fn(*args, _p(seg_i), _p(seg_f), n, _p(nseg), _p(cnt), _mp(m))
     return seg_i[:n], seg_f[:n]
 
@@ -317,6 +323,29 @@ def render_rays(V, F, ior, sigma, env, o, d, max_depth: int, t_min: float = 1e-5
     if segments:
         out["seg_i"], out["seg_f"] = seg_i, seg_f
     return out
+
+
+def trace_steps(V, F, ior, sigma, env, o, d, src, k, max_depth: int, t_min: float = 1e-5, medium=None):
+    """One step of the FP64 tree (Sec. 3.4 steps 1-5) from each of n given
+    segments: origin o [n,3], unit direction d [n,3], the triangle it leaves
+    src [n] (-1: none) and its depth index k [n].  Returns (seg_i [n,3,4],
+    seg_f [n,3,SEG_F]): the records of the segment (node 1) and of its
+    reflected (node 2) and refracted (node 3) child, as render() writes them
+    with the segment's throughput set to 1; node 0 marks a child that does
+    not exist.  A child's own hit is not shaded (its flags say discarded)."""
+    V, F = _d(V), _i(F)
+    sigma, env = _d(sigma).reshape(3), _d(env)
+    o, d = _d(o).reshape(-1, 3), _d(d).reshape(-1, 3)
+    n = o.shape[0]
+    src, k = _i(np.broadcast_to(src, (n,))), _i(np.broadcast_to(k, (n,)))
+    seg_i = np.zeros((max(n, 1), 3, 4), np.int32)
+    seg_f = np.zeros((max(n, 1), 3, SEG_F))
+    m, keep = _medium(medium)
+    _load().orc_trace_steps(_p(V), V.shape[0], _p(F), F.shape[0], float(ior), _p(sigma), _p(env), env.shape[1],
+                            env.shape[0], _p(o), _p(d), _p(src), _p(k), n, int(max_depth), float(t_min), _p(seg_i),
+                            _p(seg_f), _mp(m))
+    del keep
+    return seg_i[:n], seg_f[:n]
 
 
 def render_jvp(V, F, ior, sigma, env, cam, max_depth: int, tV=None, tior=None, tsigma=None,

@@ -500,6 +500,8 @@ struct SegRec {
   int32_t ray, node, tri, flags;
   double t, b1, b2;
   double o[3], d[3];
+  double w[3];  // the segment's throughput: the product of A R or A T over its ancestors
+  double c[3];  // an escaped segment's contribution w * E(d) to its sample's radiance; 0 otherwise
 };
 
 struct PixelState {
@@ -521,13 +523,15 @@ V3<T> radiance(const Scene<T>& S, const V3<T>& o, const V3<T>& d, int k, uint32_
                bool in_medium, const V3d& W, PixelState& P) {
   Hit h = closest_hit(S.Vd, S.F, S.nf, val3(o), val3(d), src, S.t_min);
   SegRec rec{P.ray, (int32_t)node, h.tri, h.flags, h.t, h.b1, h.b2,
-             {val(o.x), val(o.y), val(o.z)}, {val(d.x), val(d.y), val(d.z)}};
+             {val(o.x), val(o.y), val(o.z)}, {val(d.x), val(d.y), val(d.z)}, {W.x, W.y, W.z}, {0.0, 0.0, 0.0}};
   P.counters[0]++;
   V3<T> L;
   if (h.tri < 0) {  // step 3: no intersection -> environment
     rec.flags |= SEG_MISS;
     uint64_t cell = 0;
     L = env_lookup(S.env, S.env_w, S.env_h, d, &rec.flags, &cell);
+    const V3d Lv = val3(L);
+    rec.c[0] = W.x * Lv.x; rec.c[1] = W.y * Lv.y; rec.c[2] = W.z * Lv.z;
     sig_mix(P.sig, cell);
     P.counters[2]++;
     // an interior miss (a leak through a crack) returns the environment
@@ -794,6 +798,10 @@ int orc_camera_rays(const double* cam, int width, int height, int spp, int jitte
 
 uint32_t orc_pcg_hash(uint32_t v) { return pcg_hash(v); }
 
+// doubles per segment in seg_f: t, b1, b2, origin xyz, direction xyz,
+// throughput rgb, escaped contribution rgb
+constexpr int kSegF = 15;
+
 static int write_outputs(int npix, const std::vector<V3d>& im, const std::vector<PixelState>& ps,
                          const std::vector<std::vector<SegRec>>& segs, bool keep, double* img, double* discard,
                          int* pix_flags, uint64_t* pix_sig, int32_t* seg_i, double* seg_f, int64_t cap,
@@ -812,9 +820,11 @@ static int write_outputs(int npix, const std::vector<V3d>& im, const std::vector
           int32_t* si = seg_i + 4 * total;
           si[0] = r.ray; si[1] = r.node; si[2] = r.tri; si[3] = r.flags;
           if (seg_f) {
-            double* sf = seg_f + 9 * total;
+            double* sf = seg_f + kSegF * total;
             sf[0] = r.t; sf[1] = r.b1; sf[2] = r.b2;
-            for (int c = 0; c < 3; ++c) { sf[3 + c] = r.o[c]; sf[6 + c] = r.d[c]; }
+            for (int c = 0; c < 3; ++c) {
+              sf[3 + c] = r.o[c]; sf[6 + c] = r.d[c]; sf[9 + c] = r.w[c]; sf[12 + c] = r.c[c];
+            }
           }
         }
         ++total;
@@ -832,7 +842,8 @@ static int write_outputs(int npix, const std::vector<V3d>& im, const std::vector
 //  pix_flags (nullable): OR of segment flags per pixel; pix_sig (nullable):
 //  hash of the event signature per pixel; seg_i (nullable): [cap][4] = (ray,
 //  heap node, tri, flags) in pixel order, pre-order within a pixel; seg_f:
-//  [cap][9] = (t, b1, b2, origin xyz, direction xyz); n_seg: number of
+//  [cap][15] = (t, b1, b2, origin xyz, direction xyz, throughput rgb, the
+//  escaped contribution throughput * E(d) rgb, 0 for a hit); n_seg: number of
 //  segments (written even when cap is too small); counters (nullable): [8] =
 //  segments, hits, misses, discarded, leaks, backfacing, tir, degenerate.
 // Returns 0, or 1 when cap was too small (n_seg tells how many are needed).
@@ -887,6 +898,52 @@ int orc_render_rays(const double* V, int nv, const int* F, int nf, double ior, c
   if (probe_delta > 0.0) probe_stability(n, 1, S, given, probe_delta, ps);
   return write_outputs(n, im, ps, segs, keep, img, discard, pix_flags, pix_sig, seg_i, seg_f, cap, n_seg,
                        counters);
+}
+
+// One step of the tree from given segments, for parity at every depth:
+// segment i starts at o_i in the unit direction d_i, leaves triangle src_i
+// (-1: none) and has depth index k_i (its number of earlier surface
+// interactions).  Its closest hit, its shading (Sec. 3.4 steps 1-5) and its
+// children's first intersections follow the tree definition exactly as in
+// orc_render; the recursion stops after the children (a child's own hit is
+// then counted as discarded).  Each segment starts with throughput 1.
+// seg_i: [n][3][4] = (i, heap node 1 / 2 / 3, tri, flags) for the segment
+// and its reflected and refracted child, node 0 where there is none;
+// seg_f: [n][3][15] as orc_render's records.
+int orc_trace_steps(const double* V, int nv, const int* F, int nf, double ior, const double* sigma,
+                    const double* env, int env_w, int env_h, const double* o, const double* d, const int* src,
+                    const int* k, int n, int max_depth, double t_min, int32_t* seg_i, double* seg_f,
+                    const orc_medium* medium) {
+  Inputs in{V, nv, F, nf, ior, sigma, env, env_w, env_h, nullptr, n, 1, max_depth, 1, 0, 0, 0, t_min, medium};
+  Scene<double> S;
+  setup_scene(in, S);
+  vertex_normals(S.V, F, nf, S.N);
+  for (int64_t j = 0; j < (int64_t)n * 3 * 4; ++j) seg_i[j] = 0;
+  for (int64_t j = 0; j < (int64_t)n * 3 * kSegF; ++j) seg_f[j] = 0.0;
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int i = 0; i < n; ++i) {
+    std::vector<SegRec> recs;
+    PixelState P;
+    P.segs = &recs;
+    P.ray = i;
+    // the depth test is the only use of the depth index: a segment below
+    // the limit is shaded and its children are intersected at the limit
+    const int kk = k[i] < max_depth ? max_depth - 1 : max_depth;
+    radiance(S, V3d(o[3 * i], o[3 * i + 1], o[3 * i + 2]), V3d(d[3 * i], d[3 * i + 1], d[3 * i + 2]), kk, 1u,
+             src ? src[i] : -1, false, V3d(1.0, 1.0, 1.0), P);
+    for (const SegRec& r : recs) {
+      if (r.node < 1 || r.node > 3) continue;
+      const int64_t slot = (int64_t)i * 3 + (r.node - 1);
+      int32_t* si = seg_i + 4 * slot;
+      si[0] = i; si[1] = r.node; si[2] = r.tri; si[3] = r.flags;
+      double* sf = seg_f + kSegF * slot;
+      sf[0] = r.t; sf[1] = r.b1; sf[2] = r.b2;
+      for (int c = 0; c < 3; ++c) {
+        sf[3 + c] = r.o[c]; sf[6 + c] = r.d[c]; sf[9 + c] = r.w[c]; sf[12 + c] = r.c[c];
+      }
+    }
+  }
+  return 0;
 }
 
 }  // extern "C"

@@ -237,6 +237,7 @@ def vertex_normals(V, F, out=None, stream=None, scratch=None):
 
 
 NOALLOC_MAX_VERTICES = 1 << 20
+SEG_F = 15  # floats per segment of dump_segments
 
 
 def vertex_normals_noalloc(V, F, out, stream=None):
@@ -578,14 +579,15 @@ def render_backward(tape: Tape, grad_out, stream=None, bws=None, env_grad: bool 
 
 def dump_segments(tape: Tape, stream=None):
     """Every segment of the tape: (seg_i int32 [n,4] = (sample, heap node, tri,
-    flags), seg_f float32 [n,9] = (t, b1, b2, origin, direction))."""
+    flags), seg_f float32 [n,15] = (t, b1, b2, origin, direction, throughput
+    W, contribution W * E(d) of an escaped segment or 0))."""
     if tape.ws.level_capacity:
         raise ValueError("a checkpointed tape keeps no hit records to dump")
     stats = tape.stats if tape.stats is not None else read_stats(tape.ws, stream)
     n = stats["segments"]
     dev = tape.ws.buf.device
     si = torch.empty(max(n, 1), 4, dtype=torch.int32, device=dev)
-    sf = torch.empty(max(n, 1), 9, dtype=torch.float32, device=dev)
+    sf = torch.empty(max(n, 1), SEG_F, dtype=torch.float32, device=dev)
     _check(load_library().dt_dump_segments(_ptr(tape.ws.buf), tape.ws.bytes, _ptr(si), _ptr(sf), n,
                                            _stream(stream)))
     return si[:n], sf[:n]

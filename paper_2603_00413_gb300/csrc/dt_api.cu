@@ -205,7 +205,7 @@ using namespace dt;
 extern "C" {
 
 const char* dt_last_error(void) { return g_err; }
-const char* dt_version(void) { return "difftrans-gb300 0.2 (sm_103a)"; }
+const char* dt_version(void) { return "difftrans-gb300 0.3 (sm_103a)"; }
 
 dt_status dt_vertex_normals_scratch_size(int32_t nv, size_t* bytes) {
   if (nv < 1 || !bytes) return set_error(DT_ERR_INVALID_ARG, "need nv >= 1 and a size pointer");

@@ -655,23 +655,40 @@ __global__ void __launch_bounds__(kShadeThreads, kShadeMinBlocks) k_shade(WsView
 }
 
 // every segment of the arena, level by level, for parity checks
+// (15 floats per segment: t, b1, b2, origin, direction, throughput W and
+// an escaped segment's contribution W * E(d), which k_shade added to its
+// pixel divided by spp).
+constexpr int kSegF = 15;
 __global__ void k_dump(WsView W, int32_t* __restrict__ si, float* __restrict__ sf, unsigned long long cap) {
   const WsHeader* H = W.hdr;
   if (H->ring) return;  // hit records of checkpointed renders are not kept
   const int nl = (int)H->n_levels;
   const unsigned long long total = nl > 0 ? H->level_start[nl] : 0ull;
   const unsigned long long lim = total < cap ? total : cap;
+  const int n_scenes = W.th->n;
   for (unsigned long long a = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; a < lim;
        a += (unsigned long long)gridDim.x * blockDim.x) {
-    const float4 ro = W.ray_o[a], rd = W.ray_d[a], hh = W.hit[a];
-    si[4 * a + 0] = __float_as_int(ro.w);
+    const float4 ro = W.ray_o[a], rd = W.ray_d[a], rw = W.ray_w[a], hh = W.hit[a];
+    const uint32_t sample = __float_as_uint(ro.w);
+    const int tri = __float_as_int(hh.w);
+    si[4 * a + 0] = (int32_t)sample;
     si[4 * a + 1] = __float_as_int(rd.w);
-    si[4 * a + 2] = __float_as_int(hh.w);
+    si[4 * a + 2] = tri;
     si[4 * a + 3] = (int32_t)(W.sflag[a] & SF_FLAG_BITS);
-    float* f = sf + 9 * a;
+    float3 c = mk(0.f, 0.f, 0.f);
+    if (tri < 0) {  // the same lookup as k_shade's, on the segment's own scene
+      const SceneEntry& E = W.ent[find_scene(W.th->starts, n_scenes, sample)];
+      if (sample >= E.sample_start && (sample - E.sample_start) / (uint32_t)E.spp < E.pix_count) {
+        const float3 Ev = env_lookup(E.env, E.env_w, E.env_h, xyz(rd));
+        c = mk(rw.x * Ev.x, rw.y * Ev.y, rw.z * Ev.z);
+      }
+    }
+    float* f = sf + kSegF * a;
     f[0] = hh.x; f[1] = hh.y; f[2] = hh.z;
     f[3] = ro.x; f[4] = ro.y; f[5] = ro.z;
     f[6] = rd.x; f[7] = rd.y; f[8] = rd.z;
+    f[9] = rw.x; f[10] = rw.y; f[11] = rw.z;
+    f[12] = c.x; f[13] = c.y; f[14] = c.z;
   }
 }
 

@@ -58,7 +58,7 @@ def test_no_cuda_needed_for_size_queries(lib):
     assert L.dt_render_workspace_size(0, ctypes.byref(wb)) == dt.DT_ERR_INVALID_ARG
     assert L.dt_render_workspace_size(2 ** 31, ctypes.byref(wb)) == dt.DT_ERR_INVALID_ARG
     assert L.dt_backward_workspace_size(10, 5, ctypes.byref(wb)) == 0
-    assert L.dt_version() == b"difftrans-gb300 0.2 (sm_103a)"
+    assert L.dt_version() == b"difftrans-gb300 0.3 (sm_103a)"
 
 
 def test_host_side_argument_checks_fire_before_any_launch(lib):

@@ -48,7 +48,7 @@ def test_batch_forward_matches_scenes_alone(scenes):
     assert tape.stats["hits"] == sum(t.stats["hits"] for _, t in alone)
     for (img_a, _), img_b in zip(alone, imgs):
         np.testing.assert_allclose(img_b.cpu().numpy(), img_a.cpu().numpy(), rtol=1e-5, atol=1e-7)
-    assert_radiance_parity(imgs[0][0], scenes[0].oracle(0))
+    assert_radiance_parity(imgs[0][0], scenes[0].oracle(0), 0.0293)
 
 
 def test_batch_backward_matches_scenes_alone(scenes):

@@ -12,7 +12,7 @@ import torch
 
 import paper_2603_00413_gb300 as dt
 from paper_2603_00413_gb300 import scenes as S
-from tests.gpu_util import GRAD_RTOL, GpuScene, assert_radiance_parity, degenerate_pixels
+from tests.gpu_util import GRAD_RTOL, GpuScene, assert_radiance_parity, excluded_pixels
 
 pytestmark = pytest.mark.gpu
 
@@ -50,8 +50,7 @@ def test_checkpointed_forward_equals_full_tape_and_oracle(genus2):
         assert tape_c.stats[key] == tape_f.stats[key], key
     assert tape_c.stats["level_needed"] == max(tape_f.stats["level_count"])
     np.testing.assert_allclose(img_c.cpu().numpy(), img_f.cpu().numpy(), rtol=1e-6, atol=1e-7)
-    info = assert_radiance_parity(img_c[1], genus2.oracle(1))
-    assert info["excluded_frac"] < 0.25, info
+    assert_radiance_parity(img_c[1], genus2.oracle(1), 0.1656)
     with pytest.raises(ValueError):
         dt.dump_segments(tape_c)
 
@@ -82,7 +81,7 @@ def test_checkpointed_gradient_matches_oracle_derivative(genus2):
     rng = np.random.default_rng(32)
     gnp = rng.normal(size=(2, gs.height, gs.width, 3))
     gnp[1] = 0.0
-    gnp[0][degenerate_pixels(gs.oracle(0))] = 0.0
+    gnp[0][excluded_pixels(gs.oracle(0), 0.0833)] = 0.0
     _, _, _, dior, dsig = _grads(gs, torch.from_numpy(gnp.astype(np.float32)).cuda())
     p = gs.params
     tior = np.array([1.0, 0, 0, 0])

@@ -13,7 +13,7 @@ import torch
 import oracle as O
 import paper_2603_00413_gb300 as dt
 from paper_2603_00413_gb300 import scenes as S
-from tests.gpu_util import GpuScene, assert_hit_id_parity, assert_radiance_parity, degenerate_pixels
+from tests.gpu_util import GpuScene, assert_hit_id_parity, assert_radiance_parity, degenerate_pixels, step_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -55,7 +55,7 @@ def test_zero_area_faces_render_and_differentiate():
     img_0, tape_0 = g0.render()
     assert tape_d.stats["segments"] == tape_0.stats["segments"]
     np.testing.assert_allclose(img_d.cpu().numpy(), img_0.cpu().numpy(), rtol=1e-6, atol=1e-7)
-    assert_radiance_parity(img_d[0], gd.oracle(0))
+    assert_radiance_parity(img_d[0], gd.oracle(0), 0.0186)
     g = torch.randn_like(img_d)
     dVd, diord, dsigd = dt.render_backward(tape_d, g)
     dV0, dior0, dsig0 = dt.render_backward(tape_0, g)
@@ -172,18 +172,22 @@ def test_refit_tracks_moved_vertices(builder):
     np.testing.assert_array_equal(tri.cpu().numpy()[ok], otri[ok])
 
 
-def _parity(gs, view=0):
+def _parity(gs, expected_excluded, view=0):
     img, tape = gs.render()
     torch.cuda.synchronize()
     orc = gs.oracle(view, segments=True)
-    info = assert_radiance_parity(img[view], orc)
-    si, _ = dt.dump_segments(tape)
-    si = si.cpu().numpy()
+    info = assert_radiance_parity(img[view], orc, expected_excluded)
+    si, sf = dt.dump_segments(tape)
+    si, sf = si.cpu().numpy(), sf.cpu().numpy()
     npix = gs.width * gs.height
     spp = gs.params.spp
     lo, hi = view * npix * spp, (view + 1) * npix * spp
     sel = (si[:, 0] >= lo) & (si[:, 0] < hi)
-    n = assert_hit_id_parity(si[sel], orc, spp, view_offset=lo)
+    n = assert_hit_id_parity(si[sel], orc, spp, view_offset=lo, seg_gpu_f=sf[sel])
+    # and every segment of the tape, one step at a time from its own FP32 inputs
+    sit, sft = dt.dump_segments(tape)
+    step_parity(sit, sft, torch.arange(sit.shape[0], device=sit.device), gs.Vn, gs.Fn, gs.iorf, gs.sigman, gs.envn,
+                gs.params.max_depth, gs.params.t_min)
     return img, tape, orc, info, n
 
 
@@ -191,23 +195,22 @@ def test_render_glass_icosphere_matches_oracle():
     """The one-icosphere workload in full: subdivision 3, IoR 1.5, no
     absorption, 64x64 at pixel centres, depth 4, 64x32 SH environment."""
     gs = GpuScene.from_scene(S.glass_icosphere_scene())
-    img, tape, orc, info, n = _parity(gs)
+    img, tape, orc, info, n = _parity(gs, 0.0168)  # measured: 69 of 4096 pixels excluded
     st = tape.stats
     oc = orc["counters"]
     bad = degenerate_pixels(orc)
-    assert bad.sum() <= 0.02 * bad.size
     if bad.sum() == 0:
         assert st["segments"] == oc["segments"]
         assert st["hits"] == oc["hits"] and st["misses"] == oc["misses"]
         assert st["discarded"] == oc["discarded"] and st["tir"] == oc["tir"]
 
 
-@pytest.mark.parametrize("depth", [0, 1, 6])
-def test_render_absorbing_off_axis(depth):
+@pytest.mark.parametrize("depth,excluded", [(0, 0.0), (1, 0.0073), (6, 0.0089)])
+def test_render_absorbing_off_axis(depth, excluded):
     sc = S.glass_icosphere_scene(width=48, height=40)
     cam = S.camera((1.3, 0.9, 2.5), (0.05, -0.1, 0.0), (0, 1, 0), 50.0, 48, 40)
     gs = GpuScene(sc.V, sc.F, 1.45, np.array([0.5, 1.0, 1.5], np.float32), sc.env, [cam], 48, 40, depth)
-    _parity(gs)
+    _parity(gs, excluded)
 
 
 def test_sah_and_lbvh_trees_find_the_same_hits():
@@ -243,15 +246,18 @@ def test_render_genus2_multi_view_jittered():
     gs = GpuScene(V, F, 1.52, np.array([0.3, 0.1, 0.05], np.float32), env, cams, 40, 40, 8, spp=2, jitter=1,
                   seed=77)
     img, tape = gs.render()
-    for v in range(3):
+    for v, excluded in enumerate([0.1131, 0.1875, 0.1781]):
         orc = gs.oracle(v, segments=True)
-        info = assert_radiance_parity(img[v], orc)
-        assert info["excluded_frac"] < 0.25, info
-        si, _ = dt.dump_segments(tape)
-        si = si.cpu().numpy()
+        assert_radiance_parity(img[v], orc, excluded)
+        si, sf = dt.dump_segments(tape)
+        si, sf = si.cpu().numpy(), sf.cpu().numpy()
         npix = 40 * 40 * 2
         sel = (si[:, 0] >= v * npix) & (si[:, 0] < (v + 1) * npix)
-        assert_hit_id_parity(si[sel], orc, 2, view_offset=v * npix)
+        assert_hit_id_parity(si[sel], orc, 2, view_offset=v * npix, seg_gpu_f=sf[sel])
+    sit, sft = dt.dump_segments(tape)
+    info = step_parity(sit, sft, torch.arange(sit.shape[0], device=sit.device), gs.Vn, gs.Fn, gs.iorf, gs.sigman,
+                       gs.envn, 8)
+    assert info["checked_per_depth"][8] > 0, info
 
 
 def test_all_miss_view_shows_environment():
@@ -270,7 +276,7 @@ def test_single_pixel_and_single_triangle():
     env = S.sh_env_map(16, 8, 3)
     cam = S.camera((0.1, 0.1, 2.0), (0.1, 0.1, 0.0), (0, 1, 0), 30.0, 1, 1)
     gs = GpuScene(V, F, 1.5, np.zeros(3, np.float32), env, [cam], 1, 1, 3)
-    _parity(gs)
+    _parity(gs, 0.0)
 
 
 def test_arena_overflow_is_reported_and_retried():
@@ -285,7 +291,7 @@ def test_arena_overflow_is_reported_and_retried():
     img, tape = dt.render(gs.V, gs.F, gs.bvh, gs.N, gs.ior, gs.sigma, gs.env, gs.cams, 32, 32, gs.params,
                           ws=dt.Workspace(32 * 32 + 10, gs.V.device))
     assert tape.stats["status"] == dt.DT_OK and tape.ws.capacity > small.capacity
-    assert_radiance_parity(img[0], gs.oracle(0))
+    assert_radiance_parity(img[0], gs.oracle(0), 0.0293)
 
 
 def test_host_rejects_bad_arguments():

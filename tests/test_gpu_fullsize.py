@@ -10,7 +10,7 @@ import torch
 import oracle as O
 import paper_2603_00413_gb300 as dt
 from paper_2603_00413_gb300 import scenes as S
-from tests.gpu_util import GRAD_RTOL, PROBE, RAD_ATOL, RAD_RTOL
+from tests.gpu_util import EXCLUDED_MARGIN, GRAD_RTOL, PROBE, RAD_ATOL, RAD_RTOL, sample_segments_by_depth, step_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -37,34 +37,35 @@ def full():
 def _rays(sc, views, pix):
     o = np.zeros((len(views), 3))
     d = np.zeros((len(views), 3))
-    for i, (v, p) in enumerate(zip(views, pix)):
+    for v in np.unique(views):
+        sel = views == v
         oo, dd = O.camera_rays(sc.cams[v])
-        o[i], d[i] = oo[p], dd[p]
+        o[sel], d[sel] = oo[pix[sel]], dd[pix[sel]]
     return o, d
 
 
-def _sample(sc, n, seed, hits_only=False):
-    """n seeded (view, pixel) samples with their camera rays; with hits_only,
-    drawn (in rounds of candidates) among pixels whose path hits the object
-    and is not edge-degenerate."""
+def _sample(sc, n, seed):
+    """n seeded (view, pixel) samples with their camera rays."""
     rng = np.random.default_rng(seed)
-    if not hits_only:
-        views = rng.integers(0, len(sc.cams), size=n)
-        pix = rng.integers(0, 512 * 512, size=n)
-        o, d = _rays(sc, views, pix)
-        return views, pix, o, d
+    views = rng.integers(0, len(sc.cams), size=n)
+    pix = rng.integers(0, 512 * 512, size=n)
+    o, d = _rays(sc, views, pix)
+    return views, pix, o, d
+
+
+def _sample_hits(sc, n, seed):
+    """n seeded samples among the pixels whose camera ray hits the object
+    (the oracle's closest hit of the camera ray), drawn in rounds."""
+    rng = np.random.default_rng(seed)
     got_v, got_p = [], []
     for _ in range(12):
-        m = 8 * n
+        m = 6 * n
         views = rng.integers(0, len(sc.cams), size=m)
         pix = rng.integers(0, 512 * 512, size=m)
         o, d = _rays(sc, views, pix)
-        r = O.render_rays(sc.V, sc.F, sc.ior, sc.sigma, sc.env, o, d, sc.max_depth, probe=PROBE, segments=True)
-        hit = np.zeros(m, bool)
-        hit[np.unique(r["seg_i"][r["seg_i"][:, 2] >= 0, 0])] = True
-        keep = np.nonzero(hit & ((r["pix_flags"] & O.SEG_DEGENERATE) == 0))[0]
-        got_v += list(views[keep])
-        got_p += list(pix[keep])
+        hit = O.closest_hit(sc.V, sc.F, o, d, None, 1e-5)[0] >= 0
+        got_v += list(views[hit])
+        got_p += list(pix[hit])
         if len(got_v) >= n:
             break
     assert len(got_v) >= n
@@ -73,31 +74,51 @@ def _sample(sc, n, seed, hits_only=False):
     return views, pix, o, d
 
 
+def _sample_stable_hits(sc, n, seed):
+    """n seeded hit samples whose path is not excluded from parity."""
+    views, pix, o, d = _sample_hits(sc, 8 * n, seed)
+    r = O.render_rays(sc.V, sc.F, sc.ior, sc.sigma, sc.env, o, d, sc.max_depth, probe=PROBE)
+    keep = np.nonzero((r["pix_flags"] & O.SEG_DEGENERATE) == 0)[0][:n]
+    assert len(keep) == n
+    return views[keep], pix[keep], o[keep], d[keep]
+
+
+def _check_samples(img, sc, views, pix, o, d, expected_excluded):
+    r = O.render_rays(sc.V, sc.F, sc.ior, sc.sigma, sc.env, o, d, sc.max_depth, probe=PROBE)
+    bad = (r["pix_flags"] & O.SEG_DEGENERATE) != 0
+    assert bad.mean() <= expected_excluded + EXCLUDED_MARGIN, (bad.mean(), expected_excluded)
+    ok = ~bad
+    g = img.view(100, -1, 3)[torch.from_numpy(views).cuda(), torch.from_numpy(pix).cuda()].cpu().numpy()
+    err = np.abs(g - r["img"])
+    viol = (err > RAD_RTOL * np.abs(r["img"]) + RAD_ATOL) & ok[:, None]
+    rel = err[ok] / np.maximum(np.abs(r["img"][ok]), 1e-12)
+    assert not viol.any(), (int(viol.any(axis=1).sum()), float(rel.max()))
+    return int(ok.sum())
+
+
 def test_full_size_forward_sampled_pixels(full):
+    """4096 seeded (view, pixel) samples of the full render and 2048 more
+    among the pixels whose camera ray hits the object, one by one against
+    the oracle: every sample its criterion keeps within the radiance
+    tolerance, the excluded fractions bounded by their measured values (14.2
+    % of all samples; 69.1 % of the hit samples: at depth 8 most paths
+    through the two tori reflect inside several times, and a 1e-6 rad tilt
+    of the camera ray moves their radiance by more than 1e-4)."""
     sc, img, tape = full
     st = tape.stats
     assert st["status"] == dt.DT_OK
     assert st["n_levels"] == sc.max_depth + 1
     assert st["level_count"][0] == 100 * 512 * 512
-    views, pix, o, d = _sample(sc, 96, 5)
-    r = O.render_rays(sc.V, sc.F, sc.ior, sc.sigma, sc.env, o, d, sc.max_depth, probe=PROBE)
-    ok = (r["pix_flags"] & O.SEG_DEGENERATE) == 0
-    assert ok.mean() > 0.6
-    # and a sample among pixels that reach the object
-    hv, hp, ho, hd = _sample(sc, 48, 8, hits_only=True)
-    rh = O.render_rays(sc.V, sc.F, sc.ior, sc.sigma, sc.env, ho, hd, sc.max_depth)
-    gh = img.view(100, -1, 3)[torch.from_numpy(hv).cuda(), torch.from_numpy(hp).cuda()].cpu().numpy()
-    assert (np.abs(gh - rh["img"]) <= RAD_RTOL * np.abs(rh["img"]) + RAD_ATOL).all()
-    g = img.view(100, -1, 3)[torch.from_numpy(views).cuda(), torch.from_numpy(pix).cuda()].cpu().numpy()
-    err = np.abs(g - r["img"])
-    assert (err[ok] <= RAD_RTOL * np.abs(r["img"][ok]) + RAD_ATOL).all(), err[ok].max()
+    kept = _check_samples(img, sc, *_sample(sc, 4096, 5), 0.1421)
+    kept_hits = _check_samples(img, sc, *_sample_hits(sc, 2048, 8), 0.6914)
+    assert kept >= 3400 and kept_hits >= 580, (kept, kept_hits)
 
 
 def test_full_size_gradient_of_sampled_pixels(full):
     sc, img, tape = full
-    views, pix, o, d = _sample(sc, 12, 6, hits_only=True)
+    views, pix, o, d = _sample_stable_hits(sc, 24, 6)
     rng = np.random.default_rng(7)
-    gs = rng.normal(size=(12, 3))
+    gs = rng.normal(size=(24, 3))
     grad = torch.zeros(100, 512 * 512, 3, device="cuda")
     grad[torch.from_numpy(views).cuda(), torch.from_numpy(pix).cuda()] = torch.from_numpy(gs.astype(np.float32)).cuda()
     dV, dior, dsig = dt.render_backward(tape, grad.view(100, 512, 512, 3))
@@ -107,3 +128,16 @@ def test_full_size_gradient_of_sampled_pixels(full):
     dVg = dV.cpu().numpy().astype(np.float64)
     rel = np.linalg.norm(dVg - dVo) / np.linalg.norm(dVo)
     assert rel < GRAD_RTOL, rel
+
+
+def test_full_size_step_parity_every_depth(full):
+    """One-step parity over the whole 100-view tape: 500 seeded segments of
+    each depth 0..8, each traced one step by the oracle from the GPU's own
+    FP32 segment (hit id, events, children's origins, directions and
+    throughputs, escaped contributions)."""
+    sc, img, tape = full
+    si, sf = dt.dump_segments(tape)
+    rows = sample_segments_by_depth(si, 500, sc.max_depth, seed=9)
+    info = step_parity(si, sf, rows, sc.V, sc.F, sc.ior, sc.sigma, sc.env, sc.max_depth)
+    print("one-step parity:", info)
+    assert min(info["checked_per_depth"]) >= 400, info["checked_per_depth"]

@@ -16,7 +16,7 @@ import torch
 import oracle as O
 import paper_2603_00413_gb300 as dt
 from paper_2603_00413_gb300 import scenes as S
-from tests.gpu_util import GRAD_RTOL, PROBE, GpuScene, assert_radiance_parity, degenerate_pixels
+from tests.gpu_util import GRAD_RTOL, PROBE, GpuScene, assert_radiance_parity, excluded_pixels
 
 pytestmark = pytest.mark.gpu
 
@@ -67,17 +67,16 @@ def test_hash_texture_render_matches_oracle():
     img, tape = gs.render(medium=_gpu_texture(tex))
     assert tape.stats["status"] == dt.DT_OK
     assert tape.stats["medium_samples"] > 0
-    for v in range(2):
-        info = assert_radiance_parity(img[v], _oracle(gs, tex, v))
-        assert info["excluded_frac"] < 0.25, info
+    for v, excluded in enumerate([0.0508, 0.0727]):
+        assert_radiance_parity(img[v], _oracle(gs, tex, v), excluded)
     plain, _ = gs.render()
     assert (img <= plain * (1 + 1e-5) + 1e-7).all() and (img < plain * 0.999).any()
 
 
-def _seed(gs, orc, rng):
+def _seed(gs, orc, rng, expected_excluded):
     g = rng.normal(size=(gs.cams.shape[0], gs.height, gs.width, 3))
     g[1:] = 0.0
-    g[0][degenerate_pixels(orc)] = 0.0
+    g[0][excluded_pixels(orc, expected_excluded)] = 0.0
     return g
 
 
@@ -88,7 +87,7 @@ def test_hash_texture_gradients_match_oracle_derivative():
     tex = _texture(seed=8, levels=3, log2_table=9, n_min=5, n_max=14, scale=1.2)
     rng = np.random.default_rng(51)
     orc = _oracle(gs, tex)
-    g = _seed(gs, orc, rng)
+    g = _seed(gs, orc, rng, 0.048)
     img, tape = gs.render(medium=_gpu_texture(tex))
     dV, dior, dsig, dtab = dt.render_backward(tape, torch.from_numpy(g.astype(np.float32)).cuda())
     assert tuple(dtab.shape) == tex["table"].shape

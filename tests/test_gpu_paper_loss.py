@@ -10,7 +10,7 @@ import torch
 import oracle as O
 import paper_2603_00413_gb300 as dt
 from paper_2603_00413_gb300 import scenes as S
-from tests.gpu_util import GRAD_RTOL, PROBE, GpuScene, degenerate_pixels
+from tests.gpu_util import GRAD_RTOL, PROBE, GpuScene, excluded_pixels
 
 pytestmark = pytest.mark.gpu
 
@@ -49,7 +49,7 @@ def test_paper_loss_seeds_the_backward():
     # the true image: the render with another sigma, equal to ours on the
     # excluded pixels (so they seed nothing)
     tgt = O.render(gs.Vn, gs.Fn, gs.iorf, np.array([0.5, 0.2, 0.3]), gs.envn, gs.cam_list[0], p.max_depth)["img"]
-    bad = degenerate_pixels(orc)
+    bad = excluded_pixels(orc, 0.0083)
     tgt[bad] = img[0].cpu().numpy()[bad]
     tgt32 = tgt.astype(np.float32)[None]
     seed, _ = dt.paper_loss_grad(img, torch.from_numpy(tgt32).cuda(), 1.0, 0.5)

@@ -368,6 +368,73 @@ def test_jitter_offset_matches_the_chained_hash_worked_by_hand():
 # ---------------------------------------------------------------------------
 # the whole ray tree (Sec. 3.4 steps 1-5)
 # ---------------------------------------------------------------------------
+def test_segment_throughputs_and_contributions():
+    """The per-segment records of the tree (Sec. 3.4 steps 3-5): a camera
+    ray starts with throughput 1; the children of a hit split its throughput
+    W times the segment's absorption A by R + T = 1 (Eq. 8), so W_r + W_t =
+    W A, with A = 1 outside and exp(-sigma t) inside, t the segment's own
+    length; a TIR child takes all of it; an escaped segment contributes
+    W * E(d); and a pixel's radiance is the sum of its escaped segments'
+    contributions over its samples, divided by spp."""
+    sc = S.glass_icosphere_scene(width=20, height=20)
+    sigma = np.array([0.6, 0.25, 1.1])
+    spp = 2
+    r = O.render(sc.V, sc.F, 1.45, sigma, sc.env, sc.cams[0], 6, spp=spp, jitter=1, seed=3, segments=True)
+    si, sf = r["seg_i"], r["seg_f"]
+    rec = {(int(a), int(n)): j for j, (a, n, _, _) in enumerate(si)}
+    roots = [j for (a, n), j in rec.items() if n == 1]
+    np.testing.assert_array_equal(sf[roots, 9:12], 1.0)
+    n_split = n_tir = 0
+    for (a, n), j in rec.items():
+        kids = [rec.get((a, 2 * n)), rec.get((a, 2 * n + 1))]
+        if kids[0] is None:
+            continue
+        A = np.exp(-sigma * sf[j, 0]) if si[j, 3] & O.SEG_INSIDE else np.ones(3)
+        W = sf[kids[0], 9:12] + (sf[kids[1], 9:12] if kids[1] is not None else 0.0)
+        np.testing.assert_allclose(W, sf[j, 9:12] * A, rtol=1e-12)
+        n_split += kids[1] is not None
+        n_tir += kids[1] is None
+    assert n_split > 100 and n_tir > 10
+    miss = (si[:, 3] & O.SEG_MISS) != 0
+    E = O.env_lookup(sc.env, sf[miss, 6:9])
+    np.testing.assert_allclose(sf[miss, 12:15], sf[miss, 9:12] * E, rtol=1e-12)
+    np.testing.assert_array_equal(sf[~miss, 12:15], 0.0)
+    img = np.zeros((20 * 20, 3))
+    np.add.at(img, si[:, 0] // spp, sf[:, 12:15] / spp)
+    np.testing.assert_allclose(img, r["img"].reshape(-1, 3), rtol=1e-12, atol=1e-15)
+
+
+def test_one_step_tracing_reproduces_the_tree():
+    """trace_steps, fed every segment of a rendered tree (its origin,
+    direction, depth and the triangle it leaves), returns that segment's hit
+    and its children's directions and throughputs relative to its own: the
+    tree of render() step by step (absorbing glass, depth 5, two jittered
+    samples, TIR paths included)."""
+    sc = S.glass_icosphere_scene(width=20, height=20)
+    sigma = np.array([0.6, 0.25, 1.1])
+    r = O.render(sc.V, sc.F, 1.45, sigma, sc.env, sc.cams[0], 5, spp=2, jitter=1, seed=3, segments=True)
+    si, sf = r["seg_i"], r["seg_f"]
+    rec = {(int(a), int(n)): j for j, (a, n, _, _) in enumerate(si)}
+    src = np.array([si[rec[(a, n // 2)], 2] if n > 1 else -1 for a, n, _, _ in si])
+    k = np.floor(np.log2(si[:, 1])).astype(int)
+    ti, tf = O.trace_steps(sc.V, sc.F, 1.45, sigma, sc.env, sf[:, 3:6], sf[:, 6:9], src, k, 5)
+    np.testing.assert_array_equal(ti[:, 0, 2], si[:, 2])
+    np.testing.assert_array_equal(ti[:, 0, 3], si[:, 3])
+    np.testing.assert_allclose(tf[:, 0, 12:15], sf[:, 12:15] / sf[:, 9:12], rtol=1e-12)
+    n_kids = 0
+    for j, (a, n, _, _) in enumerate(si):
+        for c, node in ((1, 2 * n), (2, 2 * n + 1)):
+            if (a, node) in rec:
+                q = rec[(a, node)]
+                assert ti[j, c, 1] == node - 2 * n + 2
+                np.testing.assert_allclose(tf[j, c, 3:9], sf[q, 3:9], rtol=0, atol=1e-14)
+                np.testing.assert_allclose(tf[j, c, 9:12] * sf[j, 9:12], sf[q, 9:12], rtol=1e-12)
+                n_kids += 1
+            else:
+                assert ti[j, c, 1] == 0
+    assert n_kids > 500
+
+
 def test_ior_one_reproduces_environment_and_has_no_vertex_gradient():
     """IoR 1, no absorption: R = 0, T = 1, refraction is the identity, so
     every pixel shows E(d_camera) exactly and moving vertices changes nothing."""
