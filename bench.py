@@ -62,10 +62,15 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-scene batching comparison")
     ap.add_argument("--batch-scenes", type=int, default=64)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving comparison")
-    ap.add_argument("--serve-requests", type=int, default=200)
-    ap.add_argument("--large", action="store_true",
-                    help="add the large optimisation step (about 1.1M-triangle noisy sphere, 800x800, 8 jittered "
-                         "spp, depth 16, per-bounce checkpointing, LBVH rebuild every step)")
+    ap.add_argument("--serve-requests", type=int, default=2000, help="requests per arrival rate, at most")
+    ap.add_argument("--serve-seconds", type=float, default=15.0,
+                    help="arrival window per rate, at most (a low rate sends rate x seconds requests)")
+    ap.add_argument("--serve-rates", type=str, default="10,30,100,300,1000,2000")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the large optimisation step (about 1.1M-triangle noisy sphere, 800x800, 8 jittered "
+                         "spp, depth 16, per-bounce checkpointing, BVH rebuild every step)")
+    ap.add_argument("--no-c0", action="store_true", help="skip the forward-only icosphere leg")
+    ap.add_argument("--c0-frames", type=int, default=1000)
     ap.add_argument("--large-grid", type=int, default=240)
     ap.add_argument("--large-res", type=int, default=800)
     ap.add_argument("--large-steps", type=int, default=5)
@@ -282,39 +287,114 @@ def scope_kernels(scope: str, nf: int) -> int:
     return KERNELS_PER_SCOPE.get(scope, 1)
 
 
-def serve_leg(args, scs, dev):
+def serve_leg(args, dev):
     """Poisson streams of render and gradient requests (50/50) over 32
-    resident meshes; square images with side log-uniform in [64, 1024],
-    depth uniform in 4..16.  The continuous-batching server against the same
-    loop serving one request per launch, at two arrival rates."""
+    resident meshes (random blobs, faces log-uniform in [5k, 500k]); square
+    images with side log-uniform in [64, 1024], depth uniform in 4..16, a
+    random view each.  The continuous-batching server against the same loop
+    serving one request per launch, at each arrival rate: min(2000, rate x
+    15 s) requests, the same stream for both servers."""
     import torch
     from paper_2603_00413_gb300 import serve
     from paper_2603_00413_gb300 import scenes as S
-    res = [serve.ResidentScene.from_arrays(sc.V, sc.F, sc.ior, sc.sigma, sc.env, dev) for sc in scs[:32]]
+    t0 = time.time()
+    scs = S.serve_scenes(32, 4)
+    gen_s = time.time() - t0
+    res = [serve.ResidentScene.from_arrays(sc.V, sc.F, sc.ior, sc.sigma, sc.env, dev) for sc in scs]
     budget = int(0.5 * torch.cuda.mem_get_info(dev)[0])
+    rates = [float(x) for x in args.serve_rates.split(",")]
     out = {"workload": f"{len(res)} resident meshes ({min(r.F.shape[0] for r in res)}-"
-                       f"{max(r.F.shape[0] for r in res)} faces), {args.serve_requests} Poisson requests per rate, "
-                       f"50% render / 50% gradient, side 64-1024, depth 4-16", "rates": {}}
+                       f"{max(r.F.shape[0] for r in res)} faces), Poisson arrivals, min({args.serve_requests}, "
+                       f"rate x {args.serve_seconds:g} s) requests per rate, 50% render / 50% gradient, side "
+                       f"64-1024, depth 4-16", "mesh_gen_s": round(gen_s, 1), "rates": {}}
 
     def view(rng, side):
         return S.random_view(rng, 3.0, side, side).as_array()
 
-    for rate in (100.0, 1000.0):
-        row = {}
+    targets = {}
+
+    def target(r):  # one fixed random target image per size
+        if r.width not in targets:
+            targets[r.width] = np.random.default_rng(r.width).uniform(0, 2, size=(r.height, r.width, 3)).astype(
+                np.float32)
+        return targets[r.width]
+
+    for rate in rates:
+        n = int(min(args.serve_requests, max(20, round(rate * args.serve_seconds))))
+        row = {"requests": n}
         for name, mb, ns in (("batched", 32, 2), ("one_per_launch", 1, 1)):
             rng = np.random.default_rng(int(rate))
-            trg = np.random.default_rng(int(rate) + 7)
-            reqs = serve.poisson_requests(rng, args.serve_requests, rate, len(res), sides=(64, 1024), depths=(4, 16),
-                                          grad_frac=0.5, view_fn=view,
-                                          target_fn=lambda r: trg.uniform(0, 2, size=(r.height, r.width, 3)).astype(
-                                              np.float32))
+            reqs = serve.poisson_requests(rng, n, rate, len(res), sides=(64, 1024), depths=(4, 16),
+                                          grad_frac=0.5, view_fn=view, target_fn=target)
             srv = serve.Server(res, budget, max_batch=mb, streams=ns)
             done = srv.run(reqs, timeout=600)
             wall = max(r.finish for r in done)
-            row[name] = serve.latency_summary(done, wall)
+            summ = serve.latency_summary(done, wall)
+            row[name] = {k: (round(v, 2) if isinstance(v, float) else v) for k, v in summ.items()}
             row[name]["launches"] = srv.launches
         out["rates"][str(int(rate))] = row
     return out
+
+
+def c0_leg(args, dt, dev):
+    """The plain forward-only icosphere: subdivision 3 (1280 triangles),
+    IoR 1.5, no absorption, camera at distance 3, 64x64 at pixel centres,
+    depth 4, 64x32 SH environment.  A frame is one forward render (camera
+    rays and five trace/shade levels), launch-latency bound at ~23k
+    segments; 1000 frames are timed back to back as eager launches and as
+    replays of a captured CUDA graph of one frame."""
+    import torch
+    from paper_2603_00413_gb300 import scenes as S
+    sc = S.glass_icosphere_scene()
+    cam = sc.cams[0]
+    V = torch.from_numpy(sc.V).to(dev)
+    F = torch.from_numpy(sc.F).to(dev)
+    ior = torch.tensor([sc.ior], device=dev)
+    sigma = torch.from_numpy(np.asarray(sc.sigma, np.float32)).to(dev)
+    env = torch.from_numpy(sc.env).to(dev)
+    cams = torch.from_numpy(cam.as_array()[None]).to(dev)
+    params = dt.Params(sc.max_depth)
+    bvh = dt.build_bvh(V, F)
+    N = dt.vertex_normals(V, F)
+    img, tape = dt.render(V, F, bvh, N, ior, sigma, env, cams, cam.width, cam.height, params)
+    stats = tape.stats
+    seg = stats["segments"]
+    stream = torch.cuda.current_stream()
+
+    def frame():
+        dt.render(V, F, bvh, N, ior, sigma, env, cams, cam.width, cam.height, params, ws=tape.ws, out=img,
+                  check=False)
+
+    def timed(fn, k):
+        for _ in range(10):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    k = args.c0_frames
+    ms_eager = timed(frame, k)
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        frame()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(graph, stream=side):
+            frame()
+    ms_graph = timed(graph.replay, k)
+    chk = dt.read_stats(tape.ws)
+    assert chk["status"] == dt.DT_OK and chk["segments"] == seg, chk
+    return {"workload": f"glass icosphere ({sc.F.shape[0]} triangles), 64x64, 1 spp at pixel centres, depth "
+                        f"{sc.max_depth}, IoR {sc.ior}, forward only, {k} frames back to back",
+            "segments_per_frame": int(seg), "eager_ms_per_frame": round(ms_eager, 4),
+            "eager_segments_per_s": seg / (ms_eager / 1e3), "graph_ms_per_frame": round(ms_graph, 4),
+            "graph_segments_per_s": seg / (ms_graph / 1e3)}
 
 
 def large_leg(args, dt, dev):
@@ -391,14 +471,15 @@ def large_leg(args, dt, dev):
         assert chk["status"] == dt.DT_OK and chk["segments"] == stats["segments"], chk
         seg = stats["segments"]
         tot = sum(v[1] for v in prof.values())
-        out[mode] = {"ms_per_step": ms, "segments_per_step": int(seg), "segments_per_s": seg / (ms / 1e3),
+        top = sorted(prof.items(), key=lambda kv: -kv[1][1])[:5]
+        out[mode] = {"ms_per_step": round(ms, 3), "segments_per_step": int(seg), "segments_per_s": seg / (ms / 1e3),
                      "tape_bytes": int(ws.bytes), "level_capacity": int(ws.level_capacity),
-                     "rebuild_ms": (prof.get("lbvh_build", (1, 0.0))[1] + prof.get("sah_build", (1, 0.0))[1])
-                     / args.large_steps,
-                     "kernel_share": {k: round(v[1] / tot, 4) for k, v in prof.items()},
+                     "rebuild_ms": round((prof.get("lbvh_build", (1, 0.0))[1] + prof.get("sah_build", (1, 0.0))[1])
+                                         / args.large_steps, 3),
+                     "top_kernel_share": {k: round(v[1] / tot, 4) for k, v in top},
                      "gpu_launches_per_step": int(sum(v[0] * scope_kernels(k, Fn.shape[0]) for k, v in prof.items())
                                                   / args.large_steps),
-                     "levels": stats["level_count"], "loss": float(loss.item())}
+                     "loss": float(loss.item())}
         del ws, bws, tape, img, target, grad
         torch.cuda.empty_cache()
     # the step after the gradient (App. A): L_edge's gradient added to a
@@ -504,11 +585,12 @@ def medium_leg(args, dt, dev):
         chk = dt.read_stats(tape.ws)
         assert chk["status"] == dt.DT_OK and chk["segments"] == stats["segments"], chk
         tot = sum(v[1] for v in prof.values())
-        out[mode] = {"ms_per_step": ms, "segments_per_step": int(stats["segments"]),
+        top = sorted(prof.items(), key=lambda kv: -kv[1][1])[:4]
+        out[mode] = {"ms_per_step": round(ms, 3), "segments_per_step": int(stats["segments"]),
                      "segments_per_s": stats["segments"] / (ms / 1e3),
                      "grid_samples_per_step": int(stats["medium_samples"]),
-                     "kernel_ms": {k: round(v[1] / args.medium_steps, 3) for k, v in prof.items()},
-                     "kernel_share": {k: round(v[1] / tot, 4) for k, v in prof.items()}}
+                     "top_kernels_ms": {k: round(v[1] / args.medium_steps, 3) for k, v in top}}
+        del tot
         del tape, bws, img, grad
         torch.cuda.empty_cache()
     return out
@@ -593,12 +675,7 @@ def batch_leg(args, dt, dev, steps):
     chk = dt.read_stats(tape.ws)
     assert chk["status"] == dt.DT_OK and chk["segments"] == seg, chk
     depth_max = max(it.params.max_depth for it in items)
-    serve_out = None
-    if not args.no_serve:
-        del graph, tape, bws, plain_ws
-        torch.cuda.empty_cache()
-        serve_out = serve_leg(args, scs, dev)
-    return serve_out, {
+    return {
         "workload": f"{len(items)} random-blob scenes, {sum(it.F.shape[0] for it in items)} faces in all "
                     f"({min(it.F.shape[0] for it in items)}-{max(it.F.shape[0] for it in items)}), "
                     f"{sum(it.width * it.height for it in items)} pixels ({min(it.width for it in items)}^2-"
@@ -863,8 +940,14 @@ def run_ours(args):
                "sample": f"{args.cpu_sample} seeded pixels of the same workload ({nseg} segments), forward + "
                          f"gradient by forward mode over the parameters those paths touch, {secs:.1f} s"}
 
+    c0 = None
+    if rank == 0 and world == 1 and not args.no_c0:
+        with ClockSampler(dev.index or 0) as clk_c0:
+            c0 = c0_leg(args, dt, dev)
+        c0["clocks"] = clk_c0.summary()
+
     large = None
-    if rank == 0 and world == 1 and args.large:
+    if rank == 0 and world == 1 and not args.no_large:
         with ClockSampler(dev.index or 0) as clk_large:
             large = large_leg(args, dt, dev)
         large["clocks"] = clk_large.summary()
@@ -876,10 +959,18 @@ def run_ours(args):
         medium["clocks"] = clk_med.summary()
 
     batch = serving = None
-    if rank == 0 and world == 1 and not args.no_batch:
+    if rank == 0 and world == 1:
         del ws, bws, tape
         torch.cuda.empty_cache()
-        serving, batch = batch_leg(args, dt, dev, max(3, args.steps // 4))
+        if not args.no_batch:
+            with ClockSampler(dev.index or 0) as clk_b:
+                batch = batch_leg(args, dt, dev, max(3, args.steps // 4))
+            batch["clocks"] = clk_b.summary()
+            torch.cuda.empty_cache()
+        if not args.no_serve:
+            with ClockSampler(dev.index or 0) as clk_s:
+                serving = serve_leg(args, dev)
+            serving["clocks"] = clk_s.summary()
 
     if rank == 0:
         out = {
@@ -899,14 +990,16 @@ def run_ours(args):
             "clocks": clk.summary(),
             "e2e": e2e,
             "cpu_baseline": cpu,
-            "batch": batch,
-            "serve": serving,
-            "large": large,
-            "medium": medium,
+            "nodes_per_segment": round(stats["nodes_visited"] / seg, 3),
+            "tris_per_segment": round(stats["tris_tested"] / seg, 3),
             "paper_loss": paper_loss,
-            "levels": stats["level_count"],
-            "nodes_per_segment": stats["nodes_visited"] / seg,
-            "tris_per_segment": stats["tris_tested"] / seg,
+            "medium": medium,
+            # the other workloads last, so that the end of the line (which
+            # log tails keep) holds them
+            "large": large,
+            "batch": batch,
+            "c0": c0,
+            "serve": serving,
         }
         print(json.dumps(out))
     if world > 1:

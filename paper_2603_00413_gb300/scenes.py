@@ -465,6 +465,40 @@ def batch_scenes(n: int = 64, seed: int = 2, workers: int = None) -> list:
         return pool.map(build_batch_scene, specs, chunksize=1)
 
 
+def serve_specs(n: int = 32, seed: int = 4) -> list:
+    """The serving workload's resident meshes: n random blobs as in
+    batch_specs, with faces log-uniform in [5k, 500k]; IoR ~ U[1.3, 1.7],
+    absorption ~ U[0, 2], a 256x128 SH environment each (the requests pick
+    their own view, size and depth)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        out.append(BatchSpec(
+            index=i, prims=blob_prims(rng),
+            faces=int(round(math.exp(rng.uniform(math.log(5000), math.log(500000))))),
+            side=256, depth=8, ior=float(F32(rng.uniform(1.3, 1.7))),
+            sigma=rng.uniform(0.0, 2.0, size=3).astype(F32), env_seed=int(rng.integers(0, 2 ** 31)),
+            cam_seed=int(rng.integers(0, 2 ** 31))))
+    return out
+
+
+def serve_scenes(n: int = 32, seed: int = 4, workers: int = None) -> list:
+    """The serving workload's meshes (serve_specs), built in spawned processes."""
+    specs = serve_specs(n, seed)
+    workers = workers or min(len(specs), os.cpu_count() or 1)
+    if workers <= 1:
+        return [build_batch_scene(s) for s in specs]
+    import multiprocessing as mp
+    # the largest meshes first, so they do not finish last on one worker
+    order = sorted(range(len(specs)), key=lambda i: -specs[i].faces)
+    with mp.get_context("spawn").Pool(workers) as pool:
+        built = pool.map(build_batch_scene, [specs[i] for i in order], chunksize=1)
+    out = [None] * len(specs)
+    for i, sc in zip(order, built):
+        out[i] = sc
+    return out
+
+
 def mesh_from_field(field, target_faces: int, lo: float = -1.2, hi: float = 1.2,
                     max_grid: int = 640):
     """Extract a field's iso-surface at the grid resolution that gives about

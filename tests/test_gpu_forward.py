@@ -13,7 +13,8 @@ import torch
 import oracle as O
 import paper_2603_00413_gb300 as dt
 from paper_2603_00413_gb300 import scenes as S
-from tests.gpu_util import GpuScene, assert_hit_id_parity, assert_radiance_parity, degenerate_pixels, step_parity
+from tests.gpu_util import (GpuScene, assert_hit_id_parity, assert_radiance_parity, assert_tree_weights,
+                            degenerate_pixels, step_parity)
 
 pytestmark = pytest.mark.gpu
 
@@ -172,7 +173,7 @@ def test_refit_tracks_moved_vertices(builder):
     np.testing.assert_array_equal(tri.cpu().numpy()[ok], otri[ok])
 
 
-def _parity(gs, expected_excluded, view=0):
+def _parity(gs, expected_excluded, view=0, expected_unstable=None):
     img, tape = gs.render()
     torch.cuda.synchronize()
     orc = gs.oracle(view, segments=True)
@@ -183,7 +184,9 @@ def _parity(gs, expected_excluded, view=0):
     spp = gs.params.spp
     lo, hi = view * npix * spp, (view + 1) * npix * spp
     sel = (si[:, 0] >= lo) & (si[:, 0] < hi)
-    n = assert_hit_id_parity(si[sel], orc, spp, view_offset=lo, seg_gpu_f=sf[sel])
+    n = assert_hit_id_parity(si[sel], orc, spp, view_offset=lo)
+    if expected_unstable is not None:
+        assert_tree_weights(gs, view, si[sel], sf[sel], expected_unstable)
     # and every segment of the tape, one step at a time from its own FP32 inputs
     sit, sft = dt.dump_segments(tape)
     step_parity(sit, sft, torch.arange(sit.shape[0], device=sit.device), gs.Vn, gs.Fn, gs.iorf, gs.sigman, gs.envn,
@@ -195,7 +198,8 @@ def test_render_glass_icosphere_matches_oracle():
     """The one-icosphere workload in full: subdivision 3, IoR 1.5, no
     absorption, 64x64 at pixel centres, depth 4, 64x32 SH environment."""
     gs = GpuScene.from_scene(S.glass_icosphere_scene())
-    img, tape, orc, info, n = _parity(gs, 0.0168)  # measured: 69 of 4096 pixels excluded
+    # measured: 69 of 4096 pixels excluded, 2.9 % of the segments weight-unstable
+    img, tape, orc, info, n = _parity(gs, 0.0168, expected_unstable=0.0293)
     st = tape.stats
     oc = orc["counters"]
     bad = degenerate_pixels(orc)
@@ -205,12 +209,12 @@ def test_render_glass_icosphere_matches_oracle():
         assert st["discarded"] == oc["discarded"] and st["tir"] == oc["tir"]
 
 
-@pytest.mark.parametrize("depth,excluded", [(0, 0.0), (1, 0.0073), (6, 0.0089)])
-def test_render_absorbing_off_axis(depth, excluded):
+@pytest.mark.parametrize("depth,excluded,unstable", [(0, 0.0, 0.0), (1, 0.0073, 0.0103), (6, 0.0089, 0.0222)])
+def test_render_absorbing_off_axis(depth, excluded, unstable):
     sc = S.glass_icosphere_scene(width=48, height=40)
     cam = S.camera((1.3, 0.9, 2.5), (0.05, -0.1, 0.0), (0, 1, 0), 50.0, 48, 40)
     gs = GpuScene(sc.V, sc.F, 1.45, np.array([0.5, 1.0, 1.5], np.float32), sc.env, [cam], 48, 40, depth)
-    _parity(gs, excluded)
+    _parity(gs, excluded, expected_unstable=unstable)
 
 
 def test_sah_and_lbvh_trees_find_the_same_hits():
@@ -239,6 +243,12 @@ def test_sah_and_lbvh_trees_find_the_same_hits():
     assert sb["nodes_visited"] < 0.9 * sa["nodes_visited"], (sa["nodes_visited"], sb["nodes_visited"])
 
 
+# fraction of the segments of each view of the jittered genus-2 test whose
+# throughput or contribution is not stable under the oracle's tilt (measured
+# with the oracle alone): internal reflections amplify the tilt along the path
+UNSTABLE_G2 = [0.3311, 0.2836, 0.2326]
+
+
 def test_render_genus2_multi_view_jittered():
     V, F = S.two_tori_mesh(36)
     env = S.sh_env_map(64, 32, 1)
@@ -253,7 +263,8 @@ def test_render_genus2_multi_view_jittered():
         si, sf = si.cpu().numpy(), sf.cpu().numpy()
         npix = 40 * 40 * 2
         sel = (si[:, 0] >= v * npix) & (si[:, 0] < (v + 1) * npix)
-        assert_hit_id_parity(si[sel], orc, 2, view_offset=v * npix, seg_gpu_f=sf[sel])
+        assert_hit_id_parity(si[sel], orc, 2, view_offset=v * npix)
+        assert_tree_weights(gs, v, si[sel], sf[sel], UNSTABLE_G2[v])
     sit, sft = dt.dump_segments(tape)
     info = step_parity(sit, sft, torch.arange(sit.shape[0], device=sit.device), gs.Vn, gs.Fn, gs.iorf, gs.sigman,
                        gs.envn, 8)
@@ -276,7 +287,7 @@ def test_single_pixel_and_single_triangle():
     env = S.sh_env_map(16, 8, 3)
     cam = S.camera((0.1, 0.1, 2.0), (0.1, 0.1, 0.0), (0, 1, 0), 30.0, 1, 1)
     gs = GpuScene(V, F, 1.5, np.zeros(3, np.float32), env, [cam], 1, 1, 3)
-    _parity(gs, 0.0)
+    _parity(gs, 0.0, expected_unstable=0.0)
 
 
 def test_arena_overflow_is_reported_and_retried():

@@ -7,13 +7,15 @@ binned-SAH BVH.
 On this noisy surface a path is chaotic after a few bounces: tilting its
 camera ray by 1e-6 rad changes a later event or moves a later throughput by
 more than 1e-4, so FP32 and FP64 trees part there (measured with the oracle
-on 400 seeded pixels: 61 of 273 depth-3 segments keep their throughput
-under the tilt, 1 of 274 at depth 5, none deeper).  The checks are
+on 400 seeded pixels: 99 of 273 depth-3 segments keep their events under
+the tilt and 34 their throughput and contribution, 4 of 274 at depth 5 their
+events, none deeper).  The checks are
 therefore: (1) the checkpointed 8-sample render's statistics, and its image
 mean against a 1-sample render of the same configuration; (2) on the
 1-sample, depth-16 render, every segment at every depth whose path up to it
-is stable -- no degenerate event, the same events and throughputs within
-1e-4 when the camera ray is tilted by 1e-6 rad four ways -- against the
+is stable -- no degenerate event, the same events (and, for the weights,
+throughputs and contributions within 1e-4) when the camera ray is tilted
+by 1e-6 rad four ways -- against the
 oracle's tree: the same segments, hit triangles, events, throughput W and
 escaped contribution W * E(d); (3) one-step parity at every depth 0..16:
 for seeded segments of each depth the oracle traces one step from the GPU's
@@ -112,12 +114,12 @@ def test_large_stable_prefix_segments_every_depth(large, deep):
     g_i, g_f = si[sel].cpu().numpy(), sf[sel].cpu().numpy()
     o, d = large["o"][pix], large["d"][pix]
     osi, osf = _segments(large, o, d, pix)
-    base = {(int(a), int(n)): (int(t), int(f) & EVENTS, osf[j, 9:12]) for j, (a, n, t, f) in enumerate(osi)}
+    base = {(int(a), int(n)): (int(t), int(f) & EVENTS, osf[j, 9:15]) for j, (a, n, t, f) in enumerate(osi)}
     flags = {(int(a), int(n)): int(f) for a, n, _, f in osi}
     tilts = []
     for dt_ in _tilted(d, PROBE):
         ti, tf = _segments(large, o, dt_, pix)
-        tilts.append({(int(a), int(n)): (int(t), int(f) & EVENTS, tf[j, 9:12]) for j, (a, n, t, f) in enumerate(ti)})
+        tilts.append({(int(a), int(n)): (int(t), int(f) & EVENTS, tf[j, 9:15]) for j, (a, n, t, f) in enumerate(ti)})
 
     def step_stable(k, weights):
         if flags[k] & DEGEN:
@@ -166,14 +168,16 @@ def test_large_stable_prefix_segments_every_depth(large, deep):
     print("segments checked per depth (events / throughput / all):",
           [f"{a}/{b}/{c}" for a, b, c in zip(ev_n, w_n, all_n)])
     # measured with the oracle alone: events 399/342/226/99/31/4 at depths
-    # 0-5, throughputs 399/305/178/61/15/1, none deeper
-    assert ev_n[0] >= 390 and ev_n[3] >= 80 and w_n[3] >= 45, (ev_n.tolist(), w_n.tolist())
+    # 0-5, throughputs and contributions 399/250/128/34/7, none deeper
+    assert ev_n[0] >= 390 and ev_n[3] >= 80 and w_n[2] >= 100 and w_n[3] >= 25, (ev_n.tolist(), w_n.tolist())
 
 
 def test_large_step_parity_every_depth(large, deep):
     si, sf = deep
     rows = sample_segments_by_depth(si, 300, DEPTH, seed=24)
-    info = step_parity(si, sf, rows, large["V"], large["F"], IOR, SIGMA, large["env"], DEPTH)
+    # the noisy surface's sharp folds make more steps ill-conditioned (7.2 %
+    # measured) than the smooth meshes' 1-3 %
+    info = step_parity(si, sf, rows, large["V"], large["F"], IOR, SIGMA, large["env"], DEPTH, max_unconditioned=0.092)
     print("one-step parity:", info)
     per = info["checked_per_depth"]
     # every level of the depth-16 tree holds far more than 300 segments
