@@ -96,6 +96,34 @@ struct SceneSums {
 // 2 = some scene's is a hash texture.
 constexpr int kAdjointMinBlocks = 4;  // CTAs of 256 per SM the register budget is sized for
 
+// The attenuation A of an interior segment with an absorption grid, without
+// marching its optical depth again: the forward gave each child the
+// throughput W A F (F = R for the reflected child, T for the refracted one,
+// rounded after each product), so A = W_child / (W F) to a few ulps.  The
+// child with the larger factor is used (F >= 1/2; under TIR the reflected one
+// with F = 1).  Where W F is not a normal float (a throughput driven to the
+// subnormal range) the depth is marched as in the forward.
+template <bool kHash>
+__device__ __noinline__ float3 marched_absorption(const MediumView g, float3 o, float3 d, float t, float3 sigma) {
+  return absorption_with_depth(sigma, t, medium_depth<kHash>(g, o, d, t));
+}
+
+template <bool kHash>
+__device__ __forceinline__ float3 recovered_absorption(const WsView& W, const SceneEntry& E, const SceneEntry* Eg,
+                                                       float4 rw, int32_t ch, uint32_t fl, bool tir,
+                                                       const HitShade& h, float3 o, float3 d, float t,
+                                                       float3 sigma) {
+  const bool refl = tir || h.R >= 0.5f;
+  const unsigned long long c = refl ? (unsigned long long)ch : (unsigned long long)ch + (fl >> kRefractShift);
+  const float F = tir ? 1.0f : (refl ? h.R : h.T);
+  const float3 den = mk(rw.x * F, rw.y * F, rw.z * F);
+  if (c < W.cap && fminf(fminf(den.x, den.y), den.z) >= 1.17549435e-38f) {
+    const float4 wc = W.ray_w[c];
+    return mk(wc.x / den.x, wc.y / den.y, wc.z / den.z);
+  }
+  return marched_absorption<kHash>(medium_view(E, Eg), o, d, t, sigma);
+}
+
 template <bool kBatch, int kGrid>
 __global__ void __launch_bounds__(256, kAdjointMinBlocks) k_adjoint(WsView W, int k, const AdjRecords out_next,
                                                                    const AdjRecords out_cur, const SceneEntry E0,
@@ -159,7 +187,7 @@ __global__ void __launch_bounds__(256, kAdjointMinBlocks) k_adjoint(WsView W, in
         HitShade h;
         shade_hit(o, d, t, b1, b2, v0, v1, v2, N0, N1, N2, ior, sigma, h, tir ? 1 : 0);
         const bool med = kGrid && E.mu && !h.entering;
-        if (med) h.A = absorption_with_depth(sigma, t, medium_depth<kGrid == 2>(medium_view(E, W.ent + sc), o, d, t));
+        if (med) h.A = recovered_absorption<kGrid == 2>(W, E, W.ent + sc, rw, ch, fl, tir, h, o, d, t, sigma);
         // children: reflected at ch, refracted at ch + (flags >> kRefractShift)
         float3 Lr = mk(0.f, 0.f, 0.f), orb = Lr, drb = Lr, Lt = Lr, otb = Lr, dtb = Lr;
         const uint32_t jr = (uint32_t)ch - next_start;
