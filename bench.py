@@ -990,6 +990,7 @@ def run_ours(args):
             "clocks": clk.summary(),
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "levels": stats["level_count"],
             "nodes_per_segment": round(stats["nodes_visited"] / seg, 3),
             "tris_per_segment": round(stats["tris_tested"] / seg, 3),
             "paper_loss": paper_loss,
