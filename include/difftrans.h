@@ -457,10 +457,14 @@ dt_status dt_edge_loss_grad(const void* d_topo, int32_t nv, int32_t nf, const fl
  * hit and flag words), so that a warp's rays take similar paths through the
  * BVH.  0 traces the segments in the order they were appended.  Camera
  * rays are laid out in 8x4 pixel blocks.
- * Defaults {192, 8, 5, 4, 2, 1, 20}; results do not depend on them (the same
- * closest hit is found).  dt_set_tuning rejects values outside steps
- * 1..256, refill 1..32, trace 1..8, shade 1..16, width 2 or 4, builder 0
- * or 1, order 0 or 12..22.
+ * order_min_rays: a render (or batch) with fewer camera rays than this
+ * traces every level in append order: its levels are a few thousand
+ * segments, where the order's three launches per level cost more than the
+ * coherence gains.
+ * Defaults {192, 8, 5, 4, 2, 1, 20, 65536}; results do not depend on them
+ * (the same closest hit is found).  dt_set_tuning rejects values outside
+ * steps 1..256, refill 1..32, trace 1..8, shade 1..16, width 2 or 4,
+ * builder 0 or 1, order 0 or 12..22, order_min_rays >= 0.
  * ------------------------------------------------------------------------ */
 typedef struct dt_tuning {
   int32_t trace_steps;
@@ -470,6 +474,7 @@ typedef struct dt_tuning {
   int32_t bvh_width;
   int32_t bvh_builder;
   int32_t trace_order;
+  int32_t order_min_rays;
 } dt_tuning;
 dt_status dt_get_tuning(dt_tuning* out);
 dt_status dt_set_tuning(const dt_tuning* in);

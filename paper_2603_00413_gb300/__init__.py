@@ -100,7 +100,7 @@ class DtBatchEntry(ctypes.Structure):
 class DtTuning(ctypes.Structure):
     _fields_ = [("trace_steps", c_int32), ("trace_refill", c_int32), ("trace_blocks_per_sm", c_int32),
                 ("shade_blocks_per_sm", c_int32), ("bvh_width", c_int32), ("bvh_builder", c_int32),
-                ("trace_order", c_int32)]
+                ("trace_order", c_int32), ("order_min_rays", c_int32)]
 
 
 class DtKernelTime(ctypes.Structure):
@@ -729,7 +729,7 @@ def get_tuning() -> dict:
 def set_tuning(**kw) -> dict:
     """Set launch/scheduling knobs (trace_steps, trace_refill,
     trace_blocks_per_sm, shade_blocks_per_sm, bvh_width, bvh_builder,
-    trace_order); returns the previous values."""
+    trace_order, order_min_rays); returns the previous values."""
     old = get_tuning()
     new = dict(old)
     new.update(kw)

@@ -62,7 +62,7 @@ void launch_edge_loss_grad(const void* topo, int32_t nv, int32_t nf, const float
 // per scheduling round 192, refill at 8 idle lanes, 5 traversal and 4
 // shading CTAs per SM, binary nodes, binned SAH builder, levels after the
 // camera rays traced in the order of 20-bit buckets.
-dt_tuning g_tuning = {192, 8, 5, 4, 2, 1, 20};
+dt_tuning g_tuning = {192, 8, 5, 4, 2, 1, 20, 65536};
 
 static thread_local char g_err[512] = "";
 
@@ -470,9 +470,11 @@ dt_status dt_set_tuning(const dt_tuning* in) {
   if (in->trace_steps < 1 || in->trace_steps > 256 || in->trace_refill < 1 || in->trace_refill > 32 ||
       in->trace_blocks_per_sm < 1 || in->trace_blocks_per_sm > 8 || in->shade_blocks_per_sm < 1 ||
       in->shade_blocks_per_sm > 16 || (in->bvh_width != 2 && in->bvh_width != 4) ||
-      (in->bvh_builder != 0 && in->bvh_builder != 1) || (in->trace_order != 0 && (in->trace_order < 12 || in->trace_order > kOrderBits)))
+      (in->bvh_builder != 0 && in->bvh_builder != 1) ||
+      (in->trace_order != 0 && (in->trace_order < 12 || in->trace_order > kOrderBits)) || in->order_min_rays < 0)
     return set_error(DT_ERR_INVALID_ARG, "tuning out of range (steps 1..256, refill 1..32, trace blocks/SM 1..8, "
-                                         "shade blocks/SM 1..16, width 2 or 4, builder 0 or 1, order 0 or 12..22)");
+                                         "shade blocks/SM 1..16, width 2 or 4, builder 0 or 1, order 0 or 12..22, "
+                                         "order_min_rays >= 0)");
   g_tuning = *in;
   return DT_OK;
 }

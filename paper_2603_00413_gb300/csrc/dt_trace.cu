@@ -765,7 +765,8 @@ void launch_forward_table(const TableHeader& th, const SceneEntry* entries, void
   const int bps = g_tuning.trace_blocks_per_sm, st = g_tuning.trace_steps, rf = g_tuning.trace_refill;
   // levels after the camera rays are traced bucket by bucket (dt_order.cu);
   // the camera rays keep pixel order, which is coherent
-  const int order_bits = g_tuning.trace_order;
+  // (small renders are launch-bound: their levels keep append order)
+  const int order_bits = th.n_samples >= (uint32_t)g_tuning.order_min_rays ? g_tuning.trace_order : 0;
   for (int k = 0; k <= th.max_depth; ++k) {
     const int sorted = order_bits && k > 0;
     if (sorted) launch_order(W, k, order_bits, s);

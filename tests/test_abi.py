@@ -82,8 +82,11 @@ def test_tuning_round_trips_and_is_validated(lib):
     try:
         dt.set_tuning(trace_order=0)
         assert dt.get_tuning()["trace_order"] == 0
+        dt.set_tuning(order_min_rays=0)
+        assert dt.get_tuning()["order_min_rays"] == 0
+        dt.set_tuning(order_min_rays=old["order_min_rays"])
         for bad in (dict(trace_order=1), dict(trace_order=23), dict(bvh_width=3), dict(trace_steps=0),
-                    dict(bvh_builder=-1)):
+                    dict(bvh_builder=-1), dict(order_min_rays=-1)):
             with pytest.raises(dt.DiffTransError):
                 dt.set_tuning(**bad)
         assert dt.get_tuning() == dict(old, trace_order=0)

@@ -25,6 +25,7 @@ def _built():
     from paper_2603_00413_gb300 import build
     build.build()
     old = dt.get_tuning()
+    dt.set_tuning(order_min_rays=0)  # these small renders are ordered too
     yield
     dt.set_tuning(**old)
 
@@ -147,3 +148,20 @@ def test_order_with_tiny_levels():
     assert _sorts(prof, 6) and tape1.stats["status"] == dt.DT_OK
     np.testing.assert_array_equal(_sorted_dump(tape0)[0], _sorted_dump(tape1)[0])
     assert_radiance_parity(img1[0], gs.oracle(0), 0.3333)  # 2 of its 6 pixels
+
+
+def test_small_renders_keep_append_order():
+    """Below order_min_rays camera rays a render traces in append order (no
+    order launches) and finds the same hits as with the order."""
+    old = dt.get_tuning()
+    try:
+        gs = GpuScene.from_scene(S.glass_icosphere_scene(width=32, height=32))
+        dt.set_tuning(order_min_rays=32 * 32 + 1)
+        img0, tape0, _, prof0 = _run(gs, ORDER)
+        dt.set_tuning(order_min_rays=0)
+        img1, tape1, _, prof1 = _run(gs, ORDER)
+        assert "k_order" not in prof0 and _sorts(prof1, gs.params.max_depth)
+        np.testing.assert_array_equal(_sorted_dump(tape0)[0], _sorted_dump(tape1)[0])
+        np.testing.assert_allclose(img1.cpu().numpy(), img0.cpu().numpy(), rtol=1e-6, atol=1e-7)
+    finally:
+        dt.set_tuning(**old)
