@@ -16,7 +16,11 @@ that never blocks on the GPU:
 * retries a batch whose arena overflowed with a larger one, and learns the
   segments per pixel of each mesh and depth to size later arenas;
 * copies results back to pinned host memory and records arrival, start and
-  finish times for latency percentiles.
+  finish times for latency percentiles;
+* keeps one segment arena and one backward scratch per stream, grown when a
+  batch needs more and reused by the next batch on that stream, so that a
+  steady stream of requests allocates no device memory (an allocation that
+  misses the caching allocator can stall every stream).
 
 One request per launch is the same loop with max_batch=1 and one stream.
 """
@@ -105,6 +109,8 @@ class Server:
         self.done = []
         self.mem_used = 0
         self.seg_per_pixel = {}  # (scene, depth) -> largest observed segments per pixel
+        self.arenas = {}  # stream -> Workspace reused by the stream's next batch
+        self.scratch = {}  # stream -> (owner, aligned view) of the backward scratch
         self.t0 = None
         self.launches = 0
 
@@ -121,6 +127,24 @@ class Server:
             nv = self.scenes[r.scene].V.shape[0]
             mem += r.pixels * 12 * 2 + nv * 24 + 2 * 48 * max(r.pixels, seg // 4)
         return mem
+
+    def _arena(self, stream, seg: int):
+        """The stream's segment arena, grown (by at least a quarter) when it
+        holds fewer than seg segments."""
+        ws = self.arenas.get(stream)
+        if ws is None or ws.capacity < seg:
+            cap = seg if ws is None else max(seg, ws.capacity + ws.capacity // 4)
+            ws = Workspace(min(cap, 2 ** 31 - 1), self.device)
+            self.arenas[stream] = ws
+        return ws
+
+    def _scratch(self, stream, nbytes: int):
+        cur = self.scratch.get(stream)
+        if cur is None or cur[1].numel() < nbytes:
+            n = nbytes if cur is None else max(nbytes, cur[1].numel() + cur[1].numel() // 4)
+            cur = _aligned_empty(n, self.device)
+            self.scratch[stream] = cur
+        return cur[1]
 
     # ---- scheduling ---------------------------------------------------------------
     def now(self):
@@ -166,7 +190,7 @@ class Server:
                 b.items.append(BatchItem(sc.V, sc.F, sc.bvh, sc.N, sc.ior, sc.sigma, sc.env, cams, r.width, r.height,
                                          Params(r.depth)))
             b.outs = [torch.empty(1, r.height, r.width, 3, device=dev) for r in reqs]
-            b.ws = Workspace(sum(self._seg_estimate(r) for r in reqs), dev)
+            b.ws = self._arena(stream, sum(self._seg_estimate(r) for r in reqs))
             self._forward(b)
         self.inflight.append(b)
 
@@ -181,7 +205,7 @@ class Server:
         st = read_stats(b.ws, stream=b.stream)  # the batch has finished: no wait
         if st["status"] == DT_ERR_QUEUE_OVERFLOW:
             with torch.cuda.stream(b.stream):
-                b.ws = Workspace(min(max(2 * b.ws.capacity, int(1.3 * st["seg_needed"])), 2 ** 31 - 1), self.device)
+                b.ws = self._arena(b.stream, min(max(2 * b.ws.capacity, int(1.3 * st["seg_needed"])), 2 ** 31 - 1))
                 self._forward(b)
             return
         if st["status"] != DT_OK:
@@ -206,7 +230,7 @@ class Server:
                 from . import BatchTape
                 tape = BatchTape(b.ws, b.items, st)
                 nb = batch_backward_workspace_size(b.items, max(1, st["max_level"]))
-                _, bws = _aligned_empty(nb, dev)
+                bws = self._scratch(b.stream, nb)
                 b.gouts = render_batch_backward(tape, grads, bws=bws, stream=b.stream)
                 b.losses = losses
                 self.launches += 1
@@ -255,8 +279,10 @@ class Server:
     def run(self, requests, timeout: float = 600.0):
         """Serve `requests` (sorted by arrival time, seconds from start) in
         open loop: each becomes pending at its arrival time.  Returns the
-        finished requests."""
+        finished requests.  A server can run several streams of requests one
+        after another; its arenas and learned sizes carry over."""
         self.t0 = time.perf_counter()
+        self.done, self.launches = [], 0
         todo = collections.deque(sorted(requests, key=lambda r: r.arrival))
         total = len(todo)
         while len(self.done) < total:
