@@ -697,6 +697,46 @@ def batch_leg(args, dt, dev, steps):
     }
 
 
+def summary_digest(out: dict) -> dict:
+    """The headline numbers of every workload of one bench line, rounded."""
+    def r(x, n=3):
+        return None if x is None else round(float(x), n)
+
+    g = {"fwd_bwd_gseg_s": r(out["value"] / 1e9), "fwd_gseg_s": r(out["fwd_segments_per_s"] / 1e9),
+         "ms_per_step": r(out["ms_per_step"], 2),
+         "e2e_gseg_s": r(out["e2e"]["value"] / 1e9) if out.get("e2e") else None,
+         "k_trace_ms_per_launch": r(out["roofline"]["ms_per_launch"]), "k_trace_hbm_frac": r(out["roofline"]["frac"]),
+         "k_trace_l2_frac": r((out["roofline"].get("l2") or {}).get("frac"))}
+    lg = out.get("large")
+    if lg:
+        g["large"] = {"ckpt_ms": r(lg["checkpoint"]["ms_per_step"], 2), "full_ms": r(lg["full"]["ms_per_step"], 2),
+                      "gseg_s": r(lg["checkpoint"]["segments_per_s"] / 1e9), "rebuild_ms": lg["checkpoint"]["rebuild_ms"],
+                      "mesh_update_ms": r(lg["mesh_update"]["ms"], 2),
+                      "opt_step_ms": r(lg["mesh_update"]["optimisation_step_ms"], 2)}
+    b = out.get("batch")
+    if b:
+        g["batch"] = {"one_launch_ms": r(b["batched_ms"], 2), "graph_ms": r(b["graph_ms"], 2),
+                      "one_scene_per_launch_ms": r(b["plain_ms"], 2), "gseg_s": r(b["graph_segments_per_s"] / 1e9)}
+    c = out.get("c0")
+    if c:
+        g["c0"] = {"eager_ms_per_frame": c["eager_ms_per_frame"], "graph_ms_per_frame": c["graph_ms_per_frame"]}
+    m = out.get("medium")
+    if m:
+        g["medium_ms"] = {k: m[k]["ms_per_step"] for k in ("sigma_only", "sigma_only_env_grad", "medium", "hash_texture")
+                          if isinstance(m.get(k), dict)}
+    pl = out.get("paper_loss")
+    if pl:
+        g["paper_loss_ms"] = r(pl["ms"])
+    sv = out.get("serve")
+    if sv and sv.get("rates"):
+        g["serve"] = {"[p50, p99] ms, req/s: batched | one per launch": None}
+        for rate, e in sv["rates"].items():
+            bb, oo = e["batched"], e["one_per_launch"]
+            g["serve"][rate] = [bb["p50_ms"], bb["p99_ms"], bb["requests_per_s"], "|", oo["p50_ms"], oo["p99_ms"],
+                                oo["requests_per_s"]]
+    return g
+
+
 def rank_cameras(n_views: int, world: int, rank: int, res: int):
     """The views of one rank: every world-th view of a Fibonacci set of
     n_views * world, so ranks hold disjoint sets of the same size (weak
@@ -1014,6 +1054,9 @@ def run_ours(args):
             "c0": c0,
             "serve": serving,
         }
+        # a compact digest of every workload last, so that a log tail that
+        # keeps only the end of the line still shows each of them
+        out["summary"] = summary_digest(out)
         print(json.dumps(out))
     if world > 1:
         tdist.destroy_process_group()

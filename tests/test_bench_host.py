@@ -57,3 +57,30 @@ def test_kernel_sources_hash_follows_the_kernel_files(bench):
     h = bench.kernel_sources_hash("k_trace")
     assert h == bench.kernel_sources_hash("k_shade")  # the same translation unit
     assert len(h) == 16 and h != bench.kernel_sources_hash("k_adjoint")
+
+
+def test_summary_digest_keeps_every_workload_short(bench):
+    """The digest printed last on the bench line: the headline numbers of each
+    workload that ran, None-safe for workloads left out, and short enough for
+    a log tail of 1500 characters to hold it whole."""
+    rates = {str(r): {"batched": {"p50_ms": 3.0, "p99_ms": 12.0, "requests_per_s": float(r)},
+                      "one_per_launch": {"p50_ms": 3.1, "p99_ms": 14.0, "requests_per_s": float(r)}}
+             for r in (10, 30, 100, 300, 1000, 2000)}
+    leg = {"ms_per_step": 50.9, "segments_per_s": 1.2e9, "rebuild_ms": 4.5}
+    out = {"value": 3.27e9, "fwd_segments_per_s": 3.9e9, "ms_per_step": 37.35, "e2e": {"value": 3.28e9},
+           "roofline": {"ms_per_launch": 2.8, "frac": 0.049, "l2": {"frac": 0.47}},
+           "large": {"checkpoint": leg, "full": leg, "mesh_update": {"ms": 6.9, "optimisation_step_ms": 57.9}},
+           "batch": {"batched_ms": 26.1, "graph_ms": 25.9, "plain_ms": 109.9, "graph_segments_per_s": 2.3e9},
+           "c0": {"eager_ms_per_frame": 0.27, "graph_ms_per_frame": 0.245},
+           "medium": {"sigma_only": {"ms_per_step": 37.2}, "hash_texture": {"ms_per_step": 461.0}, "clocks": None},
+           "paper_loss": {"ms": 0.21}, "serve": {"rates": rates}}
+    g = bench.summary_digest(out)
+    assert g["fwd_bwd_gseg_s"] == 3.27 and g["e2e_gseg_s"] == 3.28
+    assert g["large"]["ckpt_ms"] == 50.9 and g["batch"]["graph_ms"] == 25.9 and g["c0"]["graph_ms_per_frame"] == 0.245
+    assert set(g["medium_ms"]) == {"sigma_only", "hash_texture"}
+    assert [k for k in g["serve"] if k[0].isdigit()] == ["10", "30", "100", "300", "1000", "2000"]
+    assert len(json.dumps(g)) < 1400
+    bare = {k: out[k] for k in ("value", "fwd_segments_per_s", "ms_per_step", "roofline")}
+    bare.update(e2e=None, large=None, batch=None, c0=None, medium=None, paper_loss=None, serve=None)
+    g = bench.summary_digest(bare)
+    assert g["e2e_gseg_s"] is None and "large" not in g and "serve" not in g
