@@ -546,7 +546,6 @@ def medium_leg(args, dt, dev):
     texture = dt.HashTexture(torch.from_numpy(tex["table"]).to(dev), tex["res"], lo, hi, tex["step"])
     bvh = dt.build_bvh(V, F)
     N = dt.vertex_normals(V, F)
-    params = dt.Params(args.depth)
     res = args.res
     stream = torch.cuda.current_stream()
     gen = torch.Generator(device=dev)
@@ -558,9 +557,14 @@ def medium_leg(args, dt, dev):
            "grid_nodes": g ** 3, "step": med["step"],
            "hash_texture_config": {"levels": args.hash_levels, "entries_per_level": 1 << args.hash_log2_table,
                                    "res": tex["res"], "table_bytes": int(texture.mu.numel() * 4)}}
-    for mode in ("medium", "hash_texture", "sigma_only", "sigma_only_env_grad"):
-        m = {"medium": medium, "hash_texture": texture}.get(mode)
+    # *_moments: the same step on a tape that keeps the medium's moments
+    # (tape_mode 2: a medium pass marches each interior segment once, in the
+    # forward, and the backward reads no medium value)
+    for mode in ("medium", "medium_moments", "hash_texture", "hash_texture_moments", "sigma_only",
+                 "sigma_only_env_grad"):
+        m = {"medium": medium, "hash_texture": texture}.get(mode.replace("_moments", ""))
         want_env = mode == "sigma_only_env_grad"
+        params = dt.Params(args.depth, moments=mode.endswith("_moments"))
         img, tape = dt.render(V, F, bvh, N, ior, sigma, env, cams, res, res, params, medium=m)
         stats = tape.stats
         _, bws = dt._aligned_empty(dt.backward_workspace_size(stats["max_level"], V.shape[0]), dev)
@@ -722,7 +726,8 @@ def summary_digest(out: dict) -> dict:
         g["c0"] = {"eager_ms_per_frame": c["eager_ms_per_frame"], "graph_ms_per_frame": c["graph_ms_per_frame"]}
     m = out.get("medium")
     if m:
-        g["medium_ms"] = {k: m[k]["ms_per_step"] for k in ("sigma_only", "sigma_only_env_grad", "medium", "hash_texture")
+        g["medium_ms"] = {k: m[k]["ms_per_step"] for k in ("sigma_only", "sigma_only_env_grad", "medium",
+                                                           "medium_moments", "hash_texture", "hash_texture_moments")
                           if isinstance(m.get(k), dict)}
     pl = out.get("paper_loss")
     if pl:

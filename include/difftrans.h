@@ -219,6 +219,16 @@ typedef struct dt_views {
  *    more).  A level larger than level_capacity is dropped past that size
  *    and reported as DT_ERR_QUEUE_OVERFLOW with dt_stats.level_needed.
  *  level_capacity: segments per ring level (tape_mode 1 only; else 0).
+ *  tape_mode 2 keeps the full tape of tape_mode 0 and, for every segment that
+ *    runs inside the object of a scene with an absorption grid or hash
+ *    texture (Eq. 11 with a spatially varying rate), the medium's optical
+ *    depth S over the segment, dS/dt and the 3x3 derivatives of S with
+ *    respect to the segment's origin and direction (24 floats, 96 bytes per
+ *    segment of the arena).  A medium pass of its own computes them between
+ *    the traversal and the shading of each level, reading the medium once;
+ *    the shading takes S from there and the backward needs no medium value
+ *    (only the scatter of dJ/dG into the grid or table marches the segment).
+ *    Images and gradients are those of tape_mode 0 up to rounding order.
  *  The workspace must be sized for the same tape_mode and level_capacity
  *  (dt_render_workspace_size_ex) and the backward must be given the same
  *  params as the forward; all entries of a batch share them. */
@@ -252,7 +262,8 @@ typedef struct dt_params {
  * ------------------------------------------------------------------------ */
 dt_status dt_render_workspace_size(int64_t seg_capacity, size_t* ws_bytes);
 /* The same for a tape_mode (see dt_params): tape_mode 1 needs
- * 1 <= level_capacity <= seg_capacity. */
+ * 1 <= level_capacity <= seg_capacity; tape_mode 2 adds 96 bytes per
+ * segment (level_capacity ignored). */
 dt_status dt_render_workspace_size_ex(int64_t seg_capacity, int32_t tape_mode, int64_t level_capacity,
                                       size_t* ws_bytes);
 dt_status dt_render(const dt_scene* scene, const dt_views* views, const dt_params* params, float* d_out,
@@ -343,7 +354,7 @@ dt_status dt_render_batch_backward(const dt_batch_entry* entries, int32_t n, con
  * xyz, throughput W rgb, contribution W * E(d) rgb of a segment that escaped
  * -- Sec. 3.4 step 3 before the 1/spp of the pixel average -- and 0 for a
  * hit); available after a render with tape_mode 0 only (after tape_mode 1
- * nothing is written).  Sample index = (view*height*width + py*width + px)*spp + s; the
+ * or 2 nothing is written).  Sample index = (view*height*width + py*width + px)*spp + s; the
  * heap node id of a camera ray is 1 and the children of node m are 2m
  * (reflected) and 2m+1 (refracted).  Flag bits: 4 inside (hit from inside),
  * 8 total internal reflection, 16 backfacing shading normal, 128 hit at

@@ -313,26 +313,37 @@ class Params:
     queues on the tape and recovers the hits in the backward from the
     source triangle each spawned child carries
     (tape_mode 1); the hit ring then holds level_capacity records per level
-    (0: chosen from the workspace, else twice the camera rays)."""
+    (0: chosen from the workspace, else twice the camera rays).
+    moments=True (tape_mode 2) keeps the full tape plus, for the interior
+    segments of a scene with an absorption grid or hash texture, the
+    medium's optical depth and its derivatives (96 bytes per segment), so
+    the backward does not read the medium's values again."""
 
     def __init__(self, max_depth: int, spp: int = 1, jitter: int = 0, seed: int = 0, t_min: float = 1e-5,
-                 checkpoint: bool = False, level_capacity: int = 0):
+                 checkpoint: bool = False, level_capacity: int = 0, moments: bool = False):
+        if checkpoint and moments:
+            raise ValueError("a tape is either checkpointed or keeps the medium moments, not both")
         self.max_depth, self.spp, self.jitter, self.seed, self.t_min = max_depth, spp, jitter, seed, t_min
         self.checkpoint, self.level_capacity = bool(checkpoint), int(level_capacity)
+        self.moments = bool(moments)
 
     def c(self, level_capacity: int = None):
         ring = self.level_capacity if level_capacity is None else level_capacity
-        return DtParams(self.max_depth, self.spp, self.jitter, 1 if self.checkpoint else 0, self.seed & (2 ** 64 - 1),
+        mode = 1 if self.checkpoint else (2 if self.moments else 0)
+        return DtParams(self.max_depth, self.spp, self.jitter, mode, self.seed & (2 ** 64 - 1),
                         self.t_min, int(ring) if self.checkpoint else 0)
 
 
-def render_workspace_size(seg_capacity: int, level_capacity: int = 0) -> int:
+def render_workspace_size(seg_capacity: int, level_capacity: int = 0, moments: bool = False) -> int:
     """Bytes of a workspace for seg_capacity segments; level_capacity > 0
-    sizes a checkpointed one (hit ring of that many records per level)."""
+    sizes a checkpointed one (hit ring of that many records per level),
+    moments=True one that keeps the medium moments (tape_mode 2)."""
     b = c_size_t()
     if level_capacity > 0:
         _check(load_library().dt_render_workspace_size_ex(int(seg_capacity), 1, int(level_capacity),
                                                           ctypes.byref(b)))
+    elif moments:
+        _check(load_library().dt_render_workspace_size_ex(int(seg_capacity), 2, 0, ctypes.byref(b)))
     else:
         _check(load_library().dt_render_workspace_size(int(seg_capacity), ctypes.byref(b)))
     return b.value
@@ -348,10 +359,11 @@ class Workspace:
     """A caller-owned segment arena (the tape) for dt_render; level_capacity
     > 0 makes it a checkpointed one (hits of two levels only)."""
 
-    def __init__(self, seg_capacity: int, device, level_capacity: int = 0):
+    def __init__(self, seg_capacity: int, device, level_capacity: int = 0, moments: bool = False):
         self.capacity = int(seg_capacity)
         self.level_capacity = int(min(level_capacity, self.capacity)) if level_capacity > 0 else 0
-        self.bytes = render_workspace_size(self.capacity, self.level_capacity)
+        self.moments = bool(moments) and not self.level_capacity
+        self.bytes = render_workspace_size(self.capacity, self.level_capacity, self.moments)
         self._raw, self.buf = _aligned_empty(self.bytes, device)
 
 
@@ -481,7 +493,7 @@ def default_capacity(n_primary: int, max_depth: int) -> int:
 def _new_workspace(params: Params, n_primary: int, device, capacity: int = None, level_capacity: int = None):
     cap = default_capacity(n_primary, params.max_depth) if capacity is None else capacity
     if not params.checkpoint:
-        return Workspace(cap, device)
+        return Workspace(cap, device, moments=params.moments)
     ring = level_capacity or params.level_capacity or 2 * n_primary
     return Workspace(cap, device, level_capacity=max(ring, 1))
 
@@ -493,7 +505,7 @@ def _grow_workspace(ws: Workspace, params: Params, stats: dict, device):
     if stats["seg_needed"] > cap:
         cap = min(max(2 * cap, int(1.3 * stats["seg_needed"])), 2 ** 31 - 1)
     if not ws.level_capacity:
-        return Workspace(cap, device)
+        return Workspace(cap, device, moments=ws.moments)
     ring = ws.level_capacity
     if stats["level_needed"] > ring:
         ring = int(1.25 * stats["level_needed"])
@@ -503,6 +515,8 @@ def _grow_workspace(ws: Workspace, params: Params, stats: dict, device):
 def _effective_params(params: Params, ws: Workspace):
     if params.checkpoint and not ws.level_capacity:
         raise ValueError("a checkpointed render needs a workspace made with level_capacity > 0")
+    if params.moments != ws.moments:
+        raise ValueError("Params(moments=...) and the workspace's moments must agree")
     return params.c(ws.level_capacity if params.checkpoint else 0)
 
 
@@ -583,6 +597,8 @@ def dump_segments(tape: Tape, stream=None):
     W, contribution W * E(d) of an escaped segment or 0))."""
     if tape.ws.level_capacity:
         raise ValueError("a checkpointed tape keeps no hit records to dump")
+    if tape.ws.moments:
+        raise ValueError("dump_segments reads tapes of tape_mode 0 only (this one keeps medium moments)")
     stats = tape.stats if tape.stats is not None else read_stats(tape.ws, stream)
     n = stats["segments"]
     dev = tape.ws.buf.device
@@ -801,16 +817,19 @@ def render_batch(items, ws: Workspace = None, outs=None, stream=None, check: boo
     n0 = sum(it.n_primary for it in items)
     depth = max(it.params.max_depth for it in items)
     p0 = items[0].params
-    if any(it.params.checkpoint != p0.checkpoint for it in items):
-        raise ValueError("all items of a batch are checkpointed or none is")
+    if any(it.params.checkpoint != p0.checkpoint or it.params.moments != p0.moments for it in items):
+        raise ValueError("all items of a batch share the tape mode (checkpoint, moments)")
     if ws is None:
-        ws = _new_workspace(Params(depth, checkpoint=p0.checkpoint, level_capacity=p0.level_capacity), n0, dev)
+        ws = _new_workspace(Params(depth, checkpoint=p0.checkpoint, level_capacity=p0.level_capacity,
+                                   moments=p0.moments), n0, dev)
     if outs is None:
         outs = [torch.empty(it.cams.shape[0], it.height, it.width, 3, dtype=torch.float32, device=dev)
                 for it in items]
     while True:
         if p0.checkpoint and not ws.level_capacity:
             raise ValueError("a checkpointed render needs a workspace made with level_capacity > 0")
+        if p0.moments != ws.moments:
+            raise ValueError("Params(moments=...) and the workspace's moments must agree")
         arr = (DtBatchEntry * n)(*[it.entry(out=o, level_capacity=ws.level_capacity) for it, o in zip(items, outs)])
         _check(lib.dt_render_batch(arr, n, _ptr(ws.buf), ws.bytes, _stream(stream)))
         if not check:

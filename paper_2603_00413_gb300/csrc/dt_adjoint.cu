@@ -213,7 +213,12 @@ __global__ void __launch_bounds__(256, kAdjointMinBlocks) k_adjoint(WsView W, in
           tbar -= dot(aa, sigma);
           if (med) {
             sbar = -aa;
-            tbar += dot(sbar, medium_depth_dt<kGrid == 2>(medium_view(E, W.ent + sc), o, d, t));
+            // tape_mode 2: dS/dt kept by the forward's medium pass (unless it did not march this segment)
+            const bool kept = W.mom && !isnan(W.mom[kMomS * W.cap + a]);
+            const float3 Sdt = kept ? mk(W.mom[(kMomDt + 0) * W.cap + a], W.mom[(kMomDt + 1) * W.cap + a],
+                                         W.mom[(kMomDt + 2) * W.cap + a])
+                                    : medium_depth_dt<kGrid == 2>(medium_view(E, W.ent + sc), o, d, t);
+            tbar += dot(sbar, Sdt);
             side = make_float4(sbar.x, sbar.y, sbar.z, t);
           }
         }
@@ -331,7 +336,22 @@ __global__ void __launch_bounds__(256, 3) k_medium_adjoint(WsView W, int k, cons
     const SceneEntry& E = kBatch ? W.ent[sc] : E0;
     if (!E.mu) continue;
     float3 ob = mk(0.f, 0.f, 0.f), db = ob;
-    medium_backward<kHash>(medium_view(E, W.ent + sc), E.dmu, xyz(ro), xyz(rd), sv.w, mk(sv.x, sv.y, sv.z), ob, db);
+    const float3 sbar = mk(sv.x, sv.y, sv.z);
+    if (W.mom && !isnan(W.mom[kMomS * W.cap + a])) {
+      // tape_mode 2: the samples' motion from the forward's moments, so only
+      // the scatter into the table marches the segment
+      const float* M = W.mom + a;
+      const unsigned long long c = W.cap;
+      ob = mk(sbar.x * M[(kMomDo + 0) * c] + sbar.y * M[(kMomDo + 3) * c] + sbar.z * M[(kMomDo + 6) * c],
+              sbar.x * M[(kMomDo + 1) * c] + sbar.y * M[(kMomDo + 4) * c] + sbar.z * M[(kMomDo + 7) * c],
+              sbar.x * M[(kMomDo + 2) * c] + sbar.y * M[(kMomDo + 5) * c] + sbar.z * M[(kMomDo + 8) * c]);
+      db = mk(sbar.x * M[(kMomDd + 0) * c] + sbar.y * M[(kMomDd + 3) * c] + sbar.z * M[(kMomDd + 6) * c],
+              sbar.x * M[(kMomDd + 1) * c] + sbar.y * M[(kMomDd + 4) * c] + sbar.z * M[(kMomDd + 7) * c],
+              sbar.x * M[(kMomDd + 2) * c] + sbar.y * M[(kMomDd + 5) * c] + sbar.z * M[(kMomDd + 8) * c]);
+      if (E.dmu) medium_scatter<kHash>(medium_view(E, W.ent + sc), E.dmu, xyz(ro), xyz(rd), sv.w, sbar);
+    } else {
+      medium_backward<kHash>(medium_view(E, W.ent + sc), E.dmu, xyz(ro), xyz(rd), sv.w, sbar, ob, db);
+    }
     if (k > 0) {  // camera rays have no parent to hand (obar, dbar) to
       float3 L, o0, d0;
       out_cur.load(i, L, o0, d0);
@@ -549,8 +569,8 @@ void launch_write_table(const WsView& W, const TableHeader& th, const SceneEntry
 // the gradient pointers, zeroes the gradients, sweeps k = D..0, then the
 // vertex-normal adjoint of every scene.
 void launch_backward_table(const TableHeader& th, const SceneEntry* entries, const void* ws, unsigned long long cap,
-                           unsigned long long ring, void* bws, unsigned long long max_level, cudaStream_t s) {
-  WsView W = ws_view(ws, cap, ring);
+                           unsigned long long ring, bool mom, void* bws, unsigned long long max_level, cudaStream_t s) {
+  WsView W = ws_view(ws, cap, ring, mom);
   BwsLayout L(max_level, 0);
   const AdjRecords buf[2] = {L.records(bws, 0), L.records(bws, 1)};
   const int n = th.n;

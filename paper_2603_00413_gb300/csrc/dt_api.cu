@@ -30,9 +30,9 @@ void launch_refit(const float* V, const int32_t* F, int32_t nf, void* bvh, void*
 SceneEntry make_entry(const dt_scene& sc, const dt_views& vw, const dt_params& p, float* out);
 void finish_table(SceneEntry* entries, int n, TableHeader& th);
 void launch_forward_table(const TableHeader& th, const SceneEntry* entries, void* ws, unsigned long long cap,
-                          unsigned long long ring, cudaStream_t s);
+                          unsigned long long ring, bool mom, cudaStream_t s);
 void launch_backward_table(const TableHeader& th, const SceneEntry* entries, const void* ws, unsigned long long cap,
-                           unsigned long long ring, void* bws, unsigned long long max_level, cudaStream_t s);
+                           unsigned long long ring, bool mom, void* bws, unsigned long long max_level, cudaStream_t s);
 size_t backward_ws_bytes_table(unsigned long long max_level, const SceneEntry* entries, int n);
 void assign_dN(SceneEntry* entries, int n, void* bws, unsigned long long max_level);
 void launch_dump(const void* ws, unsigned long long cap, int32_t* si, float* sf, unsigned long long n,
@@ -137,12 +137,13 @@ ProfScope::~ProfScope() {
 
 // the largest segment capacity whose layout fits in ws_bytes, with a hit ring
 // of `ring` records per level parity (ring = 0: one hit record per segment)
-static unsigned long long cap_from_bytes(size_t ws_bytes, unsigned long long ring = 0) {
+// and, for tape_mode 2, the medium moments of every segment
+static unsigned long long cap_from_bytes(size_t ws_bytes, unsigned long long ring = 0, bool mom = false) {
   const size_t fixed = 1024 + kTableBytes + kOrderBytes + 4096 + (ring ? 2 * ring * 16 : 0);
   if (ws_bytes < fixed) return 0;
-  unsigned long long cap = (ws_bytes - fixed + 4096) / (ring ? 56 : 72);
+  unsigned long long cap = (ws_bytes - fixed + 4096) / ((ring ? 56 : 72) + (mom ? 4 * kMomFloats : 0));
   if (cap > 0x7fffffffull) cap = 0x7fffffffull;
-  while (cap > 0 && WsLayout(cap, ring).total > ws_bytes) --cap;
+  while (cap > 0 && WsLayout(cap, ring, mom).total > ws_bytes) --cap;
   return cap;
 }
 
@@ -190,7 +191,7 @@ static dt_status check_views_params(const dt_views* vw, const dt_params* p) {
     return set_error(DT_ERR_INVALID_ARG, "max_depth must be in [0, %d] (got %d)", kMaxDepth, p->max_depth);
   if (p->spp < 1) return set_error(DT_ERR_INVALID_ARG, "spp must be >= 1");
   if (!(p->t_min >= 0.0f)) return set_error(DT_ERR_INVALID_ARG, "t_min must be >= 0");
-  if (p->tape_mode != 0 && p->tape_mode != 1) return set_error(DT_ERR_INVALID_ARG, "tape_mode must be 0 or 1");
+  if (p->tape_mode < 0 || p->tape_mode > 2) return set_error(DT_ERR_INVALID_ARG, "tape_mode must be 0, 1 or 2");
   if (p->tape_mode == 1 && p->level_capacity < 1)
     return set_error(DT_ERR_INVALID_ARG, "tape_mode 1 needs level_capacity >= 1");
   const unsigned long long n0 = (unsigned long long)vw->n_views * vw->width * vw->height * p->spp;
@@ -271,12 +272,12 @@ dt_status dt_render_workspace_size_ex(int64_t seg_capacity, int32_t tape_mode, i
   if (seg_capacity < 1 || seg_capacity > 0x7fffffffll)
     return set_error(DT_ERR_INVALID_ARG, "seg_capacity must be in [1, 2^31-1]");
   if (!ws_bytes) return set_error(DT_ERR_INVALID_ARG, "ws_bytes is NULL");
-  if (tape_mode == 0) {
-    *ws_bytes = WsLayout((unsigned long long)seg_capacity).total;
+  if (tape_mode == 0 || tape_mode == 2) {
+    *ws_bytes = WsLayout((unsigned long long)seg_capacity, 0, tape_mode == 2).total;
     return DT_OK;
   }
   if (tape_mode != 1 || level_capacity < 1 || level_capacity > seg_capacity)
-    return set_error(DT_ERR_INVALID_ARG, "tape_mode must be 0 or 1, and tape_mode 1 needs 1 <= level_capacity "
+    return set_error(DT_ERR_INVALID_ARG, "tape_mode must be 0, 1 or 2, and tape_mode 1 needs 1 <= level_capacity "
                                          "<= seg_capacity");
   *ws_bytes = WsLayout((unsigned long long)seg_capacity, (unsigned long long)level_capacity).total;
   return DT_OK;
@@ -332,6 +333,7 @@ static dt_status check_entries(const dt_batch_entry* entries, int32_t n, bool ba
 static unsigned long long ring_of(const dt_batch_entry* entries) {
   return entries[0].params.tape_mode == 1 ? (unsigned long long)entries[0].params.level_capacity : 0ull;
 }
+static bool mom_of(const dt_batch_entry* entries) { return entries[0].params.tape_mode == 2; }
 
 dt_status dt_render_batch(const dt_batch_entry* entries, int32_t n, void* d_ws, size_t ws_bytes, dt_stream stream) {
   std::vector<SceneEntry> ent;
@@ -341,11 +343,12 @@ dt_status dt_render_batch(const dt_batch_entry* entries, int32_t n, void* d_ws, 
   if (!d_ws) return set_error(DT_ERR_INVALID_ARG, "workspace is NULL");
   if (!aligned(d_ws, 256)) return set_error(DT_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
   const unsigned long long ring = ring_of(entries);
-  const unsigned long long cap = cap_from_bytes(ws_bytes, ring);
+  const bool mom = mom_of(entries);
+  const unsigned long long cap = cap_from_bytes(ws_bytes, ring, mom);
   if (cap < th.n_samples)
     return set_error(DT_ERR_INVALID_ARG, "workspace holds %llu segments, fewer than the %u camera rays", cap,
                      th.n_samples);
-  launch_forward_table(th, ent.data(), d_ws, cap, ring, (cudaStream_t)stream);
+  launch_forward_table(th, ent.data(), d_ws, cap, ring, mom, (cudaStream_t)stream);
   return check_launch("dt_render");
 }
 
@@ -421,14 +424,15 @@ dt_status dt_render_batch_backward(const dt_batch_entry* entries, int32_t n, con
   if (st) return st;
   if (!d_ws || !d_bws) return set_error(DT_ERR_INVALID_ARG, "NULL workspace");
   const unsigned long long ring = ring_of(entries);
-  const unsigned long long cap = cap_from_bytes(ws_bytes, ring);
+  const bool mom = mom_of(entries);
+  const unsigned long long cap = cap_from_bytes(ws_bytes, ring, mom);
   if (cap == 0) return set_error(DT_ERR_INVALID_ARG, "workspace too small");
   if (max_level < 1) return set_error(DT_ERR_INVALID_ARG, "max_level must be >= 1");
   if (bws_bytes < backward_ws_bytes_table((unsigned long long)max_level, ent.data(), n))
     return set_error(DT_ERR_INVALID_ARG, "backward workspace smaller than its size query");
   if (!aligned(d_bws, 256)) return set_error(DT_ERR_INVALID_ARG, "backward workspace must be 256-byte aligned");
   assign_dN(ent.data(), n, d_bws, (unsigned long long)max_level);
-  launch_backward_table(th, ent.data(), d_ws, cap, ring, d_bws, (unsigned long long)max_level,
+  launch_backward_table(th, ent.data(), d_ws, cap, ring, mom, d_bws, (unsigned long long)max_level,
                         (cudaStream_t)stream);
   return check_launch("dt_render_backward");
 }

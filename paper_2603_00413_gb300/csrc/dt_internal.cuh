@@ -160,7 +160,7 @@ struct WsHeader {
   uint32_t fetch[kMaxLevels];        // work-fetch cursors of the trace kernels
   unsigned long long counters[16];   // see CNT_*
   uint32_t ring;                     // level capacity of the hit ring (tape_mode 1), 0 = every hit kept
-  uint32_t pad0;
+  uint32_t mom;                      // 1: the medium moments of tape_mode 2 follow the hit records
 };
 
 enum { CNT_HITS = 0, CNT_MISSES, CNT_DISCARDED, CNT_BACKFACING, CNT_TIR, CNT_NODES, CNT_TRIS, CNT_MEDIUM };
@@ -275,7 +275,18 @@ struct WsView {
   unsigned long long cap;
   uint32_t ring;  // 0: hit[a] for arena index a; else hit[(k & 1) ring + i] for position i in level k
   uint32_t* order_count;  // traversal order: kOrderCounters bucket counters, then the scan's span totals
+  float* mom;     // tape_mode 2: kMomFloats arrays of cap floats (medium moments, see below); else null
 };
+
+// tape_mode 2 keeps, for every interior segment of a scene with an absorption
+// grid or hash texture, the optical depth of the medium over the segment and
+// its derivatives, written by the forward's medium pass, so that neither the
+// shading pass nor the backward marches the medium again.  Array j of the
+// kMomFloats (mom[j cap + a] for arena index a): 0-2 S (per channel), 3-5
+// dS/dt, 6-14 dS_c/do_x..z (c = 0..2, row-major), 15-23 dS_c/dd_x..z.
+// S_0 = NaN marks a segment the pass did not march (it found it entering).
+constexpr int kMomFloats = 24;
+constexpr int kMomS = 0, kMomDt = 3, kMomDo = 6, kMomDd = 15;
 
 // Where the hit record of position i of level k (arena index a) lives.
 __device__ __forceinline__ size_t hit_slot(const WsView& W, int k, uint32_t a, uint32_t i) {
@@ -336,8 +347,8 @@ __device__ __forceinline__ void scene_order_box(const float4* __restrict__ node2
 // the segment capacity only.  ring = 0: one hit per segment; else a ring of
 // two levels of `ring` hits.
 struct WsLayout {
-  size_t off_table, off_order, off_o, off_d, off_w, off_child, off_flag, off_hit, total;
-  __host__ __device__ explicit WsLayout(unsigned long long cap, unsigned long long ring = 0) {
+  size_t off_table, off_order, off_o, off_d, off_w, off_child, off_flag, off_hit, off_mom, total;
+  __host__ __device__ explicit WsLayout(unsigned long long cap, unsigned long long ring = 0, bool mom = false) {
     off_table = 1024;
     off_order = off_table + kTableBytes;
     off_o = off_order + kOrderBytes;
@@ -346,19 +357,21 @@ struct WsLayout {
     off_child = align_up(off_w + cap * sizeof(float4), 256);
     off_flag = align_up(off_child + cap * sizeof(int32_t), 256);
     off_hit = align_up(off_flag + cap * sizeof(uint32_t), 256);
-    total = align_up(off_hit + (ring ? 2 * ring : cap) * sizeof(float4), 256);
+    off_mom = align_up(off_hit + (ring ? 2 * ring : cap) * sizeof(float4), 256);
+    total = align_up(off_mom + (mom ? cap * kMomFloats * sizeof(float) : 0), 256);
   }
 };
 static_assert(sizeof(WsHeader) <= 1024, "header must fit its slot");
 
-__host__ __device__ inline WsView ws_view(const void* base, unsigned long long cap, unsigned long long ring = 0) {
-  WsLayout L(cap, ring);
+__host__ __device__ inline WsView ws_view(const void* base, unsigned long long cap, unsigned long long ring = 0,
+                                          bool mom = false) {
+  WsLayout L(cap, ring, mom);
   char* b = (char*)base;
   TableHeader* th = (TableHeader*)(b + L.off_table);
   SceneEntry* ent = (SceneEntry*)(b + L.off_table + ((sizeof(TableHeader) + 255) / 256) * 256);
   return WsView{(WsHeader*)b, th, ent, (float4*)(b + L.off_o), (float4*)(b + L.off_d), (float4*)(b + L.off_w),
                 (float4*)(b + L.off_hit), (int32_t*)(b + L.off_child), (uint32_t*)(b + L.off_flag), cap,
-                (uint32_t)ring, (uint32_t*)(b + L.off_order)};
+                (uint32_t)ring, (uint32_t*)(b + L.off_order), mom ? (float*)(b + L.off_mom) : nullptr};
 }
 
 // Segments of level k that fit in the arena (and in the hit ring, if any).

@@ -268,44 +268,19 @@ __device__ __forceinline__ void medium_atomic4(float4* p, float3 v) {
   atomicAdd(p, make_float4(v.x, v.y, v.z, 0.f));
 }
 
-// Adjoint of the optical depth at fixed t: sbar = dJ/dS (per channel, one
-// value for the whole segment).  Adds dJ/do and dJ/dd to obar and dbar and,
-// when dmu is given, dJ/dG at the nodes: sbar times the sum over samples of
-// w_i times the corner's trilinear weight.  Since sbar is constant along the
-// segment, only those scalar sums are kept per corner, over consecutive
-// samples in the same cell (a step of half a cell puts about two samples in
-// each cell a ray crosses), and added with one atomic per node when the ray
-// leaves the cell.  The sample gradient needs only sbar . G at the corners.
-__device__ __forceinline__ void medium_flush(float4* p, int sx, int sy, float3 sbar, const float* acc) {
-  medium_atomic4(p, sbar * acc[0]);
-  medium_atomic4(p + 1, sbar * acc[1]);
-  medium_atomic4(p + sx, sbar * acc[2]);
-  medium_atomic4(p + sx + 1, sbar * acc[3]);
-  medium_atomic4(p + sy, sbar * acc[4]);
-  medium_atomic4(p + sy + 1, sbar * acc[5]);
-  medium_atomic4(p + sy + sx, sbar * acc[6]);
-  medium_atomic4(p + sy + sx + 1, sbar * acc[7]);
-}
+template <bool kHash>
+__device__ __forceinline__ void medium_scatter(const MediumView& g, float4* dmu, float3 o, float3 d, float t,
+                                               float3 sbar);
 
-// The adjoint of hash_depth, level by level as medium_backward below: per
-// sample the gradient of sbar . G_l from sbar . (corner values), per cell
-// the scalar weight sums, flushed into the cell's eight entries (hashed
-// corners that share an entry add) when the ray leaves the cell.
-__device__ __forceinline__ void hash_flush(float4* dmu, const GridLevel& L, uint32_t i, uint32_t j, uint32_t k,
-                                           float3 sbar, const float* acc) {
-#pragma unroll
-  for (int q = 0; q < 8; ++q) medium_atomic4(dmu + corner_entry(L, i, j, k, q), sbar * acc[q]);
-}
-
-__device__ __forceinline__ void hash_backward(const MediumView& g, float4* dmu, float3 o, float3 d, float t,
-                                              float3 sbar, float3& obar, float3& dbar) {
+// The samples' share of the adjoint of hash_depth, level by level: per
+// sample the gradient of sbar . G_l from sbar . (corner values).
+__device__ __forceinline__ void hash_backward(const MediumView& g, float3 o, float3 d, float t, float3 sbar,
+                                              float3& obar, float3& dbar) {
   const float h = g.step;
   const int m = medium_full_steps(t, h);
   const float r = t - (float)m * h;
   for (int l = 0; l < g.levels; ++l) {
     const GridLevel L = load_level(g.lev + l);
-    float acc[8];
-    uint32_t pi = ~0u, pj = 0, pk = 0;  // the cell whose sums are pending (pi = ~0: none)
     for (int i = 0; i <= m; ++i) {
       const float w = i < m ? h : r;
       const float s = i < m ? ((float)i + 0.5f) * h : (float)m * h + 0.5f * r;
@@ -323,80 +298,263 @@ __device__ __forceinline__ void hash_backward(const MediumView& g, float4* dmu, 
               (sv[7] - sv[3]) * (c.fx * c.fy)) * (c.free_z ? L.sz : 0.0f)) * w;
       obar = obar + gp;
       dbar = dbar + gp * s;
-      if (dmu) {
-        if (c.i != pi || c.j != pj || c.k != pk) {
-          if (pi != ~0u) hash_flush(dmu, L, pi, pj, pk, sbar, acc);
-          pi = c.i;
-          pj = c.j;
-          pk = c.k;
-#pragma unroll
-          for (int q = 0; q < 8; ++q) acc[q] = 0.f;
-        }
-        acc[0] += w * (ux * uy * uz);
-        acc[1] += w * (c.fx * uy * uz);
-        acc[2] += w * (ux * c.fy * uz);
-        acc[3] += w * (c.fx * c.fy * uz);
-        acc[4] += w * (ux * uy * c.fz);
-        acc[5] += w * (c.fx * uy * c.fz);
-        acc[6] += w * (ux * c.fy * c.fz);
-        acc[7] += w * (c.fx * c.fy * c.fz);
-      }
     }
-    if (dmu && pi != ~0u) hash_flush(dmu, L, pi, pj, pk, sbar, acc);
   }
 }
 
+// Adjoint of the optical depth at fixed t: sbar = dJ/dS (per channel, one
+// value for the whole segment).  Adds dJ/do and dJ/dd to obar and dbar
+// (the samples move with o and d; the gradient of sbar . G needs only sbar .
+// G at each sample's corners) and, when dmu is given, dJ/dG at the nodes or
+// entries (medium_scatter).
 template <bool kHash>
 __device__ __forceinline__ void medium_backward(const MediumView& g, float4* dmu, float3 o, float3 d, float t,
                                                 float3 sbar, float3& obar, float3& dbar) {
   if (kHash && g.levels) {
-    hash_backward(g, dmu, o, d, t, sbar, obar, dbar);
-    return;
+    hash_backward(g, o, d, t, sbar, obar, dbar);
+  } else {
+    const float h = g.step;
+    const int m = medium_full_steps(t, h);
+    const float r = t - (float)m * h;
+    const int sx = g.nx, sy = g.nx * g.ny;
+    for (int i = 0; i <= m; ++i) {
+      const float w = i < m ? h : r;
+      const float s = i < m ? ((float)i + 0.5f) * h : (float)m * h + 0.5f * r;
+      const GridCell c = grid_cell(g, o + d * s);
+      const float4* p = g.mu + c.base;
+      // sbar . G at the eight corners
+      const float s000 = dot(sbar, xyz(__ldg(p))), s100 = dot(sbar, xyz(__ldg(p + 1)));
+      const float s010 = dot(sbar, xyz(__ldg(p + sx))), s110 = dot(sbar, xyz(__ldg(p + sx + 1)));
+      const float s001 = dot(sbar, xyz(__ldg(p + sy))), s101 = dot(sbar, xyz(__ldg(p + sy + 1)));
+      const float s011 = dot(sbar, xyz(__ldg(p + sy + sx))), s111 = dot(sbar, xyz(__ldg(p + sy + sx + 1)));
+      const float ux = 1.0f - c.fx, uy = 1.0f - c.fy, uz = 1.0f - c.fz;
+      const float3 gp =
+          mk(((s100 - s000) * (uy * uz) + (s110 - s010) * (c.fy * uz) + (s101 - s001) * (uy * c.fz) +
+              (s111 - s011) * (c.fy * c.fz)) * (c.free_x ? g.scale.x : 0.0f),
+             ((s010 - s000) * (ux * uz) + (s110 - s100) * (c.fx * uz) + (s011 - s001) * (ux * c.fz) +
+              (s111 - s101) * (c.fx * c.fz)) * (c.free_y ? g.scale.y : 0.0f),
+             ((s001 - s000) * (ux * uy) + (s101 - s100) * (c.fx * uy) + (s011 - s010) * (ux * c.fy) +
+              (s111 - s110) * (c.fx * c.fy)) * (c.free_z ? g.scale.z : 0.0f)) * w;  // w dJ/dx at this sample
+      obar = obar + gp;
+      dbar = dbar + gp * s;
+    }
   }
-  const float h = g.step;
-  const int m = medium_full_steps(t, h);
-  const float r = t - (float)m * h;
-  const int sx = g.nx, sy = g.nx * g.ny;
-  float acc[8];
-  size_t cur = ~(size_t)0;
+  if (dmu) medium_scatter<kHash>(g, dmu, o, d, t, sbar);
+}
+
+// ---------------------------------------------------------------------------
+// tape_mode 2: the medium's moments in the forward, its scatter in the backward
+// ---------------------------------------------------------------------------
+// Everything the backward needs of the optical depth S over o + s d, s in
+// [0, t], at fixed t: S; dS/dt (the partial last step, as medium_depth_dt);
+// and the motion of the samples with o and d, whose adjoint is linear in
+// sbar = dJ/dS:
+//   dJ/do = sum_c sbar_c Do[c],  Do[c] = sum_i w_i grad G_c(x_i),
+//   dJ/dd = sum_c sbar_c Dd[c],  Dd[c] = sum_i w_i s_i grad G_c(x_i),
+// so the forward, which reads the corner values of every sample anyway,
+// keeps the two 3x3 sums and the backward needs no corner value at all.
+// gx, gy, gz of trilinear_grad are the columns dG/dx_a over the channels.
+//
+// The scatter of dJ/dG into the medium walks each level's cells along the
+// segment.  Consecutive samples share their cell, or step to a neighbouring
+// cell (at most one cell along each axis) with which it shares a face, an
+// edge or a vertex: the corners the two cells share keep their pending
+// weight sums, and only the corners the step leaves behind are flushed with
+// an atomic -- on the bench's hash texture about 40 % fewer atomics than
+// flushing the whole cell at every change.
+struct MediumMoments {
+  float3 S, dt;
+  float3 ox, oy, oz;  // columns of Do: dS/do_x, dS/do_y, dS/do_z (each over the channels)
+  float3 dx, dy, dz;  // columns of Dd
+};
+
+__device__ __forceinline__ void moments_sample(MediumMoments& M, float3 G, float3 gx, float3 gy, float3 gz, float w,
+                                               float s) {
+  M.S = M.S + G * w;
+  M.ox = M.ox + gx * w;
+  M.oy = M.oy + gy * w;
+  M.oz = M.oz + gz * w;
+  const float ws = w * s;
+  M.dx = M.dx + gx * ws;
+  M.dy = M.dy + gy * ws;
+  M.dz = M.dz + gz * ws;
+}
+
+// Corner q of a cell is (q & 1, (q >> 1) & 1, q >> 2).  For a step by
+// (dx, dy, dz), each in {-1, 0, 1}: the old corners the new cell does not
+// hold, and the new corners the old cell did not hold.
+__device__ __forceinline__ unsigned corners_left(int dx, int dy, int dz) {
+  return (dx > 0 ? 0x55u : 0u) | (dx < 0 ? 0xAAu : 0u) | (dy > 0 ? 0x33u : 0u) | (dy < 0 ? 0xCCu : 0u) |
+         (dz > 0 ? 0x0Fu : 0u) | (dz < 0 ? 0xF0u : 0u);
+}
+__device__ __forceinline__ unsigned corners_added(int dx, int dy, int dz) {
+  return (dx > 0 ? 0xAAu : 0u) | (dx < 0 ? 0x55u : 0u) | (dy > 0 ? 0xCCu : 0u) | (dy < 0 ? 0x33u : 0u) |
+         (dz > 0 ? 0xF0u : 0u) | (dz < 0 ? 0x0Fu : 0u);
+}
+
+// Moves the per-corner values of the old cell to the corners they are in
+// the new one (the added corners keep stale values: the caller refills or
+// clears them).  Axis by axis over the pairs of corners that differ in it.
+template <class T>
+__device__ __forceinline__ void shift_pairs(T (&v)[8], int dl, int bit) {
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    if (q & bit) continue;
+    const T a = v[q], b = v[q | bit];
+    v[q] = dl > 0 ? b : a;
+    v[q | bit] = dl < 0 ? a : b;
+  }
+}
+template <class T>
+__device__ __forceinline__ void shift_corners(T (&v)[8], int dx, int dy, int dz) {
+  shift_pairs(v, dx, 1);
+  shift_pairs(v, dy, 2);
+  shift_pairs(v, dz, 4);
+}
+
+__device__ __forceinline__ bool one_step(int dx, int dy, int dz) {
+  return dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1;
+}
+
+// Lattice coordinates of the dense grid's cell (clamping as grid_cell).
+struct GridIJK {
+  int i, j, k;
+  float fx, fy, fz;
+  bool free_x, free_y, free_z;
+};
+__device__ __forceinline__ GridIJK grid_ijk(const MediumView& g, float3 x) {
+  GridIJK c;
+  c.fx = grid_axis(x.x, g.lo.x, g.scale.x, g.nx, c.i, c.free_x);
+  c.fy = grid_axis(x.y, g.lo.y, g.scale.y, g.ny, c.j, c.free_y);
+  c.fz = grid_axis(x.z, g.lo.z, g.scale.z, g.nz, c.k, c.free_z);
+  return c;
+}
+__device__ __forceinline__ size_t grid_corner(const MediumView& g, int i, int j, int k, int q) {
+  return ((size_t)(k + (q >> 2)) * g.ny + (size_t)(j + ((q >> 1) & 1))) * g.nx + (size_t)(i + (q & 1));
+}
+
+// One level's (or the dense grid's) samples for the forward: each sample's
+// eight corner values, its G and gradient into the moments.  (Carrying the
+// shared corners' values from cell to cell, as the scatter below carries its
+// sums, read 60 % fewer entries but made this pass twice as slow: the
+// per-sample reads are independent of one another, the carried ones are
+// not.)
+template <class Cell, class Entry>
+__device__ __forceinline__ void moments_walk(MediumMoments& M, const float4* mu, float3 o, float3 d, float h, int m,
+                                             float r, float3 scale, const Cell& cell_of, const Entry& entry_of) {
   for (int i = 0; i <= m; ++i) {
     const float w = i < m ? h : r;
     const float s = i < m ? ((float)i + 0.5f) * h : (float)m * h + 0.5f * r;
-    const GridCell c = grid_cell(g, o + d * s);
-    const float4* p = g.mu + c.base;
-    // sbar . G at the eight corners
-    const float s000 = dot(sbar, xyz(__ldg(p))), s100 = dot(sbar, xyz(__ldg(p + 1)));
-    const float s010 = dot(sbar, xyz(__ldg(p + sx))), s110 = dot(sbar, xyz(__ldg(p + sx + 1)));
-    const float s001 = dot(sbar, xyz(__ldg(p + sy))), s101 = dot(sbar, xyz(__ldg(p + sy + 1)));
-    const float s011 = dot(sbar, xyz(__ldg(p + sy + sx))), s111 = dot(sbar, xyz(__ldg(p + sy + sx + 1)));
-    const float ux = 1.0f - c.fx, uy = 1.0f - c.fy, uz = 1.0f - c.fz;
-    const float3 gp =
-        mk(((s100 - s000) * (uy * uz) + (s110 - s010) * (c.fy * uz) + (s101 - s001) * (uy * c.fz) +
-            (s111 - s011) * (c.fy * c.fz)) * (c.free_x ? g.scale.x : 0.0f),
-           ((s010 - s000) * (ux * uz) + (s110 - s100) * (c.fx * uz) + (s011 - s001) * (ux * c.fz) +
-            (s111 - s101) * (c.fx * c.fz)) * (c.free_y ? g.scale.y : 0.0f),
-           ((s001 - s000) * (ux * uy) + (s101 - s100) * (c.fx * uy) + (s011 - s010) * (ux * c.fy) +
-            (s111 - s110) * (c.fx * c.fy)) * (c.free_z ? g.scale.z : 0.0f)) * w;  // w dJ/dx at this sample
-    obar = obar + gp;
-    dbar = dbar + gp * s;
-    if (dmu) {
-      if (c.base != cur) {
-        if (cur != ~(size_t)0) medium_flush(dmu + cur, sx, sy, sbar, acc);
-        cur = c.base;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) acc[q] = 0.f;
-      }
-      acc[0] += w * (ux * uy * uz);
-      acc[1] += w * (c.fx * uy * uz);
-      acc[2] += w * (ux * c.fy * uz);
-      acc[3] += w * (c.fx * c.fy * uz);
-      acc[4] += w * (ux * uy * c.fz);
-      acc[5] += w * (c.fx * uy * c.fz);
-      acc[6] += w * (ux * c.fy * c.fz);
-      acc[7] += w * (c.fx * c.fy * c.fz);
-    }
+    const auto c = cell_of(o + d * s);
+    CellNodes qn;
+    qn.c000 = xyz(__ldg(mu + entry_of(c, 0)));
+    qn.c100 = xyz(__ldg(mu + entry_of(c, 1)));
+    qn.c010 = xyz(__ldg(mu + entry_of(c, 2)));
+    qn.c110 = xyz(__ldg(mu + entry_of(c, 3)));
+    qn.c001 = xyz(__ldg(mu + entry_of(c, 4)));
+    qn.c101 = xyz(__ldg(mu + entry_of(c, 5)));
+    qn.c011 = xyz(__ldg(mu + entry_of(c, 6)));
+    qn.c111 = xyz(__ldg(mu + entry_of(c, 7)));
+    const float3 G = trilinear(qn, c);
+    float3 gx, gy, gz;
+    trilinear_grad(qn, c, scale, gx, gy, gz);
+    moments_sample(M, G, gx, gy, gz, w, s);
+    if (i == m) M.dt = M.dt + G + (gx * d.x + gy * d.y + gz * d.z) * (0.5f * r);
   }
-  if (dmu && cur != ~(size_t)0) medium_flush(dmu + cur, sx, sy, sbar, acc);
+}
+
+template <bool kHash>
+__device__ __forceinline__ MediumMoments medium_moments(const MediumView& g, float3 o, float3 d, float t) {
+  const float h = g.step;
+  const int m = medium_full_steps(t, h);
+  const float r = t - (float)m * h;
+  MediumMoments M;
+  M.S = M.dt = M.ox = M.oy = M.oz = M.dx = M.dy = M.dz = mk(0.f, 0.f, 0.f);
+  if (kHash && g.levels) {
+    for (int l = 0; l < g.levels; ++l) {
+      const GridLevel L = load_level(g.lev + l);
+      moments_walk(M, g.mu, o, d, h, m, r, mk(L.sx, L.sy, L.sz),
+                   [&](float3 x) { return level_cell(L, g.lo, x); },
+                   [&](const LevelCell& c, int q) { return corner_entry(L, c.i, c.j, c.k, q); });
+    }
+    return M;
+  }
+  moments_walk(M, g.mu, o, d, h, m, r, g.scale, [&](float3 x) { return grid_ijk(g, x); },
+               [&](const GridIJK& c, int q) { return grid_corner(g, c.i, c.j, c.k, q); });
+  return M;
+}
+
+// dJ/dG at the table entries (or grid nodes) for one segment: sbar times
+// the sum over samples of w_i times each corner's trilinear weight.  The
+// sums are kept per corner of the current cell and carried along shared
+// corners; a corner is added to its entry with one 128-bit atomic when the
+// walk leaves it (hashed corners that share an entry add).
+template <class Cell, class Entry>
+__device__ __forceinline__ void scatter_walk(float4* dmu, float3 o, float3 d, float h, int m, float r, float3 sbar,
+                                             const Cell& cell_of, const Entry& entry_of) {
+  float acc[8];
+  int pi = 0, pj = 0, pk = 0;
+  bool have = false;
+  for (int i = 0; i <= m; ++i) {
+    const float w = i < m ? h : r;
+    const float s = i < m ? ((float)i + 0.5f) * h : (float)m * h + 0.5f * r;
+    const auto c = cell_of(o + d * s);
+    const int dx = (int)c.i - pi, dy = (int)c.j - pj, dz = (int)c.k - pk;
+    if (!have || dx || dy || dz) {
+      unsigned fresh = 0xFFu;
+      if (have) {
+        const bool near = one_step(dx, dy, dz);
+        const unsigned left = near ? corners_left(dx, dy, dz) : 0xFFu;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (left & (1u << q)) medium_atomic4(dmu + entry_of(pi, pj, pk, q), sbar * acc[q]);
+        if (near) {
+          shift_corners(acc, dx, dy, dz);
+          fresh = corners_added(dx, dy, dz);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (fresh & (1u << q)) acc[q] = 0.f;
+      have = true;
+      pi = (int)c.i;
+      pj = (int)c.j;
+      pk = (int)c.k;
+    }
+    const float ux = 1.0f - c.fx, uy = 1.0f - c.fy, uz = 1.0f - c.fz;
+    acc[0] += w * (ux * uy * uz);
+    acc[1] += w * (c.fx * uy * uz);
+    acc[2] += w * (ux * c.fy * uz);
+    acc[3] += w * (c.fx * c.fy * uz);
+    acc[4] += w * (ux * uy * c.fz);
+    acc[5] += w * (c.fx * uy * c.fz);
+    acc[6] += w * (ux * c.fy * c.fz);
+    acc[7] += w * (c.fx * c.fy * c.fz);
+  }
+  if (have) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) medium_atomic4(dmu + entry_of(pi, pj, pk, q), sbar * acc[q]);
+  }
+}
+
+template <bool kHash>
+__device__ __forceinline__ void medium_scatter(const MediumView& g, float4* dmu, float3 o, float3 d, float t,
+                                               float3 sbar) {
+  const float h = g.step;
+  const int m = medium_full_steps(t, h);
+  const float r = t - (float)m * h;
+  if (kHash && g.levels) {
+    for (int l = 0; l < g.levels; ++l) {
+      const GridLevel L = load_level(g.lev + l);
+      scatter_walk(dmu, o, d, h, m, r, sbar, [&](float3 x) { return level_cell(L, g.lo, x); },
+                   [&](int i, int j, int k, int q) {
+                     return corner_entry(L, (uint32_t)i, (uint32_t)j, (uint32_t)k, q);
+                   });
+    }
+    return;
+  }
+  scatter_walk(dmu, o, d, h, m, r, sbar, [&](float3 x) { return grid_ijk(g, x); },
+               [&](int i, int j, int k, int q) { return grid_corner(g, i, j, k, q); });
 }
 
 }  // namespace dt

@@ -95,6 +95,7 @@ __global__ void k_camera(WsView W, unsigned long long capacity) {
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
     W.hdr->capacity = capacity;
     W.hdr->ring = W.ring;
+    W.hdr->mom = W.mom ? 1u : 0u;
     W.hdr->level_count[0] = W.th->n_samples;
     W.hdr->level_start[0] = 0;
   }
@@ -578,8 +579,14 @@ __global__ void __launch_bounds__(kShadeThreads, kShadeMinBlocks) k_shade(WsView
           shade_hit(xyz(ro), d, hh.x, hh.y, hh.z, v0, v1, v2, load3(E.N + 3 * i0), load3(E.N + 3 * i1),
                     load3(E.N + 3 * i2), ior, sigma, h);
           if (kGrid && E.mu && !h.entering) {  // Sec. 3.4 step 5 with the grid's optical depth
-            h.A = absorption_with_depth(sigma, hh.x, medium_depth<kGrid == 2>(medium_view(E, W.ent + scene), xyz(ro), d, hh.x));
-            c_med += (uint32_t)medium_full_steps(hh.x, E.gstep) + 1u;
+            // tape_mode 2: the medium pass has marched it (S_0 = NaN: not marched there)
+            float3 S = mk(NAN, 0.f, 0.f);
+            if (W.mom) S = mk(W.mom[(kMomS + 0) * W.cap + a], W.mom[(kMomS + 1) * W.cap + a], W.mom[(kMomS + 2) * W.cap + a]);
+            if (isnan(S.x)) {
+              S = medium_depth<kGrid == 2>(medium_view(E, W.ent + scene), xyz(ro), d, hh.x);
+              c_med += (uint32_t)medium_full_steps(hh.x, E.gstep) + 1u;
+            }
+            h.A = absorption_with_depth(sigma, hh.x, S);
           }
           fl = h.entering ? 0u : SF_INSIDE;
           if (h.backfacing) {
@@ -682,6 +689,50 @@ __global__ void __launch_bounds__(kShadeThreads, kShadeMinBlocks) k_shade(WsView
   if (__any_sync(kFull, overflow) && lane == 0) atomicOr(&H->status, ST_QUEUE_OVERFLOW);
 }
 
+// The medium pass of tape_mode 2, between the traversal and the shading of
+// level k: for every segment that hits from inside (the shading pass's test
+// of the geometric normal) in a scene with an absorption grid or hash
+// texture, the optical depth over the segment and its derivatives
+// (medium_moments) into the moments arrays; a segment found entering gets
+// S_0 = NaN, so a shading pass that rounds the test the other way marches
+// it itself.  A pass of its own: the march's accumulators need more
+// registers than the shading pass runs with.
+template <bool kBatch, bool kHash>
+__global__ void __launch_bounds__(256, 2) k_medium_forward(WsView W, int k, const SceneEntry E0) {
+  WsHeader* H = W.hdr;
+  const int n_scenes = kBatch ? W.th->n : 1;
+  const uint32_t n = level_size(H, k);
+  const uint32_t start = H->level_start[k];
+  const unsigned long long cap = W.cap;
+  float* __restrict__ M = W.mom;
+  uint32_t c_med = 0;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t a = start + i;
+    const float4 hh = W.hit[hit_slot(W, k, a, i)];
+    const int tri = __float_as_int(hh.w);
+    if (tri < 0) continue;
+    const float4 ro = W.ray_o[a], rd = W.ray_d[a];
+    const int scene = kBatch ? find_scene(W.th->starts, n_scenes, __float_as_uint(ro.w)) : 0;
+    const SceneEntry& E = kBatch ? W.ent[scene] : E0;
+    if (!E.mu || k >= E.max_depth) continue;
+    const int i0 = __ldg(E.F + 3 * tri), i1 = __ldg(E.F + 3 * tri + 1), i2 = __ldg(E.F + 3 * tri + 2);
+    const float3 v0 = load3(E.V + 3 * i0), v1 = load3(E.V + 3 * i1), v2 = load3(E.V + 3 * i2);
+    const float3 d = xyz(rd);
+    if (dot(d, cross(v1 - v0, v2 - v0)) < 0.0f) {  // entering: no medium on this segment
+      M[kMomS * cap + a] = NAN;
+      continue;
+    }
+    const MediumMoments m = medium_moments<kHash>(medium_view(E, W.ent + scene), xyz(ro), d, hh.x);
+    c_med += (uint32_t)medium_full_steps(hh.x, E.gstep) + 1u;
+    const float v[kMomFloats] = {m.S.x,  m.S.y,  m.S.z,  m.dt.x, m.dt.y, m.dt.z, m.ox.x, m.oy.x,
+                                 m.oz.x, m.ox.y, m.oy.y, m.oz.y, m.ox.z, m.oy.z, m.oz.z, m.dx.x,
+                                 m.dy.x, m.dz.x, m.dx.y, m.dy.y, m.dz.y, m.dx.z, m.dy.z, m.dz.z};
+#pragma unroll
+    for (int j = 0; j < kMomFloats; ++j) M[j * cap + a] = v[j];
+  }
+  warp_add_u64(&H->counters[CNT_MEDIUM], c_med);
+}
+
 // every segment of the arena, level by level, for parity checks
 // (15 floats per segment: t, b1, b2, origin, direction, throughput W and
 // an escaped segment's contribution W * E(d), which k_shade added to its
@@ -690,6 +741,7 @@ constexpr int kSegF = 15;
 __global__ void k_dump(WsView W, int32_t* __restrict__ si, float* __restrict__ sf, unsigned long long cap) {
   const WsHeader* H = W.hdr;
   if (H->ring) return;  // hit records of checkpointed renders are not kept
+  if (H->mom) return;   // a tape with medium moments has another layout than the one cap was derived for
   const int nl = (int)H->n_levels;
   const unsigned long long total = nl > 0 ? H->level_start[nl] : 0ull;
   const unsigned long long lim = total < cap ? total : cap;
@@ -765,8 +817,8 @@ void launch_write_table(const WsView& W, const TableHeader& th, const SceneEntry
 // then per depth one persistent traversal and one shading pass over the
 // segments of every scene together.
 void launch_forward_table(const TableHeader& th, const SceneEntry* entries, void* ws, unsigned long long cap,
-                          unsigned long long ring, cudaStream_t s) {
-  WsView W = ws_view(ws, cap, ring);
+                          unsigned long long ring, bool mom, cudaStream_t s) {
+  WsView W = ws_view(ws, cap, ring, mom);
   const int n = th.n;
   cudaMemsetAsync(ws, 0, 1024, s);
   launch_write_table(W, th, entries, n, s);
@@ -806,6 +858,17 @@ void launch_forward_table(const TableHeader& th, const SceneEntry* entries, void
       } else {
         if (batch) launch_trace_w<2, true>(bps, s, W, k, st, rf, E0, sorted);
         else launch_trace_w<2, false>(bps, s, W, k, st, rf, E0, sorted);
+      }
+    }
+    if (W.mom && th.any_medium) {
+      ProfScope ps("k_medium_forward", s);
+      const int mb = 8 * num_sms();
+      if (th.any_medium == 2) {
+        if (batch) k_medium_forward<true, true><<<mb, 256, 0, s>>>(W, k, E0);
+        else k_medium_forward<false, true><<<mb, 256, 0, s>>>(W, k, E0);
+      } else {
+        if (batch) k_medium_forward<true, false><<<mb, 256, 0, s>>>(W, k, E0);
+        else k_medium_forward<false, false><<<mb, 256, 0, s>>>(W, k, E0);
       }
     }
     {

@@ -148,9 +148,29 @@ def test_checkpointed_workspace_is_smaller_and_validated():
     assert full - ck == pytest.approx(16 * (cap - 2 * ring), abs=4096)
     b = ctypes.c_size_t()
     assert L.dt_render_workspace_size_ex(cap, 0, 0, ctypes.byref(b)) == dt.DT_OK and b.value == full
-    assert L.dt_render_workspace_size_ex(cap, 2, ring, ctypes.byref(b)) == dt.DT_ERR_INVALID_ARG
+    assert L.dt_render_workspace_size_ex(cap, 3, ring, ctypes.byref(b)) == dt.DT_ERR_INVALID_ARG
+    assert L.dt_render_workspace_size_ex(cap, -1, 0, ctypes.byref(b)) == dt.DT_ERR_INVALID_ARG
     assert L.dt_render_workspace_size_ex(cap, 1, 0, ctypes.byref(b)) == dt.DT_ERR_INVALID_ARG
     assert L.dt_render_workspace_size_ex(cap, 1, cap + 1, ctypes.byref(b)) == dt.DT_ERR_INVALID_ARG
+
+
+def test_moments_workspace_adds_96_bytes_per_segment():
+    """tape_mode 2 keeps the full tape and 24 floats of medium moments per
+    segment; the binding sizes it through the same query and refuses a
+    checkpointed tape that would also keep moments."""
+    import paper_2603_00413_gb300 as dt
+    L = dt.load_library()
+    cap = 10_000_000
+    full = dt.render_workspace_size(cap)
+    mom = dt.render_workspace_size(cap, moments=True)
+    assert mom - full == pytest.approx(96 * cap, abs=512)
+    b = ctypes.c_size_t()
+    assert L.dt_render_workspace_size_ex(cap, 2, 0, ctypes.byref(b)) == dt.DT_OK and b.value == mom
+    assert L.dt_render_workspace_size_ex(cap, 2, 12345, ctypes.byref(b)) == dt.DT_OK and b.value == mom
+    assert dt.Params(4, moments=True).c().tape_mode == 2
+    assert dt.Params(4).c().tape_mode == 0 and dt.Params(4, checkpoint=True).c(10).tape_mode == 1
+    with pytest.raises(ValueError):
+        dt.Params(4, checkpoint=True, moments=True)
 
 
 def test_python_calls_fail_loudly_without_the_library(tmp_path):

@@ -80,15 +80,22 @@ def _seed(gs, orc, rng, expected_excluded):
     return g
 
 
-def test_hash_texture_gradients_match_oracle_derivative():
+@pytest.mark.parametrize("moments", [False, True])
+def test_hash_texture_gradients_match_oracle_derivative(moments):
     """dJ/d(table entries) along two random directions, dJ/dIoR and
-    dJ/dsigma against the oracle's forward-mode derivative (view 0)."""
+    dJ/dsigma against the oracle's forward-mode derivative (view 0); with
+    the full tape, and with the tape that keeps the medium's moments from
+    the forward (tape_mode 2: the backward reads no table value)."""
     gs = _scene(32, 28, depth=5)
+    if moments:
+        p = gs.params
+        gs.params = dt.Params(p.max_depth, p.spp, p.jitter, p.seed, p.t_min, moments=True)
     tex = _texture(seed=8, levels=3, log2_table=9, n_min=5, n_max=14, scale=1.2)
     rng = np.random.default_rng(51)
     orc = _oracle(gs, tex)
     g = _seed(gs, orc, rng, 0.048)
     img, tape = gs.render(medium=_gpu_texture(tex))
+    assert_radiance_parity(img[0], orc, 0.048)
     dV, dior, dsig, dtab = dt.render_backward(tape, torch.from_numpy(g.astype(np.float32)).cuda())
     assert tuple(dtab.shape) == tex["table"].shape
     ot = _oracle_texture(tex)
@@ -194,3 +201,62 @@ def test_hash_texture_arguments_are_checked():
                  (torch.zeros(17, 64, 4, device="cuda"), [4] * 17)):
         with pytest.raises(ValueError):
             dt.HashTexture(args[0], args[1], LO, HI, 0.1)
+
+
+def test_moments_tape_equals_full_tape():
+    """tape_mode 2 (the medium pass keeps S, dS/dt and the derivatives of S
+    with respect to each interior segment's origin and direction) against
+    the full tape: the same images and, up to rounding order, the same
+    gradients of the vertices, IoR, sigma and the table or grid; alone and
+    in a batch of a hash texture, a dense grid and a scene without either."""
+    gs = _scene(24, 24, depth=6)
+    tex = _gpu_texture(_texture(seed=10, levels=4, log2_table=9, n_min=3, n_max=16))
+    med = S.random_absorption_grid((6, 5, 7), LO, HI, seed=10, scale=1.1)
+    grid = dt.Medium(torch.from_numpy(med["mu"]).cuda(), med["lo"], med["hi"], med["step"])
+    sc = S.glass_icosphere_scene(width=20, height=20)
+    ico = GpuScene(sc.V, sc.F, 1.5, np.array([0.4, 0.2, 0.1], np.float32), sc.env, sc.cams, 20, 20, 4)
+    rng = np.random.default_rng(54)
+    g0 = torch.from_numpy(rng.normal(size=(2, 24, 24, 3)).astype(np.float32)).cuda()
+    g1 = torch.from_numpy(rng.normal(size=(1, 20, 20, 3)).astype(np.float32)).cuda()
+
+    def with_moments(x):
+        y = copy.copy(x)
+        p = x.params
+        y.params = dt.Params(p.max_depth, p.spp, p.jitter, p.seed, p.t_min, moments=True)
+        return y
+
+    def close(x, y, tol):
+        x, y = x.cpu().numpy().astype(np.float64), y.cpu().numpy().astype(np.float64)
+        assert np.linalg.norm(x - y) <= tol * max(np.linalg.norm(y), 1e-12)
+
+    refs = []
+    for scene, m, g in ((gs, tex, g0), (ico, grid, g1), (ico, None, g1)):
+        a, ta = scene.render(medium=m)
+        b, tb = with_moments(scene).render(medium=m)
+        assert tb.ws.moments and not ta.ws.moments
+        assert ta.stats["segments"] == tb.stats["segments"]
+        assert ta.stats["medium_samples"] == tb.stats["medium_samples"]
+        np.testing.assert_allclose(b.cpu().numpy(), a.cpu().numpy(), rtol=2e-6, atol=1e-7)
+        ga, gb = dt.render_backward(ta, g), dt.render_backward(tb, g)
+        assert len(ga) == len(gb)
+        for x, y in zip(gb, ga):
+            close(x, y, 1e-5)
+        refs.append((a, ga))
+    p = gs.params
+    items = [dt.BatchItem(gs.V, gs.F, gs.bvh, gs.N, gs.ior, gs.sigma, gs.env, gs.cams, 24, 24,
+                          dt.Params(p.max_depth, moments=True), medium=tex)]
+    q = ico.params
+    for m in (grid, None):
+        items.append(dt.BatchItem(ico.V, ico.F, ico.bvh, ico.N, ico.ior, ico.sigma, ico.env, ico.cams, 20, 20,
+                                  dt.Params(q.max_depth, moments=True), medium=m))
+    imgs, btape = dt.render_batch(items)
+    assert btape.ws.moments
+    out = dt.render_batch_backward(btape, [g0, g1, g1])
+    for img, grads, (a, ga) in zip(imgs, out, refs):
+        np.testing.assert_allclose(img.cpu().numpy(), a.cpu().numpy(), rtol=1e-5, atol=1e-7)
+        for x, y in zip(grads, ga):
+            close(x, y, 1e-4)
+    with pytest.raises(ValueError):
+        dt.dump_segments(tb)
+    with pytest.raises(ValueError):
+        dt.Params(4, checkpoint=True, moments=True)
