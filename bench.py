@@ -78,6 +78,9 @@ def parse():
     ap.add_argument("--medium-grid", type=int, default=64, help="nodes per axis of the absorption grid")
     ap.add_argument("--medium-views", type=int, default=100)
     ap.add_argument("--medium-steps", type=int, default=5)
+    ap.add_argument("--medium-modes", type=str,
+                    default="medium,medium_moments,hash_texture,hash_texture_moments,sigma_only,sigma_only_env_grad",
+                    help="comma-separated modes of the absorption leg")
     ap.add_argument("--hash-levels", type=int, default=8, help="levels of the hash-texture absorption mode")
     ap.add_argument("--hash-log2-table", type=int, default=19, help="log2 of the entries per hash-texture level")
     ap.add_argument("--hash-res", type=str, default="16,128", help="nodes per axis of the coarsest,finest level")
@@ -560,12 +563,16 @@ def medium_leg(args, dt, dev):
     # *_moments: the same step on a tape that keeps the medium's moments
     # (tape_mode 2: a medium pass marches each interior segment once, in the
     # forward, and the backward reads no medium value)
-    for mode in ("medium", "medium_moments", "hash_texture", "hash_texture_moments", "sigma_only",
-                 "sigma_only_env_grad"):
+    for mode in args.medium_modes.split(","):
         m = {"medium": medium, "hash_texture": texture}.get(mode.replace("_moments", ""))
         want_env = mode == "sigma_only_env_grad"
         params = dt.Params(args.depth, moments=mode.endswith("_moments"))
         img, tape = dt.render(V, F, bvh, N, ior, sigma, env, cams, res, res, params, medium=m)
+        # the timed steps run in a workspace sized to the segments the render needs
+        ws = dt.Workspace(int(tape.stats["segments"] * 1.02) + 4096, dev, moments=params.moments)
+        del tape
+        torch.cuda.empty_cache()
+        img, tape = dt.render(V, F, bvh, N, ior, sigma, env, cams, res, res, params, ws=ws, out=img, medium=m)
         stats = tape.stats
         _, bws = dt._aligned_empty(dt.backward_workspace_size(stats["max_level"], V.shape[0]), dev)
         grad = torch.randn(img.shape, device=dev, generator=gen)
@@ -601,7 +608,7 @@ def medium_leg(args, dt, dev):
                      "grid_samples_per_step": int(stats["medium_samples"]),
                      "top_kernels_ms": {k: round(v[1] / args.medium_steps, 3) for k, v in top}}
         del tot
-        del tape, bws, img, grad
+        del tape, ws, bws, img, grad
         torch.cuda.empty_cache()
     return out
 

@@ -313,50 +313,90 @@ __global__ void __launch_bounds__(256, kAdjointMinBlocks) k_adjoint(WsView W, in
   }
 }
 
+template <bool kBatch, bool kHash>
+__device__ __forceinline__ void medium_adjoint_one(const WsView& W, int k, const AdjRecords& out_cur,
+                                                   const float4* __restrict__ med_side, const SceneEntry& E0,
+                                                   uint32_t start, int n_scenes, uint32_t i) {
+  const float4 sv = med_side[i];
+  const uint32_t a = start + i;
+  const float4 ro = W.ray_o[a], rd = W.ray_d[a];
+  const int sc = kBatch ? find_scene(W.th->starts, n_scenes, __float_as_uint(ro.w)) : 0;
+  const SceneEntry& E = kBatch ? W.ent[sc] : E0;
+  if (!E.mu) return;
+  float3 ob = mk(0.f, 0.f, 0.f), db = ob;
+  const float3 sbar = mk(sv.x, sv.y, sv.z);
+  if (W.mom && !isnan(W.mom[kMomS * W.cap + a])) {
+    // tape_mode 2: the samples' motion from the forward's moments, so only
+    // the scatter into the table marches the segment
+    const float* M = W.mom + a;
+    const unsigned long long c = W.cap;
+    ob = mk(sbar.x * M[(kMomDo + 0) * c] + sbar.y * M[(kMomDo + 3) * c] + sbar.z * M[(kMomDo + 6) * c],
+            sbar.x * M[(kMomDo + 1) * c] + sbar.y * M[(kMomDo + 4) * c] + sbar.z * M[(kMomDo + 7) * c],
+            sbar.x * M[(kMomDo + 2) * c] + sbar.y * M[(kMomDo + 5) * c] + sbar.z * M[(kMomDo + 8) * c]);
+    db = mk(sbar.x * M[(kMomDd + 0) * c] + sbar.y * M[(kMomDd + 3) * c] + sbar.z * M[(kMomDd + 6) * c],
+            sbar.x * M[(kMomDd + 1) * c] + sbar.y * M[(kMomDd + 4) * c] + sbar.z * M[(kMomDd + 7) * c],
+            sbar.x * M[(kMomDd + 2) * c] + sbar.y * M[(kMomDd + 5) * c] + sbar.z * M[(kMomDd + 8) * c]);
+    if (E.dmu) medium_scatter<kHash>(medium_view(E, W.ent + sc), E.dmu, xyz(ro), xyz(rd), sv.w, sbar);
+  } else {
+    medium_backward<kHash>(medium_view(E, W.ent + sc), E.dmu, xyz(ro), xyz(rd), sv.w, sbar, ob, db);
+  }
+  if (k > 0) {  // camera rays have no parent to hand (obar, dbar) to
+    float3 L, o0, d0;
+    out_cur.load(i, L, o0, d0);
+    out_cur.store(i, L, o0 + ob, d0 + db);
+  }
+}
+
 // The absorption grid's share of the adjoint of level k, after k_adjoint:
 // for each interior segment with a grid (side = (dJ/dS, t), t > 0) the
 // samples of its optical depth move with the segment's o and d at fixed t,
 // which adds to its adjoint record (read by the parent level next), and
 // dJ/dS goes to the grid's nodes.  A pass of its own, so the march and the
 // node atomics run at the occupancy of a small kernel.  kHash: some scene's
-// grid is a hash texture.
+// grid is a hash texture.  About half of a level's segments run inside the
+// object; a warp gathers the positions that do into a queue in shared
+// memory and marches them 32 at a time, so that its lanes are not left idle
+// beside the segments that need no march.
+constexpr int kMedAdjWarps = 8;
 template <bool kBatch, bool kHash>
-__global__ void __launch_bounds__(256, 3) k_medium_adjoint(WsView W, int k, const AdjRecords out_cur,
-                                                        const float4* __restrict__ med_side, const SceneEntry E0) {
+__global__ void __launch_bounds__(32 * kMedAdjWarps, 3) k_medium_adjoint(WsView W, int k, const AdjRecords out_cur,
+                                                                       const float4* __restrict__ med_side,
+                                                                       const SceneEntry E0) {
+  __shared__ uint32_t s_queue[kMedAdjWarps][64];
   const WsHeader* H = W.hdr;
   const int n_scenes = kBatch ? W.th->n : 1;
   const uint32_t n = level_size(H, k);
   const uint32_t start = H->level_start[k];
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const float4 sv = med_side[i];
-    if (!(sv.w > 0.f) || (sv.x == 0.f && sv.y == 0.f && sv.z == 0.f)) continue;  // no grid, or no gradient
-    const uint32_t a = start + i;
-    const float4 ro = W.ray_o[a], rd = W.ray_d[a];
-    const int sc = kBatch ? find_scene(W.th->starts, n_scenes, __float_as_uint(ro.w)) : 0;
-    const SceneEntry& E = kBatch ? W.ent[sc] : E0;
-    if (!E.mu) continue;
-    float3 ob = mk(0.f, 0.f, 0.f), db = ob;
-    const float3 sbar = mk(sv.x, sv.y, sv.z);
-    if (W.mom && !isnan(W.mom[kMomS * W.cap + a])) {
-      // tape_mode 2: the samples' motion from the forward's moments, so only
-      // the scatter into the table marches the segment
-      const float* M = W.mom + a;
-      const unsigned long long c = W.cap;
-      ob = mk(sbar.x * M[(kMomDo + 0) * c] + sbar.y * M[(kMomDo + 3) * c] + sbar.z * M[(kMomDo + 6) * c],
-              sbar.x * M[(kMomDo + 1) * c] + sbar.y * M[(kMomDo + 4) * c] + sbar.z * M[(kMomDo + 7) * c],
-              sbar.x * M[(kMomDo + 2) * c] + sbar.y * M[(kMomDo + 5) * c] + sbar.z * M[(kMomDo + 8) * c]);
-      db = mk(sbar.x * M[(kMomDd + 0) * c] + sbar.y * M[(kMomDd + 3) * c] + sbar.z * M[(kMomDd + 6) * c],
-              sbar.x * M[(kMomDd + 1) * c] + sbar.y * M[(kMomDd + 4) * c] + sbar.z * M[(kMomDd + 7) * c],
-              sbar.x * M[(kMomDd + 2) * c] + sbar.y * M[(kMomDd + 5) * c] + sbar.z * M[(kMomDd + 8) * c]);
-      if (E.dmu) medium_scatter<kHash>(medium_view(E, W.ent + sc), E.dmu, xyz(ro), xyz(rd), sv.w, sbar);
-    } else {
-      medium_backward<kHash>(medium_view(E, W.ent + sc), E.dmu, xyz(ro), xyz(rd), sv.w, sbar, ob, db);
+  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t* q = s_queue[wid];
+  const uint32_t warps = gridDim.x * kMedAdjWarps;
+  uint32_t cnt = 0;  // queued positions (warp-uniform, < 64)
+  for (uint32_t base = (blockIdx.x * kMedAdjWarps + wid) * 32u;; base += warps * 32u) {
+    const bool more = base < n;
+    if (more) {
+      const uint32_t i = base + lane;
+      bool v = false;
+      if (i < n) {
+        const float4 sv = med_side[i];
+        v = sv.w > 0.f && !(sv.x == 0.f && sv.y == 0.f && sv.z == 0.f);  // a grid, and a gradient
+      }
+      const unsigned b = __ballot_sync(kFull, v);
+      if (v) q[cnt + __popc(b & ((1u << lane) - 1u))] = i;
+      cnt += (uint32_t)__popc(b);
+      __syncwarp();
     }
-    if (k > 0) {  // camera rays have no parent to hand (obar, dbar) to
-      float3 L, o0, d0;
-      out_cur.load(i, L, o0, d0);
-      out_cur.store(i, L, o0 + ob, d0 + db);
+    while (cnt >= 32u || (!more && cnt > 0u)) {
+      const uint32_t take = cnt < 32u ? cnt : 32u;
+      if (lane < take) medium_adjoint_one<kBatch, kHash>(W, k, out_cur, med_side, E0, start, n_scenes, q[lane]);
+      __syncwarp();
+      const uint32_t rest = cnt - take;
+      const uint32_t x = lane < rest ? q[take + lane] : 0u;
+      __syncwarp();
+      if (lane < rest) q[lane] = x;
+      __syncwarp();
+      cnt = rest;
     }
+    if (!more) break;
   }
 }
 

@@ -696,39 +696,76 @@ __global__ void __launch_bounds__(kShadeThreads, kShadeMinBlocks) k_shade(WsView
 // (medium_moments) into the moments arrays; a segment found entering gets
 // S_0 = NaN, so a shading pass that rounds the test the other way marches
 // it itself.  A pass of its own: the march's accumulators need more
-// registers than the shading pass runs with.
+// registers than the shading pass runs with.  A warp classifies 32
+// positions at a time (hit, a medium, not at the depth limit, from inside),
+// queues the interior ones in shared memory and marches them 32 at a time,
+// so its lanes march together rather than beside lanes whose segment needs
+// no march.
+constexpr int kMedFwdWarps = 8;
 template <bool kBatch, bool kHash>
-__global__ void __launch_bounds__(256, 2) k_medium_forward(WsView W, int k, const SceneEntry E0) {
+__global__ void __launch_bounds__(32 * kMedFwdWarps, 2) k_medium_forward(WsView W, int k, const SceneEntry E0) {
+  __shared__ uint32_t s_queue[kMedFwdWarps][64];
   WsHeader* H = W.hdr;
   const int n_scenes = kBatch ? W.th->n : 1;
   const uint32_t n = level_size(H, k);
   const uint32_t start = H->level_start[k];
   const unsigned long long cap = W.cap;
   float* __restrict__ M = W.mom;
-  uint32_t c_med = 0;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const uint32_t a = start + i;
-    const float4 hh = W.hit[hit_slot(W, k, a, i)];
-    const int tri = __float_as_int(hh.w);
-    if (tri < 0) continue;
-    const float4 ro = W.ray_o[a], rd = W.ray_d[a];
-    const int scene = kBatch ? find_scene(W.th->starts, n_scenes, __float_as_uint(ro.w)) : 0;
-    const SceneEntry& E = kBatch ? W.ent[scene] : E0;
-    if (!E.mu || k >= E.max_depth) continue;
-    const int i0 = __ldg(E.F + 3 * tri), i1 = __ldg(E.F + 3 * tri + 1), i2 = __ldg(E.F + 3 * tri + 2);
-    const float3 v0 = load3(E.V + 3 * i0), v1 = load3(E.V + 3 * i1), v2 = load3(E.V + 3 * i2);
-    const float3 d = xyz(rd);
-    if (dot(d, cross(v1 - v0, v2 - v0)) < 0.0f) {  // entering: no medium on this segment
-      M[kMomS * cap + a] = NAN;
-      continue;
+  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t* q = s_queue[wid];
+  const uint32_t warps = gridDim.x * kMedFwdWarps;
+  uint32_t c_med = 0, cnt = 0;
+  for (uint32_t base = (blockIdx.x * kMedFwdWarps + wid) * 32u;; base += warps * 32u) {
+    const bool more = base < n;
+    if (more) {
+      const uint32_t i = base + lane;
+      bool v = false;
+      if (i < n) {
+        const uint32_t a = start + i;
+        const float4 hh = W.hit[hit_slot(W, k, a, i)];
+        const int tri = __float_as_int(hh.w);
+        if (tri >= 0) {
+          const float4 rd = W.ray_d[a];
+          const int scene = kBatch ? find_scene(W.th->starts, n_scenes, __float_as_uint(W.ray_o[a].w)) : 0;
+          const SceneEntry& E = kBatch ? W.ent[scene] : E0;
+          if (E.mu && k < E.max_depth) {
+            const int i0 = __ldg(E.F + 3 * tri), i1 = __ldg(E.F + 3 * tri + 1), i2 = __ldg(E.F + 3 * tri + 2);
+            const float3 v0 = load3(E.V + 3 * i0), v1 = load3(E.V + 3 * i1), v2 = load3(E.V + 3 * i2);
+            if (dot(xyz(rd), cross(v1 - v0, v2 - v0)) < 0.0f) M[kMomS * cap + a] = NAN;  // entering: no medium
+            else v = true;
+          }
+        }
+      }
+      const unsigned b = __ballot_sync(kFull, v);
+      if (v) q[cnt + __popc(b & ((1u << lane) - 1u))] = i;
+      cnt += (uint32_t)__popc(b);
+      __syncwarp();
     }
-    const MediumMoments m = medium_moments<kHash>(medium_view(E, W.ent + scene), xyz(ro), d, hh.x);
-    c_med += (uint32_t)medium_full_steps(hh.x, E.gstep) + 1u;
-    const float v[kMomFloats] = {m.S.x,  m.S.y,  m.S.z,  m.dt.x, m.dt.y, m.dt.z, m.ox.x, m.oy.x,
-                                 m.oz.x, m.ox.y, m.oy.y, m.oz.y, m.ox.z, m.oy.z, m.oz.z, m.dx.x,
-                                 m.dy.x, m.dz.x, m.dx.y, m.dy.y, m.dz.y, m.dx.z, m.dy.z, m.dz.z};
+    while (cnt >= 32u || (!more && cnt > 0u)) {
+      const uint32_t take = cnt < 32u ? cnt : 32u;
+      if (lane < take) {
+        const uint32_t i = q[lane], a = start + i;
+        const float4 hh = W.hit[hit_slot(W, k, a, i)];
+        const float4 ro = W.ray_o[a], rd = W.ray_d[a];
+        const int scene = kBatch ? find_scene(W.th->starts, n_scenes, __float_as_uint(ro.w)) : 0;
+        const SceneEntry& E = kBatch ? W.ent[scene] : E0;
+        const MediumMoments m = medium_moments<kHash>(medium_view(E, W.ent + scene), xyz(ro), xyz(rd), hh.x);
+        c_med += (uint32_t)medium_full_steps(hh.x, E.gstep) + 1u;
+        const float v[kMomFloats] = {m.S.x,  m.S.y,  m.S.z,  m.dt.x, m.dt.y, m.dt.z, m.ox.x, m.oy.x,
+                                     m.oz.x, m.ox.y, m.oy.y, m.oz.y, m.ox.z, m.oy.z, m.oz.z, m.dx.x,
+                                     m.dy.x, m.dz.x, m.dx.y, m.dy.y, m.dz.y, m.dx.z, m.dy.z, m.dz.z};
 #pragma unroll
-    for (int j = 0; j < kMomFloats; ++j) M[j * cap + a] = v[j];
+        for (int j = 0; j < kMomFloats; ++j) M[j * cap + a] = v[j];
+      }
+      __syncwarp();
+      const uint32_t rest = cnt - take;
+      const uint32_t x = lane < rest ? q[take + lane] : 0u;
+      __syncwarp();
+      if (lane < rest) q[lane] = x;
+      __syncwarp();
+      cnt = rest;
+    }
+    if (!more) break;
   }
   warp_add_u64(&H->counters[CNT_MEDIUM], c_med);
 }
