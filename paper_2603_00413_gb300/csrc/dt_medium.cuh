@@ -433,6 +433,28 @@ __device__ __forceinline__ size_t grid_corner(const MediumView& g, int i, int j,
   return ((size_t)(k + (q >> 2)) * g.ny + (size_t)(j + ((q >> 1) & 1))) * g.nx + (size_t)(i + (q & 1));
 }
 
+// G and its gradient together, sharing the interpolation's intermediate
+// values: the differences along x feed both the x interpolations and
+// dG/dx, the differences of the x-interpolated values along y feed the y
+// interpolations and dG/dy, and the difference of the two y-interpolated
+// values along z gives G and dG/dz (the derivatives of trilinear; about
+// half of the arithmetic of trilinear and trilinear_grad apart).
+template <class Cell>
+__device__ __forceinline__ float3 trilinear_value_grad(const CellNodes& q, const Cell& c, float3 scale, float3& gx,
+                                                       float3& gy, float3& gz) {
+  const float3 a00 = q.c100 - q.c000, a10 = q.c110 - q.c010, a01 = q.c101 - q.c001, a11 = q.c111 - q.c011;
+  const float3 x00 = q.c000 + a00 * c.fx, x10 = q.c010 + a10 * c.fx;
+  const float3 x01 = q.c001 + a01 * c.fx, x11 = q.c011 + a11 * c.fx;
+  const float3 b0 = x10 - x00, b1 = x11 - x01;
+  const float3 y0 = x00 + b0 * c.fy, y1 = x01 + b1 * c.fy;
+  const float3 e = y1 - y0;
+  const float3 ax0 = a00 + (a10 - a00) * c.fy, ax1 = a01 + (a11 - a01) * c.fy;
+  gx = (ax0 + (ax1 - ax0) * c.fz) * (c.free_x ? scale.x : 0.0f);
+  gy = (b0 + (b1 - b0) * c.fz) * (c.free_y ? scale.y : 0.0f);
+  gz = e * (c.free_z ? scale.z : 0.0f);
+  return y0 + e * c.fz;
+}
+
 // One level's (or the dense grid's) samples for the forward: each sample's
 // eight corner values, its G and gradient into the moments.  (Carrying the
 // shared corners' values from cell to cell, as the scatter below carries its
@@ -455,9 +477,8 @@ __device__ __forceinline__ void moments_walk(MediumMoments& M, const float4* mu,
     qn.c101 = xyz(__ldg(mu + entry_of(c, 5)));
     qn.c011 = xyz(__ldg(mu + entry_of(c, 6)));
     qn.c111 = xyz(__ldg(mu + entry_of(c, 7)));
-    const float3 G = trilinear(qn, c);
     float3 gx, gy, gz;
-    trilinear_grad(qn, c, scale, gx, gy, gz);
+    const float3 G = trilinear_value_grad(qn, c, scale, gx, gy, gz);
     moments_sample(M, G, gx, gy, gz, w, s);
     if (i == m) M.dt = M.dt + G + (gx * d.x + gy * d.y + gz * d.z) * (0.5f * r);
   }
