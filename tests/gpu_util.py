@@ -221,7 +221,8 @@ def assert_segment_weights(gi, gf, oi, of, keys, view_offset=0):
 # ---------------------------------------------------------------------------
 EVENTS = O.SEG_INSIDE | O.SEG_TIR | O.SEG_BACKFACING | O.SEG_DISCARDED | O.SEG_MISS
 # a step whose hit lies within 1e-6 of an edge or near-ties another: its hit
-# id is not defined to FP32 (the benchmark spec's edge exclusion)
+# id is not defined to FP32 (hit ids are compared bit for bit only away from
+# edges)
 STEP_EDGE = O.SEG_NEAR_EDGE | O.SEG_NEAR_TIE
 # a step whose inside/outside, TIR or backfacing decision, or whose
 # environment lookup, sits within 1e-6 of its threshold
