@@ -368,9 +368,22 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_trace(WsView W, int k, int 
   ClosestHit h{INFINITY, 0.f, 0.f, -1};
   int stack[kTraceStack];
   // the warp's claimed batch [qb, qe) of the level's segments: one atomic on
-  // the level cursor per kTraceClaim segments, not one per refill
-  uint32_t qb = 0, qe = 0;
-  bool cursor_done = false;
+  // the level cursor per kTraceClaim segments, not one per refill.  Warp w
+  // starts with batch w of the level without an atomic, of B =
+  // min(kTraceClaim, ceil(n / warps)) segments; the cursor hands out the
+  // batches after the first of every warp.  A level smaller than
+  // kTraceClaim segments per warp is thus spread over every warp (a few
+  // thousand segments, as in a 64x64 frame, would otherwise sit in a few
+  // dozen warps whose rays run one after another), and a warp past its end
+  // leaves at once instead of queueing an atomic on the one cursor address.
+  const uint32_t warps = gridDim.x * blockDim.x / 32u;
+  uint32_t first = (n + warps - 1u) / warps;
+  if (first > (uint32_t)kTraceClaim) first = kTraceClaim;
+  const uint32_t static_span = warps * first;
+  uint32_t qb = ((blockIdx.x * blockDim.x + threadIdx.x) / 32u) * first, qe = qb + first;
+  if (qb > n) qb = n;
+  if (qe > n) qe = n;
+  bool cursor_done = static_span >= n;
   while (true) {
     const unsigned idle = __ballot_sync(kFull, !active);
     const int n_idle = __popc(idle);
@@ -379,7 +392,7 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_trace(WsView W, int k, int 
       uint32_t nb = 0;
       const bool claim = have < (uint32_t)n_idle && !cursor_done;
       if (claim) {
-        if (lane == 0) nb = atomicAdd(cursor, (uint32_t)kTraceClaim);
+        if (lane == 0) nb = atomicAdd(cursor, (uint32_t)kTraceClaim) + static_span;
         nb = __shfl_sync(kFull, nb, 0);
       }
       const uint32_t r = __popc(idle & lanes_below);
@@ -473,9 +486,21 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_trace(WsView W, int k, int 
       active = false;
     }
   }
-  warp_add_u64(&H->counters[CNT_NODES], nvis);
-  warp_add_u64(&H->counters[CNT_TRIS], ntest);
+  // the visit and test counts, summed over the CTA first: with a small level
+  // spread over every warp, one atomic per warp on these two addresses would
+  // queue thousands of atomics at the end of the launch
+  __shared__ unsigned long long s_count[2];
+  if (threadIdx.x == 0) s_count[0] = s_count[1] = 0ull;
+  __syncthreads();
+  const unsigned wv = __reduce_add_sync(kFull, nvis), wt = __reduce_add_sync(kFull, ntest);
+  if (lane == 0) {
+    if (wv) atomicAdd(&s_count[0], (unsigned long long)wv);
+    if (wt) atomicAdd(&s_count[1], (unsigned long long)wt);
+  }
   if (__any_sync(kFull, overflow) && lane == 0) atomicOr(&H->status, ST_STACK_OVERFLOW);
+  __syncthreads();
+  if (threadIdx.x == 0 && s_count[0]) atomicAdd(&H->counters[CNT_NODES], s_count[0]);
+  if (threadIdx.x == 1 && s_count[1]) atomicAdd(&H->counters[CNT_TRIS], s_count[1]);
 }
 
 // Closest hit of arbitrary rays (tooling and tests).
