@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_trace(WsView W, int k, int 
   // the warp's claimed batch [qb, qe) of the level's segments: one atomic on
   // the level cursor per kTraceClaim segments, not one per refill.  Warp w
   // starts with batch w of the level without an atomic, of B =
-  // min(kTraceClaim, ceil(n / warps)) segments; the cursor hands out the
+  // min(kTraceClaim, max(4, ceil(n / warps))) segments; the cursor hands out the
   // batches after the first of every warp.  A level smaller than
   // kTraceClaim segments per warp is thus spread over every warp (a few
   // thousand segments, as in a 64x64 frame, would otherwise sit in a few
@@ -378,6 +378,7 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_trace(WsView W, int k, int 
   // leaves at once instead of queueing an atomic on the one cursor address.
   const uint32_t warps = gridDim.x * blockDim.x / 32u;
   uint32_t first = (n + warps - 1u) / warps;
+  if (first < 4u) first = 4u;  // at least 4 rays a warp: one ray a warp leaves issue slots to idle lanes
   if (first > (uint32_t)kTraceClaim) first = kTraceClaim;
   const uint32_t static_span = warps * first;
   uint32_t qb = ((blockIdx.x * blockDim.x + threadIdx.x) / 32u) * first, qe = qb + first;
