@@ -66,14 +66,6 @@ __global__ void k_write_table_entries(SceneEntry* dst, const TableChunk src) {
   }
 }
 
-// zero every scene's image (blockIdx.y = scene)
-__global__ void k_zero_images(const SceneEntry* __restrict__ ent) {
-  const SceneEntry& E = ent[blockIdx.y];
-  const size_t n = (size_t)E.pix_count * 3;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    E.out[i] = 0.0f;
-}
-
 // Pixel of position q of a view's pixels in traversal order: bands of four
 // rows (the last one shorter when H is not a multiple of four), each taken
 // column by column, so that 32 consecutive positions of a full band cover
@@ -89,7 +81,9 @@ __device__ __forceinline__ uint32_t tiled_pixel(uint32_t q, uint32_t w, uint32_t
 // index g = sample_start + (view * H * W + py * W + px) * spp + s; the
 // samples of a view are laid out in the arena in tiled_pixel order (the
 // samples of a pixel together), so that a warp's camera rays are an 8x4
-// block of pixels rather than a row of 32.
+// block of pixels rather than a row of 32.  The thread of a pixel's first
+// sample also clears the pixel in the image the shading passes add to (one
+// launch less per render than a clearing kernel of its own).
 __global__ void k_camera(WsView W, unsigned long long capacity) {
   const SceneEntry& E = W.ent[blockIdx.y];
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
@@ -106,6 +100,10 @@ __global__ void k_camera(WsView W, unsigned long long capacity) {
     const uint32_t gp = l / (uint32_t)E.spp;
     const uint32_t view = gp / npix;
     const uint32_t p = tiled_pixel(gp % npix, (uint32_t)E.width, (uint32_t)E.height);
+    if (s == 0) {
+      float* px = E.out + 3 * ((size_t)view * npix + p);
+      px[0] = px[1] = px[2] = 0.0f;
+    }
     float jx = 0.5f, jy = 0.5f;
     if (E.jitter) jitter_offset(E.seed, view, p, s, jx, jy);
     float3 o, d;
@@ -885,17 +883,10 @@ void launch_forward_table(const TableHeader& th, const SceneEntry* entries, void
   const int n = th.n;
   cudaMemsetAsync(ws, 0, 1024, s);
   launch_write_table(W, th, entries, n, s);
-  uint32_t max_pix = 0, max_s = 0;
+  uint32_t max_s = 0;
   for (int i = 0; i < n; ++i) {
-    if (entries[i].pix_count > max_pix) max_pix = entries[i].pix_count;
     const uint32_t ns = entries[i].pix_count * (uint32_t)entries[i].spp;
     if (ns > max_s) max_s = ns;
-  }
-  int zb = (int)((3ull * max_pix + 255) / 256);
-  if (zb > 4 * num_sms()) zb = 4 * num_sms();
-  {
-    ProfScope ps("k_zero_images", s);
-    k_zero_images<<<dim3(zb > 0 ? zb : 1, n), 256, 0, s>>>(W.ent);
   }
   int cb = (int)((max_s + 255) / 256);
   if (cb > 4 * num_sms()) cb = 4 * num_sms();
