@@ -262,7 +262,7 @@ def run_reference(args):
 KERNELS_PER_SCOPE = {"k_vertex_normals": 2, "k_refit": 3, "k_camera": 1, "k_trace": 1,
                      "k_shade": 1, "k_order": 2, "order_clear": 0,
                      "k_l2_loss_grad": 1, "k_adjoint": 1, "k_face_normals_backward": 1, "lbvh_build": 21,
-                     "k_write_table": 2, "k_zero_grads": 1}
+                     "k_write_table": 1, "k_zero_grads": 1}
 
 
 def sah_levels(nf: int) -> int:

@@ -52,13 +52,17 @@ struct TableChunk {
 };
 static_assert(sizeof(TableChunk) <= 32764, "a table chunk must fit the kernel-parameter space");
 
-__global__ void k_write_table_header(TableHeader* dst, const TableHeader src) {
-  const uint32_t* a = reinterpret_cast<const uint32_t*>(&src);
-  uint32_t* b = reinterpret_cast<uint32_t*>(dst);
-  for (int i = threadIdx.x; i < (int)(sizeof(TableHeader) / 4); i += blockDim.x) b[i] = a[i];
-}
+static_assert(sizeof(TableChunk) + sizeof(TableHeader) + 64 <= 32764,
+              "the table header and a chunk must fit the kernel-parameter space together");
 
-__global__ void k_write_table_entries(SceneEntry* dst, const TableChunk src) {
+// One chunk of the table's entries, and with the first chunk the header.
+__global__ void k_write_table(TableHeader* hdst, const TableHeader hsrc, SceneEntry* dst, const TableChunk src,
+                              int with_header) {
+  if (with_header) {
+    const uint32_t* a = reinterpret_cast<const uint32_t*>(&hsrc);
+    uint32_t* b = reinterpret_cast<uint32_t*>(hdst);
+    for (int i = threadIdx.x; i < (int)(sizeof(TableHeader) / 4); i += blockDim.x) b[i] = a[i];
+  }
   const int words = (int)(sizeof(SceneEntry) / 4);
   for (int i = threadIdx.x; i < src.count * words; i += blockDim.x) {
     const int k = i / words, w = i % words;
@@ -864,13 +868,12 @@ static int traversal_limit(int32_t nf) { return 2 * n_int_of(nf) + 8; }
 // Writes the scene table (header + entries) into the workspace.
 void launch_write_table(const WsView& W, const TableHeader& th, const SceneEntry* entries, int n, cudaStream_t s) {
   ProfScope ps("k_write_table", s);
-  k_write_table_header<<<1, 256, 0, s>>>(W.th, th);
   for (int first = 0; first < n; first += kEntriesPerChunk) {
     TableChunk c;
     c.first = first;
     c.count = n - first < kEntriesPerChunk ? n - first : kEntriesPerChunk;
     for (int k = 0; k < c.count; ++k) c.e[k] = entries[first + k];
-    k_write_table_entries<<<1, 256, 0, s>>>(W.ent, c);
+    k_write_table<<<1, 256, 0, s>>>(W.th, th, W.ent, c, first == 0 ? 1 : 0);
   }
 }
 
