@@ -94,7 +94,7 @@ struct SceneSums {
 // true: each segment looks its scene up.  kGrid: 1 = some scene has an
 // absorption grid (dt_medium.cuh), whose optical depth interior segments add;
 // 2 = some scene's is a hash texture.
-constexpr int kAdjointMinBlocks = 4;  // CTAs of 256 per SM the register budget is sized for
+constexpr int kAdjointMinBlocks = 3;  // CTAs of 256 per SM the register budget is sized for (80 registers)
 
 // The attenuation A of an interior segment with an absorption grid, without
 // marching its optical depth again: the forward gave each child the
@@ -627,7 +627,7 @@ void launch_backward_table(const TableHeader& th, const SceneEntry* entries, con
     ProfScope ps("k_zero_grads", s);
     k_zero_grads<<<dim3(zb, n), 256, 0, s>>>(W.ent);
   }
-  const int blocks = g_tuning.shade_blocks_per_sm * num_sms();
+  const int blocks = kAdjointMinBlocks * num_sms();  // one wave of the resident CTAs
   const size_t smem = sizeof(float) * 4 * (size_t)n;
   float4* side = reinterpret_cast<float4*>((char*)bws + L.off_med);
   for (int k = th.max_depth; k >= 0; --k) {
