@@ -257,12 +257,15 @@ def test_views_params_and_batches_are_validated_on_the_host(lib):
     cases = [(dict(views__n_views=0), "n_views"), (dict(views__width=0), "n_views"),
              (dict(params__max_depth=31), "max_depth"), (dict(params__max_depth=-1), "max_depth"),
              (dict(params__spp=0), "spp"), (dict(params__t_min=-1.0), "t_min"),
-             (dict(params__tape_mode=2), "tape_mode"), (dict(params__tape_mode=1), "level_capacity"),
+             (dict(params__tape_mode=3), "tape_mode must be 0, 1 or 2"), (dict(params__tape_mode=1), "level_capacity"),
              (dict(views__n_views=1 << 12, views__width=1 << 10, views__height=1 << 10), "too many primary rays"),
              (dict(e__d_out=None), "d_out"), (dict(scene__nf=0), "nf >= 1")]
     for kw, words in cases:
         st, msg = status([entry(), entry(**kw)])
         assert st == dt.DT_ERR_INVALID_ARG and words in msg and "entry 1" in msg, (kw, msg)
+    # every entry valid on its own, but a full tape beside a moments tape
+    st, msg = status([entry(), entry(params__tape_mode=2)])
+    assert st == dt.DT_ERR_INVALID_ARG and "share tape_mode" in msg and "entry 1" in msg, msg
     st, msg = status([])
     assert st == dt.DT_ERR_INVALID_ARG and "batch size" in msg
     st, msg = status([entry()] * 257)
