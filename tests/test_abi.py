@@ -171,6 +171,13 @@ def test_moments_workspace_adds_96_bytes_per_segment():
     assert dt.Params(4).c().tape_mode == 0 and dt.Params(4, checkpoint=True).c(10).tape_mode == 1
     with pytest.raises(ValueError):
         dt.Params(4, checkpoint=True, moments=True)
+    # the parameters and the workspace must agree on the moments
+    from types import SimpleNamespace
+    plain, with_moments = SimpleNamespace(level_capacity=0, moments=False), SimpleNamespace(level_capacity=0, moments=True)
+    assert dt._effective_params(dt.Params(4, moments=True), with_moments).tape_mode == 2
+    for p, w in ((dt.Params(4, moments=True), plain), (dt.Params(4), with_moments)):
+        with pytest.raises(ValueError):
+            dt._effective_params(p, w)
 
 
 def test_python_calls_fail_loudly_without_the_library(tmp_path):
