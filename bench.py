@@ -120,6 +120,31 @@ def ncu_traffic(kernel: str, units_per_launch: float):
     return e.get("dram_bytes_per_unit") * units_per_launch
 
 
+def ncu_issue(kernel: str):
+    """(warp instructions per unit, threads active per instruction) of
+    `kernel` from the committed ncu summary, if it was taken on the current
+    sources of that kernel (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        e = json.load(open(path)).get(kernel)
+    except Exception:
+        return None
+    if not e or e.get("kernel_sources") != kernel_sources_hash(kernel) or "inst_per_unit" not in e:
+        return None
+    return float(e["inst_per_unit"]), float(e["threads_per_inst"])
+
+
+def issue_roofline(inst_per_unit: float, threads_per_inst: float, units_per_launch: float, ms_per_launch: float,
+                   n_sm: int, sm_mhz: float) -> dict:
+    """The instruction-issue rate of a launch against the chip's issue peak:
+    one warp instruction per cycle per scheduler, four schedulers per SM."""
+    achieved = inst_per_unit * units_per_launch / (ms_per_launch / 1000.0) / 1e9
+    peak = n_sm * 4 * sm_mhz * 1e6 / 1e9
+    return {"achieved": achieved, "peak": peak, "unit": "G warp-instructions/s", "frac": achieved / peak,
+            "instructions_per_segment": inst_per_unit, "threads_per_instruction": threads_per_inst,
+            "peak_source": f"{n_sm} SMs x 4 schedulers x {sm_mhz:.0f} MHz (median SM clock of the timed steps)"}
+
+
 def genus2_workload(n_views, res, depth, seed=1):
     from paper_2603_00413_gb300 import scenes as S
     sc, Vt = S.genus2_scene(n_views=n_views, width=res, height=res, max_depth=depth, seed=seed)
@@ -717,7 +742,8 @@ def summary_digest(out: dict) -> dict:
          "ms_per_step": r(out["ms_per_step"], 2),
          "e2e_gseg_s": r(out["e2e"]["value"] / 1e9) if out.get("e2e") else None,
          "k_trace_ms_per_launch": r(out["roofline"]["ms_per_launch"]), "k_trace_hbm_frac": r(out["roofline"]["frac"]),
-         "k_trace_l2_frac": r((out["roofline"].get("l2") or {}).get("frac"))}
+         "k_trace_l2_frac": r((out["roofline"].get("l2") or {}).get("frac")),
+         "k_trace_issue_frac": r((out["roofline"].get("issue") or {}).get("frac"))}
     lg = out.get("large")
     if lg:
         g["large"] = {"ckpt_ms": r(lg["checkpoint"]["ms_per_step"], 2), "full_ms": r(lg["full"]["ms_per_step"], 2),
@@ -924,6 +950,13 @@ def run_ours(args):
                 "l2": {"achieved": l2_achieved, "peak": l2_peak, "unit": "GB/s", "frac": l2_achieved / l2_peak,
                        "bytes_per_launch": l2_per_launch,
                        "peak_source": "measured in this run (dt_measure_l2_read_bandwidth, 32 MB x 200 passes, L1 bypassed, best of 5)"}}
+    # the traversal is bound by instruction issue (ncu: ~72 % issue-active at
+    # 4 % of HBM): its issue rate from the committed instruction count
+    iss = ncu_issue(dom)
+    if iss is not None:
+        sm_mhz = clk.summary().get("sm_mhz") or 2070.0
+        roofline["issue"] = issue_roofline(iss[0], iss[1], seg * args.steps / launches, per_launch_ms,
+                                           torch.cuda.get_device_properties(dev).multi_processor_count, sm_mhz)
     gpu_launches = int(sum(v[0] * KERNELS_PER_SCOPE.get(k, 1) for k, v in kt.items()))
     kernel_share = {k: round(v[1] / sum(x[1] for x in kt.values()), 4) for k, v in kt.items()}
 

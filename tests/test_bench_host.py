@@ -53,6 +53,24 @@ def test_ncu_traffic_scales_and_goes_stale(bench, tmp_path, monkeypatch):
     assert bench.ncu_traffic("k_trace", 1000.0) is None
 
 
+def test_issue_roofline_from_the_committed_instruction_count(bench, tmp_path, monkeypatch):
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "ncu_traffic.json").write_text(json.dumps(
+        {"k_trace": {"kernel_sources": "abc", "dram_bytes_per_unit": 75.0, "inst_per_unit": 180.0,
+                     "threads_per_inst": 16.0},
+         "k_shade": {"kernel_sources": "abc", "dram_bytes_per_unit": 110.0}}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_sources_hash", lambda k: "abc")
+    assert bench.ncu_issue("k_trace") == (180.0, 16.0)
+    assert bench.ncu_issue("k_shade") is None  # no instruction count captured
+    r = bench.issue_roofline(180.0, 16.0, 1e7, 2.0, 152, 2000.0)
+    assert r["peak"] == pytest.approx(1216.0) and r["achieved"] == pytest.approx(900.0)
+    assert r["frac"] == pytest.approx(900.0 / 1216.0)
+    monkeypatch.setattr(bench, "kernel_sources_hash", lambda k: "changed")
+    assert bench.ncu_issue("k_trace") is None
+
+
 def test_kernel_sources_hash_follows_the_kernel_files(bench):
     h = bench.kernel_sources_hash("k_trace")
     assert h == bench.kernel_sources_hash("k_shade")  # the same translation unit
