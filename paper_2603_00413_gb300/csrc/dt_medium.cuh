@@ -455,6 +455,32 @@ __device__ __forceinline__ float3 trilinear_value_grad(const CellNodes& q, const
   return y0 + e * c.fz;
 }
 
+// The eight corner entries of a level's cell, corner q = (q & 1, (q >> 1)
+// & 1, q >> 2) as corner_entry, with the per-axis terms formed once: the
+// dense index (k n + j) n + i plus 0, 1, n, n + 1, n^2, ...; or the hash
+// i ^ 2654435761 j ^ 805459861 k with (j + 1) 2654435761 = j 2654435761 +
+// 2654435761 in 32-bit arithmetic (likewise for k), so each corner is one
+// three-way XOR, a mask and the level's offset.
+__device__ __forceinline__ void level_corner_entries(const GridLevel& L, const LevelCell& c, size_t (&e)[8]) {
+  if (L.mask) {
+    const uint32_t x0 = c.i, x1 = c.i + 1u;
+    const uint32_t y0 = c.j * 2654435761u, y1 = y0 + 2654435761u;
+    const uint32_t z0 = c.k * 805459861u, z1 = z0 + 805459861u;
+    e[0] = L.off + ((x0 ^ y0 ^ z0) & L.mask);
+    e[1] = L.off + ((x1 ^ y0 ^ z0) & L.mask);
+    e[2] = L.off + ((x0 ^ y1 ^ z0) & L.mask);
+    e[3] = L.off + ((x1 ^ y1 ^ z0) & L.mask);
+    e[4] = L.off + ((x0 ^ y0 ^ z1) & L.mask);
+    e[5] = L.off + ((x1 ^ y0 ^ z1) & L.mask);
+    e[6] = L.off + ((x0 ^ y1 ^ z1) & L.mask);
+    e[7] = L.off + ((x1 ^ y1 ^ z1) & L.mask);
+  } else {
+    const uint32_t n = (uint32_t)L.n, b = L.off + (c.k * n + c.j) * n + c.i, nn = n * n;
+    e[0] = b; e[1] = b + 1u; e[2] = b + n; e[3] = b + n + 1u;
+    e[4] = b + nn; e[5] = b + nn + 1u; e[6] = b + nn + n; e[7] = b + nn + n + 1u;
+  }
+}
+
 // One level's (or the dense grid's) samples for the forward: each sample's
 // eight corner values, its G and gradient into the moments.  (Carrying the
 // shared corners' values from cell to cell, as the scatter below carries its
@@ -468,15 +494,17 @@ __device__ __forceinline__ void moments_walk(MediumMoments& M, const float4* mu,
     const float w = i < m ? h : r;
     const float s = i < m ? ((float)i + 0.5f) * h : (float)m * h + 0.5f * r;
     const auto c = cell_of(o + d * s);
+    size_t e[8];
+    entry_of(c, e);
     CellNodes qn;
-    qn.c000 = xyz(__ldg(mu + entry_of(c, 0)));
-    qn.c100 = xyz(__ldg(mu + entry_of(c, 1)));
-    qn.c010 = xyz(__ldg(mu + entry_of(c, 2)));
-    qn.c110 = xyz(__ldg(mu + entry_of(c, 3)));
-    qn.c001 = xyz(__ldg(mu + entry_of(c, 4)));
-    qn.c101 = xyz(__ldg(mu + entry_of(c, 5)));
-    qn.c011 = xyz(__ldg(mu + entry_of(c, 6)));
-    qn.c111 = xyz(__ldg(mu + entry_of(c, 7)));
+    qn.c000 = xyz(__ldg(mu + e[0]));
+    qn.c100 = xyz(__ldg(mu + e[1]));
+    qn.c010 = xyz(__ldg(mu + e[2]));
+    qn.c110 = xyz(__ldg(mu + e[3]));
+    qn.c001 = xyz(__ldg(mu + e[4]));
+    qn.c101 = xyz(__ldg(mu + e[5]));
+    qn.c011 = xyz(__ldg(mu + e[6]));
+    qn.c111 = xyz(__ldg(mu + e[7]));
     float3 gx, gy, gz;
     const float3 G = trilinear_value_grad(qn, c, scale, gx, gy, gz);
     moments_sample(M, G, gx, gy, gz, w, s);
@@ -496,12 +524,16 @@ __device__ __forceinline__ MediumMoments medium_moments(const MediumView& g, flo
       const GridLevel L = load_level(g.lev + l);
       moments_walk(M, g.mu, o, d, h, m, r, mk(L.sx, L.sy, L.sz),
                    [&](float3 x) { return level_cell(L, g.lo, x); },
-                   [&](const LevelCell& c, int q) { return corner_entry(L, c.i, c.j, c.k, q); });
+                   [&](const LevelCell& c, size_t (&e)[8]) { level_corner_entries(L, c, e); });
     }
     return M;
   }
   moments_walk(M, g.mu, o, d, h, m, r, g.scale, [&](float3 x) { return grid_ijk(g, x); },
-               [&](const GridIJK& c, int q) { return grid_corner(g, c.i, c.j, c.k, q); });
+               [&](const GridIJK& c, size_t (&e)[8]) {
+                 const size_t b = grid_corner(g, c.i, c.j, c.k, 0), sx = (size_t)g.nx, sy = (size_t)g.nx * g.ny;
+                 e[0] = b; e[1] = b + 1; e[2] = b + sx; e[3] = b + sx + 1;
+                 e[4] = b + sy; e[5] = b + sy + 1; e[6] = b + sy + sx; e[7] = b + sy + sx + 1;
+               });
   return M;
 }
 
