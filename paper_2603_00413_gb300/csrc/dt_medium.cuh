@@ -134,9 +134,7 @@ __device__ __forceinline__ int medium_full_steps(float t, float h) {
 // Instant-NGP's spatial hash of a lattice point (Mueller et al. 2022, Eq. 4
 // with d = 3): XOR of the coordinates times 1, 2654435761 and 805459861 in
 // 32-bit arithmetic; the level keeps its low bits (tables are powers of two).
-__device__ __forceinline__ uint32_t ingp_hash(uint32_t i, uint32_t j, uint32_t k) {
-  return i ^ (j * 2654435761u) ^ (k * 805459861u);
-}
+constexpr uint32_t kHashPrimeY = 2654435761u, kHashPrimeZ = 805459861u;
 
 // A level's cell containing x: fractions and clamping as grid_cell, and the
 // lattice coordinates of its (0, 0, 0) corner.
@@ -158,27 +156,45 @@ __device__ __forceinline__ LevelCell level_cell(const GridLevel& L, float3 lo, f
   return c;
 }
 
-// Table entry of the level's lattice point (i, j, k).
-__device__ __forceinline__ uint32_t level_entry(const GridLevel& L, uint32_t i, uint32_t j, uint32_t k) {
-  const uint32_t n = (uint32_t)L.n;
-  return L.off + (L.mask ? (ingp_hash(i, j, k) & L.mask) : ((k * n + j) * n + i));
-}
-
-// Corner q (x fastest, then y, then z) of the cell at (i, j, k).
-__device__ __forceinline__ uint32_t corner_entry(const GridLevel& L, uint32_t i, uint32_t j, uint32_t k, int q) {
-  return level_entry(L, i + (uint32_t)(q & 1), j + (uint32_t)((q >> 1) & 1), k + (uint32_t)(q >> 2));
+// The table entries of the eight corners of a level's cell at lattice point
+// (i, j, k), corner q = (i + (q & 1), j + ((q >> 1) & 1), k + (q >> 2)):
+// the level's first entry plus, when the lattice fits the table, the dense
+// index (k n + j) n + i (so the corners add 0, 1, n, n + 1, n^2, ...), else
+// the spatial hash masked to the table, with the per-axis terms formed once
+// ((j + 1) kHashPrimeY = j kHashPrimeY + kHashPrimeY in 32-bit arithmetic,
+// likewise for k), so each corner is one three-way XOR, a mask and an add.
+__device__ __forceinline__ void level_corner_entries(const GridLevel& L, const LevelCell& c, size_t (&e)[8]) {
+  if (L.mask) {
+    const uint32_t x0 = c.i, x1 = c.i + 1u;
+    const uint32_t y0 = c.j * kHashPrimeY, y1 = y0 + kHashPrimeY;
+    const uint32_t z0 = c.k * kHashPrimeZ, z1 = z0 + kHashPrimeZ;
+    e[0] = L.off + ((x0 ^ y0 ^ z0) & L.mask);
+    e[1] = L.off + ((x1 ^ y0 ^ z0) & L.mask);
+    e[2] = L.off + ((x0 ^ y1 ^ z0) & L.mask);
+    e[3] = L.off + ((x1 ^ y1 ^ z0) & L.mask);
+    e[4] = L.off + ((x0 ^ y0 ^ z1) & L.mask);
+    e[5] = L.off + ((x1 ^ y0 ^ z1) & L.mask);
+    e[6] = L.off + ((x0 ^ y1 ^ z1) & L.mask);
+    e[7] = L.off + ((x1 ^ y1 ^ z1) & L.mask);
+  } else {
+    const uint32_t n = (uint32_t)L.n, b = L.off + (c.k * n + c.j) * n + c.i, nn = n * n;
+    e[0] = b; e[1] = b + 1u; e[2] = b + n; e[3] = b + n + 1u;
+    e[4] = b + nn; e[5] = b + nn + 1u; e[6] = b + nn + n; e[7] = b + nn + n + 1u;
+  }
 }
 
 __device__ __forceinline__ CellNodes level_nodes(const float4* mu, const GridLevel& L, const LevelCell& c) {
+  size_t e[8];
+  level_corner_entries(L, c, e);
   CellNodes q;
-  q.c000 = xyz(__ldg(mu + corner_entry(L, c.i, c.j, c.k, 0)));
-  q.c100 = xyz(__ldg(mu + corner_entry(L, c.i, c.j, c.k, 1)));
-  q.c010 = xyz(__ldg(mu + corner_entry(L, c.i, c.j, c.k, 2)));
-  q.c110 = xyz(__ldg(mu + corner_entry(L, c.i, c.j, c.k, 3)));
-  q.c001 = xyz(__ldg(mu + corner_entry(L, c.i, c.j, c.k, 4)));
-  q.c101 = xyz(__ldg(mu + corner_entry(L, c.i, c.j, c.k, 5)));
-  q.c011 = xyz(__ldg(mu + corner_entry(L, c.i, c.j, c.k, 6)));
-  q.c111 = xyz(__ldg(mu + corner_entry(L, c.i, c.j, c.k, 7)));
+  q.c000 = xyz(__ldg(mu + e[0]));
+  q.c100 = xyz(__ldg(mu + e[1]));
+  q.c010 = xyz(__ldg(mu + e[2]));
+  q.c110 = xyz(__ldg(mu + e[3]));
+  q.c001 = xyz(__ldg(mu + e[4]));
+  q.c101 = xyz(__ldg(mu + e[5]));
+  q.c011 = xyz(__ldg(mu + e[6]));
+  q.c111 = xyz(__ldg(mu + e[7]));
   return q;
 }
 
@@ -286,8 +302,10 @@ __device__ __forceinline__ void hash_backward(const MediumView& g, float3 o, flo
       const float s = i < m ? ((float)i + 0.5f) * h : (float)m * h + 0.5f * r;
       const LevelCell c = level_cell(L, g.lo, o + d * s);
       float sv[8];  // sbar . G at the eight corners
+      size_t e[8];
+      level_corner_entries(L, c, e);
 #pragma unroll
-      for (int q = 0; q < 8; ++q) sv[q] = dot(sbar, xyz(__ldg(g.mu + corner_entry(L, c.i, c.j, c.k, q))));
+      for (int q = 0; q < 8; ++q) sv[q] = dot(sbar, xyz(__ldg(g.mu + e[q])));
       const float ux = 1.0f - c.fx, uy = 1.0f - c.fy, uz = 1.0f - c.fz;
       const float3 gp =
           mk(((sv[1] - sv[0]) * (uy * uz) + (sv[3] - sv[2]) * (c.fy * uz) + (sv[5] - sv[4]) * (uy * c.fz) +
@@ -455,32 +473,6 @@ __device__ __forceinline__ float3 trilinear_value_grad(const CellNodes& q, const
   return y0 + e * c.fz;
 }
 
-// The eight corner entries of a level's cell, corner q = (q & 1, (q >> 1)
-// & 1, q >> 2) as corner_entry, with the per-axis terms formed once: the
-// dense index (k n + j) n + i plus 0, 1, n, n + 1, n^2, ...; or the hash
-// i ^ 2654435761 j ^ 805459861 k with (j + 1) 2654435761 = j 2654435761 +
-// 2654435761 in 32-bit arithmetic (likewise for k), so each corner is one
-// three-way XOR, a mask and the level's offset.
-__device__ __forceinline__ void level_corner_entries(const GridLevel& L, const LevelCell& c, size_t (&e)[8]) {
-  if (L.mask) {
-    const uint32_t x0 = c.i, x1 = c.i + 1u;
-    const uint32_t y0 = c.j * 2654435761u, y1 = y0 + 2654435761u;
-    const uint32_t z0 = c.k * 805459861u, z1 = z0 + 805459861u;
-    e[0] = L.off + ((x0 ^ y0 ^ z0) & L.mask);
-    e[1] = L.off + ((x1 ^ y0 ^ z0) & L.mask);
-    e[2] = L.off + ((x0 ^ y1 ^ z0) & L.mask);
-    e[3] = L.off + ((x1 ^ y1 ^ z0) & L.mask);
-    e[4] = L.off + ((x0 ^ y0 ^ z1) & L.mask);
-    e[5] = L.off + ((x1 ^ y0 ^ z1) & L.mask);
-    e[6] = L.off + ((x0 ^ y1 ^ z1) & L.mask);
-    e[7] = L.off + ((x1 ^ y1 ^ z1) & L.mask);
-  } else {
-    const uint32_t n = (uint32_t)L.n, b = L.off + (c.k * n + c.j) * n + c.i, nn = n * n;
-    e[0] = b; e[1] = b + 1u; e[2] = b + n; e[3] = b + n + 1u;
-    e[4] = b + nn; e[5] = b + nn + 1u; e[6] = b + nn + n; e[7] = b + nn + n + 1u;
-  }
-}
-
 // One level's (or the dense grid's) samples for the forward: each sample's
 // eight corner values, its G and gradient into the moments.  (Carrying the
 // shared corners' values from cell to cell, as the scatter below carries its
@@ -558,9 +550,11 @@ __device__ __forceinline__ void scatter_walk(float4* dmu, float3 o, float3 d, fl
       if (have) {
         const bool near = one_step(dx, dy, dz);
         const unsigned left = near ? corners_left(dx, dy, dz) : 0xFFu;
+        size_t e[8];
+        entry_of(pi, pj, pk, e);
 #pragma unroll
         for (int q = 0; q < 8; ++q)
-          if (left & (1u << q)) medium_atomic4(dmu + entry_of(pi, pj, pk, q), sbar * acc[q]);
+          if (left & (1u << q)) medium_atomic4(dmu + e[q], sbar * acc[q]);
         if (near) {
           shift_corners(acc, dx, dy, dz);
           fresh = corners_added(dx, dy, dz);
@@ -585,8 +579,10 @@ __device__ __forceinline__ void scatter_walk(float4* dmu, float3 o, float3 d, fl
     acc[7] += w * (c.fx * c.fy * c.fz);
   }
   if (have) {
+    size_t e[8];
+    entry_of(pi, pj, pk, e);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) medium_atomic4(dmu + entry_of(pi, pj, pk, q), sbar * acc[q]);
+    for (int q = 0; q < 8; ++q) medium_atomic4(dmu + e[q], sbar * acc[q]);
   }
 }
 
@@ -600,14 +596,22 @@ __device__ __forceinline__ void medium_scatter(const MediumView& g, float4* dmu,
     for (int l = 0; l < g.levels; ++l) {
       const GridLevel L = load_level(g.lev + l);
       scatter_walk(dmu, o, d, h, m, r, sbar, [&](float3 x) { return level_cell(L, g.lo, x); },
-                   [&](int i, int j, int k, int q) {
-                     return corner_entry(L, (uint32_t)i, (uint32_t)j, (uint32_t)k, q);
+                   [&](int i, int j, int k, size_t (&e)[8]) {
+                     LevelCell c;
+                     c.i = (uint32_t)i;
+                     c.j = (uint32_t)j;
+                     c.k = (uint32_t)k;
+                     level_corner_entries(L, c, e);
                    });
     }
     return;
   }
   scatter_walk(dmu, o, d, h, m, r, sbar, [&](float3 x) { return grid_ijk(g, x); },
-               [&](int i, int j, int k, int q) { return grid_corner(g, i, j, k, q); });
+               [&](int i, int j, int k, size_t (&e)[8]) {
+                 const size_t b = grid_corner(g, i, j, k, 0), sx = (size_t)g.nx, sy = (size_t)g.nx * g.ny;
+                 e[0] = b; e[1] = b + 1; e[2] = b + sx; e[3] = b + sx + 1;
+                 e[4] = b + sy; e[5] = b + sy + 1; e[6] = b + sy + sx; e[7] = b + sy + sx + 1;
+               });
 }
 
 }  // namespace dt
