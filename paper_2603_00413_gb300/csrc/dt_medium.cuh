@@ -74,7 +74,7 @@ __device__ __forceinline__ GridCell grid_cell(const MediumView& g, float3 x) {
   c.fz = grid_axis(x.z, g.lo.z, g.scale.z, g.nz, k, c.free_z);
   c.sx = g.nx;
   c.sy = g.nx * g.ny;
-  c.base = ((size_t)k * g.ny + j) * g.nx + i;
+  c.base = ((uint32_t)k * (uint32_t)g.ny + (uint32_t)j) * (uint32_t)g.nx + (uint32_t)i;  // < 2^31 nodes (checked)
   return c;
 }
 
@@ -447,8 +447,9 @@ __device__ __forceinline__ GridIJK grid_ijk(const MediumView& g, float3 x) {
   c.fz = grid_axis(x.z, g.lo.z, g.scale.z, g.nz, c.k, c.free_z);
   return c;
 }
-__device__ __forceinline__ size_t grid_corner(const MediumView& g, int i, int j, int k, int q) {
-  return ((size_t)(k + (q >> 2)) * g.ny + (size_t)(j + ((q >> 1) & 1))) * g.nx + (size_t)(i + (q & 1));
+__device__ __forceinline__ uint32_t grid_corner(const MediumView& g, int i, int j, int k, int q) {
+  return ((uint32_t)(k + (q >> 2)) * (uint32_t)g.ny + (uint32_t)(j + ((q >> 1) & 1))) * (uint32_t)g.nx +
+         (uint32_t)(i + (q & 1));
 }
 
 // G and its gradient together, sharing the interpolation's intermediate
@@ -522,7 +523,7 @@ __device__ __forceinline__ MediumMoments medium_moments(const MediumView& g, flo
   }
   moments_walk(M, g.mu, o, d, h, m, r, g.scale, [&](float3 x) { return grid_ijk(g, x); },
                [&](const GridIJK& c, size_t (&e)[8]) {
-                 const size_t b = grid_corner(g, c.i, c.j, c.k, 0), sx = (size_t)g.nx, sy = (size_t)g.nx * g.ny;
+                 const uint32_t b = grid_corner(g, c.i, c.j, c.k, 0), sx = (uint32_t)g.nx, sy = sx * (uint32_t)g.ny;
                  e[0] = b; e[1] = b + 1; e[2] = b + sx; e[3] = b + sx + 1;
                  e[4] = b + sy; e[5] = b + sy + 1; e[6] = b + sy + sx; e[7] = b + sy + sx + 1;
                });
@@ -608,7 +609,7 @@ __device__ __forceinline__ void medium_scatter(const MediumView& g, float4* dmu,
   }
   scatter_walk(dmu, o, d, h, m, r, sbar, [&](float3 x) { return grid_ijk(g, x); },
                [&](int i, int j, int k, size_t (&e)[8]) {
-                 const size_t b = grid_corner(g, i, j, k, 0), sx = (size_t)g.nx, sy = (size_t)g.nx * g.ny;
+                 const uint32_t b = grid_corner(g, i, j, k, 0), sx = (uint32_t)g.nx, sy = sx * (uint32_t)g.ny;
                  e[0] = b; e[1] = b + 1; e[2] = b + sx; e[3] = b + sx + 1;
                  e[4] = b + sy; e[5] = b + sy + 1; e[6] = b + sy + sx; e[7] = b + sy + sx + 1;
                });
